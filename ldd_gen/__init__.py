@@ -1,0 +1,217 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module holds none of the decomposition's arithmetic.  It makes the two
+inputs of the method (Miller, Peng, Xu 2013): a symmetric int32 CSR graph
+(Definition 1.1: undirected, unweighted) and the shifts delta_u ~ Exp(beta)
+of Algorithm 2 step 1, drawn in FP64 from Philox4x32-10 (the counter layout
+is documented in ``gen.c``).  Everything is compiled C (``gen.c``), loaded
+with ctypes; the shared object is built on first use with gcc.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_LIB = os.path.join(_HERE, "libldd_gen.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into libldd_gen.so (gcc, OpenMP).  Returns the path."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, u64, u32, dbl = ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double
+        vp = ctypes.c_void_p
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        lib.ldd_philox4x32_10.argtypes = [vp, vp, vp]
+        lib.ldd_philox_stream.argtypes = [u64, u64, i64, u32, u32, vp]
+        lib.ldd_gen_uniforms.argtypes = [i64, u64, vp]
+        lib.ldd_gen_shifts.argtypes = [i64, dbl, u64, vp]
+        lib.ldd_grid2d_nnz.argtypes = [i64, i64]
+        lib.ldd_grid2d_nnz.restype = i64
+        lib.ldd_gen_grid2d.argtypes = [i64, i64, vp, vp]
+        lib.ldd_grid3d_nnz.argtypes = [i64, i64, i64]
+        lib.ldd_grid3d_nnz.restype = i64
+        lib.ldd_gen_grid3d.argtypes = [i64, i64, i64, vp, vp]
+        lib.ldd_gen_rmat.argtypes = [ctypes.c_int, i64, dbl, dbl, dbl, u64, pp, pp]
+        lib.ldd_gen_rmat.restype = i64
+        lib.ldd_gen_rgg.argtypes = [i64, dbl, u64, pp, pp]
+        lib.ldd_gen_rgg.restype = i64
+        lib.ldd_gen_free.argtypes = [vp]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------- random numbers
+def philox4x32_10(counter, key) -> np.ndarray:
+    """One Philox4x32-10 block: 4 uint32 words for a 4-word counter, 2-word key."""
+    c = np.ascontiguousarray(counter, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().ldd_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def philox_stream(seed: int, first: int, count: int, w2: int = 0, w3: int = 0) -> np.ndarray:
+    """Words for counters (i_lo, i_hi, w2, w3), i = first..first+count-1; shape (count, 4)."""
+    out = np.zeros((count, 4), dtype=np.uint32)
+    _load().ldd_philox_stream(seed, first, count, w2, w3, _ptr(out))
+    return out
+
+
+def uniforms(n: int, seed: int) -> np.ndarray:
+    """U_u in (0, 1], 53-bit, from the shift counter layout."""
+    out = np.empty(n, dtype=np.float64)
+    _load().ldd_gen_uniforms(n, seed, _ptr(out))
+    return out
+
+
+def shifts(n: int, beta: float, seed: int) -> np.ndarray:
+    """delta_u = -ln(U_u) / beta, FP64 (Algorithm 2 step 1; Section 2 CDF)."""
+    out = np.empty(n, dtype=np.float64)
+    _load().ldd_gen_shifts(n, float(beta), seed, _ptr(out))
+    return out
+
+
+# ---------------------------------------------------------------- graphs
+@dataclass
+class CSR:
+    """Symmetric int32 CSR.  ``m`` counts undirected edges (nnz // 2)."""
+    name: str
+    row_ptr: np.ndarray
+    col: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    @property
+    def m(self) -> int:
+        return self.nnz // 2
+
+
+def grid2d(nx: int, ny: int) -> CSR:
+    lib = _load()
+    nnz = lib.ldd_grid2d_nnz(nx, ny) if nx * ny > 0 else 0
+    rp = np.zeros(nx * ny + 1, dtype=np.int32)
+    col = np.zeros(max(nnz, 0), dtype=np.int32)
+    if nx * ny > 0:
+        lib.ldd_gen_grid2d(nx, ny, _ptr(rp), _ptr(col))
+    return CSR(f"grid2d_{nx}x{ny}", rp, col)
+
+
+def grid3d(nx: int, ny: int, nz: int) -> CSR:
+    lib = _load()
+    nnz = lib.ldd_grid3d_nnz(nx, ny, nz) if nx * ny * nz > 0 else 0
+    rp = np.zeros(nx * ny * nz + 1, dtype=np.int32)
+    col = np.zeros(max(nnz, 0), dtype=np.int32)
+    if nx * ny * nz > 0:
+        lib.ldd_gen_grid3d(nx, ny, nz, _ptr(rp), _ptr(col))
+    return CSR(f"grid3d_{nx}x{ny}x{nz}", rp, col)
+
+
+def _take(n: int, nnz: int, rp_p, col_p, name: str) -> CSR:
+    lib = _load()
+    if nnz < 0:
+        raise MemoryError(f"{name}: generator failed")
+    rp = np.ctypeslib.as_array(ctypes.cast(rp_p, ctypes.POINTER(ctypes.c_int32)), shape=(n + 1,)).copy()
+    col = (np.ctypeslib.as_array(ctypes.cast(col_p, ctypes.POINTER(ctypes.c_int32)), shape=(nnz,)).copy()
+           if nnz > 0 else np.zeros(0, dtype=np.int32))
+    lib.ldd_gen_free(rp_p)
+    lib.ldd_gen_free(col_p)
+    return CSR(name, rp, col)
+
+
+def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         seed: int = 7) -> CSR:
+    """R-MAT, symmetrised, self-loops and duplicate arcs removed, rows ascending."""
+    rp_p, col_p = ctypes.c_void_p(), ctypes.c_void_p()
+    nnz = _load().ldd_gen_rmat(scale, edge_factor, a, b, c, seed, ctypes.byref(rp_p), ctypes.byref(col_p))
+    return _take(1 << scale, nnz, rp_p, col_p, f"rmat{scale}_ef{edge_factor}_s{seed}")
+
+
+def rgg(n: int, seed: int, mean_degree: float = 8.0) -> CSR:
+    """Random geometric graph in [0,1)^2 with radius sqrt(mean_degree / (pi n))."""
+    radius = math.sqrt(mean_degree / (math.pi * n))
+    rp_p, col_p = ctypes.c_void_p(), ctypes.c_void_p()
+    nnz = _load().ldd_gen_rgg(n, radius, seed, ctypes.byref(rp_p), ctypes.byref(col_p))
+    return _take(n, nnz, rp_p, col_p, f"rgg{n}_s{seed}")
+
+
+def from_edges(n: int, edges, name: str = "edges") -> CSR:
+    """Symmetric CSR from an undirected edge list (self-loops and repeats dropped)."""
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        if u != v:
+            adj[u].add(v)
+            adj[v].add(u)
+    rp = np.zeros(n + 1, dtype=np.int32)
+    cols = []
+    for v in range(n):
+        nb = sorted(adj[v])
+        cols.extend(nb)
+        rp[v + 1] = rp[v] + len(nb)
+    return CSR(name, rp, np.asarray(cols, dtype=np.int32))
+
+
+def random_graph(n: int, p: float, seed: int) -> CSR:
+    """Erdos-Renyi G(n, p) from numpy's PCG64 (small test graphs only)."""
+    rng = np.random.default_rng(seed)
+    iu, ju = np.triu_indices(n, 1)
+    keep = rng.random(iu.shape[0]) < p
+    return from_edges(n, list(zip(iu[keep].tolist(), ju[keep].tolist())), f"gnp{n}_{p}_{seed}")
+
+
+# ---------------------------------------------------------------- named workloads
+WORKLOADS = {
+    # 2D 4-neighbour grid 256x256, beta 0.1, shift seed 1
+    "grid2d_256": dict(graph=("grid2d", 256, 256), betas=(0.1,), shift_seed=1),
+    # R-MAT scale 22, ef 16, (.57,.19,.19,.05), graph seed 7; beta in {0.02, 0.1, 0.5}
+    "rmat22": dict(graph=("rmat", 22, 16, 0.57, 0.19, 0.19, 7), betas=(0.02, 0.1, 0.5), shift_seed=1),
+    # 3D 6-neighbour grid 256^3, beta 0.01
+    "grid3d_256": dict(graph=("grid3d", 256, 256, 256), betas=(0.01,), shift_seed=1),
+}
+
+
+def make_graph(spec) -> CSR:
+    kind = spec[0]
+    if kind == "grid2d":
+        return grid2d(*spec[1:])
+    if kind == "grid3d":
+        return grid3d(*spec[1:])
+    if kind == "rmat":
+        return rmat(*spec[1:])
+    if kind == "rgg":
+        return rgg(*spec[1:])
+    raise ValueError(kind)

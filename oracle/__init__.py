@@ -1,0 +1,109 @@
+"""ORACLE -- test infrastructure only.
+
+Plain, slow, obviously-correct CPU implementations of the exponential-shift
+low-diameter decomposition (Miller, Peng, Xu 2013).  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference leg
+may import this package; the CUDA library never does, and the two share no
+code.  The only common dependency is ``ldd_gen`` (seeded inputs).
+
+* ``oracle_ldd``       -- multi-source Dijkstra over exact labels (C, ldd_oracle.c):
+                          Algorithm 2 via the super-source reduction of Section 4.
+* ``oracle_cut_edges`` -- Definition 1.1's count of edges between pieces.
+* ``oracle_certify``   -- O(m) optimality certificate (Lemma 3.1 predecessor +
+                          non-improvability), usable at any size.
+* ``brute.brute_ldd``  -- Algorithm 2 written out literally: all-pairs BFS and
+                          an exact-rational argmin (tiny graphs only).
+
+Every function here is pinned in ``tests/test_oracle.py`` against values and
+properties fixed by the paper and by mathematics, not against itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ldd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CERT_CODES = {
+    0: "ok",
+    1: "center out of range or negative distance",
+    2: "center is not its own center at distance 0",
+    3: "no predecessor in the same piece at distance - 1 (Lemma 3.1)",
+    4: "improvable by the vertex's own start label -delta_v",
+    5: "improvable by a neighbour's label + 1",
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile ldd_oracle.c (gcc, single-threaded, -O2).  Returns the path."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-std=c11", _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp, i64 = ctypes.c_void_p, ctypes.c_int64
+            lib.oracle_ldd.argtypes = [i64, vp, vp, vp, vp, vp]
+            lib.oracle_ldd.restype = ctypes.c_int
+            lib.oracle_cut_edges.argtypes = [i64, vp, vp, vp]
+            lib.oracle_cut_edges.restype = i64
+            lib.oracle_certify.argtypes = [i64, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
+            lib.oracle_certify.restype = ctypes.c_int
+            _lib = lib
+        return _lib
+
+
+def _c(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def oracle_ldd(row_ptr, col, delta):
+    """(center, dist) int32 arrays: argmin_u dist(u,v) - delta_u, ties to smaller u."""
+    rp, prp = _c(row_ptr, np.int32)
+    cl, pcl = _c(col, np.int32)
+    dl, pdl = _c(delta, np.float64)
+    n = rp.shape[0] - 1
+    center = np.empty(n, dtype=np.int32)
+    dist = np.empty(n, dtype=np.int32)
+    rc = _load().oracle_ldd(n, prp, pcl, pdl, center.ctypes.data, dist.ctypes.data)
+    if rc == -1:
+        raise ValueError("shifts must be finite and >= 0")
+    if rc != 0:
+        raise MemoryError("oracle_ldd allocation failed")
+    return center, dist
+
+
+def oracle_cut_edges(row_ptr, col, center) -> int:
+    rp, prp = _c(row_ptr, np.int32)
+    cl, pcl = _c(col, np.int32)
+    ce, pce = _c(center, np.int32)
+    return int(_load().oracle_cut_edges(rp.shape[0] - 1, prp, pcl, pce))
+
+
+def oracle_certify(row_ptr, col, delta, center, dist):
+    """(code, bad_vertex); code 0 means (center, dist) is the exact optimum."""
+    rp, prp = _c(row_ptr, np.int32)
+    cl, pcl = _c(col, np.int32)
+    dl, pdl = _c(delta, np.float64)
+    ce, pce = _c(center, np.int32)
+    di, pdi = _c(dist, np.int32)
+    bad = ctypes.c_int64(-1)
+    code = _load().oracle_certify(rp.shape[0] - 1, prp, pcl, pdl, pce, pdi, ctypes.byref(bad))
+    return int(code), int(bad.value)
