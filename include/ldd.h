@@ -1,0 +1,148 @@
+/*
+ * ldd.h -- C ABI of the GB300 (sm_103a) exponential-shift low-diameter
+ * decomposition library (libldd.so).
+ *
+ * Method: Miller, Peng, Xu, "Parallel Graph Decompositions Using Random
+ * Shifts" (2013).  Every vertex u carries a shift delta_u ~ Exp(beta)
+ * (Algorithm 2 step 1); every vertex v joins the center u minimising the
+ * shifted distance dist(u, v) - delta_u (Eq. (1), Algorithm 2 step 2), ties
+ * broken towards the smaller vertex id.  The library computes that
+ * assignment exactly, as the delayed-start breadth-first search of Section 4
+ * (Algorithm 1 step 3): u enters the search at round floor(delta_max) -
+ * floor(delta_u), and same-round competitors are ordered by the rank of the
+ * fractional part of their shift, which Section 4 shows is only a tie-breaker.
+ *
+ * Conventions shared by every call:
+ *  - A pointer argument may be host memory (pageable or pinned) or device
+ *    memory of the current CUDA device; the library detects which with
+ *    cudaPointerGetAttributes and copies as needed.
+ *  - The caller owns every buffer it passes.  The library owns the graph
+ *    object, its device copy of the CSR and all scratch; ldd_destroy_graph
+ *    frees them.
+ *  - Calls are synchronous: they return after the work queued on the graph's
+ *    stream (ldd_set_stream) has finished and outputs are in place.
+ *  - Every call returns an ldd_status; no C++ exception crosses this ABI.
+ *    ldd_last_error() gives a one-line description of the latest failure on
+ *    the calling thread.
+ *  - A graph object is not thread-safe: one call at a time per graph.
+ */
+#ifndef LDD_H
+#define LDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ldd_graph ldd_graph; /* opaque, library-owned device CSR + scratch */
+
+typedef enum {
+  LDD_OK = 0,
+  LDD_ERR_ARG = -1,     /* NULL pointer, bad size, beta not finite and > 0,
+                           a shift that is NaN or negative */
+  LDD_ERR_GRAPH = -2,   /* CSR fails validation (see ldd_create_graph) */
+  LDD_ERR_RANGE = -3,   /* a size or value beyond the supported range */
+  LDD_ERR_OOM = -4,     /* device or host allocation failed */
+  LDD_ERR_CUDA = -5,    /* a CUDA runtime call failed */
+  LDD_ERR_TIMEOUT = -6  /* a bounded device-side wait ran out; outputs invalid */
+} ldd_status;
+
+/*
+ * ldd_create_graph -- copy an undirected, unweighted graph (Definition 1.1)
+ * into library-owned device memory.
+ *   n        number of vertices, 0 <= n < 2^30.
+ *   nnz      number of arcs (each undirected edge appears as two arcs),
+ *            0 <= nnz < 2^31.
+ *   row_ptr  int32[n + 1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *   col_idx  int32[nnz], neighbours of v in col_idx[row_ptr[v] .. row_ptr[v+1]).
+ *   validate nonzero: check the CSR on the host (bounds, monotone rows,
+ *            symmetry: every arc (v, w) has a reverse arc (w, v)) and return
+ *            LDD_ERR_GRAPH if it fails.  Self-loops and repeated arcs are
+ *            accepted; they change neither the assignment nor the cut count's
+ *            meaning (a repeated edge is counted with its multiplicity).
+ *            With validate = 0 an asymmetric CSR gives undefined results.
+ *   out      receives the graph handle.
+ * Row order inside a row is free.  The input buffers may be freed after the
+ * call returns.
+ */
+int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                     int validate, ldd_graph** out);
+
+/*
+ * ldd_decompose -- one exponential-shift decomposition (Algorithm 2, computed
+ * as Algorithm 1 / Section 4).
+ *   g          graph from ldd_create_graph.
+ *   beta       the Exp(beta) parameter the shifts were drawn with; must be
+ *              finite and > 0.  It is checked and recorded, not used: the
+ *              assignment depends on the shifts alone.
+ *   shifts     double[n]: delta_u for every vertex, each finite, >= 0 and
+ *              < 2^31 (a NaN or negative value gives LDD_ERR_ARG, a value
+ *              >= 2^31 or infinite gives LDD_ERR_RANGE).
+ *   out_center int32[n]: out_center[v] = the u minimising dist(u,v) - delta_u,
+ *              smallest u on exact ties.  Every center is its own center.
+ *   out_dist   int32[n]: out_dist[v] = dist(out_center[v], v) in hops.
+ * Both outputs are exact (bit-identical to any correct evaluation of the
+ * definition on the same FP64 shifts).
+ */
+int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_center,
+                  int32_t* out_dist);
+
+/*
+ * ldd_cut_edges -- number of edges between pieces (Definition 1.1, second
+ * condition; Section 4 notes the check takes O(m) work).
+ *   center   int32[n] piece labels (normally ldd_decompose's out_center; any
+ *            labelling with values in [0, n) is accepted).
+ *   out_cut  receives #{arcs (v, w) : v < w, center[v] != center[w]}, i.e.
+ *            each undirected edge of a symmetric CSR counted once.
+ */
+int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut);
+
+/* ldd_set_stream -- queue all later work of g on this cudaStream_t (NULL:
+ * the legacy default stream).  A torch.cuda.Stream's .cuda_stream works. */
+int ldd_set_stream(ldd_graph* g, void* cuda_stream);
+
+/* ldd_destroy_graph -- free the graph and its device memory (NULL is a no-op). */
+void ldd_destroy_graph(ldd_graph* g);
+
+/* ldd_status_string -- static text for a status code. */
+const char* ldd_status_string(int status);
+
+/* ldd_last_error -- description of the most recent failure on this thread
+ * ("" if none).  The pointer stays valid until the next call on the thread. */
+const char* ldd_last_error(void);
+
+/*
+ * Statistics of the most recent ldd_decompose / ldd_cut_edges on g.
+ * Timings are CUDA-event durations on the graph's stream, recorded only
+ * after ldd_set_timing(g, 1); otherwise they read -1.
+ */
+typedef struct {
+  int64_t n, nnz;
+  int64_t n_active;       /* vertices with at least one arc */
+  int64_t max_floor_shift;/* A = floor(delta_max) (Algorithm 1 step 2) */
+  int64_t rounds;         /* synchronous BFS rounds executed */
+  int64_t last_level;     /* level of the last round */
+  int64_t items;          /* vertices expanded by the BFS */
+  int64_t edges;          /* arcs scanned by the BFS */
+  int64_t launches;       /* kernels launched by the last ldd_decompose */
+  int64_t cut_launches;   /* kernels launched by the last ldd_cut_edges */
+  int32_t bfs_grid;       /* CTAs of the persistent BFS kernel */
+  int32_t bfs_block;      /* threads per CTA */
+  float ms_h2d;           /* shifts host -> device (0 if already on device) */
+  float ms_rank;          /* split, fraction rank sort, keys, start buckets */
+  float ms_bfs;           /* the persistent round loop */
+  float ms_finalize;      /* keys -> (center, dist) */
+  float ms_d2h;           /* outputs device -> host (0 if device outputs) */
+  float ms_total;         /* whole ldd_decompose on the stream */
+  float ms_cut;           /* whole ldd_cut_edges on the stream */
+} ldd_stats;
+
+int ldd_get_stats(const ldd_graph* g, ldd_stats* out);
+int ldd_set_timing(ldd_graph* g, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDD_H */

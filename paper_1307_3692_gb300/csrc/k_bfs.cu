@@ -1,0 +1,289 @@
+// Round-synchronous, delayed-start multi-source BFS (Algorithm 1 step 3;
+// Section 4 of Miller, Peng, Xu 2013), as one persistent cooperative kernel.
+//
+// State: key[v] = (level << 32) | rank, initialised to v's own start label
+// (level R_v = floor(delta_max) - floor(delta_v)).  Round r expands the
+// frontier F_r = {v : final level of v is r}: every arc (v, w) offers
+// key[v] + 2^32 to w with a 64-bit atomicMin.  Because key[v] is final once
+// round r - 1 has finished, and an offer made in round r carries level r + 1,
+// the minimum over all offers is the exact label the paper's super-source
+// shortest path assigns (Section 4), including the fraction tie-break.
+//
+// F_{r+1} is built during round r from two disjoint sources:
+//   * pushes: the one atomicMin that lowers w's level from > r + 1 to r + 1
+//     appends w (its return value identifies it uniquely);
+//   * delayed starts (Section 4: the super-source edge of length L is used
+//     when the frontier reaches L): vertices of start bucket r + 1 whose key
+//     still has level r + 1.  A push in round r can only lower their rank
+//     part, so this test is stable while round r runs.
+// Appends are warp-aggregated: one 64-bit atomicAdd per warp reserves
+// (items << 32 | edges), giving every appended vertex its queue slot and the
+// exclusive edge offset of its adjacency list in the next frontier.  The next
+// round then splits the frontier's edges into equal spans, one per CTA step,
+// whatever the degree skew: a CTA loads the window of queue items that cover
+// its span into shared memory and finds each edge's item with a block-wide
+// max-scan.
+//
+// Rounds with an empty frontier jump straight to the next non-empty start
+// bucket; the loop stops as soon as every vertex with an arc is settled.
+// All device-side waits are bounded: a barrier that does not complete within
+// the spin limit sets kErrTimeout and the kernel returns.
+#include "ldd_internal.cuh"
+
+namespace ldd {
+
+namespace {
+
+constexpr u32 kFull = 0xffffffffu;
+
+struct Smem {
+  int owner[kBfsMaxSpan];
+  int rowd[kBfsMaxSpan + 1];
+  u64 cand[kBfsMaxSpan + 1];
+  int wtot[kBfsThreads / 32];
+};
+
+__device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const u32 target = gen + 1;
+    __threadfence();
+    const u32 arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicExch(&ctl->bar_gen, target);
+    } else {
+      u32 spins = 0;
+      while (ld_acquire_u32(&ctl->bar_gen) != target) {
+        if (++spins > limit || ld_acquire_u32(&ctl->err) != 0u) {
+          atomicOr(&ctl->err, kErrTimeout);
+          break;
+        }
+        if (spins > 32) __nanosleep(40);
+      }
+    }
+    __threadfence();
+    gen = target;
+  }
+  __syncthreads();
+}
+
+// Appends the lanes with `want` to the frontier: one atomic per warp.
+// qi: frontier counter index (rotates over 3), qb: queue buffer (ping-pong).
+__device__ __forceinline__ void warp_append(bool want, u32 v, const BfsArgs& a, int qi, int qb) {
+  const u32 lane = threadIdx.x & 31;
+  int rs = 0, d = 0;
+  if (want) {
+    rs = __ldg(a.row_ptr + v);
+    d = __ldg(a.row_ptr + v + 1) - rs;
+    want = d > 0;  // a vertex without arcs has nothing to expand
+  }
+  const u32 m = __ballot_sync(kFull, want);
+  if (m == 0) return;
+  const u32 dd = want ? (u32)d : 0u;
+  u32 incl = dd;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= (u32)o) incl += y;
+  }
+  const u32 tot = __shfl_sync(kFull, incl, 31);
+  u64 base = 0;
+  if (lane == 0) base = atomicAdd(&a.ctl->qctr[qi], ((u64)__popc(m) << 32) | tot);
+  base = __shfl_sync(kFull, base, 0);
+  if (want) {
+    const u32 slot = (u32)(base >> 32) + __popc(m & lanemask_lt());
+    const u32 off = (u32)base + incl - dd;
+    a.qv[qb][slot] = v;
+    a.qrow[qb][slot] = rs;
+    a.qoff[qb][slot] = off;
+    for (u32 c = (off + kBfsBase - 1) / kBfsBase; c * kBfsBase < off + dd; ++c) a.cf[qb][c] = slot;
+  }
+}
+
+// Unclaimed vertices of start bucket rr join the frontier of level rr.
+__device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u32* rv, int qi,
+                                              int qb) {
+  const int lo = __ldg(a.bptr + rr), hi = __ldg(a.bptr + rr + 1);
+  const u32 cnt = (u32)(hi - lo);
+  const u32 lane = threadIdx.x & 31;
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < cnt; base += stride) {
+    const u32 i = base + lane;
+    bool want = false;
+    u32 u = 0;
+    if (i < cnt) {
+      u = __ldg(rv + lo + i);
+      want = (u32)(ld_cg_u64(a.key + u) >> 32) == (u32)rr;
+    }
+    warp_append(want, u, a, qi, qb);
+  }
+}
+
+// In-place inclusive max-scan of s.owner[0 .. len), len <= kBfsMaxSpan.
+__device__ __forceinline__ void block_max_scan(Smem& s, int len) {
+  constexpr int kPer = kBfsMaxSpan / kBfsThreads;  // 8 consecutive entries per thread
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int b = t * kPer;
+  int run = -1;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i)
+    if (b + i < len) {
+      run = max(run, s.owner[b + i]);
+      s.owner[b + i] = run;
+    }
+  int x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x = max(x, y);
+  }
+  if (lane == 31) s.wtot[w] = x;
+  __syncthreads();
+  int carry = -1;
+  for (int i = 0; i < w; ++i) carry = max(carry, s.wtot[i]);
+  const int prev = __shfl_up_sync(kFull, x, 1);
+  if (lane > 0) carry = max(carry, prev);
+#pragma unroll
+  for (int i = 0; i < kPer; ++i)
+    if (b + i < len) s.owner[b + i] = max(s.owner[b + i], carry);
+}
+
+__device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q, u32 E, int lvl,
+                                       int qi, int qb) {
+  const u32 nb = (E + kBfsBase - 1) / kBfsBase;
+  u32 k = (nb + gridDim.x - 1) / gridDim.x;
+  k = max(1u, min(k, (u32)(kBfsMaxSpan / kBfsBase)));
+  const u32 nsuper = (nb + k - 1) / k;
+  const u32* cf = a.cf[cur];
+  const u32* qv = a.qv[cur];
+  const int* qrow = a.qrow[cur];
+  const u32* qoff = a.qoff[cur];
+  const u32 lvl_next = (u32)lvl + 1;
+  for (u32 sc = blockIdx.x; sc < nsuper; sc += gridDim.x) {
+    const u32 b0 = sc * k, b1 = min(b0 + k, nb);
+    const u32 e0 = b0 * kBfsBase, e1 = min(b1 * kBfsBase, E);
+    const u32 i0 = ld_cg_u32(cf + b0);
+    const u32 ilast = (b1 < nb) ? ld_cg_u32(cf + b1) : Q - 1;
+    const int nwin = (int)(ilast - i0) + 1;
+    const int len = (int)(e1 - e0);
+    if (nwin > kBfsMaxSpan + 1 || nwin < 1 || ilast >= Q) {  // window invariant broken
+      if (threadIdx.x == 0) atomicOr(&a.ctl->err, kErrInternal);
+      return;
+    }
+    for (int j = threadIdx.x; j < len; j += kBfsThreads) s.owner[j] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < nwin; j += kBfsThreads) {
+      const u32 it = i0 + (u32)j;
+      const u32 off = ld_cg_u32(qoff + it);
+      if (off < e1) {
+        const u32 v = ld_cg_u32(qv + it);
+        s.rowd[j] = ld_cg_i32(qrow + it) - (int)off;
+        s.cand[j] = ld_cg_u64(a.key + v) + kLevelOne;
+        atomicMax(&s.owner[off > e0 ? off - e0 : 0u], j);
+      }
+    }
+    __syncthreads();
+    block_max_scan(s, len);
+    __syncthreads();
+    for (int base = 0; base < len; base += kBfsThreads) {
+      const int kk = base + threadIdx.x;
+      bool want = false;
+      u32 w = 0;
+      if (kk < len) {
+        const int j = s.owner[kk];
+        w = (u32)__ldg(a.col + (s.rowd[j] + (int)(e0 + kk)));
+        const u64 cand = s.cand[j];
+        if (w < a.n && cand < ld_cg_u64(a.key + w)) {
+          const u64 old = atomicMin(a.key + w, cand);
+          want = (u32)(old >> 32) > lvl_next;
+        }
+      }
+      warp_append(want, w, a, qi, qb);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  Control* ctl = a.ctl;
+  if (ld_acquire_u32(&ctl->err) != 0u) return;  // validation failed upstream
+  const int A = ctl->A;
+  const u32 par_r = __popc(ctl->mask_r) & 1u;
+  const u64* rk = a.rk[par_r];
+  const u32* rv = a.rv[par_r];
+  const u32 G = gridDim.x;
+  u32 gen = 0;
+
+  // Level 0: the vertices with the largest integer shift part start.
+  append_bucket(a, 0, rv, 0, 0);
+  grid_barrier(ctl, gen, G, a.spin_limit);
+
+  u64 settled = 0, edges = 0;
+  u32 phase = 0;
+  int lvl = 0;
+  for (;;) {
+    if (ld_acquire_u32(&ctl->err) != 0u) break;
+    const u64 c = ld_cg_u64(&ctl->qctr[phase % 3]);
+    const u32 Q = (u32)(c >> 32), E = (u32)c;
+    settled += Q;
+    if (settled >= a.n_active) break;  // every vertex with an arc has its final key
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qctr[(phase + 2) % 3] = 0;
+    const int qi = (int)((phase + 1) % 3), qb = (int)((phase + 1) & 1);
+    int nlvl;
+    if (Q > 0) {
+      edges += E;
+      expand(a, s, (int)(phase & 1), Q, E, lvl, qi, qb);
+      if (lvl + 1 <= A) append_bucket(a, lvl + 1, rv, qi, qb);
+      nlvl = lvl + 1;
+    } else {
+      if (lvl + 1 > A) break;
+      const int start = __ldg(a.bptr + lvl + 1);
+      if ((u32)start >= a.n) break;
+      const int rr = (int)__ldg(rk + start);  // next non-empty start bucket
+      append_bucket(a, rr, rv, qi, qb);
+      nlvl = rr;
+    }
+    grid_barrier(ctl, gen, G, a.spin_limit);
+    ++phase;
+    lvl = nlvl;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->rounds = phase;
+    ctl->last_level = lvl;
+    ctl->items = settled;
+    ctl->edges = edges;
+  }
+}
+
+}  // namespace
+
+size_t bfs_smem_bytes() { return sizeof(Smem); }
+
+int bfs_grid_size(int num_sms, int* blocks_per_sm) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_bfs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs, kBfsThreads, sizeof(Smem));
+  if (e != cudaSuccess || per_sm < 1) return -1;
+  per_sm = per_sm > 2 ? 2 : per_sm;
+  *blocks_per_sm = per_sm;
+  return per_sm * num_sms;
+}
+
+int launch_bfs(const BfsArgs& a, int grid, cudaStream_t s, cudaError_t* err) {
+  BfsArgs copy = a;
+  void* args[] = {&copy};
+  *err = cudaLaunchCooperativeKernel((const void*)k_bfs, dim3(grid), dim3(kBfsThreads), args,
+                                     sizeof(Smem), s);
+  return *err == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace ldd

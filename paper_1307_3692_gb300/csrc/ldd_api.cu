@@ -1,0 +1,549 @@
+// C ABI of libldd.so (declared in include/ldd.h): the graph object, argument
+// checks, host/device pointer handling, scratch memory and the order of the
+// kernels of one decomposition (Miller, Peng, Xu 2013, Algorithm 1):
+//   step 1 (shifts)      : given by the caller, copied to the device if needed
+//   step 2 (delta_max)   : k_split_hist                       (k_rank.cu)
+//   Section 4 tie-break  : fraction rank sort, keys, buckets   (k_rank.cu)
+//   step 3 (BFS)         : persistent cooperative k_bfs        (k_bfs.cu)
+//   step 4 (assignment)  : k_finalize                          (k_finalize_cut.cu)
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/ldd.h"
+#include "ldd_internal.cuh"
+
+using namespace ldd;
+
+static_assert(offsetof(Control, bar_count) == kCtlBfsStateOffset, "control layout");
+static_assert(offsetof(Control, mask_f) == kCtlBfsStateOffset + kCtlBfsStateBytes,
+              "control layout");
+static_assert(offsetof(Control, cut) + sizeof(u64) == kCtlHeaderBytes, "control layout");
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int status, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(LDD_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                             \
+  } while (0)
+
+// Restores the caller's current device when a call returns.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && (prev == dev || cudaSetDevice(dev) == cudaSuccess))
+      ok = true;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// True for device or managed memory; false for pageable or pinned host memory.
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+u32 env_u32(const char* name, u32 dflt) {
+  const char* v = getenv(name);
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  unsigned long x = strtoul(v, &end, 10);
+  return (end && *end == 0 && x > 0 && x <= 0xffffffffUL) ? (u32)x : dflt;
+}
+
+}  // namespace
+
+struct ldd_graph {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  u32 n_active = 0;
+  u32 cut_items = 0;
+  // device CSR and graph tables
+  int* d_row = nullptr;
+  int* d_col = nullptr;
+  u32* d_nzv = nullptr;       // vertices with at least one arc, ascending
+  u32* d_cut_first = nullptr; // per cut span: index into d_nzv of the row holding its first arc
+  // scratch arena
+  void* arena = nullptr;
+  double* d_shift = nullptr;
+  int* d_a = nullptr;
+  u64* d_k[2] = {nullptr, nullptr};
+  u32* d_v[2] = {nullptr, nullptr};
+  u64* d_status = nullptr;
+  u32* d_order = nullptr;
+  u64* d_key = nullptr;
+  u32* d_qv[2] = {nullptr, nullptr};
+  int* d_qrow[2] = {nullptr, nullptr};
+  u32* d_qoff[2] = {nullptr, nullptr};
+  u32* d_cf[2] = {nullptr, nullptr};
+  int* d_center = nullptr;
+  int* d_dist = nullptr;
+  Control* d_ctl = nullptr;
+  int* d_bptr = nullptr;
+  u32 bptr_cap = 0;
+  size_t status_bytes = 0;
+  u32 epoch = 0;
+  // host side
+  unsigned char* h_hdr = nullptr;  // pinned copy of the control header
+  int bfs_grid = 0;
+  int bfs_per_sm = 0;
+  u32 spin_limit = 0;
+  bool timing = false;
+  cudaEvent_t ev[8] = {};
+  ldd_stats stats;
+};
+
+namespace {
+
+int free_graph_memory(ldd_graph* g) {
+  cudaFree(g->d_row);
+  cudaFree(g->d_col);
+  cudaFree(g->d_nzv);
+  cudaFree(g->d_cut_first);
+  cudaFree(g->arena);
+  cudaFree(g->d_bptr);
+  if (g->h_hdr) cudaFreeHost(g->h_hdr);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  return 0;
+}
+
+// Host-side CSR check: bounds, monotone rows, every arc has its reverse.
+int validate_csr(int32_t n, int64_t nnz, const int32_t* rp, const int32_t* col) {
+  if (rp[0] != 0) return fail(LDD_ERR_GRAPH, "row_ptr[0] = %d, expected 0", rp[0]);
+  if ((int64_t)rp[n] != nnz)
+    return fail(LDD_ERR_GRAPH, "row_ptr[n] = %d, expected nnz = %lld", rp[n], (long long)nnz);
+  for (int32_t v = 0; v < n; ++v)
+    if (rp[v + 1] < rp[v]) return fail(LDD_ERR_GRAPH, "row_ptr decreases at vertex %d", v);
+  for (int64_t e = 0; e < nnz; ++e)
+    if (col[e] < 0 || col[e] >= n)
+      return fail(LDD_ERR_GRAPH, "col_idx[%lld] = %d out of [0, %d)", (long long)e, col[e], n);
+  std::vector<int32_t> sorted(col, col + nnz);
+  for (int32_t v = 0; v < n; ++v) std::sort(sorted.begin() + rp[v], sorted.begin() + rp[v + 1]);
+  for (int32_t v = 0; v < n; ++v)
+    for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      const int32_t w = col[e];
+      if (!std::binary_search(sorted.begin() + rp[w], sorted.begin() + rp[w + 1], v))
+        return fail(LDD_ERR_GRAPH, "arc (%d, %d) has no reverse arc: the graph must be undirected",
+                    v, w);
+    }
+  return LDD_OK;
+}
+
+int alloc_scratch(ldd_graph* g) {
+  const size_t n = (size_t)g->n;
+  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const size_t ncf = (size_t)g->nnz / kBfsBase + 2;
+  g->status_bytes = ntiles * 256 * sizeof(u64);
+  struct Part {
+    void** p;
+    size_t bytes;
+  } parts[] = {
+      {(void**)&g->d_shift, 8 * n},       {(void**)&g->d_a, 4 * n},
+      {(void**)&g->d_k[0], 8 * n},        {(void**)&g->d_k[1], 8 * n},
+      {(void**)&g->d_v[0], 4 * n},        {(void**)&g->d_v[1], 4 * n},
+      {(void**)&g->d_status, g->status_bytes},
+      {(void**)&g->d_order, 4 * n},       {(void**)&g->d_key, 8 * n},
+      {(void**)&g->d_qv[0], 4 * n},       {(void**)&g->d_qv[1], 4 * n},
+      {(void**)&g->d_qrow[0], 4 * n},     {(void**)&g->d_qrow[1], 4 * n},
+      {(void**)&g->d_qoff[0], 4 * n},     {(void**)&g->d_qoff[1], 4 * n},
+      {(void**)&g->d_cf[0], 4 * ncf},     {(void**)&g->d_cf[1], 4 * ncf},
+      {(void**)&g->d_center, 4 * n},      {(void**)&g->d_dist, 4 * n},
+      {(void**)&g->d_ctl, sizeof(Control)},
+  };
+  size_t total = 0;
+  for (auto& p : parts) total += align_up(p.bytes ? p.bytes : 1, 256);
+  if (cudaMalloc(&g->arena, total) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "cudaMalloc of %zu bytes of scratch failed", total);
+  }
+  size_t off = 0;
+  for (auto& p : parts) {
+    *p.p = (char*)g->arena + off;
+    off += align_up(p.bytes ? p.bytes : 1, 256);
+  }
+  CUDA_TRY(cudaMemset(g->d_status, 0, g->status_bytes));
+  g->bptr_cap = (u32)std::min<size_t>(n + 2, 0xffffffffu);
+  if (cudaMalloc(&g->d_bptr, (size_t)g->bptr_cap * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "cudaMalloc of the start-bucket table failed");
+  }
+  return LDD_OK;
+}
+
+void record(ldd_graph* g, int i) {
+  if (g->timing) cudaEventRecord(g->ev[i], g->stream);
+}
+
+float elapsed(ldd_graph* g, int a, int b) {
+  float ms = -1.f;
+  if (!g->timing || cudaEventElapsedTime(&ms, g->ev[a], g->ev[b]) != cudaSuccess) {
+    cudaGetLastError();
+    return -1.f;
+  }
+  return ms;
+}
+
+BfsArgs bfs_args(ldd_graph* g) {
+  BfsArgs a;
+  a.row_ptr = g->d_row;
+  a.col = g->d_col;
+  a.key = g->d_key;
+  a.bptr = g->d_bptr;
+  a.rk[0] = g->d_k[0];
+  a.rk[1] = g->d_k[1];
+  a.rv[0] = g->d_v[0];
+  a.rv[1] = g->d_v[1];
+  for (int b = 0; b < 2; ++b) {
+    a.qv[b] = g->d_qv[b];
+    a.qrow[b] = g->d_qrow[b];
+    a.qoff[b] = g->d_qoff[b];
+    a.cf[b] = g->d_cf[b];
+  }
+  a.ctl = g->d_ctl;
+  a.n = (u32)g->n;
+  a.n_active = g->n_active;
+  a.spin_limit = g->spin_limit;
+  return a;
+}
+
+// BFS + finalize into (center, dist) device buffers.  Returns launches or <0.
+int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
+  int launches = 0;
+  cudaStream_t s = g->stream;
+  if (g->n_active > 0) {
+    cudaError_t e;
+    if (launch_bfs(bfs_args(g), g->bfs_grid, s, &e) < 0) {
+      *status = fail(LDD_ERR_CUDA, "cooperative launch of the BFS kernel (%d x %d) failed: %s",
+                     g->bfs_grid, kBfsThreads, cudaGetErrorString(e));
+      return -1;
+    }
+    ++launches;
+  }
+  record(g, 3);
+  launches += launch_finalize(g->d_key, g->d_order, (u32)g->n, center, dist, &g->d_ctl->err,
+                              g->num_sms, s);
+  return launches;
+}
+
+struct Header {
+  u32 err;
+  int A;
+  u32 rounds;
+  int last_level;
+  u64 items;
+  u64 edges;
+  u64 cut;
+};
+static_assert(sizeof(Header) == kCtlHeaderBytes, "header layout");
+
+}  // namespace
+
+extern "C" {
+
+const char* ldd_status_string(int status) {
+  switch (status) {
+    case LDD_OK: return "LDD_OK";
+    case LDD_ERR_ARG: return "LDD_ERR_ARG: invalid argument";
+    case LDD_ERR_GRAPH: return "LDD_ERR_GRAPH: CSR failed validation";
+    case LDD_ERR_RANGE: return "LDD_ERR_RANGE: size or value out of the supported range";
+    case LDD_ERR_OOM: return "LDD_ERR_OOM: allocation failed";
+    case LDD_ERR_CUDA: return "LDD_ERR_CUDA: CUDA runtime error";
+    case LDD_ERR_TIMEOUT: return "LDD_ERR_TIMEOUT: a bounded device wait ran out";
+    default: return "unknown ldd status";
+  }
+}
+
+const char* ldd_last_error(void) { return g_last_error; }
+
+int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                     int validate, ldd_graph** out) {
+  g_last_error[0] = 0;
+  if (!out) return fail(LDD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 0 || nnz < 0) return fail(LDD_ERR_ARG, "negative size (n = %d, nnz = %lld)", n,
+                                    (long long)nnz);
+  if (n >= (1 << 30)) return fail(LDD_ERR_RANGE, "n = %d must be < 2^30", n);
+  if (nnz >= (int64_t)1 << 31) return fail(LDD_ERR_RANGE, "nnz = %lld must be < 2^31",
+                                           (long long)nnz);
+  if (!row_ptr) return fail(LDD_ERR_ARG, "row_ptr is NULL");
+  if (nnz > 0 && !col_idx) return fail(LDD_ERR_ARG, "col_idx is NULL");
+
+  ldd_graph* g = new (std::nothrow) ldd_graph();
+  if (!g) return fail(LDD_ERR_OOM, "host allocation failed");
+  memset(&g->stats, 0, sizeof(g->stats));
+  g->n = n;
+  g->nnz = nnz;
+  int rc = LDD_OK;
+  auto bail = [&](int status) {
+    free_graph_memory(g);
+    delete g;
+    return status;
+  };
+  if (cudaGetDevice(&g->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LDD_ERR_CUDA, "no usable CUDA device"));
+  }
+  // Host copies of the CSR (the caller's buffers may live on either side).
+  std::vector<int32_t> rp((size_t)n + 1), col((size_t)nnz);
+  if (is_device_ptr(row_ptr)) {
+    if (cudaMemcpy(rp.data(), row_ptr, rp.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail(fail(LDD_ERR_CUDA, "copy of row_ptr failed"));
+  } else {
+    memcpy(rp.data(), row_ptr, rp.size() * 4);
+  }
+  if (nnz > 0) {
+    if (is_device_ptr(col_idx)) {
+      if (cudaMemcpy(col.data(), col_idx, col.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bail(fail(LDD_ERR_CUDA, "copy of col_idx failed"));
+    } else {
+      memcpy(col.data(), col_idx, col.size() * 4);
+    }
+  }
+  if (validate && (rc = validate_csr(n, nnz, rp.data(), col.data())) != LDD_OK) return bail(rc);
+  if (rp[0] != 0 || (int64_t)rp[n] != nnz)
+    return bail(fail(LDD_ERR_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] must be nnz"));
+
+  // Vertices with arcs, and the first row of every cut span.
+  std::vector<u32> nzv;
+  nzv.reserve((size_t)n);
+  for (int32_t v = 0; v < n; ++v)
+    if (rp[v + 1] > rp[v]) nzv.push_back((u32)v);
+  g->n_active = (u32)nzv.size();
+  g->cut_items = g->n_active;
+  const size_t nch = ((size_t)nnz + kCutSpan - 1) / kCutSpan;
+  std::vector<u32> first(nch + 1, 0);
+  {
+    size_t j = 0;
+    for (size_t c = 0; c < nch; ++c) {
+      const int64_t e = (int64_t)c * kCutSpan;
+      while (j + 1 < nzv.size() && rp[nzv[j] + 1] <= e) ++j;
+      first[c] = (u32)j;
+    }
+  }
+  if (cudaMalloc(&g->d_row, rp.size() * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_col, std::max<size_t>(col.size(), 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_nzv, std::max<size_t>(nzv.size(), 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_cut_first, first.size() * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LDD_ERR_OOM, "device allocation of the graph failed"));
+  }
+  if (cudaMemcpy(g->d_row, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (nnz > 0 &&
+       cudaMemcpy(g->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (!nzv.empty() &&
+       cudaMemcpy(g->d_nzv, nzv.data(), nzv.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(g->d_cut_first, first.data(), first.size() * 4, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
+  if ((rc = alloc_scratch(g)) != LDD_OK) return bail(rc);
+  if (cudaMallocHost(&g->h_hdr, 256) != cudaSuccess)
+    return bail(fail(LDD_ERR_OOM, "pinned host allocation failed"));
+  for (auto& e : g->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(LDD_ERR_CUDA, "cudaEventCreate"));
+  g->bfs_grid = bfs_grid_size(g->num_sms, &g->bfs_per_sm);
+  if (g->bfs_grid <= 0) return bail(fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed"));
+  const u32 per_sm = env_u32("LDD_BFS_BLOCKS_PER_SM", 0);
+  if (per_sm > 0 && (int)per_sm < g->bfs_per_sm) {
+    g->bfs_per_sm = (int)per_sm;
+    g->bfs_grid = g->bfs_per_sm * g->num_sms;
+  }
+  g->spin_limit = env_u32("LDD_SPIN_LIMIT", 1u << 22);
+  g->stats.n = n;
+  g->stats.nnz = nnz;
+  g->stats.n_active = g->n_active;
+  g->stats.bfs_grid = g->bfs_grid;
+  g->stats.bfs_block = kBfsThreads;
+  *out = g;
+  return LDD_OK;
+}
+
+void ldd_destroy_graph(ldd_graph* g) {
+  if (!g) return;
+  DeviceGuard dg(g->device);
+  cudaStreamSynchronize(g->stream);
+  free_graph_memory(g);
+  delete g;
+}
+
+int ldd_set_stream(ldd_graph* g, void* cuda_stream) {
+  if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  g->stream = (cudaStream_t)cuda_stream;
+  return LDD_OK;
+}
+
+int ldd_set_timing(ldd_graph* g, int enable) {
+  if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  g->timing = enable != 0;
+  return LDD_OK;
+}
+
+int ldd_get_stats(const ldd_graph* g, ldd_stats* out) {
+  if (!g || !out) return fail(LDD_ERR_ARG, "NULL argument");
+  *out = g->stats;
+  return LDD_OK;
+}
+
+int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_center,
+                  int32_t* out_dist) {
+  g_last_error[0] = 0;
+  if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  if (!(beta > 0.0) || isinf(beta)) return fail(LDD_ERR_ARG, "beta must be finite and > 0");
+  if (g->n == 0) return LDD_OK;
+  if (!shifts || !out_center || !out_dist) return fail(LDD_ERR_ARG, "NULL shifts or output");
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
+  cudaStream_t s = g->stream;
+  const size_t n = (size_t)g->n;
+  int launches = 0;
+  const bool dev_in = is_device_ptr(shifts);
+  const bool dev_c = is_device_ptr(out_center), dev_d = is_device_ptr(out_dist);
+  int* center = dev_c ? out_center : g->d_center;
+  int* dist = dev_d ? out_dist : g->d_dist;
+  if (g->epoch > 0xfffff000u) {  // status tags would wrap: clear and restart
+    CUDA_TRY(cudaMemsetAsync(g->d_status, 0, g->status_bytes, s));
+    g->epoch = 0;
+  }
+
+  record(g, 0);
+  CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
+  const double* d_shift = shifts;
+  if (!dev_in) {
+    CUDA_TRY(cudaMemcpyAsync(g->d_shift, shifts, n * 8, cudaMemcpyHostToDevice, s));
+    d_shift = g->d_shift;
+  }
+  record(g, 1);
+  launches += launch_rank_and_buckets(d_shift, (u32)n, g->d_a, g->d_k[0], g->d_v[0], g->d_k[1],
+                                      g->d_v[1], g->d_status, &g->epoch, g->d_order, g->d_key,
+                                      g->d_bptr, g->bptr_cap, g->d_ctl, g->num_sms, s);
+  record(g, 2);
+  int status = LDD_OK;
+  int l = run_bfs_finalize(g, center, dist, &status);
+  if (l < 0) return status;
+  launches += l;
+  record(g, 4);
+  CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, kCtlHeaderBytes, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  Header h;
+  memcpy(&h, g->h_hdr, sizeof(h));
+
+  if (h.err == kErrBucketCap) {
+    // floor(delta_max) exceeds n: grow the start-bucket table and rerun the
+    // bucket pointers, the BFS and the assignment (keys and sorts are intact).
+    const size_t need = (size_t)h.A + 2;
+    cudaFree(g->d_bptr);
+    g->d_bptr = nullptr;
+    g->bptr_cap = 0;
+    if (cudaMalloc(&g->d_bptr, need * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LDD_ERR_OOM, "start-bucket table of %zu entries", need);
+    }
+    g->bptr_cap = (u32)need;
+    CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(u32), s));
+    CUDA_TRY(cudaMemsetAsync((char*)g->d_ctl + kCtlBfsStateOffset, 0, kCtlBfsStateBytes, s));
+    launches += launch_bucket_ptr(g->d_k[0], g->d_k[1], g->d_ctl, (u32)n, g->d_bptr,
+                                  g->bptr_cap, g->num_sms, s);
+    l = run_bfs_finalize(g, center, dist, &status);
+    if (l < 0) return status;
+    launches += l;
+    record(g, 4);
+    CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, kCtlHeaderBytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    memcpy(&h, g->h_hdr, sizeof(h));
+  }
+  if (h.err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
+  if (h.err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");
+  if (h.err & kErrTimeout) return fail(LDD_ERR_TIMEOUT, "a device-side wait ran out");
+  if (h.err) return fail(LDD_ERR_CUDA, "device error bits 0x%x", h.err);
+
+  if (!dev_c) CUDA_TRY(cudaMemcpyAsync(out_center, center, n * 4, cudaMemcpyDeviceToHost, s));
+  if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, n * 4, cudaMemcpyDeviceToHost, s));
+  record(g, 5);
+  CUDA_TRY(cudaStreamSynchronize(s));
+
+  ldd_stats& st = g->stats;
+  st.max_floor_shift = h.A;
+  st.rounds = h.rounds;
+  st.last_level = h.last_level;
+  st.items = (int64_t)h.items;
+  st.edges = (int64_t)h.edges;
+  st.launches = launches;
+  st.ms_h2d = dev_in ? 0.f : elapsed(g, 0, 1);
+  st.ms_rank = elapsed(g, 1, 2);
+  st.ms_bfs = elapsed(g, 2, 3);
+  st.ms_finalize = elapsed(g, 3, 4);
+  st.ms_d2h = (dev_c && dev_d) ? 0.f : elapsed(g, 4, 5);
+  st.ms_total = elapsed(g, 0, 5);
+  return LDD_OK;
+}
+
+int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut) {
+  g_last_error[0] = 0;
+  if (!g || !out_cut) return fail(LDD_ERR_ARG, "NULL argument");
+  *out_cut = 0;
+  if (g->n == 0 || g->nnz == 0) return LDD_OK;
+  if (!center) return fail(LDD_ERR_ARG, "center is NULL");
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
+  cudaStream_t s = g->stream;
+  record(g, 6);
+  const int* d_center = center;
+  if (!is_device_ptr(center)) {
+    CUDA_TRY(cudaMemcpyAsync(g->d_center, center, (size_t)g->n * 4, cudaMemcpyHostToDevice, s));
+    d_center = g->d_center;
+  }
+  CUDA_TRY(cudaMemsetAsync(&g->d_ctl->cut, 0, sizeof(u64), s));
+  const int l = launch_cut(g->d_row, g->d_col, g->d_nzv, g->d_cut_first, g->cut_items,
+                           (u32)g->nnz, (u32)g->n, d_center, &g->d_ctl->cut, s);
+  CUDA_TRY(cudaMemcpyAsync(g->h_hdr + 64, &g->d_ctl->cut, sizeof(u64), cudaMemcpyDeviceToHost, s));
+  record(g, 7);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  u64 cut;
+  memcpy(&cut, g->h_hdr + 64, sizeof(cut));
+  *out_cut = (int64_t)cut;
+  g->stats.cut_launches = l;
+  g->stats.ms_cut = elapsed(g, 6, 7);
+  return LDD_OK;
+}
+
+}  // extern "C"

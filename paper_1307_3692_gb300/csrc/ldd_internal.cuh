@@ -1,0 +1,137 @@
+// Internal declarations shared by the CUDA translation units of libldd.so.
+//
+// Key layout (Section 4 of Miller, Peng, Xu 2013): the shifted distance
+// dist(u, v) - delta_u is compared as the pair
+//     level = (floor(delta_max) - floor(delta_u)) + dist(u, v)   (integer part)
+//     rank  = position of u in the order (frac(delta_u) descending, u ascending)
+// packed into one 64-bit word key = (level << 32) | rank, so that the
+// unsigned minimum of two keys is the lexicographic minimum the paper asks
+// for: smaller integer part first, larger fraction on a tie (Section 4: the
+// fractional parts are tie-breakers within an integer level and can be
+// replaced by a permutation), smaller id on an exact tie (Algorithm 2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ldd {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr u64 kLevelOne = 1ull << 32;
+
+// Bits of Control::err.
+enum : u32 {
+  kErrShiftArg = 1u << 0,    // a shift is NaN or negative
+  kErrShiftRange = 1u << 1,  // a shift is >= 2^31 or infinite
+  kErrTimeout = 1u << 2,     // a bounded device-side wait ran out
+  kErrBucketCap = 1u << 3,   // start-bucket table smaller than A + 2 (host grows it, reruns)
+  kErrInternal = 1u << 4,    // a capacity invariant failed
+};
+
+// Radix sort: 8-bit digits, 256-thread CTAs, 16 keys per thread.
+constexpr int kSortThreads = 256;
+constexpr int kSortIpt = 16;
+constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 keys per tile
+constexpr int kFracDigits = 8;                       // 64-bit fraction key
+constexpr int kRoundDigits = 4;                      // 32-bit start round
+
+// BFS: base chunk of the edge-balanced frontier, and the largest span of
+// edges one CTA takes per step (window held in shared memory).
+constexpr int kBfsThreads = 512;
+constexpr int kBfsBase = 256;
+constexpr int kBfsMaxSpan = 4096;
+
+// Cut counter: edges per CTA.
+constexpr int kCutThreads = 256;
+constexpr int kCutSpan = 2048;
+
+// Device control block; cudaMemsetAsync(0) at the start of every decomposition.
+// The header (err .. cut) is copied back to the host after every call.
+struct Control {
+  // header
+  u32 err;
+  int A;  // floor(delta_max)
+  u32 rounds;
+  int last_level;
+  u64 items;
+  u64 edges;
+  u64 cut;  // cut-edge accumulator
+  // BFS runtime state
+  u32 bar_count;
+  u32 bar_gen;
+  u64 qctr[3];  // frontier counters: (items << 32) | edges
+  // sort state
+  u32 mask_f;  // bit d: fraction digit pass d is needed
+  u32 mask_r;  // bit d: round digit pass d is needed
+  u32 tile_ctr[kFracDigits + kRoundDigits];
+  u32 hist_f[kFracDigits][256];
+  u32 off_f[kFracDigits][256];
+  u32 hist_r[kRoundDigits][256];
+  u32 off_r[kRoundDigits][256];
+};
+constexpr size_t kCtlHeaderBytes = 40;       // err .. cut
+constexpr size_t kCtlBfsStateOffset = 40;    // bar_count .. qctr
+constexpr size_t kCtlBfsStateBytes = 32;
+
+struct BfsArgs {
+  const int* row_ptr;
+  const int* col;
+  u64* key;
+  const int* bptr;   // [A + 2] start-bucket offsets into the round-sorted list
+  const u64* rk[2];  // round-sorted keys (start rounds), ping-pong pair
+  const u32* rv[2];  // round-sorted vertices, ping-pong pair
+  u32* qv[2];        // frontier queues: vertex
+  int* qrow[2];      //                  row_ptr[vertex]
+  u32* qoff[2];      //                  exclusive edge offset in the frontier
+  u32* cf[2];        // first queue slot of every base chunk of edges
+  Control* ctl;
+  u32 n;
+  u32 n_active;      // vertices with degree > 0 (the BFS settles exactly these)
+  u32 spin_limit;
+};
+
+// ---------------------------------------------------------------- launchers
+// Fraction rank and start buckets (k_rank.cu).  Returns kernels launched.
+int launch_rank_and_buckets(const double* d_shift, u32 n, int* d_a, u64* k0, u32* v0, u64* k1,
+                            u32* v1, u64* status, u32* epoch, u32* order, u64* key, int* bptr,
+                            u32 bptr_cap, Control* ctl, int num_sms, cudaStream_t s);
+int launch_bucket_ptr(const u64* k0, const u64* k1, Control* ctl, u32 n, int* bptr, u32 cap,
+                      int num_sms, cudaStream_t s);
+// Persistent BFS (k_bfs.cu).  Returns kernels launched, or -1 with the CUDA
+// error left in *err.
+int bfs_grid_size(int num_sms, int* blocks_per_sm);
+int launch_bfs(const BfsArgs& a, int grid, cudaStream_t s, cudaError_t* err);
+size_t bfs_smem_bytes();
+// Finalize and cut (k_finalize_cut.cu).
+int launch_finalize(const u64* key, const u32* order, u32 n, int* center, int* dist,
+                    const u32* err, int num_sms, cudaStream_t s);
+int launch_cut(const int* row_ptr, const int* col, const u32* nzv, const u32* cut_first,
+               u32 n_items, u32 nnz, u32 n_vert, const int* center, u64* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ u32 lanemask_lt() {
+  u32 m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ u64 ld_cg_u64(const u64* p) { return __ldcg(p); }
+__device__ __forceinline__ u32 ld_cg_u32(const u32* p) { return __ldcg(p); }
+__device__ __forceinline__ int ld_cg_i32(const int* p) { return __ldcg(p); }
+
+__device__ __forceinline__ u32 ld_acquire_u32(const u32* p) {
+  u32 v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ u64 ld_volatile_u64(const u64* p) {
+  return *reinterpret_cast<const volatile u64*>(p);
+}
+__device__ __forceinline__ void st_volatile_u64(u64* p, u64 v) {
+  *reinterpret_cast<volatile u64*>(p) = v;
+}
+
+}  // namespace ldd

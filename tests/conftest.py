@@ -19,3 +19,14 @@ def cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="session")
+def ldd():
+    """The CUDA library; built on demand so a fresh checkout can run -m gpu directly."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1307_3692_gb300 as mod
+
+    return mod

@@ -1,0 +1,68 @@
+"""The C ABI library without a GPU: it loads, exports every function that
+include/ldd.h declares, and rejects bad arguments before touching a device."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ldd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ldd_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ldd_create_graph", "ldd_decompose", "ldd_cut_edges", "ldd_set_stream",
+                     "ldd_destroy_graph", "ldd_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(ldd):
+    lib = ctypes.CDLL(ldd.library_path())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(ldd):
+    for code in range(0, -7, -1):
+        s = ldd.ldd_status_string(code)
+        assert s.startswith("LDD_")
+    assert "unknown" in ldd.ldd_status_string(42)
+
+
+def test_argument_errors_need_no_device(ldd):
+    lib = ctypes.CDLL(ldd.library_path())
+    lib.ldd_decompose.argtypes = [ctypes.c_void_p, ctypes.c_double] + [ctypes.c_void_p] * 3
+    lib.ldd_cut_edges.argtypes = [ctypes.c_void_p] * 3
+    lib.ldd_set_stream.argtypes = [ctypes.c_void_p] * 2
+    lib.ldd_create_graph.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int, ctypes.c_void_p]
+    assert lib.ldd_decompose(None, 0.1, None, None, None) == ldd.LDD_ERR_ARG
+    assert lib.ldd_cut_edges(None, None, None) == ldd.LDD_ERR_ARG
+    assert lib.ldd_set_stream(None, None) == ldd.LDD_ERR_ARG
+    out = ctypes.c_void_p()
+    rp = np.zeros(4, dtype=np.int32)
+    assert lib.ldd_create_graph(3, 0, rp.ctypes.data, None, 1, None) == ldd.LDD_ERR_ARG
+    assert lib.ldd_create_graph(-1, 0, rp.ctypes.data, None, 1, ctypes.byref(out)) == ldd.LDD_ERR_ARG
+    assert lib.ldd_create_graph(1 << 30, 0, rp.ctypes.data, None, 1, ctypes.byref(out)) == ldd.LDD_ERR_RANGE
+    assert lib.ldd_create_graph(3, 1 << 31, rp.ctypes.data, None, 1, ctypes.byref(out)) == ldd.LDD_ERR_RANGE
+    assert lib.ldd_create_graph(3, 2, None, None, 1, ctypes.byref(out)) == ldd.LDD_ERR_ARG
+    lib.ldd_destroy_graph(None)  # no-op
+    assert "NULL" in ldd.ldd_last_error() or ldd.ldd_last_error() == ""
+
+
+def test_binding_checks_dtypes(ldd):
+    with pytest.raises(TypeError):
+        ldd._addr(np.zeros(4, dtype=np.int64), "i32", 4, "row_ptr")
+    with pytest.raises(ValueError):
+        ldd._addr(np.zeros(2, dtype=np.int32), "i32", 4, "row_ptr")
+    assert ldd._addr(np.zeros(4, dtype=np.int32), "i32", 4, "row_ptr") != 0

@@ -1,0 +1,209 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+The tolerance is zero: the decomposition is integer and exact (center id and
+hop distance per vertex), and the cut count is an integer.  Sizes span
+several BFS spans (4096 arcs), several sort tiles (4096 keys) and ragged
+tails; edge cases cover empty graphs, isolated vertices, hubs wider than one
+CTA span, exact ties and the limits beta -> 0 and beta -> infinity.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import ldd_gen as gen
+import oracle
+from tests.gpu_util import assert_parity, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    yield "grid2d_37x53", gen.grid2d(37, 53), 0.1, 1
+    yield "grid2d_1x1000_path", gen.grid2d(1, 1000), 0.05, 2
+    yield "grid2d_64x64_b002", gen.grid2d(64, 64), 0.02, 3
+    yield "grid3d_9x11x13", gen.grid3d(9, 11, 13), 0.2, 4
+    yield "rmat10", gen.rmat(10), 0.1, 5
+    yield "rmat12_b05", gen.rmat(12), 0.5, 6
+    yield "rmat14_b002", gen.rmat(14), 0.02, 7
+    yield "rgg5000", gen.rgg(5000, 11), 0.1, 8
+    yield "gnp300_dense", gen.random_graph(300, 0.3, 9), 0.3, 9
+    yield "gnp2000_sparse", gen.random_graph(2000, 0.001, 10), 0.1, 10
+    hub = [(0, i) for i in range(1, 12001)] + [(i, i + 1) for i in range(1, 12000, 2)]
+    yield "star12000", gen.from_edges(12001, hub, "star12000"), 0.2, 11
+    yield "complete60", gen.from_edges(60, [(i, j) for i in range(60) for j in range(i)], "k60"), 1.0, 12
+
+
+@pytest.mark.parametrize("name,G,beta,seed", list(_cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_parity_small(ldd, cuda, name, G, beta, seed):
+    shifts = gen.shifts(G.n, beta, seed)
+    assert_parity(ldd, G, shifts, beta)
+
+
+@pytest.mark.parametrize("host", [False, True], ids=["device_buffers", "host_buffers"])
+def test_host_and_device_buffers(ldd, cuda, host):
+    G = gen.rmat(11)
+    shifts = gen.shifts(G.n, 0.1, 21)
+    assert_parity(ldd, G, shifts, 0.1, host=host)
+
+
+def test_integer_shifts_ties(ldd, cuda):
+    """floor() of the shifts: every fraction is 0, so all same-level ties go to the smaller id."""
+    G = gen.grid2d(50, 41)
+    shifts = np.floor(gen.shifts(G.n, 0.05, 31))
+    assert_parity(ldd, G, shifts, 0.05)
+
+
+def test_all_equal_shifts_are_singletons(ldd, cuda):
+    """dist(v,v) - d = -d beats 1 - d: every vertex is its own piece (Eq. (1))."""
+    G = gen.grid2d(30, 30)
+    shifts = np.full(G.n, 7.25)
+    center, dist, cut, _ = assert_parity(ldd, G, shifts, 0.1)
+    assert np.array_equal(center, np.arange(G.n)) and not dist.any() and cut == G.m
+
+
+def test_large_beta_singletons(ldd, cuda):
+    """delta_max < 1: no shift can pay for one hop, every vertex is a singleton."""
+    G = gen.rmat(12)
+    shifts = gen.shifts(G.n, 1e4, 41)
+    assert shifts.max() < 1.0
+    center, dist, cut, _ = assert_parity(ldd, G, shifts, 1e4)
+    assert np.array_equal(center, np.arange(G.n)) and cut == G.m
+
+
+def test_small_beta_one_piece_per_component(ldd, cuda):
+    """One shift far above every distance: its vertex takes its whole component
+    and dist is the BFS distance (the beta -> 0 limit)."""
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+
+    G = gen.rmat(11)
+    shifts = gen.shifts(G.n, 1.0, 51)
+    ncomp, labels = cg.connected_components(sp.csr_matrix(
+        (np.ones(G.nnz), G.col, G.row_ptr), shape=(G.n, G.n)), directed=False)
+    big = {}
+    for v in range(G.n):
+        big.setdefault(labels[v], v)
+    for lab, v in big.items():
+        shifts[v] = 1e6
+    center, dist, _, _ = assert_parity(ldd, G, shifts, 1e-5)
+    for lab, v in big.items():
+        assert (center[labels == lab] == v).all()
+
+
+def test_bucket_table_regrowth(ldd, cuda):
+    """A tiny graph with a tiny beta has floor(delta_max) > n: the start-bucket
+    table is regrown and the BFS rerun."""
+    G = gen.grid2d(3, 4)
+    shifts = gen.shifts(G.n, 0.001, 61)
+    assert math.floor(shifts.max()) + 2 > G.n + 2
+    assert_parity(ldd, G, shifts, 0.001)
+
+
+def test_no_edges_and_single_vertex(ldd, cuda):
+    G = gen.from_edges(100, [], "empty100")
+    center, dist, cut, _ = assert_parity(ldd, G, gen.shifts(100, 0.1, 71), 0.1)
+    assert np.array_equal(center, np.arange(100)) and cut == 0
+    G1 = gen.from_edges(1, [], "single")
+    assert_parity(ldd, G1, gen.shifts(1, 0.1, 72), 0.1)
+
+
+def test_zero_vertices(ldd, cuda):
+    g = ldd.LddGraph(np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32))
+    g.decompose(0.1, np.zeros(0), np.zeros(0, dtype=np.int32), np.zeros(0, dtype=np.int32))
+    assert g.cut_edges(np.zeros(0, dtype=np.int32)) == 0
+    g.close()
+
+
+def test_determinism(ldd, cuda):
+    G = gen.rmat(13)
+    shifts = gen.shifts(G.n, 0.1, 81)
+    runs = [run_gpu(ldd, G, shifts)[:3] for _ in range(4)]
+    for c, d, k in runs[1:]:
+        assert np.array_equal(c, runs[0][0]) and np.array_equal(d, runs[0][1]) and k == runs[0][2]
+
+
+def test_repeated_calls_one_graph(ldd, cuda):
+    """One graph object, many decompositions with different betas and seeds."""
+    import torch
+
+    G = gen.rmat(12)
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    c = torch.empty(G.n, dtype=torch.int32, device=cuda)
+    d = torch.empty(G.n, dtype=torch.int32, device=cuda)
+    for i, beta in enumerate([0.02, 0.5, 0.1, 0.002, 3.0]):
+        shifts = gen.shifts(G.n, beta, 90 + i)
+        g.decompose(beta, torch.from_numpy(shifts).to(cuda), c, d)
+        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts)
+        assert np.array_equal(c.cpu().numpy(), oc) and np.array_equal(d.cpu().numpy(), od)
+        assert g.cut_edges(c) == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
+    g.close()
+
+
+@pytest.mark.parametrize("bad,status", [(float("nan"), -1), (-1.0, -1), (2.0 ** 31, -3),
+                                        (float("inf"), -3)])
+def test_bad_shift_rejected(ldd, cuda, bad, status):
+    G = gen.grid2d(20, 20)
+    shifts = gen.shifts(G.n, 0.1, 5)
+    shifts[137] = bad
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    with pytest.raises(ldd.LddError) as e:
+        g.decompose(0.1, shifts, np.empty(G.n, np.int32), np.empty(G.n, np.int32))
+    assert e.value.status == status
+    # the graph stays usable
+    good = gen.shifts(G.n, 0.1, 6)
+    c, d = np.empty(G.n, np.int32), np.empty(G.n, np.int32)
+    g.decompose(0.1, good, c, d)
+    oc, od = oracle.oracle_ldd(G.row_ptr, G.col, good)
+    assert np.array_equal(c, oc) and np.array_equal(d, od)
+    g.close()
+
+
+@pytest.mark.parametrize("beta", [0.0, -0.5, float("nan"), float("inf")])
+def test_bad_beta_rejected(ldd, cuda, beta):
+    G = gen.grid2d(5, 5)
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    with pytest.raises(ldd.LddError) as e:
+        g.decompose(beta, gen.shifts(G.n, 0.1, 1), np.empty(G.n, np.int32), np.empty(G.n, np.int32))
+    assert e.value.status == ldd.LDD_ERR_ARG
+    g.close()
+
+
+def test_invalid_graphs_rejected(ldd, cuda):
+    rp = np.array([0, 1, 1], dtype=np.int32)  # arc 0->1 without 1->0
+    col = np.array([1], dtype=np.int32)
+    with pytest.raises(ldd.LddError) as e:
+        ldd.LddGraph(rp, col, validate=True)
+    assert e.value.status == ldd.LDD_ERR_GRAPH
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    col = np.array([1, 5], dtype=np.int32)  # out of range
+    with pytest.raises(ldd.LddError) as e:
+        ldd.LddGraph(rp, col, validate=True)
+    assert e.value.status == ldd.LDD_ERR_GRAPH
+    with pytest.raises(ldd.LddError) as e:
+        ldd.ldd_create_graph(2, 2, np.array([0, 2, 1], dtype=np.int32), np.array([1, 0], dtype=np.int32), 1)
+    assert e.value.status == ldd.LDD_ERR_GRAPH
+
+
+def test_stream_and_timing(ldd, cuda):
+    import torch
+
+    G = gen.rmat(12)
+    shifts = gen.shifts(G.n, 0.1, 3)
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    s = torch.cuda.Stream()
+    g.set_stream(s)
+    g.set_timing(True)
+    c = torch.empty(G.n, dtype=torch.int32, device=cuda)
+    d = torch.empty(G.n, dtype=torch.int32, device=cuda)
+    with torch.cuda.stream(s):
+        sh = torch.from_numpy(shifts).to(cuda)
+    s.synchronize()
+    g.decompose(0.1, sh, c, d)
+    st = g.stats()
+    assert st["ms_bfs"] >= 0 and st["ms_total"] >= st["ms_bfs"] and st["launches"] > 0
+    oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts)
+    assert np.array_equal(c.cpu().numpy(), oc)
+    g.close()
