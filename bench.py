@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Benchmark of the exponential-shift low-diameter decomposition on GB300.
+
+Workload (default, --workload rmat22): R-MAT scale 22 (edge factor 16,
+a,b,c,d = .57,.19,.19,.05, graph seed 7, symmetrised, self-loops and repeated
+arcs removed), shifts delta_u = -ln(U_u)/beta from Philox4x32-10 seed 1, one
+decomposition per beta in {0.02, 0.1, 0.5}.  One step = those three
+decompositions plus the cut-edge count of each (every row of the hot path:
+split, fraction rank, start buckets, BFS rounds, assignment, cut count).
+
+Metric: GTEPS = undirected edges m x decompositions / second (Graph500
+convention), whole job over all ranks.  `value` is device time with the graph
+and the shifts resident in HBM (CUDA events around every step on the
+library's stream; L2 flushed between steps, outside the events).  `e2e`
+repeats the step through the same C ABI with host buffers (pinned), so the
+shift upload, the result download and all host work are inside the clock.
+
+Under torchrun (N > 1) every rank decomposes its own replica (the method has
+no exchange step): value = N x per-rank work / the slowest rank's time.
+
+--impl reference runs the CPU oracle (the method's plain definition, single
+threaded) on the same workload, one decomposition per step, beta cycling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------------- distributed helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def reduce_max(dist, x: float, device=None) -> float:
+    """Max of a float over ranks (the slowest rank sets the job time)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(dist, x: float, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- workload
+def make_workload(name):
+    import ldd_gen as gen
+
+    spec = gen.WORKLOADS[name]
+    t0 = time.perf_counter()
+    G = gen.make_graph(spec["graph"])
+    t_graph = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    shifts = [gen.shifts(G.n, b, spec["shift_seed"]) for b in spec["betas"]]
+    t_shift = time.perf_counter() - t0
+    return spec, G, shifts, t_graph, t_shift
+
+
+def describe(name, spec, G):
+    g = spec["graph"]
+    if g[0] == "rmat":
+        gdesc = f"R-MAT scale {g[1]}, edge factor {g[2]}, (a,b,c)=({g[3]},{g[4]},{g[5]}), seed {g[6]}, symmetrised, dedup"
+    elif g[0] == "grid3d":
+        gdesc = f"3D 6-neighbour grid {g[1]}x{g[2]}x{g[3]}"
+    else:
+        gdesc = f"2D 4-neighbour grid {g[1]}x{g[2]}"
+    return {"workload": name, "graph": gdesc, "n": G.n, "m": G.m, "nnz": G.nnz,
+            "betas": list(spec["betas"]), "shift_seed": spec["shift_seed"],
+            "shifts": "FP64, delta=-ln(U)/beta, U from Philox4x32-10",
+            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, outside the timed events)"}
+
+
+def bfs_algorithmic_bytes(st, n):
+    """Minimum bytes the BFS kernel must move for one launch (push accounting):
+    per scanned arc 4 B of col + 8 B of the target key (probe / atomicMin);
+    per expanded vertex 8 B row_ptr + 8 B own key + 24 B queue write and read;
+    per start-bucket entry 4 B vertex id + 8 B key test."""
+    return 12 * st["edges"] + 40 * st["items"] + 12 * n
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_1307_3692_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per BFS launch from the committed ncu summary, if it was taken
+    on the kernels as they are now (same source hash); else None."""
+    path = os.path.join(ROOT, "profiles", f"k_bfs_{workload}.md")
+    if not os.path.exists(path):
+        return None, None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, _, v = line.strip()[2:].partition(":")
+            vals[k.strip()] = v.strip().strip("`")
+    sha = vals.get("source_sha")
+    try:
+        traffic = float(vals.get("dram_bytes_per_launch", "nan"))
+    except ValueError:
+        return None, sha
+    if sha != kernel_source_sha() or not math.isfinite(traffic):
+        return None, sha
+    return traffic, sha
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------- oracle (CPU) leg
+def run_oracle(G, shifts_list):
+    import oracle
+
+    t0 = time.perf_counter()
+    for sh in shifts_list:
+        c, _ = oracle.oracle_ldd(G.row_ptr, G.col, sh)
+        oracle.oracle_cut_edges(G.row_ptr, G.col, c)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args):
+    """The oracle as the reference implementation: rank 0 only."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    spec, G, shifts, _, _ = make_workload(args.workload)
+    betas = spec["betas"]
+    for i in range(args.warmup):
+        run_oracle(G, [shifts[i % len(betas)]])
+    times = []
+    for i in range(args.steps):
+        times.append(run_oracle(G, [shifts[i % len(betas)]]))
+    total = sum(times)
+    value = G.m * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": "LDD GTEPS", "value": value, "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+int64", "data": "synthetic",
+        "config": describe(args.workload, spec, G) | {"step": "one decomposition + cut count, beta cycling"},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} single decompositions of the {args.workload} workload"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def our_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_1307_3692_gb300 as ldd
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+
+    spec, G, shifts, t_graph, t_shift = make_workload(args.workload)
+    betas = spec["betas"]
+    n, m = G.n, G.m
+    g = ldd.LddGraph(torch.from_numpy(G.row_ptr).to(dev), torch.from_numpy(G.col).to(dev), validate=False)
+    stream = torch.cuda.Stream(device=dev)
+    g.set_stream(stream)
+    g.set_timing(True)
+    d_shifts = [torch.from_numpy(s).to(dev) for s in shifts]
+    center = torch.empty(n, dtype=torch.int32, device=dev)
+    dist_out = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(record=None):
+        launches = 0
+        for b, sh in zip(betas, d_shifts):
+            g.decompose(b, sh, center, dist_out)
+            g.cut_edges(center)
+            st = g.stats()
+            launches += st["launches"] + st["cut_launches"]
+            if record is not None:
+                record.append(st)
+        return launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    per_beta = []
+    step_ms = []
+    launches = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+            ev[i][0].record(stream)
+            launches += step(per_beta)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier(dist)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_ms = sum(step_ms) / args.steps
+    ms_per_step = reduce_max(dist, local_ms, dev)
+    work = len(betas) * m  # edges per step per rank
+    value = world * work / (ms_per_step * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the persistent BFS)
+    bfs_ms = [st["ms_bfs"] for st in per_beta]
+    bfs_bytes = [bfs_algorithmic_bytes(st, n) for st in per_beta]
+    avg_ms = sum(bfs_ms) / len(bfs_ms)
+    avg_bytes = sum(bfs_bytes) / len(bfs_bytes)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
+    traffic, traffic_sha = ncu_traffic(args.workload)
+    roofline = {"bound": "hbm", "kernel": "k_bfs", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": f"of {peak_kind}",
+                "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms}
+    # share of the step spent in each phase (device events inside the library)
+    tot = sum(st["ms_total"] for st in per_beta) + sum(st["ms_cut"] for st in per_beta)
+    phases = {k: sum(st[k] for st in per_beta) / max(tot, 1e-9) for k in
+              ("ms_rank", "ms_bfs", "ms_finalize", "ms_cut")}
+
+    # ---- end to end through the C ABI with host buffers
+    h_shifts = [torch.from_numpy(s).pin_memory() for s in shifts]
+    h_center = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_dist = torch.empty(n, dtype=torch.int32).pin_memory()
+    g_e2e = ldd.LddGraph(G.row_ptr, G.col, validate=False)
+    for b, sh in zip(betas, h_shifts):  # warm-up
+        g_e2e.decompose(b, sh, h_center, h_dist)
+        g_e2e.cut_edges(h_center)
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for b, sh in zip(betas, h_shifts):
+            g_e2e.decompose(b, sh, h_center, h_dist)
+            g_e2e.cut_edges(h_center)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    barrier(dist)
+    e2e_s = reduce_max(dist, e2e_s, dev)
+    g_e2e.close()
+    h2d = len(betas) * (8 * n + 4 * n)        # shifts in; center in for the cut count
+    d2h = len(betas) * (8 * n + 8 + 40)      # center + dist out, cut count, status header
+    e2e = {"value": world * work / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
+
+    # ---- parity spot check of the timed outputs (last beta) and CPU baseline
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts[-1])
+        assert np.array_equal(center.cpu().numpy(), oc), "timed output differs from the oracle"
+        t_cpu = run_oracle(G, shifts)
+        cpu = {"value": len(betas) * m / t_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"one full step: {len(betas)} decompositions + cut counts of {args.workload}",
+               "seconds": t_cpu}
+
+    g.close()
+    if rank == 0:
+        clk = clocks.summary()
+        line = {
+            "metric": "LDD GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": describe(args.workload, spec, G) | {
+                "step": f"{len(betas)} decompositions (one per beta) + cut counts",
+                "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "per_beta": [{"beta": b, "ms_total": st["ms_total"], "ms_rank": st["ms_rank"],
+                          "ms_bfs": st["ms_bfs"], "ms_finalize": st["ms_finalize"], "ms_cut": st["ms_cut"],
+                          "rounds": st["rounds"], "A": st["max_floor_shift"], "items": st["items"],
+                          "edges": st["edges"], "gteps": m / st["ms_total"] / 1e6}
+                         for b, st in zip(betas, per_beta[-len(betas):])],
+            "phase_share": phases,
+            "wall_s_timed_region": t_wall,
+            "host_s": {"graph_generation": t_graph, "shift_draw": t_shift},
+            "kernel_source_sha": kernel_source_sha(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

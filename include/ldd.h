@@ -119,7 +119,9 @@ const char* ldd_last_error(void);
  */
 typedef struct {
   int64_t n, nnz;
-  int64_t n_active;       /* vertices with at least one arc */
+  int64_t n_active;       /* vertices settled by the round loop: those in
+                             connected components of more than 32 vertices */
+  int64_t small_components;/* components of 2..32 vertices, solved one warp each */
   int64_t max_floor_shift;/* A = floor(delta_max) (Algorithm 1 step 2) */
   int64_t rounds;         /* synchronous BFS rounds executed */
   int64_t last_level;     /* level of the last round */

@@ -35,6 +35,8 @@ namespace ldd {
 namespace {
 
 constexpr u32 kFull = 0xffffffffu;
+constexpr int kEdgeBatch = 4;  // arcs per thread in flight
+constexpr int kWinBatch = 3;   // window items per thread in flight
 
 struct Smem {
   int owner[kBfsMaxSpan];
@@ -69,37 +71,58 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
   __syncthreads();
 }
 
-// Appends the lanes with `want` to the frontier: one atomic per warp.
+// Appends to the frontier every vertex v[i] whose bit i is set in `mask`, for
+// up to K candidates per lane, with one atomicAdd per warp: the warp scans
+// (count << 32 | degree sum) over its lanes, reserves that many queue slots
+// and edge offsets, and every lane writes its vertices in slot order.
 // qi: frontier counter index (rotates over 3), qb: queue buffer (ping-pong).
-__device__ __forceinline__ void warp_append(bool want, u32 v, const BfsArgs& a, int qi, int qb) {
+template <int K>
+__device__ __forceinline__ void warp_append(u32 mask, const u32 (&v)[K], const BfsArgs& a, int qi,
+                                            int qb) {
   const u32 lane = threadIdx.x & 31;
-  int rs = 0, d = 0;
-  if (want) {
-    rs = __ldg(a.row_ptr + v);
-    d = __ldg(a.row_ptr + v + 1) - rs;
-    want = d > 0;  // a vertex without arcs has nothing to expand
+  int rs[K], dg[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    rs[i] = 0;
+    dg[i] = 0;
+    if (mask >> i & 1u) {
+      rs[i] = __ldg(a.row_ptr + v[i]);
+      dg[i] = __ldg(a.row_ptr + v[i] + 1) - rs[i];
+    }
   }
-  const u32 m = __ballot_sync(kFull, want);
-  if (m == 0) return;
-  const u32 dd = want ? (u32)d : 0u;
-  u32 incl = dd;
+  u32 cnt = 0, dsum = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (dg[i] <= 0) {
+      mask &= ~(1u << i);  // a vertex without arcs has nothing to expand
+    } else {
+      ++cnt;
+      dsum += (u32)dg[i];
+    }
+  if (!__any_sync(kFull, mask != 0u)) return;
+  const u64 mine = ((u64)cnt << 32) | dsum;
+  u64 incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, incl, o);
+    const u64 y = __shfl_up_sync(kFull, incl, o);
     if (lane >= (u32)o) incl += y;
   }
-  const u32 tot = __shfl_sync(kFull, incl, 31);
+  const u64 tot = __shfl_sync(kFull, incl, 31);
   u64 base = 0;
-  if (lane == 0) base = atomicAdd(&a.ctl->qctr[qi], ((u64)__popc(m) << 32) | tot);
-  base = __shfl_sync(kFull, base, 0);
-  if (want) {
-    const u32 slot = (u32)(base >> 32) + __popc(m & lanemask_lt());
-    const u32 off = (u32)base + incl - dd;
-    a.qv[qb][slot] = v;
-    a.qrow[qb][slot] = rs;
-    a.qoff[qb][slot] = off;
-    for (u32 c = (off + kBfsBase - 1) / kBfsBase; c * kBfsBase < off + dd; ++c) a.cf[qb][c] = slot;
-  }
+  if (lane == 0) base = atomicAdd(&a.ctl->qctr[qi], tot);
+  base = __shfl_sync(kFull, base, 0) + (incl - mine);
+  u32 slot = (u32)(base >> 32), off = (u32)base;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (mask >> i & 1u) {
+      a.qv[qb][slot] = v[i];
+      a.qrow[qb][slot] = rs[i];
+      a.qoff[qb][slot] = off;
+      const u32 end = off + (u32)dg[i];
+      for (u32 c = (off + kBfsBase - 1) / kBfsBase; c * kBfsBase < end; ++c) a.cf[qb][c] = slot;
+      ++slot;
+      off = end;
+    }
 }
 
 // Unclaimed vertices of start bucket rr join the frontier of level rr.
@@ -111,13 +134,13 @@ __device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u3
   const u32 stride = gridDim.x * blockDim.x;
   for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < cnt; base += stride) {
     const u32 i = base + lane;
+    u32 u[1] = {0};
     bool want = false;
-    u32 u = 0;
     if (i < cnt) {
-      u = __ldg(rv + lo + i);
-      want = (u32)(ld_cg_u64(a.key + u) >> 32) == (u32)rr;
+      u[0] = __ldg(rv + lo + i);
+      want = (u32)(ld_cg_u64(a.key + u[0]) >> 32) == (u32)rr;
     }
-    warp_append(want, u, a, qi, qb);
+    warp_append<1>(want ? 1u : 0u, u, a, qi, qb);
   }
 }
 
@@ -174,33 +197,62 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
     }
     for (int j = threadIdx.x; j < len; j += kBfsThreads) s.owner[j] = 0;
     __syncthreads();
-    for (int j = threadIdx.x; j < nwin; j += kBfsThreads) {
-      const u32 it = i0 + (u32)j;
-      const u32 off = ld_cg_u32(qoff + it);
-      if (off < e1) {
-        const u32 v = ld_cg_u32(qv + it);
-        s.rowd[j] = ld_cg_i32(qrow + it) - (int)off;
-        s.cand[j] = ld_cg_u64(a.key + v) + kLevelOne;
-        atomicMax(&s.owner[off > e0 ? off - e0 : 0u], j);
+    // window: queue items covering [e0, e1); loads batched for memory-level parallelism
+    for (int j0 = 0; j0 < nwin; j0 += kBfsThreads * kWinBatch) {
+      u32 off[kWinBatch], v[kWinBatch];
+      int row[kWinBatch];
+#pragma unroll
+      for (int i = 0; i < kWinBatch; ++i) {
+        const int j = j0 + i * kBfsThreads + (int)threadIdx.x;
+        off[i] = e1;
+        if (j < nwin) {
+          off[i] = ld_cg_u32(qoff + i0 + j);
+          v[i] = ld_cg_u32(qv + i0 + j);
+          row[i] = ld_cg_i32(qrow + i0 + j);
+        }
       }
+      u64 kv[kWinBatch];
+#pragma unroll
+      for (int i = 0; i < kWinBatch; ++i)
+        if (off[i] < e1) kv[i] = ld_cg_u64(a.key + v[i]);
+#pragma unroll
+      for (int i = 0; i < kWinBatch; ++i)
+        if (off[i] < e1) {
+          const int j = j0 + i * kBfsThreads + (int)threadIdx.x;
+          s.rowd[j] = row[i] - (int)off[i];
+          s.cand[j] = kv[i] + kLevelOne;
+          atomicMax(&s.owner[off[i] > e0 ? off[i] - e0 : 0u], j);
+        }
     }
     __syncthreads();
     block_max_scan(s, len);
     __syncthreads();
-    for (int base = 0; base < len; base += kBfsThreads) {
-      const int kk = base + threadIdx.x;
-      bool want = false;
-      u32 w = 0;
-      if (kk < len) {
-        const int j = s.owner[kk];
-        w = (u32)__ldg(a.col + (s.rowd[j] + (int)(e0 + kk)));
-        const u64 cand = s.cand[j];
-        if (w < a.n && cand < ld_cg_u64(a.key + w)) {
-          const u64 old = atomicMin(a.key + w, cand);
-          want = (u32)(old >> 32) > lvl_next;
+    // edges: all loads of a batch first, then all probes, then the atomics
+    for (int base = 0; base < len; base += kBfsThreads * kEdgeBatch) {
+      u32 w[kEdgeBatch];
+      u64 cand[kEdgeBatch];
+#pragma unroll
+      for (int i = 0; i < kEdgeBatch; ++i) {
+        const int kk = base + i * kBfsThreads + (int)threadIdx.x;
+        w[i] = 0xffffffffu;
+        cand[i] = 0;
+        if (kk < len) {
+          const int j = s.owner[kk];
+          cand[i] = s.cand[j];
+          w[i] = (u32)__ldg(a.col + (s.rowd[j] + (int)(e0 + kk)));
         }
       }
-      warp_append(want, w, a, qi, qb);
+      u64 cur[kEdgeBatch];
+#pragma unroll
+      for (int i = 0; i < kEdgeBatch; ++i) cur[i] = (w[i] < a.n) ? ld_cg_u64(a.key + w[i]) : 0ull;
+      u32 mask = 0;
+#pragma unroll
+      for (int i = 0; i < kEdgeBatch; ++i)
+        if (cand[i] < cur[i]) {
+          const u64 old = atomicMin(a.key + w[i], cand[i]);
+          if ((u32)(old >> 32) > lvl_next) mask |= 1u << i;
+        }
+      warp_append<kEdgeBatch>(mask, w, a, qi, qb);
     }
     __syncthreads();
   }
@@ -244,6 +296,7 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
       const int start = __ldg(a.bptr + lvl + 1);
       if ((u32)start >= a.n) break;
       const int rr = (int)__ldg(rk + start);  // next non-empty start bucket
+      if (rr > A) break;                      // only vertices the BFS does not handle remain
       append_bucket(a, rr, rv, qi, qb);
       nlvl = rr;
     }

@@ -10,6 +10,8 @@
 //  4. start buckets (Section 4: the super-source edge of length L is looked at
 //     when the frontier reaches distance L): stable sort of the vertices by
 //     R_u, and bptr[r] = first position with R >= r, for r = 0 .. A + 1.
+//     Vertices the BFS does not handle (no arcs, or a component small enough
+//     for the warp solver) sort with R = A + 1, after every real bucket.
 //
 // The radix sort is a single-pass-per-digit ("onesweep") LSD sort: one kernel
 // per 8-bit digit; each 4096-key tile ranks its keys in shared memory with
@@ -235,9 +237,10 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 // rank -> key, and the start-round sort input (R_u, u) in rank order.
 __global__ void __launch_bounds__(256) k_rank_keys(const u32* __restrict__ v0,
                                                    const u32* __restrict__ v1,
-                                                   const int* __restrict__ a, Control* ctl, u32 n,
-                                                   u32* __restrict__ order, u64* __restrict__ key,
-                                                   u64* kR, u32* vR) {
+                                                   const int* __restrict__ a,
+                                                   const u32* __restrict__ excl, Control* ctl,
+                                                   u32 n, u32* __restrict__ order,
+                                                   u64* __restrict__ key, u64* kR, u32* vR) {
   __shared__ u32 sh[kRoundDigits][256];
   const u32 tid = threadIdx.x, lane = tid & 31;
   for (u32 i = tid; i < kRoundDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
@@ -260,6 +263,7 @@ __global__ void __launch_bounds__(256) k_rank_keys(const u32* __restrict__ v0,
       order[p] = u;
       R = (u32)(A - a[u]);
       key[u] = ((u64)R << 32) | p;
+      if (excl[u >> 5] >> (u & 31) & 1u) R = (u32)A + 1u;
       kR[p] = R;
       vR[p] = u;
     }
@@ -298,7 +302,8 @@ __global__ void __launch_bounds__(256) k_bucket_ptr(const u64* __restrict__ k0,
 
 int launch_rank_and_buckets(const double* d_shift, u32 n, int* d_a, u64* k0, u32* v0, u64* k1,
                             u32* v1, u64* status, u32* epoch, u32* order, u64* key, int* bptr,
-                            u32 bptr_cap, Control* ctl, int num_sms, cudaStream_t s) {
+                            u32 bptr_cap, const u32* excl, Control* ctl, int num_sms,
+                            cudaStream_t s) {
   const u32 gs = (u32)min((long long)(n + 255) / 256, (long long)num_sms * 8);
   const u32 ntiles = (n + kSortTile - 1) / kSortTile;
   int launches = 0;
@@ -314,7 +319,7 @@ int launch_rank_and_buckets(const double* d_shift, u32 n, int* d_a, u64* k0, u32
                                                &ctl->err);
     ++launches;
   }
-  k_rank_keys<<<gs, 256, 0, s>>>(v0, v1, d_a, ctl, n, order, key, k0, v0);
+  k_rank_keys<<<gs, 256, 0, s>>>(v0, v1, d_a, excl, ctl, n, order, key, k0, v0);
   ++launches;
   k_scan_digits<<<1, 256, 0, s>>>(&ctl->hist_r[0][0], &ctl->off_r[0][0], &ctl->mask_r,
                                   kRoundDigits, n);

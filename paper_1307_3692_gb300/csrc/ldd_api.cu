@@ -5,7 +5,8 @@
 //   step 2 (delta_max)   : k_split_hist                       (k_rank.cu)
 //   Section 4 tie-break  : fraction rank sort, keys, buckets   (k_rank.cu)
 //   step 3 (BFS)         : persistent cooperative k_bfs        (k_bfs.cu)
-//   step 4 (assignment)  : k_finalize                          (k_finalize_cut.cu)
+//                          and k_small_comp for components of <= 32 vertices
+//   step 4 (assignment)  : k_finalize                          (k_graph.cu)
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -99,6 +100,8 @@ struct ldd_graph {
   int* d_col = nullptr;
   u32* d_nzv = nullptr;       // vertices with at least one arc, ascending
   u32* d_cut_first = nullptr; // per cut span: index into d_nzv of the row holding its first arc
+  u32* d_excl = nullptr;      // bit v: v is not handled by the BFS (no arcs or a small component)
+  SmallComps sc;              // components of 2..32 vertices, solved one warp each
   // scratch arena
   void* arena = nullptr;
   double* d_shift = nullptr;
@@ -136,6 +139,11 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_col);
   cudaFree(g->d_nzv);
   cudaFree(g->d_cut_first);
+  cudaFree(g->d_excl);
+  cudaFree(g->sc.comp_off);
+  cudaFree(g->sc.comp_len);
+  cudaFree(g->sc.comp_v);
+  cudaFree(g->sc.adj);
   cudaFree(g->arena);
   cudaFree(g->d_bptr);
   if (g->h_hdr) cudaFreeHost(g->h_hdr);
@@ -207,6 +215,63 @@ int alloc_scratch(ldd_graph* g) {
   return LDD_OK;
 }
 
+// Component labels and the small-component tables (two device phases, the
+// table sizes read back in between).
+int build_component_tables(ldd_graph* g) {
+  const size_t n = (size_t)g->n;
+  if (cudaMalloc(&g->d_excl, std::max<size_t>((n + 31) / 32, 1) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "device allocation of the exclusion bitmask failed");
+  }
+  if (n == 0) return LDD_OK;
+  const size_t words = 7 * n + 2 * (n / 2 + 1) + 3;
+  u32* tmp = nullptr;
+  if (cudaMalloc(&tmp, words * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "device allocation for component labelling failed");
+  }
+  CompScratch t;
+  t.parent = tmp;
+  t.csize = tmp + n;
+  t.root_off = tmp + 2 * n;
+  t.fill = tmp + 3 * n;
+  t.lane_of = tmp + 4 * n;
+  t.comp_v = tmp + 5 * n;
+  t.comp_off = tmp + 6 * n;
+  t.comp_len = t.comp_off + (n / 2 + 1);
+  t.counters = t.comp_len + (n / 2 + 1);
+  u32 counts[3] = {0, 0, 0};
+  cudaError_t e = components_phase1(g->d_row, g->d_col, g->d_nzv, g->d_cut_first, g->cut_items,
+                                    (u32)n, (u32)g->nnz, g->num_sms, t, g->d_excl, counts, nullptr);
+  int rc = LDD_OK;
+  SmallComps& sc = g->sc;
+  if (e != cudaSuccess) {
+    rc = fail(LDD_ERR_CUDA, "component labelling failed: %s", cudaGetErrorString(e));
+  } else {
+    sc.ncomp = counts[0];
+    sc.total = counts[1];
+    g->n_active = counts[2];
+    if (sc.ncomp > 0 &&
+        (cudaMalloc(&sc.comp_off, sc.ncomp * 4) != cudaSuccess ||
+         cudaMalloc(&sc.comp_len, sc.ncomp * 4) != cudaSuccess ||
+         cudaMalloc(&sc.comp_v, sc.total * 4) != cudaSuccess ||
+         cudaMalloc(&sc.adj, sc.total * 4) != cudaSuccess)) {
+      cudaGetLastError();
+      rc = fail(LDD_ERR_OOM, "device allocation of the component tables failed");
+    } else if (sc.ncomp > 0) {
+      if (cudaMemcpy(sc.comp_off, t.comp_off, sc.ncomp * 4, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+          cudaMemcpy(sc.comp_len, t.comp_len, sc.ncomp * 4, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+          cudaMemcpy(sc.comp_v, t.comp_v, sc.total * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+        rc = fail(LDD_ERR_CUDA, "copy of the component tables failed");
+      else if ((e = components_phase2(g->d_row, g->d_col, t, sc, g->num_sms, nullptr)) !=
+               cudaSuccess)
+        rc = fail(LDD_ERR_CUDA, "component adjacency failed: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaFree(tmp);
+  return rc;
+}
+
 void record(ldd_graph* g, int i) {
   if (g->timing) cudaEventRecord(g->ev[i], g->stream);
 }
@@ -243,10 +308,12 @@ BfsArgs bfs_args(ldd_graph* g) {
   return a;
 }
 
-// BFS + finalize into (center, dist) device buffers.  Returns launches or <0.
+// Small components, BFS and finalize into (center, dist) device buffers.
+// Returns launches or < 0.
 int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
   int launches = 0;
   cudaStream_t s = g->stream;
+  launches += launch_small_comp(g->sc, g->d_key, &g->d_ctl->err, g->num_sms, s);
   if (g->n_active > 0) {
     cudaError_t e;
     if (launch_bfs(bfs_args(g), g->bfs_grid, s, &e) < 0) {
@@ -347,8 +414,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   nzv.reserve((size_t)n);
   for (int32_t v = 0; v < n; ++v)
     if (rp[v + 1] > rp[v]) nzv.push_back((u32)v);
-  g->n_active = (u32)nzv.size();
-  g->cut_items = g->n_active;
+  g->cut_items = (u32)nzv.size();
   const size_t nch = ((size_t)nnz + kCutSpan - 1) / kCutSpan;
   std::vector<u32> first(nch + 1, 0);
   {
@@ -374,6 +440,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
       cudaMemcpy(g->d_cut_first, first.data(), first.size() * 4, cudaMemcpyHostToDevice) !=
           cudaSuccess)
     return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
+  if ((rc = build_component_tables(g)) != LDD_OK) return bail(rc);
   if ((rc = alloc_scratch(g)) != LDD_OK) return bail(rc);
   if (cudaMallocHost(&g->h_hdr, 256) != cudaSuccess)
     return bail(fail(LDD_ERR_OOM, "pinned host allocation failed"));
@@ -390,6 +457,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   g->stats.n = n;
   g->stats.nnz = nnz;
   g->stats.n_active = g->n_active;
+  g->stats.small_components = g->sc.ncomp;
   g->stats.bfs_grid = g->bfs_grid;
   g->stats.bfs_block = kBfsThreads;
   *out = g;
@@ -453,7 +521,7 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
   record(g, 1);
   launches += launch_rank_and_buckets(d_shift, (u32)n, g->d_a, g->d_k[0], g->d_v[0], g->d_k[1],
                                       g->d_v[1], g->d_status, &g->epoch, g->d_order, g->d_key,
-                                      g->d_bptr, g->bptr_cap, g->d_ctl, g->num_sms, s);
+                                      g->d_bptr, g->bptr_cap, g->d_excl, g->d_ctl, g->num_sms, s);
   record(g, 2);
   int status = LDD_OK;
   int l = run_bfs_finalize(g, center, dist, &status);

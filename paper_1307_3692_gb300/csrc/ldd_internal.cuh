@@ -43,9 +43,12 @@ constexpr int kBfsThreads = 512;
 constexpr int kBfsBase = 256;
 constexpr int kBfsMaxSpan = 4096;
 
-// Cut counter: edges per CTA.
+// Cut counter and other arc-parallel kernels: arcs per CTA.
 constexpr int kCutThreads = 256;
 constexpr int kCutSpan = 2048;
+
+// Components with at most this many vertices are solved by one warp each.
+constexpr u32 kSmallComp = 32;
 
 // Device control block; cudaMemsetAsync(0) at the start of every decomposition.
 // The header (err .. cut) is copied back to the host after every call.
@@ -92,11 +95,38 @@ struct BfsArgs {
   u32 spin_limit;
 };
 
+// Components of 2..kSmallComp vertices (k_graph.cu): comp c has comp_len[c]
+// members comp_v[comp_off[c] ..], with adjacency masks over member lanes in adj.
+struct SmallComps {
+  u32 ncomp = 0;
+  u32 total = 0;
+  u32* comp_off = nullptr;
+  u32* comp_len = nullptr;
+  u32* comp_v = nullptr;
+  u32* adj = nullptr;
+};
+
+// Temporary device memory for labelling components at graph creation.
+struct CompScratch {
+  u32* parent;    // [n]
+  u32* csize;     // [n]
+  u32* root_off;  // [n]
+  u32* fill;      // [n]
+  u32* lane_of;   // [n]
+  u32* comp_off;  // [n / 2 + 1]
+  u32* comp_len;  // [n / 2 + 1]
+  u32* comp_v;    // [n]
+  u32* counters;  // [3]: components, members, vertices left to the BFS
+};
+
 // ---------------------------------------------------------------- launchers
 // Fraction rank and start buckets (k_rank.cu).  Returns kernels launched.
+// Vertices with bit v of excl set get the start round A + 1 in the bucket sort,
+// i.e. they stay out of the BFS start buckets 0..A.
 int launch_rank_and_buckets(const double* d_shift, u32 n, int* d_a, u64* k0, u32* v0, u64* k1,
                             u32* v1, u64* status, u32* epoch, u32* order, u64* key, int* bptr,
-                            u32 bptr_cap, Control* ctl, int num_sms, cudaStream_t s);
+                            u32 bptr_cap, const u32* excl, Control* ctl, int num_sms,
+                            cudaStream_t s);
 int launch_bucket_ptr(const u64* k0, const u64* k1, Control* ctl, u32 n, int* bptr, u32 cap,
                       int num_sms, cudaStream_t s);
 // Persistent BFS (k_bfs.cu).  Returns kernels launched, or -1 with the CUDA
@@ -104,11 +134,20 @@ int launch_bucket_ptr(const u64* k0, const u64* k1, Control* ctl, u32 n, int* bp
 int bfs_grid_size(int num_sms, int* blocks_per_sm);
 int launch_bfs(const BfsArgs& a, int grid, cudaStream_t s, cudaError_t* err);
 size_t bfs_smem_bytes();
-// Finalize and cut (k_finalize_cut.cu).
+// Finalize, cut and per-graph component tables (k_graph.cu).
 int launch_finalize(const u64* key, const u32* order, u32 n, int* center, int* dist,
                     const u32* err, int num_sms, cudaStream_t s);
 int launch_cut(const int* row_ptr, const int* col, const u32* nzv, const u32* cut_first,
                u32 n_items, u32 nnz, u32 n_vert, const int* center, u64* out, cudaStream_t s);
+int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s);
+// Labels components and fills t.comp_* and excl (bit v: kept out of the BFS);
+// counts = {small components, their members, vertices left to the BFS}.
+cudaError_t components_phase1(const int* row_ptr, const int* col, const u32* nzv,
+                              const u32* cut_first, u32 n_items, u32 n, u32 nnz, int num_sms,
+                              const CompScratch& t, u32* excl, u32 counts[3], cudaStream_t s);
+// Adjacency masks of the small-component members (sc.comp_v already filled).
+cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,
+                              const SmallComps& sc, int num_sms, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ u32 lanemask_lt() {

@@ -207,3 +207,73 @@ def test_stream_and_timing(ldd, cuda):
     oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts)
     assert np.array_equal(c.cpu().numpy(), oc)
     g.close()
+
+
+def _disjoint_union(parts, name):
+    edges, off = [], 0
+    for n_i, e_i in parts:
+        edges += [(u + off, v + off) for u, v in e_i]
+        off += n_i
+    return gen.from_edges(off, edges, name)
+
+
+def test_component_size_boundaries(ldd, cuda):
+    """Components of 2..32 vertices go to the warp solver, larger ones to the
+    BFS rounds: paths, cliques and stars on both sides of the 32 boundary."""
+    def path(k):
+        return k, [(i, i + 1) for i in range(k - 1)]
+
+    def clique(k):
+        return k, [(i, j) for i in range(k) for j in range(i)]
+
+    def star(k):
+        return k, [(0, i) for i in range(1, k)]
+
+    parts = [path(1), path(2), path(3), path(31), path(32), path(33), clique(32), clique(33),
+             star(32), star(33), path(200), (7, [])]
+    G = _disjoint_union(parts * 3, "mixed_components")
+    for seed, beta in [(1, 0.05), (2, 0.3), (3, 2.0)]:
+        shifts = gen.shifts(G.n, beta, seed)
+        _, _, _, st = assert_parity(ldd, G, shifts, beta)
+    # small: 2, 3, 31, 32 (path), 32 (clique), 32 (star) per copy
+    assert st["small_components"] == 3 * 6
+    assert st["n_active"] == 3 * (33 + 33 + 33 + 200)
+    shifts = np.floor(gen.shifts(G.n, 0.2, 4))  # exact ties inside the small components
+    assert_parity(ldd, G, shifts, 0.2)
+
+
+def test_many_small_components_and_a_giant(ldd, cuda):
+    """R-MAT plus thousands of tiny components: the structure that makes the
+    delayed-start rounds run to floor(delta_max) without the component split."""
+    rng = np.random.default_rng(5)
+    base = gen.rmat(13)
+    parts = [(base.n, [(v, int(w)) for v in range(base.n)
+                       for w in base.col[base.row_ptr[v]:base.row_ptr[v + 1]] if v < w])]
+    for _ in range(3000):
+        k = int(rng.integers(2, 9))
+        parts.append((k, [(i, int(rng.integers(0, i))) for i in range(1, k)]))
+    G = _disjoint_union(parts, "rmat13_plus_trees")
+    for beta in (0.02, 0.5):
+        _, _, _, st = assert_parity(ldd, G, gen.shifts(G.n, beta, 77), beta)
+        assert st["small_components"] >= 3000
+
+
+def test_component_labels_deep_trees(ldd, cuda):
+    """Long paths and a broom give deep union-find trees; the component split
+    must match scipy's labelling (reported counts) and the oracle."""
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+
+    k = 60000
+    edges = [(i, i + 1) for i in range(k - 1)]                     # a long path
+    edges += [(k + i, k + i + 1) for i in range(40)]               # a 41-vertex path
+    edges += [(k + 41 + i, k + 41 + i + 1) for i in range(20)]     # a 21-vertex path
+    edges += [(k + 62, k + 63 + i) for i in range(500)]            # a star (broom head)
+    G = gen.from_edges(k + 563 + 5, edges, "paths_and_broom")
+    A = sp.csr_matrix((np.ones(G.nnz), G.col, G.row_ptr), shape=(G.n, G.n))
+    _, lab = cg.connected_components(A, directed=False)
+    sz = np.bincount(lab)
+    for beta, seed in [(0.05, 1), (0.01, 2)]:
+        _, _, _, st = assert_parity(ldd, G, gen.shifts(G.n, beta, seed), beta)
+        assert st["small_components"] == int(((sz >= 2) & (sz <= 32)).sum())
+        assert st["n_active"] == int(sz[lab][sz[lab] > 32].size)
