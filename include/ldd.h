@@ -98,6 +98,34 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
  */
 int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut);
 
+/*
+ * ldd_cut_edges_noalloc -- the same count as ldd_cut_edges, for callers that
+ * must not allocate device memory when they ask for it: for example a process
+ * whose framework allocator owns the whole device memory pool, where a foreign
+ * cudaMalloc can fail or upset the pool's accounting, or a latency-critical
+ * loop that cannot afford the device-wide synchronisation of cudaMalloc and
+ * cudaFree.  It needs no graph object (ldd_create_graph allocates) and makes
+ * no allocation of its own; the paper has no counterpart to this entry point.
+ *   n, nnz      sizes as in ldd_create_graph; nnz must be <= 2^27 (134,217,728
+ *               arcs), the limit of the scratch below, else LDD_ERR_RANGE.
+ *   row_ptr, col_idx, center
+ *               device memory of the current CUDA device (host pointers give
+ *               LDD_ERR_ARG); layouts as in ldd_create_graph / ldd_cut_edges.
+ *               The CSR is trusted: it is not validated.
+ *   out_cut     host or device int64: receives the count.
+ *   cuda_stream the stream to run on (NULL: the legacy default stream); the
+ *               call returns after that stream has finished the work.
+ * Scratch: a fixed array of about 256 KiB in the library's device image,
+ * present on every GPU that loads the library until the process exits.  The
+ * first call on each device looks up that array's device address; make that
+ * first call before any stream capture begins.  Every call reuses the same
+ * array and clears the part that must start at zero, so two calls whose work
+ * overlaps on the GPU (different streams or threads) race and must be
+ * serialised by the caller.
+ */
+int ldd_cut_edges_noalloc(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                          const int32_t* center, int64_t* out_cut, void* cuda_stream);
+
 /* ldd_set_stream -- queue all later work of g on this cudaStream_t (NULL:
  * the legacy default stream).  A torch.cuda.Stream's .cuda_stream works. */
 int ldd_set_stream(ldd_graph* g, void* cuda_stream);

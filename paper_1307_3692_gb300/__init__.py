@@ -24,7 +24,7 @@ from ._build import LIB as _LIB_PATH
 __all__ = [
     "LddError", "LddGraph", "ldd_create_graph", "ldd_decompose", "ldd_cut_edges",
     "ldd_set_stream", "ldd_destroy_graph", "ldd_status_string", "ldd_last_error",
-    "ldd_get_stats", "ldd_set_timing", "library_path", "LDD_OK", "LDD_ERR_ARG",
+    "ldd_get_stats", "ldd_set_timing", "ldd_cut_edges_noalloc", "library_path", "LDD_OK", "LDD_ERR_ARG",
     "LDD_ERR_GRAPH", "LDD_ERR_RANGE", "LDD_ERR_OOM", "LDD_ERR_CUDA", "LDD_ERR_TIMEOUT",
 ]
 
@@ -54,6 +54,8 @@ _lib.ldd_decompose.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.ldd_decompose.restype = ctypes.c_int
 _lib.ldd_cut_edges.argtypes = [_vp, _vp, ctypes.POINTER(_i64)]
 _lib.ldd_cut_edges.restype = ctypes.c_int
+_lib.ldd_cut_edges_noalloc.argtypes = [_i32, _i64, _vp, _vp, _vp, _vp, _vp]
+_lib.ldd_cut_edges_noalloc.restype = ctypes.c_int
 _lib.ldd_set_stream.argtypes = [_vp, _vp]
 _lib.ldd_set_stream.restype = ctypes.c_int
 _lib.ldd_destroy_graph.argtypes = [_vp]
@@ -135,6 +137,18 @@ def ldd_cut_edges(g: int, center, n: int | None = None) -> int:
     out = _i64(0)
     _check(_lib.ldd_cut_edges(g, _addr(center, "i32", n, "center"), ctypes.byref(out)),
            "ldd_cut_edges")
+    return int(out.value)
+
+
+def ldd_cut_edges_noalloc(n: int, nnz: int, row_ptr, col_idx, center, stream=None) -> int:
+    """Cut count from device-resident CSR and labels, with no device allocation
+    (see include/ldd.h for who needs this and its limits)."""
+    out = _i64(0)
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(_lib.ldd_cut_edges_noalloc(n, nnz, _addr(row_ptr, "i32", n + 1, "row_ptr"),
+                                      _addr(col_idx, "i32", nnz, "col_idx"),
+                                      _addr(center, "i32", n, "center"), ctypes.byref(out),
+                                      handle or 0), "ldd_cut_edges_noalloc")
     return int(out.value)
 
 

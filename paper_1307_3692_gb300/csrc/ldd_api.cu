@@ -87,6 +87,12 @@ u32 env_u32(const char* name, u32 dflt) {
 
 }  // namespace
 
+namespace ldd {
+// Sets the text ldd_last_error() returns on this thread (used by entry points
+// defined in other translation units).
+void record_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace ldd
+
 struct ldd_graph {
   int32_t n = 0;
   int64_t nnz = 0;
