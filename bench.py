@@ -172,11 +172,13 @@ def describe(name, spec, G):
 
 
 def bfs_algorithmic_bytes(st, n):
-    """Minimum bytes the BFS kernel must move for one launch (push accounting):
-    per scanned arc 4 B of col + 8 B of the target key (probe / atomicMin);
-    per expanded vertex 8 B row_ptr + 8 B own key + 24 B queue write and read;
-    per start-bucket entry 4 B vertex id + 8 B key test."""
-    return 12 * st["edges"] + 40 * st["items"] + 12 * n
+    """Bytes the BFS kernel's executed rounds must move for one launch:
+    per arc expanded top-down or scanned bottom-up 4 B of col + 8 B of the other
+    end's key (probe / atomicMin); per vertex examined bottom-up 8 B of its key
+    + 8 B row_ptr; per settled vertex 8 B row_ptr + 8 B own key + 24 B queue
+    write and read; per start-bucket entry 4 B vertex id + 8 B key test."""
+    return (12 * (st["push_arcs"] + st["pull_arcs"]) + 16 * st["pull_vertices"]
+            + 40 * st["items"] + 12 * n)
 
 
 def kernel_source_sha():
@@ -393,8 +395,10 @@ def our_arm(args):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
             "per_beta": [{"beta": b, "ms_total": st["ms_total"], "ms_rank": st["ms_rank"],
                           "ms_bfs": st["ms_bfs"], "ms_finalize": st["ms_finalize"], "ms_cut": st["ms_cut"],
-                          "rounds": st["rounds"], "A": st["max_floor_shift"], "items": st["items"],
-                          "edges": st["edges"], "gteps": m / st["ms_total"] / 1e6}
+                          "rounds": st["rounds"], "pull_rounds": st["pull_rounds"],
+                          "A": st["max_floor_shift"], "items": st["items"],
+                          "push_arcs": st["push_arcs"], "pull_arcs": st["pull_arcs"],
+                          "pull_vertices": st["pull_vertices"], "gteps": m / st["ms_total"] / 1e6}
                          for b, st in zip(betas, per_beta[-len(betas):])],
             "phase_share": phases,
             "wall_s_timed_region": t_wall,

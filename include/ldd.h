@@ -154,7 +154,11 @@ typedef struct {
   int64_t rounds;         /* synchronous BFS rounds executed */
   int64_t last_level;     /* level of the last round */
   int64_t items;          /* vertices expanded by the BFS */
-  int64_t edges;          /* arcs scanned by the BFS */
+  int64_t edges;          /* arcs out of the expanded vertices */
+  int64_t pull_rounds;    /* rounds run bottom-up (direction-optimising BFS) */
+  int64_t push_arcs;      /* arcs expanded in top-down rounds */
+  int64_t pull_arcs;      /* arcs scanned in bottom-up rounds */
+  int64_t pull_vertices;  /* vertices examined in bottom-up rounds */
   int64_t launches;       /* kernels launched by the last ldd_decompose */
   int64_t cut_launches;   /* kernels launched by the last ldd_cut_edges */
   int32_t bfs_grid;       /* CTAs of the persistent BFS kernel */
@@ -170,6 +174,19 @@ typedef struct {
 
 int ldd_get_stats(const ldd_graph* g, ldd_stats* out);
 int ldd_set_timing(ldd_graph* g, int enable);
+
+/*
+ * ldd_get_round_profile -- diagnostic: per-round timestamps of the last BFS.
+ *   clocks[i]  SM clock (cycles) of the first CTA when round i ended; entry 0
+ *              is after the level-0 starts, so round i took clocks[i] -
+ *              clocks[i-1] cycles.
+ *   kinds[i]   1 = top-down (push), 2 = bottom-up (pull), 3 = no frontier (jump
+ *              to the next start bucket).
+ * At most cap entries (and at most 256) are written; *out_count gets the number.
+ * Host buffers.
+ */
+int ldd_get_round_profile(const ldd_graph* g, int64_t* clocks, int32_t* kinds, int cap,
+                          int* out_count);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,8 @@ from ._build import LIB as _LIB_PATH
 __all__ = [
     "LddError", "LddGraph", "ldd_create_graph", "ldd_decompose", "ldd_cut_edges",
     "ldd_set_stream", "ldd_destroy_graph", "ldd_status_string", "ldd_last_error",
-    "ldd_get_stats", "ldd_set_timing", "ldd_cut_edges_noalloc", "library_path", "LDD_OK", "LDD_ERR_ARG",
+    "ldd_get_stats", "ldd_set_timing", "ldd_cut_edges_noalloc", "ldd_get_round_profile",
+    "library_path", "LDD_OK", "LDD_ERR_ARG",
     "LDD_ERR_GRAPH", "LDD_ERR_RANGE", "LDD_ERR_OOM", "LDD_ERR_CUDA", "LDD_ERR_TIMEOUT",
 ]
 
@@ -41,7 +42,8 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 class _Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
-        "n", "nnz", "n_active", "small_components", "max_floor_shift", "rounds", "last_level", "items", "edges",
+        "n", "nnz", "n_active", "small_components", "max_floor_shift", "rounds", "last_level", "items", "edges", "pull_rounds", "push_arcs", "pull_arcs",
+        "pull_vertices",
         "launches", "cut_launches")] + [("bfs_grid", ctypes.c_int32), ("bfs_block", ctypes.c_int32)] + [
         (name, ctypes.c_float) for name in (
             "ms_h2d", "ms_rank", "ms_bfs", "ms_finalize", "ms_d2h", "ms_total", "ms_cut")]
@@ -66,6 +68,8 @@ _lib.ldd_last_error.argtypes = []
 _lib.ldd_last_error.restype = ctypes.c_char_p
 _lib.ldd_get_stats.argtypes = [_vp, ctypes.POINTER(_Stats)]
 _lib.ldd_get_stats.restype = ctypes.c_int
+_lib.ldd_get_round_profile.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+_lib.ldd_get_round_profile.restype = ctypes.c_int
 _lib.ldd_set_timing.argtypes = [_vp, ctypes.c_int]
 _lib.ldd_set_timing.restype = ctypes.c_int
 
@@ -166,6 +170,18 @@ def ldd_set_timing(g: int, enable: bool) -> None:
     _check(_lib.ldd_set_timing(g, int(bool(enable))), "ldd_set_timing")
 
 
+def ldd_get_round_profile(g: int, cap: int = 256):
+    """(clocks, kinds) of the last BFS's rounds (see include/ldd.h)."""
+    import numpy as np
+
+    clocks = np.zeros(cap, dtype=np.int64)
+    kinds = np.zeros(cap, dtype=np.int32)
+    cnt = ctypes.c_int(0)
+    _check(_lib.ldd_get_round_profile(g, clocks.ctypes.data, kinds.ctypes.data, cap,
+                                      ctypes.byref(cnt)), "ldd_get_round_profile")
+    return clocks[:cnt.value], kinds[:cnt.value]
+
+
 def ldd_get_stats(g: int) -> dict:
     st = _Stats()
     _check(_lib.ldd_get_stats(g, ctypes.byref(st)), "ldd_get_stats")
@@ -194,6 +210,9 @@ class LddGraph:
 
     def stats(self) -> dict:
         return ldd_get_stats(self.handle)
+
+    def round_profile(self):
+        return ldd_get_round_profile(self.handle)
 
     def close(self) -> None:
         if getattr(self, "handle", 0):

@@ -24,6 +24,20 @@
 // its span into shared memory and finds each edge's item with a block-wide
 // max-scan.
 //
+// Direction-optimising rounds (Beamer, Asanovic, Patterson 2012): when the
+// frontier's arcs outweigh the arcs of the still-unsettled vertices, a round
+// runs bottom-up instead: every unsettled vertex w scans its neighbours for
+// keys of level r and keeps the smallest key + 2^32.  The scan can stop once it
+// holds (r + 1, minrank_r), where minrank_r is the smallest rank among level-r
+// keys: nothing can beat it.  minrank_r is tracked exactly during round r - 1
+// as the minimum over every successful key update and every appended start
+// (each final level-r key is one of these, and each of these is >= the final
+// key of its vertex).  Only w's own thread writes key[w] in such a round, and a
+// vertex being lowered to level r + 1 is never read as a level-r key, so no
+// atomics are needed.  The first bottom-up round of a run examines every
+// vertex the BFS owns; each round lists the vertices still above level r + 1,
+// and the next bottom-up round examines only those.
+//
 // Rounds with an empty frontier jump straight to the next non-empty start
 // bucket; the loop stops as soon as every vertex with an arc is settled.
 // All device-side waits are bounded: a barrier that does not complete within
@@ -37,38 +51,53 @@ namespace {
 constexpr u32 kFull = 0xffffffffu;
 constexpr int kEdgeBatch = 4;  // arcs per thread in flight
 constexpr int kWinBatch = 3;   // window items per thread in flight
+constexpr int kPullV = 3;      // candidates per lane in flight in a bottom-up round
+constexpr u32 kProbeMinArcs = 1u << 16;  // smaller frontiers skip the key probe before atomicMin
 
 struct Smem {
   int owner[kBfsMaxSpan];
   int rowd[kBfsMaxSpan + 1];
   u64 cand[kBfsMaxSpan + 1];
   int wtot[kBfsThreads / 32];
+  u32 minrank;  // this CTA's smallest successful next-level rank in the round
 };
 
-__device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 limit) {
+// Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a
+// launch completes when the counter reaches k * nblocks, so arrival is one
+// fire-and-forget add and nobody has to reset anything.  Before arriving,
+// thread 0 publishes this CTA's smallest next-level rank to *post (and resets
+// the CTA value).  The wait is bounded: after `limit` polls (or once any CTA
+// has recorded an error) it sets kErrTimeout and returns.
+__device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 limit,
+                                             u32* post, u32* cta_min) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const u32 target = gen + 1;
+    if (*cta_min != 0xffffffffu) atomicMin(post, *cta_min);
+    *cta_min = 0xffffffffu;
+    ++gen;
+    const u64 target = (u64)gen * nblocks;
     __threadfence();
-    const u32 arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicExch(&ctl->bar_gen, target);
-    } else {
-      u32 spins = 0;
-      while (ld_acquire_u32(&ctl->bar_gen) != target) {
-        if (++spins > limit || ld_acquire_u32(&ctl->err) != 0u) {
-          atomicOr(&ctl->err, kErrTimeout);
-          break;
-        }
-        if (spins > 32) __nanosleep(40);
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->bar), "l"(1ull) : "memory");
+    u32 spins = 0;
+    for (;;) {
+      u64 seen;
+      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(&ctl->bar) : "memory");
+      if (seen >= target) break;
+      if (++spins > limit || ld_acquire_u32(&ctl->err) != 0u) {
+        atomicOr(&ctl->err, kErrTimeout);
+        break;
       }
+      if (spins > 64) __nanosleep(20);
     }
     __threadfence();
-    gen = target;
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ u32 warp_min(u32 x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(kFull, x, o));
+  return x;
 }
 
 // Appends to the frontier every vertex v[i] whose bit i is set in `mask`, for
@@ -127,54 +156,29 @@ __device__ __forceinline__ void warp_append(u32 mask, const u32 (&v)[K], const B
 
 // Unclaimed vertices of start bucket rr join the frontier of level rr.
 __device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u32* rv, int qi,
-                                              int qb) {
+                                              int qb, u32& myrank) {
   const int lo = __ldg(a.bptr + rr), hi = __ldg(a.bptr + rr + 1);
   const u32 cnt = (u32)(hi - lo);
   const u32 lane = threadIdx.x & 31;
   const u32 stride = gridDim.x * blockDim.x;
-  for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < cnt; base += stride) {
+  // trailing CTAs first: in a small round the leading CTAs are expanding
+  const u32 b = gridDim.x - 1 - blockIdx.x;
+  for (u32 base = b * blockDim.x + (threadIdx.x & ~31u); base < cnt; base += stride) {
     const u32 i = base + lane;
     u32 u[1] = {0};
     bool want = false;
     if (i < cnt) {
       u[0] = __ldg(rv + lo + i);
-      want = (u32)(ld_cg_u64(a.key + u[0]) >> 32) == (u32)rr;
+      const u64 k = ld_cg_u64(a.key + u[0]);
+      want = (u32)(k >> 32) == (u32)rr;
+      if (want) myrank = min(myrank, (u32)k);
     }
     warp_append<1>(want ? 1u : 0u, u, a, qi, qb);
   }
 }
 
-// In-place inclusive max-scan of s.owner[0 .. len), len <= kBfsMaxSpan.
-__device__ __forceinline__ void block_max_scan(Smem& s, int len) {
-  constexpr int kPer = kBfsMaxSpan / kBfsThreads;  // 8 consecutive entries per thread
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int b = t * kPer;
-  int run = -1;
-#pragma unroll
-  for (int i = 0; i < kPer; ++i)
-    if (b + i < len) {
-      run = max(run, s.owner[b + i]);
-      s.owner[b + i] = run;
-    }
-  int x = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x = max(x, y);
-  }
-  if (lane == 31) s.wtot[w] = x;
-  __syncthreads();
-  int carry = -1;
-  for (int i = 0; i < w; ++i) carry = max(carry, s.wtot[i]);
-  const int prev = __shfl_up_sync(kFull, x, 1);
-  if (lane > 0) carry = max(carry, prev);
-#pragma unroll
-  for (int i = 0; i < kPer; ++i)
-    if (b + i < len) s.owner[b + i] = max(s.owner[b + i], carry);
-}
-
 __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q, u32 E, int lvl,
-                                       int qi, int qb) {
+                                       int qi, int qb, u32& myrank) {
   const u32 nb = (E + kBfsBase - 1) / kBfsBase;
   u32 k = (nb + gridDim.x - 1) / gridDim.x;
   k = max(1u, min(k, (u32)(kBfsMaxSpan / kBfsBase)));
@@ -184,6 +188,7 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
   const int* qrow = a.qrow[cur];
   const u32* qoff = a.qoff[cur];
   const u32 lvl_next = (u32)lvl + 1;
+  const bool probe = E >= kProbeMinArcs;
   for (u32 sc = blockIdx.x; sc < nsuper; sc += gridDim.x) {
     const u32 b0 = sc * k, b1 = min(b0 + k, nb);
     const u32 e0 = b0 * kBfsBase, e1 = min(b1 * kBfsBase, E);
@@ -225,7 +230,7 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
         }
     }
     __syncthreads();
-    block_max_scan(s, len);
+    block_max_scan<kBfsThreads, kBfsMaxSpan>(s.owner, len, s.wtot);
     __syncthreads();
     // edges: all loads of a batch first, then all probes, then the atomics
     for (int base = 0; base < len; base += kBfsThreads * kEdgeBatch) {
@@ -242,19 +247,148 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
           w[i] = (u32)__ldg(a.col + (s.rowd[j] + (int)(e0 + kk)));
         }
       }
-      u64 cur[kEdgeBatch];
+      u64 cur[kEdgeBatch];  // probe before the atomic only when there are many arcs
 #pragma unroll
-      for (int i = 0; i < kEdgeBatch; ++i) cur[i] = (w[i] < a.n) ? ld_cg_u64(a.key + w[i]) : 0ull;
+      for (int i = 0; i < kEdgeBatch; ++i)
+        cur[i] = (w[i] < a.n) ? (probe ? ld_cg_u64(a.key + w[i]) : ~0ull) : 0ull;
       u32 mask = 0;
 #pragma unroll
       for (int i = 0; i < kEdgeBatch; ++i)
         if (cand[i] < cur[i]) {
           const u64 old = atomicMin(a.key + w[i], cand[i]);
+          if (old > cand[i]) myrank = min(myrank, (u32)cand[i]);
           if ((u32)(old >> 32) > lvl_next) mask |= 1u << i;
         }
       warp_append<kEdgeBatch>(mask, w, a, qi, qb);
     }
     __syncthreads();
+  }
+}
+
+// Folds a thread's smallest rank into the CTA's (lane 0 of each warp) and resets it.
+__device__ __forceinline__ void post_cta_min(Smem& s, u32& myrank) {
+  const u32 wm = warp_min(myrank);
+  if ((threadIdx.x & 31) == 0 && wm != 0xffffffffu) atomicMin(&s.minrank, wm);
+  myrank = 0xffffffffu;
+}
+
+// Appends every v[i] with bit i of `mask` set to a plain vertex list, one
+// atomic per warp.
+template <int K>
+__device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], u32* list,
+                                                 u32* count) {
+  const u32 lane = threadIdx.x & 31;
+  const u32 mine = __popc(mask);
+  u32 incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= (u32)o) incl += y;
+  }
+  const u32 tot = __shfl_sync(kFull, incl, 31);
+  if (tot == 0) return;
+  u32 base = 0;
+  if (lane == 0) base = atomicAdd(count, tot);
+  base = __shfl_sync(kFull, base, 0) + incl - mine;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (mask >> i & 1u) list[base++] = v[i];
+}
+
+// Bottom-up round from level lvl (see the file comment).  Candidates are every
+// vertex not in excl (from_list = false) or the list `cand` of ncand vertices.
+// Each lane takes kPullV candidates at a time and advances their neighbour
+// scans in lock-step, one neighbour each per step, so that up to kPullV
+// independent loads are in flight per lane.  Adds the arcs it scans and the
+// vertices it examines to the statistics.
+__device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minrank, int qi, int qb,
+                                           bool from_list, const u32* cand, u32 ncand,
+                                           u32* ulist_out, u32* ucnt_out, u32& myrank) {
+  constexpr u32 kNone = 0xffffffffu;
+  u32 scanned = 0, examined = 0;
+  const u32 lane = threadIdx.x & 31;
+  const u32 L = (u32)lvl;
+  const u64 floor_key = ((u64)(L + 1) << 32) | minrank;
+  const u32 total = from_list ? ncand : a.n;
+  const u32 stride = gridDim.x * blockDim.x * kPullV;
+  for (u32 base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * kPullV; base < total;
+       base += stride) {
+    u32 w[kPullV];
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      const u32 i = base + (u32)j * 32 + lane;
+      w[j] = kNone;
+      if (from_list) {
+        if (i < total) w[j] = ld_cg_u32(cand + i);
+      } else if (i < total) {
+        const u32 ex = __ldg(a.excl + (i >> 5));  // same word for the whole warp
+        if (!((ex >> lane) & 1u)) w[j] = i;
+      }
+    }
+    u64 kw[kPullV];
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) kw[j] = (w[j] != kNone) ? ld_cg_u64(a.key + w[j]) : 0ull;
+    u64 best[kPullV];
+    int e[kPullV], re[kPullV];
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      best[j] = kw[j];
+      e[j] = 0;
+      re[j] = 0;
+      if (w[j] != kNone) {
+        ++examined;
+        if ((u32)(kw[j] >> 32) > L && kw[j] > floor_key) {
+          e[j] = __ldg(a.row_ptr + w[j]);
+          re[j] = __ldg(a.row_ptr + w[j] + 1);
+        }
+      }
+    }
+    for (;;) {  // one neighbour of every still-scanning candidate per step
+      bool any = false;
+      u32 vv[kPullV];
+#pragma unroll
+      for (int j = 0; j < kPullV; ++j) {
+        vv[j] = kNone;
+        if (e[j] < re[j]) {
+          vv[j] = (u32)__ldg(a.col + e[j]);
+          ++e[j];
+          ++scanned;
+          any = true;
+        }
+      }
+      if (!any) break;
+      u64 kv[kPullV];
+#pragma unroll
+      for (int j = 0; j < kPullV; ++j) kv[j] = (vv[j] < a.n) ? ld_cg_u64(a.key + vv[j]) : ~0ull;
+#pragma unroll
+      for (int j = 0; j < kPullV; ++j) {
+        if ((u32)(kv[j] >> 32) == L) best[j] = min(best[j], kv[j] + kLevelOne);
+        if (best[j] <= floor_key) re[j] = e[j];  // nothing can beat (L + 1, minrank)
+      }
+    }
+    u32 mask = 0, keep = 0;
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      const bool pending = w[j] != kNone && (u32)(kw[j] >> 32) > L;
+      if (pending && best[j] < kw[j]) {
+        a.key[w[j]] = best[j];  // only this thread writes key[w] in a bottom-up round
+        myrank = min(myrank, (u32)best[j]);
+        if ((u32)(kw[j] >> 32) > L + 1) mask |= 1u << j;
+      }
+      // still above level L + 1: examined again by a following bottom-up round
+      if (pending && (u32)(min(best[j], kw[j]) >> 32) > L + 1) keep |= 1u << j;
+    }
+    warp_append<kPullV>(mask, w, a, qi, qb);
+    warp_list_append<kPullV>(keep, w, ulist_out, ucnt_out);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    scanned += __shfl_xor_sync(kFull, scanned, o);
+    examined += __shfl_xor_sync(kFull, examined, o);
+  }
+  if (lane == 0) {
+    if (scanned) atomicAdd(&a.ctl->pull_arcs, (u64)scanned);
+    if (examined) atomicAdd(&a.ctl->pull_verts, (u64)examined);
   }
 }
 
@@ -265,31 +399,61 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
   if (ld_acquire_u32(&ctl->err) != 0u) return;  // validation failed upstream
   const int A = ctl->A;
   const u32 par_r = __popc(ctl->mask_r) & 1u;
-  const u64* rk = a.rk[par_r];
+  const u32* rk = a.rk[par_r];
   const u32* rv = a.rv[par_r];
   const u32 G = gridDim.x;
   u32 gen = 0;
+  u32 myrank = 0xffffffffu;  // this thread's smallest successful next-level rank
+  if (threadIdx.x == 0) s.minrank = 0xffffffffu;
+  __syncthreads();
 
   // Level 0: the vertices with the largest integer shift part start.
-  append_bucket(a, 0, rv, 0, 0);
-  grid_barrier(ctl, gen, G, a.spin_limit);
+  append_bucket(a, 0, rv, 0, 0, myrank);
+  post_cta_min(s, myrank);
+  grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[0], &s.minrank);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->round_clk[0] = clock64();
+    ctl->round_kind[0] = kRoundSkip;
+  }
 
   u64 settled = 0, edges = 0;
-  u32 phase = 0;
+  u32 phase = 0, pulls = 0;
+  u64 push_arcs = 0;
   int lvl = 0;
+  bool pulling = false;
   for (;;) {
     if (ld_acquire_u32(&ctl->err) != 0u) break;
     const u64 c = ld_cg_u64(&ctl->qctr[phase % 3]);
     const u32 Q = (u32)(c >> 32), E = (u32)c;
     settled += Q;
-    if (settled >= a.n_active) break;  // every vertex with an arc has its final key
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qctr[(phase + 2) % 3] = 0;
+    if (settled >= a.n_active) break;  // every vertex the BFS owns has its final key
+    const u32 minrank = ld_cg_u32(&ctl->minrank[phase % 3]);
+    const u32 ncand = ld_cg_u32(&ctl->ucnt[phase % 3]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->qctr[(phase + 2) % 3] = 0;
+      ctl->minrank[(phase + 2) % 3] = 0xffffffffu;
+      ctl->ucnt[(phase + 2) % 3] = 0;
+    }
     const int qi = (int)((phase + 1) % 3), qb = (int)((phase + 1) & 1);
     int nlvl;
     if (Q > 0) {
       edges += E;
-      expand(a, s, (int)(phase & 1), Q, E, lvl, qi, qb);
-      if (lvl + 1 <= A) append_bucket(a, lvl + 1, rv, qi, qb);
+      const u64 unsettled_arcs = a.nnz_active > edges ? a.nnz_active - edges : 0;
+      const bool was_pulling = pulling;
+      if (!pulling && (u64)E * a.pull_alpha > unsettled_arcs &&
+          (u64)E * a.pull_gamma > a.n_active)
+        pulling = true;
+      else if (pulling && (u64)Q * a.pull_beta < a.n_active)
+        pulling = false;
+      if (pulling) {
+        pull_round(a, lvl, minrank, qi, qb, was_pulling, a.ulist[phase & 1], ncand,
+                   a.ulist[(phase + 1) & 1], &ctl->ucnt[qi], myrank);
+        ++pulls;
+      } else {
+        expand(a, s, (int)(phase & 1), Q, E, lvl, qi, qb, myrank);
+        push_arcs += E;
+      }
+      if (lvl + 1 <= A) append_bucket(a, lvl + 1, rv, qi, qb, myrank);
       nlvl = lvl + 1;
     } else {
       if (lvl + 1 > A) break;
@@ -297,14 +461,21 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
       if ((u32)start >= a.n) break;
       const int rr = (int)__ldg(rk + start);  // next non-empty start bucket
       if (rr > A) break;                      // only vertices the BFS does not handle remain
-      append_bucket(a, rr, rv, qi, qb);
+      append_bucket(a, rr, rv, qi, qb, myrank);
       nlvl = rr;
     }
-    grid_barrier(ctl, gen, G, a.spin_limit);
+    post_cta_min(s, myrank);
+    grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[qi], &s.minrank);
     ++phase;
     lvl = nlvl;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && phase < (u32)kRoundProfile) {
+      ctl->round_clk[phase] = clock64();
+      ctl->round_kind[phase] = Q == 0 ? kRoundSkip : (pulling ? kRoundPull : kRoundPush);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->pull_rounds = pulls;
+    ctl->push_arcs = push_arcs;
     ctl->rounds = phase;
     ctl->last_level = lvl;
     ctl->items = settled;

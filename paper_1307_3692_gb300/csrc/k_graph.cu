@@ -7,6 +7,9 @@
 //
 // cut (Definition 1.1, second condition; Section 4 notes the check costs
 // O(m) work): arcs (v, w) with v < w whose endpoints have different centers.
+// The graph keeps those arcs as a list of (v, w) pairs (8 bytes each, the same
+// bytes as its col array), so the count is one streaming pass with two
+// gathers per edge and no search for the row an arc belongs to.
 //
 // Components.  The assignment of Algorithm 2 never crosses a connected
 // component (other components are at infinite distance), so every component
@@ -22,10 +25,6 @@
 // BFS start buckets, so the round loop ends when the large components are
 // settled instead of visiting every start round up to floor(delta_max).
 //
-// Arc-parallel kernels (cut, hooking) split the arcs into equal spans, one per
-// CTA; the rows covering a span (a precomputed first-row table over the
-// vertices with arcs) are located with a block max-scan in shared memory, so
-// high-degree rows are split across CTAs and reads of col are coalesced.
 #include "ldd_internal.cuh"
 
 namespace ldd {
@@ -51,131 +50,45 @@ __global__ void __launch_bounds__(256) k_finalize(const u64* __restrict__ key,
   }
 }
 
-struct SpanSmem {
-  int owner[kCutSpan];
-  u32 v[kCutSpan + 1];
-  int aux[kCutSpan + 1];
-  int wtot[kCutThreads / 32];
-  unsigned long long wsum[kCutThreads / 32];
-};
+// Edges per thread per step: two 16-byte loads of two (v, w) pairs each.
+constexpr int kCutPairs = 2;
 
-// Fills s.owner[k] with the window index of the row that holds arc e0 + k of
-// span `c`; s.v[j] is that row's vertex and s.aux[j] = aux(vertex).  Returns
-// false (and leaves the span unprocessed) if the tables are inconsistent.
-template <class Aux>
-__device__ __forceinline__ bool span_window(SpanSmem& s, const int* __restrict__ row_ptr,
-                                            const u32* __restrict__ nzv,
-                                            const u32* __restrict__ first, u32 n_items, u32 nnz,
-                                            u32 c, u32& e0, int& len, Aux aux) {
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const u32 nch = (nnz + kCutSpan - 1) / kCutSpan;
-  e0 = c * kCutSpan;
-  const u32 e1 = min(e0 + kCutSpan, nnz);
-  len = (int)(e1 - e0);
-  const u32 i0 = first[c];
-  const u32 ilast = (c + 1 < nch) ? first[c + 1] : n_items - 1;
-  const int nwin = (int)(ilast - i0) + 1;
-  if (nwin < 1 || nwin > kCutSpan + 1 || ilast >= n_items) return false;
-  for (int j = t; j < len; j += kCutThreads) s.owner[j] = 0;
-  __syncthreads();
-  for (int j0 = 0; j0 < nwin; j0 += kCutThreads * kCutWinBatch) {
-    u32 v[kCutWinBatch], off[kCutWinBatch];
-#pragma unroll
-    for (int i = 0; i < kCutWinBatch; ++i) {
-      const int j = j0 + i * kCutThreads + t;
-      v[i] = (j < nwin) ? nzv[i0 + j] : kNone;
-    }
-    int ax[kCutWinBatch];
-#pragma unroll
-    for (int i = 0; i < kCutWinBatch; ++i) {
-      off[i] = e1;
-      if (v[i] != kNone) {
-        off[i] = (u32)row_ptr[v[i]];
-        ax[i] = aux(v[i]);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kCutWinBatch; ++i)
-      if (off[i] < e1) {
-        const int j = j0 + i * kCutThreads + t;
-        s.v[j] = v[i];
-        s.aux[j] = ax[i];
-        atomicMax(&s.owner[off[i] > e0 ? off[i] - e0 : 0u], j);
-      }
-  }
-  __syncthreads();
-  // inclusive max-scan of owner[0 .. len)
-  constexpr int kPer = kCutSpan / kCutThreads;
-  const int b = t * kPer;
-  int run = -1;
-#pragma unroll
-  for (int i = 0; i < kPer; ++i)
-    if (b + i < len) {
-      run = max(run, s.owner[b + i]);
-      s.owner[b + i] = run;
-    }
-  int x = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x = max(x, y);
-  }
-  if (lane == 31) s.wtot[w] = x;
-  __syncthreads();
-  int carry = -1;
-  for (int i = 0; i < w; ++i) carry = max(carry, s.wtot[i]);
-  const int prev = __shfl_up_sync(kFull, x, 1);
-  if (lane > 0) carry = max(carry, prev);
-#pragma unroll
-  for (int i = 0; i < kPer; ++i)
-    if (b + i < len) s.owner[b + i] = max(s.owner[b + i], carry);
-  __syncthreads();
-  return true;
-}
-
-__global__ void __launch_bounds__(kCutThreads) k_cut(const int* __restrict__ row_ptr,
-                                                     const int* __restrict__ col,
-                                                     const u32* __restrict__ nzv,
-                                                     const u32* __restrict__ first, u32 n_items,
-                                                     u32 nnz, u32 n_vert,
-                                                     const int* __restrict__ center, u64* out) {
-  __shared__ SpanSmem s;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  u32 e0;
-  int len;
-  if (!span_window(s, row_ptr, nzv, first, n_items, nnz, blockIdx.x, e0, len,
-                   [&](u32 v) { return center[v]; }))
-    return;
+__global__ void __launch_bounds__(256) k_cut(const int2* __restrict__ up, u32 m_up,
+                                             const int* __restrict__ center, u64* out) {
+  __shared__ unsigned long long wsum[8];
+  const int4* up4 = reinterpret_cast<const int4*>(up);  // cudaMalloc'd: 256-byte aligned
+  const u32 nquad = m_up / 2;
+  const u32 stride = gridDim.x * blockDim.x;
   unsigned long long cnt = 0;
-  constexpr int kPerEdge = kCutSpan / kCutThreads;
-  u32 wv[kPerEdge];
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nquad; i += stride * kCutPairs) {
+    int4 q[kCutPairs];
 #pragma unroll
-  for (int i = 0; i < kPerEdge; ++i) {
-    const int kk = i * kCutThreads + t;
-    wv[i] = (kk < len) ? (u32)col[e0 + kk] : kNone;
-  }
-  int cw[kPerEdge];
-#pragma unroll
-  for (int i = 0; i < kPerEdge; ++i) {
-    const int kk = i * kCutThreads + t;
-    cw[i] = 0;
-    if (wv[i] < n_vert && s.v[s.owner[kk]] < wv[i]) cw[i] = center[wv[i]];
-  }
-#pragma unroll
-  for (int i = 0; i < kPerEdge; ++i) {
-    const int kk = i * kCutThreads + t;
-    if (wv[i] < n_vert) {
-      const int j = s.owner[kk];
-      if (s.v[j] < wv[i] && s.aux[j] != cw[i]) ++cnt;
+    for (int k = 0; k < kCutPairs; ++k) {
+      const u32 j = i + (u32)k * stride;
+      q[k] = (j < nquad) ? __ldcs(up4 + j) : make_int4(0, 0, 0, 0);
     }
+    int c[kCutPairs][4];
+#pragma unroll
+    for (int k = 0; k < kCutPairs; ++k) {
+      c[k][0] = center[q[k].x];
+      c[k][1] = center[q[k].y];
+      c[k][2] = center[q[k].z];
+      c[k][3] = center[q[k].w];
+    }
+#pragma unroll
+    for (int k = 0; k < kCutPairs; ++k) cnt += (c[k][0] != c[k][1]) + (c[k][2] != c[k][3]);
+  }
+  if ((m_up & 1u) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd edge count: the last edge
+    const int2 e = up[m_up - 1];
+    cnt += center[e.x] != center[e.y];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
-  if (lane == 0) s.wsum[w] = cnt;
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
   __syncthreads();
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     unsigned long long tot = 0;
-    for (int i = 0; i < kCutThreads / 32; ++i) tot += s.wsum[i];
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) tot += wsum[i];
     if (tot) atomicAdd(out, tot);
   }
 }
@@ -216,22 +129,10 @@ __global__ void k_iota(u32* p, u32 n) {
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) p[v] = v;
 }
 
-__global__ void __launch_bounds__(kCutThreads) k_cc_hook(const int* __restrict__ row_ptr,
-                                                         const int* __restrict__ col,
-                                                         const u32* __restrict__ nzv,
-                                                         const u32* __restrict__ first,
-                                                         u32 n_items, u32 nnz, u32 n_vert,
-                                                         u32* parent) {
-  __shared__ SpanSmem s;
-  u32 e0;
-  int len;
-  if (!span_window(s, row_ptr, nzv, first, n_items, nnz, blockIdx.x, e0, len,
-                   [](u32) { return 0; }))
-    return;
-  for (int kk = threadIdx.x; kk < len; kk += kCutThreads) {
-    const u32 v = s.v[s.owner[kk]];
-    const u32 w = (u32)col[e0 + kk];
-    if (w < v) cc_unite(parent, v, w);  // each undirected edge once
+__global__ void k_cc_hook(const int2* __restrict__ up, u32 m_up, u32* parent) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m_up; i += gridDim.x * blockDim.x) {
+    const int2 e = up[i];
+    cc_unite(parent, (u32)e.y, (u32)e.x);
   }
 }
 
@@ -284,6 +185,7 @@ __global__ void k_small_members(const int* __restrict__ row_ptr, const u32* __re
       atomicOr(excl + (v >> 5), 1u << (v & 31));
     } else {
       atomicAdd(counters + 2, 1u);  // vertices the BFS settles
+      atomicAdd(counters + 3, (u32)(row_ptr[v + 1] - row_ptr[v]));  // and their arcs
     }
   }
 }
@@ -346,12 +248,11 @@ int launch_finalize(const u64* key, const u32* order, u32 n, int* center, int* d
   return 1;
 }
 
-int launch_cut(const int* row_ptr, const int* col, const u32* nzv, const u32* cut_first,
-               u32 n_items, u32 nnz, u32 n_vert, const int* center, u64* out, cudaStream_t s) {
-  const u32 nch = (nnz + kCutSpan - 1) / kCutSpan;
-  if (nch == 0) return 0;
-  k_cut<<<nch, kCutThreads, 0, s>>>(row_ptr, col, nzv, cut_first, n_items, nnz, n_vert, center,
-                                    out);
+int launch_cut(const int2* up, u32 m_up, const int* center, u64* out, int num_sms,
+               cudaStream_t s) {
+  if (m_up == 0) return 0;
+  const u32 g = (u32)max(1ll, min((long long)(m_up / 2 + 255) / 256, (long long)num_sms * 16));
+  k_cut<<<g, 256, 0, s>>>(up, m_up, center, out);
   return 1;
 }
 
@@ -363,26 +264,23 @@ int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sm
   return 1;
 }
 
-cudaError_t components_phase1(const int* row_ptr, const int* col, const u32* nzv,
-                              const u32* cut_first, u32 n_items, u32 n, u32 nnz, int num_sms,
-                              const CompScratch& t, u32* excl, u32 counts[3], cudaStream_t s) {
+cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 n, int num_sms,
+                              const CompScratch& t, u32* excl, u32 counts[4], cudaStream_t s) {
   const u32 g = grid_for(n, num_sms);
   cudaError_t e;
   if ((e = cudaMemsetAsync(t.csize, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(t.fill, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(t.counters, 0, 3 * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(t.counters, 0, 4 * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(t.lane_of, 0xff, (size_t)n * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(excl, 0, ((size_t)n + 31) / 32 * 4, s)) != cudaSuccess) return e;
   k_iota<<<g, 256, 0, s>>>(t.parent, n);
-  const u32 nch = (nnz + kCutSpan - 1) / kCutSpan;
-  if (nch > 0)
-    k_cc_hook<<<nch, kCutThreads, 0, s>>>(row_ptr, col, nzv, cut_first, n_items, nnz, n, t.parent);
+  if (m_up > 0) k_cc_hook<<<grid_for(m_up, num_sms), 256, 0, s>>>(up, m_up, t.parent);
   k_cc_finish<<<g, 256, 0, s>>>(t.parent, t.csize, n);
   k_small_roots<<<g, 256, 0, s>>>(t.parent, t.csize, n, t.root_off, t.comp_off, t.comp_len,
                                   t.counters);
   k_small_members<<<g, 256, 0, s>>>(row_ptr, t.parent, t.csize, t.root_off, n, t.fill, t.comp_v,
                                     t.lane_of, excl, t.counters);
-  if ((e = cudaMemcpyAsync(counts, t.counters, 3 * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(counts, t.counters, 4 * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);

@@ -25,10 +25,11 @@
 
 using namespace ldd;
 
-static_assert(offsetof(Control, bar_count) == kCtlBfsStateOffset, "control layout");
+static_assert(offsetof(Control, bar) == kCtlBfsStateOffset, "control layout");
 static_assert(offsetof(Control, mask_f) == kCtlBfsStateOffset + kCtlBfsStateBytes,
               "control layout");
 static_assert(offsetof(Control, cut) + sizeof(u64) == kCtlHeaderBytes, "control layout");
+static_assert(offsetof(Control, minrank) == kCtlMinrankOffset, "control layout");
 
 namespace {
 
@@ -100,12 +101,12 @@ struct ldd_graph {
   int num_sms = 0;
   cudaStream_t stream = nullptr;
   u32 n_active = 0;
-  u32 cut_items = 0;
+  u64 nnz_active = 0;
+  u32 m_up = 0;                // arcs (v, w) with v < w
   // device CSR and graph tables
   int* d_row = nullptr;
   int* d_col = nullptr;
-  u32* d_nzv = nullptr;       // vertices with at least one arc, ascending
-  u32* d_cut_first = nullptr; // per cut span: index into d_nzv of the row holding its first arc
+  int2* d_up = nullptr;        // the arcs (v, w) with v < w, in CSR order
   u32* d_excl = nullptr;      // bit v: v is not handled by the BFS (no arcs or a small component)
   SmallComps sc;              // components of 2..32 vertices, solved one warp each
   // scratch arena
@@ -121,6 +122,7 @@ struct ldd_graph {
   int* d_qrow[2] = {nullptr, nullptr};
   u32* d_qoff[2] = {nullptr, nullptr};
   u32* d_cf[2] = {nullptr, nullptr};
+  u32* d_ulist[2] = {nullptr, nullptr};
   int* d_center = nullptr;
   int* d_dist = nullptr;
   Control* d_ctl = nullptr;
@@ -133,6 +135,9 @@ struct ldd_graph {
   int bfs_grid = 0;
   int bfs_per_sm = 0;
   u32 spin_limit = 0;
+  u32 pull_alpha = 0;
+  u32 pull_beta = 0;
+  u32 pull_gamma = 0;
   bool timing = false;
   cudaEvent_t ev[8] = {};
   ldd_stats stats;
@@ -143,8 +148,7 @@ namespace {
 int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_row);
   cudaFree(g->d_col);
-  cudaFree(g->d_nzv);
-  cudaFree(g->d_cut_first);
+  cudaFree(g->d_up);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
   cudaFree(g->sc.comp_len);
@@ -198,6 +202,7 @@ int alloc_scratch(ldd_graph* g) {
       {(void**)&g->d_qrow[0], 4 * n},     {(void**)&g->d_qrow[1], 4 * n},
       {(void**)&g->d_qoff[0], 4 * n},     {(void**)&g->d_qoff[1], 4 * n},
       {(void**)&g->d_cf[0], 4 * ncf},     {(void**)&g->d_cf[1], 4 * ncf},
+      {(void**)&g->d_ulist[0], 4 * n},    {(void**)&g->d_ulist[1], 4 * n},
       {(void**)&g->d_center, 4 * n},      {(void**)&g->d_dist, 4 * n},
       {(void**)&g->d_ctl, sizeof(Control)},
   };
@@ -230,7 +235,7 @@ int build_component_tables(ldd_graph* g) {
     return fail(LDD_ERR_OOM, "device allocation of the exclusion bitmask failed");
   }
   if (n == 0) return LDD_OK;
-  const size_t words = 7 * n + 2 * (n / 2 + 1) + 3;
+  const size_t words = 7 * n + 2 * (n / 2 + 1) + 4;
   u32* tmp = nullptr;
   if (cudaMalloc(&tmp, words * 4) != cudaSuccess) {
     cudaGetLastError();
@@ -246,9 +251,9 @@ int build_component_tables(ldd_graph* g) {
   t.comp_off = tmp + 6 * n;
   t.comp_len = t.comp_off + (n / 2 + 1);
   t.counters = t.comp_len + (n / 2 + 1);
-  u32 counts[3] = {0, 0, 0};
-  cudaError_t e = components_phase1(g->d_row, g->d_col, g->d_nzv, g->d_cut_first, g->cut_items,
-                                    (u32)n, (u32)g->nnz, g->num_sms, t, g->d_excl, counts, nullptr);
+  u32 counts[4] = {0, 0, 0, 0};
+  cudaError_t e = components_phase1(g->d_row, g->d_up, g->m_up, (u32)n, g->num_sms, t, g->d_excl,
+                                    counts, nullptr);
   int rc = LDD_OK;
   SmallComps& sc = g->sc;
   if (e != cudaSuccess) {
@@ -257,6 +262,7 @@ int build_component_tables(ldd_graph* g) {
     sc.ncomp = counts[0];
     sc.total = counts[1];
     g->n_active = counts[2];
+    g->nnz_active = counts[3];
     if (sc.ncomp > 0 &&
         (cudaMalloc(&sc.comp_off, sc.ncomp * 4) != cudaSuccess ||
          cudaMalloc(&sc.comp_len, sc.ncomp * 4) != cudaSuccess ||
@@ -297,8 +303,8 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.col = g->d_col;
   a.key = g->d_key;
   a.bptr = g->d_bptr;
-  a.rk[0] = g->d_k[0];
-  a.rk[1] = g->d_k[1];
+  a.rk[0] = reinterpret_cast<const u32*>(g->d_k[0]);  // round keys are 32-bit
+  a.rk[1] = reinterpret_cast<const u32*>(g->d_k[1]);
   a.rv[0] = g->d_v[0];
   a.rv[1] = g->d_v[1];
   for (int b = 0; b < 2; ++b) {
@@ -306,11 +312,17 @@ BfsArgs bfs_args(ldd_graph* g) {
     a.qrow[b] = g->d_qrow[b];
     a.qoff[b] = g->d_qoff[b];
     a.cf[b] = g->d_cf[b];
+    a.ulist[b] = g->d_ulist[b];
   }
+  a.excl = g->d_excl;
   a.ctl = g->d_ctl;
   a.n = (u32)g->n;
   a.n_active = g->n_active;
+  a.nnz_active = g->nnz_active;
   a.spin_limit = g->spin_limit;
+  a.pull_alpha = g->pull_alpha;
+  a.pull_beta = g->pull_beta;
+  a.pull_gamma = g->pull_gamma;
   return a;
 }
 
@@ -321,7 +333,11 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
   cudaStream_t s = g->stream;
   launches += launch_small_comp(g->sc, g->d_key, &g->d_ctl->err, g->num_sms, s);
   if (g->n_active > 0) {
-    cudaError_t e;
+    cudaError_t e = cudaMemsetAsync((char*)g->d_ctl + kCtlMinrankOffset, 0xff, 3 * sizeof(u32), s);
+    if (e != cudaSuccess) {
+      *status = fail(LDD_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+      return -1;
+    }
     if (launch_bfs(bfs_args(g), g->bfs_grid, s, &e) < 0) {
       *status = fail(LDD_ERR_CUDA, "cooperative launch of the BFS kernel (%d x %d) failed: %s",
                      g->bfs_grid, kBfsThreads, cudaGetErrorString(e));
@@ -335,7 +351,7 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
   return launches;
 }
 
-struct Header {
+struct Header {  // the control block up to and including the BFS runtime state
   u32 err;
   int A;
   u32 rounds;
@@ -343,8 +359,17 @@ struct Header {
   u64 items;
   u64 edges;
   u64 cut;
+  u64 bar;
+  u64 qctr[3];
+  u32 minrank[3];
+  u32 pull_rounds;
+  u64 push_arcs;
+  u64 pull_arcs;
+  u64 pull_verts;
+  u32 ucnt[3];
+  u32 pad0;
 };
-static_assert(sizeof(Header) == kCtlHeaderBytes, "header layout");
+static_assert(sizeof(Header) == kCtlHeaderBytes + kCtlBfsStateBytes, "header layout");
 
 }  // namespace
 
@@ -415,36 +440,25 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   if (rp[0] != 0 || (int64_t)rp[n] != nnz)
     return bail(fail(LDD_ERR_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] must be nnz"));
 
-  // Vertices with arcs, and the first row of every cut span.
-  std::vector<u32> nzv;
-  nzv.reserve((size_t)n);
+  // The arcs (v, w) with v < w: one entry per undirected edge (cut count,
+  // component labelling).
+  std::vector<int2> up;
+  up.reserve((size_t)nnz / 2 + 1);
   for (int32_t v = 0; v < n; ++v)
-    if (rp[v + 1] > rp[v]) nzv.push_back((u32)v);
-  g->cut_items = (u32)nzv.size();
-  const size_t nch = ((size_t)nnz + kCutSpan - 1) / kCutSpan;
-  std::vector<u32> first(nch + 1, 0);
-  {
-    size_t j = 0;
-    for (size_t c = 0; c < nch; ++c) {
-      const int64_t e = (int64_t)c * kCutSpan;
-      while (j + 1 < nzv.size() && rp[nzv[j] + 1] <= e) ++j;
-      first[c] = (u32)j;
-    }
-  }
+    for (int64_t e = rp[v]; e < rp[v + 1]; ++e)
+      if (col[e] > v) up.push_back(make_int2(v, col[e]));
+  g->m_up = (u32)up.size();
   if (cudaMalloc(&g->d_row, rp.size() * 4) != cudaSuccess ||
       cudaMalloc(&g->d_col, std::max<size_t>(col.size(), 1) * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_nzv, std::max<size_t>(nzv.size(), 1) * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_cut_first, first.size() * 4) != cudaSuccess) {
+      cudaMalloc(&g->d_up, std::max<size_t>(up.size(), 1) * sizeof(int2)) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(LDD_ERR_OOM, "device allocation of the graph failed"));
   }
   if (cudaMemcpy(g->d_row, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       (nnz > 0 &&
        cudaMemcpy(g->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
-      (!nzv.empty() &&
-       cudaMemcpy(g->d_nzv, nzv.data(), nzv.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
-      cudaMemcpy(g->d_cut_first, first.data(), first.size() * 4, cudaMemcpyHostToDevice) !=
-          cudaSuccess)
+      (!up.empty() && cudaMemcpy(g->d_up, up.data(), up.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice) != cudaSuccess))
     return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
   if ((rc = build_component_tables(g)) != LDD_OK) return bail(rc);
   if ((rc = alloc_scratch(g)) != LDD_OK) return bail(rc);
@@ -460,6 +474,9 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
     g->bfs_grid = g->bfs_per_sm * g->num_sms;
   }
   g->spin_limit = env_u32("LDD_SPIN_LIMIT", 1u << 22);
+  g->pull_alpha = env_u32("LDD_PULL_ALPHA", 14);
+  g->pull_beta = env_u32("LDD_PULL_BETA", 24);
+  g->pull_gamma = env_u32("LDD_PULL_GAMMA", 8);
   g->stats.n = n;
   g->stats.nnz = nnz;
   g->stats.n_active = g->n_active;
@@ -481,6 +498,22 @@ void ldd_destroy_graph(ldd_graph* g) {
 int ldd_set_stream(ldd_graph* g, void* cuda_stream) {
   if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
   g->stream = (cudaStream_t)cuda_stream;
+  return LDD_OK;
+}
+
+int ldd_get_round_profile(const ldd_graph* g, int64_t* clocks, int32_t* kinds, int cap,
+                          int* out_count) {
+  if (!g || !clocks || !kinds || !out_count || cap < 0) return fail(LDD_ERR_ARG, "NULL argument");
+  DeviceGuard dg(g->device);
+  const int count = (int)std::min<int64_t>(std::min<int64_t>(g->stats.rounds + 1, kRoundProfile),
+                                           cap);
+  *out_count = count;
+  if (count <= 0) return LDD_OK;
+  CUDA_TRY(cudaMemcpyAsync(clocks, g->d_ctl->round_clk, (size_t)count * 8, cudaMemcpyDeviceToHost,
+                           g->stream));
+  CUDA_TRY(cudaMemcpyAsync(kinds, g->d_ctl->round_kind, (size_t)count * 4, cudaMemcpyDeviceToHost,
+                           g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
   return LDD_OK;
 }
 
@@ -525,20 +558,27 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
     d_shift = g->d_shift;
   }
   record(g, 1);
-  launches += launch_rank_and_buckets(d_shift, (u32)n, g->d_a, g->d_k[0], g->d_v[0], g->d_k[1],
-                                      g->d_v[1], g->d_status, &g->epoch, g->d_order, g->d_key,
-                                      g->d_bptr, g->bptr_cap, g->d_excl, g->d_ctl, g->num_sms, s);
-  record(g, 2);
-  int status = LDD_OK;
-  int l = run_bfs_finalize(g, center, dist, &status);
-  if (l < 0) return status;
-  launches += l;
-  record(g, 4);
-  CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, kCtlHeaderBytes, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaStreamSynchronize(s));
   Header h;
-  memcpy(&h, g->h_hdr, sizeof(h));
+  int status = LDD_OK;
+  for (int exact64 = 0; exact64 < 2; ++exact64) {
+    if (exact64) CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
+    launches += launch_rank_and_buckets(d_shift, (u32)n, g->d_a, g->d_k[0], g->d_v[0], g->d_k[1],
+                                        g->d_v[1], g->d_status, &g->epoch, g->d_order, g->d_key,
+                                        g->d_bptr, g->bptr_cap, g->d_excl, exact64 != 0, g->d_ctl,
+                                        g->num_sms, s);
+    record(g, 2);
+    int l = run_bfs_finalize(g, center, dist, &status);
+    if (l < 0) return status;
+    launches += l;
+    record(g, 4);
+    CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));
+    memcpy(&h, g->h_hdr, sizeof(h));
+    // A long run of equal 32-bit fraction codes with different fractions:
+    // everything after the fix-up was skipped; redo it with the exact key.
+    if (h.err != kErrRankRetry) break;
+  }
 
   if (h.err == kErrBucketCap) {
     // floor(delta_max) exceeds n: grow the start-bucket table and rerun the
@@ -556,11 +596,11 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
     CUDA_TRY(cudaMemsetAsync((char*)g->d_ctl + kCtlBfsStateOffset, 0, kCtlBfsStateBytes, s));
     launches += launch_bucket_ptr(g->d_k[0], g->d_k[1], g->d_ctl, (u32)n, g->d_bptr,
                                   g->bptr_cap, g->num_sms, s);
-    l = run_bfs_finalize(g, center, dist, &status);
+    const int l = run_bfs_finalize(g, center, dist, &status);
     if (l < 0) return status;
     launches += l;
     record(g, 4);
-    CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, kCtlHeaderBytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&h, g->h_hdr, sizeof(h));
   }
@@ -580,6 +620,10 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
   st.last_level = h.last_level;
   st.items = (int64_t)h.items;
   st.edges = (int64_t)h.edges;
+  st.pull_rounds = h.pull_rounds;
+  st.push_arcs = (int64_t)h.push_arcs;
+  st.pull_arcs = (int64_t)h.pull_arcs;
+  st.pull_vertices = (int64_t)h.pull_verts;
   st.launches = launches;
   st.ms_h2d = dev_in ? 0.f : elapsed(g, 0, 1);
   st.ms_rank = elapsed(g, 1, 2);
@@ -606,14 +650,13 @@ int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut) {
     d_center = g->d_center;
   }
   CUDA_TRY(cudaMemsetAsync(&g->d_ctl->cut, 0, sizeof(u64), s));
-  const int l = launch_cut(g->d_row, g->d_col, g->d_nzv, g->d_cut_first, g->cut_items,
-                           (u32)g->nnz, (u32)g->n, d_center, &g->d_ctl->cut, s);
-  CUDA_TRY(cudaMemcpyAsync(g->h_hdr + 64, &g->d_ctl->cut, sizeof(u64), cudaMemcpyDeviceToHost, s));
+  const int l = launch_cut(g->d_up, g->m_up, d_center, &g->d_ctl->cut, g->num_sms, s);
+  CUDA_TRY(cudaMemcpyAsync(g->h_hdr + 128, &g->d_ctl->cut, sizeof(u64), cudaMemcpyDeviceToHost, s));
   record(g, 7);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
   u64 cut;
-  memcpy(&cut, g->h_hdr + 64, sizeof(cut));
+  memcpy(&cut, g->h_hdr + 128, sizeof(cut));
   *out_cut = (int64_t)cut;
   g->stats.cut_launches = l;
   g->stats.ms_cut = elapsed(g, 6, 7);

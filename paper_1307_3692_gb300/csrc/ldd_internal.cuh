@@ -28,6 +28,7 @@ enum : u32 {
   kErrTimeout = 1u << 2,     // a bounded device-side wait ran out
   kErrBucketCap = 1u << 3,   // start-bucket table smaller than A + 2 (host grows it, reruns)
   kErrInternal = 1u << 4,    // a capacity invariant failed
+  kErrRankRetry = 1u << 5,   // a long run of equal 32-bit fraction codes: redo the rank exactly
 };
 
 // Radix sort: 8-bit digits, 256-thread CTAs, 16 keys per thread.
@@ -43,12 +44,11 @@ constexpr int kBfsThreads = 512;
 constexpr int kBfsBase = 256;
 constexpr int kBfsMaxSpan = 4096;
 
-// Cut counter and other arc-parallel kernels: arcs per CTA.
-constexpr int kCutThreads = 256;
-constexpr int kCutSpan = 2048;
-
 // Components with at most this many vertices are solved by one warp each.
 constexpr u32 kSmallComp = 32;
+
+constexpr int kRoundProfile = 256;
+enum : int { kRoundPush = 1, kRoundPull = 2, kRoundSkip = 3 };
 
 // Device control block; cudaMemsetAsync(0) at the start of every decomposition.
 // The header (err .. cut) is copied back to the host after every call.
@@ -62,9 +62,15 @@ struct Control {
   u64 edges;
   u64 cut;  // cut-edge accumulator
   // BFS runtime state
-  u32 bar_count;
-  u32 bar_gen;
-  u64 qctr[3];  // frontier counters: (items << 32) | edges
+  u64 bar;         // grid-barrier arrivals (monotonic within one launch)
+  u64 qctr[3];     // frontier counters: (items << 32) | edges
+  u32 minrank[3];  // smallest rank among the keys of each frontier level (reset to ~0)
+  u32 pull_rounds; // rounds run bottom-up
+  u64 push_arcs;   // arcs expanded top-down
+  u64 pull_arcs;   // arcs scanned bottom-up
+  u64 pull_verts;  // vertices examined bottom-up
+  u32 ucnt[3];     // lengths of the still-unsettled lists of bottom-up rounds
+  u32 pad0;
   // sort state
   u32 mask_f;  // bit d: fraction digit pass d is needed
   u32 mask_r;  // bit d: round digit pass d is needed
@@ -73,26 +79,37 @@ struct Control {
   u32 off_f[kFracDigits][256];
   u32 hist_r[kRoundDigits][256];
   u32 off_r[kRoundDigits][256];
+  // round profile of the last BFS: SM clock of CTA 0 at the end of each round
+  // (entry 0: after the level-0 starts) and the round's kind
+  long long round_clk[kRoundProfile];
+  int round_kind[kRoundProfile];
 };
 constexpr size_t kCtlHeaderBytes = 40;       // err .. cut
-constexpr size_t kCtlBfsStateOffset = 40;    // bar_count .. qctr
-constexpr size_t kCtlBfsStateBytes = 32;
+constexpr size_t kCtlBfsStateOffset = 40;    // bar_count .. pull_rounds
+constexpr size_t kCtlBfsStateBytes = 88;
+constexpr size_t kCtlMinrankOffset = 72;
 
 struct BfsArgs {
   const int* row_ptr;
   const int* col;
   u64* key;
   const int* bptr;   // [A + 2] start-bucket offsets into the round-sorted list
-  const u64* rk[2];  // round-sorted keys (start rounds), ping-pong pair
+  const u32* rk[2];  // round-sorted keys (start rounds), ping-pong pair
   const u32* rv[2];  // round-sorted vertices, ping-pong pair
   u32* qv[2];        // frontier queues: vertex
   int* qrow[2];      //                  row_ptr[vertex]
   u32* qoff[2];      //                  exclusive edge offset in the frontier
   u32* cf[2];        // first queue slot of every base chunk of edges
+  u32* ulist[2];     // vertices still unsettled after a bottom-up round (ping-pong)
+  const u32* excl;   // bit v: v is not handled by the BFS
   Control* ctl;
   u32 n;
-  u32 n_active;      // vertices with degree > 0 (the BFS settles exactly these)
+  u32 n_active;      // vertices the BFS settles (components of more than 32 vertices)
+  u64 nnz_active;    // their arcs
   u32 spin_limit;
+  u32 pull_alpha;    // go bottom-up when frontier arcs * alpha > unsettled arcs
+  u32 pull_gamma;    //   and frontier arcs * gamma > n_active (a bottom-up round reads every key)
+  u32 pull_beta;     // go back top-down when frontier vertices * beta < n_active
 };
 
 // Components of 2..kSmallComp vertices (k_graph.cu): comp c has comp_len[c]
@@ -116,17 +133,19 @@ struct CompScratch {
   u32* comp_off;  // [n / 2 + 1]
   u32* comp_len;  // [n / 2 + 1]
   u32* comp_v;    // [n]
-  u32* counters;  // [3]: components, members, vertices left to the BFS
+  u32* counters;  // [4]: components, members, vertices left to the BFS, their arcs
 };
 
 // ---------------------------------------------------------------- launchers
 // Fraction rank and start buckets (k_rank.cu).  Returns kernels launched.
 // Vertices with bit v of excl set get the start round A + 1 in the bucket sort,
-// i.e. they stay out of the BFS start buckets 0..A.
+// i.e. they stay out of the BFS start buckets 0..A.  exact64 = false: 32-bit
+// fraction codes plus run fix-up (may set kErrRankRetry); true: 64-bit
+// fraction bits.  The key buffers hold 8n bytes each.
 int launch_rank_and_buckets(const double* d_shift, u32 n, int* d_a, u64* k0, u32* v0, u64* k1,
                             u32* v1, u64* status, u32* epoch, u32* order, u64* key, int* bptr,
-                            u32 bptr_cap, const u32* excl, Control* ctl, int num_sms,
-                            cudaStream_t s);
+                            u32 bptr_cap, const u32* excl, bool exact64, Control* ctl,
+                            int num_sms, cudaStream_t s);
 int launch_bucket_ptr(const u64* k0, const u64* k1, Control* ctl, u32 n, int* bptr, u32 cap,
                       int num_sms, cudaStream_t s);
 // Persistent BFS (k_bfs.cu).  Returns kernels launched, or -1 with the CUDA
@@ -137,14 +156,14 @@ size_t bfs_smem_bytes();
 // Finalize, cut and per-graph component tables (k_graph.cu).
 int launch_finalize(const u64* key, const u32* order, u32 n, int* center, int* dist,
                     const u32* err, int num_sms, cudaStream_t s);
-int launch_cut(const int* row_ptr, const int* col, const u32* nzv, const u32* cut_first,
-               u32 n_items, u32 nnz, u32 n_vert, const int* center, u64* out, cudaStream_t s);
+// Cut count over the upper arcs (v, w), v < w, of the graph.
+int launch_cut(const int2* up, u32 m_up, const int* center, u64* out, int num_sms,
+               cudaStream_t s);
 int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s);
 // Labels components and fills t.comp_* and excl (bit v: kept out of the BFS);
-// counts = {small components, their members, vertices left to the BFS}.
-cudaError_t components_phase1(const int* row_ptr, const int* col, const u32* nzv,
-                              const u32* cut_first, u32 n_items, u32 n, u32 nnz, int num_sms,
-                              const CompScratch& t, u32* excl, u32 counts[3], cudaStream_t s);
+// counts = {small components, their members, vertices left to the BFS, their arcs}.
+cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 n, int num_sms,
+                              const CompScratch& t, u32* excl, u32 counts[4], cudaStream_t s);
 // Adjacency masks of the small-component members (sc.comp_v already filled).
 cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,
                               const SmallComps& sc, int num_sms, cudaStream_t s);
@@ -164,6 +183,42 @@ __device__ __forceinline__ u32 ld_acquire_u32(const u32* p) {
   u32 v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Inclusive max-scan of a[0 .. len) in shared memory (len <= kLen) by a CTA of
+// kThreads threads.  Warp w owns the contiguous block [w * kLen / kWarps, ...)
+// and scans it 32 elements at a time with shuffles, so shared-memory accesses
+// are one word per lane (no bank conflicts); warp maxima are combined through
+// wtot[kThreads / 32].  The caller synchronises before and after.
+template <int kThreads, int kLen>
+__device__ __forceinline__ void block_max_scan(int* a, int len, int* wtot) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kPerWarp = kLen / kWarps;
+  static_assert(kPerWarp % 32 == 0, "scan block must be whole warps");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int base = w * kPerWarp;
+  int carry = -1;
+  for (int c = 0; c < kPerWarp && base + c < len; c += 32) {
+    const int i = base + c + lane;
+    int x = (i < len) ? a[i] : -1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x = max(x, y);
+    }
+    x = max(x, carry);
+    if (i < len) a[i] = x;
+    carry = __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) wtot[w] = carry;
+  __syncthreads();
+  int pre = -1;
+  for (int i = 0; i < w; ++i) pre = max(pre, wtot[i]);
+  if (pre >= 0)
+    for (int c = 0; c < kPerWarp && base + c < len; c += 32) {
+      const int i = base + c + lane;
+      if (i < len) a[i] = max(a[i], pre);
+    }
 }
 
 __device__ __forceinline__ u64 ld_volatile_u64(const u64* p) {

@@ -277,3 +277,39 @@ def test_component_labels_deep_trees(ldd, cuda):
         _, _, _, st = assert_parity(ldd, G, gen.shifts(G.n, beta, seed), beta)
         assert st["small_components"] == int(((sz >= 2) & (sz <= 32)).sum())
         assert st["n_active"] == int(sz[lab][sz[lab] > 32].size)
+
+
+@pytest.mark.parametrize("kind", ["equal_codes_unequal_fractions", "tiny_shifts", "half_ties"])
+def test_fraction_rank_exact_fallback(ldd, cuda, kind):
+    """Runs of vertices whose fractions agree in their top 32 bits but differ
+    below (or are all below 2^-32) force the exact 64-bit rank path; runs of
+    exactly equal fractions keep the fast path (ties resolved by id)."""
+    rng = np.random.default_rng(3)
+    G = gen.grid2d(40, 30)
+    if kind == "equal_codes_unequal_fractions":
+        shifts = rng.integers(0, 40, G.n) + 0.5 + rng.integers(0, 1 << 12, G.n) * 2.0 ** -45
+    elif kind == "tiny_shifts":
+        shifts = rng.random(G.n) * 2.0 ** -33 + rng.integers(0, 3, G.n)
+    else:
+        shifts = rng.integers(0, 60, G.n) * 0.5
+    assert_parity(ldd, G, shifts, 0.1)
+
+
+@pytest.mark.parametrize("mode", ["always_pull", "alternate", "default"])
+def test_bottom_up_rounds(ldd, cuda, mode, monkeypatch):
+    """Bottom-up (pull) rounds with the exact min-rank early exit give the same
+    keys as top-down rounds: forced every round, alternated, and by heuristic."""
+    env = {"always_pull": ("1000000000", "1000000000"), "alternate": ("1000000000", "1"),
+           "default": ("14", "24")}[mode]
+    monkeypatch.setenv("LDD_PULL_ALPHA", env[0])
+    monkeypatch.setenv("LDD_PULL_BETA", env[1])
+    cases = [(gen.rmat(13), 0.1, 1), (gen.rmat(14), 0.02, 2), (gen.grid2d(60, 70), 0.05, 3),
+             (gen.grid3d(14, 15, 16), 0.2, 4), (gen.rgg(4000, 5), 0.3, 5)]
+    for G, beta, seed in cases:
+        for floor_shifts in (False, True):
+            shifts = gen.shifts(G.n, beta, seed)
+            if floor_shifts:
+                shifts = np.floor(shifts)  # fraction ties: the id breaks them
+            _, _, _, st = assert_parity(ldd, G, shifts, beta)
+            if mode != "default":
+                assert st["pull_rounds"] > 0
