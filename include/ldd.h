@@ -177,13 +177,14 @@ int ldd_set_timing(ldd_graph* g, int enable);
 
 /*
  * ldd_get_round_profile -- diagnostic: per-round timestamps of the last BFS.
- *   clocks[i]  SM clock (cycles) of the first CTA when round i ended; entry 0
- *              is after the level-0 starts, so round i took clocks[i] -
- *              clocks[i-1] cycles.
+ *   clocks[3i .. 3i+2]  SM clock (cycles) of the first CTA in round i: after
+ *              its expansion, after its start-bucket scan, and when its closing
+ *              barrier released the CTA.  Entry 0 is the level-0 starts, so
+ *              round i took clocks[3i+2] - clocks[3i-1] cycles.
  *   kinds[i]   1 = top-down (push), 2 = bottom-up (pull), 3 = no frontier (jump
  *              to the next start bucket).
- * At most cap entries (and at most 256) are written; *out_count gets the number.
- * Host buffers.
+ * At most cap rounds (and at most 256) are written; *out_count gets the number.
+ * Host buffers of 3 * cap and cap entries.
  */
 int ldd_get_round_profile(const ldd_graph* g, int64_t* clocks, int32_t* kinds, int cap,
                           int* out_count);

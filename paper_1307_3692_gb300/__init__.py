@@ -174,7 +174,7 @@ def ldd_get_round_profile(g: int, cap: int = 256):
     """(clocks, kinds) of the last BFS's rounds (see include/ldd.h)."""
     import numpy as np
 
-    clocks = np.zeros(cap, dtype=np.int64)
+    clocks = np.zeros((cap, 3), dtype=np.int64)
     kinds = np.zeros(cap, dtype=np.int32)
     cnt = ctypes.c_int(0)
     _check(_lib.ldd_get_round_profile(g, clocks.ctypes.data, kinds.ctypes.data, cap,

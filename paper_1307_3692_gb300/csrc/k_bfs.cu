@@ -411,8 +411,10 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
   append_bucket(a, 0, rv, 0, 0, myrank);
   post_cta_min(s, myrank);
   grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[0], &s.minrank);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->round_clk[0] = clock64();
+  const bool profiler = blockIdx.x == 0 && threadIdx.x == 0;
+  if (profiler) {
+    const long long t = clock64();
+    ctl->round_clk[0][0] = ctl->round_clk[0][1] = ctl->round_clk[0][2] = t;
     ctl->round_kind[0] = kRoundSkip;
   }
 
@@ -453,6 +455,7 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
         expand(a, s, (int)(phase & 1), Q, E, lvl, qi, qb, myrank);
         push_arcs += E;
       }
+      if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
       if (lvl + 1 <= A) append_bucket(a, lvl + 1, rv, qi, qb, myrank);
       nlvl = lvl + 1;
     } else {
@@ -461,15 +464,17 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
       if ((u32)start >= a.n) break;
       const int rr = (int)__ldg(rk + start);  // next non-empty start bucket
       if (rr > A) break;                      // only vertices the BFS does not handle remain
+      if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
       append_bucket(a, rr, rv, qi, qb, myrank);
       nlvl = rr;
     }
+    if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][1] = clock64();
     post_cta_min(s, myrank);
     grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[qi], &s.minrank);
     ++phase;
     lvl = nlvl;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && phase < (u32)kRoundProfile) {
-      ctl->round_clk[phase] = clock64();
+    if (profiler && phase < (u32)kRoundProfile) {
+      ctl->round_clk[phase][2] = clock64();
       ctl->round_kind[phase] = Q == 0 ? kRoundSkip : (pulling ? kRoundPull : kRoundPush);
     }
   }

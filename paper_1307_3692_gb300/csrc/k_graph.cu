@@ -32,8 +32,6 @@ namespace ldd {
 namespace {
 
 constexpr u32 kFull = 0xffffffffu;
-constexpr int kCutWinBatch = 4;
-constexpr u32 kNone = 0xffffffffu;
 
 __global__ void __launch_bounds__(256) k_finalize(const u64* __restrict__ key,
                                                   const u32* __restrict__ order, u32 n,

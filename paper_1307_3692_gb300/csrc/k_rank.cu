@@ -3,30 +3,28 @@
 //  1. split (Algorithm 1 step 2, Section 4): a_u = floor(delta_u),
 //     f_u = delta_u - a_u (exact in FP64), A = max a_u = floor(delta_max).
 //  2. fraction rank (Section 4: the fractional parts are tie-breakers within
-//     an integer level and can be replaced by a permutation): the stable order
-//     of (f_u descending, u ascending) gives order[rank] = u.
+//     an integer level and can be replaced by a permutation): rank_u = the
+//     position of u in the order (f_u descending, u ascending), order[rank] = u.
 //  3. keys: key_u = ((A - a_u) << 32) | rank_u, i.e. u's own start label at
 //     round R_u = A - a_u.
 //  4. start buckets (Section 4: the super-source edge of length L is looked at
-//     when the frontier reaches distance L): stable sort of the vertices by
-//     R_u, and bptr[r] = first position with R >= r, for r = 0 .. A + 1.
-//     Vertices the BFS does not handle (no arcs, or a component small enough
-//     for the warp solver) sort with R = A + 1, after every real bucket.
+//     when the frontier reaches distance L): the vertices the BFS handles,
+//     grouped by R_u (any order inside a group); bptr[r] = start of group r,
+//     r = 0 .. A + 1.
 //
-// Fraction rank, fast path: c_u = floor(f_u * 2^32) is a 32-bit code that is
-// monotone in f_u, so a stable LSD sort of ~c_u (4 passes of 8 bits) orders
-// the vertices by f descending except inside runs of equal codes, where they
-// are in id order.  A fix-up pass sorts every such run of at most 32 vertices
-// by the exact (f descending, id ascending); a run longer than 32 whose
-// fractions are not all equal (never seen with drawn shifts, possible with
-// crafted ones) makes the host redo the rank with the exact 64-bit path:
-// the order-preserving bits of f itself as the key, 8 passes.
+// Fraction rank, fast path (most-significant-digit bucketing): the bucket of u
+// is the top B bits of ~floor(f_u * 2^32), which is monotone in f_u, with
+// 2^B about n / 16 so that buckets hold ~16 vertices.  A global histogram, an
+// exclusive scan, one scatter of (bits of f_u, u) into the buckets, and one
+// warp per bucket that ranks its members exactly by (f descending, u
+// ascending) with the full FP64 fractions.  A bucket larger than kLocalMax
+// (crafted shifts, e.g. all fractions equal) makes the host redo the rank with
+// the exact path: a stable LSD radix sort of the order-preserving bits of f
+// (8 "onesweep" passes of 8 bits).
 //
-// The radix sort is a single-pass-per-digit ("onesweep") LSD sort: one kernel
-// per 8-bit digit; each 4096-key tile ranks its keys in shared memory with
-// warp match, publishes its per-digit counts and finds its global offsets by
-// decoupled look-back over the preceding tiles.  Digits that are the same
-// for every key are skipped (their pass is a no-op).
+// Start buckets: a counting sort by R_u (histogram while the keys are built,
+// an exclusive scan that is bptr, and a scatter in which each CTA reserves its
+// range of every group with one atomic).
 #include "ldd_internal.cuh"
 
 namespace ldd {
@@ -35,7 +33,12 @@ namespace {
 
 constexpr u32 kFull = 0xffffffffu;
 constexpr u32 kLookbackSpinLimit = 1u << 24;  // ~1 s of polling, then kErrTimeout
-constexpr int kRunMax = 32;                   // longest run of equal codes sorted in place
+constexpr u32 kLocalMax = 1024;               // largest fraction bucket ranked in place
+constexpr int kScanThreads = 256;
+constexpr int kScanIpt = 16;
+constexpr int kScanTile = kScanThreads * kScanIpt;
+constexpr u32 kRBins = 4096;                  // start rounds counted in shared memory
+constexpr int kRChunk = 16;                   // vertices per thread in the start-bucket scatter
 
 __device__ __forceinline__ bool failed(const Control* ctl) {
   return *(volatile const u32*)&ctl->err != 0u;
@@ -54,27 +57,160 @@ __device__ __forceinline__ void hist_add(u32* sh, u32 digit, bool valid, u32 lan
   }
 }
 
-// Exact fraction of a validated shift, with -0 folded into +0.
-__device__ __forceinline__ double frac_of(double d) {
+// Exact fraction of a validated shift, with -0 folded into +0; the bits of a
+// non-negative double order like its value.
+__device__ __forceinline__ u64 frac_bits(double d) {
   const double f = d - floor(d);
-  return f == 0.0 ? 0.0 : f;
+  return f == 0.0 ? 0ull : (u64)__double_as_longlong(f);
 }
 
-// Split.  KeyT = u32: key = ~floor(f * 2^32); KeyT = u64: key = ~bits(f).
-template <typename KeyT>
-__global__ void __launch_bounds__(256) k_split(const double* __restrict__ delta, u32 n,
-                                               int* __restrict__ a_out, KeyT* __restrict__ kout,
-                                               u32* __restrict__ vout, Control* ctl) {
-  constexpr int kDigits = (int)sizeof(KeyT);
-  __shared__ u32 sh[kDigits][256];
+__device__ __forceinline__ void split_one(double d, u32& err, int& a, double& f) {
+  a = 0;
+  f = 0.0;
+  if (!(d >= 0.0)) {
+    err |= kErrShiftArg;
+  } else if (!(d < 2147483648.0)) {
+    err |= kErrShiftRange;
+  } else {
+    const double fl = floor(d);
+    a = (int)fl;
+    f = d - fl;  // exact: fl <= d < 2 fl, or fl = 0
+  }
+}
+
+__device__ __forceinline__ void finish_split(u32 err, int amax, Control* ctl) {
   __shared__ int s_amax;
   __shared__ u32 s_err;
-  const u32 tid = threadIdx.x, lane = tid & 31;
-  for (u32 i = tid; i < kDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     s_amax = 0;
     s_err = 0;
   }
+  __syncthreads();
+  if (err) atomicOr(&s_err, err);
+  atomicMax(&s_amax, amax);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_err) atomicOr(&ctl->err, s_err);
+    atomicMax(&ctl->A, s_amax);
+  }
+}
+
+// ---------------------------------------------------------------- fast path
+__device__ __forceinline__ u32 bucket_of(double f, int B) {
+  const u32 code = (u32)floor(f * 4294967296.0);  // f * 2^32 < 2^32, exact scaling
+  return (~code) >> (32 - B);                      // larger fraction, smaller bucket
+}
+
+__global__ void __launch_bounds__(256) k_bsplit(const double* __restrict__ delta, u32 n, int B,
+                                                int* __restrict__ a_out, u32* __restrict__ cnt,
+                                                Control* ctl) {
+  int amax = 0;
+  u32 err = 0;
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+    int a;
+    double f;
+    split_one(delta[u], err, a, f);
+    a_out[u] = a;
+    atomicAdd(cnt + bucket_of(f, B), 1u);
+    amax = max(amax, a);
+  }
+  finish_split(err, amax, ctl);
+}
+
+// Scatter (bits of f_u, u) records into the buckets (cur[] holds the bucket
+// starts and ends up holding the bucket ends).  A bucket too large to rank in
+// place sends the host to the exact path instead.
+__global__ void __launch_bounds__(256) k_bscatter(const double* __restrict__ delta, int B,
+                                                  u32* cur, u32 n, ulonglong2* __restrict__ tmp,
+                                                  Control* ctl) {
+  if (failed(ctl)) return;
+  if (*(volatile const u32*)&ctl->maxbucket > kLocalMax) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrRankRetry);
+    return;
+  }
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+    const double d = delta[u];
+    const double f = d - floor(d);  // validated by k_bsplit
+    const u32 pos = atomicAdd(cur + bucket_of(f, B), 1u);
+    if (pos < n) tmp[pos] = make_ulonglong2(frac_bits(d), u);
+  }
+}
+
+// Ranks bucket [s, s + len) of the records (len <= 32): each member's exact
+// position is the number of members before it in (f descending, id ascending).
+__device__ __forceinline__ void rank_small(const ulonglong2 rec, u32 s, u32 len, u32 lane,
+                                           u32* __restrict__ order, u32* __restrict__ rank) {
+  u32 r = 0;
+  for (u32 j = 0; j < len; ++j) {
+    const u64 fj = __shfl_sync(kFull, rec.x, j);
+    const u32 uj = (u32)__shfl_sync(kFull, rec.y, j);
+    r += (fj > rec.x || (fj == rec.x && uj < (u32)rec.y)) ? 1u : 0u;
+  }
+  if (lane < len) {
+    order[s + r] = (u32)rec.y;
+    rank[(u32)rec.y] = s + r;
+  }
+}
+
+// One warp per bucket [end[b-1], end[b]), two buckets per step for more loads
+// in flight; buckets of more than 32 members are ranked by counting against
+// all members.
+__global__ void __launch_bounds__(256) k_bsort(const u32* __restrict__ end, u32 nbkt,
+                                               const ulonglong2* __restrict__ tmp, u32 n,
+                                               u32* __restrict__ order, u32* __restrict__ rank,
+                                               Control* ctl) {
+  if (failed(ctl)) return;
+  const u32 lane = threadIdx.x & 31;
+  const u32 warps = gridDim.x * (blockDim.x / 32);
+  for (u32 b0 = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); b0 < nbkt; b0 += 2 * warps) {
+    const u32 b1 = b0 + warps;
+    u32 s[2], e[2];
+    s[0] = b0 ? end[b0 - 1] : 0u;
+    e[0] = end[b0];
+    s[1] = 0;
+    e[1] = 0;
+    if (b1 < nbkt) {
+      s[1] = end[b1 - 1];
+      e[1] = end[b1];
+    }
+    ulonglong2 rec[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      rec[k] = make_ulonglong2(0ull, 0ull);
+      if (e[k] > s[k] && e[k] <= n && e[k] - s[k] <= 32 && lane < e[k] - s[k])
+        rec[k] = tmp[s[k] + lane];
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (e[k] <= s[k] || e[k] > n) continue;
+      const u32 len = e[k] - s[k];
+      if (len <= 32) {
+        rank_small(rec[k], s[k], len, lane, order, rank);
+      } else {
+        for (u32 i = lane; i < len; i += 32) {
+          const ulonglong2 me = tmp[s[k] + i];
+          u32 r = 0;
+          for (u32 j = 0; j < len; ++j) {
+            const ulonglong2 o = tmp[s[k] + j];
+            r += (o.x > me.x || (o.x == me.x && (u32)o.y < (u32)me.y)) ? 1u : 0u;
+          }
+          order[s[k] + r] = (u32)me.y;
+          rank[(u32)me.y] = s[k] + r;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- exact path
+__global__ void __launch_bounds__(256) k_split64(const double* __restrict__ delta, u32 n,
+                                                 int* __restrict__ a_out, u64* __restrict__ kout,
+                                                 u32* __restrict__ vout, Control* ctl) {
+  __shared__ u32 sh[kFracDigits][256];
+  const u32 tid = threadIdx.x, lane = tid & 31;
+  for (u32 i = tid; i < kFracDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
   int amax = 0;
   u32 err = 0;
@@ -82,45 +218,27 @@ __global__ void __launch_bounds__(256) k_split(const double* __restrict__ delta,
   for (u32 base = blockIdx.x * blockDim.x + (tid & ~31u); base < n; base += stride) {
     const u32 idx = base + lane;
     const bool valid = idx < n;
-    KeyT key = 0;
+    u64 key = 0;
     if (valid) {
-      const double d = delta[idx];
-      int a = 0;
-      double f = 0.0;
-      if (!(d >= 0.0)) {
-        err |= kErrShiftArg;
-      } else if (!(d < 2147483648.0)) {
-        err |= kErrShiftRange;
-      } else {
-        const double fl = floor(d);
-        a = (int)fl;
-        f = d - fl;  // exact: fl <= d < 2 fl, or fl = 0
-      }
-      if (sizeof(KeyT) == 4) {
-        key = (KeyT)~(u32)floor(f * 4294967296.0);  // f * 2^32 < 2^32, exact scaling
-      } else {
-        key = (KeyT)~(f == 0.0 ? 0ull : (u64)__double_as_longlong(f));
-      }
+      int a;
+      double f;
+      split_one(delta[idx], err, a, f);
+      key = ~(f == 0.0 ? 0ull : (u64)__double_as_longlong(f));  // ascending key: f descending
       a_out[idx] = a;
       kout[idx] = key;
       vout[idx] = idx;
       amax = max(amax, a);
     }
 #pragma unroll
-    for (int dg = 0; dg < kDigits; ++dg)
+    for (int dg = 0; dg < kFracDigits; ++dg)
       hist_add(sh[dg], (u32)(key >> (8 * dg)) & 255u, valid, lane);
   }
-  if (err) atomicOr(&s_err, err);
-  atomicMax(&s_amax, amax);
   __syncthreads();
-  if (tid == 0) {
-    if (s_err) atomicOr(&ctl->err, s_err);
-    atomicMax(&ctl->A, s_amax);
-  }
-  for (u32 i = tid; i < kDigits * 256; i += blockDim.x) {
+  for (u32 i = tid; i < kFracDigits * 256; i += blockDim.x) {
     const u32 c = (&sh[0][0])[i];
     if (c) atomicAdd(&(&ctl->hist_f[0][0])[i], c);
   }
+  finish_split(err, amax, ctl);
 }
 
 // Exclusive offsets of every digit histogram; a digit whose keys all share
@@ -156,38 +274,36 @@ __global__ void __launch_bounds__(256) k_scan_digits(const u32* __restrict__ his
 
 constexpr int kSortWarps = kSortThreads / 32;
 
-template <typename KeyT>
 struct SortSmem {
-  KeyT keys[kSortTile];             // the tile, staged in sorted order for the write-out
+  u64 keys[kSortTile];         // the tile, staged in sorted order for the write-out
   u32 vals[kSortTile];
-  u32 whist[kSortWarps][256];       // per-warp digit counts, then per-warp offsets
-  u32 tile_excl[256];               // start of each digit's run inside the tile
-  u32 base[256];                    // global start of this tile's run of each digit
+  u32 whist[kSortWarps][256];  // per-warp digit counts, then per-warp offsets
+  u32 tile_excl[256];          // start of each digit's run inside the tile
+  u32 base[256];               // global start of this tile's run of each digit
   u32 wsum[kSortWarps];
   u32 tile;
   u32 bad;
 };
 
-// One stable LSD pass on digit `pass` (bits shift..shift+7).  Buffers are a
-// ping-pong pair; the input side is the parity of the passes run before.  The
-// tile is reordered by digit in shared memory first, so that the write-out of
-// each digit's run is contiguous and coalesced.
-template <typename KeyT>
+// One stable LSD pass on digit `pass` (bits shift..shift+7) of 64-bit keys.
+// Buffers are a ping-pong pair; the input side is the parity of the passes run
+// before.  Each 4096-key tile ranks its keys per digit in shared memory with
+// warp match, finds its global offsets by decoupled look-back over the
+// preceding tiles, and writes each digit's run out contiguously.
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
-    KeyT* __restrict__ k0, u32* __restrict__ v0, KeyT* __restrict__ k1, u32* __restrict__ v1,
-    u32 n, int pass, int shift, const u32* __restrict__ mask_ptr,
-    const u32* __restrict__ digit_off, u64* __restrict__ status, u32* __restrict__ tile_ctr,
-    u32 epoch, u32* err) {
+    u64* __restrict__ k0, u32* __restrict__ v0, u64* __restrict__ k1, u32* __restrict__ v1, u32 n,
+    int pass, int shift, const u32* __restrict__ mask_ptr, const u32* __restrict__ digit_off,
+    u64* __restrict__ status, u32* __restrict__ tile_ctr, u32 epoch, u32* err) {
   const u32 mask = *mask_ptr;
   if (!((mask >> pass) & 1u) || *(volatile u32*)err != 0u) return;
   const int par = __popc(mask & ((1u << pass) - 1u)) & 1;
-  const KeyT* kin = par ? k1 : k0;
+  const u64* kin = par ? k1 : k0;
   const u32* vin = par ? v1 : v0;
-  KeyT* kout = par ? k0 : k1;
+  u64* kout = par ? k0 : k1;
   u32* vout = par ? v0 : v1;
 
   extern __shared__ __align__(16) unsigned char sort_smem_raw[];
-  SortSmem<KeyT>& sm = *reinterpret_cast<SortSmem<KeyT>*>(sort_smem_raw);
+  SortSmem& sm = *reinterpret_cast<SortSmem*>(sort_smem_raw);
   const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     sm.tile = atomicAdd(tile_ctr, 1u);
@@ -199,19 +315,14 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   const u32 tile0 = tile * kSortTile;
   const u32 base = tile0 + warp * (32 * kSortIpt);
 
-  KeyT key[kSortIpt];
+  u64 key[kSortIpt];
   u32 val[kSortIpt];
   u32 rk[kSortIpt];
 #pragma unroll
   for (int k = 0; k < kSortIpt; ++k) {
     const u32 idx = base + k * 32 + lane;
-    if (idx < n) {
-      key[k] = kin[idx];
-      val[k] = vin[idx];
-    } else {
-      key[k] = 0;
-      val[k] = 0;
-    }
+    key[k] = (idx < n) ? kin[idx] : 0ull;
+    val[k] = (idx < n) ? vin[idx] : 0u;
   }
   const u32 lt = lanemask_lt();
 #pragma unroll
@@ -228,9 +339,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     __syncwarp();
   }
   __syncthreads();
-  // thread tid owns digit tid: per-warp offsets, tile total, and (below) the
-  // tile-local start of each digit and the global start from the look-back
-  const u32 dg = tid;
+  const u32 dg = tid;  // thread tid owns digit tid
   u32 run = 0;
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) {
@@ -279,7 +388,6 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   sm.base[dg] = digit_off[dg] + excl;
   __syncthreads();
   if (sm.bad) return;  // offsets unknown: write nothing
-  // stage the tile in digit order
 #pragma unroll
   for (int k = 0; k < kSortIpt; ++k) {
     const u32 idx = base + k * 32 + lane;
@@ -291,10 +399,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
   }
   __syncthreads();
-  // write out: consecutive threads, consecutive positions of one digit's run
   const u32 tile_n = min((u32)kSortTile, n - tile0);
   for (u32 i = tid; i < tile_n; i += kSortThreads) {
-    const KeyT kv = sm.keys[i];
+    const u64 kv = sm.keys[i];
     const u32 d = (u32)(kv >> shift) & 255u;
     const u32 pos = sm.base[d] + (i - sm.tile_excl[d]);
     if (pos < n) {
@@ -304,120 +411,253 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   }
 }
 
-// Exact order inside runs of equal 32-bit fraction codes (see the file comment).
-__global__ void __launch_bounds__(256) k_fixup_runs(const u32* __restrict__ k0, u32* v0,
-                                                    const u32* __restrict__ k1, u32* v1,
-                                                    const double* __restrict__ delta, Control* ctl,
-                                                    u32 n) {
+// order[p] = u and rank[u] = p for the sorted fraction order (exact path).
+__global__ void __launch_bounds__(256) k_rank_scatter(const u32* __restrict__ v0,
+                                                      const u32* __restrict__ v1, Control* ctl,
+                                                      u32 n, u32* __restrict__ order,
+                                                      u32* __restrict__ rank) {
   if (failed(ctl)) return;
-  const u32 par = __popc(ctl->mask_f) & 1u;
-  const u32* K = par ? k1 : k0;
-  u32* U = par ? v1 : v0;
+  const u32* vals = (__popc(ctl->mask_f) & 1u) ? v1 : v0;
   const u32 stride = gridDim.x * blockDim.x;
   for (u32 p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const u32 kp = K[p];
-    const bool cont = p > 0 && K[p - 1] == kp;  // p continues a run
-    if (!cont && p + 1 < n && K[p + 1] == kp) {
-      // p starts a run: measure it (up to kRunMax + 1) and sort it if short
-      u32 len = 1;
-      while (len <= (u32)kRunMax && p + len < n && K[p + len] == kp) ++len;
-      if (len <= (u32)kRunMax) {
-        double f[kRunMax];
-        u32 u[kRunMax];
-        for (u32 i = 0; i < len; ++i) {
-          u[i] = U[p + i];
-          f[i] = frac_of(delta[u[i]]);
-        }
-        for (u32 i = 1; i < len; ++i) {  // insertion sort: f descending, id ascending
-          const double fi = f[i];
-          const u32 ui = u[i];
-          u32 j = i;
-          while (j > 0 && (f[j - 1] < fi || (f[j - 1] == fi && u[j - 1] > ui))) {
-            f[j] = f[j - 1];
-            u[j] = u[j - 1];
-            --j;
-          }
-          f[j] = fi;
-          u[j] = ui;
-        }
-        for (u32 i = 0; i < len; ++i) U[p + i] = u[i];
-      }
-    } else if (cont) {
-      // Inside a run.  Adjacent fractions that differ need sorting; if the run
-      // is longer than kRunMax nobody sorts it here, so ask for the exact path.
-      // (A short run may be being sorted concurrently; that only affects which
-      // threads get here, never the length test.)
-      if (frac_of(delta[U[p]]) != frac_of(delta[U[p - 1]])) {
-        u32 lo = p, hi = p;
-        while (hi - lo <= (u32)kRunMax && lo > 0 && K[lo - 1] == kp) --lo;
-        while (hi - lo <= (u32)kRunMax && hi + 1 < n && K[hi + 1] == kp) ++hi;
-        if (hi - lo + 1 > (u32)kRunMax) atomicOr(&ctl->err, kErrRankRetry);
-      }
+    u32 u = vals[p];
+    if (u >= n) {  // cannot happen for a permutation; never index with it
+      atomicOr(&ctl->err, kErrInternal);
+      u = 0;
     }
+    order[p] = u;
+    rank[u] = p;
   }
 }
 
-// rank -> key, and the start-round sort input (R_u, u) in rank order.
-__global__ void __launch_bounds__(256) k_rank_keys(const u32* __restrict__ v0,
-                                                   const u32* __restrict__ v1,
-                                                   const int* __restrict__ a,
-                                                   const u32* __restrict__ excl, Control* ctl,
-                                                   u32 n, u32* __restrict__ order,
-                                                   u64* __restrict__ key, u32* kR, u32* vR) {
-  __shared__ u32 sh[kRoundDigits][256];
-  const u32 tid = threadIdx.x, lane = tid & 31;
-  for (u32 i = tid; i < kRoundDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
-  __syncthreads();
+// ---------------------------------------------------------------- device scan
+// In-place exclusive scan of data[0 .. len), single pass with decoupled
+// look-back over 4096-element tiles.  len = A + 2 when len_from_A (the
+// start-round histogram), else len_host.  Optionally copies the result to
+// copy[] and records the largest input value in *maxv.  Tiles take tickets in
+// order, so every tile's predecessors are running or done; every wait is
+// bounded.  One warp looks back over 32 predecessor tiles at a time.
+__global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy, u32 len_host,
+                                                            int len_from_A, u64* __restrict__ status,
+                                                            u32 epoch, u32* tile_ctr, u32* maxv,
+                                                            Control* ctl) {
+  __shared__ u32 s_tile, s_excl, s_bad;
+  __shared__ u32 s_wsum[kScanThreads / 32];
+  __shared__ u32 s_wmax[kScanThreads / 32];
   if (failed(ctl)) return;
-  const u32 par = __popc(ctl->mask_f) & 1u;
-  const u32* vals = par ? v1 : v0;
-  const int A = ctl->A;
-  const u32 stride = gridDim.x * blockDim.x;
-  for (u32 base = blockIdx.x * blockDim.x + (tid & ~31u); base < n; base += stride) {
-    const u32 p = base + lane;
-    const bool valid = p < n;
-    u32 R = 0;
-    if (valid) {
-      u32 u = vals[p];
-      if (u >= n) {  // cannot happen for a permutation; never index with it
-        atomicOr(&ctl->err, kErrInternal);
-        u = 0;
-      }
-      order[p] = u;
-      R = (u32)(A - a[u]);
-      key[u] = ((u64)R << 32) | p;
-      if (excl[u >> 5] >> (u & 31) & 1u) R = (u32)A + 1u;
-      kR[p] = R;
-      vR[p] = u;
-    }
+  const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_tile = atomicAdd(tile_ctr, 1u);
+    s_bad = 0;
+    s_excl = 0;
+  }
+  __syncthreads();
+  const u32 tile = s_tile;
+  const u32 len = len_from_A ? (u32)ctl->A + 2u : len_host;
+  const u32 t0 = tile * kScanTile;
+  if (t0 >= len) return;  // tiles past the end: no later tile needs them
+  const u32 my0 = t0 + tid * kScanIpt;
+  u32 v[kScanIpt];
+  u32 tot = 0, mx = 0;
 #pragma unroll
-    for (int dg = 0; dg < kRoundDigits; ++dg) hist_add(sh[dg], (R >> (8 * dg)) & 255u, valid, lane);
+  for (int i = 0; i < kScanIpt; ++i) {
+    v[i] = (my0 + i < len) ? data[my0 + i] : 0u;
+    tot += v[i];
+    mx = max(mx, v[i]);
+  }
+  u32 x = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, x, o);
+    if (lane >= (u32)o) x += y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  if (lane == 31) s_wsum[warp] = x;
+  if (lane == 0) s_wmax[warp] = mx;
+  __syncthreads();
+  u32 wpre = 0, tile_tot = 0, tile_max = 0;
+  for (u32 w = 0; w < kScanThreads / 32; ++w) {
+    if (w < warp) wpre += s_wsum[w];
+    tile_tot += s_wsum[w];
+    tile_max = max(tile_max, s_wmax[w]);
+  }
+  if (warp == 0) {
+    const u64 tag = (u64)epoch << 32;
+    u64* mine = status + tile;
+    if (tile == 0) {
+      if (lane == 0) st_volatile_u64(mine, tag | (2ull << 30) | tile_tot);
+    } else {
+      if (lane == 0) st_volatile_u64(mine, tag | (1ull << 30) | tile_tot);
+      u32 excl = 0;
+      int p = (int)tile - 1;
+      u32 spins = 0;
+      bool bad = false;
+      while (p >= 0) {
+        // lane l looks at tile p - l; "before tile 0" counts as an inclusive prefix of 0
+        const int q = p - (int)lane;
+        const u64 sv = (q >= 0) ? ld_volatile_u64(status + q) : (tag | (2ull << 30));
+        const bool ready = (u32)(sv >> 32) == epoch;
+        const bool pref = ready && ((((u32)sv) >> 30) == 2u);
+        const u32 pmask = __ballot_sync(kFull, pref);
+        const u32 limit = pmask ? (u32)(__ffs(pmask) - 1) : 31u;  // lanes 0..limit are needed
+        const u32 rmask = __ballot_sync(kFull, ready);
+        const u32 need = (limit == 31u) ? kFull : ((2u << limit) - 1u);
+        if ((rmask & need) != need) {
+          if (++spins > kLookbackSpinLimit) {
+            bad = true;
+            break;
+          }
+          if (spins > 16) __nanosleep(64);
+          continue;
+        }
+        u32 val = (lane <= limit) ? ((u32)sv & 0x3fffffffu) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(kFull, val, o);
+        excl += val;
+        if (pmask) break;
+        p -= 32;
+      }
+      if (lane == 0) {
+        if (bad) {
+          atomicOr(&ctl->err, kErrTimeout);
+          s_bad = 1;
+        } else {
+          st_volatile_u64(mine, tag | (2ull << 30) | (excl + tile_tot));
+        }
+        s_excl = excl;
+      }
+    }
   }
   __syncthreads();
-  for (u32 i = tid; i < kRoundDigits * 256; i += blockDim.x) {
-    const u32 c = (&sh[0][0])[i];
-    if (c) atomicAdd(&(&ctl->hist_r[0][0])[i], c);
+  if (s_bad) return;
+  if (tid == 0 && maxv && tile_max) atomicMax(maxv, tile_max);
+  u32 run = s_excl + wpre + x - tot;
+#pragma unroll
+  for (int i = 0; i < kScanIpt; ++i) {
+    if (my0 + i < len) {
+      data[my0 + i] = run;
+      if (copy) copy[my0 + i] = run;
+    }
+    run += v[i];
   }
 }
 
-// bptr[r] = first position of the round-sorted list with R >= r, r = 0..A+1.
-__global__ void __launch_bounds__(256) k_bucket_ptr(const u32* __restrict__ k0,
-                                                    const u32* __restrict__ k1, Control* ctl, u32 n,
-                                                    int* __restrict__ bptr, u32 cap) {
+// ---------------------------------------------------------------- keys and start buckets
+__global__ void __launch_bounds__(256) k_zero_rounds(int* bptr, u32 cap, Control* ctl) {
   if (failed(ctl)) return;
-  const int A = ctl->A;
-  if ((u64)A + 2 > cap) {
+  if ((u64)ctl->A + 2 > cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrBucketCap);
     return;
   }
-  const u32* keys = (__popc(ctl->mask_r) & 1) ? k1 : k0;
+  const u32 len = (u32)ctl->A + 2u;
+  for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < len; r += gridDim.x * blockDim.x)
+    bptr[r] = 0;
+}
+
+// In vertex order: key_u = ((A - a_u) << 32) | rank_u, and the count of every
+// start round R_u among the vertices the BFS handles (into rcnt).
+__global__ void __launch_bounds__(256) k_keys(const int* __restrict__ a,
+                                              const u32* __restrict__ rank,
+                                              const u32* __restrict__ excl, Control* ctl, u32 n,
+                                              u64* __restrict__ key, u32* rcnt) {
+  __shared__ u32 sh[kRBins];
+  if (failed(ctl)) return;
+  const int A = ctl->A;
+  const bool small = (u32)A + 1u <= kRBins;
+  const u32 tid = threadIdx.x, lane = tid & 31;
+  if (small)
+    for (u32 i = tid; i <= (u32)A; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
   const u32 stride = gridDim.x * blockDim.x;
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int R = (int)keys[i];
-    const int prev = (i == 0) ? -1 : (int)keys[i - 1];
-    for (int r = prev + 1; r <= R; ++r) bptr[r] = (int)i;
-    if (i == n - 1)
-      for (int r = R + 1; r <= A + 1; ++r) bptr[r] = (int)n;
+  for (u32 base = blockIdx.x * blockDim.x + (tid & ~31u); base < n; base += stride) {
+    const u32 u = base + lane;
+    bool count = false;
+    u32 R = 0;
+    if (u < n) {
+      R = (u32)(A - a[u]);
+      key[u] = ((u64)R << 32) | rank[u];
+      count = !(excl[u >> 5] >> (u & 31) & 1u);
+    }
+    const u32 act = __ballot_sync(kFull, count);
+    if (act) {
+      const u32 peers = __match_any_sync(kFull, count ? R : 0xffffffffu) & act;
+      if (count && (peers & lanemask_lt()) == 0) {
+        const u32 c = __popc(peers);
+        if (small) atomicAdd(&sh[R], c);
+        else atomicAdd(rcnt + R, c);
+      }
+    }
+  }
+  __syncthreads();
+  if (small)
+    for (u32 i = tid; i <= (u32)A; i += blockDim.x)
+      if (sh[i]) atomicAdd(rcnt + i, sh[i]);
+}
+
+// Start-bucket scatter: bv[pos] = u, rk[pos] = R_u for every vertex the BFS
+// handles.  With few rounds, each CTA counts its chunk in shared memory and
+// reserves its range of every group with one atomic; otherwise one atomic per
+// warp and round.
+__global__ void __launch_bounds__(256) k_rscatter(const int* __restrict__ a,
+                                                  const u32* __restrict__ excl, Control* ctl,
+                                                  u32 n, u32* cursor, u32* __restrict__ bv,
+                                                  u32* __restrict__ rk) {
+  __shared__ u32 s_cnt[kRBins];
+  if (failed(ctl)) return;
+  const int A = ctl->A;
+  const bool small = (u32)A + 1u <= kRBins;
+  const u32 tid = threadIdx.x, lane = tid & 31;
+  const u32 chunk = blockDim.x * kRChunk;
+  for (u32 c0 = blockIdx.x * chunk; c0 < n; c0 += gridDim.x * chunk) {
+    if (small) {
+      for (u32 i = tid; i <= (u32)A; i += blockDim.x) s_cnt[i] = 0;
+      __syncthreads();
+    }
+    u32 R[kRChunk];
+    u32 local[kRChunk];
+#pragma unroll
+    for (int k = 0; k < kRChunk; ++k) {
+      const u32 u = c0 + (u32)k * blockDim.x + tid;
+      bool take = false;
+      R[k] = 0xffffffffu;
+      if (u < n) {
+        take = !(excl[u >> 5] >> (u & 31) & 1u);
+        if (take) R[k] = (u32)(A - a[u]);
+      }
+      local[k] = 0;
+      const u32 act = __ballot_sync(kFull, take);
+      if (act) {
+        const u32 peers = __match_any_sync(kFull, R[k]) & act;
+        const int leader = take ? __ffs(peers) - 1 : (int)lane;
+        u32 got = 0;
+        if (take && (int)lane == leader)
+          got = small ? atomicAdd(&s_cnt[R[k]], (u32)__popc(peers))
+                      : atomicAdd(cursor + R[k], (u32)__popc(peers));
+        got = __shfl_sync(kFull, got, leader);
+        local[k] = got + __popc(peers & lanemask_lt());
+      }
+    }
+    if (small) {
+      __syncthreads();
+      for (u32 i = tid; i <= (u32)A; i += blockDim.x) {
+        const u32 c = s_cnt[i];
+        s_cnt[i] = c ? atomicAdd(cursor + i, c) : 0u;  // this chunk's base in group i
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < kRChunk; ++k) {
+      const u32 u = c0 + (u32)k * blockDim.x + tid;
+      if (R[k] != 0xffffffffu) {
+        const u32 pos = (small ? s_cnt[R[k]] : 0u) + local[k];
+        if (pos < n) {
+          bv[pos] = u;
+          rk[pos] = R[k];
+        }
+      }
+    }
+    if (small) __syncthreads();
   }
 }
 
@@ -425,78 +665,75 @@ u32 grid_stride_blocks(u32 n, int num_sms) {
   return (u32)max(1ll, min((long long)(n + 255) / 256, (long long)num_sms * 8));
 }
 
-// Shared memory of a onesweep pass beyond the default 48 KiB (64-bit keys):
-// set once per device.
-template <typename KeyT>
 void allow_sort_smem() {
   static bool done[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
   if (!done[dev]) {
-    cudaFuncSetAttribute(k_onesweep<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SortSmem<KeyT>));
+    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SortSmem));
     done[dev] = true;
   }
 }
 
-template <typename KeyT>
-int launch_sort_passes(KeyT* k0, u32* v0, KeyT* k1, u32* v1, u32 n, int first_tile_ctr,
-                       const u32* hist, u32* off, u32* mask, int ndig, u64* status, u32* epoch,
-                       Control* ctl, cudaStream_t s) {
-  allow_sort_smem<KeyT>();
-  const u32 ntiles = (n + kSortTile - 1) / kSortTile;
-  int launches = 0;
-  k_scan_digits<<<1, 256, 0, s>>>(hist, off, mask, ndig, n);
-  ++launches;
-  for (int d = 0; d < ndig; ++d) {
-    const u32 ep = ++(*epoch);
-    k_onesweep<KeyT><<<ntiles, kSortThreads, sizeof(SortSmem<KeyT>), s>>>(k0, v0, k1, v1, n, d, 8 * d, mask,
-                                                     off + 256 * d, status,
-                                                     &ctl->tile_ctr[first_tile_ctr + d], ep,
-                                                     &ctl->err);
-    ++launches;
-  }
-  return launches;
-}
-
 }  // namespace
 
-int launch_rank_and_buckets(const double* d_shift, u32 n, int* d_a, u64* k0, u32* v0, u64* k1,
-                            u32* v1, u64* status, u32* epoch, u32* order, u64* key, int* bptr,
-                            u32 bptr_cap, const u32* excl, bool exact64, Control* ctl,
-                            int num_sms, cudaStream_t s) {
-  const u32 gs = grid_stride_blocks(n, num_sms);
-  int launches = 0;
-  u32* k0w = reinterpret_cast<u32*>(k0);
-  u32* k1w = reinterpret_cast<u32*>(k1);
-  if (!exact64) {
-    k_split<u32><<<gs, 256, 0, s>>>(d_shift, n, d_a, k0w, v0, ctl);
-    ++launches;
-    launches += launch_sort_passes<u32>(k0w, v0, k1w, v1, n, 0, &ctl->hist_f[0][0],
-                                        &ctl->off_f[0][0], &ctl->mask_f, 4, status, epoch, ctl, s);
-    k_fixup_runs<<<gs, 256, 0, s>>>(k0w, v0, k1w, v1, d_shift, ctl, n);
-    ++launches;
-  } else {
-    k_split<u64><<<gs, 256, 0, s>>>(d_shift, n, d_a, k0, v0, ctl);
-    ++launches;
-    launches += launch_sort_passes<u64>(k0, v0, k1, v1, n, 0, &ctl->hist_f[0][0],
-                                        &ctl->off_f[0][0], &ctl->mask_f, kFracDigits, status,
-                                        epoch, ctl, s);
-  }
-  k_rank_keys<<<gs, 256, 0, s>>>(v0, v1, d_a, excl, ctl, n, order, key, k0w, v0);
-  ++launches;
-  launches += launch_sort_passes<u32>(k0w, v0, k1w, v1, n, kFracDigits, &ctl->hist_r[0][0],
-                                      &ctl->off_r[0][0], &ctl->mask_r, kRoundDigits, status,
-                                      epoch, ctl, s);
-  launches += launch_bucket_ptr(k0, k1, ctl, n, bptr, bptr_cap, num_sms, s);
-  return launches;
+u32 fraction_bucket_bits(u32 n) {
+  u32 b = 1;
+  while (b < 26 && (1ull << (b + 4)) < n) ++b;  // about 16 vertices per bucket
+  return b;
 }
 
-int launch_bucket_ptr(const u64* k0, const u64* k1, Control* ctl, u32 n, int* bptr, u32 cap,
-                      int num_sms, cudaStream_t s) {
-  k_bucket_ptr<<<grid_stride_blocks(n, num_sms), 256, 0, s>>>(
-      reinterpret_cast<const u32*>(k0), reinterpret_cast<const u32*>(k1), ctl, n, bptr, cap);
-  return 1;
+int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
+  const u32 n = r.n;
+  Control* ctl = r.ctl;
+  const u32 gs = grid_stride_blocks(n, r.num_sms);
+  int launches = 0;
+  const u32 B = fraction_bucket_bits(n), nbkt = 1u << B;
+  u32* k1w = reinterpret_cast<u32*>(r.k1);  // 2 max(n, 64) 32-bit words
+  u32* rank = k1w + max(n, nbkt);           // after the bucket counters
+  if (!exact64) {
+    u32* cnt = k1w;  // [nbkt <= n]: counts, then bucket starts, then bucket ends
+    cudaMemsetAsync(cnt, 0, (size_t)nbkt * 4, s);
+    k_bsplit<<<gs, 256, 0, s>>>(r.shift, n, (int)B, r.a, cnt, ctl);
+    const u32 ntile = (nbkt + kScanTile - 1) / kScanTile;
+    k_scan_excl<<<ntile, kScanThreads, 0, s>>>(cnt, nullptr, nbkt, 0, r.status, ++(*r.epoch),
+                                                &ctl->tile_ctr[0], &ctl->maxbucket, ctl);
+    // records of 16 bytes: k0 and v0/v1 are not needed until the start buckets
+    ulonglong2* tmp = reinterpret_cast<ulonglong2*>(r.tmp16);
+    k_bscatter<<<gs, 256, 0, s>>>(r.shift, (int)B, cnt, n, tmp, ctl);
+    k_bsort<<<(u32)min((long long)(nbkt + 15) / 16, (long long)r.num_sms * 16), 256, 0, s>>>(
+        cnt, nbkt, tmp, n, r.order, rank, ctl);
+    launches += 4;
+  } else {
+    allow_sort_smem();
+    k_split64<<<gs, 256, 0, s>>>(r.shift, n, r.a, r.k0, r.v0, ctl);
+    k_scan_digits<<<1, 256, 0, s>>>(&ctl->hist_f[0][0], &ctl->off_f[0][0], &ctl->mask_f,
+                                    kFracDigits, n);
+    launches += 2;
+    const u32 ntiles = (n + kSortTile - 1) / kSortTile;
+    for (int d = 0; d < kFracDigits; ++d) {
+      k_onesweep<<<ntiles, kSortThreads, sizeof(SortSmem), s>>>(
+          r.k0, r.v0, r.k1, r.v1, n, d, 8 * d, &ctl->mask_f, ctl->off_f[d], r.status,
+          &ctl->tile_ctr[2 + d], ++(*r.epoch), &ctl->err);
+      ++launches;
+    }
+    k_rank_scatter<<<gs, 256, 0, s>>>(r.v0, r.v1, ctl, n, r.order, rank);
+    ++launches;
+  }
+  // keys and the start-round counting sort (groups in any order inside)
+  const u32 rtiles = (r.bptr_cap + kScanTile - 1) / kScanTile;
+  k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
+                                                                            ctl);
+  k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, reinterpret_cast<u32*>(r.bptr));
+  k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(reinterpret_cast<u32*>(r.bptr), r.rcur, 0, 1,
+                                               r.status, ++(*r.epoch), &ctl->tile_ctr[1], nullptr,
+                                               ctl);
+  k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
+                        (long long)r.num_sms * 8),
+               256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));
+  launches += 4;
+  return launches;
 }
 
 }  // namespace ldd

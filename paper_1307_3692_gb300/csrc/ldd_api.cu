@@ -123,10 +123,12 @@ struct ldd_graph {
   u32* d_qoff[2] = {nullptr, nullptr};
   u32* d_cf[2] = {nullptr, nullptr};
   u32* d_ulist[2] = {nullptr, nullptr};
+  void* d_tmp16 = nullptr;
   int* d_center = nullptr;
   int* d_dist = nullptr;
   Control* d_ctl = nullptr;
   int* d_bptr = nullptr;
+  u32* d_rcur = nullptr;
   u32 bptr_cap = 0;
   size_t status_bytes = 0;
   u32 epoch = 0;
@@ -156,6 +158,7 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->sc.adj);
   cudaFree(g->arena);
   cudaFree(g->d_bptr);
+  cudaFree(g->d_rcur);
   if (g->h_hdr) cudaFreeHost(g->h_hdr);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
@@ -186,7 +189,8 @@ int validate_csr(int32_t n, int64_t nnz, const int32_t* rp, const int32_t* col) 
 
 int alloc_scratch(ldd_graph* g) {
   const size_t n = (size_t)g->n;
-  const size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const size_t nk = std::max<size_t>(n, 64);  // 64-bit words per key buffer
+  const size_t ntiles = (n + kSortTile - 1) / kSortTile + 1;
   const size_t ncf = (size_t)g->nnz / kBfsBase + 2;
   g->status_bytes = ntiles * 256 * sizeof(u64);
   struct Part {
@@ -194,7 +198,7 @@ int alloc_scratch(ldd_graph* g) {
     size_t bytes;
   } parts[] = {
       {(void**)&g->d_shift, 8 * n},       {(void**)&g->d_a, 4 * n},
-      {(void**)&g->d_k[0], 8 * n},        {(void**)&g->d_k[1], 8 * n},
+      {(void**)&g->d_k[0], 8 * nk},       {(void**)&g->d_k[1], 8 * nk},
       {(void**)&g->d_v[0], 4 * n},        {(void**)&g->d_v[1], 4 * n},
       {(void**)&g->d_status, g->status_bytes},
       {(void**)&g->d_order, 4 * n},       {(void**)&g->d_key, 8 * n},
@@ -203,6 +207,7 @@ int alloc_scratch(ldd_graph* g) {
       {(void**)&g->d_qoff[0], 4 * n},     {(void**)&g->d_qoff[1], 4 * n},
       {(void**)&g->d_cf[0], 4 * ncf},     {(void**)&g->d_cf[1], 4 * ncf},
       {(void**)&g->d_ulist[0], 4 * n},    {(void**)&g->d_ulist[1], 4 * n},
+      {(void**)&g->d_tmp16, 16 * n},
       {(void**)&g->d_center, 4 * n},      {(void**)&g->d_dist, 4 * n},
       {(void**)&g->d_ctl, sizeof(Control)},
   };
@@ -219,7 +224,8 @@ int alloc_scratch(ldd_graph* g) {
   }
   CUDA_TRY(cudaMemset(g->d_status, 0, g->status_bytes));
   g->bptr_cap = (u32)std::min<size_t>(n + 2, 0xffffffffu);
-  if (cudaMalloc(&g->d_bptr, (size_t)g->bptr_cap * sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&g->d_bptr, (size_t)g->bptr_cap * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&g->d_rcur, (size_t)g->bptr_cap * sizeof(u32)) != cudaSuccess) {
     cudaGetLastError();
     return fail(LDD_ERR_OOM, "cudaMalloc of the start-bucket table failed");
   }
@@ -303,10 +309,8 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.col = g->d_col;
   a.key = g->d_key;
   a.bptr = g->d_bptr;
-  a.rk[0] = reinterpret_cast<const u32*>(g->d_k[0]);  // round keys are 32-bit
-  a.rk[1] = reinterpret_cast<const u32*>(g->d_k[1]);
-  a.rv[0] = g->d_v[0];
-  a.rv[1] = g->d_v[1];
+  a.rk[0] = a.rk[1] = reinterpret_cast<const u32*>(g->d_k[0]);  // start rounds, 32-bit
+  a.rv[0] = a.rv[1] = g->d_v[0];                                 // start-bucket vertices
   for (int b = 0; b < 2; ++b) {
     a.qv[b] = g->d_qv[b];
     a.qrow[b] = g->d_qrow[b];
@@ -509,8 +513,8 @@ int ldd_get_round_profile(const ldd_graph* g, int64_t* clocks, int32_t* kinds, i
                                            cap);
   *out_count = count;
   if (count <= 0) return LDD_OK;
-  CUDA_TRY(cudaMemcpyAsync(clocks, g->d_ctl->round_clk, (size_t)count * 8, cudaMemcpyDeviceToHost,
-                           g->stream));
+  CUDA_TRY(cudaMemcpyAsync(clocks, g->d_ctl->round_clk, (size_t)count * 3 * 8,
+                           cudaMemcpyDeviceToHost, g->stream));
   CUDA_TRY(cudaMemcpyAsync(kinds, g->d_ctl->round_kind, (size_t)count * 4, cudaMemcpyDeviceToHost,
                            g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -558,16 +562,33 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
     d_shift = g->d_shift;
   }
   record(g, 1);
+  RankBufs rb;
+  rb.shift = d_shift;
+  rb.n = (u32)n;
+  rb.num_sms = g->num_sms;
+  rb.a = g->d_a;
+  rb.k0 = g->d_k[0];
+  rb.k1 = g->d_k[1];
+  rb.v0 = g->d_v[0];
+  rb.v1 = g->d_v[1];
+  rb.tmp16 = g->d_tmp16;
+  rb.status = g->d_status;
+  rb.epoch = &g->epoch;
+  rb.order = g->d_order;
+  rb.key = g->d_key;
+  rb.excl = g->d_excl;
+  rb.ctl = g->d_ctl;
   Header h;
   int status = LDD_OK;
-  for (int exact64 = 0; exact64 < 2; ++exact64) {
-    if (exact64) CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
-    launches += launch_rank_and_buckets(d_shift, (u32)n, g->d_a, g->d_k[0], g->d_v[0], g->d_k[1],
-                                        g->d_v[1], g->d_status, &g->epoch, g->d_order, g->d_key,
-                                        g->d_bptr, g->bptr_cap, g->d_excl, exact64 != 0, g->d_ctl,
-                                        g->num_sms, s);
+  bool exact64 = false;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (attempt) CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
+    rb.bptr = g->d_bptr;
+    rb.rcur = g->d_rcur;
+    rb.bptr_cap = g->bptr_cap;
+    launches += launch_rank_and_buckets(rb, exact64, s);
     record(g, 2);
-    int l = run_bfs_finalize(g, center, dist, &status);
+    const int l = run_bfs_finalize(g, center, dist, &status);
     if (l < 0) return status;
     launches += l;
     record(g, 4);
@@ -575,34 +596,29 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&h, g->h_hdr, sizeof(h));
-    // A long run of equal 32-bit fraction codes with different fractions:
-    // everything after the fix-up was skipped; redo it with the exact key.
-    if (h.err != kErrRankRetry) break;
-  }
-
-  if (h.err == kErrBucketCap) {
-    // floor(delta_max) exceeds n: grow the start-bucket table and rerun the
-    // bucket pointers, the BFS and the assignment (keys and sorts are intact).
-    const size_t need = (size_t)h.A + 2;
-    cudaFree(g->d_bptr);
-    g->d_bptr = nullptr;
-    g->bptr_cap = 0;
-    if (cudaMalloc(&g->d_bptr, need * sizeof(int)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(LDD_ERR_OOM, "start-bucket table of %zu entries", need);
+    if (h.err == kErrRankRetry) {
+      // A fraction bucket too large to rank in place (crafted shifts): every
+      // kernel after the bucket scan was skipped; redo with the exact path.
+      exact64 = true;
+      continue;
     }
-    g->bptr_cap = (u32)need;
-    CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(u32), s));
-    CUDA_TRY(cudaMemsetAsync((char*)g->d_ctl + kCtlBfsStateOffset, 0, kCtlBfsStateBytes, s));
-    launches += launch_bucket_ptr(g->d_k[0], g->d_k[1], g->d_ctl, (u32)n, g->d_bptr,
-                                  g->bptr_cap, g->num_sms, s);
-    const int l = run_bfs_finalize(g, center, dist, &status);
-    if (l < 0) return status;
-    launches += l;
-    record(g, 4);
-    CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    memcpy(&h, g->h_hdr, sizeof(h));
+    if (h.err == kErrBucketCap) {
+      // floor(delta_max) + 2 exceeds the start-bucket table: grow it, redo.
+      const size_t need = (size_t)h.A + 2;
+      cudaFree(g->d_bptr);
+      cudaFree(g->d_rcur);
+      g->d_bptr = nullptr;
+      g->d_rcur = nullptr;
+      g->bptr_cap = 0;
+      if (cudaMalloc(&g->d_bptr, need * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&g->d_rcur, need * sizeof(u32)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LDD_ERR_OOM, "start-bucket table of %zu entries", need);
+      }
+      g->bptr_cap = (u32)need;
+      continue;
+    }
+    break;
   }
   if (h.err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
   if (h.err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");

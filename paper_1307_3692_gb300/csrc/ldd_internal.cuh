@@ -72,16 +72,18 @@ struct Control {
   u32 ucnt[3];     // lengths of the still-unsettled lists of bottom-up rounds
   u32 pad0;
   // sort state
-  u32 mask_f;  // bit d: fraction digit pass d is needed
-  u32 mask_r;  // bit d: round digit pass d is needed
+  u32 mask_f;     // bit d: fraction digit pass d is needed (exact path)
+  u32 mask_r;     // unused (start buckets are a counting sort)
+  u32 maxbucket;  // largest fraction bucket (fast path)
   u32 tile_ctr[kFracDigits + kRoundDigits];
   u32 hist_f[kFracDigits][256];
   u32 off_f[kFracDigits][256];
   u32 hist_r[kRoundDigits][256];
   u32 off_r[kRoundDigits][256];
-  // round profile of the last BFS: SM clock of CTA 0 at the end of each round
-  // (entry 0: after the level-0 starts) and the round's kind
-  long long round_clk[kRoundProfile];
+  // round profile of the last BFS, SM clock of CTA 0: for round i, [i][0] after
+  // its expansion, [i][1] after its start-bucket scan, [i][2] when its
+  // barrier let CTA 0 go (entry 0: the level-0 starts); and the round's kind
+  long long round_clk[kRoundProfile][3];
   int round_kind[kRoundProfile];
 };
 constexpr size_t kCtlHeaderBytes = 40;       // err .. cut
@@ -138,16 +140,32 @@ struct CompScratch {
 
 // ---------------------------------------------------------------- launchers
 // Fraction rank and start buckets (k_rank.cu).  Returns kernels launched.
-// Vertices with bit v of excl set get the start round A + 1 in the bucket sort,
-// i.e. they stay out of the BFS start buckets 0..A.  exact64 = false: 32-bit
-// fraction codes plus run fix-up (may set kErrRankRetry); true: 64-bit
-// fraction bits.  The key buffers hold 8n bytes each.
-int launch_rank_and_buckets(const double* d_shift, u32 n, int* d_a, u64* k0, u32* v0, u64* k1,
-                            u32* v1, u64* status, u32* epoch, u32* order, u64* key, int* bptr,
-                            u32 bptr_cap, const u32* excl, bool exact64, Control* ctl,
-                            int num_sms, cudaStream_t s);
-int launch_bucket_ptr(const u64* k0, const u64* k1, Control* ctl, u32 n, int* bptr, u32 cap,
-                      int num_sms, cudaStream_t s);
+// Buffers of the fraction rank and the start buckets (k_rank.cu).
+struct RankBufs {
+  const double* shift;  // [n] shifts on the device
+  u32 n;
+  int num_sms;
+  int* a;               // [n] floor(shift)
+  u64* k0;              // [max(n, 64)] 64-bit words each: keys / scratch
+  u64* k1;
+  u32* v0;              // [n] values / scratch; ends as the start-bucket vertices
+  u32* v1;
+  void* tmp16;          // [n] 16-byte records (fraction bucket scatter)
+  u64* status;          // look-back status words (epoch-tagged)
+  u32* epoch;
+  u32* order;           // [n] rank -> vertex
+  u64* key;             // [n] start keys
+  int* bptr;            // [bptr_cap] start-bucket offsets (rounds 0 .. A + 1)
+  u32* rcur;            // [bptr_cap] scatter cursors
+  u32 bptr_cap;
+  const u32* excl;      // bit v: v is not handled by the BFS (no start bucket)
+  Control* ctl;
+};
+// exact64 = false: fraction buckets + in-bucket exact ranks (may set
+// kErrRankRetry); true: exact 64-bit LSD radix sort.  The start buckets end in
+// v0 (vertices) and k0 viewed as 32-bit words (their rounds).
+int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s);
+u32 fraction_bucket_bits(u32 n);
 // Persistent BFS (k_bfs.cu).  Returns kernels launched, or -1 with the CUDA
 // error left in *err.
 int bfs_grid_size(int num_sms, int* blocks_per_sm);
