@@ -182,11 +182,11 @@ def bfs_algorithmic_bytes(st, n):
 
 
 def kernel_source_sha():
+    """Hash of the BFS kernel's sources (its file and the shared header)."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1307_3692_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(src, f), "rb").read())
+    for f in ("k_bfs.cu", "ldd_internal.cuh"):
+        h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -398,7 +398,8 @@ def our_arm(args):
                           "rounds": st["rounds"], "pull_rounds": st["pull_rounds"],
                           "A": st["max_floor_shift"], "items": st["items"],
                           "push_arcs": st["push_arcs"], "pull_arcs": st["pull_arcs"],
-                          "pull_vertices": st["pull_vertices"], "gteps": m / st["ms_total"] / 1e6}
+                          "pull_vertices": st["pull_vertices"], "exact_rank": st["exact_rank"],
+                          "gteps": m / st["ms_total"] / 1e6}
                          for b, st in zip(betas, per_beta[-len(betas):])],
             "phase_share": phases,
             "wall_s_timed_region": t_wall,

@@ -161,6 +161,8 @@ typedef struct {
   int64_t pull_vertices;  /* vertices examined in bottom-up rounds */
   int64_t launches;       /* kernels launched by the last ldd_decompose */
   int64_t cut_launches;   /* kernels launched by the last ldd_cut_edges */
+  int64_t exact_rank;     /* 1 if the fraction rank needed the exact radix-sort
+                             path (a fraction bucket overflowed), else 0 */
   int32_t bfs_grid;       /* CTAs of the persistent BFS kernel */
   int32_t bfs_block;      /* threads per CTA */
   float ms_h2d;           /* shifts host -> device (0 if already on device) */

@@ -44,7 +44,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "n", "nnz", "n_active", "small_components", "max_floor_shift", "rounds", "last_level", "items", "edges", "pull_rounds", "push_arcs", "pull_arcs",
         "pull_vertices",
-        "launches", "cut_launches")] + [("bfs_grid", ctypes.c_int32), ("bfs_block", ctypes.c_int32)] + [
+        "launches", "cut_launches", "exact_rank")] + [("bfs_grid", ctypes.c_int32), ("bfs_block", ctypes.c_int32)] + [
         (name, ctypes.c_float) for name in (
             "ms_h2d", "ms_rank", "ms_bfs", "ms_finalize", "ms_d2h", "ms_total", "ms_cut")]
 

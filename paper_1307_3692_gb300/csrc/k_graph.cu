@@ -34,12 +34,18 @@ namespace {
 constexpr u32 kFull = 0xffffffffu;
 
 __global__ void __launch_bounds__(256) k_finalize(const u64* __restrict__ key,
-                                                  const u32* __restrict__ order, u32 n,
+                                                  const u32* __restrict__ order,
+                                                  const u32* __restrict__ solo, u32 n,
                                                   int* __restrict__ center, int* __restrict__ dist,
                                                   const u32* err) {
   if (*(volatile const u32*)err != 0u) return;  // outputs are not written after a failure
   const u32 stride = gridDim.x * blockDim.x;
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    if ((__ldg(solo + (v >> 5)) >> (v & 31)) & 1u) {  // alone in its component: key unused
+      center[v] = (int)v;
+      dist[v] = 0;
+      continue;
+    }
     const u64 k = key[v];
     const u32 c = order[min((u32)k, n - 1)];
     const u64 kc = key[c];
@@ -168,7 +174,7 @@ __global__ void k_small_roots(const u32* __restrict__ parent, const u32* __restr
 __global__ void k_small_members(const int* __restrict__ row_ptr, const u32* __restrict__ parent,
                                 const u32* __restrict__ csize, const u32* __restrict__ root_off,
                                 u32 n, u32* fill, u32* comp_v, u32* lane_of, u32* excl,
-                                u32* counters) {
+                                u32* solo, u32* counters) {
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const u32 r = parent[v];
     const u32 sz = csize[r];
@@ -179,6 +185,7 @@ __global__ void k_small_members(const int* __restrict__ row_ptr, const u32* __re
       comp_v[root_off[r] + pos] = v;
       lane_of[v] = pos;
     }
+    if (sz == 1) atomicOr(solo + (v >> 5), 1u << (v & 31));
     if (small || no_arcs) {
       atomicOr(excl + (v >> 5), 1u << (v & 31));
     } else {
@@ -240,9 +247,9 @@ u32 grid_for(u32 n, int num_sms) {
 
 }  // namespace
 
-int launch_finalize(const u64* key, const u32* order, u32 n, int* center, int* dist,
-                    const u32* err, int num_sms, cudaStream_t s) {
-  k_finalize<<<grid_for(n, num_sms), 256, 0, s>>>(key, order, n, center, dist, err);
+int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, int* center,
+                    int* dist, const u32* err, int num_sms, cudaStream_t s) {
+  k_finalize<<<grid_for(n, num_sms), 256, 0, s>>>(key, order, solo, n, center, dist, err);
   return 1;
 }
 
@@ -263,7 +270,8 @@ int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sm
 }
 
 cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 n, int num_sms,
-                              const CompScratch& t, u32* excl, u32 counts[4], cudaStream_t s) {
+                              const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
+                              cudaStream_t s) {
   const u32 g = grid_for(n, num_sms);
   cudaError_t e;
   if ((e = cudaMemsetAsync(t.csize, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
@@ -271,13 +279,14 @@ cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 
   if ((e = cudaMemsetAsync(t.counters, 0, 4 * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(t.lane_of, 0xff, (size_t)n * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(excl, 0, ((size_t)n + 31) / 32 * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(solo, 0, ((size_t)n + 31) / 32 * 4, s)) != cudaSuccess) return e;
   k_iota<<<g, 256, 0, s>>>(t.parent, n);
   if (m_up > 0) k_cc_hook<<<grid_for(m_up, num_sms), 256, 0, s>>>(up, m_up, t.parent);
   k_cc_finish<<<g, 256, 0, s>>>(t.parent, t.csize, n);
   k_small_roots<<<g, 256, 0, s>>>(t.parent, t.csize, n, t.root_off, t.comp_off, t.comp_len,
                                   t.counters);
   k_small_members<<<g, 256, 0, s>>>(row_ptr, t.parent, t.csize, t.root_off, n, t.fill, t.comp_v,
-                                    t.lane_of, excl, t.counters);
+                                    t.lane_of, excl, solo, t.counters);
   if ((e = cudaMemcpyAsync(counts, t.counters, 4 * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -14,13 +14,16 @@
 //
 // Fraction rank, fast path (most-significant-digit bucketing): the bucket of u
 // is the top B bits of ~floor(f_u * 2^32), which is monotone in f_u, with
-// 2^B about n / 16 so that buckets hold ~16 vertices.  A global histogram, an
-// exclusive scan, one scatter of (bits of f_u, u) into the buckets, and one
-// warp per bucket that ranks its members exactly by (f descending, u
-// ascending) with the full FP64 fractions.  A bucket larger than kLocalMax
-// (crafted shifts, e.g. all fractions equal) makes the host redo the rank with
-// the exact path: a stable LSD radix sort of the order-preserving bits of f
-// (8 "onesweep" passes of 8 bits).
+// 2^B about n / 16 so that buckets hold ~16 vertices.  One pass over the
+// shifts drops a 16-byte record (bits of f_u, a_u, u) into a free slot of its
+// bucket (kSlotCap slots each); an exclusive scan of the bucket counts gives
+// every bucket's first rank; one warp per bucket then ranks its members
+// exactly by (f descending, u ascending) with the full FP64 fractions and
+// writes order[] and the keys directly.  Vertices alone in their component
+// are not ranked (their center is themselves).  A full bucket (crafted
+// shifts, e.g. all fractions equal) makes the host redo the rank with the
+// exact path: a stable LSD radix sort of the order-preserving bits of f
+// (8 "onesweep" passes of 8 bits) over all vertices.
 //
 // Start buckets: a counting sort by R_u (histogram while the keys are built,
 // an exclusive scan that is bptr, and a scatter in which each CTA reserves its
@@ -33,7 +36,7 @@ namespace {
 
 constexpr u32 kFull = 0xffffffffu;
 constexpr u32 kLookbackSpinLimit = 1u << 24;  // ~1 s of polling, then kErrTimeout
-constexpr u32 kLocalMax = 1024;               // largest fraction bucket ranked in place
+constexpr u32 kSlotCap = 64;                  // record slots per fraction bucket (mean <= 16)
 constexpr int kScanThreads = 256;
 constexpr int kScanIpt = 16;
 constexpr int kScanTile = kScanThreads * kScanIpt;
@@ -57,10 +60,9 @@ __device__ __forceinline__ void hist_add(u32* sh, u32 digit, bool valid, u32 lan
   }
 }
 
-// Exact fraction of a validated shift, with -0 folded into +0; the bits of a
+// Bits of a fraction f in [0, 1), with -0 folded into +0; the bits of a
 // non-negative double order like its value.
-__device__ __forceinline__ u64 frac_bits(double d) {
-  const double f = d - floor(d);
+__device__ __forceinline__ u64 fraction_bits(double f) {
   return f == 0.0 ? 0ull : (u64)__double_as_longlong(f);
 }
 
@@ -101,9 +103,13 @@ __device__ __forceinline__ u32 bucket_of(double f, int B) {
   return (~code) >> (32 - B);                      // larger fraction, smaller bucket
 }
 
-__global__ void __launch_bounds__(256) k_bsplit(const double* __restrict__ delta, u32 n, int B,
+// Pass 1, the only read of the shifts: split and validate every shift, and
+// drop (bits of f_u, a_u, u) into the next free slot of u's bucket unless u
+// is alone in its component.  A full bucket sends the host to the exact path.
+__global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta,
+                                                const u32* __restrict__ solo, u32 n, int B,
                                                 int* __restrict__ a_out, u32* __restrict__ cnt,
-                                                Control* ctl) {
+                                                ulonglong2* __restrict__ slots, Control* ctl) {
   int amax = 0;
   u32 err = 0;
   const u32 stride = gridDim.x * blockDim.x;
@@ -112,96 +118,113 @@ __global__ void __launch_bounds__(256) k_bsplit(const double* __restrict__ delta
     double f;
     split_one(delta[u], err, a, f);
     a_out[u] = a;
-    atomicAdd(cnt + bucket_of(f, B), 1u);
     amax = max(amax, a);
+    if ((__ldg(solo + (u >> 5)) >> (u & 31)) & 1u) continue;
+    const u32 b = bucket_of(f, B);
+    const u32 pos = atomicAdd(cnt + b, 1u);
+    if (pos < kSlotCap)
+      slots[(size_t)b * kSlotCap + pos] =
+          make_ulonglong2(fraction_bits(f), ((u64)(u32)a << 32) | u);
+    else
+      err |= kErrRankRetry;
   }
   finish_split(err, amax, ctl);
 }
 
-// Scatter (bits of f_u, u) records into the buckets (cur[] holds the bucket
-// starts and ends up holding the bucket ends).  A bucket too large to rank in
-// place sends the host to the exact path instead.
-__global__ void __launch_bounds__(256) k_bscatter(const double* __restrict__ delta, int B,
-                                                  u32* cur, u32 n, ulonglong2* __restrict__ tmp,
-                                                  Control* ctl) {
-  if (failed(ctl)) return;
-  if (*(volatile const u32*)&ctl->maxbucket > kLocalMax) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrRankRetry);
-    return;
-  }
-  const u32 stride = gridDim.x * blockDim.x;
-  for (u32 u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
-    const double d = delta[u];
-    const double f = d - floor(d);  // validated by k_bsplit
-    const u32 pos = atomicAdd(cur + bucket_of(f, B), 1u);
-    if (pos < n) tmp[pos] = make_ulonglong2(frac_bits(d), u);
+// Adds one to the count of start round R for every lane with take set, one
+// atomic per distinct R in the warp (shared memory when A + 1 <= kRBins).
+__device__ __forceinline__ void count_round(u32 R, bool take, bool small, u32* sh, u32* rcnt) {
+  const u32 act = __ballot_sync(kFull, take);
+  if (!act) return;
+  const u32 peers = __match_any_sync(kFull, take ? R : 0xffffffffu) & act;
+  if (take && (peers & lanemask_lt()) == 0) {
+    if (small) atomicAdd(&sh[R], (u32)__popc(peers));
+    else atomicAdd(rcnt + R, (u32)__popc(peers));
   }
 }
 
-// Ranks bucket [s, s + len) of the records (len <= 32): each member's exact
-// position is the number of members before it in (f descending, id ascending).
-__device__ __forceinline__ void rank_small(const ulonglong2 rec, u32 s, u32 len, u32 lane,
-                                           u32* __restrict__ order, u32* __restrict__ rank) {
-  u32 r = 0;
-  for (u32 j = 0; j < len; ++j) {
-    const u64 fj = __shfl_sync(kFull, rec.x, j);
-    const u32 uj = (u32)__shfl_sync(kFull, rec.y, j);
-    r += (fj > rec.x || (fj == rec.x && uj < (u32)rec.y)) ? 1u : 0u;
+// Writes what rank p of record rec gives: order[p] = u and u's start key
+// ((A - a_u) << 32) | p; counts u under its start round if the BFS handles u.
+// Called by the whole warp.
+__device__ __forceinline__ void emit_rank(bool valid, const ulonglong2 rec, u32 p, u32 n, int A,
+                                          const u32* __restrict__ excl, bool small, u32* sh,
+                                          u32* rcnt, u32* __restrict__ order,
+                                          u64* __restrict__ key) {
+  const u32 u = (u32)rec.y;
+  const u32 R = (u32)(A - (int)(u32)(rec.y >> 32));
+  bool take = false;
+  if (valid && p < n && u < n) {
+    order[p] = u;
+    key[u] = ((u64)R << 32) | p;
+    take = !((__ldg(excl + (u >> 5)) >> (u & 31)) & 1u);
   }
-  if (lane < len) {
-    order[s + r] = (u32)rec.y;
-    rank[(u32)rec.y] = s + r;
-  }
+  count_round(R, take, small, sh, rcnt);
 }
 
-// One warp per bucket [end[b-1], end[b]), two buckets per step for more loads
-// in flight; buckets of more than 32 members are ranked by counting against
-// all members.
-__global__ void __launch_bounds__(256) k_bsort(const u32* __restrict__ end, u32 nbkt,
-                                               const ulonglong2* __restrict__ tmp, u32 n,
-                                               u32* __restrict__ order, u32* __restrict__ rank,
-                                               Control* ctl) {
+// Pass 2: one warp per bucket b, whose len = start[b + 1] - start[b] members
+// sit in slots [b * kSlotCap, b * kSlotCap + len).  A member's rank is
+// start[b] + the number of members before it in (f descending, id
+// ascending).  Two buckets per warp and step, for more loads in flight.
+__global__ void __launch_bounds__(256) k_bsort(const u32* __restrict__ start, u32 nbkt,
+                                               const ulonglong2* __restrict__ slots,
+                                               const u32* __restrict__ excl, u32 n,
+                                               u32* __restrict__ order, u64* __restrict__ key,
+                                               u32* rcnt, Control* ctl) {
+  __shared__ u32 sh[kRBins];
   if (failed(ctl)) return;
-  const u32 lane = threadIdx.x & 31;
+  const int A = ctl->A;
+  const bool small = (u32)A + 1u <= kRBins;
+  const u32 tid = threadIdx.x, lane = tid & 31;
+  if (small)
+    for (u32 i = tid; i <= (u32)A; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
   const u32 warps = gridDim.x * (blockDim.x / 32);
-  for (u32 b0 = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); b0 < nbkt; b0 += 2 * warps) {
-    const u32 b1 = b0 + warps;
-    u32 s[2], e[2];
-    s[0] = b0 ? end[b0 - 1] : 0u;
-    e[0] = end[b0];
-    s[1] = 0;
-    e[1] = 0;
-    if (b1 < nbkt) {
-      s[1] = end[b1 - 1];
-      e[1] = end[b1];
-    }
+  for (u32 b0 = blockIdx.x * (blockDim.x / 32) + (tid >> 5); b0 < nbkt; b0 += 2 * warps) {
+    u32 s[2], len[2];
     ulonglong2 rec[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      rec[k] = make_ulonglong2(0ull, 0ull);
-      if (e[k] > s[k] && e[k] <= n && e[k] - s[k] <= 32 && lane < e[k] - s[k])
-        rec[k] = tmp[s[k] + lane];
+      const u32 b = b0 + (u32)k * warps;
+      s[k] = 0;
+      len[k] = 0;
+      if (b < nbkt) {
+        s[k] = start[b];
+        const u32 e = start[b + 1];
+        if (e > s[k] && e - s[k] <= kSlotCap) len[k] = e - s[k];
+      }
+      rec[k] = (lane < len[k]) ? slots[(size_t)b * kSlotCap + lane] : make_ulonglong2(0ull, 0ull);
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      if (e[k] <= s[k] || e[k] > n) continue;
-      const u32 len = e[k] - s[k];
-      if (len <= 32) {
-        rank_small(rec[k], s[k], len, lane, order, rank);
+      if (len[k] == 0) continue;
+      const ulonglong2* bs = slots + (size_t)(b0 + (u32)k * warps) * kSlotCap;
+      if (len[k] <= 32) {
+        u32 r = 0;
+        for (u32 j = 0; j < len[k]; ++j) {
+          const u64 fj = __shfl_sync(kFull, rec[k].x, j);
+          const u32 uj = (u32)__shfl_sync(kFull, rec[k].y, j);
+          r += (fj > rec[k].x || (fj == rec[k].x && uj < (u32)rec[k].y)) ? 1u : 0u;
+        }
+        emit_rank(lane < len[k], rec[k], s[k] + r, n, A, excl, small, sh, rcnt, order, key);
       } else {
-        for (u32 i = lane; i < len; i += 32) {
-          const ulonglong2 me = tmp[s[k] + i];
+        for (u32 i0 = 0; i0 < len[k]; i0 += 32) {
+          const u32 i = i0 + lane;
+          const bool valid = i < len[k];
+          const ulonglong2 me = valid ? bs[i] : make_ulonglong2(0ull, 0ull);
           u32 r = 0;
-          for (u32 j = 0; j < len; ++j) {
-            const ulonglong2 o = tmp[s[k] + j];
+          for (u32 j = 0; j < len[k]; ++j) {
+            const ulonglong2 o = bs[j];
             r += (o.x > me.x || (o.x == me.x && (u32)o.y < (u32)me.y)) ? 1u : 0u;
           }
-          order[s[k] + r] = (u32)me.y;
-          rank[(u32)me.y] = s[k] + r;
+          emit_rank(valid, me, s[k] + r, n, A, excl, small, sh, rcnt, order, key);
         }
       }
     }
   }
+  __syncthreads();
+  if (small)
+    for (u32 i = tid; i <= (u32)A; i += blockDim.x)
+      if (sh[i]) atomicAdd(rcnt + i, sh[i]);
 }
 
 // ---------------------------------------------------------------- exact path
@@ -223,7 +246,7 @@ __global__ void __launch_bounds__(256) k_split64(const double* __restrict__ delt
       int a;
       double f;
       split_one(delta[idx], err, a, f);
-      key = ~(f == 0.0 ? 0ull : (u64)__double_as_longlong(f));  // ascending key: f descending
+      key = ~fraction_bits(f);  // ascending key: f descending
       a_out[idx] = a;
       kout[idx] = key;
       vout[idx] = idx;
@@ -684,28 +707,32 @@ u32 fraction_bucket_bits(u32 n) {
   return b;
 }
 
+size_t fraction_slot_bytes(u32 n) {
+  return ((size_t)1 << fraction_bucket_bits(n)) * kSlotCap * sizeof(ulonglong2);
+}
+
 int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
   const u32 n = r.n;
   Control* ctl = r.ctl;
   const u32 gs = grid_stride_blocks(n, r.num_sms);
   int launches = 0;
-  const u32 B = fraction_bucket_bits(n), nbkt = 1u << B;
-  u32* k1w = reinterpret_cast<u32*>(r.k1);  // 2 max(n, 64) 32-bit words
-  u32* rank = k1w + max(n, nbkt);           // after the bucket counters
+  const u32 rtiles = (r.bptr_cap + kScanTile - 1) / kScanTile;
+  u32* rcnt = reinterpret_cast<u32*>(r.bptr);
   if (!exact64) {
-    u32* cnt = k1w;  // [nbkt <= n]: counts, then bucket starts, then bucket ends
-    cudaMemsetAsync(cnt, 0, (size_t)nbkt * 4, s);
-    k_bsplit<<<gs, 256, 0, s>>>(r.shift, n, (int)B, r.a, cnt, ctl);
-    const u32 ntile = (nbkt + kScanTile - 1) / kScanTile;
-    k_scan_excl<<<ntile, kScanThreads, 0, s>>>(cnt, nullptr, nbkt, 0, r.status, ++(*r.epoch),
-                                                &ctl->tile_ctr[0], &ctl->maxbucket, ctl);
-    // records of 16 bytes: k0 and v0/v1 are not needed until the start buckets
-    ulonglong2* tmp = reinterpret_cast<ulonglong2*>(r.tmp16);
-    k_bscatter<<<gs, 256, 0, s>>>(r.shift, (int)B, cnt, n, tmp, ctl);
+    const u32 B = fraction_bucket_bits(n), nbkt = 1u << B;
+    u32* cnt = reinterpret_cast<u32*>(r.k1);  // [nbkt + 1] counts, then first ranks
+    ulonglong2* slots = reinterpret_cast<ulonglong2*>(r.slots);
+    cudaMemsetAsync(cnt, 0, (size_t)(nbkt + 1) * 4, s);
+    k_bplace<<<gs, 256, 0, s>>>(r.shift, r.solo, n, (int)B, r.a, cnt, slots, ctl);
+    k_scan_excl<<<(nbkt + 1 + kScanTile - 1) / kScanTile, kScanThreads, 0, s>>>(
+        cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, ctl);
+    k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
+                                                                              ctl);
     k_bsort<<<(u32)min((long long)(nbkt + 15) / 16, (long long)r.num_sms * 16), 256, 0, s>>>(
-        cnt, nbkt, tmp, n, r.order, rank, ctl);
+        cnt, nbkt, slots, r.excl, n, r.order, r.key, rcnt, ctl);
     launches += 4;
   } else {
+    u32* rank = reinterpret_cast<u32*>(r.k1) + n;  // k1 holds 2 max(n, 64) 32-bit words
     allow_sort_smem();
     k_split64<<<gs, 256, 0, s>>>(r.shift, n, r.a, r.k0, r.v0, ctl);
     k_scan_digits<<<1, 256, 0, s>>>(&ctl->hist_f[0][0], &ctl->off_f[0][0], &ctl->mask_f,
@@ -719,20 +746,18 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
       ++launches;
     }
     k_rank_scatter<<<gs, 256, 0, s>>>(r.v0, r.v1, ctl, n, r.order, rank);
-    ++launches;
+    k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
+                                                                              ctl);
+    k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
+    launches += 3;
   }
-  // keys and the start-round counting sort (groups in any order inside)
-  const u32 rtiles = (r.bptr_cap + kScanTile - 1) / kScanTile;
-  k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
-                                                                            ctl);
-  k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, reinterpret_cast<u32*>(r.bptr));
-  k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(reinterpret_cast<u32*>(r.bptr), r.rcur, 0, 1,
-                                               r.status, ++(*r.epoch), &ctl->tile_ctr[1], nullptr,
-                                               ctl);
+  // the start-round counting sort (groups in any order inside)
+  k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
+                                               &ctl->tile_ctr[1], nullptr, ctl);
   k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
                         (long long)r.num_sms * 8),
                256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));
-  launches += 4;
+  launches += 2;
   return launches;
 }
 

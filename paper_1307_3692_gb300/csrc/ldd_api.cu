@@ -108,6 +108,7 @@ struct ldd_graph {
   int* d_col = nullptr;
   int2* d_up = nullptr;        // the arcs (v, w) with v < w, in CSR order
   u32* d_excl = nullptr;      // bit v: v is not handled by the BFS (no arcs or a small component)
+  u32* d_solo = nullptr;      // bit v: v is alone in its component (inside the d_excl allocation)
   SmallComps sc;              // components of 2..32 vertices, solved one warp each
   // scratch arena
   void* arena = nullptr;
@@ -123,7 +124,7 @@ struct ldd_graph {
   u32* d_qoff[2] = {nullptr, nullptr};
   u32* d_cf[2] = {nullptr, nullptr};
   u32* d_ulist[2] = {nullptr, nullptr};
-  void* d_tmp16 = nullptr;
+  void* d_slots = nullptr;
   int* d_center = nullptr;
   int* d_dist = nullptr;
   Control* d_ctl = nullptr;
@@ -207,7 +208,7 @@ int alloc_scratch(ldd_graph* g) {
       {(void**)&g->d_qoff[0], 4 * n},     {(void**)&g->d_qoff[1], 4 * n},
       {(void**)&g->d_cf[0], 4 * ncf},     {(void**)&g->d_cf[1], 4 * ncf},
       {(void**)&g->d_ulist[0], 4 * n},    {(void**)&g->d_ulist[1], 4 * n},
-      {(void**)&g->d_tmp16, 16 * n},
+      {(void**)&g->d_slots, n ? fraction_slot_bytes((u32)n) : 0},
       {(void**)&g->d_center, 4 * n},      {(void**)&g->d_dist, 4 * n},
       {(void**)&g->d_ctl, sizeof(Control)},
   };
@@ -236,14 +237,15 @@ int alloc_scratch(ldd_graph* g) {
 // table sizes read back in between).
 int build_component_tables(ldd_graph* g) {
   const size_t n = (size_t)g->n;
-  if (cudaMalloc(&g->d_excl, std::max<size_t>((n + 31) / 32, 1) * 4) != cudaSuccess) {
+  const size_t words = std::max<size_t>((n + 31) / 32, 1);
+  if (cudaMalloc(&g->d_excl, 2 * words * 4) != cudaSuccess) {
     cudaGetLastError();
-    return fail(LDD_ERR_OOM, "device allocation of the exclusion bitmask failed");
+    return fail(LDD_ERR_OOM, "device allocation of the exclusion bitmasks failed");
   }
+  g->d_solo = g->d_excl + words;
   if (n == 0) return LDD_OK;
-  const size_t words = 7 * n + 2 * (n / 2 + 1) + 4;
   u32* tmp = nullptr;
-  if (cudaMalloc(&tmp, words * 4) != cudaSuccess) {
+  if (cudaMalloc(&tmp, (7 * n + 2 * (n / 2 + 1) + 4) * 4) != cudaSuccess) {
     cudaGetLastError();
     return fail(LDD_ERR_OOM, "device allocation for component labelling failed");
   }
@@ -259,7 +261,7 @@ int build_component_tables(ldd_graph* g) {
   t.counters = t.comp_len + (n / 2 + 1);
   u32 counts[4] = {0, 0, 0, 0};
   cudaError_t e = components_phase1(g->d_row, g->d_up, g->m_up, (u32)n, g->num_sms, t, g->d_excl,
-                                    counts, nullptr);
+                                    g->d_solo, counts, nullptr);
   int rc = LDD_OK;
   SmallComps& sc = g->sc;
   if (e != cudaSuccess) {
@@ -350,8 +352,8 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
     ++launches;
   }
   record(g, 3);
-  launches += launch_finalize(g->d_key, g->d_order, (u32)g->n, center, dist, &g->d_ctl->err,
-                              g->num_sms, s);
+  launches += launch_finalize(g->d_key, g->d_order, g->d_solo, (u32)g->n, center, dist,
+                              &g->d_ctl->err, g->num_sms, s);
   return launches;
 }
 
@@ -571,12 +573,13 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
   rb.k1 = g->d_k[1];
   rb.v0 = g->d_v[0];
   rb.v1 = g->d_v[1];
-  rb.tmp16 = g->d_tmp16;
+  rb.slots = g->d_slots;
   rb.status = g->d_status;
   rb.epoch = &g->epoch;
   rb.order = g->d_order;
   rb.key = g->d_key;
   rb.excl = g->d_excl;
+  rb.solo = g->d_solo;
   rb.ctl = g->d_ctl;
   Header h;
   int status = LDD_OK;
@@ -632,6 +635,7 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
 
   ldd_stats& st = g->stats;
   st.max_floor_shift = h.A;
+  st.exact_rank = exact64 ? 1 : 0;
   st.rounds = h.rounds;
   st.last_level = h.last_level;
   st.items = (int64_t)h.items;

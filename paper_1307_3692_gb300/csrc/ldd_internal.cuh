@@ -150,7 +150,7 @@ struct RankBufs {
   u64* k1;
   u32* v0;              // [n] values / scratch; ends as the start-bucket vertices
   u32* v1;
-  void* tmp16;          // [n] 16-byte records (fraction bucket scatter)
+  void* slots;          // fraction_slot_bytes(n): bucket record slots (fast path)
   u64* status;          // look-back status words (epoch-tagged)
   u32* epoch;
   u32* order;           // [n] rank -> vertex
@@ -159,29 +159,34 @@ struct RankBufs {
   u32* rcur;            // [bptr_cap] scatter cursors
   u32 bptr_cap;
   const u32* excl;      // bit v: v is not handled by the BFS (no start bucket)
+  const u32* solo;      // bit v: v is alone in its component (no rank needed)
   Control* ctl;
 };
-// exact64 = false: fraction buckets + in-bucket exact ranks (may set
-// kErrRankRetry); true: exact 64-bit LSD radix sort.  The start buckets end in
-// v0 (vertices) and k0 viewed as 32-bit words (their rounds).
+// exact64 = false: fraction buckets + in-bucket exact ranks of the vertices
+// not alone in their component (may set kErrRankRetry); true: exact 64-bit
+// LSD radix sort of all vertices.  The start buckets end in v0 (vertices) and
+// k0 viewed as 32-bit words (their rounds).
 int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s);
 u32 fraction_bucket_bits(u32 n);
+size_t fraction_slot_bytes(u32 n);
 // Persistent BFS (k_bfs.cu).  Returns kernels launched, or -1 with the CUDA
 // error left in *err.
 int bfs_grid_size(int num_sms, int* blocks_per_sm);
 int launch_bfs(const BfsArgs& a, int grid, cudaStream_t s, cudaError_t* err);
 size_t bfs_smem_bytes();
 // Finalize, cut and per-graph component tables (k_graph.cu).
-int launch_finalize(const u64* key, const u32* order, u32 n, int* center, int* dist,
-                    const u32* err, int num_sms, cudaStream_t s);
+int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, int* center,
+                    int* dist, const u32* err, int num_sms, cudaStream_t s);
 // Cut count over the upper arcs (v, w), v < w, of the graph.
 int launch_cut(const int2* up, u32 m_up, const int* center, u64* out, int num_sms,
                cudaStream_t s);
 int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s);
 // Labels components and fills t.comp_* and excl (bit v: kept out of the BFS);
 // counts = {small components, their members, vertices left to the BFS, their arcs}.
+// excl and solo: bitmasks of (n + 31) / 32 words each.
 cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 n, int num_sms,
-                              const CompScratch& t, u32* excl, u32 counts[4], cudaStream_t s);
+                              const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
+                              cudaStream_t s);
 // Adjacency masks of the small-component members (sc.comp_v already filled).
 cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,
                               const SmallComps& sc, int num_sms, cudaStream_t s);

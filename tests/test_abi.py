@@ -66,3 +66,23 @@ def test_binding_checks_dtypes(ldd):
     with pytest.raises(ValueError):
         ldd._addr(np.zeros(2, dtype=np.int32), "i32", 4, "row_ptr")
     assert ldd._addr(np.zeros(4, dtype=np.int32), "i32", 4, "row_ptr") != 0
+
+
+def test_stats_layout_matches_header(ldd, tmp_path):
+    """The binding's ldd_stats mirror has the C struct's size and offsets."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in ldd._Stats._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "ldd.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(ldd_stats));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(ldd_stats, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(ldd._Stats)
+    assert got[1:] == [getattr(ldd._Stats, f).offset for f in fields]

@@ -279,20 +279,58 @@ def test_component_labels_deep_trees(ldd, cuda):
         assert st["n_active"] == int(sz[lab][sz[lab] > 32].size)
 
 
-@pytest.mark.parametrize("kind", ["equal_codes_unequal_fractions", "tiny_shifts", "half_ties"])
-def test_fraction_rank_exact_fallback(ldd, cuda, kind):
-    """Runs of vertices whose fractions agree in their top 32 bits but differ
-    below (or are all below 2^-32) force the exact 64-bit rank path; runs of
-    exactly equal fractions keep the fast path (ties resolved by id)."""
+@pytest.mark.parametrize("kind,exact", [("equal_codes_unequal_fractions", 1), ("tiny_shifts", 1),
+                                        ("half_ties", 1), ("short_equal_runs", 0)])
+def test_fraction_rank_exact_fallback(ldd, cuda, kind, exact):
+    """Fractions crowded into one bucket (equal in their top 32 bits but not
+    below, all below 2^-32, or only two distinct values) overflow the bucket
+    slots and force the exact 64-bit rank path; short runs of exactly equal
+    fractions stay on the bucket path, their ties resolved by id."""
     rng = np.random.default_rng(3)
     G = gen.grid2d(40, 30)
     if kind == "equal_codes_unequal_fractions":
         shifts = rng.integers(0, 40, G.n) + 0.5 + rng.integers(0, 1 << 12, G.n) * 2.0 ** -45
     elif kind == "tiny_shifts":
         shifts = rng.random(G.n) * 2.0 ** -33 + rng.integers(0, 3, G.n)
-    else:
+    elif kind == "half_ties":
         shifts = rng.integers(0, 60, G.n) * 0.5
-    assert_parity(ldd, G, shifts, 0.1)
+    else:  # 400 distinct fractions, three vertices each
+        fr = rng.random(400)
+        shifts = rng.integers(0, 30, G.n) + fr[rng.permutation(G.n) % 400]
+    _, _, _, st = assert_parity(ldd, G, shifts, 0.1)
+    assert st["exact_rank"] == exact
+
+
+@pytest.mark.parametrize("beta", [0.02, 0.5, 1.0])
+def test_fraction_rank_bucket_path_taken(ldd, cuda, beta):
+    """Exponential shifts with beta <= 1 are ranked on the bucket path (the
+    exact path is only for crowded fractions)."""
+    G = gen.rmat(14)
+    _, _, _, st = assert_parity(ldd, G, gen.shifts(G.n, beta, 41), beta)
+    assert st["exact_rank"] == 0
+
+
+def test_self_loops_and_repeated_arcs(ldd, cuda):
+    """Self-loops and repeated arcs change no distance; a vertex whose only
+    arcs are self-loops is a component of its own (its own center).  The cut
+    counts repeated edges with their multiplicity."""
+    base = gen.rmat(11)
+    rng = np.random.default_rng(21)
+    adj = [list(base.col[base.row_ptr[v]:base.row_ptr[v + 1]]) for v in range(base.n)]
+    for v in rng.choice(base.n, 300, replace=False):
+        adj[v].append(int(v))
+    for v in rng.choice(base.n, 200, replace=False):
+        w = next((int(x) for x in adj[v] if x != v), None)
+        if w is not None:
+            adj[v].append(w)
+            adj[w].append(int(v))
+    rp = np.zeros(base.n + 1, dtype=np.int32)
+    rp[1:] = np.cumsum([len(a) for a in adj])
+    col = np.asarray([x for a in adj for x in sorted(a)], dtype=np.int32)
+    G = gen.CSR("rmat11_loops_multi", rp, col)
+    assert any(len(a) > 0 and all(x == v for x in a) for v, a in enumerate(adj))
+    for beta in (0.05, 0.5):
+        assert_parity(ldd, G, gen.shifts(G.n, beta, 31), beta)
 
 
 @pytest.mark.parametrize("mode", ["always_pull", "alternate", "default"])
