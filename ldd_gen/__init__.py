@@ -201,6 +201,9 @@ WORKLOADS = {
     "rmat22": dict(graph=("rmat", 22, 16, 0.57, 0.19, 0.19, 7), betas=(0.02, 0.1, 0.5), shift_seed=1),
     # 3D 6-neighbour grid 256^3, beta 0.01
     "grid3d_256": dict(graph=("grid3d", 256, 256, 256), betas=(0.01,), shift_seed=1),
+    # R-MAT scale 20 with the scale-22 parameters: a quarter-size case whose
+    # arrays still exceed the L2 cache, for detailed kernel profiles
+    "rmat20": dict(graph=("rmat", 20, 16, 0.57, 0.19, 0.19, 7), betas=(0.02, 0.1, 0.5), shift_seed=1),
 }
 
 

@@ -54,45 +54,81 @@ __global__ void __launch_bounds__(256) k_finalize(const u64* __restrict__ key,
   }
 }
 
-// Edges per thread per step: two 16-byte loads of two (v, w) pairs each.
-constexpr int kCutPairs = 2;
+// Labels of the hot table's vertices, gathered once per cut count.
+__global__ void k_hot_centers(const u32* __restrict__ hot, u32 n_hot,
+                              const int* __restrict__ center, int* __restrict__ hot_center) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_hot) hot_center[i] = center[hot[i]];
+}
 
-__global__ void __launch_bounds__(256) k_cut(const int2* __restrict__ up, u32 m_up,
-                                             const int* __restrict__ center, u64* out) {
-  __shared__ unsigned long long wsum[8];
-  const int4* up4 = reinterpret_cast<const int4*>(up);  // cudaMalloc'd: 256-byte aligned
-  const u32 nquad = m_up / 2;
+// Edges per thread per step: two 16-byte loads of two (cold, hot) entries
+// each.  The next step's loads are issued before this step's label reads, so
+// the stream and the gathers overlap.  Cold endpoints come in sorted order
+// (their label reads coalesce); hot endpoints in the hot table read shared
+// memory instead of a random global gather.
+constexpr int kCutPairs = 2;
+constexpr int kCutThreads = 1024;
+
+__device__ __forceinline__ int hot_label(int y, const int* __restrict__ center, const int* s_hot) {
+  return y < 0 ? s_hot[y & 0x7fffffff] : center[y];
+}
+
+__global__ void __launch_bounds__(kCutThreads, 1) k_cut(const int2* __restrict__ list, u32 m,
+                                                        const int* __restrict__ center,
+                                                        const int* __restrict__ hot_center,
+                                                        u32 n_hot, u64* out) {
+  extern __shared__ int4 cut_smem[];
+  int* s_hot = reinterpret_cast<int*>(cut_smem);
+  __shared__ unsigned long long wsum[kCutThreads / 32];
+  const u32 tid = threadIdx.x;
+  const int4* hc4 = reinterpret_cast<const int4*>(hot_center);  // cudaMalloc'd: aligned
+  for (u32 i = tid; i < n_hot / 4; i += blockDim.x) cut_smem[i] = __ldg(hc4 + i);
+  for (u32 i = (n_hot & ~3u) + tid; i < n_hot; i += blockDim.x) s_hot[i] = hot_center[i];
+  __syncthreads();
+  const int4* l4 = reinterpret_cast<const int4*>(list);  // cudaMalloc'd: 256-byte aligned
+  const u32 nquad = m / 2;
   const u32 stride = gridDim.x * blockDim.x;
+  const u32 step = stride * kCutPairs;
   unsigned long long cnt = 0;
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nquad; i += stride * kCutPairs) {
-    int4 q[kCutPairs];
+  u32 i = blockIdx.x * blockDim.x + tid;
+  int4 q[kCutPairs];
+#pragma unroll
+  for (int k = 0; k < kCutPairs; ++k) {
+    const u32 j = i + (u32)k * stride;
+    q[k] = (j < nquad) ? __ldcs(l4 + j) : make_int4(0, 0, 0, 0);
+  }
+  for (; i < nquad; i += step) {
+    int4 nq[kCutPairs];
 #pragma unroll
     for (int k = 0; k < kCutPairs; ++k) {
-      const u32 j = i + (u32)k * stride;
-      q[k] = (j < nquad) ? __ldcs(up4 + j) : make_int4(0, 0, 0, 0);
+      const u32 j = i + step + (u32)k * stride;  // < 2^32: nquad < 2^29, step < 2^22
+      nq[k] = (j < nquad) ? __ldcs(l4 + j) : make_int4(0, 0, 0, 0);
     }
     int c[kCutPairs][4];
 #pragma unroll
     for (int k = 0; k < kCutPairs; ++k) {
       c[k][0] = center[q[k].x];
-      c[k][1] = center[q[k].y];
+      c[k][1] = hot_label(q[k].y, center, s_hot);
       c[k][2] = center[q[k].z];
-      c[k][3] = center[q[k].w];
+      c[k][3] = hot_label(q[k].w, center, s_hot);
     }
 #pragma unroll
-    for (int k = 0; k < kCutPairs; ++k) cnt += (c[k][0] != c[k][1]) + (c[k][2] != c[k][3]);
+    for (int k = 0; k < kCutPairs; ++k) {
+      cnt += (c[k][0] != c[k][1]) + (c[k][2] != c[k][3]);
+      q[k] = nq[k];
+    }
   }
-  if ((m_up & 1u) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd edge count: the last edge
-    const int2 e = up[m_up - 1];
-    cnt += center[e.x] != center[e.y];
+  if ((m & 1u) && blockIdx.x == 0 && tid == 0) {  // odd edge count: the last edge
+    const int2 e = list[m - 1];
+    cnt += center[e.x] != hot_label(e.y, center, s_hot);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+  if ((tid & 31) == 0) wsum[tid >> 5] = cnt;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     unsigned long long tot = 0;
-    for (int i = 0; i < (int)(blockDim.x / 32); ++i) tot += wsum[i];
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += wsum[w];
     if (tot) atomicAdd(out, tot);
   }
 }
@@ -253,12 +289,26 @@ int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, in
   return 1;
 }
 
-int launch_cut(const int2* up, u32 m_up, const int* center, u64* out, int num_sms,
-               cudaStream_t s) {
-  if (m_up == 0) return 0;
-  const u32 g = (u32)max(1ll, min((long long)(m_up / 2 + 255) / 256, (long long)num_sms * 16));
-  k_cut<<<g, 256, 0, s>>>(up, m_up, center, out);
-  return 1;
+int launch_cut(const int2* list, u32 m, const int* center, const u32* hot, u32 n_hot,
+               int* hot_center, u64* out, int num_sms, cudaStream_t s) {
+  if (m == 0) return 0;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(k_cut, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kHotSlots * sizeof(int)));
+    attr_set[dev] = true;
+  }
+  int launches = 0;
+  if (n_hot > 0) {
+    k_hot_centers<<<(n_hot + 255) / 256, 256, 0, s>>>(hot, n_hot, center, hot_center);
+    ++launches;
+  }
+  const u32 g = (u32)max(1ll, min((long long)(m / 2 + kCutThreads - 1) / kCutThreads,
+                                  (long long)num_sms));
+  k_cut<<<g, kCutThreads, (size_t)n_hot * sizeof(int), s>>>(list, m, center, hot_center, n_hot,
+                                                            out);
+  return launches + 1;
 }
 
 int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s) {

@@ -60,23 +60,35 @@ __device__ __forceinline__ void hist_add(u32* sh, u32 digit, bool valid, u32 lan
   }
 }
 
-// Bits of a fraction f in [0, 1), with -0 folded into +0; the bits of a
-// non-negative double order like its value.
-__device__ __forceinline__ u64 fraction_bits(double f) {
-  return f == 0.0 ? 0ull : (u64)__double_as_longlong(f);
-}
-
-__device__ __forceinline__ void split_one(double d, u32& err, int& a, double& f) {
+// Splits a shift d into a = floor(d) and the IEEE-754 bits of its fraction
+// f = d - a (exact), with integer operations on d's bits only: FP64
+// arithmetic is slow on this part and the split runs once per vertex.  The
+// bits of a non-negative double order like its value, so fb orders the
+// fractions.  d = -0 counts as +0.  NaN or d < 0 sets kErrShiftArg, d >= 2^31
+// (or +inf) kErrShiftRange; a = 0 and fb = 0 then.
+__device__ __forceinline__ void split_bits(double d, u32& err, int& a, u64& fb) {
+  constexpr u64 kMan = (1ull << 52) - 1;
+  const u64 b = (u64)__double_as_longlong(d);
+  const u32 ex = (u32)(b >> 52) & 0x7ffu;
   a = 0;
-  f = 0.0;
-  if (!(d >= 0.0)) {
+  fb = 0;
+  if (ex == 0x7ffu && (b & kMan) != 0) {  // NaN, either sign
     err |= kErrShiftArg;
-  } else if (!(d < 2147483648.0)) {
+  } else if (b >> 63) {                   // negative; -0 is +0
+    if (b << 1) err |= kErrShiftArg;
+  } else if (ex >= 1023u + 31u) {         // >= 2^31 or +inf
     err |= kErrShiftRange;
+  } else if (ex < 1023u) {                // d < 1: a = 0, f = d
+    fb = b;
   } else {
-    const double fl = floor(d);
-    a = (int)fl;
-    f = d - fl;  // exact: fl <= d < 2 fl, or fl = 0
+    const u32 E = ex - 1023u;             // d = M * 2^(E - 52), 0 <= E <= 30
+    const u64 M = (b & kMan) | (1ull << 52);
+    a = (int)(M >> (52 - E));
+    const u64 fr = M & ((1ull << (52 - E)) - 1);  // f = fr * 2^(E - 52)
+    if (fr) {
+      const int p = 63 - __clzll((long long)fr);  // leading bit of fr: f in [2^(p+E-52), 2^(p+E-51))
+      fb = ((u64)(p + (int)E - 52 + 1023) << 52) | ((fr << (52 - p)) & kMan);
+    }
   }
 }
 
@@ -98,41 +110,74 @@ __device__ __forceinline__ void finish_split(u32 err, int amax, Control* ctl) {
 }
 
 // ---------------------------------------------------------------- fast path
-__device__ __forceinline__ u32 bucket_of(double f, int B) {
-  const u32 code = (u32)floor(f * 4294967296.0);  // f * 2^32 < 2^32, exact scaling
-  return (~code) >> (32 - B);                      // larger fraction, smaller bucket
+// Top B bits of ~floor(f * 2^32) for the fraction with bits fb: larger
+// fractions get smaller buckets.  f = M * 2^(Ef - 52) with Ef <= -1, so
+// floor(f * 2^32) = M >> (20 - Ef) < 2^32.
+__device__ __forceinline__ u32 bucket_of(u64 fb, int B) {
+  const u32 ef = (u32)(fb >> 52);
+  const u64 M = (fb & ((1ull << 52) - 1)) | (ef ? (1ull << 52) : 0ull);
+  const int Ef = ef ? (int)ef - 1023 : -1022;
+  const int sh = 20 - Ef;
+  const u32 code = sh >= 64 ? 0u : (u32)(M >> sh);
+  return (~code) >> (32 - B);
 }
 
 // Pass 1, the only read of the shifts: split and validate every shift, and
-// drop (bits of f_u, a_u, u) into the next free slot of u's bucket unless u
-// is alone in its component.  A full bucket sends the host to the exact path.
+// drop a record into the next free slot of u's bucket unless u is alone in
+// its component.  Record: x = bits of f_u; y = (a_u << 32) | u, with bit 31
+// set when the BFS does not handle u (u < 2^30).  Each thread takes
+// kPlaceIpt vertices per step so that their loads and slot atomics overlap.
+// A full bucket sends the host to the exact path.
+constexpr int kPlaceIpt = 4;
+
 __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta,
-                                                const u32* __restrict__ solo, u32 n, int B,
+                                                const u32* __restrict__ solo,
+                                                const u32* __restrict__ excl, u32 n, int B,
                                                 int* __restrict__ a_out, u32* __restrict__ cnt,
                                                 ulonglong2* __restrict__ slots, Control* ctl) {
   int amax = 0;
   u32 err = 0;
   const u32 stride = gridDim.x * blockDim.x;
-  for (u32 u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
-    int a;
-    double f;
-    split_one(delta[u], err, a, f);
-    a_out[u] = a;
-    amax = max(amax, a);
-    if ((__ldg(solo + (u >> 5)) >> (u & 31)) & 1u) continue;
-    const u32 b = bucket_of(f, B);
-    const u32 pos = atomicAdd(cnt + b, 1u);
-    if (pos < kSlotCap)
-      slots[(size_t)b * kSlotCap + pos] =
-          make_ulonglong2(fraction_bits(f), ((u64)(u32)a << 32) | u);
-    else
-      err |= kErrRankRetry;
+  for (u32 base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += stride * kPlaceIpt) {
+    double d[kPlaceIpt];
+#pragma unroll
+    for (int k = 0; k < kPlaceIpt; ++k) {
+      const u32 u = base + (u32)k * stride;
+      d[k] = (u < n) ? __ldcs(delta + u) : 0.0;
+    }
+    u32 bkt[kPlaceIpt], pos[kPlaceIpt];
+    ulonglong2 rec[kPlaceIpt];
+#pragma unroll
+    for (int k = 0; k < kPlaceIpt; ++k) {
+      const u32 u = base + (u32)k * stride;
+      bkt[k] = 0xffffffffu;
+      if (u < n) {
+        int a;
+        u64 fb;
+        split_bits(d[k], err, a, fb);
+        a_out[u] = a;
+        amax = max(amax, a);
+        if (!((__ldg(solo + (u >> 5)) >> (u & 31)) & 1u)) {
+          const u32 out = ((__ldg(excl + (u >> 5)) >> (u & 31)) & 1u) << 31;
+          bkt[k] = bucket_of(fb, B);
+          rec[k] = make_ulonglong2(fb, ((u64)(u32)a << 32) | u | out);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kPlaceIpt; ++k) pos[k] = bkt[k] != 0xffffffffu ? atomicAdd(cnt + bkt[k], 1u) : 0u;
+#pragma unroll
+    for (int k = 0; k < kPlaceIpt; ++k) {
+      if (bkt[k] == 0xffffffffu) continue;
+      if (pos[k] < kSlotCap) slots[(size_t)bkt[k] * kSlotCap + pos[k]] = rec[k];
+      else err |= kErrRankRetry;
+    }
   }
   finish_split(err, amax, ctl);
 }
 
 // Adds one to the count of start round R for every lane with take set, one
-// atomic per distinct R in the warp (shared memory when A + 1 <= kRBins).
+// atomic per distinct R in the warp (shared memory when small).
 __device__ __forceinline__ void count_round(u32 R, bool take, bool small, u32* sh, u32* rcnt) {
   const u32 act = __ballot_sync(kFull, take);
   if (!act) return;
@@ -143,80 +188,116 @@ __device__ __forceinline__ void count_round(u32 R, bool take, bool small, u32* s
   }
 }
 
+// True if record o comes before record me in (f descending, id ascending).
+__device__ __forceinline__ bool rec_before(const ulonglong2 o, const ulonglong2 me) {
+  const u32 uo = (u32)o.y & 0x7fffffffu, um = (u32)me.y & 0x7fffffffu;
+  return o.x > me.x || (o.x == me.x && uo < um);
+}
+
 // Writes what rank p of record rec gives: order[p] = u and u's start key
 // ((A - a_u) << 32) | p; counts u under its start round if the BFS handles u.
 // Called by the whole warp.
 __device__ __forceinline__ void emit_rank(bool valid, const ulonglong2 rec, u32 p, u32 n, int A,
-                                          const u32* __restrict__ excl, bool small, u32* sh,
-                                          u32* rcnt, u32* __restrict__ order,
-                                          u64* __restrict__ key) {
-  const u32 u = (u32)rec.y;
+                                          bool small, u32* sh, u32* rcnt,
+                                          u32* __restrict__ order, u64* __restrict__ key) {
+  const u32 u = (u32)rec.y & 0x7fffffffu;
   const u32 R = (u32)(A - (int)(u32)(rec.y >> 32));
   bool take = false;
   if (valid && p < n && u < n) {
     order[p] = u;
     key[u] = ((u64)R << 32) | p;
-    take = !((__ldg(excl + (u >> 5)) >> (u & 31)) & 1u);
+    take = !((u32)rec.y >> 31);
   }
   count_round(R, take, small, sh, rcnt);
 }
 
-// Pass 2: one warp per bucket b, whose len = start[b + 1] - start[b] members
-// sit in slots [b * kSlotCap, b * kSlotCap + len).  A member's rank is
-// start[b] + the number of members before it in (f descending, id
-// ascending).  Two buckets per warp and step, for more loads in flight.
-__global__ void __launch_bounds__(256) k_bsort(const u32* __restrict__ start, u32 nbkt,
-                                               const ulonglong2* __restrict__ slots,
-                                               const u32* __restrict__ excl, u32 n,
+// Pass 2: blocks take tiles of kTileBuckets consecutive buckets.  The tile's
+// records (bucket b's len = start[b + 1] - start[b] records sit in slots
+// [b * kSlotCap, b * kSlotCap + len)) are staged densely in shared memory in
+// bucket order, one thread per record; then every thread ranks one record
+// against the members of its own bucket: rank = start[b] + the number of
+// members before it in (f descending, id ascending).  A tile with more than
+// kTileRecs records (crowded fractions just short of a slot overflow) is
+// ranked from global memory instead.
+constexpr u32 kTileBuckets = 128;  // <= threads per CTA (one capacity check each)
+constexpr u32 kTileRecs = 2560;
+constexpr u32 kSortRBins = 1024;  // start rounds counted in shared memory here
+
+struct BsortSmem {
+  ulonglong2 rec[kTileRecs];
+  u32 st[kTileBuckets + 1];
+  u32 hist[kSortRBins];
+};
+
+// Index i of the bucket holding dense position q: st[i] <= st[0] + q < st[i + 1].
+__device__ __forceinline__ u32 tile_bucket(const u32* st, u32 nb, u32 q) {
+  const u32 target = st[0] + q;
+  u32 lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const u32 mid = (lo + hi + 1) >> 1;
+    if (st[mid] <= target) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256, 4) k_bsort(const u32* __restrict__ start, u32 nbkt,
+                                               const ulonglong2* __restrict__ slots, u32 n,
                                                u32* __restrict__ order, u64* __restrict__ key,
                                                u32* rcnt, Control* ctl) {
-  __shared__ u32 sh[kRBins];
+  extern __shared__ __align__(16) unsigned char bsort_raw[];
+  BsortSmem& sm = *reinterpret_cast<BsortSmem*>(bsort_raw);
   if (failed(ctl)) return;
   const int A = ctl->A;
-  const bool small = (u32)A + 1u <= kRBins;
-  const u32 tid = threadIdx.x, lane = tid & 31;
+  const bool small = (u32)A + 1u <= kSortRBins;
+  const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (small)
-    for (u32 i = tid; i <= (u32)A; i += blockDim.x) sh[i] = 0;
-  __syncthreads();
-  const u32 warps = gridDim.x * (blockDim.x / 32);
-  for (u32 b0 = blockIdx.x * (blockDim.x / 32) + (tid >> 5); b0 < nbkt; b0 += 2 * warps) {
-    u32 s[2], len[2];
-    ulonglong2 rec[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const u32 b = b0 + (u32)k * warps;
-      s[k] = 0;
-      len[k] = 0;
-      if (b < nbkt) {
-        s[k] = start[b];
-        const u32 e = start[b + 1];
-        if (e > s[k] && e - s[k] <= kSlotCap) len[k] = e - s[k];
+    for (u32 i = tid; i <= (u32)A; i += blockDim.x) sm.hist[i] = 0;
+  const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
+  for (u32 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const u32 b0 = t * kTileBuckets;
+    const u32 nb = min(kTileBuckets, nbkt - b0);
+    __syncthreads();  // previous tile done with sm.rec / sm.st
+    for (u32 i = tid; i <= nb; i += blockDim.x) sm.st[i] = start[b0 + i];
+    __syncthreads();
+    // a bucket beyond kSlotCap cannot reach here (k_bplace flags it); checked anyway
+    const bool full = tid < nb && sm.st[tid + 1] - sm.st[tid] > kSlotCap;
+    const bool overfull = __syncthreads_or(full) != 0;
+    const u32 total = sm.st[nb] - sm.st[0];
+    if (!overfull && total <= kTileRecs) {
+      for (u32 q = tid; q < total; q += blockDim.x) {
+        const u32 i = tile_bucket(sm.st, nb, q);
+        sm.rec[q] = slots[(size_t)(b0 + i) * kSlotCap + (sm.st[0] + q - sm.st[i])];
       }
-      rec[k] = (lane < len[k]) ? slots[(size_t)b * kSlotCap + lane] : make_ulonglong2(0ull, 0ull);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (len[k] == 0) continue;
-      const ulonglong2* bs = slots + (size_t)(b0 + (u32)k * warps) * kSlotCap;
-      if (len[k] <= 32) {
-        u32 r = 0;
-        for (u32 j = 0; j < len[k]; ++j) {
-          const u64 fj = __shfl_sync(kFull, rec[k].x, j);
-          const u32 uj = (u32)__shfl_sync(kFull, rec[k].y, j);
-          r += (fj > rec[k].x || (fj == rec[k].x && uj < (u32)rec[k].y)) ? 1u : 0u;
-        }
-        emit_rank(lane < len[k], rec[k], s[k] + r, n, A, excl, small, sh, rcnt, order, key);
-      } else {
-        for (u32 i0 = 0; i0 < len[k]; i0 += 32) {
-          const u32 i = i0 + lane;
-          const bool valid = i < len[k];
-          const ulonglong2 me = valid ? bs[i] : make_ulonglong2(0ull, 0ull);
+      __syncthreads();
+      for (u32 q0 = 0; q0 < total; q0 += blockDim.x) {
+        const u32 q = q0 + tid;
+        const bool valid = q < total;
+        ulonglong2 me = make_ulonglong2(0ull, 0ull);
+        u32 p = 0;
+        if (valid) {
+          const u32 i = tile_bucket(sm.st, nb, q);
+          me = sm.rec[q];
+          const u32 lo = sm.st[i] - sm.st[0], hi = sm.st[i + 1] - sm.st[0];
           u32 r = 0;
-          for (u32 j = 0; j < len[k]; ++j) {
-            const ulonglong2 o = bs[j];
-            r += (o.x > me.x || (o.x == me.x && (u32)o.y < (u32)me.y)) ? 1u : 0u;
-          }
-          emit_rank(valid, me, s[k] + r, n, A, excl, small, sh, rcnt, order, key);
+          for (u32 j = lo; j < hi; ++j) r += rec_before(sm.rec[j], me) ? 1u : 0u;
+          p = sm.st[i] + r;
+        }
+        emit_rank(valid, me, p, n, A, small, sm.hist, rcnt, order, key);
+      }
+    } else {
+      // one warp per bucket, records read from global memory
+      for (u32 i = warp; i < nb; i += blockDim.x / 32) {
+        const u32 s0 = sm.st[i], len = sm.st[i + 1] - sm.st[i];
+        if (len > kSlotCap) continue;  // cannot happen: k_bplace flags a full bucket
+        const ulonglong2* bs = slots + (size_t)(b0 + i) * kSlotCap;
+        for (u32 i0 = 0; i0 < len; i0 += 32) {
+          const u32 q = i0 + lane;
+          const bool valid = q < len;
+          const ulonglong2 me = valid ? bs[q] : make_ulonglong2(0ull, 0ull);
+          u32 r = 0;
+          for (u32 j = 0; j < len; ++j) r += rec_before(bs[j], me) ? 1u : 0u;
+          emit_rank(valid, me, s0 + r, n, A, small, sm.hist, rcnt, order, key);
         }
       }
     }
@@ -224,7 +305,7 @@ __global__ void __launch_bounds__(256) k_bsort(const u32* __restrict__ start, u3
   __syncthreads();
   if (small)
     for (u32 i = tid; i <= (u32)A; i += blockDim.x)
-      if (sh[i]) atomicAdd(rcnt + i, sh[i]);
+      if (sm.hist[i]) atomicAdd(rcnt + i, sm.hist[i]);
 }
 
 // ---------------------------------------------------------------- exact path
@@ -244,9 +325,9 @@ __global__ void __launch_bounds__(256) k_split64(const double* __restrict__ delt
     u64 key = 0;
     if (valid) {
       int a;
-      double f;
-      split_one(delta[idx], err, a, f);
-      key = ~fraction_bits(f);  // ascending key: f descending
+      u64 fb;
+      split_bits(delta[idx], err, a, fb);
+      key = ~fb;  // ascending key: f descending
       a_out[idx] = a;
       kout[idx] = key;
       vout[idx] = idx;
@@ -688,6 +769,17 @@ u32 grid_stride_blocks(u32 n, int num_sms) {
   return (u32)max(1ll, min((long long)(n + 255) / 256, (long long)num_sms * 8));
 }
 
+void allow_bsort_smem() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  if (!done[dev]) {
+    cudaFuncSetAttribute(k_bsort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(BsortSmem));
+    done[dev] = true;
+  }
+}
+
 void allow_sort_smem() {
   static bool done[64] = {};
   int dev = 0;
@@ -723,13 +815,16 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
     u32* cnt = reinterpret_cast<u32*>(r.k1);  // [nbkt + 1] counts, then first ranks
     ulonglong2* slots = reinterpret_cast<ulonglong2*>(r.slots);
     cudaMemsetAsync(cnt, 0, (size_t)(nbkt + 1) * 4, s);
-    k_bplace<<<gs, 256, 0, s>>>(r.shift, r.solo, n, (int)B, r.a, cnt, slots, ctl);
+    k_bplace<<<grid_stride_blocks((n + kPlaceIpt - 1) / kPlaceIpt, r.num_sms), 256, 0, s>>>(
+        r.shift, r.solo, r.excl, n, (int)B, r.a, cnt, slots, ctl);
     k_scan_excl<<<(nbkt + 1 + kScanTile - 1) / kScanTile, kScanThreads, 0, s>>>(
         cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, ctl);
     k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
                                                                               ctl);
-    k_bsort<<<(u32)min((long long)(nbkt + 15) / 16, (long long)r.num_sms * 16), 256, 0, s>>>(
-        cnt, nbkt, slots, r.excl, n, r.order, r.key, rcnt, ctl);
+    allow_bsort_smem();
+    const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
+    k_bsort<<<(u32)min((long long)ntiles, (long long)r.num_sms * 4), 256, sizeof(BsortSmem), s>>>(
+        cnt, nbkt, slots, n, r.order, r.key, rcnt, ctl);
     launches += 4;
   } else {
     u32* rank = reinterpret_cast<u32*>(r.k1) + n;  // k1 holds 2 max(n, 64) 32-bit words

@@ -106,7 +106,11 @@ struct ldd_graph {
   // device CSR and graph tables
   int* d_row = nullptr;
   int* d_col = nullptr;
-  int2* d_up = nullptr;        // the arcs (v, w) with v < w, in CSR order
+  int2* d_up = nullptr;        // the arcs (v, w) with v < w; after component labelling, the
+                               // cut list (cold, hot) of launch_cut
+  u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
+  int* d_hot_center = nullptr; // their labels, gathered per cut count
+  u32 n_hot = 0;
   u32* d_excl = nullptr;      // bit v: v is not handled by the BFS (no arcs or a small component)
   u32* d_solo = nullptr;      // bit v: v is alone in its component (inside the d_excl allocation)
   SmallComps sc;              // components of 2..32 vertices, solved one warp each
@@ -152,6 +156,8 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_row);
   cudaFree(g->d_col);
   cudaFree(g->d_up);
+  cudaFree(g->d_hot);
+  cudaFree(g->d_hot_center);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
   cudaFree(g->sc.comp_len);
@@ -290,6 +296,49 @@ int build_component_tables(ldd_graph* g) {
   }
   cudaFree(tmp);
   return rc;
+}
+
+// Rewrites d_up as the cut list of launch_cut (after the component labelling,
+// which reads it as arcs): each edge oriented from its cold endpoint to its
+// hot one (larger degree, ties to the smaller id), grouped by the cold
+// endpoint with a counting sort, and hot endpoints in the hot table encoded as
+// (slot | 2^31).  With degree skew most label reads of the cut then hit the
+// shared-memory copy of the hot table, and the cold side is read in order.
+int build_cut_list(ldd_graph* g, const std::vector<int32_t>& rp, const std::vector<int2>& up) {
+  const size_t n = (size_t)g->n, m = up.size();
+  if (m == 0) return LDD_OK;
+  auto deg = [&](int32_t v) { return rp[v + 1] - rp[v]; };
+  auto hotter = [&](int32_t a, int32_t b) {
+    const int32_t da = deg(a), db = deg(b);
+    return da > db || (da == db && a < b);
+  };
+  const size_t K = std::min<size_t>(kHotSlots, n);
+  std::vector<int32_t> ids(n);
+  for (size_t v = 0; v < n; ++v) ids[v] = (int32_t)v;
+  if (K < n) std::nth_element(ids.begin(), ids.begin() + K, ids.end(), hotter);
+  std::sort(ids.begin(), ids.begin() + K, hotter);
+  std::vector<int32_t> slot(n, -1);
+  for (size_t i = 0; i < K; ++i) slot[ids[i]] = (int32_t)i;
+  std::vector<u32> start(n + 1, 0);
+  for (const int2& e : up) ++start[(hotter(e.x, e.y) ? e.y : e.x) + 1];
+  for (size_t v = 0; v < n; ++v) start[v + 1] += start[v];
+  std::vector<int2> list(m);
+  for (const int2& e : up) {
+    const bool xh = hotter(e.x, e.y);
+    const int32_t hot = xh ? e.x : e.y, cold = xh ? e.y : e.x;
+    const int32_t enc = slot[hot] >= 0 ? (int32_t)(0x80000000u | (u32)slot[hot]) : hot;
+    list[start[cold]++] = make_int2(cold, enc);
+  }
+  g->n_hot = (u32)K;
+  if (cudaMalloc(&g->d_hot, K * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_hot_center, K * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "device allocation of the hot table failed");
+  }
+  if (cudaMemcpy(g->d_hot, ids.data(), K * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g->d_up, list.data(), m * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LDD_ERR_CUDA, "upload of the cut list failed");
+  return LDD_OK;
 }
 
 void record(ldd_graph* g, int i) {
@@ -467,6 +516,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
                                  cudaMemcpyHostToDevice) != cudaSuccess))
     return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
   if ((rc = build_component_tables(g)) != LDD_OK) return bail(rc);
+  if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
   if ((rc = alloc_scratch(g)) != LDD_OK) return bail(rc);
   if (cudaMallocHost(&g->h_hdr, 256) != cudaSuccess)
     return bail(fail(LDD_ERR_OOM, "pinned host allocation failed"));
@@ -670,7 +720,8 @@ int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut) {
     d_center = g->d_center;
   }
   CUDA_TRY(cudaMemsetAsync(&g->d_ctl->cut, 0, sizeof(u64), s));
-  const int l = launch_cut(g->d_up, g->m_up, d_center, &g->d_ctl->cut, g->num_sms, s);
+  const int l = launch_cut(g->d_up, g->m_up, d_center, g->d_hot, g->n_hot, g->d_hot_center,
+                           &g->d_ctl->cut, g->num_sms, s);
   CUDA_TRY(cudaMemcpyAsync(g->h_hdr + 128, &g->d_ctl->cut, sizeof(u64), cudaMemcpyDeviceToHost, s));
   record(g, 7);
   CUDA_TRY(cudaGetLastError());

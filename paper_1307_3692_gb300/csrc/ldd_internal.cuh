@@ -177,9 +177,14 @@ size_t bfs_smem_bytes();
 // Finalize, cut and per-graph component tables (k_graph.cu).
 int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, int* center,
                     int* dist, const u32* err, int num_sms, cudaStream_t s);
-// Cut count over the upper arcs (v, w), v < w, of the graph.
-int launch_cut(const int2* up, u32 m_up, const int* center, u64* out, int num_sms,
-               cudaStream_t s);
+// Cut count over the graph's cut list: one entry (cold, hot) per undirected
+// edge {v, w}, v < w (repeated edges repeated), with hot the endpoint of larger
+// degree (ties: smaller id), sorted by cold.  hot < 0 stands for slot
+// hot & 0x7fffffff of the hot table: the (at most kHotSlots) highest-degree
+// vertices, whose labels the cut kernel keeps in shared memory.
+constexpr u32 kHotSlots = 49152;  // 192 KiB of labels per CTA
+int launch_cut(const int2* list, u32 m, const int* center, const u32* hot, u32 n_hot,
+               int* hot_center, u64* out, int num_sms, cudaStream_t s);
 int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s);
 // Labels components and fills t.comp_* and excl (bit v: kept out of the BFS);
 // counts = {small components, their members, vertices left to the BFS, their arcs}.

@@ -28,6 +28,7 @@ def _cases():
     yield "rmat10", gen.rmat(10), 0.1, 5
     yield "rmat12_b05", gen.rmat(12), 0.5, 6
     yield "rmat14_b002", gen.rmat(14), 0.02, 7
+    yield "rmat17_b01", gen.rmat(17), 0.1, 13  # more vertices than the cut's hot table
     yield "rgg5000", gen.rgg(5000, 11), 0.1, 8
     yield "gnp300_dense", gen.random_graph(300, 0.3, 9), 0.3, 9
     yield "gnp2000_sparse", gen.random_graph(2000, 0.001, 10), 0.1, 10
@@ -299,6 +300,22 @@ def test_fraction_rank_exact_fallback(ldd, cuda, kind, exact):
         shifts = rng.integers(0, 30, G.n) + fr[rng.permutation(G.n) % 400]
     _, _, _, st = assert_parity(ldd, G, shifts, 0.1)
     assert st["exact_rank"] == exact
+
+
+def test_special_shift_values(ldd, cuda):
+    """The split of a shift into floor and fraction works on the bits of the
+    double: subnormals, -0, values one ulp either side of an integer, and
+    large values with few fraction bits must split exactly as floor() does."""
+    rng = np.random.default_rng(17)
+    G = gen.rmat(12)
+    special = np.array([0.0, -0.0, 5e-324, 2.2250738585072014e-308, 1e-300, 2.0 ** -40,
+                        np.nextafter(1.0, 0.0), 1.0, np.nextafter(1.0, 2.0), np.nextafter(2.0, 0.0),
+                        2.0, 0.5, 3.0000000000000004, 1048575.9999999999, 1048576.0,
+                        np.nextafter(1048576.0, 2e6), 524288.5, 7.25])
+    shifts = np.where(rng.random(G.n) < 0.5, special[rng.integers(0, special.size, G.n)],
+                      gen.shifts(G.n, 0.1, 17))
+    _, _, _, st = assert_parity(ldd, G, shifts, 0.1)
+    assert st["max_floor_shift"] == int(np.floor(shifts.max()))
 
 
 @pytest.mark.parametrize("beta", [0.02, 0.5, 1.0])
