@@ -296,7 +296,8 @@ __device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], u3
 }
 
 // Bottom-up round from level lvl (see the file comment).  Candidates are every
-// vertex not in excl (from_list = false) or the list `cand` of ncand vertices.
+// vertex not in excl (from_list = false; a.active lists them when it is set)
+// or the list `cand` of ncand vertices.
 // Each lane takes kPullV candidates at a time and advances their neighbour
 // scans in lock-step, one neighbour each per step, so that up to kPullV
 // independent loads are in flight per lane.  Adds the arcs it scans and the
@@ -309,6 +310,11 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
   const u32 lane = threadIdx.x & 31;
   const u32 L = (u32)lvl;
   const u64 floor_key = ((u64)(L + 1) << 32) | minrank;
+  if (!from_list && a.active) {  // the first bottom-up round: the BFS's own vertices
+    from_list = true;
+    cand = a.active;
+    ncand = a.n_active;
+  }
   const u32 total = from_list ? ncand : a.n;
   const u32 stride = gridDim.x * blockDim.x * kPullV;
   for (u32 base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * kPullV; base < total;
@@ -325,23 +331,26 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
         if (!((ex >> lane) & 1u)) w[j] = i;
       }
     }
+    // the key and the adjacency range together: one round trip, not two
     u64 kw[kPullV];
-#pragma unroll
-    for (int j = 0; j < kPullV; ++j) kw[j] = (w[j] != kNone) ? ld_cg_u64(a.key + w[j]) : 0ull;
-    u64 best[kPullV];
     int e[kPullV], re[kPullV];
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
-      best[j] = kw[j];
+      kw[j] = 0ull;
       e[j] = 0;
       re[j] = 0;
       if (w[j] != kNone) {
-        ++examined;
-        if ((u32)(kw[j] >> 32) > L && kw[j] > floor_key) {
-          e[j] = __ldg(a.row_ptr + w[j]);
-          re[j] = __ldg(a.row_ptr + w[j] + 1);
-        }
+        kw[j] = ld_cg_u64(a.key + w[j]);
+        e[j] = __ldg(a.row_ptr + w[j]);
+        re[j] = __ldg(a.row_ptr + w[j] + 1);
       }
+    }
+    u64 best[kPullV];
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      best[j] = kw[j];
+      if (w[j] != kNone) ++examined;
+      if (!((u32)(kw[j] >> 32) > L && kw[j] > floor_key)) re[j] = e[j];  // settled or unbeatable
     }
     for (;;) {  // one neighbour of every still-scanning candidate per step
       bool any = false;

@@ -108,6 +108,7 @@ struct ldd_graph {
   int* d_col = nullptr;
   int2* d_up = nullptr;        // the arcs (v, w) with v < w; after component labelling, the
                                // cut list (cold, hot) of launch_cut
+  u32* d_active = nullptr;     // vertices the BFS handles, ascending (when few enough)
   u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
   int* d_hot_center = nullptr; // their labels, gathered per cut count
   u32 n_hot = 0;
@@ -157,6 +158,7 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_col);
   cudaFree(g->d_up);
   cudaFree(g->d_hot);
+  cudaFree(g->d_active);
   cudaFree(g->d_hot_center);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
@@ -341,6 +343,31 @@ int build_cut_list(ldd_graph* g, const std::vector<int32_t>& rp, const std::vect
   return LDD_OK;
 }
 
+// The vertices the BFS handles, in ascending order, for the first bottom-up
+// round of a decomposition -- built only when they are at most 3/4 of all
+// vertices (else scanning every id and skipping the excluded ones is cheaper
+// than reading the list).
+int build_active_list(ldd_graph* g) {
+  const size_t n = (size_t)g->n;
+  if (n == 0 || (size_t)g->n_active * 4 > n * 3) return LDD_OK;
+  std::vector<u32> excl((n + 31) / 32);
+  if (cudaMemcpy(excl.data(), g->d_excl, excl.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(LDD_ERR_CUDA, "copy of the exclusion bitmask failed");
+  std::vector<u32> act;
+  act.reserve(g->n_active);
+  for (size_t v = 0; v < n; ++v)
+    if (!((excl[v >> 5] >> (v & 31)) & 1u)) act.push_back((u32)v);
+  if (act.size() != g->n_active) return fail(LDD_ERR_CUDA, "inconsistent component tables");
+  if (act.empty()) return LDD_OK;
+  if (cudaMalloc(&g->d_active, act.size() * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "device allocation of the active list failed");
+  }
+  if (cudaMemcpy(g->d_active, act.data(), act.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LDD_ERR_CUDA, "upload of the active list failed");
+  return LDD_OK;
+}
+
 void record(ldd_graph* g, int i) {
   if (g->timing) cudaEventRecord(g->ev[i], g->stream);
 }
@@ -370,6 +397,7 @@ BfsArgs bfs_args(ldd_graph* g) {
     a.ulist[b] = g->d_ulist[b];
   }
   a.excl = g->d_excl;
+  a.active = g->d_active;
   a.ctl = g->d_ctl;
   a.n = (u32)g->n;
   a.n_active = g->n_active;
@@ -517,6 +545,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
     return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
   if ((rc = build_component_tables(g)) != LDD_OK) return bail(rc);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
+  if ((rc = build_active_list(g)) != LDD_OK) return bail(rc);
   if ((rc = alloc_scratch(g)) != LDD_OK) return bail(rc);
   if (cudaMallocHost(&g->h_hdr, 256) != cudaSuccess)
     return bail(fail(LDD_ERR_OOM, "pinned host allocation failed"));

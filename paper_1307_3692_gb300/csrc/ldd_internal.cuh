@@ -104,6 +104,7 @@ struct BfsArgs {
   u32* cf[2];        // first queue slot of every base chunk of edges
   u32* ulist[2];     // vertices still unsettled after a bottom-up round (ping-pong)
   const u32* excl;   // bit v: v is not handled by the BFS
+  const u32* active; // the vertices the BFS handles, ascending (n_active), or null
   Control* ctl;
   u32 n;
   u32 n_active;      // vertices the BFS settles (components of more than 32 vertices)
