@@ -125,47 +125,75 @@ __device__ __forceinline__ u32 bucket_of(u64 fb, int B) {
 // Pass 1, the only read of the shifts: split and validate every shift, and
 // drop a record into the next free slot of u's bucket unless u is alone in
 // its component.  Record: x = bits of f_u; y = (a_u << 32) | u, with bit 31
-// set when the BFS does not handle u (u < 2^30).  Each thread takes
-// kPlaceIpt vertices per step so that their loads and slot atomics overlap.
-// A full bucket sends the host to the exact path.
+// set when the BFS does not handle u (u < 2^30).  Vertices the BFS handles are
+// also counted by their floor a_u into acnt (the start-round histogram in
+// reverse order; acnt is all zero on entry).  Each thread takes kPlaceIpt
+// vertices per step so that their loads and slot atomics overlap.  A full
+// bucket sends the host to the exact path.
 constexpr int kPlaceIpt = 4;
+
+// Adds one to the count of floor value a for every lane with take set, one
+// atomic per distinct a in the warp; floors below kRBins go to the CTA's
+// shared histogram.  A floor beyond the table (a + 2 > cap) sets kErrBucketCap.
+__device__ __forceinline__ void count_floor(int a, bool take, u32* sh, u32* acnt, u32 cap,
+                                            u32& err) {
+  const u32 act = __ballot_sync(kFull, take);
+  if (!act) return;
+  const u32 peers = __match_any_sync(kFull, take ? (u32)a : 0xffffffffu) & act;
+  if (take && (peers & lanemask_lt()) == 0) {
+    const u32 c = (u32)__popc(peers);
+    if ((u32)a < kRBins) atomicAdd(&sh[a], c);
+    else if ((u64)(u32)a + 2 <= cap) atomicAdd(acnt + a, c);
+    else err |= kErrBucketCap;
+  }
+}
 
 __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta,
                                                 const u32* __restrict__ solo,
                                                 const u32* __restrict__ excl, u32 n, int B,
-                                                int* __restrict__ a_out, u32* __restrict__ cnt,
-                                                ulonglong2* __restrict__ slots, Control* ctl) {
+                                                u32* __restrict__ cnt, ulonglong2* __restrict__ slots,
+                                                u32* acnt, u32 cap, Control* ctl) {
+  __shared__ u32 sh[kRBins];
+  const u32 tid = threadIdx.x, lane = tid & 31;
+  for (u32 i = tid; i < kRBins; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
   int amax = 0;
   u32 err = 0;
   const u32 stride = gridDim.x * blockDim.x;
-  for (u32 base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += stride * kPlaceIpt) {
+  // warp-uniform trip count: the histogram adds are warp collectives
+  for (u32 wb = blockIdx.x * blockDim.x + (tid & ~31u); wb < n; wb += stride * kPlaceIpt) {
     double d[kPlaceIpt];
 #pragma unroll
     for (int k = 0; k < kPlaceIpt; ++k) {
-      const u32 u = base + (u32)k * stride;
+      const u32 u = wb + lane + (u32)k * stride;
       d[k] = (u < n) ? __ldcs(delta + u) : 0.0;
     }
     u32 bkt[kPlaceIpt], pos[kPlaceIpt];
+    int fl[kPlaceIpt];
+    bool own[kPlaceIpt];
     ulonglong2 rec[kPlaceIpt];
 #pragma unroll
     for (int k = 0; k < kPlaceIpt; ++k) {
-      const u32 u = base + (u32)k * stride;
+      const u32 u = wb + lane + (u32)k * stride;
       bkt[k] = 0xffffffffu;
+      fl[k] = 0;
+      own[k] = false;
       if (u < n) {
-        int a;
         u64 fb;
-        split_bits(d[k], err, a, fb);
-        a_out[u] = a;
-        amax = max(amax, a);
+        split_bits(d[k], err, fl[k], fb);
+        amax = max(amax, fl[k]);
         if (!((__ldg(solo + (u >> 5)) >> (u & 31)) & 1u)) {
-          const u32 out = ((__ldg(excl + (u >> 5)) >> (u & 31)) & 1u) << 31;
+          const u32 out = (__ldg(excl + (u >> 5)) >> (u & 31)) & 1u;
+          own[k] = out == 0u;
           bkt[k] = bucket_of(fb, B);
-          rec[k] = make_ulonglong2(fb, ((u64)(u32)a << 32) | u | out);
+          rec[k] = make_ulonglong2(fb, ((u64)(u32)fl[k] << 32) | u | (out << 31));
         }
       }
     }
 #pragma unroll
     for (int k = 0; k < kPlaceIpt; ++k) pos[k] = bkt[k] != 0xffffffffu ? atomicAdd(cnt + bkt[k], 1u) : 0u;
+#pragma unroll
+    for (int k = 0; k < kPlaceIpt; ++k) count_floor(fl[k], own[k], sh, acnt, cap, err);
 #pragma unroll
     for (int k = 0; k < kPlaceIpt; ++k) {
       if (bkt[k] == 0xffffffffu) continue;
@@ -173,18 +201,32 @@ __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta
       else err |= kErrRankRetry;
     }
   }
+  __syncthreads();
+  for (u32 i = tid; i < kRBins; i += blockDim.x)
+    if (sh[i] && (u64)i + 2 <= cap) atomicAdd(acnt + i, sh[i]);
+    else if (sh[i]) err |= kErrBucketCap;
   finish_split(err, amax, ctl);
 }
 
-// Adds one to the count of start round R for every lane with take set, one
-// atomic per distinct R in the warp (shared memory when small).
-__device__ __forceinline__ void count_round(u32 R, bool take, bool small, u32* sh, u32* rcnt) {
-  const u32 act = __ballot_sync(kFull, take);
-  if (!act) return;
-  const u32 peers = __match_any_sync(kFull, take ? R : 0xffffffffu) & act;
-  if (take && (peers & lanemask_lt()) == 0) {
-    if (small) atomicAdd(&sh[R], (u32)__popc(peers));
-    else atomicAdd(rcnt + R, (u32)__popc(peers));
+// Start-round counts in round order, rcnt[r] = acnt[A - r] for r = 0 .. A and
+// rcnt[A + 1] = 0, ready for the exclusive scan that makes them bptr; acnt is
+// cleared on the way (all zero for the next decomposition).  A table too
+// small for A + 2 rounds sets kErrBucketCap.
+__global__ void __launch_bounds__(256) k_round_counts(u32* acnt, u32* rcnt, u32 cap, Control* ctl) {
+  if (failed(ctl)) return;
+  const int A = ctl->A;
+  if ((u64)A + 2 > cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrBucketCap);
+    return;
+  }
+  const u32 len = (u32)A + 2u;
+  for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < len; r += gridDim.x * blockDim.x) {
+    u32 c = 0;
+    if (r <= (u32)A) {
+      c = acnt[(u32)A - r];
+      acnt[(u32)A - r] = 0;
+    }
+    rcnt[r] = c;
   }
 }
 
@@ -195,20 +237,38 @@ __device__ __forceinline__ bool rec_before(const ulonglong2 o, const ulonglong2 
 }
 
 // Writes what rank p of record rec gives: order[p] = u and u's start key
-// ((A - a_u) << 32) | p; counts u under its start round if the BFS handles u.
-// Called by the whole warp.
-__device__ __forceinline__ void emit_rank(bool valid, const ulonglong2 rec, u32 p, u32 n, int A,
-                                          bool small, u32* sh, u32* rcnt,
-                                          u32* __restrict__ order, u64* __restrict__ key) {
+// ((A - a_u) << 32) | p.  Returns true if u goes into a start bucket (the BFS
+// handles u).
+__device__ __forceinline__ bool emit_key(bool valid, const ulonglong2 rec, u32 p, u32 n, int A,
+                                         u32* __restrict__ order, u64* __restrict__ key) {
   const u32 u = (u32)rec.y & 0x7fffffffu;
+  if (!(valid && p < n && u < n)) return false;
   const u32 R = (u32)(A - (int)(u32)(rec.y >> 32));
-  bool take = false;
-  if (valid && p < n && u < n) {
-    order[p] = u;
-    key[u] = ((u64)R << 32) | p;
-    take = !((u32)rec.y >> 31);
+  order[p] = u;
+  key[u] = ((u64)R << 32) | p;
+  return !((u32)rec.y >> 31);
+}
+
+// Places u into start bucket R (bv[pos] = u, rk[pos] = R, pos from the
+// bucket's global cursor), one atomic per distinct R in the warp.  Called by
+// the whole warp.
+__device__ __forceinline__ void place_start_warp(bool take, u32 u, u32 R, u32 n, u32* rcur,
+                                                 u32* __restrict__ bv, u32* __restrict__ rk) {
+  const u32 lane = threadIdx.x & 31;
+  const u32 act = __ballot_sync(kFull, take);
+  if (!act) return;
+  const u32 peers = __match_any_sync(kFull, take ? R : 0xffffffffu) & act;
+  const int leader = take ? __ffs(peers) - 1 : (int)lane;
+  u32 base = 0;
+  if (take && (int)lane == leader) base = atomicAdd(rcur + R, (u32)__popc(peers));
+  base = __shfl_sync(kFull, base, leader);
+  if (take) {
+    const u32 pos = base + (u32)__popc(peers & lanemask_lt());
+    if (pos < n) {
+      bv[pos] = u;
+      rk[pos] = R;
+    }
   }
-  count_round(R, take, small, sh, rcnt);
 }
 
 // Pass 2: blocks take tiles of kTileBuckets consecutive buckets.  The tile's
@@ -216,17 +276,21 @@ __device__ __forceinline__ void emit_rank(bool valid, const ulonglong2 rec, u32 
 // [b * kSlotCap, b * kSlotCap + len)) are staged densely in shared memory in
 // bucket order, one thread per record; then every thread ranks one record
 // against the members of its own bucket: rank = start[b] + the number of
-// members before it in (f descending, id ascending).  A tile with more than
-// kTileRecs records (crowded fractions just short of a slot overflow) is
-// ranked from global memory instead.
+// members before it in (f descending, id ascending), and writes order[] and
+// the key.  The tile's vertices then go into their start buckets: counted per
+// start round in shared memory, one global reservation per round and tile,
+// then written.  A tile with more than kTileRecs records (crowded fractions
+// just short of a slot overflow) is ranked from global memory instead, and
+// with more than kSortRBins start rounds the reservations are per warp.
 constexpr u32 kTileBuckets = 128;  // <= threads per CTA (one capacity check each)
 constexpr u32 kTileRecs = 2560;
-constexpr u32 kSortRBins = 1024;  // start rounds counted in shared memory here
+constexpr u32 kSortRBins = 2048;
 
 struct BsortSmem {
   ulonglong2 rec[kTileRecs];
+  u32 loc[kTileRecs];     // record's offset within its start round's share of the tile
+  u32 rc[kSortRBins];     // the tile's count per start round, then its base in the round
   u32 st[kTileBuckets + 1];
-  u32 hist[kSortRBins];
 };
 
 // Index i of the bucket holding dense position q: st[i] <= st[0] + q < st[i + 1].
@@ -241,23 +305,24 @@ __device__ __forceinline__ u32 tile_bucket(const u32* st, u32 nb, u32 q) {
   return lo;
 }
 
-__global__ void __launch_bounds__(256, 4) k_bsort(const u32* __restrict__ start, u32 nbkt,
-                                               const ulonglong2* __restrict__ slots, u32 n,
-                                               u32* __restrict__ order, u64* __restrict__ key,
-                                               u32* rcnt, Control* ctl) {
+__global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start, u32 nbkt,
+                                                  const ulonglong2* __restrict__ slots, u32 n,
+                                                  u32* __restrict__ order, u64* __restrict__ key,
+                                                  u32* rcur, u32* __restrict__ bv,
+                                                  u32* __restrict__ rk, Control* ctl) {
   extern __shared__ __align__(16) unsigned char bsort_raw[];
   BsortSmem& sm = *reinterpret_cast<BsortSmem*>(bsort_raw);
   if (failed(ctl)) return;
   const int A = ctl->A;
-  const bool small = (u32)A + 1u <= kSortRBins;
+  const bool small = (u32)A < kSortRBins;
   const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (small)
-    for (u32 i = tid; i <= (u32)A; i += blockDim.x) sm.hist[i] = 0;
+    for (u32 i = tid; i <= (u32)A; i += blockDim.x) sm.rc[i] = 0;
   const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
   for (u32 t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const u32 b0 = t * kTileBuckets;
     const u32 nb = min(kTileBuckets, nbkt - b0);
-    __syncthreads();  // previous tile done with sm.rec / sm.st
+    __syncthreads();  // previous tile done with sm
     for (u32 i = tid; i <= nb; i += blockDim.x) sm.st[i] = start[b0 + i];
     __syncthreads();
     // a bucket beyond kSlotCap cannot reach here (k_bplace flags it); checked anyway
@@ -283,7 +348,34 @@ __global__ void __launch_bounds__(256, 4) k_bsort(const u32* __restrict__ start,
           for (u32 j = lo; j < hi; ++j) r += rec_before(sm.rec[j], me) ? 1u : 0u;
           p = sm.st[i] + r;
         }
-        emit_rank(valid, me, p, n, A, small, sm.hist, rcnt, order, key);
+        const bool take = emit_key(valid, me, p, n, A, order, key);
+        const u32 R = (u32)(A - (int)(u32)(me.y >> 32));
+        if (small) {
+          if (take) sm.loc[q] = atomicAdd(&sm.rc[R], 1u);
+        } else {
+          place_start_warp(take, (u32)me.y & 0x7fffffffu, R, n, rcur, bv, rk);
+        }
+      }
+      if (small) {
+        __syncthreads();
+        for (u32 i = tid; i <= (u32)A; i += blockDim.x) {
+          const u32 c = sm.rc[i];
+          sm.rc[i] = c ? atomicAdd(rcur + i, c) : 0u;  // this tile's base in round i
+        }
+        __syncthreads();
+        for (u32 q = tid; q < total; q += blockDim.x) {
+          const ulonglong2 me = sm.rec[q];
+          const u32 u = (u32)me.y & 0x7fffffffu;
+          if (((u32)me.y >> 31) || u >= n) continue;
+          const u32 R = (u32)(A - (int)(u32)(me.y >> 32));
+          const u32 pos = sm.rc[R] + sm.loc[q];
+          if (pos < n) {
+            bv[pos] = u;
+            rk[pos] = R;
+          }
+        }
+        __syncthreads();
+        for (u32 i = tid; i <= (u32)A; i += blockDim.x) sm.rc[i] = 0;
       }
     } else {
       // one warp per bucket, records read from global memory
@@ -297,15 +389,13 @@ __global__ void __launch_bounds__(256, 4) k_bsort(const u32* __restrict__ start,
           const ulonglong2 me = valid ? bs[q] : make_ulonglong2(0ull, 0ull);
           u32 r = 0;
           for (u32 j = 0; j < len; ++j) r += rec_before(bs[j], me) ? 1u : 0u;
-          emit_rank(valid, me, s0 + r, n, A, small, sm.hist, rcnt, order, key);
+          const bool take = emit_key(valid, me, s0 + r, n, A, order, key);
+          place_start_warp(take, (u32)me.y & 0x7fffffffu, (u32)(A - (int)(u32)(me.y >> 32)), n,
+                           rcur, bv, rk);
         }
       }
     }
   }
-  __syncthreads();
-  if (small)
-    for (u32 i = tid; i <= (u32)A; i += blockDim.x)
-      if (sm.hist[i]) atomicAdd(rcnt + i, sm.hist[i]);
 }
 
 // ---------------------------------------------------------------- exact path
@@ -811,49 +901,52 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
   const u32 rtiles = (r.bptr_cap + kScanTile - 1) / kScanTile;
   u32* rcnt = reinterpret_cast<u32*>(r.bptr);
   if (!exact64) {
+    // split + records + floor counts; bucket starts; round counts (the scan
+    // below makes them bptr); ranks, keys and the start buckets in one pass
     const u32 B = fraction_bucket_bits(n), nbkt = 1u << B;
     u32* cnt = reinterpret_cast<u32*>(r.k1);  // [nbkt + 1] counts, then first ranks
     ulonglong2* slots = reinterpret_cast<ulonglong2*>(r.slots);
+    if (r.acnt_dirty) cudaMemsetAsync(r.acnt, 0, (size_t)r.bptr_cap * 4, s);
     cudaMemsetAsync(cnt, 0, (size_t)(nbkt + 1) * 4, s);
     k_bplace<<<grid_stride_blocks((n + kPlaceIpt - 1) / kPlaceIpt, r.num_sms), 256, 0, s>>>(
-        r.shift, r.solo, r.excl, n, (int)B, r.a, cnt, slots, ctl);
+        r.shift, r.solo, r.excl, n, (int)B, cnt, slots, r.acnt, r.bptr_cap, ctl);
     k_scan_excl<<<(nbkt + 1 + kScanTile - 1) / kScanTile, kScanThreads, 0, s>>>(
         cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, ctl);
-    k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
-                                                                              ctl);
+    k_round_counts<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.acnt, rcnt,
+                                                                               r.bptr_cap, ctl);
+    k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
+                                                 &ctl->tile_ctr[1], nullptr, ctl);
     allow_bsort_smem();
     const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
-    k_bsort<<<(u32)min((long long)ntiles, (long long)r.num_sms * 4), 256, sizeof(BsortSmem), s>>>(
-        cnt, nbkt, slots, n, r.order, r.key, rcnt, ctl);
-    launches += 4;
-  } else {
-    u32* rank = reinterpret_cast<u32*>(r.k1) + n;  // k1 holds 2 max(n, 64) 32-bit words
-    allow_sort_smem();
-    k_split64<<<gs, 256, 0, s>>>(r.shift, n, r.a, r.k0, r.v0, ctl);
-    k_scan_digits<<<1, 256, 0, s>>>(&ctl->hist_f[0][0], &ctl->off_f[0][0], &ctl->mask_f,
-                                    kFracDigits, n);
-    launches += 2;
-    const u32 ntiles = (n + kSortTile - 1) / kSortTile;
-    for (int d = 0; d < kFracDigits; ++d) {
-      k_onesweep<<<ntiles, kSortThreads, sizeof(SortSmem), s>>>(
-          r.k0, r.v0, r.k1, r.v1, n, d, 8 * d, &ctl->mask_f, ctl->off_f[d], r.status,
-          &ctl->tile_ctr[2 + d], ++(*r.epoch), &ctl->err);
-      ++launches;
-    }
-    k_rank_scatter<<<gs, 256, 0, s>>>(r.v0, r.v1, ctl, n, r.order, rank);
-    k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
-                                                                              ctl);
-    k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
-    launches += 3;
+    k_bsort<<<(u32)min((long long)ntiles, (long long)r.num_sms * 3), 256, sizeof(BsortSmem), s>>>(
+        cnt, nbkt, slots, n, r.order, r.key, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0), ctl);
+    return launches + 5;
   }
-  // the start-round counting sort (groups in any order inside)
+  // exact path: stable LSD radix sort of all fractions, then keys and the
+  // start-round counting sort (groups in any order inside)
+  u32* rank = reinterpret_cast<u32*>(r.k1) + n;  // k1 holds 2 max(n, 64) 32-bit words
+  allow_sort_smem();
+  k_split64<<<gs, 256, 0, s>>>(r.shift, n, r.a, r.k0, r.v0, ctl);
+  k_scan_digits<<<1, 256, 0, s>>>(&ctl->hist_f[0][0], &ctl->off_f[0][0], &ctl->mask_f,
+                                  kFracDigits, n);
+  launches += 2;
+  const u32 ntiles = (n + kSortTile - 1) / kSortTile;
+  for (int d = 0; d < kFracDigits; ++d) {
+    k_onesweep<<<ntiles, kSortThreads, sizeof(SortSmem), s>>>(
+        r.k0, r.v0, r.k1, r.v1, n, d, 8 * d, &ctl->mask_f, ctl->off_f[d], r.status,
+        &ctl->tile_ctr[2 + d], ++(*r.epoch), &ctl->err);
+    ++launches;
+  }
+  k_rank_scatter<<<gs, 256, 0, s>>>(r.v0, r.v1, ctl, n, r.order, rank);
+  k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
+                                                                            ctl);
+  k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
   k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
                                                &ctl->tile_ctr[1], nullptr, ctl);
   k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
                         (long long)r.num_sms * 8),
                256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));
-  launches += 2;
-  return launches;
+  return launches + 5;
 }
 
 }  // namespace ldd

@@ -135,6 +135,8 @@ struct ldd_graph {
   Control* d_ctl = nullptr;
   int* d_bptr = nullptr;
   u32* d_rcur = nullptr;
+  u32* d_acnt = nullptr;       // start-round counts by floor value (all zero between calls)
+  bool acnt_dirty = true;      // d_acnt may hold counts: clear before the next fast path
   u32 bptr_cap = 0;
   size_t status_bytes = 0;
   u32 epoch = 0;
@@ -168,6 +170,7 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->arena);
   cudaFree(g->d_bptr);
   cudaFree(g->d_rcur);
+  cudaFree(g->d_acnt);
   if (g->h_hdr) cudaFreeHost(g->h_hdr);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
@@ -233,8 +236,10 @@ int alloc_scratch(ldd_graph* g) {
   }
   CUDA_TRY(cudaMemset(g->d_status, 0, g->status_bytes));
   g->bptr_cap = (u32)std::min<size_t>(n + 2, 0xffffffffu);
+  g->acnt_dirty = true;  // cleared by the first fast-path attempt
   if (cudaMalloc(&g->d_bptr, (size_t)g->bptr_cap * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&g->d_rcur, (size_t)g->bptr_cap * sizeof(u32)) != cudaSuccess) {
+      cudaMalloc(&g->d_rcur, (size_t)g->bptr_cap * sizeof(u32)) != cudaSuccess ||
+      cudaMalloc(&g->d_acnt, (size_t)g->bptr_cap * sizeof(u32)) != cudaSuccess) {
     cudaGetLastError();
     return fail(LDD_ERR_OOM, "cudaMalloc of the start-bucket table failed");
   }
@@ -667,7 +672,10 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
     if (attempt) CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
     rb.bptr = g->d_bptr;
     rb.rcur = g->d_rcur;
+    rb.acnt = g->d_acnt;
+    rb.acnt_dirty = g->acnt_dirty;
     rb.bptr_cap = g->bptr_cap;
+    if (!exact64) g->acnt_dirty = true;  // until this attempt has consumed the counts
     launches += launch_rank_and_buckets(rb, exact64, s);
     record(g, 2);
     const int l = run_bfs_finalize(g, center, dist, &status);
@@ -678,29 +686,31 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&h, g->h_hdr, sizeof(h));
-    if (h.err == kErrRankRetry) {
-      // A fraction bucket too large to rank in place (crafted shifts): every
-      // kernel after the bucket scan was skipped; redo with the exact path.
-      exact64 = true;
-      continue;
-    }
-    if (h.err == kErrBucketCap) {
+    if (!exact64 && h.err == 0) g->acnt_dirty = false;  // k_round_counts cleared them
+    const u32 retry = kErrRankRetry | kErrBucketCap;
+    if (h.err == 0 || (h.err & ~retry) != 0) break;
+    // A fraction bucket too full to rank in place (crafted shifts): every
+    // kernel after the split was skipped; redo with the exact path.
+    if (h.err & kErrRankRetry) exact64 = true;
+    if (h.err & kErrBucketCap) {
       // floor(delta_max) + 2 exceeds the start-bucket table: grow it, redo.
       const size_t need = (size_t)h.A + 2;
       cudaFree(g->d_bptr);
       cudaFree(g->d_rcur);
+      cudaFree(g->d_acnt);
       g->d_bptr = nullptr;
       g->d_rcur = nullptr;
+      g->d_acnt = nullptr;
       g->bptr_cap = 0;
       if (cudaMalloc(&g->d_bptr, need * sizeof(int)) != cudaSuccess ||
-          cudaMalloc(&g->d_rcur, need * sizeof(u32)) != cudaSuccess) {
+          cudaMalloc(&g->d_rcur, need * sizeof(u32)) != cudaSuccess ||
+          cudaMalloc(&g->d_acnt, need * sizeof(u32)) != cudaSuccess) {
         cudaGetLastError();
         return fail(LDD_ERR_OOM, "start-bucket table of %zu entries", need);
       }
       g->bptr_cap = (u32)need;
-      continue;
+      g->acnt_dirty = true;  // cleared by the next fast-path attempt
     }
-    break;
   }
   if (h.err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
   if (h.err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");

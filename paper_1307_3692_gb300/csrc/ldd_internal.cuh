@@ -158,6 +158,8 @@ struct RankBufs {
   u64* key;             // [n] start keys
   int* bptr;            // [bptr_cap] start-bucket offsets (rounds 0 .. A + 1)
   u32* rcur;            // [bptr_cap] scatter cursors
+  u32* acnt;            // [bptr_cap] start-round counts by floor (fast path; all zero between calls)
+  bool acnt_dirty;      // acnt may hold counts of an unfinished call: clear it first
   u32 bptr_cap;
   const u32* excl;      // bit v: v is not handled by the BFS (no start bucket)
   const u32* solo;      // bit v: v is alone in its component (no rank needed)
