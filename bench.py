@@ -171,14 +171,15 @@ def describe(name, spec, G):
             "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, outside the timed events)"}
 
 
-def bfs_algorithmic_bytes(st, n):
+def bfs_algorithmic_bytes(st):
     """Bytes the BFS kernel's executed rounds must move for one launch:
     per arc expanded top-down or scanned bottom-up 4 B of col + 8 B of the other
     end's key (probe / atomicMin); per vertex examined bottom-up 8 B of its key
     + 8 B row_ptr; per settled vertex 8 B row_ptr + 8 B own key + 24 B queue
-    write and read; per start-bucket entry 4 B vertex id + 8 B key test."""
+    write and read; per start-bucket entry (one per vertex the BFS handles)
+    4 B vertex id + 8 B key test."""
     return (12 * (st["push_arcs"] + st["pull_arcs"]) + 16 * st["pull_vertices"]
-            + 40 * st["items"] + 12 * n)
+            + 40 * st["items"] + 12 * st["n_active"])
 
 
 def kernel_source_sha():
@@ -285,11 +286,13 @@ def our_arm(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
 
+    cuts = {}
+
     def step(record=None):
         launches = 0
         for b, sh in zip(betas, d_shifts):
             g.decompose(b, sh, center, dist_out)
-            g.cut_edges(center)
+            cuts[b] = g.cut_edges(center)
             st = g.stats()
             launches += st["launches"] + st["cut_launches"]
             if record is not None:
@@ -327,7 +330,7 @@ def our_arm(args):
 
     # ---- roofline of the dominant kernel (the persistent BFS)
     bfs_ms = [st["ms_bfs"] for st in per_beta]
-    bfs_bytes = [bfs_algorithmic_bytes(st, n) for st in per_beta]
+    bfs_bytes = [bfs_algorithmic_bytes(st) for st in per_beta]
     avg_ms = sum(bfs_ms) / len(bfs_ms)
     avg_bytes = sum(bfs_bytes) / len(bfs_bytes)
     peak, peak_kind = measured_peak_hbm()
@@ -342,28 +345,28 @@ def our_arm(args):
     phases = {k: sum(st[k] for st in per_beta) / max(tot, 1e-9) for k in
               ("ms_rank", "ms_bfs", "ms_finalize", "ms_cut")}
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: one pipelined batch
+    # call per step (shift uploads and result downloads overlap the device work)
     h_shifts = [torch.from_numpy(s).pin_memory() for s in shifts]
-    h_center = torch.empty(n, dtype=torch.int32).pin_memory()
-    h_dist = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_center = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in betas]
+    h_dist = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in betas]
     g_e2e = ldd.LddGraph(G.row_ptr, G.col, validate=False)
-    for b, sh in zip(betas, h_shifts):  # warm-up
-        g_e2e.decompose(b, sh, h_center, h_dist)
-        g_e2e.cut_edges(h_center)
+    for _ in range(2):  # warm-up (also allocates the pipeline's staging)
+        g_e2e.decompose_batch(betas, h_shifts, h_center, h_dist)
     barrier(dist)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for b, sh in zip(betas, h_shifts):
-            g_e2e.decompose(b, sh, h_center, h_dist)
-            g_e2e.cut_edges(h_center)
+        e2e_cuts = g_e2e.decompose_batch(betas, h_shifts, h_center, h_dist)
     e2e_s = (time.perf_counter() - t0) / args.steps
     barrier(dist)
     e2e_s = reduce_max(dist, e2e_s, dev)
     g_e2e.close()
-    h2d = len(betas) * (8 * n + 4 * n)        # shifts in; center in for the cut count
+    h2d = len(betas) * 8 * n                 # shifts in
     d2h = len(betas) * (8 * n + 8 + 40)      # center + dist out, cut count, status header
     e2e = {"value": world * work / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
+           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s,
+           "api": "ldd_decompose_batch (pinned host buffers)",
+           "cuts_match_device_path": e2e_cuts == [cuts[b] for b in betas]}
 
     # ---- parity spot check of the timed outputs (last beta) and CPU baseline
     cpu = None

@@ -99,6 +99,33 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
 int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut);
 
 /*
+ * ldd_decompose_batch -- k independent decompositions of g, one per shift
+ * vector (as ldd_decompose, Algorithm 2 via Algorithm 1 / Section 4), and
+ * optionally the cut count of each (Definition 1.1), pipelined: while
+ * decomposition i runs, shift vector i + 1 is copied to the device and the
+ * results of decomposition i - 1 are copied back, on two copy streams of the
+ * library's own.  Tree-embedding callers draw many shift vectors per graph
+ * (Section 1); a sweep over beta is the same call.
+ *   k           number of decompositions (0 is a no-op).
+ *   betas       double[k]: as ldd_decompose's beta, each finite and > 0.
+ *   shifts      k pointers, each to n doubles (host or device) as in
+ *               ldd_decompose.
+ *   out_center  k pointers, each to n int32 (host or device).
+ *   out_dist    k pointers, each to n int32 (host or device).
+ *   out_cut     NULL, or int64[k] on the host: out_cut[i] = the cut count of
+ *               decomposition i, computed on the device before its labels
+ *               are copied back (no upload of the labels).
+ * Host buffers overlap with the device work only if they are page-locked
+ * (cudaHostAlloc / cudaHostRegister); otherwise the copies still happen, in
+ * order.  The library keeps two shift slots and two output slots (32 n bytes)
+ * after the first call.  On failure the call returns the status of the first
+ * decomposition that failed; outputs of the ones before it are complete,
+ * later ones are unspecified.  Results are identical to k ldd_decompose calls.
+ */
+int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* const* shifts,
+                        int32_t* const* out_center, int32_t* const* out_dist, int64_t* out_cut);
+
+/*
  * ldd_cut_edges_noalloc -- the same count as ldd_cut_edges, for callers that
  * must not allocate device memory when they ask for it: for example a process
  * whose framework allocator owns the whole device memory pool, where a foreign

@@ -54,6 +54,8 @@ _lib.ldd_create_graph.argtypes = [_i32, _i64, _vp, _vp, ctypes.c_int, ctypes.POI
 _lib.ldd_create_graph.restype = ctypes.c_int
 _lib.ldd_decompose.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.ldd_decompose.restype = ctypes.c_int
+_lib.ldd_decompose_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+_lib.ldd_decompose_batch.restype = ctypes.c_int
 _lib.ldd_cut_edges.argtypes = [_vp, _vp, ctypes.POINTER(_i64)]
 _lib.ldd_cut_edges.restype = ctypes.c_int
 _lib.ldd_cut_edges_noalloc.argtypes = [_i32, _i64, _vp, _vp, _vp, _vp, _vp]
@@ -137,6 +139,24 @@ def ldd_decompose(g: int, beta: float, shifts, out_center, out_dist, n: int | No
                               _addr(out_dist, "i32", n, "out_dist")), "ldd_decompose")
 
 
+def ldd_decompose_batch(g: int, betas, shifts, out_center, out_dist, n: int | None = None,
+                        want_cut: bool = True):
+    """k pipelined decompositions (include/ldd.h); returns the k cut counts
+    (or None without want_cut).  shifts, out_center, out_dist: sequences of k
+    buffers each."""
+    k = len(betas)
+    if not (len(shifts) == len(out_center) == len(out_dist) == k):
+        raise ValueError("betas, shifts, out_center and out_dist need the same length")
+    b = (ctypes.c_double * max(k, 1))(*[float(x) for x in betas])
+    sp = (_vp * max(k, 1))(*[_addr(x, "f64", n, "shifts") for x in shifts])
+    cp = (_vp * max(k, 1))(*[_addr(x, "i32", n, "out_center") for x in out_center])
+    dp = (_vp * max(k, 1))(*[_addr(x, "i32", n, "out_dist") for x in out_dist])
+    cuts = (_i64 * max(k, 1))()
+    _check(_lib.ldd_decompose_batch(g, k, b, sp, cp, dp, cuts if want_cut else None),
+           "ldd_decompose_batch")
+    return [int(cuts[i]) for i in range(k)] if want_cut else None
+
+
 def ldd_cut_edges(g: int, center, n: int | None = None) -> int:
     out = _i64(0)
     _check(_lib.ldd_cut_edges(g, _addr(center, "i32", n, "center"), ctypes.byref(out)),
@@ -198,6 +218,10 @@ class LddGraph:
 
     def decompose(self, beta: float, shifts, out_center, out_dist) -> None:
         ldd_decompose(self.handle, beta, shifts, out_center, out_dist, self.n)
+
+    def decompose_batch(self, betas, shifts, out_center, out_dist, want_cut: bool = True):
+        return ldd_decompose_batch(self.handle, betas, shifts, out_center, out_dist, self.n,
+                                   want_cut)
 
     def cut_edges(self, center) -> int:
         return ldd_cut_edges(self.handle, center, self.n)

@@ -150,6 +150,10 @@ struct ldd_graph {
   u32 pull_gamma = 0;
   bool timing = false;
   cudaEvent_t ev[8] = {};
+  // pipelined batches (ldd_decompose_batch), set up on first use
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_out[2] = {};
+  void* batch_arena = nullptr;  // two shift slots (8n each) and two output slots (8n each)
   ldd_stats stats;
 };
 
@@ -171,9 +175,17 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_bptr);
   cudaFree(g->d_rcur);
   cudaFree(g->d_acnt);
+  cudaFree(g->batch_arena);
   if (g->h_hdr) cudaFreeHost(g->h_hdr);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i) {
+    if (g->ev_in[i]) cudaEventDestroy(g->ev_in[i]);
+    if (g->ev_used[i]) cudaEventDestroy(g->ev_used[i]);
+    if (g->ev_out[i]) cudaEventDestroy(g->ev_out[i]);
+  }
+  if (g->copy_in) cudaStreamDestroy(g->copy_in);
+  if (g->copy_out) cudaStreamDestroy(g->copy_out);
   return 0;
 }
 
@@ -459,6 +471,151 @@ struct Header {  // the control block up to and including the BFS runtime state
 };
 static_assert(sizeof(Header) == kCtlHeaderBytes + kCtlBfsStateBytes, "header layout");
 
+// One decomposition with the shifts already on the device and device
+// outputs, on the graph's stream (events 1 .. 4 when timing): rank and start
+// buckets, the round loop, finalize, with the retries of the fast rank path.
+// Fills the device-side statistics of g->stats.
+int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* dist,
+                        int* launches_out) {
+  cudaStream_t s = g->stream;
+  const size_t n = (size_t)g->n;
+  int launches = 0;
+  RankBufs rb;
+  rb.shift = d_shift;
+  rb.n = (u32)n;
+  rb.num_sms = g->num_sms;
+  rb.a = g->d_a;
+  rb.k0 = g->d_k[0];
+  rb.k1 = g->d_k[1];
+  rb.v0 = g->d_v[0];
+  rb.v1 = g->d_v[1];
+  rb.slots = g->d_slots;
+  rb.status = g->d_status;
+  rb.epoch = &g->epoch;
+  rb.order = g->d_order;
+  rb.key = g->d_key;
+  rb.excl = g->d_excl;
+  rb.solo = g->d_solo;
+  rb.ctl = g->d_ctl;
+  Header h;
+  int status = LDD_OK;
+  bool exact64 = false;
+  if (g->epoch > 0xfffff000u) {  // status tags would wrap: clear and restart
+    CUDA_TRY(cudaMemsetAsync(g->d_status, 0, g->status_bytes, s));
+    g->epoch = 0;
+  }
+  CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
+  record(g, 1);
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (attempt) CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
+    rb.bptr = g->d_bptr;
+    rb.rcur = g->d_rcur;
+    rb.acnt = g->d_acnt;
+    rb.acnt_dirty = g->acnt_dirty;
+    rb.bptr_cap = g->bptr_cap;
+    if (!exact64) g->acnt_dirty = true;  // until this attempt has consumed the counts
+    launches += launch_rank_and_buckets(rb, exact64, s);
+    record(g, 2);
+    const int l = run_bfs_finalize(g, center, dist, &status);
+    if (l < 0) return status;
+    launches += l;
+    record(g, 4);
+    CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));
+    memcpy(&h, g->h_hdr, sizeof(h));
+    if (!exact64 && h.err == 0) g->acnt_dirty = false;  // k_round_counts cleared them
+    const u32 retry = kErrRankRetry | kErrBucketCap;
+    if (h.err == 0 || (h.err & ~retry) != 0) break;
+    // A fraction bucket too full to rank in place (crafted shifts): every
+    // kernel after the split was skipped; redo with the exact path.
+    if (h.err & kErrRankRetry) exact64 = true;
+    if (h.err & kErrBucketCap) {
+      // floor(delta_max) + 2 exceeds the start-bucket table: grow it, redo.
+      const size_t need = (size_t)h.A + 2;
+      cudaFree(g->d_bptr);
+      cudaFree(g->d_rcur);
+      cudaFree(g->d_acnt);
+      g->d_bptr = nullptr;
+      g->d_rcur = nullptr;
+      g->d_acnt = nullptr;
+      g->bptr_cap = 0;
+      if (cudaMalloc(&g->d_bptr, need * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&g->d_rcur, need * sizeof(u32)) != cudaSuccess ||
+          cudaMalloc(&g->d_acnt, need * sizeof(u32)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LDD_ERR_OOM, "start-bucket table of %zu entries", need);
+      }
+      g->bptr_cap = (u32)need;
+      g->acnt_dirty = true;  // cleared by the next fast-path attempt
+    }
+  }
+  if (h.err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
+  if (h.err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");
+  if (h.err & kErrTimeout) return fail(LDD_ERR_TIMEOUT, "a device-side wait ran out");
+  if (h.err) return fail(LDD_ERR_CUDA, "device error bits 0x%x", h.err);
+  ldd_stats& st = g->stats;
+  st.max_floor_shift = h.A;
+  st.exact_rank = exact64 ? 1 : 0;
+  st.rounds = h.rounds;
+  st.last_level = h.last_level;
+  st.items = (int64_t)h.items;
+  st.edges = (int64_t)h.edges;
+  st.pull_rounds = h.pull_rounds;
+  st.push_arcs = (int64_t)h.push_arcs;
+  st.pull_arcs = (int64_t)h.pull_arcs;
+  st.pull_vertices = (int64_t)h.pull_verts;
+  st.ms_rank = elapsed(g, 1, 2);
+  st.ms_bfs = elapsed(g, 2, 3);
+  st.ms_finalize = elapsed(g, 3, 4);
+  *launches_out = launches;
+  return LDD_OK;
+}
+
+// Cut count of a device labelling on the graph's stream (events 6, 7).
+int cut_on_device(ldd_graph* g, const int* d_center, int64_t* out_cut) {
+  cudaStream_t s = g->stream;
+  record(g, 6);
+  CUDA_TRY(cudaMemsetAsync(&g->d_ctl->cut, 0, sizeof(u64), s));
+  const int l = launch_cut(g->d_up, g->m_up, d_center, g->d_hot, g->n_hot, g->d_hot_center,
+                           &g->d_ctl->cut, g->num_sms, s);
+  CUDA_TRY(cudaMemcpyAsync(g->h_hdr + 128, &g->d_ctl->cut, sizeof(u64), cudaMemcpyDeviceToHost, s));
+  record(g, 7);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  u64 cut;
+  memcpy(&cut, g->h_hdr + 128, sizeof(cut));
+  *out_cut = (int64_t)cut;
+  g->stats.cut_launches = l;
+  g->stats.ms_cut = elapsed(g, 6, 7);
+  return LDD_OK;
+}
+
+// Streams and staging of ldd_decompose_batch, created on first use.
+int setup_batch(ldd_graph* g) {
+  if (g->batch_arena) return LDD_OK;
+  const size_t n = (size_t)g->n;
+  if (cudaStreamCreateWithFlags(&g->copy_in, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&g->copy_out, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_CUDA, "cudaStreamCreate for the batch pipeline failed");
+  }
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&g->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_used[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_out[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LDD_ERR_CUDA, "cudaEventCreate for the batch pipeline failed");
+    }
+  if (cudaMalloc(&g->batch_arena, 4 * align_up(8 * n, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    g->batch_arena = nullptr;
+    return fail(LDD_ERR_OOM, "cudaMalloc of the batch staging (%zu bytes) failed",
+                4 * align_up(8 * n, 256));
+  }
+  return LDD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -630,116 +787,113 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
   if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
   cudaStream_t s = g->stream;
   const size_t n = (size_t)g->n;
-  int launches = 0;
   const bool dev_in = is_device_ptr(shifts);
   const bool dev_c = is_device_ptr(out_center), dev_d = is_device_ptr(out_dist);
   int* center = dev_c ? out_center : g->d_center;
   int* dist = dev_d ? out_dist : g->d_dist;
-  if (g->epoch > 0xfffff000u) {  // status tags would wrap: clear and restart
-    CUDA_TRY(cudaMemsetAsync(g->d_status, 0, g->status_bytes, s));
-    g->epoch = 0;
-  }
-
   record(g, 0);
-  CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
   const double* d_shift = shifts;
   if (!dev_in) {
     CUDA_TRY(cudaMemcpyAsync(g->d_shift, shifts, n * 8, cudaMemcpyHostToDevice, s));
     d_shift = g->d_shift;
   }
-  record(g, 1);
-  RankBufs rb;
-  rb.shift = d_shift;
-  rb.n = (u32)n;
-  rb.num_sms = g->num_sms;
-  rb.a = g->d_a;
-  rb.k0 = g->d_k[0];
-  rb.k1 = g->d_k[1];
-  rb.v0 = g->d_v[0];
-  rb.v1 = g->d_v[1];
-  rb.slots = g->d_slots;
-  rb.status = g->d_status;
-  rb.epoch = &g->epoch;
-  rb.order = g->d_order;
-  rb.key = g->d_key;
-  rb.excl = g->d_excl;
-  rb.solo = g->d_solo;
-  rb.ctl = g->d_ctl;
-  Header h;
-  int status = LDD_OK;
-  bool exact64 = false;
-  for (int attempt = 0; attempt < 4; ++attempt) {
-    if (attempt) CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
-    rb.bptr = g->d_bptr;
-    rb.rcur = g->d_rcur;
-    rb.acnt = g->d_acnt;
-    rb.acnt_dirty = g->acnt_dirty;
-    rb.bptr_cap = g->bptr_cap;
-    if (!exact64) g->acnt_dirty = true;  // until this attempt has consumed the counts
-    launches += launch_rank_and_buckets(rb, exact64, s);
-    record(g, 2);
-    const int l = run_bfs_finalize(g, center, dist, &status);
-    if (l < 0) return status;
-    launches += l;
-    record(g, 4);
-    CUDA_TRY(cudaMemcpyAsync(g->h_hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaStreamSynchronize(s));
-    memcpy(&h, g->h_hdr, sizeof(h));
-    if (!exact64 && h.err == 0) g->acnt_dirty = false;  // k_round_counts cleared them
-    const u32 retry = kErrRankRetry | kErrBucketCap;
-    if (h.err == 0 || (h.err & ~retry) != 0) break;
-    // A fraction bucket too full to rank in place (crafted shifts): every
-    // kernel after the split was skipped; redo with the exact path.
-    if (h.err & kErrRankRetry) exact64 = true;
-    if (h.err & kErrBucketCap) {
-      // floor(delta_max) + 2 exceeds the start-bucket table: grow it, redo.
-      const size_t need = (size_t)h.A + 2;
-      cudaFree(g->d_bptr);
-      cudaFree(g->d_rcur);
-      cudaFree(g->d_acnt);
-      g->d_bptr = nullptr;
-      g->d_rcur = nullptr;
-      g->d_acnt = nullptr;
-      g->bptr_cap = 0;
-      if (cudaMalloc(&g->d_bptr, need * sizeof(int)) != cudaSuccess ||
-          cudaMalloc(&g->d_rcur, need * sizeof(u32)) != cudaSuccess ||
-          cudaMalloc(&g->d_acnt, need * sizeof(u32)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(LDD_ERR_OOM, "start-bucket table of %zu entries", need);
-      }
-      g->bptr_cap = (u32)need;
-      g->acnt_dirty = true;  // cleared by the next fast-path attempt
-    }
-  }
-  if (h.err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
-  if (h.err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");
-  if (h.err & kErrTimeout) return fail(LDD_ERR_TIMEOUT, "a device-side wait ran out");
-  if (h.err) return fail(LDD_ERR_CUDA, "device error bits 0x%x", h.err);
-
+  int launches = 0;
+  const int rc = decompose_on_device(g, d_shift, center, dist, &launches);
+  if (rc != LDD_OK) return rc;
   if (!dev_c) CUDA_TRY(cudaMemcpyAsync(out_center, center, n * 4, cudaMemcpyDeviceToHost, s));
   if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, n * 4, cudaMemcpyDeviceToHost, s));
   record(g, 5);
   CUDA_TRY(cudaStreamSynchronize(s));
-
   ldd_stats& st = g->stats;
-  st.max_floor_shift = h.A;
-  st.exact_rank = exact64 ? 1 : 0;
-  st.rounds = h.rounds;
-  st.last_level = h.last_level;
-  st.items = (int64_t)h.items;
-  st.edges = (int64_t)h.edges;
-  st.pull_rounds = h.pull_rounds;
-  st.push_arcs = (int64_t)h.push_arcs;
-  st.pull_arcs = (int64_t)h.pull_arcs;
-  st.pull_vertices = (int64_t)h.pull_verts;
   st.launches = launches;
   st.ms_h2d = dev_in ? 0.f : elapsed(g, 0, 1);
-  st.ms_rank = elapsed(g, 1, 2);
-  st.ms_bfs = elapsed(g, 2, 3);
-  st.ms_finalize = elapsed(g, 3, 4);
   st.ms_d2h = (dev_c && dev_d) ? 0.f : elapsed(g, 4, 5);
   st.ms_total = elapsed(g, 0, 5);
+  return LDD_OK;
+}
+
+int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* const* shifts,
+                        int32_t* const* out_center, int32_t* const* out_dist, int64_t* out_cut) {
+  g_last_error[0] = 0;
+  if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  if (k < 0) return fail(LDD_ERR_ARG, "k = %d is negative", k);
+  if (k == 0) return LDD_OK;
+  if (!betas || !shifts || !out_center || !out_dist)
+    return fail(LDD_ERR_ARG, "NULL betas, shifts or output array");
+  for (int i = 0; i < k; ++i) {
+    if (!(betas[i] > 0.0) || isinf(betas[i]))
+      return fail(LDD_ERR_ARG, "betas[%d] must be finite and > 0", i);
+    if (g->n > 0 && (!shifts[i] || !out_center[i] || !out_dist[i]))
+      return fail(LDD_ERR_ARG, "NULL shifts[%d] or output %d", i, i);
+  }
+  if (out_cut)
+    for (int i = 0; i < k; ++i) out_cut[i] = 0;
+  if (g->n == 0) return LDD_OK;
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
+  int rc = setup_batch(g);
+  if (rc != LDD_OK) return rc;
+  const size_t n = (size_t)g->n, slot_bytes = align_up(8 * n, 256);
+  double* d_in[2] = {(double*)g->batch_arena,
+                     (double*)((char*)g->batch_arena + slot_bytes)};
+  int* d_c[2] = {(int*)((char*)g->batch_arena + 2 * slot_bytes),
+                 (int*)((char*)g->batch_arena + 3 * slot_bytes)};
+  int* d_d[2] = {d_c[0] + n, d_c[1] + n};
+  cudaStream_t s = g->stream;
+  // slot j's shift buffer is free once the decomposition that read it is done
+  // (ev_used) and its output buffers once their download is done (ev_out)
+  auto upload = [&](int i) -> int {
+    if (is_device_ptr(shifts[i])) return LDD_OK;
+    const int j = i & 1;
+    CUDA_TRY(cudaStreamWaitEvent(g->copy_in, g->ev_used[j], 0));
+    CUDA_TRY(cudaMemcpyAsync(d_in[j], shifts[i], n * 8, cudaMemcpyHostToDevice, g->copy_in));
+    CUDA_TRY(cudaEventRecord(g->ev_in[j], g->copy_in));
+    return LDD_OK;
+  };
+  for (int j = 0; j < 2; ++j) {  // a fresh pipeline: nothing in flight
+    CUDA_TRY(cudaEventRecord(g->ev_used[j], s));
+    CUDA_TRY(cudaEventRecord(g->ev_out[j], g->copy_out));
+  }
+  // on a failure, copies into the caller's buffers must be over before returning
+  auto drain = [&](int status) {
+    cudaStreamSynchronize(g->copy_in);
+    cudaStreamSynchronize(g->copy_out);
+    cudaStreamSynchronize(s);
+    return status;
+  };
+  record(g, 0);
+  if ((rc = upload(0)) != LDD_OK) return drain(rc);
+  int launches = 0;
+  for (int i = 0; i < k; ++i) {
+    const int j = i & 1;
+    if (i + 1 < k && (rc = upload(i + 1)) != LDD_OK) return drain(rc);  // overlaps decomposition i
+    const bool dev_in = is_device_ptr(shifts[i]);
+    const bool dev_c = is_device_ptr(out_center[i]), dev_d = is_device_ptr(out_dist[i]);
+    if (!dev_in) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_in[j], 0));
+    if (!dev_c || !dev_d) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_out[j], 0));
+    int* center = dev_c ? out_center[i] : d_c[j];
+    int* dist = dev_d ? out_dist[i] : d_d[j];
+    int l = 0;
+    if ((rc = decompose_on_device(g, dev_in ? shifts[i] : d_in[j], center, dist, &l)) != LDD_OK)
+      return drain(rc);
+    launches += l;
+    if (out_cut && (rc = cut_on_device(g, center, &out_cut[i])) != LDD_OK) return drain(rc);
+    CUDA_TRY(cudaEventRecord(g->ev_used[j], s));
+    if (!dev_c || !dev_d) {  // download overlaps decomposition i + 1
+      CUDA_TRY(cudaStreamWaitEvent(g->copy_out, g->ev_used[j], 0));
+      if (!dev_c)
+        CUDA_TRY(cudaMemcpyAsync(out_center[i], center, n * 4, cudaMemcpyDeviceToHost, g->copy_out));
+      if (!dev_d)
+        CUDA_TRY(cudaMemcpyAsync(out_dist[i], dist, n * 4, cudaMemcpyDeviceToHost, g->copy_out));
+      CUDA_TRY(cudaEventRecord(g->ev_out[j], g->copy_out));
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->copy_out));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  g->stats.launches = launches;
+  g->stats.ms_h2d = -1.f;  // overlapped: not attributable
+  g->stats.ms_d2h = -1.f;
+  g->stats.ms_total = -1.f;
   return LDD_OK;
 }
 
@@ -751,26 +905,13 @@ int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut) {
   if (!center) return fail(LDD_ERR_ARG, "center is NULL");
   DeviceGuard dg(g->device);
   if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
-  cudaStream_t s = g->stream;
-  record(g, 6);
   const int* d_center = center;
   if (!is_device_ptr(center)) {
-    CUDA_TRY(cudaMemcpyAsync(g->d_center, center, (size_t)g->n * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(g->d_center, center, (size_t)g->n * 4, cudaMemcpyHostToDevice,
+                             g->stream));
     d_center = g->d_center;
   }
-  CUDA_TRY(cudaMemsetAsync(&g->d_ctl->cut, 0, sizeof(u64), s));
-  const int l = launch_cut(g->d_up, g->m_up, d_center, g->d_hot, g->n_hot, g->d_hot_center,
-                           &g->d_ctl->cut, g->num_sms, s);
-  CUDA_TRY(cudaMemcpyAsync(g->h_hdr + 128, &g->d_ctl->cut, sizeof(u64), cudaMemcpyDeviceToHost, s));
-  record(g, 7);
-  CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaStreamSynchronize(s));
-  u64 cut;
-  memcpy(&cut, g->h_hdr + 128, sizeof(cut));
-  *out_cut = (int64_t)cut;
-  g->stats.cut_launches = l;
-  g->stats.ms_cut = elapsed(g, 6, 7);
-  return LDD_OK;
+  return cut_on_device(g, d_center, out_cut);
 }
 
 }  // extern "C"

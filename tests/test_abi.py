@@ -48,6 +48,8 @@ def test_argument_errors_need_no_device(ldd):
                                      ctypes.c_int, ctypes.c_void_p]
     assert lib.ldd_decompose(None, 0.1, None, None, None) == ldd.LDD_ERR_ARG
     assert lib.ldd_cut_edges(None, None, None) == ldd.LDD_ERR_ARG
+    lib.ldd_decompose_batch.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5
+    assert lib.ldd_decompose_batch(None, 1, None, None, None, None, None) == ldd.LDD_ERR_ARG
     assert lib.ldd_set_stream(None, None) == ldd.LDD_ERR_ARG
     out = ctypes.c_void_p()
     rp = np.zeros(4, dtype=np.int32)

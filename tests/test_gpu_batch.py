@@ -1,0 +1,99 @@
+"""ldd_decompose_batch: k pipelined decompositions must give exactly what k
+separate ldd_decompose + ldd_cut_edges calls give, whatever mix of host and
+device buffers, and stop cleanly at a failing item."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import ldd_gen as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _pinned(a: np.ndarray) -> torch.Tensor:
+    t = torch.empty(a.shape, dtype=torch.from_numpy(a).dtype, pin_memory=True)
+    t.copy_(torch.from_numpy(a))
+    return t
+
+
+def test_batch_matches_single_calls_and_oracle(ldd, cuda):
+    G = gen.rmat(13)
+    betas = [0.02, 0.1, 0.5, 0.1, 1.0]
+    shifts = [gen.shifts(G.n, b, 100 + i) for i, b in enumerate(betas)]
+    # mixed placement: pinned host, device, pageable host
+    sh = [_pinned(shifts[0]), torch.from_numpy(shifts[1]).to(cuda), shifts[2],
+          _pinned(shifts[3]), torch.from_numpy(shifts[4]).to(cuda)]
+    cen = [torch.empty(G.n, dtype=torch.int32, pin_memory=True),
+           torch.empty(G.n, dtype=torch.int32, device=cuda),
+           np.empty(G.n, dtype=np.int32),
+           torch.empty(G.n, dtype=torch.int32, device=cuda),
+           torch.empty(G.n, dtype=torch.int32, pin_memory=True)]
+    dis = [torch.empty(G.n, dtype=torch.int32, pin_memory=True),
+           np.empty(G.n, dtype=np.int32),
+           torch.empty(G.n, dtype=torch.int32, device=cuda),
+           torch.empty(G.n, dtype=torch.int32, device=cuda),
+           torch.empty(G.n, dtype=torch.int32, pin_memory=True)]
+    g = ldd.LddGraph(torch.from_numpy(G.row_ptr).to(cuda), torch.from_numpy(G.col).to(cuda))
+    cuts = g.decompose_batch(betas, sh, cen, dis)
+    as_np = lambda x: x.cpu().numpy() if hasattr(x, "cpu") else x
+    for i, b in enumerate(betas):
+        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts[i])
+        assert np.array_equal(as_np(cen[i]), oc), f"item {i}: center"
+        assert np.array_equal(as_np(dis[i]), od), f"item {i}: dist"
+        assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc), f"item {i}: cut"
+    # the batch leaves the graph usable for single calls, and a second batch agrees
+    c1 = np.empty(G.n, dtype=np.int32)
+    d1 = np.empty(G.n, dtype=np.int32)
+    g.decompose(betas[0], shifts[0], c1, d1)
+    assert np.array_equal(c1, as_np(cen[0]))
+    again = g.decompose_batch(betas[:2], [shifts[0], shifts[1]],
+                              [np.empty(G.n, np.int32) for _ in range(2)],
+                              [np.empty(G.n, np.int32) for _ in range(2)])
+    assert again == cuts[:2]
+    g.close()
+
+
+def test_batch_with_fallback_items(ldd, cuda):
+    """Items that need the exact rank path or a larger start-bucket table
+    inside a pipelined batch."""
+    G = gen.grid2d(40, 30)
+    rng = np.random.default_rng(9)
+    crowded = rng.random(G.n) * 2.0 ** -33 + rng.integers(0, 3, G.n)  # exact path
+    huge = gen.shifts(G.n, 0.1, 3)
+    huge[7] = 5000.5                                                    # A + 2 > n + 2
+    normal = gen.shifts(G.n, 0.1, 4)
+    items = [normal, crowded, huge, normal]
+    cen = [np.empty(G.n, np.int32) for _ in items]
+    dis = [np.empty(G.n, np.int32) for _ in items]
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    cuts = g.decompose_batch([0.1] * 4, items, cen, dis)
+    for i, shifts in enumerate(items):
+        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts)
+        assert np.array_equal(cen[i], oc) and np.array_equal(dis[i], od), f"item {i}"
+        assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
+    g.close()
+
+
+def test_batch_stops_at_a_bad_item(ldd, cuda):
+    G = gen.grid2d(20, 20)
+    good = gen.shifts(G.n, 0.2, 1)
+    bad = good.copy()
+    bad[5] = -1.0
+    cen = [np.full(G.n, -7, np.int32) for _ in range(3)]
+    dis = [np.full(G.n, -7, np.int32) for _ in range(3)]
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    with pytest.raises(ldd.LddError) as e:
+        g.decompose_batch([0.2] * 3, [good, bad, good], cen, dis)
+    assert e.value.status == ldd.LDD_ERR_ARG
+    oc, od = oracle.oracle_ldd(G.row_ptr, G.col, good)
+    assert np.array_equal(cen[0], oc) and np.array_equal(dis[0], od)  # before the failure
+    with pytest.raises(ldd.LddError):
+        g.decompose_batch([0.2, float("nan")], [good, good], cen[:2], dis[:2])
+    assert g.decompose_batch([], [], [], []) == []
+    # still usable
+    assert g.decompose_batch([0.2], [good], cen[:1], dis[:1]) == [
+        oracle.oracle_cut_edges(G.row_ptr, G.col, oc)]
+    g.close()
