@@ -126,6 +126,51 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
                         int32_t* const* out_center, int32_t* const* out_dist, int64_t* out_cut);
 
 /*
+ * ldd_create_union -- one graph object for a batch: the disjoint union of k
+ * graphs (the members), so that one call decomposes all of them.  Algorithm 2
+ * never assigns a vertex to a center at infinite distance, so on a disjoint
+ * union it decomposes every member independently with that member's own
+ * shifts; ldd_union_decompose returns exactly what k ldd_decompose calls
+ * would.  A member may appear several times (k shift vectors of one graph, as
+ * tree-embedding callers draw them, Section 1).
+ *   k        number of members, >= 1.
+ *   members  k graphs from ldd_create_graph, on one device (unions are not
+ *            accepted as members).  Their tables are copied on the device;
+ *            the members may be destroyed after the call returns.
+ *   out      receives the union handle.
+ * Limits: the sum of the members' vertex counts, each rounded up to a
+ * multiple of 32, must be < 2^30, and the sum of their arc counts < 2^31
+ * (else LDD_ERR_RANGE).  ldd_decompose, ldd_decompose_batch and
+ * ldd_cut_edges reject a union (LDD_ERR_ARG); ldd_set_stream, ldd_set_timing,
+ * ldd_get_stats and ldd_destroy_graph work as for any graph.
+ */
+int ldd_create_union(int k, ldd_graph* const* members, ldd_graph** out);
+
+/* ldd_union_size -- number of members and total = n_0 + ... + n_{k-1} (the
+ * length of a union's shift and output arrays); either pointer may be NULL. */
+int ldd_union_size(const ldd_graph* u, int32_t* out_k, int64_t* out_total);
+
+/*
+ * ldd_union_decompose -- decompose every member of a union in one pass
+ * (Algorithm 2 via Algorithm 1 / Section 4 on the union: one rank of all
+ * shifts, one persistent round loop over every member's frontier, one
+ * finalize), and optionally count each member's cut edges (Definition 1.1).
+ * Arrays use the caller layout: member s's n_s entries at offset
+ * n_0 + ... + n_{s-1}, in member order.
+ *   betas       double[k] on the host: each member's beta (finite, > 0;
+ *               checked, not used, as in ldd_decompose).
+ *   shifts      double[total] (host or device): member s's shifts, each as
+ *               in ldd_decompose.
+ *   out_center  int32[total] (host or device): member-local center ids.
+ *   out_dist    int32[total] (host or device): hop distances.
+ *   out_cut     NULL, or int64[k] on the host: member s's cut count.
+ * Results are identical to k separate ldd_decompose / ldd_cut_edges calls.
+ * Errors as in ldd_decompose; a bad shift in any member fails the whole call.
+ */
+int ldd_union_decompose(ldd_graph* u, const double* betas, const double* shifts,
+                        int32_t* out_center, int32_t* out_dist, int64_t* out_cut);
+
+/*
  * ldd_cut_edges_noalloc -- the same count as ldd_cut_edges, for callers that
  * must not allocate device memory when they ask for it: for example a process
  * whose framework allocator owns the whole device memory pool, where a foreign
@@ -199,10 +244,29 @@ typedef struct {
   float ms_d2h;           /* outputs device -> host (0 if device outputs) */
   float ms_total;         /* whole ldd_decompose on the stream */
   float ms_cut;           /* whole ldd_cut_edges on the stream */
+  float ms_replay;        /* the replayed CUDA graph (rank .. finalize), when replayed */
+  int32_t replayed;       /* 1: the last decomposition ran as a graph replay */
 } ldd_stats;
 
 int ldd_get_stats(const ldd_graph* g, ldd_stats* out);
 int ldd_set_timing(ldd_graph* g, int enable);
+
+/*
+ * ldd_set_graph_replay -- enable (1) or disable (0) CUDA-graph replay of the
+ * decomposition on g (a plain graph or a union).  Once enabled, the first
+ * call runs as usual and the next one captures the fast path -- every kernel
+ * from the control-block reset (a union's shift spread included) through
+ * finalize, a union's cut counts when asked for, and the status copy to the
+ * host -- into a CUDA graph on an internal stream; later calls copy their
+ * shifts into the library's input buffer, replay that graph on g's stream
+ * (one launch instead of about a dozen), and copy the outputs out of the
+ * library's buffers.  Results are identical.  Calls that need the exact rank
+ * path or a larger start-bucket table run the regular path instead, and a
+ * capture the driver refuses leaves g on the regular path for good (until
+ * replay is enabled again); ldd_get_stats' replayed field tells which ran.
+ * Disabling frees the captured graphs.
+ */
+int ldd_set_graph_replay(ldd_graph* g, int enable);
 
 /*
  * ldd_get_round_profile -- diagnostic: per-round timestamps of the last BFS.

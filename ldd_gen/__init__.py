@@ -206,6 +206,51 @@ WORKLOADS = {
     "rmat20": dict(graph=("rmat", 20, 16, 0.57, 0.19, 0.19, 7), betas=(0.02, 0.1, 0.5), shift_seed=1),
 }
 
+# Batched workloads (one union decomposition per step):
+#  rgg_batch_1024: 1,024 random geometric graphs in the unit square, n uniform
+#    on [1,000, 200,000], mean degree 8, beta uniform on [0.02, 0.5), graph and
+#    shift seed 11 + i (batch_members).
+#  rmat20_seeds_64: 64 shift vectors (seeds 1 .. 64) of one R-MAT scale-20
+#    graph (the scale-22 parameters, seed 7) at beta 0.1.
+BATCH_WORKLOADS = {
+    "rgg_batch_1024": dict(kind="rgg", count=1024, n_lo=1000, n_hi=200000, beta_lo=0.02,
+                           beta_hi=0.5, master_seed=11),
+    "rmat20_seeds_64": dict(kind="seeds", graph=("rmat", 20, 16, 0.57, 0.19, 0.19, 7),
+                            copies=64, beta=0.1, first_seed=1),
+}
+
+
+def batch_members(count: int, n_lo: int, n_hi: int, beta_lo: float, beta_hi: float,
+                  master_seed: int):
+    """Per-member (n, beta, graph_seed, shift_seed) of a batch of random graphs:
+    n uniform on [n_lo, n_hi] and beta uniform on [beta_lo, beta_hi), both
+    from Philox4x32-10 with key master_seed and counter (i, 0, 3, 0) (words 0-1
+    give n, words 2-3 beta, each as a 53-bit uniform); graph seed and shift
+    seed are master_seed + i."""
+    w = philox_stream(master_seed, 0, count, 3, 0).astype(np.uint64)
+    u1 = ((w[:, 0] << np.uint64(32)) | w[:, 1]) >> np.uint64(11)
+    u2 = ((w[:, 2] << np.uint64(32)) | w[:, 3]) >> np.uint64(11)
+    u1 = u1.astype(np.float64) * 2.0 ** -53
+    u2 = u2.astype(np.float64) * 2.0 ** -53
+    span = n_hi - n_lo + 1
+    out = []
+    for i in range(count):
+        n = n_lo + min(int(u1[i] * span), span - 1)
+        beta = beta_lo + (beta_hi - beta_lo) * float(u2[i])
+        out.append((n, beta, master_seed + i, master_seed + i))
+    return out
+
+
+def rgg_batch(count: int = 1024, n_lo: int = 1000, n_hi: int = 200000, beta_lo: float = 0.02,
+              beta_hi: float = 0.5, master_seed: int = 11, mean_degree: float = 8.0):
+    """A batch of random geometric graphs with their own beta and shifts:
+    list of (CSR, beta, shifts)."""
+    out = []
+    for n, beta, gseed, sseed in batch_members(count, n_lo, n_hi, beta_lo, beta_hi, master_seed):
+        G = rgg(n, gseed, mean_degree)
+        out.append((G, beta, shifts(n, beta, sseed)))
+    return out
+
 
 def make_graph(spec) -> CSR:
     kind = spec[0]

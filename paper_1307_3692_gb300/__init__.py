@@ -25,6 +25,7 @@ __all__ = [
     "LddError", "LddGraph", "ldd_create_graph", "ldd_decompose", "ldd_cut_edges",
     "ldd_set_stream", "ldd_destroy_graph", "ldd_status_string", "ldd_last_error",
     "ldd_get_stats", "ldd_set_timing", "ldd_cut_edges_noalloc", "ldd_get_round_profile",
+    "ldd_decompose_batch", "ldd_set_graph_replay", "ldd_create_union", "ldd_union_size", "ldd_union_decompose", "LddUnion",
     "library_path", "LDD_OK", "LDD_ERR_ARG",
     "LDD_ERR_GRAPH", "LDD_ERR_RANGE", "LDD_ERR_OOM", "LDD_ERR_CUDA", "LDD_ERR_TIMEOUT",
 ]
@@ -46,7 +47,8 @@ class _Stats(ctypes.Structure):
         "pull_vertices",
         "launches", "cut_launches", "exact_rank")] + [("bfs_grid", ctypes.c_int32), ("bfs_block", ctypes.c_int32)] + [
         (name, ctypes.c_float) for name in (
-            "ms_h2d", "ms_rank", "ms_bfs", "ms_finalize", "ms_d2h", "ms_total", "ms_cut")]
+            "ms_h2d", "ms_rank", "ms_bfs", "ms_finalize", "ms_d2h", "ms_total", "ms_cut",
+            "ms_replay")] + [("replayed", ctypes.c_int32)]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -56,6 +58,12 @@ _lib.ldd_decompose.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.ldd_decompose.restype = ctypes.c_int
 _lib.ldd_decompose_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.ldd_decompose_batch.restype = ctypes.c_int
+_lib.ldd_create_union.argtypes = [ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_lib.ldd_create_union.restype = ctypes.c_int
+_lib.ldd_union_size.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]
+_lib.ldd_union_size.restype = ctypes.c_int
+_lib.ldd_union_decompose.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.ldd_union_decompose.restype = ctypes.c_int
 _lib.ldd_cut_edges.argtypes = [_vp, _vp, ctypes.POINTER(_i64)]
 _lib.ldd_cut_edges.restype = ctypes.c_int
 _lib.ldd_cut_edges_noalloc.argtypes = [_i32, _i64, _vp, _vp, _vp, _vp, _vp]
@@ -74,6 +82,8 @@ _lib.ldd_get_round_profile.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINT
 _lib.ldd_get_round_profile.restype = ctypes.c_int
 _lib.ldd_set_timing.argtypes = [_vp, ctypes.c_int]
 _lib.ldd_set_timing.restype = ctypes.c_int
+_lib.ldd_set_graph_replay.argtypes = [_vp, ctypes.c_int]
+_lib.ldd_set_graph_replay.restype = ctypes.c_int
 
 
 def library_path() -> str:
@@ -157,6 +167,37 @@ def ldd_decompose_batch(g: int, betas, shifts, out_center, out_dist, n: int | No
     return [int(cuts[i]) for i in range(k)] if want_cut else None
 
 
+def ldd_create_union(members) -> int:
+    """Handle of the disjoint union of the member graphs (handles or LddGraph)."""
+    hs = [getattr(m, "handle", m) for m in members]
+    arr = (_vp * max(len(hs), 1))(*hs)
+    out = _vp()
+    _check(_lib.ldd_create_union(len(hs), arr, ctypes.byref(out)), "ldd_create_union")
+    return int(out.value)
+
+
+def ldd_union_size(u: int) -> tuple[int, int]:
+    """(k, total) of a union."""
+    k, total = _i32(0), _i64(0)
+    _check(_lib.ldd_union_size(u, ctypes.byref(k), ctypes.byref(total)), "ldd_union_size")
+    return int(k.value), int(total.value)
+
+
+def ldd_union_decompose(u: int, betas, shifts, out_center, out_dist, want_cut: bool = True):
+    """Every member of a union in one pass (include/ldd.h); returns the k cut
+    counts (or None without want_cut)."""
+    k, total = ldd_union_size(u)
+    if len(betas) != k:
+        raise ValueError(f"{len(betas)} betas for {k} members")
+    b = (ctypes.c_double * k)(*[float(x) for x in betas])
+    cuts = (_i64 * k)()
+    _check(_lib.ldd_union_decompose(u, b, _addr(shifts, "f64", total, "shifts"),
+                                    _addr(out_center, "i32", total, "out_center"),
+                                    _addr(out_dist, "i32", total, "out_dist"),
+                                    cuts if want_cut else None), "ldd_union_decompose")
+    return [int(cuts[i]) for i in range(k)] if want_cut else None
+
+
 def ldd_cut_edges(g: int, center, n: int | None = None) -> int:
     out = _i64(0)
     _check(_lib.ldd_cut_edges(g, _addr(center, "i32", n, "center"), ctypes.byref(out)),
@@ -188,6 +229,10 @@ def ldd_destroy_graph(g: int) -> None:
 
 def ldd_set_timing(g: int, enable: bool) -> None:
     _check(_lib.ldd_set_timing(g, int(bool(enable))), "ldd_set_timing")
+
+
+def ldd_set_graph_replay(g: int, enable: bool) -> None:
+    _check(_lib.ldd_set_graph_replay(g, int(bool(enable))), "ldd_set_graph_replay")
 
 
 def ldd_get_round_profile(g: int, cap: int = 256):
@@ -232,6 +277,9 @@ class LddGraph:
     def set_timing(self, enable: bool) -> None:
         ldd_set_timing(self.handle, enable)
 
+    def set_graph_replay(self, enable: bool) -> None:
+        ldd_set_graph_replay(self.handle, enable)
+
     def stats(self) -> dict:
         return ldd_get_stats(self.handle)
 
@@ -248,3 +296,25 @@ class LddGraph:
             self.close()
         except Exception:
             pass
+
+
+class LddUnion(LddGraph):
+    """Owns a union handle (ldd_create_union): k member graphs decomposed in
+    one pass.  ``offsets[s]`` is member s's first entry in the caller layout."""
+
+    def __init__(self, members):
+        self.handle = ldd_create_union(members)
+        self.k, self.total = ldd_union_size(self.handle)
+        ns = [int(getattr(m, "n")) for m in members] if all(hasattr(m, "n") for m in members) \
+            else None
+        self.offsets = None if ns is None else [sum(ns[:i]) for i in range(len(ns) + 1)]
+        self.n = self.total
+
+    def decompose(self, betas, shifts, out_center, out_dist, want_cut: bool = True):
+        return ldd_union_decompose(self.handle, betas, shifts, out_center, out_dist, want_cut)
+
+    def decompose_batch(self, *a, **kw):
+        raise TypeError("a union is decomposed with decompose()")
+
+    def cut_edges(self, center) -> int:
+        raise TypeError("a union's cut counts come from decompose()")

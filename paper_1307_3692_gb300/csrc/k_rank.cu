@@ -25,9 +25,17 @@
 // exact path: a stable LSD radix sort of the order-preserving bits of f
 // (8 "onesweep" passes of 8 bits) over all vertices.
 //
+// Batches (disjoint unions of member graphs, k_union.cu): every member's
+// floors are lifted by one integer, lift_s = max_t A_t - A_s, so that each
+// member's own largest shift starts at round 0 and the members' rounds run in
+// step.  A constant added to every level of one member changes no comparison
+// inside that member, and members never compete.
+//
 // Start buckets: a counting sort by R_u (histogram while the keys are built,
 // an exclusive scan that is bptr, and a scatter in which each CTA reserves its
 // range of every group with one atomic).
+#include <algorithm>
+
 #include "ldd_internal.cuh"
 
 namespace ldd {
@@ -152,7 +160,9 @@ __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta
                                                 const u32* __restrict__ solo,
                                                 const u32* __restrict__ excl, u32 n, int B,
                                                 u32* __restrict__ cnt, ulonglong2* __restrict__ slots,
-                                                u32* acnt, u32 cap, Control* ctl) {
+                                                u32* acnt, u32 cap,
+                                                const u32* __restrict__ wmem,
+                                                const int* __restrict__ lift, Control* ctl) {
   __shared__ u32 sh[kRBins];
   const u32 tid = threadIdx.x, lane = tid & 31;
   for (u32 i = tid; i < kRBins; i += blockDim.x) sh[i] = 0;
@@ -181,6 +191,7 @@ __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta
       if (u < n) {
         u64 fb;
         split_bits(d[k], err, fl[k], fb);
+        if (lift) fl[k] += __ldg(lift + __ldg(wmem + (u >> 5)));
         amax = max(amax, fl[k]);
         if (!((__ldg(solo + (u >> 5)) >> (u & 31)) & 1u)) {
           const u32 out = (__ldg(excl + (u >> 5)) >> (u & 31)) & 1u;
@@ -401,7 +412,9 @@ __global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start,
 // ---------------------------------------------------------------- exact path
 __global__ void __launch_bounds__(256) k_split64(const double* __restrict__ delta, u32 n,
                                                  int* __restrict__ a_out, u64* __restrict__ kout,
-                                                 u32* __restrict__ vout, Control* ctl) {
+                                                 u32* __restrict__ vout,
+                                                 const u32* __restrict__ wmem,
+                                                 const int* __restrict__ lift, Control* ctl) {
   __shared__ u32 sh[kFracDigits][256];
   const u32 tid = threadIdx.x, lane = tid & 31;
   for (u32 i = tid; i < kFracDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
@@ -417,6 +430,7 @@ __global__ void __launch_bounds__(256) k_split64(const double* __restrict__ delt
       int a;
       u64 fb;
       split_bits(delta[idx], err, a, fb);
+      if (lift) a += __ldg(lift + __ldg(wmem + (idx >> 5)));
       key = ~fb;  // ascending key: f descending
       a_out[idx] = a;
       kout[idx] = key;
@@ -889,6 +903,12 @@ u32 fraction_bucket_bits(u32 n) {
   return b;
 }
 
+size_t rank_status_words(u32 n, u32 bptr_cap) {
+  const u32 nbkt = 1u << fraction_bucket_bits(n);
+  return std::max<size_t>((nbkt + 1 + kScanTile - 1) / kScanTile,
+                          ((size_t)bptr_cap + kScanTile - 1) / kScanTile);
+}
+
 size_t fraction_slot_bytes(u32 n) {
   return ((size_t)1 << fraction_bucket_bits(n)) * kSlotCap * sizeof(ulonglong2);
 }
@@ -909,7 +929,7 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
     if (r.acnt_dirty) cudaMemsetAsync(r.acnt, 0, (size_t)r.bptr_cap * 4, s);
     cudaMemsetAsync(cnt, 0, (size_t)(nbkt + 1) * 4, s);
     k_bplace<<<grid_stride_blocks((n + kPlaceIpt - 1) / kPlaceIpt, r.num_sms), 256, 0, s>>>(
-        r.shift, r.solo, r.excl, n, (int)B, cnt, slots, r.acnt, r.bptr_cap, ctl);
+        r.shift, r.solo, r.excl, n, (int)B, cnt, slots, r.acnt, r.bptr_cap, r.wmem, r.lift, ctl);
     k_scan_excl<<<(nbkt + 1 + kScanTile - 1) / kScanTile, kScanThreads, 0, s>>>(
         cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, ctl);
     k_round_counts<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.acnt, rcnt,
@@ -926,7 +946,7 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
   // start-round counting sort (groups in any order inside)
   u32* rank = reinterpret_cast<u32*>(r.k1) + n;  // k1 holds 2 max(n, 64) 32-bit words
   allow_sort_smem();
-  k_split64<<<gs, 256, 0, s>>>(r.shift, n, r.a, r.k0, r.v0, ctl);
+  k_split64<<<gs, 256, 0, s>>>(r.shift, n, r.a, r.k0, r.v0, r.wmem, r.lift, ctl);
   k_scan_digits<<<1, 256, 0, s>>>(&ctl->hist_f[0][0], &ctl->off_f[0][0], &ctl->mask_f,
                                   kFracDigits, n);
   launches += 2;

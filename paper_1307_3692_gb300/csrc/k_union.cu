@@ -1,0 +1,302 @@
+// Batches as disjoint unions (Miller, Peng, Xu 2013, Algorithm 2).
+//
+// Algorithm 2 assigns every vertex to the argmin over u of dist(u, v) - delta_u,
+// and a vertex of another graph is at infinite distance.  So the decomposition
+// of a disjoint union G_0 + G_1 + ... with the concatenated shifts is, member
+// by member, the decomposition of each G_s with its own shifts: the integer
+// levels of one member all move by the same constant (floor(delta_max) of the
+// union instead of the member's), and the fraction ranks of one member keep
+// their relative order (union ids preserve the members' id order).  A batch
+// of graphs -- or of shift vectors of one graph -- therefore runs as one
+// decomposition: one persistent BFS whose frontier holds every member's
+// frontier, one rank, one finalize.
+//
+// Layout of the union.  Member s occupies union vertices
+// [voff_s, voff_s + n_s) followed by pad_s = roundup(n_s, 32) - n_s isolated
+// pad vertices, so that every member starts on a 32-vertex boundary and its
+// per-vertex bitmask words are copied whole.  Arcs, cut-list entries and
+// small-component records are concatenated in member order with their vertex
+// ids moved by voff_s.  Outputs use the caller's layout: member s's n_s
+// entries at ooff_s = n_0 + ... + n_{s-1}, with member-local ids.
+//
+// Every table is built by one launch (k_union_concat, blockIdx.y = table);
+// an element finds its member by a binary search over the table's member
+// offsets.
+//
+// Level alignment.  With one floor(delta_max) for the whole union, a member
+// whose own largest shift is small would start late, and until then its
+// unsettled vertices would sit in every bottom-up scan.  Each call therefore
+// lifts member s's floors by max_t A_t - A_s, A_s the largest floor among
+// the member's vertices that the round loop handles (k_union_spread,
+// k_union_lift; applied by the rank's split), so that every member's first
+// start is at round 0 and the members' frontiers grow and shrink together.
+#include "ldd_internal.cuh"
+
+namespace ldd {
+
+namespace {
+
+// Member s of off[0 .. k]: the last s with off[s] <= x (x < off[k]).  With
+// empty members (equal offsets) this is the non-empty one holding x.
+__device__ __forceinline__ u32 member_of(const u32* __restrict__ off, u32 k, u32 x) {
+  u32 lo = 0, hi = k;  // off[lo] <= x < off[hi]
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_union_concat(const UnionMember* __restrict__ mem,
+                                                      UnionOffsets off, u32 k, UnionTables t) {
+  const u32 stride = gridDim.x * blockDim.x;
+  const u32 first = blockIdx.x * blockDim.x + threadIdx.x;
+  switch (blockIdx.y) {
+    case 0: {  // row_ptr: member rows moved by eoff; pads are empty rows
+      const u32 N = off.v[k];
+      for (u32 u = first; u <= N; u += stride) {
+        if (u == N) {
+          t.row[N] = (int)off.e[k];
+          continue;
+        }
+        const u32 s = member_of(off.v, k, u);
+        const UnionMember& m = mem[s];
+        const u32 v = u - off.v[s];
+        t.row[u] = (int)(off.e[s] + (v < m.n ? (u32)__ldg(m.row + v) : m.nnz));
+      }
+      break;
+    }
+    case 1: {  // col: neighbour ids moved by voff
+      const u32 E = off.e[k];
+      for (u32 e = first; e < E; e += stride) {
+        const u32 s = member_of(off.e, k, e);
+        t.col[e] = __ldg(mem[s].col + (e - off.e[s])) + (int)off.v[s];
+      }
+      break;
+    }
+    case 2: {  // cut list: hot-table slots resolved to vertex ids, ids moved
+      const u32 M = off.u[k];
+      for (u32 i = first; i < M; i += stride) {
+        const u32 s = member_of(off.u, k, i);
+        const UnionMember& m = mem[s];
+        const int2 p = m.up[i - off.u[s]];
+        const int hot = p.y < 0 ? (int)__ldg(m.hot + (p.y & 0x7fffffff)) : p.y;
+        t.up[i] = make_int2(p.x + (int)off.v[s], hot + (int)off.v[s]);
+      }
+      break;
+    }
+    case 3: {  // exclusion and singleton bitmasks: whole words, pad bits set
+      const u32 W = off.v[k] / 32;
+      for (u32 w = first; w < W; w += stride) {
+        const u32 s = member_of(off.v, k, w * 32);
+        const UnionMember& m = mem[s];
+        const u32 lw = w - off.v[s] / 32;
+        const u32 lo = lw * 32;  // first local vertex of the word
+        const u32 pad = lo + 32 <= m.n ? 0u : (lo >= m.n ? 0xffffffffu : ~0u << (m.n - lo));
+        const u32 ex = lo < m.n ? __ldg(m.excl + lw) : 0u;
+        const u32 so = lo < m.n ? __ldg(m.solo + lw) : 0u;
+        t.excl[w] = ex | pad;
+        t.solo[w] = so | pad;
+      }
+      break;
+    }
+    case 4: {  // small components: member ranges and sizes
+      const u32 C = off.c[k];
+      for (u32 c = first; c < C; c += stride) {
+        const u32 s = member_of(off.c, k, c);
+        const UnionMember& m = mem[s];
+        t.comp_off[c] = __ldg(m.comp_off + (c - off.c[s])) + off.m[s];
+        t.comp_len[c] = __ldg(m.comp_len + (c - off.c[s]));
+      }
+      break;
+    }
+    case 5: {  // small components: member lists and lane adjacency masks
+      const u32 T = off.m[k];
+      for (u32 i = first; i < T; i += stride) {
+        const u32 s = member_of(off.m, k, i);
+        const UnionMember& m = mem[s];
+        t.comp_v[i] = __ldg(m.comp_v + (i - off.m[s])) + off.v[s];
+        t.adj[i] = __ldg(m.adj + (i - off.m[s]));
+      }
+      break;
+    }
+    case 7: {  // member of every 32-vertex word (the rank's floor lift)
+      const u32 W = off.v[k] / 32;
+      for (u32 w = first; w < W; w += stride) t.wmem[w] = member_of(off.v, k, w * 32);
+      break;
+    }
+    case 6: {  // vertices the BFS handles, ascending (when every member lists them)
+      if (!t.active) break;
+      const u32 A = off.a[k];
+      for (u32 i = first; i < A; i += stride) {
+        const u32 s = member_of(off.a, k, i);
+        t.active[i] = __ldg(mem[s].active + (i - off.a[s])) + off.v[s];
+      }
+      break;
+    }
+    default: break;
+  }
+}
+
+// floor(d) of a valid shift (finite, 0 <= d < 2^31), from the bits of d; 0
+// for anything else (the rank's split rejects those shifts).
+__device__ __forceinline__ int floor_of(double d) {
+  const u64 b = (u64)__double_as_longlong(d);
+  const u32 ex = (u32)(b >> 52) & 0x7ffu;
+  if ((b >> 63) || ex < 1023u || ex >= 1023u + 31u) return 0;
+  const u64 M = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  return (int)(M >> (52 - (ex - 1023u)));
+}
+
+// Concatenated input shifts (caller layout) to the union layout (pads get 0),
+// and into amax[s] (zero on entry) the largest floor among member s's vertices
+// that the round loop handles (excl bit clear): isolated vertices and small
+// components never enter the rounds, so they must not set the alignment.  A
+// warp's 32 consecutive union vertices belong to one member (members start on
+// 32-vertex boundaries) and share one excl word, so each warp step ends in
+// one atomicMax.
+__global__ void __launch_bounds__(256) k_union_spread(const double* __restrict__ in,
+                                                      UnionOffsets off, u32 k,
+                                                      const u32* __restrict__ excl,
+                                                      double* __restrict__ out, int* amax) {
+  const u32 N = off.v[k];
+  const u32 lane = threadIdx.x & 31;
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < N; wb += stride) {
+    const u32 u = wb + lane;
+    const u32 s = member_of(off.v, k, wb);
+    const u32 v = u - off.v[s];
+    const u32 n = off.o[s + 1] - off.o[s];
+    const double d = v < n ? __ldcs(in + off.o[s] + v) : 0.0;
+    out[u] = d;
+    int a = ((__ldg(excl + (wb >> 5)) >> lane) & 1u) ? 0 : floor_of(d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if (lane == 0 && a > 0) atomicMax(amax + s, a);
+  }
+}
+
+// lift[s] = max_t amax[t] - amax[s]: every member's largest shift then starts
+// the round loop at round 0.  One CTA.
+__global__ void __launch_bounds__(1024) k_union_lift(const int* __restrict__ amax, u32 k,
+                                                     int* __restrict__ lift) {
+  __shared__ int wmax[32];
+  __shared__ int gmax;
+  int m = 0;
+  for (u32 s = threadIdx.x; s < k; s += blockDim.x) m = max(m, amax[s]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int g = 0;
+    for (u32 w = 0; w < blockDim.x / 32; ++w) g = max(g, wmax[w]);
+    gmax = g;
+  }
+  __syncthreads();
+  for (u32 s = threadIdx.x; s < k; s += blockDim.x) lift[s] = gmax - amax[s];
+}
+
+// Algorithm 1 step 4 in the caller's layout: output i is vertex v of member
+// s, union vertex u = voff_s + v.  Its settled key names the center
+// order[rank] (a union id of the same member); the member-local center id is
+// that minus voff_s, and the hop distance is the key's level minus the
+// center's own level.
+__global__ void __launch_bounds__(256) k_union_finalize(const u64* __restrict__ key,
+                                                        const u32* __restrict__ order,
+                                                        const u32* __restrict__ solo,
+                                                        UnionOffsets off, u32 k,
+                                                        int* __restrict__ center,
+                                                        int* __restrict__ dist, const u32* err) {
+  if (*(volatile const u32*)err != 0u) return;
+  const u32 total = off.o[k], N = off.v[k];
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const u32 s = member_of(off.o, k, i);
+    const u32 v = i - off.o[s], u = off.v[s] + v;
+    if ((__ldg(solo + (u >> 5)) >> (u & 31)) & 1u) {
+      center[i] = (int)v;
+      dist[i] = 0;
+      continue;
+    }
+    const u64 kv = key[u];
+    const u32 c = order[min((u32)kv, N - 1)];
+    const u64 kc = key[c];
+    center[i] = (int)(c - off.v[s]);
+    dist[i] = (int)((u32)(kv >> 32) - (u32)(kc >> 32));
+  }
+}
+
+// Cut count per member (Definition 1.1): the union cut list is cut into
+// chunks of at most kUnionCutChunk edges that never straddle two members;
+// chunk b belongs to member member_of(chunk_off, k, b).  Labels are read in
+// the caller's layout (member-local ids), where union vertex u of member s
+// sits at ooff_s + u - voff_s.
+__global__ void __launch_bounds__(256) k_union_cut(const int2* __restrict__ up,
+                                                   const u32* __restrict__ chunk_off,
+                                                   UnionOffsets off, u32 k,
+                                                   const int* __restrict__ center,
+                                                   unsigned long long* __restrict__ cut) {
+  __shared__ unsigned long long wsum[8];
+  const u32 nchunk = chunk_off[k];
+  for (u32 b = blockIdx.x; b < nchunk; b += gridDim.x) {
+    const u32 s = member_of(chunk_off, k, b);
+    const u32 lo = off.u[s] + (b - chunk_off[s]) * kUnionCutChunk;
+    const u32 hi = min(lo + kUnionCutChunk, off.u[s + 1]);
+    const long long delta = (long long)off.o[s] - (long long)off.v[s];
+    unsigned long long cnt = 0;
+    for (u32 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const int2 e = __ldcs(up + i);
+      cnt += center[e.x + delta] != center[e.y + delta];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tot = 0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += wsum[w];
+      if (tot) atomicAdd(cut + s, tot);
+    }
+    __syncthreads();
+  }
+}
+
+u32 blocks_for(u64 n, int num_sms) {
+  return (u32)max(1ll, min((long long)((n + 255) / 256), (long long)num_sms * 8));
+}
+
+}  // namespace
+
+int launch_union_concat(const UnionMember* mem, const UnionOffsets& off, u32 k,
+                        const UnionTables& t, u64 largest, int num_sms, cudaStream_t s) {
+  k_union_concat<<<dim3(blocks_for(largest + 1, num_sms), 8), 256, 0, s>>>(mem, off, k, t);
+  return 1;
+}
+
+int launch_union_spread(const double* in, const UnionOffsets& off, u32 k, u32 N,
+                        const u32* excl, double* out, int* amax, int* lift, int num_sms,
+                        cudaStream_t s) {
+  cudaMemsetAsync(amax, 0, (size_t)k * sizeof(int), s);
+  k_union_spread<<<blocks_for(N, num_sms), 256, 0, s>>>(in, off, k, excl, out, amax);
+  k_union_lift<<<1, 1024, 0, s>>>(amax, k, lift);
+  return 2;
+}
+
+int launch_union_finalize(const u64* key, const u32* order, const u32* solo,
+                          const UnionOffsets& off, u32 k, u32 total, int* center, int* dist,
+                          const u32* err, int num_sms, cudaStream_t s) {
+  k_union_finalize<<<blocks_for(total, num_sms), 256, 0, s>>>(key, order, solo, off, k, center,
+                                                              dist, err);
+  return 1;
+}
+
+int launch_union_cut(const int2* up, const u32* chunk_off, u32 nchunk, const UnionOffsets& off,
+                     u32 k, const int* center, u64* cut, int num_sms, cudaStream_t s) {
+  if (nchunk == 0) return 0;
+  const u32 g = (u32)min((long long)nchunk, (long long)num_sms * 8);
+  k_union_cut<<<g, 256, 0, s>>>(up, chunk_off, off, k, center,
+                                reinterpret_cast<unsigned long long*>(cut));
+  return 1;
+}
+
+}  // namespace ldd

@@ -154,6 +154,32 @@ struct ldd_graph {
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_out[2] = {};
   void* batch_arena = nullptr;  // two shift slots (8n each) and two output slots (8n each)
+  // disjoint unions (ldd_create_union): member offsets and caller-layout staging
+  struct Union {
+    u32 k = 0;
+    u32 total = 0;                 // n_0 + ... + n_{k-1}: caller-layout length
+    u32 nchunk = 0;                // cut chunks (chunk_off[k])
+    std::vector<u32> h_ooff;       // caller-layout offsets, k + 1
+    std::vector<u32> h_voff;       // union-vertex offsets, k + 1
+    UnionMember* d_mem = nullptr;  // k member views (valid only while building)
+    u32* d_offs = nullptr;         // 8 arrays of k + 1: v, e, u, c, m, a, o, chunk
+    UnionOffsets off{};
+    double* d_shift_in = nullptr;  // [total] caller-layout shifts from the host
+    int* d_out_c = nullptr;        // [total] caller-layout labels (host outputs, cut count)
+    int* d_out_d = nullptr;        // [total]
+    u64* d_cut = nullptr;          // [k]
+    u32* d_wmem = nullptr;         // [N / 32] member of every 32-vertex word
+    int* d_amax = nullptr;         // [k] largest floor of each member, then [k] its lift
+  };
+  Union* uni = nullptr;
+  // captured CUDA graph of one fast-path decomposition (ldd_set_graph_replay)
+  bool replay = false;
+  bool replay_broken = false;        // capture failed once: regular path only
+  int regular_runs = 0;              // regular decompositions so far (capture waits for one)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec[2] = {};     // [with union cut counts]
+  int replay_launches[2] = {};
+  u64* h_cut = nullptr;              // pinned copy of a union's cut counts
   ldd_stats stats;
 };
 
@@ -186,6 +212,21 @@ int free_graph_memory(ldd_graph* g) {
   }
   if (g->copy_in) cudaStreamDestroy(g->copy_in);
   if (g->copy_out) cudaStreamDestroy(g->copy_out);
+  for (auto& x : g->gexec)
+    if (x) cudaGraphExecDestroy(x);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  if (g->h_cut) cudaFreeHost(g->h_cut);
+  if (g->uni) {
+    cudaFree(g->uni->d_mem);
+    cudaFree(g->uni->d_offs);
+    cudaFree(g->uni->d_shift_in);
+    cudaFree(g->uni->d_out_c);
+    cudaFree(g->uni->d_cut);
+    cudaFree(g->uni->d_wmem);
+    cudaFree(g->uni->d_amax);
+    delete g->uni;
+    g->uni = nullptr;
+  }
   return 0;
 }
 
@@ -446,9 +487,42 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
     ++launches;
   }
   record(g, 3);
-  launches += launch_finalize(g->d_key, g->d_order, g->d_solo, (u32)g->n, center, dist,
-                              &g->d_ctl->err, g->num_sms, s);
+  if (g->uni)  // caller layout, member-local ids
+    launches += launch_union_finalize(g->d_key, g->d_order, g->d_solo, g->uni->off, g->uni->k,
+                                      g->uni->total, center, dist, &g->d_ctl->err, g->num_sms, s);
+  else
+    launches += launch_finalize(g->d_key, g->d_order, g->d_solo, (u32)g->n, center, dist,
+                                &g->d_ctl->err, g->num_sms, s);
   return launches;
+}
+
+// Scratch arena, pinned header, events and launch parameters: the part of
+// graph creation that only depends on the sizes and the tables being built.
+int finish_setup(ldd_graph* g) {
+  int rc;
+  if ((rc = alloc_scratch(g)) != LDD_OK) return rc;
+  if (cudaMallocHost(&g->h_hdr, 256) != cudaSuccess)
+    return fail(LDD_ERR_OOM, "pinned host allocation failed");
+  for (auto& e : g->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(LDD_ERR_CUDA, "cudaEventCreate");
+  g->bfs_grid = bfs_grid_size(g->num_sms, &g->bfs_per_sm);
+  if (g->bfs_grid <= 0) return fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed");
+  const u32 per_sm = env_u32("LDD_BFS_BLOCKS_PER_SM", 0);
+  if (per_sm > 0 && (int)per_sm < g->bfs_per_sm) {
+    g->bfs_per_sm = (int)per_sm;
+    g->bfs_grid = g->bfs_per_sm * g->num_sms;
+  }
+  g->spin_limit = env_u32("LDD_SPIN_LIMIT", 1u << 22);
+  g->pull_alpha = env_u32("LDD_PULL_ALPHA", 14);
+  g->pull_beta = env_u32("LDD_PULL_BETA", 24);
+  g->pull_gamma = env_u32("LDD_PULL_GAMMA", 8);
+  g->stats.n = g->n;
+  g->stats.nnz = g->nnz;
+  g->stats.n_active = g->n_active;
+  g->stats.small_components = g->sc.ncomp;
+  g->stats.bfs_grid = g->bfs_grid;
+  g->stats.bfs_block = kBfsThreads;
+  return LDD_OK;
 }
 
 struct Header {  // the control block up to and including the BFS runtime state
@@ -471,18 +545,10 @@ struct Header {  // the control block up to and including the BFS runtime state
 };
 static_assert(sizeof(Header) == kCtlHeaderBytes + kCtlBfsStateBytes, "header layout");
 
-// One decomposition with the shifts already on the device and device
-// outputs, on the graph's stream (events 1 .. 4 when timing): rank and start
-// buckets, the round loop, finalize, with the retries of the fast rank path.
-// Fills the device-side statistics of g->stats.
-int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* dist,
-                        int* launches_out) {
-  cudaStream_t s = g->stream;
-  const size_t n = (size_t)g->n;
-  int launches = 0;
+RankBufs rank_bufs(ldd_graph* g, const double* d_shift) {
   RankBufs rb;
   rb.shift = d_shift;
-  rb.n = (u32)n;
+  rb.n = (u32)g->n;
   rb.num_sms = g->num_sms;
   rb.a = g->d_a;
   rb.k0 = g->d_k[0];
@@ -496,7 +562,55 @@ int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* d
   rb.key = g->d_key;
   rb.excl = g->d_excl;
   rb.solo = g->d_solo;
+  rb.wmem = g->uni ? g->uni->d_wmem : nullptr;
+  rb.lift = g->uni ? g->uni->d_amax + g->uni->k : nullptr;
   rb.ctl = g->d_ctl;
+  rb.bptr = g->d_bptr;
+  rb.rcur = g->d_rcur;
+  rb.acnt = g->d_acnt;
+  rb.acnt_dirty = g->acnt_dirty;
+  rb.bptr_cap = g->bptr_cap;
+  return rb;
+}
+
+void header_stats(ldd_graph* g, const Header& h, bool exact64) {
+  ldd_stats& st = g->stats;
+  st.max_floor_shift = h.A;
+  st.exact_rank = exact64 ? 1 : 0;
+  st.rounds = h.rounds;
+  st.last_level = h.last_level;
+  st.items = (int64_t)h.items;
+  st.edges = (int64_t)h.edges;
+  st.pull_rounds = h.pull_rounds;
+  st.push_arcs = (int64_t)h.push_arcs;
+  st.pull_arcs = (int64_t)h.pull_arcs;
+  st.pull_vertices = (int64_t)h.pull_verts;
+}
+
+int header_error(u32 err) {
+  if (err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
+  if (err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");
+  if (err & kErrTimeout) return fail(LDD_ERR_TIMEOUT, "a device-side wait ran out");
+  return fail(LDD_ERR_CUDA, "device error bits 0x%x", err);
+}
+
+void drop_replay(ldd_graph* g) {
+  for (auto& x : g->gexec)
+    if (x) {
+      cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+}
+
+// One decomposition with the shifts already on the device and device
+// outputs, on the graph's stream (events 1 .. 4 when timing): rank and start
+// buckets, the round loop, finalize, with the retries of the fast rank path.
+// Fills the device-side statistics of g->stats.
+int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* dist,
+                        int* launches_out) {
+  cudaStream_t s = g->stream;
+  int launches = 0;
+  RankBufs rb = rank_bufs(g, d_shift);
   Header h;
   int status = LDD_OK;
   bool exact64 = false;
@@ -508,6 +622,7 @@ int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* d
   record(g, 1);
   for (int attempt = 0; attempt < 4; ++attempt) {
     if (attempt) CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
+    rb = rank_bufs(g, d_shift);
     rb.bptr = g->d_bptr;
     rb.rcur = g->d_rcur;
     rb.acnt = g->d_acnt;
@@ -548,27 +663,138 @@ int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* d
       }
       g->bptr_cap = (u32)need;
       g->acnt_dirty = true;  // cleared by the next fast-path attempt
+      drop_replay(g);        // a captured replay holds the old table
     }
   }
-  if (h.err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
-  if (h.err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");
-  if (h.err & kErrTimeout) return fail(LDD_ERR_TIMEOUT, "a device-side wait ran out");
-  if (h.err) return fail(LDD_ERR_CUDA, "device error bits 0x%x", h.err);
+  if (h.err) return header_error(h.err);
+  header_stats(g, h, exact64);
   ldd_stats& st = g->stats;
-  st.max_floor_shift = h.A;
-  st.exact_rank = exact64 ? 1 : 0;
-  st.rounds = h.rounds;
-  st.last_level = h.last_level;
-  st.items = (int64_t)h.items;
-  st.edges = (int64_t)h.edges;
-  st.pull_rounds = h.pull_rounds;
-  st.push_arcs = (int64_t)h.push_arcs;
-  st.pull_arcs = (int64_t)h.pull_arcs;
-  st.pull_vertices = (int64_t)h.pull_verts;
   st.ms_rank = elapsed(g, 1, 2);
   st.ms_bfs = elapsed(g, 2, 3);
   st.ms_finalize = elapsed(g, 3, 4);
+  st.replayed = 0;
+  ++g->regular_runs;
   *launches_out = launches;
+  return LDD_OK;
+}
+
+// The library-owned outputs a replay writes: caller layout for a union.
+int* replay_center(ldd_graph* g) { return g->uni ? g->uni->d_out_c : g->d_center; }
+int* replay_dist(ldd_graph* g) { return g->uni ? g->uni->d_out_d : g->d_dist; }
+
+// Queues one fast-path decomposition on g->stream with no host synchronisation,
+// as it is captured: control block and look-back status cleared, [a union's
+// shifts spread from the caller layout,] rank with the fixed epochs 1 and 2,
+// BFS, finalize into the library's outputs, [the union's cut counts,] and the
+// header copied to the pinned host block.  Returns kernels queued, or -1.
+int enqueue_fast(ldd_graph* g, bool want_cut) {
+  cudaStream_t s = g->stream;
+  int launches = 0;
+  if (cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s) != cudaSuccess) return -1;
+  const size_t words = rank_status_words((u32)g->n, g->bptr_cap);
+  if (cudaMemsetAsync(g->d_status, 0, words * sizeof(u64), s) != cudaSuccess) return -1;
+  if (g->uni) {
+    ldd_graph::Union& U = *g->uni;
+    launches += launch_union_spread(U.d_shift_in, U.off, U.k, (u32)g->n, g->d_excl, g->d_shift, U.d_amax,
+                                    U.d_amax + U.k, g->num_sms, s);
+  }
+  u32 epoch = 0;  // the two scans run with epochs 1 and 2 on cleared status words
+  RankBufs rb = rank_bufs(g, g->d_shift);
+  rb.epoch = &epoch;
+  rb.acnt_dirty = false;  // cleared before every launch of the replay
+  launches += launch_rank_and_buckets(rb, false, s);
+  int status = LDD_OK;
+  const int l = run_bfs_finalize(g, replay_center(g), replay_dist(g), &status);
+  if (l < 0) return -1;
+  launches += l;
+  if (g->uni && want_cut) {
+    ldd_graph::Union& U = *g->uni;
+    if (cudaMemsetAsync(U.d_cut, 0, (size_t)U.k * 8, s) != cudaSuccess) return -1;
+    launches += launch_union_cut(g->d_up, U.d_offs + 7 * ((size_t)U.k + 1), U.nchunk, U.off, U.k,
+                                 U.d_out_c, U.d_cut, g->num_sms, s);
+    if (cudaMemcpyAsync(g->h_cut, U.d_cut, (size_t)U.k * 8, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+      return -1;
+  }
+  if (cudaMemcpyAsync(g->h_hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return -1;
+  return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+// Captures enqueue_fast into an executable graph (slot: with union cut
+// counts).  A capture that fails marks the graph replay_broken; the regular
+// path then runs.
+void capture_fast(ldd_graph* g, bool want_cut) {
+  const int slot = want_cut ? 1 : 0;
+  if (!g->cap_stream &&
+      cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    g->replay_broken = true;
+    return;
+  }
+  if (g->uni && want_cut && !g->h_cut &&
+      cudaMallocHost(&g->h_cut, std::max<size_t>(g->uni->k, 1) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    g->replay_broken = true;
+    return;
+  }
+  cudaStream_t saved = g->stream;
+  const bool saved_timing = g->timing;
+  g->stream = g->cap_stream;
+  g->timing = false;
+  cudaGraph_t graph = nullptr;
+  int launches = -1;
+  if (cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    launches = enqueue_fast(g, want_cut);
+    if (cudaStreamEndCapture(g->cap_stream, &graph) != cudaSuccess) launches = -1;
+  }
+  g->stream = saved;
+  g->timing = saved_timing;
+  cudaGraphExec_t exec = nullptr;
+  if (launches < 0 || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    g->replay_broken = true;
+    exec = nullptr;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  g->gexec[slot] = exec;
+  g->replay_launches[slot] = launches;
+}
+
+constexpr int kRunRegular = 1;  // replay_fast: take the regular path instead
+
+// One decomposition by graph replay, the shifts already in the library's
+// input buffer (d_shift, or a union's caller-layout d_shift_in).  Returns
+// LDD_OK, an error, or kRunRegular (no capture yet, capture failed, or the
+// fast rank path asked for a retry).
+int replay_fast(ldd_graph* g, bool want_cut, int* launches_out) {
+  if (!g->replay || g->replay_broken || g->regular_runs == 0) return kRunRegular;
+  const int slot = want_cut ? 1 : 0;
+  cudaStream_t s = g->stream;
+  if (g->acnt_dirty) {
+    CUDA_TRY(cudaMemsetAsync(g->d_acnt, 0, (size_t)g->bptr_cap * 4, s));
+    g->acnt_dirty = false;
+  }
+  if (!g->gexec[slot]) capture_fast(g, want_cut);
+  if (!g->gexec[slot]) return kRunRegular;
+  record(g, 1);
+  CUDA_TRY(cudaGraphLaunch(g->gexec[slot], s));
+  record(g, 4);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  Header h;
+  memcpy(&h, g->h_hdr, sizeof(h));
+  if (h.err & (kErrRankRetry | kErrBucketCap)) {
+    g->acnt_dirty = true;  // the counts may be half consumed
+    return kRunRegular;
+  }
+  if (h.err) return header_error(h.err);
+  header_stats(g, h, false);
+  ldd_stats& st = g->stats;
+  st.ms_rank = st.ms_bfs = st.ms_finalize = -1.f;
+  st.ms_replay = elapsed(g, 1, 4);
+  st.replayed = 1;
+  *launches_out = g->replay_launches[slot];
   return LDD_OK;
 }
 
@@ -708,28 +934,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   if ((rc = build_component_tables(g)) != LDD_OK) return bail(rc);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
   if ((rc = build_active_list(g)) != LDD_OK) return bail(rc);
-  if ((rc = alloc_scratch(g)) != LDD_OK) return bail(rc);
-  if (cudaMallocHost(&g->h_hdr, 256) != cudaSuccess)
-    return bail(fail(LDD_ERR_OOM, "pinned host allocation failed"));
-  for (auto& e : g->ev)
-    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(LDD_ERR_CUDA, "cudaEventCreate"));
-  g->bfs_grid = bfs_grid_size(g->num_sms, &g->bfs_per_sm);
-  if (g->bfs_grid <= 0) return bail(fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed"));
-  const u32 per_sm = env_u32("LDD_BFS_BLOCKS_PER_SM", 0);
-  if (per_sm > 0 && (int)per_sm < g->bfs_per_sm) {
-    g->bfs_per_sm = (int)per_sm;
-    g->bfs_grid = g->bfs_per_sm * g->num_sms;
-  }
-  g->spin_limit = env_u32("LDD_SPIN_LIMIT", 1u << 22);
-  g->pull_alpha = env_u32("LDD_PULL_ALPHA", 14);
-  g->pull_beta = env_u32("LDD_PULL_BETA", 24);
-  g->pull_gamma = env_u32("LDD_PULL_GAMMA", 8);
-  g->stats.n = n;
-  g->stats.nnz = nnz;
-  g->stats.n_active = g->n_active;
-  g->stats.small_components = g->sc.ncomp;
-  g->stats.bfs_grid = g->bfs_grid;
-  g->stats.bfs_block = kBfsThreads;
+  if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);
   *out = g;
   return LDD_OK;
 }
@@ -780,6 +985,7 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
                   int32_t* out_dist) {
   g_last_error[0] = 0;
   if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  if (g->uni) return fail(LDD_ERR_ARG, "a union graph is decomposed by ldd_union_decompose");
   if (!(beta > 0.0) || isinf(beta)) return fail(LDD_ERR_ARG, "beta must be finite and > 0");
   if (g->n == 0) return LDD_OK;
   if (!shifts || !out_center || !out_dist) return fail(LDD_ERR_ARG, "NULL shifts or output");
@@ -793,13 +999,28 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
   int* dist = dev_d ? out_dist : g->d_dist;
   record(g, 0);
   const double* d_shift = shifts;
-  if (!dev_in) {
+  int launches = 0;
+  int rc = kRunRegular;
+  if (g->replay && !g->replay_broken && g->regular_runs > 0) {
+    // replay: inputs and outputs go through the library's own buffers
+    CUDA_TRY(cudaMemcpyAsync(g->d_shift, shifts, n * 8,
+                             dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    d_shift = g->d_shift;
+    rc = replay_fast(g, false, &launches);
+    if (rc != LDD_OK && rc != kRunRegular) return rc;
+    if (rc == LDD_OK) {
+      center = g->d_center;
+      dist = g->d_dist;
+      if (dev_c)
+        CUDA_TRY(cudaMemcpyAsync(out_center, center, n * 4, cudaMemcpyDeviceToDevice, s));
+      if (dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+  } else if (!dev_in) {
     CUDA_TRY(cudaMemcpyAsync(g->d_shift, shifts, n * 8, cudaMemcpyHostToDevice, s));
     d_shift = g->d_shift;
   }
-  int launches = 0;
-  const int rc = decompose_on_device(g, d_shift, center, dist, &launches);
-  if (rc != LDD_OK) return rc;
+  if (rc == kRunRegular && (rc = decompose_on_device(g, d_shift, center, dist, &launches)) != LDD_OK)
+    return rc;
   if (!dev_c) CUDA_TRY(cudaMemcpyAsync(out_center, center, n * 4, cudaMemcpyDeviceToHost, s));
   if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, n * 4, cudaMemcpyDeviceToHost, s));
   record(g, 5);
@@ -816,6 +1037,7 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
                         int32_t* const* out_center, int32_t* const* out_dist, int64_t* out_cut) {
   g_last_error[0] = 0;
   if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  if (g->uni) return fail(LDD_ERR_ARG, "a union graph is decomposed by ldd_union_decompose");
   if (k < 0) return fail(LDD_ERR_ARG, "k = %d is negative", k);
   if (k == 0) return LDD_OK;
   if (!betas || !shifts || !out_center || !out_dist)
@@ -900,6 +1122,7 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
 int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut) {
   g_last_error[0] = 0;
   if (!g || !out_cut) return fail(LDD_ERR_ARG, "NULL argument");
+  if (g->uni) return fail(LDD_ERR_ARG, "a union graph's cut counts come from ldd_union_decompose");
   *out_cut = 0;
   if (g->n == 0 || g->nnz == 0) return LDD_OK;
   if (!center) return fail(LDD_ERR_ARG, "center is NULL");
@@ -912,6 +1135,229 @@ int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut) {
     d_center = g->d_center;
   }
   return cut_on_device(g, d_center, out_cut);
+}
+
+int ldd_create_union(int k, ldd_graph* const* members, ldd_graph** out) {
+  g_last_error[0] = 0;
+  if (!out) return fail(LDD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || !members) return fail(LDD_ERR_ARG, "need k >= 1 members (k = %d)", k);
+  int dev = -1;
+  for (int i = 0; i < k; ++i) {
+    const ldd_graph* m = members[i];
+    if (!m) return fail(LDD_ERR_ARG, "member %d is NULL", i);
+    if (m->uni) return fail(LDD_ERR_ARG, "member %d is itself a union", i);
+    if (i == 0) dev = m->device;
+    if (m->device != dev) return fail(LDD_ERR_ARG, "members live on different devices");
+  }
+  DeviceGuard dg(dev);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", dev);
+  // member offsets of every table (64-bit sums, range-checked)
+  std::vector<u64> o[8];
+  for (auto& v : o) v.assign((size_t)k + 1, 0);
+  bool all_active = true;
+  for (int i = 0; i < k; ++i) {
+    const ldd_graph* m = members[i];
+    o[0][i + 1] = o[0][i] + ((u64)m->n + 31) / 32 * 32;
+    o[1][i + 1] = o[1][i] + (u64)m->nnz;
+    o[2][i + 1] = o[2][i] + m->m_up;
+    o[3][i + 1] = o[3][i] + m->sc.ncomp;
+    o[4][i + 1] = o[4][i] + m->sc.total;
+    o[5][i + 1] = o[5][i] + m->n_active;
+    o[6][i + 1] = o[6][i] + (u64)m->n;
+    o[7][i + 1] = o[7][i] + (m->m_up + kUnionCutChunk - 1) / kUnionCutChunk;
+    if (m->n_active > 0 && !m->d_active) all_active = false;
+  }
+  const u64 N = o[0][k], E = o[1][k];
+  if (N >= (1u << 30)) return fail(LDD_ERR_RANGE, "union of %llu vertices (padded) must be < 2^30",
+                                   (unsigned long long)N);
+  if (E >= (1ull << 31)) return fail(LDD_ERR_RANGE, "union of %llu arcs must be < 2^31",
+                                     (unsigned long long)E);
+  ldd_graph* g = new (std::nothrow) ldd_graph();
+  if (!g) return fail(LDD_ERR_OOM, "host allocation failed");
+  auto bail = [&](int status) {
+    free_graph_memory(g);
+    delete g;
+    return status;
+  };
+  g->uni = new (std::nothrow) ldd_graph::Union();
+  if (!g->uni) return bail(fail(LDD_ERR_OOM, "host allocation failed"));
+  ldd_graph::Union& U = *g->uni;
+  memset(&g->stats, 0, sizeof(g->stats));
+  g->device = dev;
+  if (cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LDD_ERR_CUDA, "no usable CUDA device"));
+  }
+  g->n = (int32_t)N;
+  g->nnz = (int64_t)E;
+  g->m_up = (u32)o[2][k];
+  g->sc.ncomp = (u32)o[3][k];
+  g->sc.total = (u32)o[4][k];
+  g->n_active = (u32)o[5][k];
+  u64 nnz_active = 0;
+  for (int i = 0; i < k; ++i) nnz_active += members[i]->nnz_active;
+  g->nnz_active = nnz_active;
+  U.k = (u32)k;
+  U.total = (u32)o[6][k];
+  U.nchunk = (u32)o[7][k];
+  U.h_voff.assign(o[0].begin(), o[0].end());
+  U.h_ooff.assign(o[6].begin(), o[6].end());
+  const size_t words = std::max<size_t>(N / 32, 1);
+  const bool active = all_active && g->n_active > 0;
+  if (cudaMalloc(&g->d_row, (N + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_col, std::max<u64>(E, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_up, std::max<u64>(g->m_up, 1) * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&g->d_excl, 2 * words * 4) != cudaSuccess ||
+      (g->sc.ncomp > 0 && (cudaMalloc(&g->sc.comp_off, g->sc.ncomp * 4) != cudaSuccess ||
+                           cudaMalloc(&g->sc.comp_len, g->sc.ncomp * 4) != cudaSuccess ||
+                           cudaMalloc(&g->sc.comp_v, g->sc.total * 4) != cudaSuccess ||
+                           cudaMalloc(&g->sc.adj, g->sc.total * 4) != cudaSuccess)) ||
+      (active && cudaMalloc(&g->d_active, (size_t)g->n_active * 4) != cudaSuccess) ||
+      cudaMalloc(&U.d_mem, (size_t)k * sizeof(UnionMember)) != cudaSuccess ||
+      cudaMalloc(&U.d_offs, 8 * ((size_t)k + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&U.d_shift_in, std::max<size_t>(U.total, 1) * 8) != cudaSuccess ||
+      cudaMalloc(&U.d_out_c, std::max<size_t>(U.total, 1) * 8) != cudaSuccess ||
+      cudaMalloc(&U.d_cut, (size_t)k * 8) != cudaSuccess ||
+      cudaMalloc(&U.d_wmem, words * 4) != cudaSuccess ||
+      cudaMalloc(&U.d_amax, 2 * (size_t)k * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LDD_ERR_OOM, "device allocation of the union (%llu vertices, %llu arcs) "
+                     "failed", (unsigned long long)N, (unsigned long long)E));
+  }
+  g->d_solo = g->d_excl + words;
+  U.d_out_d = U.d_out_c + std::max<size_t>(U.total, 1);
+  std::vector<UnionMember> mv((size_t)k);
+  for (int i = 0; i < k; ++i) {
+    const ldd_graph* m = members[i];
+    UnionMember& d = mv[(size_t)i];
+    d.row = m->d_row;
+    d.col = m->d_col;
+    d.up = m->d_up;
+    d.hot = m->d_hot;
+    d.excl = m->d_excl;
+    d.solo = m->d_solo;
+    d.comp_off = m->sc.comp_off;
+    d.comp_len = m->sc.comp_len;
+    d.comp_v = m->sc.comp_v;
+    d.adj = m->sc.adj;
+    d.active = m->d_active;
+    d.n = (u32)m->n;
+    d.nnz = (u32)m->nnz;
+  }
+  std::vector<u32> offs(8 * ((size_t)k + 1));
+  for (int t = 0; t < 8; ++t)
+    for (int i = 0; i <= k; ++i) offs[(size_t)t * (k + 1) + i] = (u32)o[t][i];
+  const u32* d = U.d_offs;
+  const size_t K1 = (size_t)k + 1;
+  U.off = UnionOffsets{d, d + K1, d + 2 * K1, d + 3 * K1, d + 4 * K1, d + 5 * K1, d + 6 * K1};
+  if (cudaMemcpy(U.d_mem, mv.data(), mv.size() * sizeof(UnionMember), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(U.d_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(LDD_ERR_CUDA, "upload of the union tables failed"));
+  UnionTables t{g->d_row, g->d_col, g->d_up, g->d_excl, g->d_solo, g->sc.comp_off,
+                g->sc.comp_len, g->sc.comp_v, g->sc.adj, g->d_active, U.d_wmem};
+  const u64 largest = std::max<u64>(std::max<u64>(N + 1, E), g->m_up);
+  launch_union_concat(U.d_mem, U.off, U.k, t, largest, g->num_sms, nullptr);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(nullptr) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LDD_ERR_CUDA, "building the union tables failed"));
+  }
+  int rc;
+  if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);
+  *out = g;
+  return LDD_OK;
+}
+
+int ldd_union_size(const ldd_graph* u, int32_t* out_k, int64_t* out_total) {
+  if (!u || !u->uni) return fail(LDD_ERR_ARG, "not a union graph");
+  if (out_k) *out_k = (int32_t)u->uni->k;
+  if (out_total) *out_total = (int64_t)u->uni->total;
+  return LDD_OK;
+}
+
+int ldd_union_decompose(ldd_graph* u, const double* betas, const double* shifts,
+                        int32_t* out_center, int32_t* out_dist, int64_t* out_cut) {
+  g_last_error[0] = 0;
+  if (!u || !u->uni) return fail(LDD_ERR_ARG, "not a union graph");
+  ldd_graph::Union& U = *u->uni;
+  if (!betas) return fail(LDD_ERR_ARG, "betas is NULL");
+  for (u32 i = 0; i < U.k; ++i)
+    if (!(betas[i] > 0.0) || isinf(betas[i]))
+      return fail(LDD_ERR_ARG, "betas[%u] must be finite and > 0", i);
+  if (out_cut)
+    for (u32 i = 0; i < U.k; ++i) out_cut[i] = 0;
+  if (U.total == 0) return LDD_OK;
+  if (!shifts || !out_center || !out_dist) return fail(LDD_ERR_ARG, "NULL shifts or output");
+  DeviceGuard dg(u->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", u->device);
+  cudaStream_t s = u->stream;
+  const size_t total = U.total;
+  const bool dev_c = is_device_ptr(out_center), dev_d = is_device_ptr(out_dist);
+  int* center = dev_c ? out_center : U.d_out_c;
+  int* dist = dev_d ? out_dist : U.d_out_d;
+  record(u, 0);
+  const bool dev_in = is_device_ptr(shifts);
+  const double* in = shifts;
+  int launches = 0, cut_launches = 0;
+  int rc = kRunRegular;
+  if (u->replay && !u->replay_broken && u->regular_runs > 0) {
+    CUDA_TRY(cudaMemcpyAsync(U.d_shift_in, shifts, total * 8,
+                             dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    in = U.d_shift_in;
+    rc = replay_fast(u, out_cut != nullptr, &launches);
+    if (rc != LDD_OK && rc != kRunRegular) return rc;
+    if (rc == LDD_OK) {
+      center = U.d_out_c;
+      dist = U.d_out_d;
+      if (out_cut)
+        for (u32 i = 0; i < U.k; ++i) out_cut[i] = (int64_t)u->h_cut[i];
+      if (dev_c)
+        CUDA_TRY(cudaMemcpyAsync(out_center, center, total * 4, cudaMemcpyDeviceToDevice, s));
+      if (dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, total * 4, cudaMemcpyDeviceToDevice, s));
+    }
+  } else if (!dev_in) {
+    CUDA_TRY(cudaMemcpyAsync(U.d_shift_in, shifts, total * 8, cudaMemcpyHostToDevice, s));
+    in = U.d_shift_in;
+  }
+  if (rc == kRunRegular) {
+    launches = launch_union_spread(in, U.off, U.k, (u32)u->n, u->d_excl, u->d_shift, U.d_amax,
+                                   U.d_amax + U.k, u->num_sms, s);
+    int l = 0;
+    if ((rc = decompose_on_device(u, u->d_shift, center, dist, &l)) != LDD_OK) return rc;
+    launches += l;
+    if (out_cut) {
+      record(u, 6);
+      CUDA_TRY(cudaMemsetAsync(U.d_cut, 0, (size_t)U.k * 8, s));
+      cut_launches = launch_union_cut(u->d_up, U.d_offs + 7 * ((size_t)U.k + 1), U.nchunk, U.off,
+                                      U.k, center, U.d_cut, u->num_sms, s);
+      CUDA_TRY(cudaMemcpyAsync(out_cut, U.d_cut, (size_t)U.k * 8, cudaMemcpyDeviceToHost, s));
+      record(u, 7);
+    }
+  }
+  if (!dev_c) CUDA_TRY(cudaMemcpyAsync(out_center, center, total * 4, cudaMemcpyDeviceToHost, s));
+  if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, total * 4, cudaMemcpyDeviceToHost, s));
+  record(u, 5);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  ldd_stats& st = u->stats;
+  st.launches = launches;
+  st.cut_launches = cut_launches;
+  st.ms_cut = (out_cut && !st.replayed) ? elapsed(u, 6, 7) : (out_cut ? -1.f : 0.f);
+  st.ms_total = elapsed(u, 0, 5);
+  return LDD_OK;
+}
+
+int ldd_set_graph_replay(ldd_graph* g, int enable) {
+  if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  DeviceGuard dg(g->device);
+  g->replay = enable != 0;
+  if (!g->replay) {
+    cudaStreamSynchronize(g->stream);
+    drop_replay(g);
+  }
+  g->replay_broken = false;  // a new request gets a new capture attempt
+  return LDD_OK;
 }
 
 }  // extern "C"

@@ -163,6 +163,8 @@ struct RankBufs {
   u32 bptr_cap;
   const u32* excl;      // bit v: v is not handled by the BFS (no start bucket)
   const u32* solo;      // bit v: v is alone in its component (no rank needed)
+  const u32* wmem;      // unions: member of every 32-vertex word; else null
+  const int* lift;      // unions: floor lift of every member (a_u += lift); else null
   Control* ctl;
 };
 // exact64 = false: fraction buckets + in-bucket exact ranks of the vertices
@@ -171,6 +173,9 @@ struct RankBufs {
 // k0 viewed as 32-bit words (their rounds).
 int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s);
 u32 fraction_bucket_bits(u32 n);
+// Look-back status words the fast path's two scans use (status[0 ..)); a
+// captured replay clears them and runs with the fixed epochs 1 and 2.
+size_t rank_status_words(u32 n, u32 bptr_cap);
 size_t fraction_slot_bytes(u32 n);
 // Persistent BFS (k_bfs.cu).  Returns kernels launched, or -1 with the CUDA
 // error left in *err.
@@ -198,6 +203,65 @@ cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 
 // Adjacency masks of the small-component members (sc.comp_v already filled).
 cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,
                               const SmallComps& sc, int num_sms, cudaStream_t s);
+
+// ---------------------------------------------------------------- batches (k_union.cu)
+// A batch of graphs runs as their disjoint union (member s at union vertices
+// [voff_s, voff_s + n_s), padded to a multiple of 32).  Device view of one
+// member's tables, read once while the union is built.
+struct UnionMember {
+  const int* row;
+  const int* col;
+  const int2* up;       // cut list (cold, hot), hot < 0: slot of the hot table
+  const u32* hot;
+  const u32* excl;
+  const u32* solo;
+  const u32* comp_off;
+  const u32* comp_len;
+  const u32* comp_v;
+  const u32* adj;
+  const u32* active;    // null unless every member has one
+  u32 n;
+  u32 nnz;
+};
+// Member offsets, k + 1 device words each: union vertices (v), arcs (e),
+// cut-list entries (u), small components (c) and their members (m), active
+// list entries (a), and caller-layout outputs (o: n_0 + ... + n_{s-1}).
+struct UnionOffsets {
+  const u32* v;
+  const u32* e;
+  const u32* u;
+  const u32* c;
+  const u32* m;
+  const u32* a;
+  const u32* o;
+};
+struct UnionTables {
+  int* row;
+  int* col;
+  int2* up;
+  u32* excl;
+  u32* solo;
+  u32* comp_off;
+  u32* comp_len;
+  u32* comp_v;
+  u32* adj;
+  u32* active;
+  u32* wmem;  // member of every 32-vertex word
+};
+constexpr u32 kUnionCutChunk = 8192;  // cut-list entries per block step, within one member
+// largest = the longest table (elements), for the grid size.
+int launch_union_concat(const UnionMember* mem, const UnionOffsets& off, u32 k,
+                        const UnionTables& t, u64 largest, int num_sms, cudaStream_t s);
+// Shifts to the union layout, and every member's floor lift (amax, lift: k ints).
+int launch_union_spread(const double* in, const UnionOffsets& off, u32 k, u32 N,
+                        const u32* excl, double* out, int* amax, int* lift, int num_sms,
+                        cudaStream_t s);
+int launch_union_finalize(const u64* key, const u32* order, const u32* solo,
+                          const UnionOffsets& off, u32 k, u32 total, int* center, int* dist,
+                          const u32* err, int num_sms, cudaStream_t s);
+// chunk_off[0 .. k]: first cut chunk of each member (nchunk = chunk_off[k]).
+int launch_union_cut(const int2* up, const u32* chunk_off, u32 nchunk, const UnionOffsets& off,
+                     u32 k, const int* center, u64* cut, int num_sms, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ u32 lanemask_lt() {

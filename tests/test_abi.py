@@ -51,6 +51,18 @@ def test_argument_errors_need_no_device(ldd):
     lib.ldd_decompose_batch.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5
     assert lib.ldd_decompose_batch(None, 1, None, None, None, None, None) == ldd.LDD_ERR_ARG
     assert lib.ldd_set_stream(None, None) == ldd.LDD_ERR_ARG
+    lib.ldd_create_union.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.ldd_union_size.argtypes = [ctypes.c_void_p] * 3
+    lib.ldd_union_decompose.argtypes = [ctypes.c_void_p] * 6
+    u = ctypes.c_void_p()
+    assert lib.ldd_create_union(0, None, ctypes.byref(u)) == ldd.LDD_ERR_ARG
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert lib.ldd_create_union(2, nulls, ctypes.byref(u)) == ldd.LDD_ERR_ARG
+    assert lib.ldd_create_union(1, nulls, None) == ldd.LDD_ERR_ARG
+    assert lib.ldd_union_size(None, None, None) == ldd.LDD_ERR_ARG
+    assert lib.ldd_union_decompose(None, None, None, None, None, None) == ldd.LDD_ERR_ARG
+    lib.ldd_set_graph_replay.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.ldd_set_graph_replay(None, 1) == ldd.LDD_ERR_ARG
     out = ctypes.c_void_p()
     rp = np.zeros(4, dtype=np.int32)
     assert lib.ldd_create_graph(3, 0, rp.ctypes.data, None, 1, None) == ldd.LDD_ERR_ARG

@@ -130,3 +130,18 @@ def test_order_statistics_fact_2_1():
         gaps.append(d[-1] - d[-2])
     assert stats.kstest(gaps, "expon", args=(0, 1.0 / beta)).pvalue > 1e-3
     assert math.isclose(np.mean(gaps) * beta, 1.0, rel_tol=0.08)
+
+
+def test_batch_members_recipe():
+    """The batched workload's per-member sizes and betas: deterministic, inside
+    their ranges, roughly uniform, and seeds master + i."""
+    m = gen.batch_members(1024, 1000, 200000, 0.02, 0.5, 11)
+    assert m == gen.batch_members(1024, 1000, 200000, 0.02, 0.5, 11)
+    ns = np.array([x[0] for x in m])
+    bs = np.array([x[1] for x in m])
+    assert ns.min() >= 1000 and ns.max() <= 200000
+    assert bs.min() >= 0.02 and bs.max() < 0.5
+    assert abs(ns.mean() - 100500) < 0.05 * 100500  # uniform mean, 1024 draws
+    assert abs(bs.mean() - 0.26) < 0.02
+    assert [x[2] for x in m[:3]] == [11, 12, 13] and [x[3] for x in m[:3]] == [11, 12, 13]
+    assert gen.batch_members(4, 5, 5, 0.1, 0.1, 3)[0][:2] == (5, 0.1)
