@@ -593,6 +593,204 @@ def batch_arm(args):
     return 0
 
 
+# ----------------------------------------------------------------- serving
+def serve_arm(args):
+    """A Poisson request stream replayed in real time against the batched
+    server and, on the same stream, against one-at-a-time plain calls."""
+    import numpy as np
+    import torch
+
+    import ldd_gen as gen
+    import paper_1307_3692_gb300 as ldd
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    spec = gen.SERVE_WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    Gs = [gen.rmat(sc) for sc in spec["rmat_scales"]] + [gen.grid2d(w, w) for w in spec["grids"]]
+    names = [f"rmat{sc}" for sc in spec["rmat_scales"]] + [f"grid{w}x{w}" for w in spec["grids"]]
+    gs = [ldd.LddGraph(torch.from_numpy(G.row_ptr).to(dev), torch.from_numpy(G.col).to(dev),
+                       validate=False) for G in Gs]
+    betas, S = spec["betas"], spec["seeds"]
+    pool = {}
+    for gi, G in enumerate(Gs):
+        for bi, b in enumerate(betas):
+            for si in range(S):
+                pool[gi, bi, si] = torch.from_numpy(
+                    gen.shifts(G.n, b, 1000 + 100 * gi + 10 * bi + si)).pin_memory()
+    ring = 8  # output buffers per graph (results of a benchmark stream are not kept)
+    outs = [[(torch.empty(G.n, dtype=torch.int32).pin_memory(),
+              torch.empty(G.n, dtype=torch.int32).pin_memory()) for _ in range(ring)] for G in Gs]
+    reqs = gen.serve_requests(len(Gs), len(betas), S, spec["rate"], spec["seconds"],
+                              spec["master_seed"] + rank)
+    t_setup = time.perf_counter() - t0
+    check_every = max(1, len(reqs) // 16)
+
+    def replay(srv):
+        # warm-up: one request per graph (first-use allocations stay untimed)
+        for gi, G in enumerate(Gs):
+            c, d = outs[gi][0]
+            srv.wait(srv.submit(gs[gi], betas[0], pool[gi, 0, 0], c, d, np.zeros(1, np.int64)))
+        tickets, checks, cuts = [], {}, []
+        start = time.perf_counter()
+        late = 0.0
+        for i, (t_arr, gi, bi, si) in enumerate(reqs):
+            while True:
+                dt = t_arr - (time.perf_counter() - start)
+                if dt <= 0:
+                    late = max(late, -dt)
+                    break
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+            if i % check_every == 0:
+                c = np.empty(Gs[gi].n, np.int32)
+                d = np.empty(Gs[gi].n, np.int32)
+                checks[i] = (c, d)
+            else:
+                c, d = outs[gi][i % ring]
+            cut = np.zeros(1, np.int64)
+            cuts.append(cut)
+            tickets.append(srv.submit(gs[gi], betas[bi], pool[gi, bi, si], c, d, cut))
+        infos = [srv.wait(t) for t in tickets]
+        return infos, checks, late
+
+    def summarise(infos, late):
+        lat = np.array([(x["end_us"] - x["submit_us"]) / 1e3 for x in infos])
+        span = (max(x["end_us"] for x in infos) - min(x["submit_us"] for x in infos)) / 1e6
+        bs = np.array([x["batch_size"] for x in infos])
+        return {"requests": len(infos), "throughput_rps": len(infos) / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+                "batches": int(len(set(x["batch_id"] for x in infos))),
+                "mean_batch_size": float(bs.mean()), "span_s": span,
+                "max_submit_lag_ms": 1e3 * late}
+
+    budget = spec["hbm_budget"]
+    srv = ldd.LddServer(budget, max_batch=args.max_batch, slots=2)
+    with ClockSampler(local) as clocks:
+        infos_b, checks_b, late_b = replay(srv)
+    srv.close()
+    one = ldd.LddServer(budget, max_batch=1, slots=1, one_at_a_time=True)
+    infos_1, checks_1, late_1 = replay(one)
+    one.close()
+    batched, single = summarise(infos_b, late_b), summarise(infos_1, late_1)
+    # mix check: sampled requests equal their results alone (and the other arm)
+    mismatches = 0
+    for i, (c, d) in checks_b.items():
+        _, gi, bi, si = reqs[i]
+        ac = np.empty(Gs[gi].n, np.int32)
+        ad = np.empty(Gs[gi].n, np.int32)
+        gs[gi].decompose(betas[bi], pool[gi, bi, si], ac, ad)
+        c1, d1 = checks_1[i]
+        mismatches += int(not (np.array_equal(c, ac) and np.array_equal(d, ad)
+                               and np.array_equal(c1, ac) and np.array_equal(d1, ad)))
+    m_req = np.mean([Gs[gi].m for _, gi, _, _ in reqs])
+    if rank == 0:
+        clk = clocks.summary()
+        line = {
+            "metric": "LDD served decompositions/s", "value": world * batched["throughput_rps"],
+            "unit": "decompositions/s", "n_gpus": world, "steps": 1, "warmup": len(Gs),
+            "ms_per_step": 1e3 * batched["span_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload,
+                       "graphs": names, "betas": list(betas), "shift_vectors_per_graph_beta": S,
+                       "arrivals": f"Poisson, mean {spec['rate']:.0f}/s for {spec['seconds']} s "
+                                   f"(seed {spec['master_seed']})",
+                       "hbm_budget_bytes": budget, "slots": 2, "max_batch": args.max_batch,
+                       "mean_edges_per_request": float(m_req),
+                       "step": "the whole request stream, replayed in real time",
+                       "parallelism": f"replicas x{world}"},
+            "batched": batched, "one_at_a_time": single,
+            "p99_speedup": single["p99_ms"] / batched["p99_ms"],
+            "throughput_speedup": batched["throughput_rps"] / single["throughput_rps"],
+            "served_gteps": batched["throughput_rps"] * m_req / 1e9,
+            "mix_check": {"sampled": len(checks_b), "mismatches": mismatches,
+                          "against": "ldd_decompose alone on the same graph and shifts"},
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": world * batched["throughput_rps"], "unit": "decompositions/s",
+                    "h2d_bytes_per_step": int(sum(8 * Gs[gi].n for _, gi, _, _ in reqs)),
+                    "d2h_bytes_per_step": int(sum(8 * Gs[gi].n + 8 for _, gi, _, _ in reqs)),
+                    "api": "ldd_server_submit / ldd_server_wait, pinned host buffers"},
+            "gpu_launches": None,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                       "reasons": clk["reasons"]},
+            "host_s": {"setup": t_setup},
+        }
+        print(json.dumps(line), flush=True)
+    for g in gs:
+        g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# ----------------------------------------------------------------- Figure 1
+def fig1_arm(args):
+    """The paper's only experiment (Figure 1): a 1000 x 1000 grid decomposed at
+    beta in {0.002, 0.005, 0.01, 0.02, 0.05, 0.1}.  The figure shows the
+    pieces; this reports what it illustrates, per beta over a few shift
+    seeds: pieces, radius, cut fraction against Corollary 3.5's 1 - e^-beta,
+    delta_max against Lemma 3.2's H_n / beta, and the GPU time, with every
+    labelling checked equal to the oracle's."""
+    import numpy as np
+    import torch
+
+    import ldd_gen as gen
+    import oracle
+    import paper_1307_3692_gb300 as ldd
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    G = gen.grid2d(1000, 1000)
+    g = ldd.LddGraph(torch.from_numpy(G.row_ptr).to(dev), torch.from_numpy(G.col).to(dev),
+                     validate=False)
+    g.set_timing(True)
+    c = torch.empty(G.n, dtype=torch.int32, device=dev)
+    d = torch.empty(G.n, dtype=torch.int32, device=dev)
+    H = float(np.sum(1.0 / np.arange(1, G.n + 1)))
+    rows = []
+    mismatches = 0
+    seeds = range(1, 1 + max(1, args.steps))
+    for beta in (0.002, 0.005, 0.01, 0.02, 0.05, 0.1):
+        acc = {"pieces": [], "max_radius": [], "mean_radius": [], "cut_fraction": [],
+               "delta_max": [], "ms": []}
+        for seed in seeds:
+            sh = gen.shifts(G.n, beta, seed)
+            dsh = torch.from_numpy(sh).to(dev)
+            g.decompose(beta, dsh, c, d)  # warm
+            g.decompose(beta, dsh, c, d)
+            ms = g.stats()["ms_total"]
+            cut = g.cut_edges(c)
+            gc, gd = c.cpu().numpy(), d.cpu().numpy()
+            if not args.no_cpu_baseline:
+                oc, od = oracle.oracle_ldd(G.row_ptr, G.col, sh)
+                mismatches += int(not (np.array_equal(gc, oc) and np.array_equal(gd, od)))
+            acc["pieces"].append(len(np.unique(gc)))
+            acc["max_radius"].append(int(gd.max()))
+            acc["mean_radius"].append(float(gd.mean()))
+            acc["cut_fraction"].append(cut / G.m)
+            acc["delta_max"].append(float(sh.max()))
+            acc["ms"].append(ms)
+        row = {"beta": beta} | {k: float(np.mean(v)) for k, v in acc.items()}
+        row |= {"cut_bound_1_minus_exp": 1 - math.exp(-beta), "H_n_over_beta": H / beta,
+                "gteps": G.m / (row["ms"] * 1e-3) / 1e9}
+        rows.append(row)
+    g.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "LDD Figure 1 sweep", "value": float(np.mean([r["gteps"] for r in rows])),
+            "unit": "GTEPS", "n_gpus": 1, "steps": len(seeds), "warmup": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u64",
+            "config": {"workload": "fig1", "graph": "2D 4-neighbour grid 1000x1000",
+                       "seeds": list(seeds)},
+            "rows": rows, "oracle_mismatches": None if args.no_cpu_baseline else mismatches}),
+            flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,12 +799,28 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-batch", type=int, default=256,
+                    help="serving: most requests per batch")
     ap.add_argument("--no-replay", action="store_true",
                     help="batched workloads: run the regular path instead of the captured CUDA graph")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     import ldd_gen
 
+    if args.workload == "fig1":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the Figure 1 sweep checks every labelling against the oracle "
+                              "itself"}), flush=True)
+            return 0
+        return fig1_arm(args)
+    if args.workload in ldd_gen.SERVE_WORKLOADS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the serving workload has no reference arm; its line compares "
+                              "against one-at-a-time plain calls"}), flush=True)
+            return 0
+        return serve_arm(args)
     if args.workload in ldd_gen.BATCH_WORKLOADS:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":

@@ -99,6 +99,45 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
 int ldd_cut_edges(ldd_graph* g, const int32_t* center, int64_t* out_cut);
 
 /*
+ * ldd_decompose_ranked -- the permutation variant of Section 4: the
+ * fractional parts of the shifts only break ties inside an integer level, and
+ * a random permutation of the vertices can stand in for them.  Every vertex u
+ * brings an integer shift levels[u] (e.g. floor(delta_u), delta_u ~ Exp(beta))
+ * and a tie-break position perm[u]; every vertex v joins the u minimising
+ * (dist(u, v) - levels[u], perm[u]) lexicographically, so a smaller position
+ * wins among equal integer shifted distances.  No sort is needed: the
+ * permutation is the rank.
+ *   levels      int32[n] (host or device), each >= 0.
+ *   perm        int32[n] (host or device), a permutation of 0 .. n-1.
+ *   out_center, out_dist  as in ldd_decompose.
+ * A negative level or a perm that is not a permutation gives LDD_ERR_ARG.
+ */
+int ldd_decompose_ranked(ldd_graph* g, const int32_t* levels, const int32_t* perm,
+                         int32_t* out_center, int32_t* out_dist);
+
+/*
+ * ldd_decompose_retry -- the Las Vegas loop of Theorem 1.2's proof: decompose
+ * with shifts[0], shifts[1], ... until one decomposition meets both bounds of
+ * the wanted (beta, d) decomposition (Definition 1.1): at most max_cut edges
+ * between pieces and every vertex within max_radius hops of its center (so
+ * every piece has strong diameter <= 2 max_radius, Lemma 3.1).  The paper
+ * shows a constant expected number of tries for max_cut ~ beta m and
+ * max_radius = O(log n / beta) (Lemma 3.2, Corollary 3.5).
+ *   k, shifts    k shift vectors (each n doubles, host or device), tried in
+ *                order; the caller draws them (independent Exp(beta) draws).
+ *   out_center, out_dist  the accepted decomposition (the last one tried if
+ *                none is accepted); host or device.
+ *   out_cut, out_radius   NULL or host: its cut count and max distance.
+ *   out_accepted host: the index of the accepted vector, or -1 if none of the
+ *                k met the bounds (the call still returns LDD_OK).
+ * Cut count and radius are computed on the device for every try.
+ */
+int ldd_decompose_retry(ldd_graph* g, double beta, int k, const double* const* shifts,
+                        int64_t max_cut, int32_t max_radius, int32_t* out_center,
+                        int32_t* out_dist, int64_t* out_cut, int32_t* out_radius,
+                        int32_t* out_accepted);
+
+/*
  * ldd_decompose_batch -- k independent decompositions of g, one per shift
  * vector (as ldd_decompose, Algorithm 2 via Algorithm 1 / Section 4), and
  * optionally the cut count of each (Definition 1.1), pipelined: while
@@ -169,6 +208,78 @@ int ldd_union_size(const ldd_graph* u, int32_t* out_k, int64_t* out_total);
  */
 int ldd_union_decompose(ldd_graph* u, const double* betas, const double* shifts,
                         int32_t* out_center, int32_t* out_dist, int64_t* out_cut);
+
+/*
+ * Request server: continuous batching of decomposition requests.
+ *
+ * A server owns `slots` workspaces (union graphs of fixed capacity, bought
+ * with the HBM budget) and one worker thread per workspace.  Requests --
+ * (graph, beta, shifts, output buffers), any mix of graphs -- queue in arrival
+ * order.  A free worker takes every waiting request that still fits its
+ * workspace (the admission test: the requests' device footprint -- vertices,
+ * arcs, cut-list entries, small components -- against the workspace's
+ * capacities) and decomposes them as one disjoint union (see
+ * ldd_create_union): exactly the per-request results, computed together.
+ * The round loop of one batch holds the device at a time; meanwhile the other
+ * workers build their unions and copy shifts in and results out, so requests
+ * that arrive while a batch runs join the next one as soon as a workspace
+ * frees up.  A request whose input fails (a bad shift) fails alone: its batch
+ * is rerun request by request.  Graphs passed to a server must stay alive and
+ * must not be destroyed until their requests are collected; with
+ * one_at_a_time set, they must not be used on another thread meanwhile.
+ */
+typedef struct ldd_server ldd_server;
+
+typedef struct {
+  int64_t hbm_budget_bytes; /* device memory for all workspaces together (> 0) */
+  int32_t max_batch;        /* most requests per batch (>= 1) */
+  int32_t slots;            /* workspaces and worker threads (>= 1) */
+  int32_t one_at_a_time;    /* 1: no batching -- one worker runs each request as
+                               ldd_decompose_batch(g, 1, ...) in arrival order
+                               (the comparison mode); budget and caps unused */
+  int32_t reserved;         /* 0 */
+  int64_t max_vertices;     /* per batch, members padded to multiples of 32;
+                               0: as many as the per-slot budget allows (< 2^30) */
+  int64_t max_arcs;         /* per batch; 0: derived from the budget (< 2^31) */
+} ldd_server_config;
+
+typedef struct {
+  int32_t status;     /* LDD_OK or the request's error */
+  int32_t batch_size; /* requests decomposed together with this one */
+  int64_t batch_id;   /* batches in the order workers took them */
+  double submit_us;   /* server clock: microseconds since ldd_server_create */
+  double start_us;    /* taken by a worker */
+  double end_us;      /* results in the caller's buffers */
+} ldd_request_info;
+
+/* ldd_server_create -- a server on the current device.  LDD_ERR_RANGE if the
+ * caps do not fit the budget; LDD_ERR_OOM if the workspaces cannot be had. */
+int ldd_server_create(const ldd_server_config* cfg, ldd_server** out);
+
+/*
+ * ldd_server_submit -- queue one decomposition of g (Algorithm 2, as
+ * ldd_decompose) and, if out_cut is not NULL, its cut count (Definition 1.1).
+ *   shifts      double[n] host memory (page-locked for copies that overlap).
+ *   out_center, out_dist  int32[n] host memory; out_cut: host int64 or NULL.
+ * The buffers must stay valid until ldd_server_wait returns for the ticket.
+ * LDD_ERR_RANGE: g alone exceeds a workspace.  out_ticket receives the
+ * request's ticket.
+ */
+int ldd_server_submit(ldd_server* s, ldd_graph* g, double beta, const double* shifts,
+                      int32_t* out_center, int32_t* out_dist, int64_t* out_cut,
+                      int64_t* out_ticket);
+
+/* ldd_server_wait -- block until the request is done, fill *info (may be
+ * NULL), release the ticket, and return the request's status. */
+int ldd_server_wait(ldd_server* s, int64_t ticket, ldd_request_info* info);
+
+/* ldd_server_footprint -- device bytes one request on g takes of a workspace
+ * (the admission measure). */
+int ldd_server_footprint(const ldd_server* s, const ldd_graph* g, int64_t* out_bytes);
+
+/* ldd_server_destroy -- finish every queued request, stop the workers and free
+ * the workspaces.  Uncollected tickets are dropped.  NULL is a no-op. */
+int ldd_server_destroy(ldd_server* s);
 
 /*
  * ldd_cut_edges_noalloc -- the same count as ldd_cut_edges, for callers that
@@ -250,6 +361,35 @@ typedef struct {
 
 int ldd_get_stats(const ldd_graph* g, ldd_stats* out);
 int ldd_set_timing(ldd_graph* g, int enable);
+
+/*
+ * Launch parameters of the round loop, per graph (or union).  None changes a
+ * result; each changes only speed.
+ */
+typedef struct {
+  int32_t bfs_blocks_per_sm; /* CTAs of the persistent round loop per SM (1 or 2) */
+  int32_t pull_alpha;        /* go bottom-up when frontier arcs x alpha > unsettled arcs */
+  int32_t pull_beta;         /* back to top-down when frontier vertices x beta < BFS vertices */
+  int32_t pull_gamma;        /* ... and bottom-up only when frontier arcs x gamma > BFS vertices */
+  int32_t probe_min_arcs;    /* top-down rounds with at least this many arcs read a key
+                                before its atomicMin */
+  float ms;                  /* ldd_autotune: the best decomposition time seen, ms */
+} ldd_tuning;
+
+int ldd_get_tuning(const ldd_graph* g, ldd_tuning* out);
+/* LDD_ERR_ARG when a field is out of range. */
+int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t);
+
+/*
+ * ldd_autotune -- pick g's launch parameters for this workload by timing
+ * decompositions (CUDA events on g's stream, best of reps after one warm-up)
+ * while trying a few values of one parameter at a time (push/pull thresholds,
+ * key-probe threshold, CTAs per SM), keeping a value only for a gain of 2 %
+ * or more.  shifts: a representative shift vector (n doubles; a union's
+ * caller-layout total), host or device.  The chosen parameters stay on g and
+ * are returned in *out.  Results of later decompositions are unaffected.
+ */
+int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out);
 
 /*
  * ldd_set_graph_replay -- enable (1) or disable (0) CUDA-graph replay of the

@@ -100,6 +100,26 @@ def shifts(n: int, beta: float, seed: int) -> np.ndarray:
     return out
 
 
+def permutation(n: int, seed: int) -> np.ndarray:
+    """A uniform random permutation of 0 .. n-1 as positions: perm[u] = the
+    position of u after sorting the vertices by a 64-bit Philox4x32-10 word
+    (key seed, counter (u, 0, 5, 0); ties by u)."""
+    w = philox_stream(seed, 0, n, 5, 0).astype(np.uint64)
+    key = (w[:, 0] << np.uint64(32)) | w[:, 1]
+    order = np.lexsort((np.arange(n), key))
+    perm = np.empty(n, dtype=np.int32)
+    perm[order] = np.arange(n, dtype=np.int32)
+    return perm
+
+
+def ranked_inputs(n: int, beta: float, seed: int):
+    """Inputs of the permutation variant: levels = floor of the Exp(beta)
+    shifts of ``shifts(n, beta, seed)`` and an independent random permutation
+    (seed + 1) as the tie-break."""
+    levels = np.floor(shifts(n, beta, seed)).astype(np.int32)
+    return levels, permutation(n, seed + 1)
+
+
 # ---------------------------------------------------------------- graphs
 @dataclass
 class CSR:
@@ -212,6 +232,17 @@ WORKLOADS = {
 #    shift seed 11 + i (batch_members).
 #  rmat20_seeds_64: 64 shift vectors (seeds 1 .. 64) of one R-MAT scale-20
 #    graph (the scale-22 parameters, seed 7) at beta 0.1.
+# Serving workload: a Poisson stream (mean 2,000 requests/s for 2 s) over
+# resident R-MAT graphs of scales 14..22 (the scale-22 parameters, seed 7) and
+# 2D grids 64^2 .. 2048^2; beta from {0.02, 0.05, 0.1, 0.2, 0.5}; each request
+# takes one of two pre-drawn shift vectors per (graph, beta), shift seed
+# 1000 + 100 graph + 10 beta + seed index; a 120 GB HBM budget.
+SERVE_WORKLOADS = {
+    "serve_mix": dict(rmat_scales=tuple(range(14, 23)), grids=(64, 128, 256, 512, 1024, 2048),
+                      betas=(0.02, 0.05, 0.1, 0.2, 0.5), seeds=2, rate=2000.0, seconds=2.0,
+                      master_seed=21, hbm_budget=120 << 30),
+}
+
 BATCH_WORKLOADS = {
     "rgg_batch_1024": dict(kind="rgg", count=1024, n_lo=1000, n_hi=200000, beta_lo=0.02,
                            beta_hi=0.5, master_seed=11),
@@ -250,6 +281,31 @@ def rgg_batch(count: int = 1024, n_lo: int = 1000, n_hi: int = 200000, beta_lo: 
         G = rgg(n, gseed, mean_degree)
         out.append((G, beta, shifts(n, beta, sseed)))
     return out
+
+
+def serve_requests(n_graphs: int, n_betas: int, n_seeds: int, rate: float, seconds: float,
+                   master_seed: int):
+    """A Poisson stream of requests: (arrival_s, graph index, beta index, seed
+    index) in arrival order.  Request i draws Philox4x32-10 with key
+    master_seed and counter (i, 0, 4, 0): words 0-1 give the exponential
+    inter-arrival gap -ln(U)/rate (U a 53-bit uniform on (0, 1]), words 2 and 3
+    the graph and the (beta, seed) pair by modulo."""
+    out = []
+    t = 0.0
+    i = 0
+    chunk = 4096
+    while True:
+        w = philox_stream(master_seed, i, chunk, 4, 0).astype(np.uint64)
+        u = (((w[:, 0] << np.uint64(32)) | w[:, 1]) >> np.uint64(11)).astype(np.float64)
+        u = (u + 1.0) * 2.0 ** -53
+        for j in range(chunk):
+            t += -math.log(u[j]) / rate
+            if t >= seconds:
+                return out
+            gi = int(w[j, 2] % np.uint64(n_graphs))
+            pair = int(w[j, 3] % np.uint64(n_betas * n_seeds))
+            out.append((t, gi, pair // n_seeds, pair % n_seeds))
+        i += chunk
 
 
 def make_graph(spec) -> CSR:

@@ -8,6 +8,9 @@ code.  The only common dependency is ``ldd_gen`` (seeded inputs).
 
 * ``oracle_ldd``       -- multi-source Dijkstra over exact labels (C, ldd_oracle.c):
                           Algorithm 2 via the super-source reduction of Section 4.
+* ``oracle_ldd_ranked`` -- the permutation variant of Section 4 (integer
+                          levels + a tie-break permutation), through
+                          ``oracle_ldd`` on shifts that order the same way.
 * ``oracle_cut_edges`` -- Definition 1.1's count of edges between pieces.
 * ``oracle_certify``   -- O(m) optimality certificate (Lemma 3.1 predecessor +
                           non-improvability), usable at any size.
@@ -88,6 +91,28 @@ def oracle_ldd(row_ptr, col, delta):
     if rc != 0:
         raise MemoryError("oracle_ldd allocation failed")
     return center, dist
+
+
+def oracle_ldd_ranked(row_ptr, col, levels, perm):
+    """(center, dist) of the permutation variant: v joins the u minimising
+    (dist(u, v) - levels[u], perm[u]).  Section 4 notes the fractional part of
+    a shift only orders vertices inside an integer level, so the shifts
+    levels[u] + (n - perm[u]) / (n + 1) -- whose fractional parts fall in
+    perm order -- give the same assignment; the call checks that FP64 kept
+    that order (floor and strict order inside every level) before using them."""
+    lv = np.ascontiguousarray(levels, dtype=np.int64)
+    pm = np.ascontiguousarray(perm, dtype=np.int64)
+    n = lv.shape[0]
+    if n and (lv.min() < 0 or not np.array_equal(np.sort(pm), np.arange(n))):
+        raise ValueError("levels must be >= 0 and perm a permutation of 0 .. n-1")
+    delta = lv.astype(np.float64) + (n - pm).astype(np.float64) / (n + 1)
+    if n:
+        by = np.lexsort((pm, lv))  # level ascending, position ascending
+        same = lv[by][1:] == lv[by][:-1]
+        if (not np.array_equal(np.floor(delta), lv.astype(np.float64))
+                or not np.all(delta[by][1:][same] < delta[by][:-1][same])):
+            raise ValueError("levels too large for an exact FP64 stand-in")
+    return oracle_ldd(row_ptr, col, delta)
 
 
 def oracle_cut_edges(row_ptr, col, center) -> int:

@@ -52,6 +52,27 @@ def brute_ldd(row_ptr, col, delta):
     return center, dist
 
 
+def brute_ldd_ranked(row_ptr, col, levels, perm):
+    """The permutation variant (Section 4: a random permutation stands in for
+    the fractional parts) written out: v joins the u minimising
+    (dist(u, v) - levels[u], perm[u]), all integers."""
+    n = len(row_ptr) - 1
+    apsp = [bfs_distances(n, row_ptr, col, u) for u in range(n)]
+    center, dist = [], []
+    for v in range(n):
+        best = None
+        for u in range(n):
+            d = apsp[u][v]
+            if d is None:
+                continue
+            cand = (d - int(levels[u]), int(perm[u]))
+            if best is None or cand < best:
+                best = (cand[0], cand[1], u)
+        center.append(best[2])
+        dist.append(apsp[best[2]][v])
+    return center, dist
+
+
 def brute_cut_edges(row_ptr, col, center):
     """Edges {v, w} (each counted once, v < w) with endpoints in different pieces."""
     n = len(row_ptr) - 1

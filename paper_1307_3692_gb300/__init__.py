@@ -25,7 +25,8 @@ __all__ = [
     "LddError", "LddGraph", "ldd_create_graph", "ldd_decompose", "ldd_cut_edges",
     "ldd_set_stream", "ldd_destroy_graph", "ldd_status_string", "ldd_last_error",
     "ldd_get_stats", "ldd_set_timing", "ldd_cut_edges_noalloc", "ldd_get_round_profile",
-    "ldd_decompose_batch", "ldd_set_graph_replay", "ldd_create_union", "ldd_union_size", "ldd_union_decompose", "LddUnion",
+    "ldd_decompose_batch", "ldd_decompose_ranked", "ldd_autotune", "ldd_get_tuning",
+    "ldd_set_tuning", "ldd_decompose_retry", "default_bounds", "ldd_set_graph_replay", "ldd_create_union", "LddServer", "ldd_union_size", "ldd_union_decompose", "LddUnion",
     "library_path", "LDD_OK", "LDD_ERR_ARG",
     "LDD_ERR_GRAPH", "LDD_ERR_RANGE", "LDD_ERR_OOM", "LDD_ERR_CUDA", "LDD_ERR_TIMEOUT",
 ]
@@ -56,6 +57,12 @@ _lib.ldd_create_graph.argtypes = [_i32, _i64, _vp, _vp, ctypes.c_int, ctypes.POI
 _lib.ldd_create_graph.restype = ctypes.c_int
 _lib.ldd_decompose.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.ldd_decompose.restype = ctypes.c_int
+_lib.ldd_decompose_retry.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _vp, _i64, _i32, _vp,
+                                     _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                     ctypes.POINTER(_i32)]
+_lib.ldd_decompose_retry.restype = ctypes.c_int
+_lib.ldd_decompose_ranked.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.ldd_decompose_ranked.restype = ctypes.c_int
 _lib.ldd_decompose_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.ldd_decompose_batch.restype = ctypes.c_int
 _lib.ldd_create_union.argtypes = [ctypes.c_int, _vp, ctypes.POINTER(_vp)]
@@ -64,6 +71,30 @@ _lib.ldd_union_size.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]
 _lib.ldd_union_size.restype = ctypes.c_int
 _lib.ldd_union_decompose.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.ldd_union_decompose.restype = ctypes.c_int
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("one_at_a_time", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("max_vertices", ctypes.c_int64),
+                ("max_arcs", ctypes.c_int64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("batch_id", ctypes.c_int64), ("submit_us", ctypes.c_double),
+                ("start_us", ctypes.c_double), ("end_us", ctypes.c_double)]
+
+
+_lib.ldd_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]
+_lib.ldd_server_create.restype = ctypes.c_int
+_lib.ldd_server_submit.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp,
+                                   ctypes.POINTER(_i64)]
+_lib.ldd_server_submit.restype = ctypes.c_int
+_lib.ldd_server_wait.argtypes = [_vp, _i64, ctypes.POINTER(RequestInfo)]
+_lib.ldd_server_wait.restype = ctypes.c_int
+_lib.ldd_server_footprint.argtypes = [_vp, _vp, ctypes.POINTER(_i64)]
+_lib.ldd_server_footprint.restype = ctypes.c_int
+_lib.ldd_server_destroy.argtypes = [_vp]
+_lib.ldd_server_destroy.restype = ctypes.c_int
 _lib.ldd_cut_edges.argtypes = [_vp, _vp, ctypes.POINTER(_i64)]
 _lib.ldd_cut_edges.restype = ctypes.c_int
 _lib.ldd_cut_edges_noalloc.argtypes = [_i32, _i64, _vp, _vp, _vp, _vp, _vp]
@@ -82,6 +113,18 @@ _lib.ldd_get_round_profile.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINT
 _lib.ldd_get_round_profile.restype = ctypes.c_int
 _lib.ldd_set_timing.argtypes = [_vp, ctypes.c_int]
 _lib.ldd_set_timing.restype = ctypes.c_int
+class Tuning(ctypes.Structure):
+    _fields_ = [("bfs_blocks_per_sm", ctypes.c_int32), ("pull_alpha", ctypes.c_int32),
+                ("pull_beta", ctypes.c_int32), ("pull_gamma", ctypes.c_int32),
+                ("probe_min_arcs", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+_lib.ldd_get_tuning.argtypes = [_vp, ctypes.POINTER(Tuning)]
+_lib.ldd_get_tuning.restype = ctypes.c_int
+_lib.ldd_set_tuning.argtypes = [_vp, ctypes.POINTER(Tuning)]
+_lib.ldd_set_tuning.restype = ctypes.c_int
+_lib.ldd_autotune.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(Tuning)]
+_lib.ldd_autotune.restype = ctypes.c_int
 _lib.ldd_set_graph_replay.argtypes = [_vp, ctypes.c_int]
 _lib.ldd_set_graph_replay.restype = ctypes.c_int
 
@@ -147,6 +190,37 @@ def ldd_decompose(g: int, beta: float, shifts, out_center, out_dist, n: int | No
     _check(_lib.ldd_decompose(g, float(beta), _addr(shifts, "f64", n, "shifts"),
                               _addr(out_center, "i32", n, "out_center"),
                               _addr(out_dist, "i32", n, "out_dist")), "ldd_decompose")
+
+
+def ldd_decompose_retry(g: int, beta: float, shifts, max_cut: int, max_radius: int, out_center,
+                        out_dist, n: int | None = None):
+    """Las Vegas loop of Theorem 1.2's proof (include/ldd.h): returns
+    (accepted index or -1, cut, radius)."""
+    k = len(shifts)
+    sp = (_vp * max(k, 1))(*[_addr(x, "f64", n, "shifts") for x in shifts])
+    cut, rad, acc = _i64(0), _i32(0), _i32(-1)
+    _check(_lib.ldd_decompose_retry(g, float(beta), k, sp, int(max_cut), int(max_radius),
+                                    _addr(out_center, "i32", n, "out_center"),
+                                    _addr(out_dist, "i32", n, "out_dist"), ctypes.byref(cut),
+                                    ctypes.byref(rad), ctypes.byref(acc)), "ldd_decompose_retry")
+    return int(acc.value), int(cut.value), int(rad.value)
+
+
+def default_bounds(n: int, m: int, beta: float, c: float = 2.0):
+    """(max_cut, max_radius) of a (beta, c ln(n) / beta) decomposition: at most
+    beta m cut edges (Definition 1.1) and radius at most c ln(n) / beta
+    (Lemma 3.2: delta_max exceeds it with probability about n^(1 - c))."""
+    import math
+    return int(math.floor(beta * m)), int(math.ceil(c * math.log(max(n, 2)) / beta))
+
+
+def ldd_decompose_ranked(g: int, levels, perm, out_center, out_dist, n: int | None = None) -> None:
+    """The permutation variant (include/ldd.h): integer levels and a tie-break
+    permutation in place of FP64 shifts."""
+    _check(_lib.ldd_decompose_ranked(g, _addr(levels, "i32", n, "levels"),
+                                     _addr(perm, "i32", n, "perm"),
+                                     _addr(out_center, "i32", n, "out_center"),
+                                     _addr(out_dist, "i32", n, "out_dist")), "ldd_decompose_ranked")
 
 
 def ldd_decompose_batch(g: int, betas, shifts, out_center, out_dist, n: int | None = None,
@@ -231,6 +305,33 @@ def ldd_set_timing(g: int, enable: bool) -> None:
     _check(_lib.ldd_set_timing(g, int(bool(enable))), "ldd_set_timing")
 
 
+def _tuning_dict(t: Tuning) -> dict:
+    return {name: getattr(t, name) for name, _ in Tuning._fields_}
+
+
+def ldd_get_tuning(g: int) -> dict:
+    t = Tuning()
+    _check(_lib.ldd_get_tuning(g, ctypes.byref(t)), "ldd_get_tuning")
+    return _tuning_dict(t)
+
+
+def ldd_set_tuning(g: int, **fields) -> None:
+    t = Tuning()
+    _check(_lib.ldd_get_tuning(g, ctypes.byref(t)), "ldd_get_tuning")
+    for k, v in fields.items():
+        setattr(t, k, v)
+    _check(_lib.ldd_set_tuning(g, ctypes.byref(t)), "ldd_set_tuning")
+
+
+def ldd_autotune(g: int, shifts, reps: int = 2, n: int | None = None) -> dict:
+    """Times decompositions of this shift vector while varying the launch
+    parameters (include/ldd.h); keeps and returns the best."""
+    t = Tuning()
+    _check(_lib.ldd_autotune(g, _addr(shifts, "f64", n, "shifts"), int(reps), ctypes.byref(t)),
+           "ldd_autotune")
+    return _tuning_dict(t)
+
+
 def ldd_set_graph_replay(g: int, enable: bool) -> None:
     _check(_lib.ldd_set_graph_replay(g, int(bool(enable))), "ldd_set_graph_replay")
 
@@ -268,6 +369,14 @@ class LddGraph:
         return ldd_decompose_batch(self.handle, betas, shifts, out_center, out_dist, self.n,
                                    want_cut)
 
+    def decompose_ranked(self, levels, perm, out_center, out_dist) -> None:
+        ldd_decompose_ranked(self.handle, levels, perm, out_center, out_dist, self.n)
+
+    def decompose_retry(self, beta: float, shifts, max_cut: int, max_radius: int, out_center,
+                        out_dist):
+        return ldd_decompose_retry(self.handle, beta, shifts, max_cut, max_radius, out_center,
+                                   out_dist, self.n)
+
     def cut_edges(self, center) -> int:
         return ldd_cut_edges(self.handle, center, self.n)
 
@@ -279,6 +388,15 @@ class LddGraph:
 
     def set_graph_replay(self, enable: bool) -> None:
         ldd_set_graph_replay(self.handle, enable)
+
+    def tuning(self) -> dict:
+        return ldd_get_tuning(self.handle)
+
+    def set_tuning(self, **fields) -> None:
+        ldd_set_tuning(self.handle, **fields)
+
+    def autotune(self, shifts, reps: int = 2) -> dict:
+        return ldd_autotune(self.handle, shifts, reps, self.n)
 
     def stats(self) -> dict:
         return ldd_get_stats(self.handle)
@@ -318,3 +436,67 @@ class LddUnion(LddGraph):
 
     def cut_edges(self, center) -> int:
         raise TypeError("a union's cut counts come from decompose()")
+
+
+def _cut_addr(out_cut):
+    """Address of a one-element int64 holder: a ctypes.c_int64 or a numpy array."""
+    if out_cut is None:
+        return None
+    if isinstance(out_cut, ctypes.c_int64):
+        return ctypes.addressof(out_cut)
+    if hasattr(out_cut, "__array_interface__") and out_cut.dtype.str == "<i8" and out_cut.size >= 1:
+        return int(out_cut.__array_interface__["data"][0])
+    raise TypeError("out_cut: need a ctypes.c_int64 or an int64 numpy array")
+
+
+class LddServer:
+    """A request server (ldd_server_* in include/ldd.h): continuous batching of
+    decompositions of resident graphs.  submit() takes host buffers and
+    returns a ticket; wait() blocks for it and returns its ldd_request_info as
+    a dict (times in microseconds on the server's clock)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_batch: int = 64, slots: int = 2,
+                 one_at_a_time: bool = False, max_vertices: int = 0, max_arcs: int = 0):
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_batch), int(slots), int(one_at_a_time),
+                           0, int(max_vertices), int(max_arcs))
+        out = _vp()
+        _check(_lib.ldd_server_create(ctypes.byref(cfg), ctypes.byref(out)), "ldd_server_create")
+        self.handle = int(out.value)
+        self._keep = {}
+
+    def submit(self, graph, beta: float, shifts, out_center, out_dist, out_cut=None) -> int:
+        n = graph.n
+        t = _i64(-1)
+        _check(_lib.ldd_server_submit(self.handle, graph.handle, float(beta),
+                                      _addr(shifts, "f64", n, "shifts"),
+                                      _addr(out_center, "i32", n, "out_center"),
+                                      _addr(out_dist, "i32", n, "out_dist"),
+                                      _cut_addr(out_cut),
+                                      ctypes.byref(t)), "ldd_server_submit")
+        self._keep[int(t.value)] = (shifts, out_center, out_dist, out_cut)
+        return int(t.value)
+
+    def wait(self, ticket: int) -> dict:
+        info = RequestInfo()
+        status = _lib.ldd_server_wait(self.handle, int(ticket), ctypes.byref(info))
+        self._keep.pop(int(ticket), None)
+        _check(status, "ldd_server_wait")
+        return {name: getattr(info, name) for name, _ in RequestInfo._fields_}
+
+    def footprint(self, graph) -> int:
+        out = _i64(0)
+        _check(_lib.ldd_server_footprint(self.handle, graph.handle, ctypes.byref(out)),
+               "ldd_server_footprint")
+        return int(out.value)
+
+    def close(self) -> None:
+        if getattr(self, "handle", 0):
+            _lib.ldd_server_destroy(self.handle)
+            self.handle = 0
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

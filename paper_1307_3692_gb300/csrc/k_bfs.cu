@@ -34,7 +34,9 @@
 // (each final level-r key is one of these, and each of these is >= the final
 // key of its vertex).  Only w's own thread writes key[w] in such a round, and a
 // vertex being lowered to level r + 1 is never read as a level-r key, so no
-// atomics are needed.  The first bottom-up round of a run examines every
+// atomics are needed.  On a union of graphs (k_union.cu) the floor is kept
+// per member: the smallest level-r rank of w's own member, since no other
+// member's key can reach w.  The first bottom-up round of a run examines every
 // vertex the BFS owns; each round lists the vertices still above level r + 1,
 // and the next bottom-up round examines only those.
 //
@@ -52,7 +54,11 @@ constexpr u32 kFull = 0xffffffffu;
 constexpr int kEdgeBatch = 4;  // arcs per thread in flight
 constexpr int kWinBatch = 3;   // window items per thread in flight
 constexpr int kPullV = 3;      // candidates per lane in flight in a bottom-up round
-constexpr u32 kProbeMinArcs = 1u << 16;  // smaller frontiers skip the key probe before atomicMin
+constexpr int kPullLong = 32;  // longer adjacency lists are scanned by the whole warp
+constexpr int kPullCoop = 4;   // neighbours per lane per step of a warp-wide scan
+// Unions of at most this many members keep their per-member floors in shared
+// memory (two tables after Smem); larger unions use the global table directly.
+constexpr u32 kSmemMembers = 4096;
 
 struct Smem {
   int owner[kBfsMaxSpan];
@@ -98,6 +104,59 @@ __device__ __forceinline__ u32 warp_min(u32 x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(kFull, x, o));
   return x;
+}
+
+__device__ __forceinline__ u64 warp_min64(u64 x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = min(x, (u64)__shfl_xor_sync(kFull, x, o));
+  return x;
+}
+
+// Records a successful next-level key (vertex v, rank) for the bottom-up
+// floor of the next round.  Plain graph: the thread's running minimum
+// (folded into the CTA's and the grid's at the barrier).  Union: the minimum
+// of v's member -- another member's smaller rank can never reach v, so the
+// floor is per member -- in the CTA's shared table s_acc (flushed to slot
+// `slot` of a.mrank before the barrier), or, for unions too large for it,
+// in a.mrank directly, read before the atomic so that the atomic only runs
+// when it lowers the entry.  A warp whose valid lanes share one member makes
+// one update.  Every lane of the warp calls this.
+template <bool U>
+__device__ __forceinline__ void note_rank(const BfsArgs& a, u32 slot, bool valid, u32 v, u32 rank,
+                                          u32& myrank, u32* s_acc) {
+  if (!U) {
+    if (valid) myrank = min(myrank, rank);
+    return;
+  }
+  if (!__any_sync(kFull, valid)) return;
+  const u32 m = valid ? __ldg(a.wmem + (v >> 5)) : 0xffffffffu;
+  const u32 lane = threadIdx.x & 31;
+  const u32 act = __ballot_sync(kFull, valid);
+  const u32 m0 = __shfl_sync(kFull, m, __ffs(act) - 1);
+  const bool one = __all_sync(kFull, !valid || m == m0);
+  const u32 r = one ? warp_min(valid ? rank : 0xffffffffu) : rank;
+  if ((one && lane == 0) || (!one && valid)) {
+    const u32 mm = one ? m0 : m;
+    if (s_acc) {
+      if (r < s_acc[mm]) atomicMin(s_acc + mm, r);
+    } else {
+      u32* p = a.mrank + (size_t)slot * a.kmem + mm;
+      if (r < ld_cg_u32(p)) atomicMin(p, r);
+    }
+  }
+}
+
+// Union: the CTA's per-member minima into slot `slot` of a.mrank, and the
+// shared table reset.  Called by the whole CTA between __syncthreads.
+__device__ __forceinline__ void flush_members(const BfsArgs& a, u32 slot, u32* s_acc) {
+  for (u32 m = threadIdx.x; m < a.kmem; m += blockDim.x) {
+    const u32 r = s_acc[m];
+    if (r != 0xffffffffu) {
+      u32* p = a.mrank + (size_t)slot * a.kmem + m;
+      if (r < ld_cg_u32(p)) atomicMin(p, r);
+      s_acc[m] = 0xffffffffu;
+    }
+  }
 }
 
 // Appends to the frontier every vertex v[i] whose bit i is set in `mask`, for
@@ -155,8 +214,9 @@ __device__ __forceinline__ void warp_append(u32 mask, const u32 (&v)[K], const B
 }
 
 // Unclaimed vertices of start bucket rr join the frontier of level rr.
+template <bool U>
 __device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u32* rv, int qi,
-                                              int qb, u32& myrank) {
+                                              int qb, u32& myrank, u32* s_acc) {
   const int lo = __ldg(a.bptr + rr), hi = __ldg(a.bptr + rr + 1);
   const u32 cnt = (u32)(hi - lo);
   const u32 lane = threadIdx.x & 31;
@@ -167,18 +227,20 @@ __device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u3
     const u32 i = base + lane;
     u32 u[1] = {0};
     bool want = false;
+    u64 k = 0;
     if (i < cnt) {
       u[0] = __ldg(rv + lo + i);
-      const u64 k = ld_cg_u64(a.key + u[0]);
+      k = ld_cg_u64(a.key + u[0]);
       want = (u32)(k >> 32) == (u32)rr;
-      if (want) myrank = min(myrank, (u32)k);
     }
+    note_rank<U>(a, (u32)qi, want, u[0], (u32)k, myrank, s_acc);
     warp_append<1>(want ? 1u : 0u, u, a, qi, qb);
   }
 }
 
+template <bool U>
 __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q, u32 E, int lvl,
-                                       int qi, int qb, u32& myrank) {
+                                       int qi, int qb, u32& myrank, u32* s_acc) {
   const u32 nb = (E + kBfsBase - 1) / kBfsBase;
   u32 k = (nb + gridDim.x - 1) / gridDim.x;
   k = max(1u, min(k, (u32)(kBfsMaxSpan / kBfsBase)));
@@ -188,7 +250,7 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
   const int* qrow = a.qrow[cur];
   const u32* qoff = a.qoff[cur];
   const u32 lvl_next = (u32)lvl + 1;
-  const bool probe = E >= kProbeMinArcs;
+  const bool probe = E >= a.probe_min_arcs;  // smaller frontiers skip the key probe
   for (u32 sc = blockIdx.x; sc < nsuper; sc += gridDim.x) {
     const u32 b0 = sc * k, b1 = min(b0 + k, nb);
     const u32 e0 = b0 * kBfsBase, e1 = min(b1 * kBfsBase, E);
@@ -251,14 +313,17 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
 #pragma unroll
       for (int i = 0; i < kEdgeBatch; ++i)
         cur[i] = (w[i] < a.n) ? (probe ? ld_cg_u64(a.key + w[i]) : ~0ull) : 0ull;
-      u32 mask = 0;
+      u32 mask = 0, won = 0;
 #pragma unroll
       for (int i = 0; i < kEdgeBatch; ++i)
         if (cand[i] < cur[i]) {
           const u64 old = atomicMin(a.key + w[i], cand[i]);
-          if (old > cand[i]) myrank = min(myrank, (u32)cand[i]);
+          if (old > cand[i]) won |= 1u << i;
           if ((u32)(old >> 32) > lvl_next) mask |= 1u << i;
         }
+#pragma unroll
+      for (int i = 0; i < kEdgeBatch; ++i)
+        note_rank<U>(a, (u32)qi, (won >> i) & 1u, w[i], (u32)cand[i], myrank, s_acc);
       warp_append<kEdgeBatch>(mask, w, a, qi, qb);
     }
     __syncthreads();
@@ -302,14 +367,15 @@ __device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], u3
 // scans in lock-step, one neighbour each per step, so that up to kPullV
 // independent loads are in flight per lane.  Adds the arcs it scans and the
 // vertices it examines to the statistics.
-__device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minrank, int qi, int qb,
-                                           bool from_list, const u32* cand, u32 ncand,
-                                           u32* ulist_out, u32* ucnt_out, u32& myrank) {
+template <bool U>
+__device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minrank, u32 mslot,
+                                           int qi, int qb, bool from_list, const u32* cand,
+                                           u32 ncand, u32* ulist_out, u32* ucnt_out,
+                                           u32& myrank, u32* s_acc, const u32* s_floor) {
   constexpr u32 kNone = 0xffffffffu;
   u32 scanned = 0, examined = 0;
   const u32 lane = threadIdx.x & 31;
   const u32 L = (u32)lvl;
-  const u64 floor_key = ((u64)(L + 1) << 32) | minrank;
   if (!from_list && a.active) {  // the first bottom-up round: the BFS's own vertices
     from_list = true;
     cand = a.active;
@@ -346,13 +412,26 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
       }
     }
     u64 best[kPullV];
+    u32 fr[kPullV];  // floor rank: nothing beats (L + 1, fr); union: w's own member's
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      fr[j] = minrank;
+      if (U && w[j] != kNone) {
+        const u32 m = __ldg(a.wmem + (w[j] >> 5));
+        fr[j] = s_floor ? s_floor[m] : ld_cg_u32(a.mrank + (size_t)mslot * a.kmem + m);
+      }
+    }
+    const u64 lvl_key = (u64)(L + 1) << 32;
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       best[j] = kw[j];
       if (w[j] != kNone) ++examined;
-      if (!((u32)(kw[j] >> 32) > L && kw[j] > floor_key)) re[j] = e[j];  // settled or unbeatable
+      if (!((u32)(kw[j] >> 32) > L && kw[j] > (lvl_key | fr[j]))) re[j] = e[j];  // settled or unbeatable
+      if (U && fr[j] == 0xffffffffu) re[j] = e[j];  // w's member has no level-L key
     }
-    for (;;) {  // one neighbour of every still-scanning candidate per step
+    // one neighbour of every still-scanning candidate per step, for at most
+    // kPullLong steps: most scans stop at their first neighbours
+    for (int step = 0; step < kPullLong; ++step) {
       bool any = false;
       u32 vv[kPullV];
 #pragma unroll
@@ -372,21 +451,60 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
 #pragma unroll
       for (int j = 0; j < kPullV; ++j) {
         if ((u32)(kv[j] >> 32) == L) best[j] = min(best[j], kv[j] + kLevelOne);
-        if (best[j] <= floor_key) re[j] = e[j];  // nothing can beat (L + 1, minrank)
+        if (best[j] <= (lvl_key | fr[j])) re[j] = e[j];  // nothing can beat (L + 1, fr)
       }
     }
-    u32 mask = 0, keep = 0;
+    // scans still going after kPullLong neighbours (hubs with no early exit):
+    // the warp takes them one at a time, 32 x kPullCoop coalesced neighbours
+    // per step, with the same early exit per step
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      u32 lm = __ballot_sync(kFull, e[j] < re[j]);
+      while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int eb = __shfl_sync(kFull, e[j], src), ee = __shfl_sync(kFull, re[j], src);
+        const u64 fj = lvl_key | __shfl_sync(kFull, fr[j], src);
+        u64 b = __shfl_sync(kFull, best[j], src);
+        int pos = eb;
+        while (pos < ee) {
+          u32 vq[kPullCoop];
+#pragma unroll
+          for (int q = 0; q < kPullCoop; ++q) {
+            const int idx = pos + q * 32 + (int)lane;
+            vq[q] = idx < ee ? (u32)__ldg(a.col + idx) : kNone;
+          }
+          u64 lb = ~0ull;
+#pragma unroll
+          for (int q = 0; q < kPullCoop; ++q) {
+            const u64 kq = vq[q] < a.n ? ld_cg_u64(a.key + vq[q]) : ~0ull;
+            if ((u32)(kq >> 32) == L) lb = min(lb, kq + kLevelOne);
+          }
+          b = min(b, warp_min64(lb));
+          pos += 32 * kPullCoop;
+          if (b <= fj) break;  // warp-uniform: nothing can beat (L + 1, minrank)
+        }
+        if ((int)lane == src) {
+          best[j] = b;
+          scanned += (u32)(min(pos, ee) - eb);
+        }
+      }
+    }
+    u32 mask = 0, keep = 0, won = 0;
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       const bool pending = w[j] != kNone && (u32)(kw[j] >> 32) > L;
       if (pending && best[j] < kw[j]) {
         a.key[w[j]] = best[j];  // only this thread writes key[w] in a bottom-up round
-        myrank = min(myrank, (u32)best[j]);
+        won |= 1u << j;
         if ((u32)(kw[j] >> 32) > L + 1) mask |= 1u << j;
       }
       // still above level L + 1: examined again by a following bottom-up round
       if (pending && (u32)(min(best[j], kw[j]) >> 32) > L + 1) keep |= 1u << j;
     }
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j)
+      note_rank<U>(a, (u32)qi, (won >> j) & 1u, w[j], (u32)best[j], myrank, s_acc);
     warp_append<kPullV>(mask, w, a, qi, qb);
     warp_list_append<kPullV>(keep, w, ulist_out, ucnt_out);
   }
@@ -401,9 +519,19 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
   }
 }
 
+// U: a union of graphs (per-member bottom-up floors); a separate instance so
+// that the plain kernel carries none of it.
+template <bool U>
 __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  // union with few enough members: per-member next-level minima and
+  // current-level floors in shared memory, after Smem
+  u32* s_acc = (U && a.kmem <= kSmemMembers)
+                   ? reinterpret_cast<u32*>(smem_raw + sizeof(Smem)) : nullptr;
+  u32* s_floor = s_acc ? s_acc + kSmemMembers : nullptr;
+  if (s_acc)
+    for (u32 m = threadIdx.x; m < a.kmem; m += blockDim.x) s_acc[m] = 0xffffffffu;
   Control* ctl = a.ctl;
   if (ld_acquire_u32(&ctl->err) != 0u) return;  // validation failed upstream
   const int A = ctl->A;
@@ -417,8 +545,12 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
   __syncthreads();
 
   // Level 0: the vertices with the largest integer shift part start.
-  append_bucket(a, 0, rv, 0, 0, myrank);
+  append_bucket<U>(a, 0, rv, 0, 0, myrank, s_acc);
   post_cta_min(s, myrank);
+  if (s_acc) {
+    __syncthreads();
+    flush_members(a, 0, s_acc);
+  }
   grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[0], &s.minrank);
   const bool profiler = blockIdx.x == 0 && threadIdx.x == 0;
   if (profiler) {
@@ -445,6 +577,9 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
       ctl->minrank[(phase + 2) % 3] = 0xffffffffu;
       ctl->ucnt[(phase + 2) % 3] = 0;
     }
+    if (U)  // the members' floors of the slot that the next round fills
+      for (u32 m = blockIdx.x * blockDim.x + threadIdx.x; m < a.kmem; m += G * blockDim.x)
+        a.mrank[(size_t)((phase + 2) % 3) * a.kmem + m] = 0xffffffffu;
     const int qi = (int)((phase + 1) % 3), qb = (int)((phase + 1) & 1);
     int nlvl;
     if (Q > 0) {
@@ -457,15 +592,20 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
       else if (pulling && (u64)Q * a.pull_beta < a.n_active)
         pulling = false;
       if (pulling) {
-        pull_round(a, lvl, minrank, qi, qb, was_pulling, a.ulist[phase & 1], ncand,
-                   a.ulist[(phase + 1) & 1], &ctl->ucnt[qi], myrank);
+        if (s_floor) {  // this level's per-member floors, read once per CTA
+          for (u32 m = threadIdx.x; m < a.kmem; m += blockDim.x)
+            s_floor[m] = ld_cg_u32(a.mrank + (size_t)(phase % 3) * a.kmem + m);
+          __syncthreads();
+        }
+        pull_round<U>(a, lvl, minrank, phase % 3, qi, qb, was_pulling, a.ulist[phase & 1], ncand,
+                      a.ulist[(phase + 1) & 1], &ctl->ucnt[qi], myrank, s_acc, s_floor);
         ++pulls;
       } else {
-        expand(a, s, (int)(phase & 1), Q, E, lvl, qi, qb, myrank);
+        expand<U>(a, s, (int)(phase & 1), Q, E, lvl, qi, qb, myrank, s_acc);
         push_arcs += E;
       }
       if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
-      if (lvl + 1 <= A) append_bucket(a, lvl + 1, rv, qi, qb, myrank);
+      if (lvl + 1 <= A) append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc);
       nlvl = lvl + 1;
     } else {
       if (lvl + 1 > A) break;
@@ -474,11 +614,15 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
       const int rr = (int)__ldg(rk + start);  // next non-empty start bucket
       if (rr > A) break;                      // only vertices the BFS does not handle remain
       if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
-      append_bucket(a, rr, rv, qi, qb, myrank);
+      append_bucket<U>(a, rr, rv, qi, qb, myrank, s_acc);
       nlvl = rr;
     }
     if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][1] = clock64();
     post_cta_min(s, myrank);
+    if (s_acc) {
+      __syncthreads();
+      flush_members(a, (u32)qi, s_acc);
+    }
     grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[qi], &s.minrank);
     ++phase;
     lvl = nlvl;
@@ -502,14 +646,22 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
 size_t bfs_smem_bytes() { return sizeof(Smem); }
 
 int bfs_grid_size(int num_sms, int* blocks_per_sm) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_bfs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    attr_set = true;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(k_bfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(Smem));
+    cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(Smem) + 2 * kSmemMembers * sizeof(u32)));
+    attr_set[dev] = true;
   }
-  int per_sm = 0;
-  cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs, kBfsThreads, sizeof(Smem));
+  int per_sm = 0, per_sm_u = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs<false>,
+                                                                kBfsThreads, sizeof(Smem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm_u, k_bfs<true>, kBfsThreads, sizeof(Smem) + 2 * kSmemMembers * sizeof(u32));
+  per_sm = min(per_sm, per_sm_u);
   if (e != cudaSuccess || per_sm < 1) return -1;
   per_sm = per_sm > 2 ? 2 : per_sm;
   *blocks_per_sm = per_sm;
@@ -519,8 +671,9 @@ int bfs_grid_size(int num_sms, int* blocks_per_sm) {
 int launch_bfs(const BfsArgs& a, int grid, cudaStream_t s, cudaError_t* err) {
   BfsArgs copy = a;
   void* args[] = {&copy};
-  *err = cudaLaunchCooperativeKernel((const void*)k_bfs, dim3(grid), dim3(kBfsThreads), args,
-                                     sizeof(Smem), s);
+  const void* fn = a.mrank ? (const void*)k_bfs<true> : (const void*)k_bfs<false>;
+  const size_t smem = sizeof(Smem) + (a.mrank ? 2 * kSmemMembers * sizeof(u32) : 0);
+  *err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBfsThreads), args, smem, s);
   return *err == cudaSuccess ? 1 : -1;
 }
 

@@ -277,6 +277,16 @@ __global__ void __launch_bounds__(256) k_small_comp(const u32* __restrict__ comp
   }
 }
 
+// Largest value of x[0 .. n) (non-negative ints) into *out (zero on entry).
+__global__ void __launch_bounds__(256) k_max_i32(const int* __restrict__ x, u32 n, u32* out) {
+  u32 m = 0;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = max(m, (u32)max(x[i], 0));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 u32 grid_for(u32 n, int num_sms) {
   return (u32)max(1ll, min((long long)(n + 255) / 256, (long long)num_sms * 8));
 }
@@ -309,6 +319,12 @@ int launch_cut(const int2* list, u32 m, const int* center, const u32* hot, u32 n
   k_cut<<<g, kCutThreads, (size_t)n_hot * sizeof(int), s>>>(list, m, center, hot_center, n_hot,
                                                             out);
   return launches + 1;
+}
+
+int launch_max_dist(const int* dist, u32 n, u32* out, int num_sms, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(u32), s);
+  k_max_i32<<<grid_for(n, num_sms), 256, 0, s>>>(dist, n, out);
+  return 1;
 }
 
 int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s) {

@@ -869,6 +869,34 @@ __global__ void __launch_bounds__(256) k_rscatter(const int* __restrict__ a,
   }
 }
 
+// ---------------------------------------------------------------- ranked variant
+// Section 4: the fractional parts of the shifts only order the vertices of one
+// integer level, and a random permutation of the vertices can stand in for
+// them.  Input: the integer parts a_u (levels[u] >= 0) and the permutation
+// (perm[u] = u's tie-break position, smaller first).  The rank is perm itself;
+// order[perm[u]] = u, with a duplicate position detected by the exchange
+// (order is all ones on entry).  Bad input sets kErrPermArg.
+__global__ void __launch_bounds__(256) k_ranked_split(const int* __restrict__ levels,
+                                                      const int* __restrict__ perm, u32 n,
+                                                      int* __restrict__ a_out, u32* order,
+                                                      Control* ctl) {
+  int amax = 0;
+  u32 err = 0;
+  for (u32 u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    const int a = levels[u];
+    const int p = perm[u];
+    if (a < 0 || p < 0 || (u32)p >= n) {
+      err |= kErrPermArg;
+      a_out[u] = 0;
+      continue;
+    }
+    a_out[u] = a;
+    amax = max(amax, a);
+    if (atomicExch(order + p, u) != 0xffffffffu) err |= kErrPermArg;  // p taken twice
+  }
+  finish_split(err, amax, ctl);
+}
+
 u32 grid_stride_blocks(u32 n, int num_sms) {
   return (u32)max(1ll, min((long long)(n + 255) / 256, (long long)num_sms * 8));
 }
@@ -967,6 +995,27 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
                         (long long)r.num_sms * 8),
                256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));
   return launches + 5;
+}
+
+int launch_ranked_and_buckets(const RankBufs& r, const int* levels, const int* perm,
+                              cudaStream_t s) {
+  const u32 n = r.n;
+  Control* ctl = r.ctl;
+  const u32 gs = grid_stride_blocks(n, r.num_sms);
+  const u32 rtiles = (r.bptr_cap + kScanTile - 1) / kScanTile;
+  u32* rcnt = reinterpret_cast<u32*>(r.bptr);
+  const u32* rank = reinterpret_cast<const u32*>(perm);
+  cudaMemsetAsync(r.order, 0xff, (size_t)n * 4, s);
+  k_ranked_split<<<gs, 256, 0, s>>>(levels, perm, n, r.a, r.order, ctl);
+  k_zero_rounds<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.bptr, r.bptr_cap,
+                                                                            ctl);
+  k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
+  k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
+                                               &ctl->tile_ctr[1], nullptr, ctl);
+  k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
+                        (long long)r.num_sms * 8),
+               256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));
+  return 5;
 }
 
 }  // namespace ldd

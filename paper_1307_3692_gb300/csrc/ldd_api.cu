@@ -21,7 +21,7 @@
 #include <vector>
 
 #include "../../include/ldd.h"
-#include "ldd_internal.cuh"
+#include "ldd_graph.cuh"
 
 using namespace ldd;
 
@@ -31,11 +31,10 @@ static_assert(offsetof(Control, mask_f) == kCtlBfsStateOffset + kCtlBfsStateByte
 static_assert(offsetof(Control, cut) + sizeof(u64) == kCtlHeaderBytes, "control layout");
 static_assert(offsetof(Control, minrank) == kCtlMinrankOffset, "control layout");
 
-namespace {
+namespace ldd {
 
 thread_local char g_last_error[512] = "";
 
-int fail(int status, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 int fail(int status, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -43,28 +42,6 @@ int fail(int status, const char* fmt, ...) {
   va_end(ap);
   return status;
 }
-
-#define CUDA_TRY(expr)                                                                   \
-  do {                                                                                   \
-    cudaError_t e_ = (expr);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail(LDD_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
-                  __LINE__);                                                             \
-  } while (0)
-
-// Restores the caller's current device when a call returns.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && (prev == dev || cudaSetDevice(dev) == cudaSuccess))
-      ok = true;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 // True for device or managed memory; false for pageable or pinned host memory.
 bool is_device_ptr(const void* p) {
@@ -86,111 +63,20 @@ u32 env_u32(const char* name, u32 dflt) {
   return (end && *end == 0 && x > 0 && x <= 0xffffffffUL) ? (u32)x : dflt;
 }
 
-}  // namespace
-
-namespace ldd {
 // Sets the text ldd_last_error() returns on this thread (used by entry points
 // defined in other translation units).
 void record_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 }  // namespace ldd
 
-struct ldd_graph {
-  int32_t n = 0;
-  int64_t nnz = 0;
-  int device = 0;
-  int num_sms = 0;
-  cudaStream_t stream = nullptr;
-  u32 n_active = 0;
-  u64 nnz_active = 0;
-  u32 m_up = 0;                // arcs (v, w) with v < w
-  // device CSR and graph tables
-  int* d_row = nullptr;
-  int* d_col = nullptr;
-  int2* d_up = nullptr;        // the arcs (v, w) with v < w; after component labelling, the
-                               // cut list (cold, hot) of launch_cut
-  u32* d_active = nullptr;     // vertices the BFS handles, ascending (when few enough)
-  u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
-  int* d_hot_center = nullptr; // their labels, gathered per cut count
-  u32 n_hot = 0;
-  u32* d_excl = nullptr;      // bit v: v is not handled by the BFS (no arcs or a small component)
-  u32* d_solo = nullptr;      // bit v: v is alone in its component (inside the d_excl allocation)
-  SmallComps sc;              // components of 2..32 vertices, solved one warp each
-  // scratch arena
-  void* arena = nullptr;
-  double* d_shift = nullptr;
-  int* d_a = nullptr;
-  u64* d_k[2] = {nullptr, nullptr};
-  u32* d_v[2] = {nullptr, nullptr};
-  u64* d_status = nullptr;
-  u32* d_order = nullptr;
-  u64* d_key = nullptr;
-  u32* d_qv[2] = {nullptr, nullptr};
-  int* d_qrow[2] = {nullptr, nullptr};
-  u32* d_qoff[2] = {nullptr, nullptr};
-  u32* d_cf[2] = {nullptr, nullptr};
-  u32* d_ulist[2] = {nullptr, nullptr};
-  void* d_slots = nullptr;
-  int* d_center = nullptr;
-  int* d_dist = nullptr;
-  Control* d_ctl = nullptr;
-  int* d_bptr = nullptr;
-  u32* d_rcur = nullptr;
-  u32* d_acnt = nullptr;       // start-round counts by floor value (all zero between calls)
-  bool acnt_dirty = true;      // d_acnt may hold counts: clear before the next fast path
-  u32 bptr_cap = 0;
-  size_t status_bytes = 0;
-  u32 epoch = 0;
-  // host side
-  unsigned char* h_hdr = nullptr;  // pinned copy of the control header
-  int bfs_grid = 0;
-  int bfs_per_sm = 0;
-  u32 spin_limit = 0;
-  u32 pull_alpha = 0;
-  u32 pull_beta = 0;
-  u32 pull_gamma = 0;
-  bool timing = false;
-  cudaEvent_t ev[8] = {};
-  // pipelined batches (ldd_decompose_batch), set up on first use
-  cudaStream_t copy_in = nullptr, copy_out = nullptr;
-  cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_out[2] = {};
-  void* batch_arena = nullptr;  // two shift slots (8n each) and two output slots (8n each)
-  // disjoint unions (ldd_create_union): member offsets and caller-layout staging
-  struct Union {
-    u32 k = 0;
-    u32 total = 0;                 // n_0 + ... + n_{k-1}: caller-layout length
-    u32 nchunk = 0;                // cut chunks (chunk_off[k])
-    std::vector<u32> h_ooff;       // caller-layout offsets, k + 1
-    std::vector<u32> h_voff;       // union-vertex offsets, k + 1
-    UnionMember* d_mem = nullptr;  // k member views (valid only while building)
-    u32* d_offs = nullptr;         // 8 arrays of k + 1: v, e, u, c, m, a, o, chunk
-    UnionOffsets off{};
-    double* d_shift_in = nullptr;  // [total] caller-layout shifts from the host
-    int* d_out_c = nullptr;        // [total] caller-layout labels (host outputs, cut count)
-    int* d_out_d = nullptr;        // [total]
-    u64* d_cut = nullptr;          // [k]
-    u32* d_wmem = nullptr;         // [N / 32] member of every 32-vertex word
-    int* d_amax = nullptr;         // [k] largest floor of each member, then [k] its lift
-  };
-  Union* uni = nullptr;
-  // captured CUDA graph of one fast-path decomposition (ldd_set_graph_replay)
-  bool replay = false;
-  bool replay_broken = false;        // capture failed once: regular path only
-  int regular_runs = 0;              // regular decompositions so far (capture waits for one)
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec[2] = {};     // [with union cut counts]
-  int replay_launches[2] = {};
-  u64* h_cut = nullptr;              // pinned copy of a union's cut counts
-  ldd_stats stats;
-};
 
-namespace {
+namespace ldd {
 
 int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_row);
   cudaFree(g->d_col);
   cudaFree(g->d_up);
   cudaFree(g->d_hot);
-  cudaFree(g->d_active);
+  if (!g->uni) cudaFree(g->d_active);  // a union's list lives in d_active_buf
   cudaFree(g->d_hot_center);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
@@ -217,6 +103,7 @@ int free_graph_memory(ldd_graph* g) {
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   if (g->h_cut) cudaFreeHost(g->h_cut);
   if (g->uni) {
+    cudaFree(g->uni->d_active_buf);
     cudaFree(g->uni->d_mem);
     cudaFree(g->uni->d_offs);
     cudaFree(g->uni->d_shift_in);
@@ -224,6 +111,7 @@ int free_graph_memory(ldd_graph* g) {
     cudaFree(g->uni->d_cut);
     cudaFree(g->uni->d_wmem);
     cudaFree(g->uni->d_amax);
+    cudaFree(g->uni->d_mrank);
     delete g->uni;
     g->uni = nullptr;
   }
@@ -464,6 +352,10 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.pull_alpha = g->pull_alpha;
   a.pull_beta = g->pull_beta;
   a.pull_gamma = g->pull_gamma;
+  a.probe_min_arcs = g->probe_min_arcs;
+  a.wmem = g->uni ? g->uni->d_wmem : nullptr;
+  a.mrank = g->uni ? g->uni->d_mrank : nullptr;
+  a.kmem = g->uni ? g->uni->k : 0;
   return a;
 }
 
@@ -475,6 +367,8 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
   launches += launch_small_comp(g->sc, g->d_key, &g->d_ctl->err, g->num_sms, s);
   if (g->n_active > 0) {
     cudaError_t e = cudaMemsetAsync((char*)g->d_ctl + kCtlMinrankOffset, 0xff, 3 * sizeof(u32), s);
+    if (e == cudaSuccess && g->uni)
+      e = cudaMemsetAsync(g->uni->d_mrank, 0xff, 3 * (size_t)g->uni->k * sizeof(u32), s);
     if (e != cudaSuccess) {
       *status = fail(LDD_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
       return -1;
@@ -516,6 +410,7 @@ int finish_setup(ldd_graph* g) {
   g->pull_alpha = env_u32("LDD_PULL_ALPHA", 14);
   g->pull_beta = env_u32("LDD_PULL_BETA", 24);
   g->pull_gamma = env_u32("LDD_PULL_GAMMA", 8);
+  g->probe_min_arcs = env_u32("LDD_PROBE_MIN_ARCS", 1u << 16);
   g->stats.n = g->n;
   g->stats.nnz = g->nnz;
   g->stats.n_active = g->n_active;
@@ -589,6 +484,8 @@ void header_stats(ldd_graph* g, const Header& h, bool exact64) {
 
 int header_error(u32 err) {
   if (err & kErrShiftArg) return fail(LDD_ERR_ARG, "a shift is NaN or negative");
+  if (err & kErrPermArg)
+    return fail(LDD_ERR_ARG, "levels must be >= 0 and perm a permutation of 0 .. n-1");
   if (err & kErrShiftRange) return fail(LDD_ERR_RANGE, "a shift is >= 2^31 or infinite");
   if (err & kErrTimeout) return fail(LDD_ERR_TIMEOUT, "a device-side wait ran out");
   return fail(LDD_ERR_CUDA, "device error bits 0x%x", err);
@@ -607,7 +504,7 @@ void drop_replay(ldd_graph* g) {
 // buckets, the round loop, finalize, with the retries of the fast rank path.
 // Fills the device-side statistics of g->stats.
 int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* dist,
-                        int* launches_out) {
+                        int* launches_out, const int* d_levels, const int* d_perm) {
   cudaStream_t s = g->stream;
   int launches = 0;
   RankBufs rb = rank_bufs(g, d_shift);
@@ -628,8 +525,9 @@ int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* d
     rb.acnt = g->d_acnt;
     rb.acnt_dirty = g->acnt_dirty;
     rb.bptr_cap = g->bptr_cap;
-    if (!exact64) g->acnt_dirty = true;  // until this attempt has consumed the counts
-    launches += launch_rank_and_buckets(rb, exact64, s);
+    if (!exact64 && !d_levels) g->acnt_dirty = true;  // until this attempt has consumed the counts
+    launches += d_levels ? launch_ranked_and_buckets(rb, d_levels, d_perm, s)
+                         : launch_rank_and_buckets(rb, exact64, s);
     record(g, 2);
     const int l = run_bfs_finalize(g, center, dist, &status);
     if (l < 0) return status;
@@ -639,7 +537,7 @@ int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* d
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&h, g->h_hdr, sizeof(h));
-    if (!exact64 && h.err == 0) g->acnt_dirty = false;  // k_round_counts cleared them
+    if (!exact64 && !d_levels && h.err == 0) g->acnt_dirty = false;  // k_round_counts cleared them
     const u32 retry = kErrRankRetry | kErrBucketCap;
     if (h.err == 0 || (h.err & ~retry) != 0) break;
     // A fraction bucket too full to rank in place (crafted shifts): every
@@ -695,8 +593,8 @@ int enqueue_fast(ldd_graph* g, bool want_cut) {
   if (cudaMemsetAsync(g->d_status, 0, words * sizeof(u64), s) != cudaSuccess) return -1;
   if (g->uni) {
     ldd_graph::Union& U = *g->uni;
-    launches += launch_union_spread(U.d_shift_in, U.off, U.k, (u32)g->n, g->d_excl, g->d_shift, U.d_amax,
-                                    U.d_amax + U.k, g->num_sms, s);
+    launches += launch_union_spread(U.d_shift_in, U.off, U.k, (u32)g->n, g->d_excl, g->d_shift,
+                                    U.d_amax, U.d_amax + U.k, g->num_sms, s);
   }
   u32 epoch = 0;  // the two scans run with epochs 1 and 2 on cleared status words
   RankBufs rb = rank_bufs(g, g->d_shift);
@@ -710,8 +608,8 @@ int enqueue_fast(ldd_graph* g, bool want_cut) {
   if (g->uni && want_cut) {
     ldd_graph::Union& U = *g->uni;
     if (cudaMemsetAsync(U.d_cut, 0, (size_t)U.k * 8, s) != cudaSuccess) return -1;
-    launches += launch_union_cut(g->d_up, U.d_offs + 7 * ((size_t)U.k + 1), U.nchunk, U.off, U.k,
-                                 U.d_out_c, U.d_cut, g->num_sms, s);
+    launches += launch_union_cut(g->d_up, U.d_offs + 7 * ((size_t)U.cap.k + 1), U.nchunk, U.off,
+                                 U.k, U.d_out_c, U.d_cut, g->num_sms, s);
     if (cudaMemcpyAsync(g->h_cut, U.d_cut, (size_t)U.k * 8, cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
       return -1;
@@ -842,7 +740,189 @@ int setup_batch(ldd_graph* g) {
   return LDD_OK;
 }
 
-}  // namespace
+// ---------------------------------------------------------------- unions
+UnionCaps union_needs(int k, ldd_graph* const* members) {
+  UnionCaps c;
+  c.k = (u32)k;
+  for (int i = 0; i < k; ++i) {
+    const ldd_graph* m = members[i];
+    c.N += ((u64)m->n + 31) / 32 * 32;
+    c.E += (u64)m->nnz;
+    c.M += m->m_up;
+    c.C += m->sc.ncomp;
+    c.T += m->sc.total;
+    c.total += (u64)m->n;
+  }
+  return c;
+}
+
+u64 union_bytes(const UnionCaps& c) {
+  // tables: row, col, cut list, masks, small components, active list, word
+  // members; staging: shifts in, outputs, offsets; scratch arena; start
+  // buckets (three tables of N + 2)
+  const u64 N = c.N, words = std::max<u64>(N / 32, 1);
+  u64 b = 4 * (N + 1) + 4 * c.E + 8 * c.M + 8 * words + 8 * c.C + 8 * c.T + 4 * N + 4 * words;
+  b += 16 * c.total + 8 * c.total + 32ull * (c.k + 1) + 8ull * c.k + sizeof(UnionMember) * c.k;
+  const u64 nk = std::max<u64>(N, 64);
+  b += 8 * N + 4 * N + 16 * nk + 8 * N + ((N + kSortTile - 1) / kSortTile + 1) * 2048 + 4 * N +
+       8 * N + 24 * N + 8 * (c.E / kBfsBase + 2) + 8 * N + (N ? fraction_slot_bytes((u32)N) : 0) +
+       8 * N + sizeof(Control);
+  b += 12 * (N + 2);
+  return b;
+}
+
+int union_alloc(ldd_graph** out, int dev, const UnionCaps& c) {
+  *out = nullptr;
+  ldd_graph* g = new (std::nothrow) ldd_graph();
+  if (!g) return fail(LDD_ERR_OOM, "host allocation failed");
+  auto bail = [&](int status) {
+    free_graph_memory(g);
+    delete g;
+    return status;
+  };
+  g->uni = new (std::nothrow) ldd_graph::Union();
+  if (!g->uni) return bail(fail(LDD_ERR_OOM, "host allocation failed"));
+  ldd_graph::Union& U = *g->uni;
+  U.cap = c;
+  memset(&g->stats, 0, sizeof(g->stats));
+  g->device = dev;
+  if (cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LDD_ERR_CUDA, "no usable CUDA device"));
+  }
+  const u64 N = c.N, words = std::max<u64>(N / 32, 1), K = std::max<u32>(c.k, 1);
+  const u64 total = std::max<u64>(c.total, 1);
+  if (cudaMalloc(&g->d_row, (N + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_col, std::max<u64>(c.E, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_up, std::max<u64>(c.M, 1) * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&g->d_excl, 2 * words * 4) != cudaSuccess ||
+      cudaMalloc(&g->sc.comp_off, std::max<u64>(c.C, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->sc.comp_len, std::max<u64>(c.C, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->sc.comp_v, std::max<u64>(c.T, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->sc.adj, std::max<u64>(c.T, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&U.d_active_buf, std::max<u64>(N, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&U.d_mem, K * sizeof(UnionMember)) != cudaSuccess ||
+      cudaMalloc(&U.d_offs, 8 * (K + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&U.d_shift_in, total * 8) != cudaSuccess ||
+      cudaMalloc(&U.d_out_c, total * 8) != cudaSuccess ||
+      cudaMalloc(&U.d_cut, K * 8) != cudaSuccess ||
+      cudaMalloc(&U.d_wmem, words * 4) != cudaSuccess ||
+      cudaMalloc(&U.d_amax, 2 * K * 4) != cudaSuccess ||
+      cudaMalloc(&U.d_mrank, 3 * K * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(LDD_ERR_OOM, "device allocation of a union (%llu vertices, %llu arcs) "
+                     "failed", (unsigned long long)N, (unsigned long long)c.E));
+  }
+  g->d_solo = g->d_excl + words;
+  U.d_out_d = U.d_out_c + total;
+  const u32* d = U.d_offs;
+  const size_t K1 = K + 1;
+  U.off = UnionOffsets{d, d + K1, d + 2 * K1, d + 3 * K1, d + 4 * K1, d + 5 * K1, d + 6 * K1};
+  // the scratch arena and launch set-up are sized by the capacities
+  g->n = (int32_t)N;
+  g->nnz = (int64_t)c.E;
+  int rc = finish_setup(g);
+  if (rc != LDD_OK) return bail(rc);
+  *out = g;
+  return LDD_OK;
+}
+
+int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, bool sync) {
+  ldd_graph::Union& U = *g->uni;
+  const UnionCaps need = union_needs(k, members);
+  if ((u32)k > U.cap.k || need.N > U.cap.N || need.E > U.cap.E || need.M > U.cap.M ||
+      need.C > U.cap.C || need.T > U.cap.T || need.total > U.cap.total)
+    return fail(LDD_ERR_RANGE, "members exceed the union's capacity");
+  const size_t K1 = (size_t)U.cap.k + 1;
+  std::vector<u32> offs(8 * K1, 0);
+  bool all_active = true;
+  u64 nnz_active = 0, n_active = 0;
+  auto at = [&](int t, int i) -> u32& { return offs[(size_t)t * K1 + (size_t)i]; };
+  for (int i = 0; i < k; ++i) {
+    const ldd_graph* m = members[i];
+    at(0, i + 1) = at(0, i) + (u32)(((u64)m->n + 31) / 32 * 32);
+    at(1, i + 1) = at(1, i) + (u32)m->nnz;
+    at(2, i + 1) = at(2, i) + m->m_up;
+    at(3, i + 1) = at(3, i) + m->sc.ncomp;
+    at(4, i + 1) = at(4, i) + m->sc.total;
+    at(5, i + 1) = at(5, i) + m->n_active;
+    at(6, i + 1) = at(6, i) + (u32)m->n;
+    at(7, i + 1) = at(7, i) + (m->m_up + kUnionCutChunk - 1) / kUnionCutChunk;
+    if (m->n_active > 0 && !m->d_active) all_active = false;
+    nnz_active += m->nnz_active;
+    n_active += m->n_active;
+  }
+  g->n = (int32_t)need.N;
+  g->nnz = (int64_t)need.E;
+  g->m_up = (u32)need.M;
+  g->sc.ncomp = (u32)need.C;
+  g->sc.total = (u32)need.T;
+  g->n_active = (u32)n_active;
+  g->nnz_active = nnz_active;
+  g->d_active = (all_active && n_active > 0) ? U.d_active_buf : nullptr;
+  U.k = (u32)k;
+  U.total = (u32)need.total;
+  U.nchunk = at(7, k);
+  U.h_voff.assign(offs.begin(), offs.begin() + k + 1);
+  U.h_ooff.assign(offs.begin() + 6 * K1, offs.begin() + 6 * K1 + k + 1);
+  std::vector<UnionMember> mv((size_t)k);
+  for (int i = 0; i < k; ++i) {
+    const ldd_graph* m = members[i];
+    UnionMember& d = mv[(size_t)i];
+    d.row = m->d_row;
+    d.col = m->d_col;
+    d.up = m->d_up;
+    d.hot = m->d_hot;
+    d.excl = m->d_excl;
+    d.solo = m->d_solo;
+    d.comp_off = m->sc.comp_off;
+    d.comp_len = m->sc.comp_len;
+    d.comp_v = m->sc.comp_v;
+    d.adj = m->sc.adj;
+    d.active = m->d_active;
+    d.n = (u32)m->n;
+    d.nnz = (u32)m->nnz;
+  }
+  drop_replay(g);  // captured graphs hold the old sizes
+  CUDA_TRY(cudaMemcpyAsync(U.d_mem, mv.data(), mv.size() * sizeof(UnionMember),
+                           cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(U.d_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, s));
+  UnionTables t{g->d_row, g->d_col, g->d_up, g->d_excl, g->d_solo, g->sc.comp_off,
+                g->sc.comp_len, g->sc.comp_v, g->sc.adj, g->d_active, U.d_wmem};
+  const u64 largest = std::max<u64>(std::max<u64>(need.N + 1, need.E), need.M);
+  launch_union_concat(U.d_mem, U.off, U.k, t, largest, g->num_sms, s);
+  CUDA_TRY(cudaGetLastError());
+  if (sync) CUDA_TRY(cudaStreamSynchronize(s));
+  g->stats.n = g->n;
+  g->stats.nnz = g->nnz;
+  g->stats.n_active = g->n_active;
+  g->stats.small_components = g->sc.ncomp;
+  return LDD_OK;
+}
+
+int union_run(ldd_graph* u, const double* d_in, int* center, int* dist, bool want_cut,
+              int* launches_out, int* cut_launches_out) {
+  ldd_graph::Union& U = *u->uni;
+  cudaStream_t s = u->stream;
+  int launches = launch_union_spread(d_in, U.off, U.k, (u32)u->n, u->d_excl, u->d_shift, U.d_amax,
+                                     U.d_amax + U.k, u->num_sms, s);
+  int l = 0, rc;
+  if ((rc = decompose_on_device(u, u->d_shift, center, dist, &l)) != LDD_OK) return rc;
+  launches += l;
+  int cl = 0;
+  if (want_cut) {
+    record(u, 6);
+    CUDA_TRY(cudaMemsetAsync(U.d_cut, 0, (size_t)U.k * 8, s));
+    cl = launch_union_cut(u->d_up, U.d_offs + 7 * ((size_t)U.cap.k + 1), U.nchunk, U.off, U.k,
+                          center, U.d_cut, u->num_sms, s);
+    record(u, 7);
+  }
+  *launches_out = launches;
+  *cut_launches_out = cl;
+  return LDD_OK;
+}
+
+}  // namespace ldd
 
 extern "C" {
 
@@ -1033,6 +1113,106 @@ int ldd_decompose(ldd_graph* g, double beta, const double* shifts, int32_t* out_
   return LDD_OK;
 }
 
+int ldd_decompose_ranked(ldd_graph* g, const int32_t* levels, const int32_t* perm,
+                         int32_t* out_center, int32_t* out_dist) {
+  g_last_error[0] = 0;
+  if (!g) return fail(LDD_ERR_ARG, "graph is NULL");
+  if (g->uni) return fail(LDD_ERR_ARG, "a union graph is decomposed by ldd_union_decompose");
+  if (g->n == 0) return LDD_OK;
+  if (!levels || !perm || !out_center || !out_dist)
+    return fail(LDD_ERR_ARG, "NULL levels, perm or output");
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
+  cudaStream_t s = g->stream;
+  const size_t n = (size_t)g->n;
+  const bool dev_c = is_device_ptr(out_center), dev_d = is_device_ptr(out_dist);
+  int* center = dev_c ? out_center : g->d_center;
+  int* dist = dev_d ? out_dist : g->d_dist;
+  record(g, 0);
+  // host inputs go to scratch the ranked path leaves alone (v1, k1)
+  const int* d_levels = levels;
+  const int* d_perm = perm;
+  if (!is_device_ptr(levels)) {
+    CUDA_TRY(cudaMemcpyAsync(g->d_v[1], levels, n * 4, cudaMemcpyHostToDevice, s));
+    d_levels = reinterpret_cast<const int*>(g->d_v[1]);
+  }
+  if (!is_device_ptr(perm)) {
+    CUDA_TRY(cudaMemcpyAsync(g->d_k[1], perm, n * 4, cudaMemcpyHostToDevice, s));
+    d_perm = reinterpret_cast<const int*>(g->d_k[1]);
+  }
+  int launches = 0;
+  const int rc = decompose_on_device(g, nullptr, center, dist, &launches, d_levels, d_perm);
+  if (rc != LDD_OK) return rc;
+  if (!dev_c) CUDA_TRY(cudaMemcpyAsync(out_center, center, n * 4, cudaMemcpyDeviceToHost, s));
+  if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, n * 4, cudaMemcpyDeviceToHost, s));
+  record(g, 5);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  ldd_stats& st = g->stats;
+  st.launches = launches;
+  st.ms_h2d = elapsed(g, 0, 1);
+  st.ms_d2h = (dev_c && dev_d) ? 0.f : elapsed(g, 4, 5);
+  st.ms_total = elapsed(g, 0, 5);
+  return LDD_OK;
+}
+
+int ldd_decompose_retry(ldd_graph* g, double beta, int k, const double* const* shifts,
+                        int64_t max_cut, int32_t max_radius, int32_t* out_center,
+                        int32_t* out_dist, int64_t* out_cut, int32_t* out_radius,
+                        int32_t* out_accepted) {
+  g_last_error[0] = 0;
+  if (out_accepted) *out_accepted = -1;
+  if (!g || !out_accepted) return fail(LDD_ERR_ARG, "NULL graph or out_accepted");
+  if (g->uni) return fail(LDD_ERR_ARG, "a union graph is decomposed by ldd_union_decompose");
+  if (!(beta > 0.0) || isinf(beta)) return fail(LDD_ERR_ARG, "beta must be finite and > 0");
+  if (k < 1 || !shifts) return fail(LDD_ERR_ARG, "need k >= 1 shift vectors (k = %d)", k);
+  if (g->n == 0) {
+    *out_accepted = 0;
+    if (out_cut) *out_cut = 0;
+    if (out_radius) *out_radius = 0;
+    return LDD_OK;
+  }
+  if (!out_center || !out_dist) return fail(LDD_ERR_ARG, "NULL output");
+  for (int i = 0; i < k; ++i)
+    if (!shifts[i]) return fail(LDD_ERR_ARG, "shifts[%d] is NULL", i);
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
+  cudaStream_t s = g->stream;
+  const size_t n = (size_t)g->n;
+  const bool dev_c = is_device_ptr(out_center), dev_d = is_device_ptr(out_dist);
+  int* center = dev_c ? out_center : g->d_center;
+  int* dist = dev_d ? out_dist : g->d_dist;
+  u32* d_radius = &g->d_ctl->radius;
+  int64_t cut = 0;
+  u32 radius = 0;
+  int launches = 0;
+  for (int i = 0; i < k; ++i) {
+    const double* d_shift = shifts[i];
+    if (!is_device_ptr(shifts[i])) {
+      CUDA_TRY(cudaMemcpyAsync(g->d_shift, shifts[i], n * 8, cudaMemcpyHostToDevice, s));
+      d_shift = g->d_shift;
+    }
+    int l = 0, rc;
+    if ((rc = decompose_on_device(g, d_shift, center, dist, &l)) != LDD_OK) return rc;
+    launches += l;
+    if ((rc = cut_on_device(g, center, &cut)) != LDD_OK) return rc;
+    launches += g->stats.cut_launches;
+    launches += launch_max_dist(dist, (u32)n, d_radius, g->num_sms, s);
+    CUDA_TRY(cudaMemcpyAsync(&radius, d_radius, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (cut <= max_cut && (int64_t)radius <= (int64_t)max_radius) {
+      *out_accepted = i;
+      break;
+    }
+  }
+  if (!dev_c) CUDA_TRY(cudaMemcpyAsync(out_center, center, n * 4, cudaMemcpyDeviceToHost, s));
+  if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, n * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (out_cut) *out_cut = cut;
+  if (out_radius) *out_radius = (int32_t)radius;
+  g->stats.launches = launches;
+  return LDD_OK;
+}
+
 int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* const* shifts,
                         int32_t* const* out_center, int32_t* const* out_dist, int64_t* out_cut) {
   g_last_error[0] = 0;
@@ -1152,119 +1332,20 @@ int ldd_create_union(int k, ldd_graph* const* members, ldd_graph** out) {
   }
   DeviceGuard dg(dev);
   if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", dev);
-  // member offsets of every table (64-bit sums, range-checked)
-  std::vector<u64> o[8];
-  for (auto& v : o) v.assign((size_t)k + 1, 0);
-  bool all_active = true;
-  for (int i = 0; i < k; ++i) {
-    const ldd_graph* m = members[i];
-    o[0][i + 1] = o[0][i] + ((u64)m->n + 31) / 32 * 32;
-    o[1][i + 1] = o[1][i] + (u64)m->nnz;
-    o[2][i + 1] = o[2][i] + m->m_up;
-    o[3][i + 1] = o[3][i] + m->sc.ncomp;
-    o[4][i + 1] = o[4][i] + m->sc.total;
-    o[5][i + 1] = o[5][i] + m->n_active;
-    o[6][i + 1] = o[6][i] + (u64)m->n;
-    o[7][i + 1] = o[7][i] + (m->m_up + kUnionCutChunk - 1) / kUnionCutChunk;
-    if (m->n_active > 0 && !m->d_active) all_active = false;
-  }
-  const u64 N = o[0][k], E = o[1][k];
-  if (N >= (1u << 30)) return fail(LDD_ERR_RANGE, "union of %llu vertices (padded) must be < 2^30",
-                                   (unsigned long long)N);
-  if (E >= (1ull << 31)) return fail(LDD_ERR_RANGE, "union of %llu arcs must be < 2^31",
-                                     (unsigned long long)E);
-  ldd_graph* g = new (std::nothrow) ldd_graph();
-  if (!g) return fail(LDD_ERR_OOM, "host allocation failed");
-  auto bail = [&](int status) {
+  const UnionCaps c = union_needs(k, members);
+  if (c.N >= (1u << 30))
+    return fail(LDD_ERR_RANGE, "union of %llu vertices (padded) must be < 2^30",
+                (unsigned long long)c.N);
+  if (c.E >= (1ull << 31))
+    return fail(LDD_ERR_RANGE, "union of %llu arcs must be < 2^31", (unsigned long long)c.E);
+  ldd_graph* g = nullptr;
+  int rc = union_alloc(&g, dev, c);
+  if (rc != LDD_OK) return rc;
+  if ((rc = union_fill(g, k, members, nullptr, true)) != LDD_OK) {
     free_graph_memory(g);
     delete g;
-    return status;
-  };
-  g->uni = new (std::nothrow) ldd_graph::Union();
-  if (!g->uni) return bail(fail(LDD_ERR_OOM, "host allocation failed"));
-  ldd_graph::Union& U = *g->uni;
-  memset(&g->stats, 0, sizeof(g->stats));
-  g->device = dev;
-  if (cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(LDD_ERR_CUDA, "no usable CUDA device"));
+    return rc;
   }
-  g->n = (int32_t)N;
-  g->nnz = (int64_t)E;
-  g->m_up = (u32)o[2][k];
-  g->sc.ncomp = (u32)o[3][k];
-  g->sc.total = (u32)o[4][k];
-  g->n_active = (u32)o[5][k];
-  u64 nnz_active = 0;
-  for (int i = 0; i < k; ++i) nnz_active += members[i]->nnz_active;
-  g->nnz_active = nnz_active;
-  U.k = (u32)k;
-  U.total = (u32)o[6][k];
-  U.nchunk = (u32)o[7][k];
-  U.h_voff.assign(o[0].begin(), o[0].end());
-  U.h_ooff.assign(o[6].begin(), o[6].end());
-  const size_t words = std::max<size_t>(N / 32, 1);
-  const bool active = all_active && g->n_active > 0;
-  if (cudaMalloc(&g->d_row, (N + 1) * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_col, std::max<u64>(E, 1) * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_up, std::max<u64>(g->m_up, 1) * sizeof(int2)) != cudaSuccess ||
-      cudaMalloc(&g->d_excl, 2 * words * 4) != cudaSuccess ||
-      (g->sc.ncomp > 0 && (cudaMalloc(&g->sc.comp_off, g->sc.ncomp * 4) != cudaSuccess ||
-                           cudaMalloc(&g->sc.comp_len, g->sc.ncomp * 4) != cudaSuccess ||
-                           cudaMalloc(&g->sc.comp_v, g->sc.total * 4) != cudaSuccess ||
-                           cudaMalloc(&g->sc.adj, g->sc.total * 4) != cudaSuccess)) ||
-      (active && cudaMalloc(&g->d_active, (size_t)g->n_active * 4) != cudaSuccess) ||
-      cudaMalloc(&U.d_mem, (size_t)k * sizeof(UnionMember)) != cudaSuccess ||
-      cudaMalloc(&U.d_offs, 8 * ((size_t)k + 1) * 4) != cudaSuccess ||
-      cudaMalloc(&U.d_shift_in, std::max<size_t>(U.total, 1) * 8) != cudaSuccess ||
-      cudaMalloc(&U.d_out_c, std::max<size_t>(U.total, 1) * 8) != cudaSuccess ||
-      cudaMalloc(&U.d_cut, (size_t)k * 8) != cudaSuccess ||
-      cudaMalloc(&U.d_wmem, words * 4) != cudaSuccess ||
-      cudaMalloc(&U.d_amax, 2 * (size_t)k * 4) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(LDD_ERR_OOM, "device allocation of the union (%llu vertices, %llu arcs) "
-                     "failed", (unsigned long long)N, (unsigned long long)E));
-  }
-  g->d_solo = g->d_excl + words;
-  U.d_out_d = U.d_out_c + std::max<size_t>(U.total, 1);
-  std::vector<UnionMember> mv((size_t)k);
-  for (int i = 0; i < k; ++i) {
-    const ldd_graph* m = members[i];
-    UnionMember& d = mv[(size_t)i];
-    d.row = m->d_row;
-    d.col = m->d_col;
-    d.up = m->d_up;
-    d.hot = m->d_hot;
-    d.excl = m->d_excl;
-    d.solo = m->d_solo;
-    d.comp_off = m->sc.comp_off;
-    d.comp_len = m->sc.comp_len;
-    d.comp_v = m->sc.comp_v;
-    d.adj = m->sc.adj;
-    d.active = m->d_active;
-    d.n = (u32)m->n;
-    d.nnz = (u32)m->nnz;
-  }
-  std::vector<u32> offs(8 * ((size_t)k + 1));
-  for (int t = 0; t < 8; ++t)
-    for (int i = 0; i <= k; ++i) offs[(size_t)t * (k + 1) + i] = (u32)o[t][i];
-  const u32* d = U.d_offs;
-  const size_t K1 = (size_t)k + 1;
-  U.off = UnionOffsets{d, d + K1, d + 2 * K1, d + 3 * K1, d + 4 * K1, d + 5 * K1, d + 6 * K1};
-  if (cudaMemcpy(U.d_mem, mv.data(), mv.size() * sizeof(UnionMember), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(U.d_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-    return bail(fail(LDD_ERR_CUDA, "upload of the union tables failed"));
-  UnionTables t{g->d_row, g->d_col, g->d_up, g->d_excl, g->d_solo, g->sc.comp_off,
-                g->sc.comp_len, g->sc.comp_v, g->sc.adj, g->d_active, U.d_wmem};
-  const u64 largest = std::max<u64>(std::max<u64>(N + 1, E), g->m_up);
-  launch_union_concat(U.d_mem, U.off, U.k, t, largest, g->num_sms, nullptr);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(nullptr) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(LDD_ERR_CUDA, "building the union tables failed"));
-  }
-  int rc;
-  if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);
   *out = g;
   return LDD_OK;
 }
@@ -1321,19 +1402,11 @@ int ldd_union_decompose(ldd_graph* u, const double* betas, const double* shifts,
     in = U.d_shift_in;
   }
   if (rc == kRunRegular) {
-    launches = launch_union_spread(in, U.off, U.k, (u32)u->n, u->d_excl, u->d_shift, U.d_amax,
-                                   U.d_amax + U.k, u->num_sms, s);
-    int l = 0;
-    if ((rc = decompose_on_device(u, u->d_shift, center, dist, &l)) != LDD_OK) return rc;
-    launches += l;
-    if (out_cut) {
-      record(u, 6);
-      CUDA_TRY(cudaMemsetAsync(U.d_cut, 0, (size_t)U.k * 8, s));
-      cut_launches = launch_union_cut(u->d_up, U.d_offs + 7 * ((size_t)U.k + 1), U.nchunk, U.off,
-                                      U.k, center, U.d_cut, u->num_sms, s);
+    if ((rc = union_run(u, in, center, dist, out_cut != nullptr, &launches, &cut_launches)) !=
+        LDD_OK)
+      return rc;
+    if (out_cut)
       CUDA_TRY(cudaMemcpyAsync(out_cut, U.d_cut, (size_t)U.k * 8, cudaMemcpyDeviceToHost, s));
-      record(u, 7);
-    }
   }
   if (!dev_c) CUDA_TRY(cudaMemcpyAsync(out_center, center, total * 4, cudaMemcpyDeviceToHost, s));
   if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist, dist, total * 4, cudaMemcpyDeviceToHost, s));
@@ -1345,6 +1418,123 @@ int ldd_union_decompose(ldd_graph* u, const double* betas, const double* shifts,
   st.cut_launches = cut_launches;
   st.ms_cut = (out_cut && !st.replayed) ? elapsed(u, 6, 7) : (out_cut ? -1.f : 0.f);
   st.ms_total = elapsed(u, 0, 5);
+  return LDD_OK;
+}
+
+int ldd_get_tuning(const ldd_graph* g, ldd_tuning* out) {
+  if (!g || !out) return fail(LDD_ERR_ARG, "NULL argument");
+  out->bfs_blocks_per_sm = g->bfs_per_sm;
+  out->pull_alpha = (int32_t)g->pull_alpha;
+  out->pull_beta = (int32_t)g->pull_beta;
+  out->pull_gamma = (int32_t)g->pull_gamma;
+  out->probe_min_arcs = (int32_t)g->probe_min_arcs;
+  out->ms = -1.f;
+  return LDD_OK;
+}
+
+int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
+  if (!g || !t) return fail(LDD_ERR_ARG, "NULL argument");
+  int max_per_sm = 0;
+  if (bfs_grid_size(g->num_sms, &max_per_sm) <= 0)
+    return fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed");
+  if (t->bfs_blocks_per_sm < 1 || t->bfs_blocks_per_sm > max_per_sm || t->pull_alpha < 0 ||
+      t->pull_beta < 1 || t->pull_gamma < 0 || t->probe_min_arcs < 0)
+    return fail(LDD_ERR_ARG, "tuning out of range (blocks per SM 1 .. %d)", max_per_sm);
+  g->bfs_per_sm = t->bfs_blocks_per_sm;
+  g->bfs_grid = g->bfs_per_sm * g->num_sms;
+  g->pull_alpha = (u32)t->pull_alpha;
+  g->pull_beta = (u32)t->pull_beta;
+  g->pull_gamma = (u32)t->pull_gamma;
+  g->probe_min_arcs = (u32)t->probe_min_arcs;
+  g->stats.bfs_grid = g->bfs_grid;
+  drop_replay(g);  // captured kernels carry the old parameters
+  return LDD_OK;
+}
+
+int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) {
+  g_last_error[0] = 0;
+  if (!g || !shifts || !out) return fail(LDD_ERR_ARG, "NULL argument");
+  if (reps < 1) return fail(LDD_ERR_ARG, "reps must be >= 1");
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
+  if (g->n == 0) return ldd_get_tuning(g, out);
+  cudaStream_t s = g->stream;
+  const size_t n = g->uni ? (size_t)g->uni->total : (size_t)g->n;
+  // shifts to the device once; outputs to the library's buffers
+  double* d_in = g->uni ? g->uni->d_shift_in : g->d_shift;
+  CUDA_TRY(cudaMemcpyAsync(d_in, shifts, n * 8,
+                           is_device_ptr(shifts) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return fail(LDD_ERR_CUDA, "cudaEventCreate failed");
+  }
+  const bool saved_replay = g->replay;
+  g->replay = false;
+  // one decomposition with the current parameters, best of reps (ms), or < 0
+  auto measure = [&](float* best) -> int {
+    *best = 1e30f;
+    for (int r = 0; r <= reps; ++r) {  // the first run warms up
+      int l = 0, cl = 0, rc;
+      CUDA_TRY(cudaEventRecord(e0, s));
+      if (g->uni)
+        rc = union_run(g, d_in, g->uni->d_out_c, g->uni->d_out_d, false, &l, &cl);
+      else
+        rc = decompose_on_device(g, d_in, g->d_center, g->d_dist, &l);
+      if (rc != LDD_OK) return rc;
+      CUDA_TRY(cudaEventRecord(e1, s));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) *best = std::min(*best, ms);
+    }
+    return LDD_OK;
+  };
+  ldd_tuning cur;
+  ldd_get_tuning(g, &cur);
+  float best_ms;
+  int rc = measure(&best_ms);
+  int max_per_sm = 1;
+  bfs_grid_size(g->num_sms, &max_per_sm);
+  // coordinate descent, one parameter at a time over a few candidates
+  const int32_t alphas[] = {4, 8, 14, 24, 48};
+  const int32_t betas[] = {8, 16, 24, 48, 96};
+  const int32_t gammas[] = {2, 4, 8, 16, 64};
+  const int32_t probes[] = {1 << 12, 1 << 16, 1 << 20, 1 << 30};
+  for (int param = 0; param < 5 && rc == LDD_OK; ++param) {
+    const int32_t* vals = param == 0 ? alphas : param == 1 ? betas : param == 2 ? gammas : probes;
+    int nv = param == 3 ? 4 : 5;
+    int32_t per_sm_vals[2] = {1, max_per_sm};
+    if (param == 4) {
+      vals = per_sm_vals;
+      nv = max_per_sm > 1 ? 2 : 1;
+    }
+    for (int i = 0; i < nv && rc == LDD_OK; ++i) {
+      ldd_tuning t = cur;
+      int32_t* field = param == 0 ? &t.pull_alpha : param == 1 ? &t.pull_beta
+                     : param == 2 ? &t.pull_gamma : param == 3 ? &t.probe_min_arcs
+                                                  : &t.bfs_blocks_per_sm;
+      if (*field == vals[i]) continue;
+      *field = vals[i];
+      if ((rc = ldd_set_tuning(g, &t)) != LDD_OK) break;
+      float ms;
+      if ((rc = measure(&ms)) != LDD_OK) break;
+      if (ms < best_ms * 0.98f) {  // keep only a clear gain
+        best_ms = ms;
+        cur = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->replay = saved_replay;
+  const int rc2 = ldd_set_tuning(g, &cur);
+  if (rc != LDD_OK) return rc;
+  if (rc2 != LDD_OK) return rc2;
+  *out = cur;
+  out->ms = best_ms;
   return LDD_OK;
 }
 

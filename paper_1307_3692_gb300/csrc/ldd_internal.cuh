@@ -29,6 +29,7 @@ enum : u32 {
   kErrBucketCap = 1u << 3,   // start-bucket table smaller than A + 2 (host grows it, reruns)
   kErrInternal = 1u << 4,    // a capacity invariant failed
   kErrRankRetry = 1u << 5,   // a long run of equal 32-bit fraction codes: redo the rank exactly
+  kErrPermArg = 1u << 6,     // ranked variant: a negative level or perm not a permutation
 };
 
 // Radix sort: 8-bit digits, 256-thread CTAs, 16 keys per thread.
@@ -85,6 +86,7 @@ struct Control {
   // barrier let CTA 0 go (entry 0: the level-0 starts); and the round's kind
   long long round_clk[kRoundProfile][3];
   int round_kind[kRoundProfile];
+  u32 radius;  // max dist of the last labelling (ldd_decompose_retry)
 };
 constexpr size_t kCtlHeaderBytes = 40;       // err .. cut
 constexpr size_t kCtlBfsStateOffset = 40;    // bar_count .. pull_rounds
@@ -113,6 +115,10 @@ struct BfsArgs {
   u32 pull_alpha;    // go bottom-up when frontier arcs * alpha > unsettled arcs
   u32 pull_gamma;    //   and frontier arcs * gamma > n_active (a bottom-up round reads every key)
   u32 pull_beta;     // go back top-down when frontier vertices * beta < n_active
+  u32 probe_min_arcs;  // top-down rounds with at least this many arcs read a key before its atomicMin
+  const u32* wmem;   // unions: member of every 32-vertex word; else null
+  u32* mrank;        // unions: [3][kmem] smallest rank per level slot and member (~0 on entry)
+  u32 kmem;          // unions: members
 };
 
 // Components of 2..kSmallComp vertices (k_graph.cu): comp c has comp_len[c]
@@ -172,6 +178,11 @@ struct RankBufs {
 // LSD radix sort of all vertices.  The start buckets end in v0 (vertices) and
 // k0 viewed as 32-bit words (their rounds).
 int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s);
+// Ranked variant (Section 4's permutation in place of the fractional parts):
+// integer levels and a tie-break permutation given; no sort.  The same start
+// buckets and keys as the exact path.
+int launch_ranked_and_buckets(const RankBufs& r, const int* levels, const int* perm,
+                              cudaStream_t s);
 u32 fraction_bucket_bits(u32 n);
 // Look-back status words the fast path's two scans use (status[0 ..)); a
 // captured replay clears them and runs with the fixed epochs 1 and 2.
@@ -194,6 +205,8 @@ constexpr u32 kHotSlots = 49152;  // 192 KiB of labels per CTA
 int launch_cut(const int2* list, u32 m, const int* center, const u32* hot, u32 n_hot,
                int* hot_center, u64* out, int num_sms, cudaStream_t s);
 int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s);
+// The radius of a decomposition: max over v of dist[v], into *out.
+int launch_max_dist(const int* dist, u32 n, u32* out, int num_sms, cudaStream_t s);
 // Labels components and fills t.comp_* and excl (bit v: kept out of the BFS);
 // counts = {small components, their members, vertices left to the BFS, their arcs}.
 // excl and solo: bitmasks of (n + 31) / 32 words each.

@@ -61,6 +61,35 @@ def test_argument_errors_need_no_device(ldd):
     assert lib.ldd_create_union(1, nulls, None) == ldd.LDD_ERR_ARG
     assert lib.ldd_union_size(None, None, None) == ldd.LDD_ERR_ARG
     assert lib.ldd_union_decompose(None, None, None, None, None, None) == ldd.LDD_ERR_ARG
+    lib.ldd_server_create.argtypes = [ctypes.c_void_p] * 2
+    lib.ldd_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double] + [ctypes.c_void_p] * 5
+    lib.ldd_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    lib.ldd_server_destroy.argtypes = [ctypes.c_void_p]
+    srv = ctypes.c_void_p()
+    assert lib.ldd_server_create(None, ctypes.byref(srv)) == ldd.LDD_ERR_ARG
+    bad = ldd.ServerConfig(1 << 30, 0, 1, 0, 0, 0, 0)  # max_batch 0
+    assert lib.ldd_server_create(ctypes.byref(bad), ctypes.byref(srv)) == ldd.LDD_ERR_ARG
+    bad = ldd.ServerConfig(0, 4, 1, 0, 0, 0, 0)  # no budget
+    assert lib.ldd_server_create(ctypes.byref(bad), ctypes.byref(srv)) == ldd.LDD_ERR_ARG
+    t = ctypes.c_int64()
+    assert lib.ldd_server_submit(None, None, 0.1, None, None, None, None, ctypes.byref(t)) == ldd.LDD_ERR_ARG
+    assert lib.ldd_server_wait(None, 0, None) == ldd.LDD_ERR_ARG
+    assert lib.ldd_server_destroy(None) == ldd.LDD_OK
+    lib.ldd_decompose_retry.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32] + [ctypes.c_void_p] * 5
+    acc = ctypes.c_int32(5)
+    assert lib.ldd_decompose_retry(None, 0.1, 1, None, 0, 0, None, None, None, None,
+                                   ctypes.byref(acc)) == ldd.LDD_ERR_ARG
+    assert acc.value == -1
+    lib.ldd_decompose_ranked.argtypes = [ctypes.c_void_p] * 5
+    assert lib.ldd_decompose_ranked(None, None, None, None, None) == ldd.LDD_ERR_ARG
+    lib.ldd_get_tuning.argtypes = [ctypes.c_void_p] * 2
+    lib.ldd_set_tuning.argtypes = [ctypes.c_void_p] * 2
+    lib.ldd_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    tun = ldd.Tuning()
+    assert lib.ldd_get_tuning(None, ctypes.byref(tun)) == ldd.LDD_ERR_ARG
+    assert lib.ldd_set_tuning(None, ctypes.byref(tun)) == ldd.LDD_ERR_ARG
+    assert lib.ldd_autotune(None, None, 1, ctypes.byref(tun)) == ldd.LDD_ERR_ARG
     lib.ldd_set_graph_replay.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert lib.ldd_set_graph_replay(None, 1) == ldd.LDD_ERR_ARG
     out = ctypes.c_void_p()
