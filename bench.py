@@ -665,7 +665,12 @@ def serve_arm(args):
         lat = np.array([(x["end_us"] - x["submit_us"]) / 1e3 for x in infos])
         span = (max(x["end_us"] for x in infos) - min(x["submit_us"] for x in infos)) / 1e6
         bs = np.array([x["batch_size"] for x in infos])
+        batches = {x["batch_id"]: x for x in infos}
+        fill = np.array([x["batch_fill_us"] for x in batches.values()]) / 1e3
+        run = np.array([x["batch_run_us"] for x in batches.values()]) / 1e3
         return {"requests": len(infos), "throughput_rps": len(infos) / span,
+                "mean_batch_fill_ms": float(fill.mean()), "mean_batch_run_ms": float(run.mean()),
+                "device_busy_fraction": float(run.sum() / 1e3 / span),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
                 "batches": int(len(set(x["batch_id"] for x in infos))),

@@ -250,6 +250,8 @@ typedef struct {
   double submit_us;   /* server clock: microseconds since ldd_server_create */
   double start_us;    /* taken by a worker */
   double end_us;      /* results in the caller's buffers */
+  double batch_fill_us; /* its batch: union built and shifts copied in (host clock) */
+  double batch_run_us;  /* its batch: decomposition and cut counts on the device */
 } ldd_request_info;
 
 /* ldd_server_create -- a server on the current device.  LDD_ERR_RANGE if the

@@ -81,7 +81,8 @@ class ServerConfig(ctypes.Structure):
 class RequestInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
                 ("batch_id", ctypes.c_int64), ("submit_us", ctypes.c_double),
-                ("start_us", ctypes.c_double), ("end_us", ctypes.c_double)]
+                ("start_us", ctypes.c_double), ("end_us", ctypes.c_double),
+                ("batch_fill_us", ctypes.c_double), ("batch_run_us", ctypes.c_double)]
 
 
 _lib.ldd_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]

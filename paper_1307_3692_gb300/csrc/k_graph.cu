@@ -6,10 +6,8 @@
 // center's key (a center is its own center, so its key is its start key).
 //
 // cut (Definition 1.1, second condition; Section 4 notes the check costs
-// O(m) work): arcs (v, w) with v < w whose endpoints have different centers.
-// The graph keeps those arcs as a list of (v, w) pairs (8 bytes each, the same
-// bytes as its col array), so the count is one streaming pass with two
-// gathers per edge and no search for the row an arc belongs to.
+// O(m) work): edges {v, w} whose endpoints have different centers, each
+// counted once, over the graph's grouped cut list (4 bytes per edge).
 //
 // Components.  The assignment of Algorithm 2 never crosses a connected
 // component (other components are at infinite distance), so every component
@@ -61,75 +59,157 @@ __global__ void k_hot_centers(const u32* __restrict__ hot, u32 n_hot,
   if (i < n_hot) hot_center[i] = center[hot[i]];
 }
 
-// Edges per thread per step: two 16-byte loads of two (cold, hot) entries
-// each.  The next step's loads are issued before this step's label reads, so
-// the stream and the gathers overlap.  Cold endpoints come in sorted order
-// (their label reads coalesce); hot endpoints in the hot table read shared
-// memory instead of a random global gather.
-constexpr int kCutPairs = 2;
+// Cut count over the grouped cut list (CutList in ldd_internal.cuh), in two
+// streaming passes.  k_group_labels reads every group's cold label once.
+// k_cut then streams the edges: each warp step covers 128 edges, one 16-byte
+// load of 4 hot endpoints per lane; an edge finds its group from its block's
+// first group and group-start mask (one popc), so its cold label is one
+// gather from the per-group labels (consecutive edges share it).  Hot
+// endpoints in the hot table read shared memory; others are one gather each.
+// The next step's edge and block loads are issued before this step's label
+// reads, and there is no block-wide synchronisation.
+//
+// U = true: a union of graphs (k_union.cu): hot[] and grp_v[] are already in
+// the caller layout, and every member's count goes to its own counter, one
+// atomic per warp step when the step's edges share a member.
 constexpr int kCutThreads = 1024;
 
-__device__ __forceinline__ int hot_label(int y, const int* __restrict__ center, const int* s_hot) {
-  return y < 0 ? s_hot[y & 0x7fffffff] : center[y];
+template <bool U>
+__global__ void __launch_bounds__(256) k_group_labels(CutList cl, const int* __restrict__ center) {
+  for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < cl.ngrp; g += gridDim.x * blockDim.x) {
+    const int lab = center[__ldg(cl.grp_v + g)];
+    if (U)  // member and label in one word: one gather per edge in k_cut
+      reinterpret_cast<u64*>(cl.grp_lab)[g] = ((u64)__ldg(cl.grp_m + g) << 32) | (u32)lab;
+    else
+      cl.grp_lab[g] = lab;
+  }
 }
 
-__global__ void __launch_bounds__(kCutThreads, 1) k_cut(const int2* __restrict__ list, u32 m,
-                                                        const int* __restrict__ center,
+__device__ __forceinline__ u32 bits_upto(u32 j) { return j >= 31u ? 0xffffffffu : (2u << j) - 1u; }
+
+template <bool U>
+__global__ void __launch_bounds__(kCutThreads, 1) k_cut(CutList cl, const int* __restrict__ center,
                                                         const int* __restrict__ hot_center,
                                                         u32 n_hot, u64* out) {
   extern __shared__ int4 cut_smem[];
   int* s_hot = reinterpret_cast<int*>(cut_smem);
   __shared__ unsigned long long wsum[kCutThreads / 32];
-  const u32 tid = threadIdx.x;
-  const int4* hc4 = reinterpret_cast<const int4*>(hot_center);  // cudaMalloc'd: aligned
-  for (u32 i = tid; i < n_hot / 4; i += blockDim.x) cut_smem[i] = __ldg(hc4 + i);
-  for (u32 i = (n_hot & ~3u) + tid; i < n_hot; i += blockDim.x) s_hot[i] = hot_center[i];
-  __syncthreads();
-  const int4* l4 = reinterpret_cast<const int4*>(list);  // cudaMalloc'd: 256-byte aligned
-  const u32 nquad = m / 2;
-  const u32 stride = gridDim.x * blockDim.x;
-  const u32 step = stride * kCutPairs;
+  const u32 tid = threadIdx.x, lane = tid & 31;
+  if (!U) {
+    const int4* hc4 = reinterpret_cast<const int4*>(hot_center);  // cudaMalloc'd: aligned
+    for (u32 i = tid; i < n_hot / 4; i += blockDim.x) cut_smem[i] = __ldg(hc4 + i);
+    for (u32 i = (n_hot & ~3u) + tid; i < n_hot; i += blockDim.x) s_hot[i] = hot_center[i];
+    __syncthreads();
+  }
+  const int4* hot4 = reinterpret_cast<const int4*>(cl.hot);  // cudaMalloc'd: aligned
+  const u32 nchunk = (cl.m + 127) / 128;                       // 128 edges per warp step
+  const u32 stride = gridDim.x * (kCutThreads / 32);
   unsigned long long cnt = 0;
-  u32 i = blockIdx.x * blockDim.x + tid;
-  int4 q[kCutPairs];
-#pragma unroll
-  for (int k = 0; k < kCutPairs; ++k) {
-    const u32 j = i + (u32)k * stride;
-    q[k] = (j < nquad) ? __ldcs(l4 + j) : make_int4(0, 0, 0, 0);
-  }
-  for (; i < nquad; i += step) {
-    int4 nq[kCutPairs];
-#pragma unroll
-    for (int k = 0; k < kCutPairs; ++k) {
-      const u32 j = i + step + (u32)k * stride;  // < 2^32: nquad < 2^29, step < 2^22
-      nq[k] = (j < nquad) ? __ldcs(l4 + j) : make_int4(0, 0, 0, 0);
+  u32 c = blockIdx.x * (kCutThreads / 32) + (tid >> 5);
+  // lane's four edges: 4 lane .. 4 lane + 3 of the chunk, in block lane / 8
+  auto load = [&](u32 cc, int4& h, u32& bg, u32& bm) {
+    const u32 e0 = cc * 128 + 4 * lane;
+    if (e0 + 3 < cl.m) {
+      h = __ldcs(hot4 + (e0 >> 2));
+    } else {
+      h.x = e0 < cl.m ? cl.hot[e0] : 0;
+      h.y = e0 + 1 < cl.m ? cl.hot[e0 + 1] : 0;
+      h.z = e0 + 2 < cl.m ? cl.hot[e0 + 2] : 0;
+      h.w = 0;
     }
-    int c[kCutPairs][4];
+    const u32 b = e0 >> 5;
+    bg = b < cl.nblk ? __ldg(cl.blk_g + b) : 0u;
+    bm = b < cl.nblk ? __ldg(cl.blk_mask + b) : 0u;
+  };
+  int4 h;
+  u32 bg = 0, bm = 0;
+  if (c < nchunk) load(c, h, bg, bm);
+  for (; c < nchunk; c += stride) {
+    int4 nh = make_int4(0, 0, 0, 0);
+    u32 nbg = 0, nbm = 0;
+    if (c + stride < nchunk) load(c + stride, nh, nbg, nbm);
+    const u32 e0 = c * 128 + 4 * lane, j0 = (4 * lane) & 31u;
+    const int hv[4] = {h.x, h.y, h.z, h.w};
+    u32 g[4];
 #pragma unroll
-    for (int k = 0; k < kCutPairs; ++k) {
-      c[k][0] = center[q[k].x];
-      c[k][1] = hot_label(q[k].y, center, s_hot);
-      c[k][2] = center[q[k].z];
-      c[k][3] = hot_label(q[k].w, center, s_hot);
+    for (int q = 0; q < 4; ++q) g[q] = bg + __popc(bm & bits_upto(j0 + (u32)q));
+    int cl_lab[4], hl[4];
+    u32 gm[4];  // unions: the member of each edge
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool valid = e0 + (u32)q < cl.m;
+      if (U) {
+        const u64 lm = valid ? __ldg(reinterpret_cast<const u64*>(cl.grp_lab) + g[q]) : 0ull;
+        cl_lab[q] = (int)(u32)lm;
+        gm[q] = (u32)(lm >> 32);
+        hl[q] = valid ? center[hv[q]] : 0;
+      } else {
+        cl_lab[q] = valid ? __ldg(cl.grp_lab + g[q]) : 0;
+        hl[q] = valid ? (hv[q] < 0 ? s_hot[hv[q] & 0x7fffffff] : center[hv[q]]) : 0;
+      }
     }
+    if (U) {
+      // per-member counts: the lane's edges, then the warp when all share a member
+      const bool valid0 = e0 < cl.m;
+      const u32 ms0 = valid0 ? gm[0] : 0xffffffffu;
+      // members are sorted: the lane's edges share one if its first and last do
+      const u32 qlast = valid0 ? min(3u, cl.m - 1 - e0) : 0u;
+      u32 ms3 = ms0;
 #pragma unroll
-    for (int k = 0; k < kCutPairs; ++k) {
-      cnt += (c[k][0] != c[k][1]) + (c[k][2] != c[k][3]);
-      q[k] = nq[k];
+      for (int q = 1; q < 4; ++q)
+        if ((u32)q == qlast) ms3 = gm[q];
+      u32 mine = 0;
+      bool split = ms3 != ms0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (e0 + (u32)q < cl.m && cl_lab[q] != hl[q]) {
+          if (!split) {
+            ++mine;
+          } else {
+            atomicAdd(reinterpret_cast<unsigned long long*>(out + gm[q]), 1ull);
+          }
+        }
+      const u32 act = __ballot_sync(0xffffffffu, valid0);
+      if (act) {
+        const u32 m0 = __shfl_sync(0xffffffffu, ms0, __ffs(act) - 1);
+        const bool one = __all_sync(0xffffffffu, !valid0 || (!split && ms0 == m0));
+        if (one) {
+          u32 tot = mine;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+          if (lane == 0 && tot) atomicAdd(reinterpret_cast<unsigned long long*>(out + m0),
+                                          (unsigned long long)tot);
+        } else if (!split && mine) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(out + ms0), (unsigned long long)mine);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cnt += e0 + (u32)q < cl.m && cl_lab[q] != hl[q];
+    }
+    h = nh;
+    bg = nbg;
+    bm = nbm;
+  }
+  if (!U) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
+    if (lane == 0) wsum[tid >> 5] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long tot = 0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += wsum[w];
+      if (tot) atomicAdd(reinterpret_cast<unsigned long long*>(out), tot);
     }
   }
-  if ((m & 1u) && blockIdx.x == 0 && tid == 0) {  // odd edge count: the last edge
-    const int2 e = list[m - 1];
-    cnt += center[e.x] != hot_label(e.y, center, s_hot);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
-  if ((tid & 31) == 0) wsum[tid >> 5] = cnt;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long tot = 0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += wsum[w];
-    if (tot) atomicAdd(out, tot);
+}
+
+// blk_g and blk_mask of a union's concatenated groups (blk_mask zero on entry).
+__global__ void k_cut_blocks(CutList cl) {
+  for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < cl.ngrp; g += gridDim.x * blockDim.x) {
+    const u32 lo = cl.grp_off[g], hi = cl.grp_off[g + 1];
+    if (lo & 31u) atomicOr(cl.blk_mask + (lo >> 5), 1u << (lo & 31u));
+    for (u32 b = (lo + 31) / 32; b * 32 < hi; ++b) cl.blk_g[b] = g;
   }
 }
 
@@ -299,26 +379,43 @@ int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, in
   return 1;
 }
 
-int launch_cut(const int2* list, u32 m, const int* center, const u32* hot, u32 n_hot,
-               int* hot_center, u64* out, int num_sms, cudaStream_t s) {
-  if (m == 0) return 0;
+int launch_cut(const CutList& cl, const int* center, const u32* hot, u32 n_hot, int* hot_center,
+               u64* out, int num_sms, cudaStream_t s) {
+  if (cl.m == 0) return 0;
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaFuncSetAttribute(k_cut, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_cut<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(kHotSlots * sizeof(int)));
     attr_set[dev] = true;
   }
-  int launches = 0;
+  int launches = 1;
   if (n_hot > 0) {
     k_hot_centers<<<(n_hot + 255) / 256, 256, 0, s>>>(hot, n_hot, center, hot_center);
     ++launches;
   }
-  const u32 g = (u32)max(1ll, min((long long)(m / 2 + kCutThreads - 1) / kCutThreads,
-                                  (long long)num_sms));
-  k_cut<<<g, kCutThreads, (size_t)n_hot * sizeof(int), s>>>(list, m, center, hot_center, n_hot,
-                                                            out);
+  k_group_labels<false><<<grid_for(cl.ngrp, num_sms), 256, 0, s>>>(cl, center);
+  const u32 g = (u32)max(1ll, min((long long)(cl.m + 4095) / 4096, (long long)num_sms));
+  k_cut<false><<<g, kCutThreads, (size_t)n_hot * sizeof(int), s>>>(cl, center, hot_center, n_hot,
+                                                                   out);
   return launches + 1;
+}
+
+int launch_union_cut(const CutList& cl, const UnionOffsets& off, const u32* wmem,
+                     const int* center, u64* cut, int num_sms, cudaStream_t s) {
+  (void)off;
+  (void)wmem;
+  if (cl.m == 0) return 0;
+  k_group_labels<true><<<grid_for(cl.ngrp, num_sms), 256, 0, s>>>(cl, center);
+  const u32 g = (u32)max(1ll, min((long long)(cl.m + 4095) / 4096, (long long)num_sms));
+  k_cut<true><<<g, kCutThreads, 0, s>>>(cl, center, nullptr, 0, cut);
+  return 2;
+}
+
+int launch_cut_blocks(const CutList& cl, int num_sms, cudaStream_t s) {
+  cudaMemsetAsync(cl.blk_mask, 0, (size_t)cl.nblk * 4, s);
+  k_cut_blocks<<<grid_for(cl.ngrp ? cl.ngrp : 1, num_sms), 256, 0, s>>>(cl);
+  return 1;
 }
 
 int launch_max_dist(const int* dist, u32 n, u32* out, int num_sms, cudaStream_t s) {

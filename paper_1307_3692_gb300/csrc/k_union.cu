@@ -14,14 +14,15 @@
 // Layout of the union.  Member s occupies union vertices
 // [voff_s, voff_s + n_s) followed by pad_s = roundup(n_s, 32) - n_s isolated
 // pad vertices, so that every member starts on a 32-vertex boundary and its
-// per-vertex bitmask words are copied whole.  Arcs, cut-list entries and
-// small-component records are concatenated in member order with their vertex
-// ids moved by voff_s.  Outputs use the caller's layout: member s's n_s
+// per-vertex bitmask words are copied whole.  Arcs, cut-list edges and groups
+// and small-component records are concatenated in member order with their
+// vertex ids moved by voff_s.  The union's cut list has no hot table and
+// holds caller-layout indices (the cut count reads the outputs).  Outputs use the caller's layout: member s's n_s
 // entries at ooff_s = n_0 + ... + n_{s-1}, with member-local ids.
 //
 // Every table is built by one launch (k_union_concat, blockIdx.y = table);
-// an element finds its member by a binary search over the table's member
-// offsets.
+// a block finds the member of its chunk's first element by a binary search
+// over the table's member offsets, and its threads walk forward from there.
 //
 // Level alignment.  With one floor(delta_max) for the whole union, a member
 // whose own largest shift is small would start late, and until then its
@@ -47,48 +48,73 @@ __device__ __forceinline__ u32 member_of(const u32* __restrict__ off, u32 k, u32
   return lo;
 }
 
+// Calls f(x, s) for every x in [0, X) with s = member_of(off, k, x * scale).  A block
+// takes kConcatChunk consecutive elements at a time and finds the member of
+// the first one once; each thread then walks forward from it (members are
+// contiguous and ordered, and a thread's x only grows).
+constexpr u32 kConcatChunk = 2048;
+
+template <typename F>
+__device__ __forceinline__ void for_each_member_elem(const u32* __restrict__ off, u32 k, u32 X,
+                                                     F f, u32 scale = 1) {
+  __shared__ u32 s_first;
+  for (u32 base = blockIdx.x * kConcatChunk; base < X; base += gridDim.x * kConcatChunk) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_first = member_of(off, k, base * scale);
+    __syncthreads();
+    u32 s = s_first;
+    const u32 end = min(base + kConcatChunk, X);
+    for (u32 x = base + threadIdx.x; x < end; x += blockDim.x) {
+      while (__ldg(off + s + 1) <= x * scale) ++s;
+      f(x, s);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_union_concat(const UnionMember* __restrict__ mem,
                                                       UnionOffsets off, u32 k, UnionTables t) {
-  const u32 stride = gridDim.x * blockDim.x;
-  const u32 first = blockIdx.x * blockDim.x + threadIdx.x;
   switch (blockIdx.y) {
     case 0: {  // row_ptr: member rows moved by eoff; pads are empty rows
       const u32 N = off.v[k];
-      for (u32 u = first; u <= N; u += stride) {
-        if (u == N) {
-          t.row[N] = (int)off.e[k];
-          continue;
-        }
-        const u32 s = member_of(off.v, k, u);
+      if (blockIdx.x == 0 && threadIdx.x == 0) t.row[N] = (int)off.e[k];
+      for_each_member_elem(off.v, k, N, [&](u32 u, u32 s) {
         const UnionMember& m = mem[s];
         const u32 v = u - off.v[s];
         t.row[u] = (int)(off.e[s] + (v < m.n ? (u32)__ldg(m.row + v) : m.nnz));
-      }
+      });
       break;
     }
-    case 1: {  // col: neighbour ids moved by voff
-      const u32 E = off.e[k];
-      for (u32 e = first; e < E; e += stride) {
-        const u32 s = member_of(off.e, k, e);
+    case 1:  // col: neighbour ids moved by voff
+      for_each_member_elem(off.e, k, off.e[k], [&](u32 e, u32 s) {
         t.col[e] = __ldg(mem[s].col + (e - off.e[s])) + (int)off.v[s];
-      }
+      });
       break;
-    }
-    case 2: {  // cut list: hot-table slots resolved to vertex ids, ids moved
-      const u32 M = off.u[k];
-      for (u32 i = first; i < M; i += stride) {
-        const u32 s = member_of(off.u, k, i);
+    case 2:  // cut list edges: hot-table slots resolved, ids moved to the caller layout
+      for_each_member_elem(off.u, k, off.u[k], [&](u32 i, u32 s) {
         const UnionMember& m = mem[s];
-        const int2 p = m.up[i - off.u[s]];
-        const int hot = p.y < 0 ? (int)__ldg(m.hot + (p.y & 0x7fffffff)) : p.y;
-        t.up[i] = make_int2(p.x + (int)off.v[s], hot + (int)off.v[s]);
-      }
+        const int h = __ldg(m.cut_hot + (i - off.u[s]));
+        const int hot = h < 0 ? (int)__ldg(m.hot + (h & 0x7fffffff)) : h;
+        t.cut.hot[i] = hot + (int)off.o[s];  // caller layout: the cut reads outputs
+      });
+      break;
+    case 8: {  // cut list groups: cold vertices (caller layout), members, edge offsets
+      const u32 G = off.g[k];
+      if (blockIdx.x == 0 && threadIdx.x == 0) t.cut.grp_off[G] = off.u[k];
+      for_each_member_elem(off.g, k, G, [&](u32 i, u32 s) {
+        const UnionMember& m = mem[s];
+        t.cut.grp_v[i] = __ldg(m.grp_v + (i - off.g[s])) + off.o[s];
+        t.cut.grp_m[i] = s;
+        t.cut.grp_off[i] = __ldg(m.grp_off + (i - off.g[s])) + off.u[s];
+      });
       break;
     }
-    case 3: {  // exclusion and singleton bitmasks: whole words, pad bits set
-      const u32 W = off.v[k] / 32;
-      for (u32 w = first; w < W; w += stride) {
-        const u32 s = member_of(off.v, k, w * 32);
+    case 3:  // exclusion and singleton bitmasks: whole words, pad bits set
+    case 7:  // and the member of every 32-vertex word (the rank's floor lift)
+      for_each_member_elem(off.v, k, off.v[k] / 32, [&](u32 w, u32 s) {
+        if (blockIdx.y == 7) {
+          t.wmem[w] = s;
+          return;
+        }
         const UnionMember& m = mem[s];
         const u32 lw = w - off.v[s] / 32;
         const u32 lo = lw * 32;  // first local vertex of the word
@@ -97,43 +123,28 @@ __global__ void __launch_bounds__(256) k_union_concat(const UnionMember* __restr
         const u32 so = lo < m.n ? __ldg(m.solo + lw) : 0u;
         t.excl[w] = ex | pad;
         t.solo[w] = so | pad;
-      }
+      }, 32u);
       break;
-    }
-    case 4: {  // small components: member ranges and sizes
-      const u32 C = off.c[k];
-      for (u32 c = first; c < C; c += stride) {
-        const u32 s = member_of(off.c, k, c);
+    case 4:  // small components: member ranges and sizes
+      for_each_member_elem(off.c, k, off.c[k], [&](u32 c, u32 s) {
         const UnionMember& m = mem[s];
         t.comp_off[c] = __ldg(m.comp_off + (c - off.c[s])) + off.m[s];
         t.comp_len[c] = __ldg(m.comp_len + (c - off.c[s]));
-      }
+      });
       break;
-    }
-    case 5: {  // small components: member lists and lane adjacency masks
-      const u32 T = off.m[k];
-      for (u32 i = first; i < T; i += stride) {
-        const u32 s = member_of(off.m, k, i);
+    case 5:  // small components: member lists and lane adjacency masks
+      for_each_member_elem(off.m, k, off.m[k], [&](u32 i, u32 s) {
         const UnionMember& m = mem[s];
         t.comp_v[i] = __ldg(m.comp_v + (i - off.m[s])) + off.v[s];
         t.adj[i] = __ldg(m.adj + (i - off.m[s]));
-      }
+      });
       break;
-    }
-    case 7: {  // member of every 32-vertex word (the rank's floor lift)
-      const u32 W = off.v[k] / 32;
-      for (u32 w = first; w < W; w += stride) t.wmem[w] = member_of(off.v, k, w * 32);
-      break;
-    }
-    case 6: {  // vertices the BFS handles, ascending (when every member lists them)
+    case 6:  // vertices the BFS handles, ascending (when every member lists them)
       if (!t.active) break;
-      const u32 A = off.a[k];
-      for (u32 i = first; i < A; i += stride) {
-        const u32 s = member_of(off.a, k, i);
+      for_each_member_elem(off.a, k, off.a[k], [&](u32 i, u32 s) {
         t.active[i] = __ldg(mem[s].active + (i - off.a[s])) + off.v[s];
-      }
+      });
       break;
-    }
     default: break;
   }
 }
@@ -226,41 +237,6 @@ __global__ void __launch_bounds__(256) k_union_finalize(const u64* __restrict__ 
   }
 }
 
-// Cut count per member (Definition 1.1): the union cut list is cut into
-// chunks of at most kUnionCutChunk edges that never straddle two members;
-// chunk b belongs to member member_of(chunk_off, k, b).  Labels are read in
-// the caller's layout (member-local ids), where union vertex u of member s
-// sits at ooff_s + u - voff_s.
-__global__ void __launch_bounds__(256) k_union_cut(const int2* __restrict__ up,
-                                                   const u32* __restrict__ chunk_off,
-                                                   UnionOffsets off, u32 k,
-                                                   const int* __restrict__ center,
-                                                   unsigned long long* __restrict__ cut) {
-  __shared__ unsigned long long wsum[8];
-  const u32 nchunk = chunk_off[k];
-  for (u32 b = blockIdx.x; b < nchunk; b += gridDim.x) {
-    const u32 s = member_of(chunk_off, k, b);
-    const u32 lo = off.u[s] + (b - chunk_off[s]) * kUnionCutChunk;
-    const u32 hi = min(lo + kUnionCutChunk, off.u[s + 1]);
-    const long long delta = (long long)off.o[s] - (long long)off.v[s];
-    unsigned long long cnt = 0;
-    for (u32 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const int2 e = __ldcs(up + i);
-      cnt += center[e.x + delta] != center[e.y + delta];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long tot = 0;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += wsum[w];
-      if (tot) atomicAdd(cut + s, tot);
-    }
-    __syncthreads();
-  }
-}
-
 u32 blocks_for(u64 n, int num_sms) {
   return (u32)max(1ll, min((long long)((n + 255) / 256), (long long)num_sms * 8));
 }
@@ -269,8 +245,11 @@ u32 blocks_for(u64 n, int num_sms) {
 
 int launch_union_concat(const UnionMember* mem, const UnionOffsets& off, u32 k,
                         const UnionTables& t, u64 largest, int num_sms, cudaStream_t s) {
-  k_union_concat<<<dim3(blocks_for(largest + 1, num_sms), 8), 256, 0, s>>>(mem, off, k, t);
-  return 1;
+  const u32 bx = (u32)max(1ll, min((long long)((largest + kConcatChunk - 1) / kConcatChunk),
+                                   (long long)num_sms * 8));
+  k_union_concat<<<dim3(bx, 9), 256, 0, s>>>(mem, off, k, t);
+  launch_cut_blocks(t.cut, num_sms, s);  // after the groups are in place
+  return 2;
 }
 
 int launch_union_spread(const double* in, const UnionOffsets& off, u32 k, u32 N,
@@ -287,15 +266,6 @@ int launch_union_finalize(const u64* key, const u32* order, const u32* solo,
                           const u32* err, int num_sms, cudaStream_t s) {
   k_union_finalize<<<blocks_for(total, num_sms), 256, 0, s>>>(key, order, solo, off, k, center,
                                                               dist, err);
-  return 1;
-}
-
-int launch_union_cut(const int2* up, const u32* chunk_off, u32 nchunk, const UnionOffsets& off,
-                     u32 k, const int* center, u64* cut, int num_sms, cudaStream_t s) {
-  if (nchunk == 0) return 0;
-  const u32 g = (u32)min((long long)nchunk, (long long)num_sms * 8);
-  k_union_cut<<<g, 256, 0, s>>>(up, chunk_off, off, k, center,
-                                reinterpret_cast<unsigned long long*>(cut));
   return 1;
 }
 

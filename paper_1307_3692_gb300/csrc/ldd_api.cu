@@ -74,7 +74,13 @@ namespace ldd {
 int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_row);
   cudaFree(g->d_col);
-  cudaFree(g->d_up);
+  cudaFree(g->cut.hot);
+  cudaFree(g->cut.grp_off);
+  cudaFree(g->cut.grp_v);
+  cudaFree(g->cut.blk_g);
+  cudaFree(g->cut.blk_mask);
+  cudaFree(g->cut.grp_m);
+  cudaFree(g->cut.grp_lab);
   cudaFree(g->d_hot);
   if (!g->uni) cudaFree(g->d_active);  // a union's list lives in d_active_buf
   cudaFree(g->d_hot_center);
@@ -189,7 +195,7 @@ int alloc_scratch(ldd_graph* g) {
 
 // Component labels and the small-component tables (two device phases, the
 // table sizes read back in between).
-int build_component_tables(ldd_graph* g) {
+int build_component_tables(ldd_graph* g, const int2* d_arcs) {
   const size_t n = (size_t)g->n;
   const size_t words = std::max<size_t>((n + 31) / 32, 1);
   if (cudaMalloc(&g->d_excl, 2 * words * 4) != cudaSuccess) {
@@ -214,7 +220,7 @@ int build_component_tables(ldd_graph* g) {
   t.comp_len = t.comp_off + (n / 2 + 1);
   t.counters = t.comp_len + (n / 2 + 1);
   u32 counts[4] = {0, 0, 0, 0};
-  cudaError_t e = components_phase1(g->d_row, g->d_up, g->m_up, (u32)n, g->num_sms, t, g->d_excl,
+  cudaError_t e = components_phase1(g->d_row, d_arcs, g->m_up, (u32)n, g->num_sms, t, g->d_excl,
                                     g->d_solo, counts, nullptr);
   int rc = LDD_OK;
   SmallComps& sc = g->sc;
@@ -246,45 +252,74 @@ int build_component_tables(ldd_graph* g) {
   return rc;
 }
 
-// Rewrites d_up as the cut list of launch_cut (after the component labelling,
-// which reads it as arcs): each edge oriented from its cold endpoint to its
-// hot one (larger degree, ties to the smaller id), grouped by the cold
-// endpoint with a counting sort, and hot endpoints in the hot table encoded as
-// (slot | 2^31).  With degree skew most label reads of the cut then hit the
-// shared-memory copy of the hot table, and the cold side is read in order.
+// The grouped cut list of launch_cut (CutList): each edge oriented from its
+// cold endpoint to its hot one (larger degree, ties to the smaller id),
+// grouped by the cold endpoint with a counting sort, and hot endpoints in the
+// hot table encoded as (slot | 2^31).  With degree skew most label reads of
+// the cut then hit the shared-memory copy of the hot table, the cold side is
+// read once per group, and the edge stream is 4 bytes per edge.
 int build_cut_list(ldd_graph* g, const std::vector<int32_t>& rp, const std::vector<int2>& up) {
   const size_t n = (size_t)g->n, m = up.size();
-  if (m == 0) return LDD_OK;
+  CutList& cl = g->cut;
+  cl.m = (u32)m;
+  cl.nblk = (u32)((m + 31) / 32);
   auto deg = [&](int32_t v) { return rp[v + 1] - rp[v]; };
   auto hotter = [&](int32_t a, int32_t b) {
     const int32_t da = deg(a), db = deg(b);
     return da > db || (da == db && a < b);
   };
-  const size_t K = std::min<size_t>(kHotSlots, n);
+  const size_t K = m ? std::min<size_t>(kHotSlots, n) : 0;
   std::vector<int32_t> ids(n);
   for (size_t v = 0; v < n; ++v) ids[v] = (int32_t)v;
-  if (K < n) std::nth_element(ids.begin(), ids.begin() + K, ids.end(), hotter);
+  if (K > 0 && K < n) std::nth_element(ids.begin(), ids.begin() + K, ids.end(), hotter);
   std::sort(ids.begin(), ids.begin() + K, hotter);
   std::vector<int32_t> slot(n, -1);
   for (size_t i = 0; i < K; ++i) slot[ids[i]] = (int32_t)i;
   std::vector<u32> start(n + 1, 0);
   for (const int2& e : up) ++start[(hotter(e.x, e.y) ? e.y : e.x) + 1];
   for (size_t v = 0; v < n; ++v) start[v + 1] += start[v];
-  std::vector<int2> list(m);
+  std::vector<u32> grp_off, grp_v;
+  for (size_t v = 0; v < n; ++v)
+    if (start[v + 1] > start[v]) {
+      grp_v.push_back((u32)v);
+      grp_off.push_back(start[v]);
+    }
+  cl.ngrp = (u32)grp_v.size();
+  grp_off.push_back((u32)m);
+  std::vector<int32_t> hot(m);
   for (const int2& e : up) {
     const bool xh = hotter(e.x, e.y);
-    const int32_t hot = xh ? e.x : e.y, cold = xh ? e.y : e.x;
-    const int32_t enc = slot[hot] >= 0 ? (int32_t)(0x80000000u | (u32)slot[hot]) : hot;
-    list[start[cold]++] = make_int2(cold, enc);
+    const int32_t h = xh ? e.x : e.y, cold = xh ? e.y : e.x;
+    hot[start[cold]++] = slot[h] >= 0 ? (int32_t)(0x80000000u | (u32)slot[h]) : h;
+  }
+  std::vector<u32> blk_g(std::max<size_t>(cl.nblk, 1), 0), blk_mask(std::max<size_t>(cl.nblk, 1), 0);
+  for (u32 gi = 0; gi < cl.ngrp; ++gi) {
+    const u32 lo = grp_off[gi], hi = grp_off[gi + 1];
+    if (lo & 31u) blk_mask[lo >> 5] |= 1u << (lo & 31u);
+    for (u32 b = (lo + 31) / 32; b * 32 < hi; ++b) blk_g[b] = gi;
   }
   g->n_hot = (u32)K;
-  if (cudaMalloc(&g->d_hot, K * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_hot_center, K * 4) != cudaSuccess) {
+  if (cudaMalloc(&cl.hot, std::max<size_t>(m, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&cl.grp_off, grp_off.size() * 4) != cudaSuccess ||
+      cudaMalloc(&cl.grp_v, std::max<size_t>(grp_v.size(), 1) * 4) != cudaSuccess ||
+      cudaMalloc(&cl.grp_lab, std::max<size_t>(grp_v.size(), 1) * 4) != cudaSuccess ||
+      cudaMalloc(&cl.blk_g, blk_g.size() * 4) != cudaSuccess ||
+      cudaMalloc(&cl.blk_mask, blk_mask.size() * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_hot, std::max<size_t>(K, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_hot_center, std::max<size_t>(K, 1) * 4) != cudaSuccess) {
     cudaGetLastError();
-    return fail(LDD_ERR_OOM, "device allocation of the hot table failed");
+    return fail(LDD_ERR_OOM, "device allocation of the cut list failed");
   }
-  if (cudaMemcpy(g->d_hot, ids.data(), K * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(g->d_up, list.data(), m * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+  if ((K && cudaMemcpy(g->d_hot, ids.data(), K * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (m && cudaMemcpy(cl.hot, hot.data(), m * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(cl.grp_off, grp_off.data(), grp_off.size() * 4, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      (cl.ngrp && cudaMemcpy(cl.grp_v, grp_v.data(), grp_v.size() * 4, cudaMemcpyHostToDevice) !=
+                      cudaSuccess) ||
+      cudaMemcpy(cl.blk_g, blk_g.data(), blk_g.size() * 4, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(cl.blk_mask, blk_mask.data(), blk_mask.size() * 4, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
     return fail(LDD_ERR_CUDA, "upload of the cut list failed");
   return LDD_OK;
 }
@@ -608,8 +643,7 @@ int enqueue_fast(ldd_graph* g, bool want_cut) {
   if (g->uni && want_cut) {
     ldd_graph::Union& U = *g->uni;
     if (cudaMemsetAsync(U.d_cut, 0, (size_t)U.k * 8, s) != cudaSuccess) return -1;
-    launches += launch_union_cut(g->d_up, U.d_offs + 7 * ((size_t)U.cap.k + 1), U.nchunk, U.off,
-                                 U.k, U.d_out_c, U.d_cut, g->num_sms, s);
+    launches += launch_union_cut(g->cut, U.off, U.d_wmem, U.d_out_c, U.d_cut, g->num_sms, s);
     if (cudaMemcpyAsync(g->h_cut, U.d_cut, (size_t)U.k * 8, cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
       return -1;
@@ -701,7 +735,7 @@ int cut_on_device(ldd_graph* g, const int* d_center, int64_t* out_cut) {
   cudaStream_t s = g->stream;
   record(g, 6);
   CUDA_TRY(cudaMemsetAsync(&g->d_ctl->cut, 0, sizeof(u64), s));
-  const int l = launch_cut(g->d_up, g->m_up, d_center, g->d_hot, g->n_hot, g->d_hot_center,
+  const int l = launch_cut(g->cut, d_center, g->d_hot, g->n_hot, g->d_hot_center,
                            &g->d_ctl->cut, g->num_sms, s);
   CUDA_TRY(cudaMemcpyAsync(g->h_hdr + 128, &g->d_ctl->cut, sizeof(u64), cudaMemcpyDeviceToHost, s));
   record(g, 7);
@@ -749,6 +783,7 @@ UnionCaps union_needs(int k, ldd_graph* const* members) {
     c.N += ((u64)m->n + 31) / 32 * 32;
     c.E += (u64)m->nnz;
     c.M += m->m_up;
+    c.G += m->cut.ngrp;
     c.C += m->sc.ncomp;
     c.T += m->sc.total;
     c.total += (u64)m->n;
@@ -761,7 +796,8 @@ u64 union_bytes(const UnionCaps& c) {
   // members; staging: shifts in, outputs, offsets; scratch arena; start
   // buckets (three tables of N + 2)
   const u64 N = c.N, words = std::max<u64>(N / 32, 1);
-  u64 b = 4 * (N + 1) + 4 * c.E + 8 * c.M + 8 * words + 8 * c.C + 8 * c.T + 4 * N + 4 * words;
+  u64 b = 4 * (N + 1) + 4 * c.E + 4 * c.M + 20 * c.G + 8 * (c.M / 32 + 1) + 8 * words +
+          8 * c.C + 8 * c.T + 4 * N + 4 * words;
   b += 16 * c.total + 8 * c.total + 32ull * (c.k + 1) + 8ull * c.k + sizeof(UnionMember) * c.k;
   const u64 nk = std::max<u64>(N, 64);
   b += 8 * N + 4 * N + 16 * nk + 8 * N + ((N + kSortTile - 1) / kSortTile + 1) * 2048 + 4 * N +
@@ -794,7 +830,13 @@ int union_alloc(ldd_graph** out, int dev, const UnionCaps& c) {
   const u64 total = std::max<u64>(c.total, 1);
   if (cudaMalloc(&g->d_row, (N + 1) * 4) != cudaSuccess ||
       cudaMalloc(&g->d_col, std::max<u64>(c.E, 1) * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_up, std::max<u64>(c.M, 1) * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&g->cut.hot, std::max<u64>(c.M, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->cut.grp_off, (c.G + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->cut.grp_v, std::max<u64>(c.G, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->cut.grp_m, std::max<u64>(c.G, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->cut.grp_lab, std::max<u64>(c.G, 1) * 8) != cudaSuccess ||
+      cudaMalloc(&g->cut.blk_g, (c.M / 32 + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&g->cut.blk_mask, (c.M / 32 + 1) * 4) != cudaSuccess ||
       cudaMalloc(&g->d_excl, 2 * words * 4) != cudaSuccess ||
       cudaMalloc(&g->sc.comp_off, std::max<u64>(c.C, 1) * 4) != cudaSuccess ||
       cudaMalloc(&g->sc.comp_len, std::max<u64>(c.C, 1) * 4) != cudaSuccess ||
@@ -817,7 +859,8 @@ int union_alloc(ldd_graph** out, int dev, const UnionCaps& c) {
   U.d_out_d = U.d_out_c + total;
   const u32* d = U.d_offs;
   const size_t K1 = K + 1;
-  U.off = UnionOffsets{d, d + K1, d + 2 * K1, d + 3 * K1, d + 4 * K1, d + 5 * K1, d + 6 * K1};
+  U.off = UnionOffsets{d,          d + K1,     d + 2 * K1, d + 3 * K1,
+                       d + 4 * K1, d + 5 * K1, d + 6 * K1, d + 7 * K1};
   // the scratch arena and launch set-up are sized by the capacities
   g->n = (int32_t)N;
   g->nnz = (int64_t)c.E;
@@ -831,7 +874,7 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
   ldd_graph::Union& U = *g->uni;
   const UnionCaps need = union_needs(k, members);
   if ((u32)k > U.cap.k || need.N > U.cap.N || need.E > U.cap.E || need.M > U.cap.M ||
-      need.C > U.cap.C || need.T > U.cap.T || need.total > U.cap.total)
+      need.G > U.cap.G || need.C > U.cap.C || need.T > U.cap.T || need.total > U.cap.total)
     return fail(LDD_ERR_RANGE, "members exceed the union's capacity");
   const size_t K1 = (size_t)U.cap.k + 1;
   std::vector<u32> offs(8 * K1, 0);
@@ -847,7 +890,7 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
     at(4, i + 1) = at(4, i) + m->sc.total;
     at(5, i + 1) = at(5, i) + m->n_active;
     at(6, i + 1) = at(6, i) + (u32)m->n;
-    at(7, i + 1) = at(7, i) + (m->m_up + kUnionCutChunk - 1) / kUnionCutChunk;
+    at(7, i + 1) = at(7, i) + m->cut.ngrp;
     if (m->n_active > 0 && !m->d_active) all_active = false;
     nnz_active += m->nnz_active;
     n_active += m->n_active;
@@ -862,7 +905,9 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
   g->d_active = (all_active && n_active > 0) ? U.d_active_buf : nullptr;
   U.k = (u32)k;
   U.total = (u32)need.total;
-  U.nchunk = at(7, k);
+  g->cut.m = (u32)need.M;
+  g->cut.ngrp = (u32)need.G;
+  g->cut.nblk = (u32)((need.M + 31) / 32);
   U.h_voff.assign(offs.begin(), offs.begin() + k + 1);
   U.h_ooff.assign(offs.begin() + 6 * K1, offs.begin() + 6 * K1 + k + 1);
   std::vector<UnionMember> mv((size_t)k);
@@ -871,7 +916,9 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
     UnionMember& d = mv[(size_t)i];
     d.row = m->d_row;
     d.col = m->d_col;
-    d.up = m->d_up;
+    d.cut_hot = m->cut.hot;
+    d.grp_off = m->cut.grp_off;
+    d.grp_v = m->cut.grp_v;
     d.hot = m->d_hot;
     d.excl = m->d_excl;
     d.solo = m->d_solo;
@@ -887,7 +934,7 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
   CUDA_TRY(cudaMemcpyAsync(U.d_mem, mv.data(), mv.size() * sizeof(UnionMember),
                            cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(U.d_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, s));
-  UnionTables t{g->d_row, g->d_col, g->d_up, g->d_excl, g->d_solo, g->sc.comp_off,
+  UnionTables t{g->d_row, g->d_col, g->cut, g->d_excl, g->d_solo, g->sc.comp_off,
                 g->sc.comp_len, g->sc.comp_v, g->sc.adj, g->d_active, U.d_wmem};
   const u64 largest = std::max<u64>(std::max<u64>(need.N + 1, need.E), need.M);
   launch_union_concat(U.d_mem, U.off, U.k, t, largest, g->num_sms, s);
@@ -913,8 +960,7 @@ int union_run(ldd_graph* u, const double* d_in, int* center, int* dist, bool wan
   if (want_cut) {
     record(u, 6);
     CUDA_TRY(cudaMemsetAsync(U.d_cut, 0, (size_t)U.k * 8, s));
-    cl = launch_union_cut(u->d_up, U.d_offs + 7 * ((size_t)U.cap.k + 1), U.nchunk, U.off, U.k,
-                          center, U.d_cut, u->num_sms, s);
+    cl = launch_union_cut(u->cut, U.off, U.d_wmem, center, U.d_cut, u->num_sms, s);
     record(u, 7);
   }
   *launches_out = launches;
@@ -999,19 +1045,25 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
     for (int64_t e = rp[v]; e < rp[v + 1]; ++e)
       if (col[e] > v) up.push_back(make_int2(v, col[e]));
   g->m_up = (u32)up.size();
+  int2* d_arcs = nullptr;  // the arcs (v, w), v < w, for the component labelling only
   if (cudaMalloc(&g->d_row, rp.size() * 4) != cudaSuccess ||
       cudaMalloc(&g->d_col, std::max<size_t>(col.size(), 1) * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_up, std::max<size_t>(up.size(), 1) * sizeof(int2)) != cudaSuccess) {
+      cudaMalloc(&d_arcs, std::max<size_t>(up.size(), 1) * sizeof(int2)) != cudaSuccess) {
     cudaGetLastError();
+    cudaFree(d_arcs);
     return bail(fail(LDD_ERR_OOM, "device allocation of the graph failed"));
   }
   if (cudaMemcpy(g->d_row, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       (nnz > 0 &&
        cudaMemcpy(g->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
-      (!up.empty() && cudaMemcpy(g->d_up, up.data(), up.size() * sizeof(int2),
-                                 cudaMemcpyHostToDevice) != cudaSuccess))
+      (!up.empty() && cudaMemcpy(d_arcs, up.data(), up.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaFree(d_arcs);
     return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
-  if ((rc = build_component_tables(g)) != LDD_OK) return bail(rc);
+  }
+  rc = build_component_tables(g, d_arcs);
+  cudaFree(d_arcs);
+  if (rc != LDD_OK) return bail(rc);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
   if ((rc = build_active_list(g)) != LDD_OK) return bail(rc);
   if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);

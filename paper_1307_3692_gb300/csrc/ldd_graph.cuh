@@ -46,7 +46,8 @@ size_t align_up(size_t x, size_t a);
 struct UnionCaps {
   u64 N = 0;      // union vertices, members padded to multiples of 32
   u64 E = 0;      // arcs
-  u64 M = 0;      // cut-list entries
+  u64 M = 0;      // cut-list entries (undirected edges)
+  u64 G = 0;      // cut-list groups (cold vertices with edges)
   u64 C = 0;      // small components
   u64 T = 0;      // their members
   u64 total = 0;  // caller-layout entries (sum of member sizes)
@@ -68,8 +69,7 @@ struct ldd_graph {
   // device CSR and graph tables
   int* d_row = nullptr;
   int* d_col = nullptr;
-  int2* d_up = nullptr;        // the arcs (v, w) with v < w; after component labelling, the
-                               // cut list (cold, hot) of launch_cut
+  CutList cut;                 // grouped cut list (cut count of Definition 1.1)
   u32* d_active = nullptr;     // vertices the BFS handles, ascending (when few enough)
   u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
   int* d_hot_center = nullptr; // their labels, gathered per cut count
@@ -122,11 +122,10 @@ struct ldd_graph {
     UnionCaps cap;                 // capacities the tables were allocated for
     u32 k = 0;
     u32 total = 0;                 // n_0 + ... + n_{k-1}: caller-layout length
-    u32 nchunk = 0;                // cut chunks (chunk_off[k])
     std::vector<u32> h_ooff;       // caller-layout offsets, k + 1
     std::vector<u32> h_voff;       // union-vertex offsets, k + 1
     UnionMember* d_mem = nullptr;  // k member views (valid only while building)
-    u32* d_offs = nullptr;         // 8 arrays of cap.k + 1: v, e, u, c, m, a, o, chunk
+    u32* d_offs = nullptr;         // 8 arrays of cap.k + 1: v, e, u, c, m, a, o, g
     u32* d_active_buf = nullptr;   // [cap.N] active list (g->d_active when every member has one)
     UnionOffsets off{};
     double* d_shift_in = nullptr;  // [total] caller-layout shifts from the host

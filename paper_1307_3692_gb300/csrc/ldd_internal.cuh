@@ -196,14 +196,35 @@ size_t bfs_smem_bytes();
 // Finalize, cut and per-graph component tables (k_graph.cu).
 int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, int* center,
                     int* dist, const u32* err, int num_sms, cudaStream_t s);
-// Cut count over the graph's cut list: one entry (cold, hot) per undirected
-// edge {v, w}, v < w (repeated edges repeated), with hot the endpoint of larger
-// degree (ties: smaller id), sorted by cold.  hot < 0 stands for slot
-// hot & 0x7fffffff of the hot table: the (at most kHotSlots) highest-degree
-// vertices, whose labels the cut kernel keeps in shared memory.
+// Cut list of Definition 1.1's count.  Every undirected edge {v, w} (repeated
+// edges repeated) is stored once, oriented from its cold endpoint (smaller
+// degree; ties: larger id) to its hot one, and grouped by the cold endpoint:
+// group g (one per cold vertex that has edges, ascending) is hot[grp_off[g] ..
+// grp_off[g + 1]) with cold vertex grp_v[g].  hot[e] < 0 stands for slot
+// hot[e] & 0x7fffffff of the hot table (the at most kHotSlots highest-degree
+// vertices, whose labels the cut kernel keeps in shared memory).  The edges
+// come in blocks of 32: blk_g[b] is the group of edge 32 b, and bit j of
+// blk_mask[b] is set when edge 32 b + j (j > 0) starts a group, so edge
+// 32 b + j is in group blk_g[b] + popc(blk_mask[b] & bits 0 .. j).  About 4.3
+// bytes per edge, plus 12 per group (cold vertex, offset, its label per call).
+// In a union (k_union.cu) hot[] and grp_v[] hold caller-layout indices
+// (member-local id + the member's output offset) and grp_m[g] the member.
 constexpr u32 kHotSlots = 49152;  // 192 KiB of labels per CTA
-int launch_cut(const int2* list, u32 m, const int* center, const u32* hot, u32 n_hot,
-               int* hot_center, u64* out, int num_sms, cudaStream_t s);
+struct CutList {
+  int* hot = nullptr;
+  u32* grp_off = nullptr;   // [ngrp + 1]
+  u32* grp_v = nullptr;     // [ngrp]
+  u32* grp_m = nullptr;     // [ngrp] unions only
+  int* grp_lab = nullptr;   // [ngrp] labels of the cold vertices, per cut count
+                            //   (unions: [2 ngrp] words, (member << 32) | label)
+  u32* blk_g = nullptr;     // [nblk]
+  u32* blk_mask = nullptr;  // [nblk]
+  u32 m = 0;
+  u32 ngrp = 0;
+  u32 nblk = 0;             // (m + 31) / 32
+};
+int launch_cut(const CutList& cl, const int* center, const u32* hot, u32 n_hot, int* hot_center,
+               u64* out, int num_sms, cudaStream_t s);
 int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sms, cudaStream_t s);
 // The radius of a decomposition: max over v of dist[v], into *out.
 int launch_max_dist(const int* dist, u32 n, u32* out, int num_sms, cudaStream_t s);
@@ -224,8 +245,10 @@ cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScra
 struct UnionMember {
   const int* row;
   const int* col;
-  const int2* up;       // cut list (cold, hot), hot < 0: slot of the hot table
-  const u32* hot;
+  const int* cut_hot;   // cut list (see CutList): hot endpoints, < 0: slot of the hot table
+  const u32* grp_off;
+  const u32* grp_v;
+  const u32* hot;       // hot table
   const u32* excl;
   const u32* solo;
   const u32* comp_off;
@@ -238,7 +261,8 @@ struct UnionMember {
 };
 // Member offsets, k + 1 device words each: union vertices (v), arcs (e),
 // cut-list entries (u), small components (c) and their members (m), active
-// list entries (a), and caller-layout outputs (o: n_0 + ... + n_{s-1}).
+// list entries (a), caller-layout outputs (o: n_0 + ... + n_{s-1}), and
+// cut-list groups (g).
 struct UnionOffsets {
   const u32* v;
   const u32* e;
@@ -247,11 +271,12 @@ struct UnionOffsets {
   const u32* m;
   const u32* a;
   const u32* o;
+  const u32* g;
 };
 struct UnionTables {
   int* row;
   int* col;
-  int2* up;
+  CutList cut;
   u32* excl;
   u32* solo;
   u32* comp_off;
@@ -261,7 +286,6 @@ struct UnionTables {
   u32* active;
   u32* wmem;  // member of every 32-vertex word
 };
-constexpr u32 kUnionCutChunk = 8192;  // cut-list entries per block step, within one member
 // largest = the longest table (elements), for the grid size.
 int launch_union_concat(const UnionMember* mem, const UnionOffsets& off, u32 k,
                         const UnionTables& t, u64 largest, int num_sms, cudaStream_t s);
@@ -272,9 +296,12 @@ int launch_union_spread(const double* in, const UnionOffsets& off, u32 k, u32 N,
 int launch_union_finalize(const u64* key, const u32* order, const u32* solo,
                           const UnionOffsets& off, u32 k, u32 total, int* center, int* dist,
                           const u32* err, int num_sms, cudaStream_t s);
-// chunk_off[0 .. k]: first cut chunk of each member (nchunk = chunk_off[k]).
-int launch_union_cut(const int2* up, const u32* chunk_off, u32 nchunk, const UnionOffsets& off,
-                     u32 k, const int* center, u64* cut, int num_sms, cudaStream_t s);
+// Every member's cut count (cut[s], zero on entry) over the union's cut list
+// (hot ids resolved, no hot table); labels in the caller layout.
+int launch_union_cut(const CutList& cl, const UnionOffsets& off, const u32* wmem,
+                     const int* center, u64* cut, int num_sms, cudaStream_t s);
+// The union's block tables (cl.blk_g, cl.blk_mask) from its concatenated groups.
+int launch_cut_blocks(const CutList& cl, int num_sms, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ u32 lanemask_lt() {

@@ -63,11 +63,12 @@ struct Request {
   double submit_us = 0.0, start_us = 0.0, end_us = 0.0;
   int64_t batch_id = -1;
   int32_t batch_size = 0;
+  double fill_us = 0.0, run_us = 0.0;  // the batch's phases
 };
 
 bool fits(const UnionCaps& a, const UnionCaps& b, const UnionCaps& cap) {
   return a.N + b.N <= cap.N && a.E + b.E <= cap.E && a.M + b.M <= cap.M &&
-         a.C + b.C <= cap.C && a.T + b.T <= cap.T && a.total + b.total <= cap.total &&
+         a.G + b.G <= cap.G && a.C + b.C <= cap.C && a.T + b.T <= cap.T && a.total + b.total <= cap.total &&
          a.k + b.k <= cap.k;
 }
 
@@ -75,6 +76,7 @@ void add_to(UnionCaps& a, const UnionCaps& b) {
   a.N += b.N;
   a.E += b.E;
   a.M += b.M;
+  a.G += b.G;
   a.C += b.C;
   a.T += b.T;
   a.total += b.total;
@@ -92,6 +94,7 @@ UnionCaps caps_for(u64 budget, int max_batch, u64 max_vertices, u64 max_arcs) {
   N = N / 32 * 32;
   for (;;) {
     c.N = N;
+    c.G = std::min<u64>(N, c.M);
     c.C = N / 2;
     c.T = N;
     c.total = N;
@@ -152,6 +155,7 @@ int run_batch(ldd_server* S, int slot, const std::vector<Request*>& batch) {
     members[(size_t)i] = batch[(size_t)i]->g;
     want_cut |= batch[(size_t)i]->out_cut != nullptr;
   }
+  const double t0 = S->now_us();
   int rc = union_fill(u, k, members.data(), s, false);
   if (rc != LDD_OK) return rc;
   for (int i = 0; i < k; ++i) {
@@ -159,11 +163,21 @@ int run_batch(ldd_server* S, int slot, const std::vector<Request*>& batch) {
     CUDA_TRY(cudaMemcpyAsync(U.d_shift_in + U.h_ooff[(size_t)i], r->shifts,
                              (size_t)r->g->n * 8, cudaMemcpyHostToDevice, s));
   }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const double t1 = S->now_us();
   int launches = 0, cut_launches = 0;
+  double t2, t3;
   {
     std::lock_guard<std::mutex> lk(S->dev_mu);
+    t2 = S->now_us();
     rc = union_run(u, U.d_shift_in, U.d_out_c, U.d_out_d, want_cut, &launches, &cut_launches);
     if (rc != LDD_OK) return rc;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    t3 = S->now_us();
+  }
+  for (Request* r : batch) {
+    r->fill_us = t1 - t0;
+    r->run_us = t3 - t2;
   }
   if (want_cut)
     CUDA_TRY(cudaMemcpyAsync(S->h_cut[(size_t)slot], U.d_cut, (size_t)k * 8,
@@ -387,6 +401,8 @@ int ldd_server_wait(ldd_server* S, int64_t ticket, ldd_request_info* info) {
     info->submit_us = r->submit_us;
     info->start_us = r->start_us;
     info->end_us = r->end_us;
+    info->batch_fill_us = r->fill_us;
+    info->batch_run_us = r->run_us;
   }
   if (status != LDD_OK) fail(status, "%s", r->msg);
   S->reqs[(size_t)ticket].reset();
