@@ -248,6 +248,9 @@ BATCH_WORKLOADS = {
                            beta_hi=0.5, master_seed=11),
     "rmat20_seeds_64": dict(kind="seeds", graph=("rmat", 20, 16, 0.57, 0.19, 0.19, 7),
                             copies=64, beta=0.1, first_seed=1),
+    # the first 128 graphs of rgg_batch_1024: a profiling case a few GB in size
+    "rgg_batch_128": dict(kind="rgg", count=128, n_lo=1000, n_hi=200000, beta_lo=0.02,
+                          beta_hi=0.5, master_seed=11),
 }
 
 
