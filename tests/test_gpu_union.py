@@ -131,3 +131,29 @@ def test_union_errors(ldd, cuda):
     assert cuts[0] == cuts[1] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
     u.close()
     g.close()
+
+
+def test_union_of_many_members(ldd, cuda):
+    """More members than the round loop keeps per-member floors for in shared
+    memory (4,096): the global per-member table path.  Every member is a
+    connected 6x7 grid (42 vertices, so the round loop handles it), plus one
+    larger R-MAT member; betas and seeds vary per member."""
+    small = gen.grid2d(6, 7)
+    big = gen.rmat(12)
+    gs = ldd.LddGraph(small.row_ptr, small.col)
+    gb = ldd.LddGraph(big.row_ptr, big.col)
+    k = 4300
+    members = [gs] * k + [gb]
+    Gs = [small] * k + [big]
+    rng = np.random.default_rng(8)
+    betas = [float(x) for x in rng.uniform(0.05, 1.0, k + 1)]
+    shifts = [gen.shifts(G.n, b, 7000 + i) for i, (G, b) in enumerate(zip(Gs, betas))]
+    u = ldd.LddUnion(members)
+    cen = torch.empty(u.total, dtype=torch.int32, device=cuda)
+    dis = torch.empty(u.total, dtype=torch.int32, device=cuda)
+    cuts = u.decompose(betas, torch.from_numpy(np.concatenate(shifts)).to(cuda), cen, dis)
+    _check_members(Gs, shifts, cen.cpu().numpy(), dis.cpu().numpy(), cuts, u.offsets)
+    assert u.stats()["rounds"] > 0
+    u.close()
+    gs.close()
+    gb.close()
