@@ -2,11 +2,16 @@
 // checks, host/device pointer handling, scratch memory and the order of the
 // kernels of one decomposition (Miller, Peng, Xu 2013, Algorithm 1):
 //   step 1 (shifts)      : given by the caller, copied to the device if needed
-//   step 2 (delta_max)   : k_split_hist                       (k_rank.cu)
-//   Section 4 tie-break  : fraction rank sort, keys, buckets   (k_rank.cu)
+//   step 2 (delta_max)   : the split of k_bplace / k_split64   (k_rank.cu)
+//   Section 4 tie-break  : fraction rank, keys, start buckets  (k_rank.cu)
 //   step 3 (BFS)         : persistent cooperative k_bfs        (k_bfs.cu)
 //                          and k_small_comp for components of <= 32 vertices
 //   step 4 (assignment)  : k_finalize                          (k_graph.cu)
+// and of the entry points built on it: cut counts (Definition 1.1), the
+// permutation variant and the retry loop (Section 4, Theorem 1.2's proof),
+// pipelined batches, disjoint unions (k_union.cu), CUDA-graph replay of the
+// fast path, and launch-parameter tuning.  The request server is in
+// ldd_server.cu.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
