@@ -475,6 +475,9 @@ def batch_arm(args):
     center = torch.empty(total, dtype=torch.int32, device=dev)
     dist_out = torch.empty(total, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    tuning = None
+    if not args.no_autotune:  # launch parameters picked for this batch (results unaffected)
+        tuning = u.autotune(d_shift, reps=1)
     for _ in range(args.warmup):
         cuts = u.decompose(betas, d_shift, center, dist_out)
     torch.cuda.synchronize()
@@ -583,6 +586,7 @@ def batch_arm(args):
                     "ms_per_step": 1e3 * e2e_s, "api": "ldd_union_decompose (pinned host buffers)"},
             "gpu_launches": launches,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "autotuned": tuning,
             "union": {"replayed_in_timed_steps": sts[-1]["replayed"],
                       "ms_replay": sts[-1]["ms_replay"], "rounds": st["rounds"], "pull_rounds": st["pull_rounds"], "A": st["max_floor_shift"],
                       "ms_rank": st["ms_rank"], "ms_bfs": st["ms_bfs"], "ms_finalize": st["ms_finalize"],
@@ -811,6 +815,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-batch", type=int, default=256,
                     help="serving: most requests per batch")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workloads: keep the default launch parameters")
     ap.add_argument("--no-replay", action="store_true",
                     help="batched workloads: run the regular path instead of the captured CUDA graph")
     args = ap.parse_args(argv)

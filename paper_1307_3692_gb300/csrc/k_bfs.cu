@@ -520,9 +520,14 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
 }
 
 // U: a union of graphs (per-member bottom-up floors); a separate instance so
-// that the plain kernel carries none of it.
-template <bool U>
-__global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
+// that the plain kernel carries none of it.  kPerSm: the CTAs per SM the
+// instance is built for.  One CTA per SM leaves it 128 registers per thread
+// (no spills) and the cheapest grid barrier, the best for thin frontiers and
+// single graphs; two give twice the warps, the best for the wide bottom-up
+// rounds of many-seed unions.  The launch parameter bfs_blocks_per_sm picks
+// the instance.
+template <bool U, int kPerSm>
+__global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   // union with few enough members: per-member next-level minima and
@@ -645,35 +650,45 @@ __global__ void __launch_bounds__(kBfsThreads, 2) k_bfs(BfsArgs a) {
 
 size_t bfs_smem_bytes() { return sizeof(Smem); }
 
+namespace {
+size_t bfs_smem(bool u) { return sizeof(Smem) + (u ? 2 * kSmemMembers * sizeof(u32) : 0); }
+
+const void* bfs_kernel(bool u, int per_sm) {
+  if (u) return per_sm >= 2 ? (const void*)k_bfs<true, 2> : (const void*)k_bfs<true, 1>;
+  return per_sm >= 2 ? (const void*)k_bfs<false, 2> : (const void*)k_bfs<false, 1>;
+}
+}  // namespace
+
 int bfs_grid_size(int num_sms, int* blocks_per_sm) {
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaFuncSetAttribute(k_bfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(Smem));
-    cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(Smem) + 2 * kSmemMembers * sizeof(u32)));
+    for (int u = 0; u < 2; ++u)
+      for (int p = 1; p <= 2; ++p)
+        cudaFuncSetAttribute(bfs_kernel(u != 0, p), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bfs_smem(u != 0));
     attr_set[dev] = true;
   }
-  int per_sm = 0, per_sm_u = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs<false>,
-                                                                kBfsThreads, sizeof(Smem));
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm_u, k_bfs<true>, kBfsThreads, sizeof(Smem) + 2 * kSmemMembers * sizeof(u32));
-  per_sm = min(per_sm, per_sm_u);
-  if (e != cudaSuccess || per_sm < 1) return -1;
-  per_sm = per_sm > 2 ? 2 : per_sm;
+  // the most CTAs per SM (1 or 2) that every instance built for it reaches
+  int per_sm = 2;
+  for (int u = 0; u < 2; ++u)
+    for (int p = 1; p <= 2; ++p) {
+      int got = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, bfs_kernel(u != 0, p), kBfsThreads,
+                                                        bfs_smem(u != 0)) != cudaSuccess)
+        return -1;
+      if (got < 1) return -1;
+      if (got < p) per_sm = min(per_sm, got);
+    }
   *blocks_per_sm = per_sm;
   return per_sm * num_sms;
 }
 
-int launch_bfs(const BfsArgs& a, int grid, cudaStream_t s, cudaError_t* err) {
+int launch_bfs(const BfsArgs& a, int grid, int per_sm, cudaStream_t s, cudaError_t* err) {
   BfsArgs copy = a;
   void* args[] = {&copy};
-  const void* fn = a.mrank ? (const void*)k_bfs<true> : (const void*)k_bfs<false>;
-  const size_t smem = sizeof(Smem) + (a.mrank ? 2 * kSmemMembers * sizeof(u32) : 0);
-  *err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBfsThreads), args, smem, s);
+  *err = cudaLaunchCooperativeKernel(bfs_kernel(a.mrank != nullptr, per_sm), dim3(grid),
+                                     dim3(kBfsThreads), args, bfs_smem(a.mrank != nullptr), s);
   return *err == cudaSuccess ? 1 : -1;
 }
 

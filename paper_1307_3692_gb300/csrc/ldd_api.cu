@@ -413,7 +413,7 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
       *status = fail(LDD_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
       return -1;
     }
-    if (launch_bfs(bfs_args(g), g->bfs_grid, s, &e) < 0) {
+    if (launch_bfs(bfs_args(g), g->bfs_grid, g->bfs_per_sm, s, &e) < 0) {
       *status = fail(LDD_ERR_CUDA, "cooperative launch of the BFS kernel (%d x %d) failed: %s",
                      g->bfs_grid, kBfsThreads, cudaGetErrorString(e));
       return -1;
@@ -439,13 +439,16 @@ int finish_setup(ldd_graph* g) {
     return fail(LDD_ERR_OOM, "pinned host allocation failed");
   for (auto& e : g->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(LDD_ERR_CUDA, "cudaEventCreate");
-  g->bfs_grid = bfs_grid_size(g->num_sms, &g->bfs_per_sm);
-  if (g->bfs_grid <= 0) return fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed");
+  int max_per_sm = 0;
+  if (bfs_grid_size(g->num_sms, &max_per_sm) <= 0)
+    return fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed");
+  // one CTA per SM for a single graph (thin frontiers, cheapest barrier), two
+  // for a union (its wide bottom-up rounds of many members want the warps);
+  // ldd_autotune and ldd_set_tuning choose per workload
+  g->bfs_per_sm = std::min(max_per_sm, g->uni ? 2 : 1);
   const u32 per_sm = env_u32("LDD_BFS_BLOCKS_PER_SM", 0);
-  if (per_sm > 0 && (int)per_sm < g->bfs_per_sm) {
-    g->bfs_per_sm = (int)per_sm;
-    g->bfs_grid = g->bfs_per_sm * g->num_sms;
-  }
+  if (per_sm > 0 && (int)per_sm <= max_per_sm) g->bfs_per_sm = (int)per_sm;
+  g->bfs_grid = g->bfs_per_sm * g->num_sms;
   g->spin_limit = env_u32("LDD_SPIN_LIMIT", 1u << 22);
   g->pull_alpha = env_u32("LDD_PULL_ALPHA", 14);
   g->pull_beta = env_u32("LDD_PULL_BETA", 24);

@@ -190,8 +190,10 @@ size_t rank_status_words(u32 n, u32 bptr_cap);
 size_t fraction_slot_bytes(u32 n);
 // Persistent BFS (k_bfs.cu).  Returns kernels launched, or -1 with the CUDA
 // error left in *err.
+// The most CTAs per SM (1 or 2) the round loop can use; returns that times num_sms.
 int bfs_grid_size(int num_sms, int* blocks_per_sm);
-int launch_bfs(const BfsArgs& a, int grid, cudaStream_t s, cudaError_t* err);
+// per_sm (1 or 2) picks the kernel instance built for that many CTAs per SM.
+int launch_bfs(const BfsArgs& a, int grid, int per_sm, cudaStream_t s, cudaError_t* err);
 size_t bfs_smem_bytes();
 // Finalize, cut and per-graph component tables (k_graph.cu).
 int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, int* center,
