@@ -140,10 +140,12 @@ int ldd_decompose_retry(ldd_graph* g, double beta, int k, const double* const* s
 /*
  * ldd_decompose_batch -- k independent decompositions of g, one per shift
  * vector (as ldd_decompose, Algorithm 2 via Algorithm 1 / Section 4), and
- * optionally the cut count of each (Definition 1.1), pipelined: while
- * decomposition i runs, shift vector i + 1 is copied to the device and the
- * results of decomposition i - 1 are copied back, on two copy streams of the
- * library's own.  Tree-embedding callers draw many shift vectors per graph
+ * optionally the cut count of each (Definition 1.1), pipelined: the k
+ * decompositions are queued back to back with one host synchronisation at the
+ * end, and while decomposition i runs, shift vector i + 1 is copied to the
+ * device and the results of decomposition i - 1 are copied back, on two copy
+ * streams of the library's own.  A decomposition whose shifts need the exact
+ * fraction rank (crafted ties) is redone alone after the others.  Tree-embedding callers draw many shift vectors per graph
  * (Section 1); a sweep over beta is the same call.
  *   k           number of decompositions (0 is a no-op).
  *   betas       double[k]: as ldd_decompose's beta, each finite and > 0.

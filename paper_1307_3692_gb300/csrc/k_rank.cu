@@ -219,28 +219,6 @@ __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta
   finish_split(err, amax, ctl);
 }
 
-// Start-round counts in round order, rcnt[r] = acnt[A - r] for r = 0 .. A and
-// rcnt[A + 1] = 0, ready for the exclusive scan that makes them bptr; acnt is
-// cleared on the way (all zero for the next decomposition).  A table too
-// small for A + 2 rounds sets kErrBucketCap.
-__global__ void __launch_bounds__(256) k_round_counts(u32* acnt, u32* rcnt, u32 cap, Control* ctl) {
-  if (failed(ctl)) return;
-  const int A = ctl->A;
-  if ((u64)A + 2 > cap) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrBucketCap);
-    return;
-  }
-  const u32 len = (u32)A + 2u;
-  for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < len; r += gridDim.x * blockDim.x) {
-    u32 c = 0;
-    if (r <= (u32)A) {
-      c = acnt[(u32)A - r];
-      acnt[(u32)A - r] = 0;
-    }
-    rcnt[r] = c;
-  }
-}
-
 // True if record o comes before record me in (f descending, id ascending).
 __device__ __forceinline__ bool rec_before(const ulonglong2 o, const ulonglong2 me) {
   const u32 uo = (u32)o.y & 0x7fffffffu, um = (u32)me.y & 0x7fffffffu;
@@ -282,58 +260,58 @@ __device__ __forceinline__ void place_start_warp(bool take, u32 u, u32 R, u32 n,
   }
 }
 
-// Pass 2: blocks take tiles of kTileBuckets consecutive buckets.  The tile's
-// records (bucket b's len = start[b + 1] - start[b] records sit in slots
-// [b * kSlotCap, b * kSlotCap + len)) are staged densely in shared memory in
-// bucket order, one thread per record; then every thread ranks one record
-// against the members of its own bucket: rank = start[b] + the number of
-// members before it in (f descending, id ascending), and writes order[] and
-// the key.  The tile's vertices then go into their start buckets: counted per
-// start round in shared memory, one global reservation per round and tile,
-// then written.  A tile with more than kTileRecs records (crowded fractions
-// just short of a slot overflow) is ranked from global memory instead, and
-// with more than kSortRBins start rounds the reservations are per warp.
-constexpr u32 kTileBuckets = 128;  // <= threads per CTA (one capacity check each)
-constexpr u32 kTileRecs = 2560;
+// Pass 2: CTAs take tiles of kTileBuckets consecutive buckets, in ticket
+// order.  The tile's records (bucket b's len = start[b + 1] - start[b] records
+// sit in slots [b * kSlotCap, b * kSlotCap + len)) are staged densely in
+// shared memory in bucket order: first every position learns its bucket and
+// the bucket's span of positions (one warp per bucket, shared memory only),
+// then one thread per position copies its record.  Every thread then ranks
+// one record against the members of its own bucket: rank = start[b] + the
+// number of members before it in (f descending, id ascending), comparing the
+// fraction bits alone unless another member has the same bits; and writes
+// order[] and the key.  The tile's vertices then go into their start buckets:
+// counted per start round in shared memory, one global reservation per round
+// and tile, then written.  A tile with more than kTileRecs records (crowded
+// fractions just short of a slot overflow) is ranked from global memory
+// instead, and with more than kSortRBins start rounds the reservations are
+// per warp.
+constexpr u32 kTileBuckets = 128;  // <= threads per CTA (one capacity check each); < 256
+constexpr u32 kTileRecs = 2560;    // < 2^16: spans are two 16-bit positions
 constexpr u32 kSortRBins = 2048;
 
 struct BsortSmem {
-  ulonglong2 rec[kTileRecs];
-  u32 loc[kTileRecs];     // record's offset within its start round's share of the tile
-  u32 rc[kSortRBins];     // the tile's count per start round, then its base in the round
-  u32 st[kTileBuckets + 1];
+  u64 fx[kTileRecs];         // fraction bits of the tile's records, bucket order
+  u64 fy[kTileRecs];         // (a_u << 32) | u | (not handled by the BFS) << 31
+  u32 span[kTileRecs];       // (first << 16) | end: the record's bucket as tile positions
+  u32 loc[kTileRecs];        // record's offset within its start round's share of the tile
+  u32 rc[kSortRBins];        // the tile's count per start round, then its base in the round
+  u32 st[kTileBuckets + 1];  // global first rank of every bucket of the tile, and the end
+  unsigned char bi[kTileRecs];  // record's bucket within the tile
+  u32 tile;
 };
-
-// Index i of the bucket holding dense position q: st[i] <= st[0] + q < st[i + 1].
-__device__ __forceinline__ u32 tile_bucket(const u32* st, u32 nb, u32 q) {
-  const u32 target = st[0] + q;
-  u32 lo = 0, hi = nb - 1;
-  while (lo < hi) {
-    const u32 mid = (lo + hi + 1) >> 1;
-    if (st[mid] <= target) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
 __global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start, u32 nbkt,
                                                   const ulonglong2* __restrict__ slots, u32 n,
                                                   u32* __restrict__ order, u64* __restrict__ key,
                                                   u32* rcur, u32* __restrict__ bv,
-                                                  u32* __restrict__ rk, Control* ctl) {
+                                                  u32* __restrict__ rk, u32* ticket, Control* ctl) {
   extern __shared__ __align__(16) unsigned char bsort_raw[];
   BsortSmem& sm = *reinterpret_cast<BsortSmem*>(bsort_raw);
   if (failed(ctl)) return;
   const int A = ctl->A;
   const bool small = (u32)A < kSortRBins;
-  const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   if (small)
     for (u32 i = tid; i <= (u32)A; i += blockDim.x) sm.rc[i] = 0;
   const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
-  for (u32 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (;;) {
+    __syncthreads();  // previous tile done with sm
+    if (tid == 0) sm.tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const u32 t = sm.tile;
+    if (t >= ntiles) break;
     const u32 b0 = t * kTileBuckets;
     const u32 nb = min(kTileBuckets, nbkt - b0);
-    __syncthreads();  // previous tile done with sm
     for (u32 i = tid; i <= nb; i += blockDim.x) sm.st[i] = start[b0 + i];
     __syncthreads();
     // a bucket beyond kSlotCap cannot reach here (k_bplace flags it); checked anyway
@@ -341,9 +319,20 @@ __global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start,
     const bool overfull = __syncthreads_or(full) != 0;
     const u32 total = sm.st[nb] - sm.st[0];
     if (!overfull && total <= kTileRecs) {
+      for (u32 i = warp; i < nb; i += nwarp) {
+        const u32 s0 = sm.st[i] - sm.st[0], e = sm.st[i + 1] - sm.st[0];
+        for (u32 q = s0 + lane; q < e; q += 32) {
+          sm.span[q] = (s0 << 16) | e;
+          sm.bi[q] = (unsigned char)i;
+        }
+      }
+      __syncthreads();
+#pragma unroll 4
       for (u32 q = tid; q < total; q += blockDim.x) {
-        const u32 i = tile_bucket(sm.st, nb, q);
-        sm.rec[q] = slots[(size_t)(b0 + i) * kSlotCap + (sm.st[0] + q - sm.st[i])];
+        const u32 i = sm.bi[q];
+        const ulonglong2 rec = slots[(size_t)(b0 + i) * kSlotCap + (q - (sm.span[q] >> 16))];
+        sm.fx[q] = rec.x;
+        sm.fy[q] = rec.y;
       }
       __syncthreads();
       for (u32 q0 = 0; q0 < total; q0 += blockDim.x) {
@@ -352,12 +341,20 @@ __global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start,
         ulonglong2 me = make_ulonglong2(0ull, 0ull);
         u32 p = 0;
         if (valid) {
-          const u32 i = tile_bucket(sm.st, nb, q);
-          me = sm.rec[q];
-          const u32 lo = sm.st[i] - sm.st[0], hi = sm.st[i + 1] - sm.st[0];
-          u32 r = 0;
-          for (u32 j = lo; j < hi; ++j) r += rec_before(sm.rec[j], me) ? 1u : 0u;
-          p = sm.st[i] + r;
+          me = make_ulonglong2(sm.fx[q], sm.fy[q]);
+          const u32 sp = sm.span[q], lo = sp >> 16, hi = sp & 0xffffu;
+          u32 r = 0, eq = 0;
+          for (u32 j = lo; j < hi; ++j) {
+            const u64 x = sm.fx[j];
+            r += x > me.x ? 1u : 0u;
+            eq += x == me.x ? 1u : 0u;
+          }
+          if (eq > 1) {  // another member with the same fraction: the smaller id goes first
+            const u32 um = (u32)me.y & 0x7fffffffu;
+            for (u32 j = lo; j < hi; ++j)
+              r += (sm.fx[j] == me.x && ((u32)sm.fy[j] & 0x7fffffffu) < um) ? 1u : 0u;
+          }
+          p = sm.st[0] + lo + r;
         }
         const bool take = emit_key(valid, me, p, n, A, order, key);
         const u32 R = (u32)(A - (int)(u32)(me.y >> 32));
@@ -375,10 +372,10 @@ __global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start,
         }
         __syncthreads();
         for (u32 q = tid; q < total; q += blockDim.x) {
-          const ulonglong2 me = sm.rec[q];
-          const u32 u = (u32)me.y & 0x7fffffffu;
-          if (((u32)me.y >> 31) || u >= n) continue;
-          const u32 R = (u32)(A - (int)(u32)(me.y >> 32));
+          const u64 y = sm.fy[q];
+          const u32 u = (u32)y & 0x7fffffffu;
+          if (((u32)y >> 31) || u >= n) continue;
+          const u32 R = (u32)(A - (int)(u32)(y >> 32));
           const u32 pos = sm.rc[R] + sm.loc[q];
           if (pos < n) {
             bv[pos] = u;
@@ -390,7 +387,7 @@ __global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start,
       }
     } else {
       // one warp per bucket, records read from global memory
-      for (u32 i = warp; i < nb; i += blockDim.x / 32) {
+      for (u32 i = warp; i < nb; i += nwarp) {
         const u32 s0 = sm.st[i], len = sm.st[i + 1] - sm.st[i];
         if (len > kSlotCap) continue;  // cannot happen: k_bplace flags a full bucket
         const ulonglong2* bs = slots + (size_t)(b0 + i) * kSlotCap;
@@ -641,18 +638,31 @@ __global__ void __launch_bounds__(256) k_rank_scatter(const u32* __restrict__ v0
 // ---------------------------------------------------------------- device scan
 // In-place exclusive scan of data[0 .. len), single pass with decoupled
 // look-back over 4096-element tiles.  len = A + 2 when len_from_A (the
-// start-round histogram), else len_host.  Optionally copies the result to
-// copy[] and records the largest input value in *maxv.  Tiles take tickets in
-// order, so every tile's predecessors are running or done; every wait is
-// bounded.  One warp looks back over 32 predecessor tiles at a time.
+// start-round histogram), else len_host.  With rev_src (fast path), the input
+// is the floor histogram read in reverse, data[r] = rev_src[A - r] for
+// r = 0 .. A and 0 for r = A + 1, and rev_src is cleared on the way (all zero
+// for the next decomposition); a table of fewer than A + 2 entries (cap) sets
+// kErrBucketCap.  Optionally copies the result to copy[] and records the
+// largest input value in *maxv.  Tiles take tickets in order, so every tile's
+// predecessors are running or done; every wait is bounded.  One warp looks
+// back over 32 predecessor tiles at a time.
 __global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy, u32 len_host,
                                                             int len_from_A, u64* __restrict__ status,
                                                             u32 epoch, u32* tile_ctr, u32* maxv,
-                                                            Control* ctl) {
+                                                            u32* rev_src, u32 cap, Control* ctl) {
   __shared__ u32 s_tile, s_excl, s_bad;
   __shared__ u32 s_wsum[kScanThreads / 32];
   __shared__ u32 s_wmax[kScanThreads / 32];
-  if (failed(ctl)) return;
+  if (failed(ctl)) {
+    // an upstream error skips the scan; the floor counts are still cleared, so
+    // a decomposition queued behind this one starts from zero counts
+    if (rev_src) {
+      const u32 end = (u32)min((u64)(u32)ctl->A + 1, (u64)cap);
+      for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < end; r += gridDim.x * blockDim.x)
+        rev_src[r] = 0;
+    }
+    return;
+  }
   const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     s_tile = atomicAdd(tile_ctr, 1u);
@@ -661,7 +671,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy
   }
   __syncthreads();
   const u32 tile = s_tile;
-  const u32 len = len_from_A ? (u32)ctl->A + 2u : len_host;
+  const int A = ctl->A;
+  if (rev_src && (u64)A + 2 > cap) {
+    if (tile == 0 && tid == 0) atomicOr(&ctl->err, kErrBucketCap);
+    for (u32 r = tile * kScanTile + tid; r < min(cap, (tile + 1) * kScanTile); r += blockDim.x)
+      rev_src[r] = 0;  // cleared as above
+    return;
+  }
+  const u32 len = len_from_A ? (u32)A + 2u : len_host;
   const u32 t0 = tile * kScanTile;
   if (t0 >= len) return;  // tiles past the end: no later tile needs them
   const u32 my0 = t0 + tid * kScanIpt;
@@ -669,7 +686,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy
   u32 tot = 0, mx = 0;
 #pragma unroll
   for (int i = 0; i < kScanIpt; ++i) {
-    v[i] = (my0 + i < len) ? data[my0 + i] : 0u;
+    const u32 r = my0 + i;
+    if (rev_src) {
+      v[i] = 0;
+      if (r <= (u32)A) {
+        v[i] = rev_src[(u32)A - r];
+        rev_src[(u32)A - r] = 0;
+      }
+    } else {
+      v[i] = (r < len) ? data[r] : 0u;
+    }
     tot += v[i];
     mx = max(mx, v[i]);
   }
@@ -912,6 +938,20 @@ void allow_bsort_smem() {
   }
 }
 
+// CTAs of k_bplace resident on one SM: its grid is one full wave.
+int bplace_blocks_per_sm() {
+  static int per_sm[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 4;
+  if (per_sm[dev] <= 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bplace, 256, 0) != cudaSuccess || b < 1)
+      b = 4;
+    per_sm[dev] = b;
+  }
+  return per_sm[dev];
+}
+
 void allow_sort_smem() {
   static bool done[64] = {};
   int dev = 0;
@@ -956,19 +996,22 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
     ulonglong2* slots = reinterpret_cast<ulonglong2*>(r.slots);
     if (r.acnt_dirty) cudaMemsetAsync(r.acnt, 0, (size_t)r.bptr_cap * 4, s);
     cudaMemsetAsync(cnt, 0, (size_t)(nbkt + 1) * 4, s);
-    k_bplace<<<grid_stride_blocks((n + kPlaceIpt - 1) / kPlaceIpt, r.num_sms), 256, 0, s>>>(
+    const u32 place_grid = (u32)min((long long)(n + 256 * kPlaceIpt - 1) / (256 * kPlaceIpt),
+                                    (long long)r.num_sms * bplace_blocks_per_sm());
+    k_bplace<<<max(place_grid, 1u), 256, 0, s>>>(
         r.shift, r.solo, r.excl, n, (int)B, cnt, slots, r.acnt, r.bptr_cap, r.wmem, r.lift, ctl);
     k_scan_excl<<<(nbkt + 1 + kScanTile - 1) / kScanTile, kScanThreads, 0, s>>>(
-        cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, ctl);
-    k_round_counts<<<grid_stride_blocks(r.bptr_cap, r.num_sms), 256, 0, s>>>(r.acnt, rcnt,
-                                                                               r.bptr_cap, ctl);
+        cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, nullptr, 0,
+        ctl);
     k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
-                                                 &ctl->tile_ctr[1], nullptr, ctl);
+                                                 &ctl->tile_ctr[1], nullptr, r.acnt, r.bptr_cap,
+                                                 ctl);
     allow_bsort_smem();
     const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
     k_bsort<<<(u32)min((long long)ntiles, (long long)r.num_sms * 3), 256, sizeof(BsortSmem), s>>>(
-        cnt, nbkt, slots, n, r.order, r.key, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0), ctl);
-    return launches + 5;
+        cnt, nbkt, slots, n, r.order, r.key, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0),
+        &ctl->tile_ctr[kFracDigits + kRoundDigits - 1], ctl);
+    return launches + 4;
   }
   // exact path: stable LSD radix sort of all fractions, then keys and the
   // start-round counting sort (groups in any order inside)
@@ -990,7 +1033,7 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
                                                                             ctl);
   k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
   k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
-                                               &ctl->tile_ctr[1], nullptr, ctl);
+                                               &ctl->tile_ctr[1], nullptr, nullptr, 0, ctl);
   k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
                         (long long)r.num_sms * 8),
                256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));
@@ -1011,7 +1054,7 @@ int launch_ranked_and_buckets(const RankBufs& r, const int* levels, const int* p
                                                                             ctl);
   k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
   k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
-                                               &ctl->tile_ctr[1], nullptr, ctl);
+                                               &ctl->tile_ctr[1], nullptr, nullptr, 0, ctl);
   k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
                         (long long)r.num_sms * 8),
                256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));

@@ -100,6 +100,7 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_acnt);
   cudaFree(g->batch_arena);
   if (g->h_hdr) cudaFreeHost(g->h_hdr);
+  if (g->h_bhdr) cudaFreeHost(g->h_bhdr);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i) {
@@ -757,6 +758,60 @@ int cut_on_device(ldd_graph* g, const int* d_center, int64_t* out_cut) {
   return LDD_OK;
 }
 
+// One fast-path decomposition of a plain graph queued on g->stream with no
+// host synchronisation: control block cleared, rank, BFS, finalize into
+// center/dist, the cut count when want_cut (it accumulates in the control
+// header), and the header copied to the pinned block hdr.  A fast rank path
+// that asks for the exact path leaves the floor counts cleared and skips the
+// rest, so the decompositions queued behind it run as usual.
+int enqueue_pipelined(ldd_graph* g, const double* d_shift, int* center, int* dist, bool want_cut,
+                      unsigned char* hdr, int* launches) {
+  cudaStream_t s = g->stream;
+  if (g->epoch > 0xfffff000u) {  // status tags would wrap: clear and restart
+    CUDA_TRY(cudaMemsetAsync(g->d_status, 0, g->status_bytes, s));
+    g->epoch = 0;
+  }
+  CUDA_TRY(cudaMemsetAsync(g->d_ctl, 0, sizeof(Control), s));
+  if (g->acnt_dirty) {
+    CUDA_TRY(cudaMemsetAsync(g->d_acnt, 0, (size_t)g->bptr_cap * 4, s));
+    g->acnt_dirty = false;
+  }
+  RankBufs rb = rank_bufs(g, d_shift);
+  rb.acnt_dirty = false;
+  int l = launch_rank_and_buckets(rb, false, s);
+  int status = LDD_OK;
+  const int lb = run_bfs_finalize(g, center, dist, &status);
+  if (lb < 0) {
+    g->acnt_dirty = true;
+    return status;
+  }
+  l += lb;
+  if (want_cut)
+    l += launch_cut(g->cut, center, g->d_hot, g->n_hot, g->d_hot_center, &g->d_ctl->cut,
+                    g->num_sms, s);
+  CUDA_TRY(cudaMemcpyAsync(hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g->acnt_dirty = true;
+    return fail(LDD_ERR_CUDA, "%s", cudaGetErrorString(e));
+  }
+  *launches += l;
+  return LDD_OK;
+}
+
+int ensure_batch_headers(ldd_graph* g, int k) {
+  if (g->h_bhdr_cap >= k) return LDD_OK;
+  if (g->h_bhdr) cudaFreeHost(g->h_bhdr);
+  g->h_bhdr = nullptr;
+  g->h_bhdr_cap = 0;
+  if (cudaMallocHost(&g->h_bhdr, (size_t)k * sizeof(Header)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "pinned host allocation of %d headers failed", k);
+  }
+  g->h_bhdr_cap = k;
+  return LDD_OK;
+}
+
 // Streams and staging of ldd_decompose_batch, created on first use.
 int setup_batch(ldd_graph* g) {
   if (g->batch_arena) return LDD_OK;
@@ -1295,6 +1350,7 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
   if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
   int rc = setup_batch(g);
   if (rc != LDD_OK) return rc;
+  if ((rc = ensure_batch_headers(g, k)) != LDD_OK) return rc;
   const size_t n = (size_t)g->n, slot_bytes = align_up(8 * n, 256);
   double* d_in[2] = {(double*)g->batch_arena,
                      (double*)((char*)g->batch_arena + slot_bytes)};
@@ -1335,11 +1391,9 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
     if (!dev_c || !dev_d) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_out[j], 0));
     int* center = dev_c ? out_center[i] : d_c[j];
     int* dist = dev_d ? out_dist[i] : d_d[j];
-    int l = 0;
-    if ((rc = decompose_on_device(g, dev_in ? shifts[i] : d_in[j], center, dist, &l)) != LDD_OK)
+    if ((rc = enqueue_pipelined(g, dev_in ? shifts[i] : d_in[j], center, dist, out_cut != nullptr,
+                                g->h_bhdr + (size_t)i * sizeof(Header), &launches)) != LDD_OK)
       return drain(rc);
-    launches += l;
-    if (out_cut && (rc = cut_on_device(g, center, &out_cut[i])) != LDD_OK) return drain(rc);
     CUDA_TRY(cudaEventRecord(g->ev_used[j], s));
     if (!dev_c || !dev_d) {  // download overlaps decomposition i + 1
       CUDA_TRY(cudaStreamWaitEvent(g->copy_out, g->ev_used[j], 0));
@@ -1352,10 +1406,41 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
   }
   CUDA_TRY(cudaStreamSynchronize(g->copy_out));
   CUDA_TRY(cudaStreamSynchronize(s));
+  // headers in order: the first hard error is the call's status; a fast rank
+  // path that asked for the exact path (or a larger start-bucket table) is
+  // redone alone on the regular path, which handles both
+  for (int i = 0; i < k; ++i) {
+    Header h;
+    memcpy(&h, g->h_bhdr + (size_t)i * sizeof(Header), sizeof(h));
+    const u32 retry = kErrRankRetry | kErrBucketCap;
+    if (h.err & ~retry) return header_error(h.err);
+    if (h.err == 0) {
+      header_stats(g, h, false);
+      if (out_cut) out_cut[i] = (int64_t)h.cut;
+      continue;
+    }
+    const bool dev_in = is_device_ptr(shifts[i]);
+    const bool dev_c = is_device_ptr(out_center[i]), dev_d = is_device_ptr(out_dist[i]);
+    if (!dev_in)
+      CUDA_TRY(cudaMemcpyAsync(d_in[0], shifts[i], n * 8, cudaMemcpyHostToDevice, s));
+    int* center = dev_c ? out_center[i] : d_c[0];
+    int* dist = dev_d ? out_dist[i] : d_d[0];
+    int l = 0;
+    if ((rc = decompose_on_device(g, dev_in ? shifts[i] : d_in[0], center, dist, &l)) != LDD_OK)
+      return drain(rc);
+    launches += l;
+    if (out_cut && (rc = cut_on_device(g, center, &out_cut[i])) != LDD_OK) return drain(rc);
+    if (!dev_c)
+      CUDA_TRY(cudaMemcpyAsync(out_center[i], center, n * 4, cudaMemcpyDeviceToHost, s));
+    if (!dev_d) CUDA_TRY(cudaMemcpyAsync(out_dist[i], dist, n * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
   g->stats.launches = launches;
   g->stats.ms_h2d = -1.f;  // overlapped: not attributable
   g->stats.ms_d2h = -1.f;
   g->stats.ms_total = -1.f;
+  g->stats.ms_rank = g->stats.ms_bfs = g->stats.ms_finalize = g->stats.ms_cut = -1.f;
+  g->stats.replayed = 0;
   return LDD_OK;
 }
 

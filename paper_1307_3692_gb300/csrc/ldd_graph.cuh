@@ -104,6 +104,8 @@ struct ldd_graph {
   u32 epoch = 0;
   // host side
   unsigned char* h_hdr = nullptr;  // pinned copy of the control header
+  unsigned char* h_bhdr = nullptr;  // pinned headers of a pipelined batch, one per decomposition
+  int h_bhdr_cap = 0;
   int bfs_grid = 0;
   int bfs_per_sm = 0;
   u32 spin_limit = 0;

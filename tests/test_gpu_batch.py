@@ -56,23 +56,36 @@ def test_batch_matches_single_calls_and_oracle(ldd, cuda):
     g.close()
 
 
-def test_batch_with_fallback_items(ldd, cuda):
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_batch_with_fallback_items(ldd, cuda, where):
     """Items that need the exact rank path or a larger start-bucket table
-    inside a pipelined batch."""
+    inside a pipelined batch: they are redone alone after the others, and the
+    items queued behind them (which start from the floor counts the failed
+    item left) are still exact."""
     G = gen.grid2d(40, 30)
     rng = np.random.default_rng(9)
     crowded = rng.random(G.n) * 2.0 ** -33 + rng.integers(0, 3, G.n)  # exact path
     huge = gen.shifts(G.n, 0.1, 3)
     huge[7] = 5000.5                                                    # A + 2 > n + 2
     normal = gen.shifts(G.n, 0.1, 4)
-    items = [normal, crowded, huge, normal]
-    cen = [np.empty(G.n, np.int32) for _ in items]
-    dis = [np.empty(G.n, np.int32) for _ in items]
+    other = gen.shifts(G.n, 0.3, 5)
+    items = [normal, crowded, other, crowded, huge, normal, other]
+    betas = [0.1, 0.1, 0.3, 0.1, 0.1, 0.1, 0.3]
     g = ldd.LddGraph(G.row_ptr, G.col)
-    cuts = g.decompose_batch([0.1] * 4, items, cen, dis)
+    if where == "host":
+        sh = items
+        cen = [np.empty(G.n, np.int32) for _ in items]
+        dis = [np.empty(G.n, np.int32) for _ in items]
+    else:
+        sh = [torch.from_numpy(x).to(cuda) for x in items]
+        cen = [torch.empty(G.n, dtype=torch.int32, device=cuda) for _ in items]
+        dis = [torch.empty(G.n, dtype=torch.int32, device=cuda) for _ in items]
+    cuts = g.decompose_batch(betas, sh, cen, dis)
     for i, shifts in enumerate(items):
         oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts)
-        assert np.array_equal(cen[i], oc) and np.array_equal(dis[i], od), f"item {i}"
+        c = cen[i] if where == "host" else cen[i].cpu().numpy()
+        d = dis[i] if where == "host" else dis[i].cpu().numpy()
+        assert np.array_equal(c, oc) and np.array_equal(d, od), f"item {i}"
         assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
     g.close()
 
