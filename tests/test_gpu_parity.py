@@ -284,8 +284,8 @@ def test_component_labels_deep_trees(ldd, cuda):
                                         ("half_ties", 1), ("short_equal_runs", 0)])
 def test_fraction_rank_exact_fallback(ldd, cuda, kind, exact):
     """Fractions crowded into one bucket (equal in their top 32 bits but not
-    below, all below 2^-32, or only two distinct values) overflow the bucket
-    slots and force the exact 64-bit rank path; short runs of exactly equal
+    below, all below 2^-32, or only two distinct values) fill one bucket beyond its
+    cap and force the exact 64-bit rank path; short runs of exactly equal
     fractions stay on the bucket path, their ties resolved by id."""
     rng = np.random.default_rng(3)
     G = gen.grid2d(40, 30)
