@@ -759,13 +759,15 @@ int cut_on_device(ldd_graph* g, const int* d_center, int64_t* out_cut) {
 }
 
 // One fast-path decomposition of a plain graph queued on g->stream with no
-// host synchronisation: control block cleared, rank, BFS, finalize into
-// center/dist, the cut count when want_cut (it accumulates in the control
-// header), and the header copied to the pinned block hdr.  A fast rank path
-// that asks for the exact path leaves the floor counts cleared and skips the
-// rest, so the decompositions queued behind it run as usual.
-int enqueue_pipelined(ldd_graph* g, const double* d_shift, int* center, int* dist, bool want_cut,
-                      unsigned char* hdr, int* launches) {
+// host synchronisation, in two parts.  enqueue_pipelined: control block
+// cleared, rank, BFS, finalize into center/dist; the shifts are no longer
+// needed and the labels are final once it has run.  enqueue_cut_header: the
+// cut count when want_cut (it accumulates in the control header) and the
+// header copied to the pinned block hdr.  A fast rank path that asks for the
+// exact path leaves the floor counts cleared and skips the rest, so the
+// decompositions queued behind it run as usual.
+int enqueue_pipelined(ldd_graph* g, const double* d_shift, int* center, int* dist,
+                      int* launches) {
   cudaStream_t s = g->stream;
   if (g->epoch > 0xfffff000u) {  // status tags would wrap: clear and restart
     CUDA_TRY(cudaMemsetAsync(g->d_status, 0, g->status_bytes, s));
@@ -785,17 +787,22 @@ int enqueue_pipelined(ldd_graph* g, const double* d_shift, int* center, int* dis
     g->acnt_dirty = true;
     return status;
   }
-  l += lb;
+  *launches += l + lb;
+  return LDD_OK;
+}
+
+int enqueue_cut_header(ldd_graph* g, const int* center, bool want_cut, unsigned char* hdr,
+                       int* launches) {
+  cudaStream_t s = g->stream;
   if (want_cut)
-    l += launch_cut(g->cut, center, g->d_hot, g->n_hot, g->d_hot_center, &g->d_ctl->cut,
-                    g->num_sms, s);
+    *launches += launch_cut(g->cut, center, g->d_hot, g->n_hot, g->d_hot_center,
+                            &g->d_ctl->cut, g->num_sms, s);
   CUDA_TRY(cudaMemcpyAsync(hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g->acnt_dirty = true;
     return fail(LDD_ERR_CUDA, "%s", cudaGetErrorString(e));
   }
-  *launches += l;
   return LDD_OK;
 }
 
@@ -1391,11 +1398,11 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
     if (!dev_c || !dev_d) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_out[j], 0));
     int* center = dev_c ? out_center[i] : d_c[j];
     int* dist = dev_d ? out_dist[i] : d_d[j];
-    if ((rc = enqueue_pipelined(g, dev_in ? shifts[i] : d_in[j], center, dist, out_cut != nullptr,
-                                g->h_bhdr + (size_t)i * sizeof(Header), &launches)) != LDD_OK)
+    if ((rc = enqueue_pipelined(g, dev_in ? shifts[i] : d_in[j], center, dist, &launches)) !=
+        LDD_OK)
       return drain(rc);
     CUDA_TRY(cudaEventRecord(g->ev_used[j], s));
-    if (!dev_c || !dev_d) {  // download overlaps decomposition i + 1
+    if (!dev_c || !dev_d) {  // download overlaps the cut count and decomposition i + 1
       CUDA_TRY(cudaStreamWaitEvent(g->copy_out, g->ev_used[j], 0));
       if (!dev_c)
         CUDA_TRY(cudaMemcpyAsync(out_center[i], center, n * 4, cudaMemcpyDeviceToHost, g->copy_out));
@@ -1403,6 +1410,9 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
         CUDA_TRY(cudaMemcpyAsync(out_dist[i], dist, n * 4, cudaMemcpyDeviceToHost, g->copy_out));
       CUDA_TRY(cudaEventRecord(g->ev_out[j], g->copy_out));
     }
+    if ((rc = enqueue_cut_header(g, center, out_cut != nullptr,
+                                 g->h_bhdr + (size_t)i * sizeof(Header), &launches)) != LDD_OK)
+      return drain(rc);
   }
   CUDA_TRY(cudaStreamSynchronize(g->copy_out));
   CUDA_TRY(cudaStreamSynchronize(s));
