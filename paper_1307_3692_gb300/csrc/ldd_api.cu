@@ -101,6 +101,8 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->batch_arena);
   if (g->h_hdr) cudaFreeHost(g->h_hdr);
   if (g->h_bhdr) cudaFreeHost(g->h_bhdr);
+  if (g->h_bcut) cudaFreeHost(g->h_bcut);
+  cudaFree(g->d_bcut);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i) {
@@ -110,6 +112,9 @@ int free_graph_memory(ldd_graph* g) {
   }
   if (g->copy_in) cudaStreamDestroy(g->copy_in);
   if (g->copy_out) cudaStreamDestroy(g->copy_out);
+  if (g->cut_stream) cudaStreamDestroy(g->cut_stream);
+  for (int i = 0; i < 2; ++i)
+    if (g->ev_cut[i]) cudaEventDestroy(g->ev_cut[i]);
   for (auto& x : g->gexec)
     if (x) cudaGraphExecDestroy(x);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
@@ -759,15 +764,13 @@ int cut_on_device(ldd_graph* g, const int* d_center, int64_t* out_cut) {
 }
 
 // One fast-path decomposition of a plain graph queued on g->stream with no
-// host synchronisation, in two parts.  enqueue_pipelined: control block
-// cleared, rank, BFS, finalize into center/dist; the shifts are no longer
-// needed and the labels are final once it has run.  enqueue_cut_header: the
-// cut count when want_cut (it accumulates in the control header) and the
-// header copied to the pinned block hdr.  A fast rank path that asks for the
-// exact path leaves the floor counts cleared and skips the rest, so the
-// decompositions queued behind it run as usual.
-int enqueue_pipelined(ldd_graph* g, const double* d_shift, int* center, int* dist,
-                      int* launches) {
+// host synchronisation, in two parts.  enqueue_rank: control block cleared,
+// rank and start buckets.  enqueue_bfs_finalize: BFS and finalize into
+// center/dist; the shifts are no longer needed and the labels are final once
+// it has run.  A fast rank path that asks for the exact path leaves the floor
+// counts cleared and skips the rest, so the decompositions queued behind it
+// run as usual.
+int enqueue_rank(ldd_graph* g, const double* d_shift, int* launches) {
   cudaStream_t s = g->stream;
   if (g->epoch > 0xfffff000u) {  // status tags would wrap: clear and restart
     CUDA_TRY(cudaMemsetAsync(g->d_status, 0, g->status_bytes, s));
@@ -780,40 +783,41 @@ int enqueue_pipelined(ldd_graph* g, const double* d_shift, int* center, int* dis
   }
   RankBufs rb = rank_bufs(g, d_shift);
   rb.acnt_dirty = false;
-  int l = launch_rank_and_buckets(rb, false, s);
+  *launches += launch_rank_and_buckets(rb, false, s);
+  return LDD_OK;
+}
+
+int enqueue_bfs_finalize(ldd_graph* g, int* center, int* dist, int* launches) {
   int status = LDD_OK;
   const int lb = run_bfs_finalize(g, center, dist, &status);
   if (lb < 0) {
     g->acnt_dirty = true;
     return status;
   }
-  *launches += l + lb;
-  return LDD_OK;
-}
-
-int enqueue_cut_header(ldd_graph* g, const int* center, bool want_cut, unsigned char* hdr,
-                       int* launches) {
-  cudaStream_t s = g->stream;
-  if (want_cut)
-    *launches += launch_cut(g->cut, center, g->d_hot, g->n_hot, g->d_hot_center,
-                            &g->d_ctl->cut, g->num_sms, s);
-  CUDA_TRY(cudaMemcpyAsync(hdr, g->d_ctl, sizeof(Header), cudaMemcpyDeviceToHost, s));
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g->acnt_dirty = true;
     return fail(LDD_ERR_CUDA, "%s", cudaGetErrorString(e));
   }
+  *launches += lb;
   return LDD_OK;
 }
 
+// Pinned headers and the device / pinned cut counts of a batch of k.
 int ensure_batch_headers(ldd_graph* g, int k) {
   if (g->h_bhdr_cap >= k) return LDD_OK;
   if (g->h_bhdr) cudaFreeHost(g->h_bhdr);
+  if (g->h_bcut) cudaFreeHost(g->h_bcut);
+  cudaFree(g->d_bcut);
   g->h_bhdr = nullptr;
+  g->h_bcut = nullptr;
+  g->d_bcut = nullptr;
   g->h_bhdr_cap = 0;
-  if (cudaMallocHost(&g->h_bhdr, (size_t)k * sizeof(Header)) != cudaSuccess) {
+  if (cudaMallocHost(&g->h_bhdr, (size_t)k * sizeof(Header)) != cudaSuccess ||
+      cudaMallocHost(&g->h_bcut, (size_t)k * sizeof(u64)) != cudaSuccess ||
+      cudaMalloc(&g->d_bcut, (size_t)k * sizeof(u64)) != cudaSuccess) {
     cudaGetLastError();
-    return fail(LDD_ERR_OOM, "pinned host allocation of %d headers failed", k);
+    return fail(LDD_ERR_OOM, "batch state for %d decompositions: allocation failed", k);
   }
   g->h_bhdr_cap = k;
   return LDD_OK;
@@ -824,14 +828,16 @@ int setup_batch(ldd_graph* g) {
   if (g->batch_arena) return LDD_OK;
   const size_t n = (size_t)g->n;
   if (cudaStreamCreateWithFlags(&g->copy_in, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&g->copy_out, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&g->copy_out, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&g->cut_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return fail(LDD_ERR_CUDA, "cudaStreamCreate for the batch pipeline failed");
   }
   for (int i = 0; i < 2; ++i)
     if (cudaEventCreateWithFlags(&g->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_used[i], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g->ev_out[i], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&g->ev_out[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_cut[i], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return fail(LDD_ERR_CUDA, "cudaEventCreate for the batch pipeline failed");
     }
@@ -1383,9 +1389,18 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
   auto drain = [&](int status) {
     cudaStreamSynchronize(g->copy_in);
     cudaStreamSynchronize(g->copy_out);
+    cudaStreamSynchronize(g->cut_stream);
     cudaStreamSynchronize(s);
     return status;
   };
+  // cut counts run on their own stream, each overlapping the next
+  // decomposition's rank; a round loop waits for the previous cut count, so
+  // that it runs alone and the output slot that cut count reads is free
+  const bool cuts = out_cut != nullptr;
+  if (cuts) {
+    CUDA_TRY(cudaMemsetAsync(g->d_bcut, 0, (size_t)k * sizeof(u64), s));
+    for (int j = 0; j < 2; ++j) CUDA_TRY(cudaEventRecord(g->ev_cut[j], s));
+  }
   record(g, 0);
   if ((rc = upload(0)) != LDD_OK) return drain(rc);
   int launches = 0;
@@ -1398,9 +1413,12 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
     if (!dev_c || !dev_d) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_out[j], 0));
     int* center = dev_c ? out_center[i] : d_c[j];
     int* dist = dev_d ? out_dist[i] : d_d[j];
-    if ((rc = enqueue_pipelined(g, dev_in ? shifts[i] : d_in[j], center, dist, &launches)) !=
-        LDD_OK)
+    if ((rc = enqueue_rank(g, dev_in ? shifts[i] : d_in[j], &launches)) != LDD_OK)
       return drain(rc);
+    if (cuts && i > 0) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_cut[(i - 1) & 1], 0));
+    if ((rc = enqueue_bfs_finalize(g, center, dist, &launches)) != LDD_OK) return drain(rc);
+    CUDA_TRY(cudaMemcpyAsync(g->h_bhdr + (size_t)i * sizeof(Header), g->d_ctl, sizeof(Header),
+                             cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaEventRecord(g->ev_used[j], s));
     if (!dev_c || !dev_d) {  // download overlaps the cut count and decomposition i + 1
       CUDA_TRY(cudaStreamWaitEvent(g->copy_out, g->ev_used[j], 0));
@@ -1410,10 +1428,18 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
         CUDA_TRY(cudaMemcpyAsync(out_dist[i], dist, n * 4, cudaMemcpyDeviceToHost, g->copy_out));
       CUDA_TRY(cudaEventRecord(g->ev_out[j], g->copy_out));
     }
-    if ((rc = enqueue_cut_header(g, center, out_cut != nullptr,
-                                 g->h_bhdr + (size_t)i * sizeof(Header), &launches)) != LDD_OK)
-      return drain(rc);
+    if (cuts) {
+      CUDA_TRY(cudaStreamWaitEvent(g->cut_stream, g->ev_used[j], 0));
+      launches += launch_cut(g->cut, center, g->d_hot, g->n_hot, g->d_hot_center, g->d_bcut + i,
+                             g->num_sms, g->cut_stream);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaEventRecord(g->ev_cut[j], g->cut_stream));
+    }
   }
+  if (cuts)
+    CUDA_TRY(cudaMemcpyAsync(g->h_bcut, g->d_bcut, (size_t)k * sizeof(u64), cudaMemcpyDeviceToHost,
+                             g->cut_stream));
+  CUDA_TRY(cudaStreamSynchronize(g->cut_stream));
   CUDA_TRY(cudaStreamSynchronize(g->copy_out));
   CUDA_TRY(cudaStreamSynchronize(s));
   // headers in order: the first hard error is the call's status; a fast rank
@@ -1426,7 +1452,7 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
     if (h.err & ~retry) return header_error(h.err);
     if (h.err == 0) {
       header_stats(g, h, false);
-      if (out_cut) out_cut[i] = (int64_t)h.cut;
+      if (out_cut) out_cut[i] = (int64_t)g->h_bcut[i];
       continue;
     }
     const bool dev_in = is_device_ptr(shifts[i]);

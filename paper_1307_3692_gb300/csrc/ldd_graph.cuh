@@ -117,7 +117,10 @@ struct ldd_graph {
   cudaEvent_t ev[8] = {};
   // pipelined batches (ldd_decompose_batch), set up on first use
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
-  cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_out[2] = {};
+  cudaStream_t cut_stream = nullptr;  // cut counts, overlapping the next decomposition's rank
+  cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_out[2] = {}, ev_cut[2] = {};
+  u64* d_bcut = nullptr;              // [h_bhdr_cap] cut counts of a batch (device)
+  u64* h_bcut = nullptr;              // [h_bhdr_cap] their pinned copy
   void* batch_arena = nullptr;  // two shift slots (8n each) and two output slots (8n each)
   // disjoint unions (ldd_create_union): member offsets and caller-layout staging
   struct Union {
