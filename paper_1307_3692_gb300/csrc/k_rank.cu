@@ -130,7 +130,9 @@ __device__ __forceinline__ u32 bucket_of(u64 fb, int B) {
   return (~code) >> (32 - B);
 }
 
-// Pass 1, the only read of the shifts: split and validate every shift, and
+// Pass 1, the only read of the shifts (vertices u0 .. n-1 per launch; one
+// launch per chunk while the shifts are still arriving): split and validate
+// every shift, and
 // drop a record into the next free slot of u's bucket unless u is alone in
 // its component.  Record: x = bits of f_u; y = (a_u << 32) | u, with bit 31
 // set when the BFS does not handle u (u < 2^30).  Vertices the BFS handles are
@@ -158,8 +160,9 @@ __device__ __forceinline__ void count_floor(int a, bool take, u32* sh, u32* acnt
 
 __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta,
                                                 const u32* __restrict__ solo,
-                                                const u32* __restrict__ excl, u32 n, int B,
-                                                u32* __restrict__ cnt, ulonglong2* __restrict__ slots,
+                                                const u32* __restrict__ excl, u32 u0, u32 n,
+                                                int B, u32* __restrict__ cnt,
+                                                ulonglong2* __restrict__ slots,
                                                 u32* acnt, u32 cap,
                                                 const u32* __restrict__ wmem,
                                                 const int* __restrict__ lift, Control* ctl) {
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta
   u32 err = 0;
   const u32 stride = gridDim.x * blockDim.x;
   // warp-uniform trip count: the histogram adds are warp collectives
-  for (u32 wb = blockIdx.x * blockDim.x + (tid & ~31u); wb < n; wb += stride * kPlaceIpt) {
+  for (u32 wb = u0 + blockIdx.x * blockDim.x + (tid & ~31u); wb < n; wb += stride * kPlaceIpt) {
     double d[kPlaceIpt];
 #pragma unroll
     for (int k = 0; k < kPlaceIpt; ++k) {
@@ -981,7 +984,8 @@ size_t fraction_slot_bytes(u32 n) {
   return ((size_t)1 << fraction_bucket_bits(n)) * kSlotCap * sizeof(ulonglong2);
 }
 
-int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
+int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
+                            const ShiftChunks* chunks) {
   const u32 n = r.n;
   Control* ctl = r.ctl;
   const u32 gs = grid_stride_blocks(n, r.num_sms);
@@ -996,10 +1000,22 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
     ulonglong2* slots = reinterpret_cast<ulonglong2*>(r.slots);
     if (r.acnt_dirty) cudaMemsetAsync(r.acnt, 0, (size_t)r.bptr_cap * 4, s);
     cudaMemsetAsync(cnt, 0, (size_t)(nbkt + 1) * 4, s);
-    const u32 place_grid = (u32)min((long long)(n + 256 * kPlaceIpt - 1) / (256 * kPlaceIpt),
-                                    (long long)r.num_sms * bplace_blocks_per_sm());
-    k_bplace<<<max(place_grid, 1u), 256, 0, s>>>(
-        r.shift, r.solo, r.excl, n, (int)B, cnt, slots, r.acnt, r.bptr_cap, r.wmem, r.lift, ctl);
+    const int nchunk = chunks ? chunks->n : 0;
+    u32 lo = 0;
+    for (int c = 0; c <= nchunk; ++c) {
+      // chunk c is vertices [lo, hi), complete once its event has fired
+      const u32 hi = c < nchunk ? std::min(chunks->end[c], n) : n;
+      if (c < nchunk) cudaStreamWaitEvent(s, chunks->ev[c], 0);
+      if (hi <= lo) continue;
+      const u32 m = hi - lo;
+      const u32 place_grid = (u32)min((long long)(m + 256 * kPlaceIpt - 1) / (256 * kPlaceIpt),
+                                      (long long)r.num_sms * bplace_blocks_per_sm());
+      k_bplace<<<max(place_grid, 1u), 256, 0, s>>>(r.shift, r.solo, r.excl, lo, hi, (int)B, cnt,
+                                                   slots, r.acnt, r.bptr_cap, r.wmem, r.lift,
+                                                   ctl);
+      ++launches;
+      lo = hi;
+    }
     k_scan_excl<<<(nbkt + 1 + kScanTile - 1) / kScanTile, kScanThreads, 0, s>>>(
         cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, nullptr, 0,
         ctl);
@@ -1011,11 +1027,13 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s) {
     k_bsort<<<(u32)min((long long)ntiles, (long long)r.num_sms * 3), 256, sizeof(BsortSmem), s>>>(
         cnt, nbkt, slots, n, r.order, r.key, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0),
         &ctl->tile_ctr[kFracDigits + kRoundDigits - 1], ctl);
-    return launches + 4;
+    return launches + 3;
   }
   // exact path: stable LSD radix sort of all fractions, then keys and the
   // start-round counting sort (groups in any order inside)
   u32* rank = reinterpret_cast<u32*>(r.k1) + n;  // k1 holds 2 max(n, 64) 32-bit words
+  if (chunks)
+    for (int c = 0; c < chunks->n; ++c) cudaStreamWaitEvent(s, chunks->ev[c], 0);
   allow_sort_smem();
   k_split64<<<gs, 256, 0, s>>>(r.shift, n, r.a, r.k0, r.v0, r.wmem, r.lift, ctl);
   k_scan_digits<<<1, 256, 0, s>>>(&ctl->hist_f[0][0], &ctl->off_f[0][0], &ctl->mask_f,

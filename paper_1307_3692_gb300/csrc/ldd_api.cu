@@ -115,6 +115,8 @@ int free_graph_memory(ldd_graph* g) {
   if (g->cut_stream) cudaStreamDestroy(g->cut_stream);
   for (int i = 0; i < 2; ++i)
     if (g->ev_cut[i]) cudaEventDestroy(g->ev_cut[i]);
+  for (auto& e : g->ev_chunk)
+    if (e) cudaEventDestroy(e);
   for (auto& x : g->gexec)
     if (x) cudaGraphExecDestroy(x);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
@@ -770,7 +772,8 @@ int cut_on_device(ldd_graph* g, const int* d_center, int64_t* out_cut) {
 // it has run.  A fast rank path that asks for the exact path leaves the floor
 // counts cleared and skips the rest, so the decompositions queued behind it
 // run as usual.
-int enqueue_rank(ldd_graph* g, const double* d_shift, int* launches) {
+int enqueue_rank(ldd_graph* g, const double* d_shift, int* launches,
+                 const ShiftChunks* chunks = nullptr) {
   cudaStream_t s = g->stream;
   if (g->epoch > 0xfffff000u) {  // status tags would wrap: clear and restart
     CUDA_TRY(cudaMemsetAsync(g->d_status, 0, g->status_bytes, s));
@@ -783,7 +786,7 @@ int enqueue_rank(ldd_graph* g, const double* d_shift, int* launches) {
   }
   RankBufs rb = rank_bufs(g, d_shift);
   rb.acnt_dirty = false;
-  *launches += launch_rank_and_buckets(rb, false, s);
+  *launches += launch_rank_and_buckets(rb, false, s, chunks);
   return LDD_OK;
 }
 
@@ -838,6 +841,11 @@ int setup_batch(ldd_graph* g) {
         cudaEventCreateWithFlags(&g->ev_used[i], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_out[i], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_cut[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LDD_ERR_CUDA, "cudaEventCreate for the batch pipeline failed");
+    }
+  for (auto& e : g->ev_chunk)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return fail(LDD_ERR_CUDA, "cudaEventCreate for the batch pipeline failed");
     }
@@ -1373,11 +1381,36 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
   cudaStream_t s = g->stream;
   // slot j's shift buffer is free once the decomposition that read it is done
   // (ev_used) and its output buffers once their download is done (ev_out)
+  // The first host shift vector nothing can overlap goes up in pieces, and the
+  // rank's first pass starts on each piece as it lands.
+  constexpr int kC = ldd_graph::kUploadChunks;
+  u32 chunk_end[kC];
+  ShiftChunks first;
+  const bool chunk_first = !is_device_ptr(shifts[0]) && n >= ((size_t)1 << 20);
+  if (chunk_first) {
+    for (int c = 0; c < kC; ++c)
+      chunk_end[c] = c + 1 < kC ? (u32)(((n * (c + 1) / kC) + 31) & ~(size_t)31) : (u32)n;
+    first.n = kC;
+    first.end = chunk_end;
+    first.ev = g->ev_chunk;
+  }
   auto upload = [&](int i) -> int {
     if (is_device_ptr(shifts[i])) return LDD_OK;
     const int j = i & 1;
     CUDA_TRY(cudaStreamWaitEvent(g->copy_in, g->ev_used[j], 0));
-    CUDA_TRY(cudaMemcpyAsync(d_in[j], shifts[i], n * 8, cudaMemcpyHostToDevice, g->copy_in));
+    if (i == 0 && chunk_first) {
+      size_t lo = 0;
+      for (int c = 0; c < kC; ++c) {
+        const size_t hi = std::min<size_t>(chunk_end[c], n);
+        if (hi > lo)
+          CUDA_TRY(cudaMemcpyAsync(d_in[j] + lo, shifts[i] + lo, (hi - lo) * 8,
+                                   cudaMemcpyHostToDevice, g->copy_in));
+        CUDA_TRY(cudaEventRecord(g->ev_chunk[c], g->copy_in));
+        lo = std::max(lo, hi);
+      }
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(d_in[j], shifts[i], n * 8, cudaMemcpyHostToDevice, g->copy_in));
+    }
     CUDA_TRY(cudaEventRecord(g->ev_in[j], g->copy_in));
     return LDD_OK;
   };
@@ -1409,11 +1442,13 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
     if (i + 1 < k && (rc = upload(i + 1)) != LDD_OK) return drain(rc);  // overlaps decomposition i
     const bool dev_in = is_device_ptr(shifts[i]);
     const bool dev_c = is_device_ptr(out_center[i]), dev_d = is_device_ptr(out_dist[i]);
-    if (!dev_in) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_in[j], 0));
+    const bool pieces = i == 0 && chunk_first;  // the rank waits for each piece itself
+    if (!dev_in && !pieces) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_in[j], 0));
     if (!dev_c || !dev_d) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_out[j], 0));
     int* center = dev_c ? out_center[i] : d_c[j];
     int* dist = dev_d ? out_dist[i] : d_d[j];
-    if ((rc = enqueue_rank(g, dev_in ? shifts[i] : d_in[j], &launches)) != LDD_OK)
+    if ((rc = enqueue_rank(g, dev_in ? shifts[i] : d_in[j], &launches,
+                           pieces ? &first : nullptr)) != LDD_OK)
       return drain(rc);
     if (cuts && i > 0) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_cut[(i - 1) & 1], 0));
     if ((rc = enqueue_bfs_finalize(g, center, dist, &launches)) != LDD_OK) return drain(rc);

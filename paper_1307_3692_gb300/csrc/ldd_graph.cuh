@@ -119,6 +119,8 @@ struct ldd_graph {
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaStream_t cut_stream = nullptr;  // cut counts, overlapping the next decomposition's rank
   cudaEvent_t ev_in[2] = {}, ev_used[2] = {}, ev_out[2] = {}, ev_cut[2] = {};
+  static constexpr int kUploadChunks = 4;  // the first shift vector of a batch, uploaded in pieces
+  cudaEvent_t ev_chunk[kUploadChunks] = {};
   u64* d_bcut = nullptr;              // [h_bhdr_cap] cut counts of a batch (device)
   u64* h_bcut = nullptr;              // [h_bhdr_cap] their pinned copy
   void* batch_arena = nullptr;  // two shift slots (8n each) and two output slots (8n each)

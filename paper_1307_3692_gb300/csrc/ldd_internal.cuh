@@ -177,7 +177,15 @@ struct RankBufs {
 // not alone in their component (may set kErrRankRetry); true: exact 64-bit
 // LSD radix sort of all vertices.  The start buckets end in v0 (vertices) and
 // k0 viewed as 32-bit words (their rounds).
-int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s);
+// chunks (optional): the shifts are still arriving; chunk c is complete once
+// ev[c] has fired and covers the vertices up to end[c] (ascending).
+struct ShiftChunks {
+  int n = 0;
+  const u32* end = nullptr;
+  const cudaEvent_t* ev = nullptr;
+};
+int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
+                            const ShiftChunks* chunks = nullptr);
 // Ranked variant (Section 4's permutation in place of the fractional parts):
 // integer levels and a tie-break permutation given; no sort.  The same start
 // buckets and keys as the exact path.

@@ -110,3 +110,21 @@ def test_batch_stops_at_a_bad_item(ldd, cuda):
     assert g.decompose_batch([0.2], [good], cen[:1], dis[:1]) == [
         oracle.oracle_cut_edges(G.row_ptr, G.col, oc)]
     g.close()
+
+
+def test_batch_first_vector_uploaded_in_pieces(ldd, cuda):
+    """A host shift vector of at least 2^20 entries at the head of a batch goes up
+    in pieces, each ranked as it lands; every item must still equal the oracle."""
+    G = gen.grid2d(1024, 1024)
+    betas = [0.1, 0.3, 0.05]
+    items = [gen.shifts(G.n, b, 40 + i) for i, b in enumerate(betas)]
+    sh = [_pinned(x) for x in items]
+    cen = [_pinned(np.zeros(G.n, np.int32)) for _ in items]
+    dis = [_pinned(np.zeros(G.n, np.int32)) for _ in items]
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    cuts = g.decompose_batch(betas, sh, cen, dis)
+    for i, shifts in enumerate(items):
+        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts)
+        assert np.array_equal(cen[i].numpy(), oc) and np.array_equal(dis[i].numpy(), od), f"item {i}"
+        assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
+    g.close()
