@@ -17,9 +17,9 @@
 // 2^B about n / 16 so that buckets hold ~16 vertices.  One pass over the
 // shifts drops a 16-byte record (bits of f_u, a_u, u) into a free slot of its
 // bucket (kSlotCap slots each); an exclusive scan of the bucket counts gives
-// every bucket's first rank; one warp per bucket then ranks its members
-// exactly by (f descending, u ascending) with the full FP64 fractions and
-// writes order[] and the keys directly.  Vertices alone in their component
+// every bucket's first rank; tiles of buckets staged in shared memory then
+// rank every member exactly by (f descending, u ascending) with the full FP64
+// fractions, one thread per record, and write order[] and the keys directly.  Vertices alone in their component
 // are not ranked (their center is themselves).  A full bucket (crafted
 // shifts, e.g. all fractions equal) makes the host redo the rank with the
 // exact path: a stable LSD radix sort of the order-preserving bits of f

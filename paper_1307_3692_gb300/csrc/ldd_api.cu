@@ -588,7 +588,7 @@ int decompose_on_device(ldd_graph* g, const double* d_shift, int* center, int* d
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&h, g->h_hdr, sizeof(h));
-    if (!exact64 && !d_levels && h.err == 0) g->acnt_dirty = false;  // k_round_counts cleared them
+    if (!exact64 && !d_levels && h.err == 0) g->acnt_dirty = false;  // the scan cleared them
     const u32 retry = kErrRankRetry | kErrBucketCap;
     if (h.err == 0 || (h.err & ~retry) != 0) break;
     // A fraction bucket too full to rank in place (crafted shifts): every
