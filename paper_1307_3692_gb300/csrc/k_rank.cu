@@ -19,11 +19,12 @@
 // bucket (kSlotCap slots each); an exclusive scan of the bucket counts gives
 // every bucket's first rank; tiles of buckets staged in shared memory then
 // rank every member exactly by (f descending, u ascending) with the full FP64
-// fractions, one thread per record, and write order[] and the keys directly.  Vertices alone in their component
-// are not ranked (their center is themselves).  A full bucket (crafted
-// shifts, e.g. all fractions equal) makes the host redo the rank with the
-// exact path: a stable LSD radix sort of the order-preserving bits of f
-// (8 "onesweep" passes of 8 bits) over all vertices.
+// fractions, one thread per record, and write order[] and the keys directly.
+// Vertices alone in their component are not ranked (their center is
+// themselves).  A full bucket (crafted shifts, e.g. all fractions equal)
+// makes the host redo the rank with the exact path: a stable LSD radix sort
+// of the order-preserving bits of f (8 "onesweep" passes of 8 bits) over all
+// vertices.
 //
 // Batches (disjoint unions of member graphs, k_union.cu): every member's
 // floors are lifted by one integer, lift_s = max_t A_t - A_s, so that each
@@ -138,9 +139,11 @@ __device__ __forceinline__ u32 bucket_of(u64 fb, int B) {
 // set when the BFS does not handle u (u < 2^30).  Vertices the BFS handles are
 // also counted by their floor a_u into acnt (the start-round histogram in
 // reverse order; acnt is all zero on entry).  Each thread takes kPlaceIpt
-// vertices per step so that their loads and slot atomics overlap.  A full
-// bucket sends the host to the exact path.
-constexpr int kPlaceIpt = 4;
+// vertices per step so that their loads and slot atomics overlap: two below
+// 2^24 vertices, four above (the single graphs gain from more resident warps,
+// the larger unions from more loads in flight).  A full bucket sends the host
+// to the exact path.
+constexpr u32 kPlaceWideFrom = 1u << 24;
 
 // Adds one to the count of floor value a for every lane with take set, one
 // atomic per distinct a in the warp; floors below kRBins go to the CTA's
@@ -158,6 +161,7 @@ __device__ __forceinline__ void count_floor(int a, bool take, u32* sh, u32* acnt
   }
 }
 
+template <int kPlaceIpt>
 __global__ void __launch_bounds__(256) k_bplace(const double* __restrict__ delta,
                                                 const u32* __restrict__ solo,
                                                 const u32* __restrict__ excl, u32 u0, u32 n,
@@ -278,9 +282,10 @@ __device__ __forceinline__ void place_start_warp(bool take, u32 u, u32 R, u32 n,
 // fractions just short of a slot overflow) is ranked from global memory
 // instead, and with more than kSortRBins start rounds the reservations are
 // per warp.
-constexpr u32 kTileBuckets = 128;  // <= threads per CTA (one capacity check each); < 256
-constexpr u32 kTileRecs = 2560;    // < 2^16: spans are two 16-bit positions
+constexpr u32 kTileBuckets = 64;   // <= threads per CTA (one capacity check each); < 256
+constexpr u32 kTileRecs = 1280;    // < 2^16: spans are two 16-bit positions
 constexpr u32 kSortRBins = 2048;
+constexpr int kBsortPerSm = 5;     // resident CTAs per SM: 5 x 39 KB shared, <= 51 registers
 
 struct BsortSmem {
   u64 fx[kTileRecs];         // fraction bits of the tile's records, bucket order
@@ -293,11 +298,10 @@ struct BsortSmem {
   u32 tile;
 };
 
-__global__ void __launch_bounds__(256, 3) k_bsort(const u32* __restrict__ start, u32 nbkt,
-                                                  const ulonglong2* __restrict__ slots, u32 n,
-                                                  u32* __restrict__ order, u64* __restrict__ key,
-                                                  u32* rcur, u32* __restrict__ bv,
-                                                  u32* __restrict__ rk, u32* ticket, Control* ctl) {
+__global__ void __launch_bounds__(256, kBsortPerSm)
+    k_bsort(const u32* __restrict__ start, u32 nbkt, const ulonglong2* __restrict__ slots, u32 n,
+            u32* __restrict__ order, u64* __restrict__ key, u32* rcur, u32* __restrict__ bv,
+            u32* __restrict__ rk, u32* ticket, Control* ctl) {
   extern __shared__ __align__(16) unsigned char bsort_raw[];
   BsortSmem& sm = *reinterpret_cast<BsortSmem*>(bsort_raw);
   if (failed(ctl)) return;
@@ -941,18 +945,20 @@ void allow_bsort_smem() {
   }
 }
 
-// CTAs of k_bplace resident on one SM: its grid is one full wave.
-int bplace_blocks_per_sm() {
-  static int per_sm[64] = {};
+// CTAs of a k_bplace instance resident on one SM: its grid is one full wave.
+int bplace_blocks_per_sm(bool wide) {
+  static int per_sm[2][64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 4;
-  if (per_sm[dev] <= 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bplace, 256, 0) != cudaSuccess || b < 1)
+  int& b = per_sm[wide ? 1 : 0][dev];
+  if (b <= 0) {
+    const void* fn = wide ? (const void*)k_bplace<4> : (const void*)k_bplace<2>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, 256, 0) != cudaSuccess || b < 1) {
+      cudaGetLastError();
       b = 4;
-    per_sm[dev] = b;
+    }
   }
-  return per_sm[dev];
+  return b;
 }
 
 void allow_sort_smem() {
@@ -1008,11 +1014,19 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
       if (c < nchunk) cudaStreamWaitEvent(s, chunks->ev[c], 0);
       if (hi <= lo) continue;
       const u32 m = hi - lo;
-      const u32 place_grid = (u32)min((long long)(m + 256 * kPlaceIpt - 1) / (256 * kPlaceIpt),
-                                      (long long)r.num_sms * bplace_blocks_per_sm());
-      k_bplace<<<max(place_grid, 1u), 256, 0, s>>>(r.shift, r.solo, r.excl, lo, hi, (int)B, cnt,
-                                                   slots, r.acnt, r.bptr_cap, r.wmem, r.lift,
-                                                   ctl);
+      const bool wide = n >= kPlaceWideFrom;
+      const int ipt = wide ? 4 : 2;
+      const u32 place_grid =
+          (u32)min((long long)(m + 256 * ipt - 1) / (256 * ipt),
+                   (long long)r.num_sms * bplace_blocks_per_sm(wide));
+      if (wide)
+        k_bplace<4><<<max(place_grid, 1u), 256, 0, s>>>(r.shift, r.solo, r.excl, lo, hi, (int)B,
+                                                        cnt, slots, r.acnt, r.bptr_cap, r.wmem,
+                                                        r.lift, ctl);
+      else
+        k_bplace<2><<<max(place_grid, 1u), 256, 0, s>>>(r.shift, r.solo, r.excl, lo, hi, (int)B,
+                                                        cnt, slots, r.acnt, r.bptr_cap, r.wmem,
+                                                        r.lift, ctl);
       ++launches;
       lo = hi;
     }
@@ -1024,7 +1038,8 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
                                                  ctl);
     allow_bsort_smem();
     const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
-    k_bsort<<<(u32)min((long long)ntiles, (long long)r.num_sms * 3), 256, sizeof(BsortSmem), s>>>(
+    const u32 sort_grid = (u32)min((long long)ntiles, (long long)r.num_sms * kBsortPerSm);
+    k_bsort<<<sort_grid, 256, sizeof(BsortSmem), s>>>(
         cnt, nbkt, slots, n, r.order, r.key, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0),
         &ctl->tile_ctr[kFracDigits + kRoundDigits - 1], ctl);
     return launches + 3;
