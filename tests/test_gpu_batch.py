@@ -128,3 +128,22 @@ def test_batch_first_vector_uploaded_in_pieces(ldd, cuda):
         assert np.array_equal(cen[i].numpy(), oc) and np.array_equal(dis[i].numpy(), od), f"item {i}"
         assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
     g.close()
+
+
+def test_batch_first_vector_in_pieces_needs_the_exact_rank(ldd, cuda):
+    """The first host vector goes up in pieces; when its fractions are crowded
+    (exact rank path) it is redone alone after the others, from the host copy."""
+    G = gen.grid2d(1024, 1024)
+    rng = np.random.default_rng(12)
+    crowded = rng.random(G.n) * 2.0 ** -33 + rng.integers(0, 4, G.n)
+    items = [crowded, gen.shifts(G.n, 0.2, 13)]
+    sh = [_pinned(x) for x in items]
+    cen = [_pinned(np.zeros(G.n, np.int32)) for _ in items]
+    dis = [_pinned(np.zeros(G.n, np.int32)) for _ in items]
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    cuts = g.decompose_batch([0.1, 0.2], sh, cen, dis)
+    for i, shifts in enumerate(items):
+        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts)
+        assert np.array_equal(cen[i].numpy(), oc) and np.array_equal(dis[i].numpy(), od), f"item {i}"
+        assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
+    g.close()
