@@ -31,6 +31,12 @@ namespace {
 
 constexpr u32 kFull = 0xffffffffu;
 
+// Each thread takes kFinIpt vertices per step (coalesced across the warp) and
+// issues their loads level by level (own keys, then the centers, then the
+// centers' keys), so that the three dependent gathers of several vertices
+// are in flight together.
+constexpr int kFinIpt = 4;
+
 __global__ void __launch_bounds__(256) k_finalize(const u64* __restrict__ key,
                                                   const u32* __restrict__ order,
                                                   const u32* __restrict__ solo, u32 n,
@@ -38,17 +44,30 @@ __global__ void __launch_bounds__(256) k_finalize(const u64* __restrict__ key,
                                                   const u32* err) {
   if (*(volatile const u32*)err != 0u) return;  // outputs are not written after a failure
   const u32 stride = gridDim.x * blockDim.x;
-  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-    if ((__ldg(solo + (v >> 5)) >> (v & 31)) & 1u) {  // alone in its component: key unused
-      center[v] = (int)v;
-      dist[v] = 0;
-      continue;
+  for (u32 v0 = blockIdx.x * blockDim.x + threadIdx.x; v0 < n; v0 += stride * kFinIpt) {
+    u32 v[kFinIpt], c[kFinIpt];
+    bool live[kFinIpt], alone[kFinIpt];
+    u64 k[kFinIpt], kc[kFinIpt];
+#pragma unroll
+    for (int q = 0; q < kFinIpt; ++q) {
+      v[q] = v0 + (u32)q * stride;
+      live[q] = v[q] < n;
+      // alone in its component: the key is unused, the vertex is its own center
+      alone[q] = live[q] && ((__ldg(solo + (v[q] >> 5)) >> (v[q] & 31)) & 1u);
+      k[q] = (live[q] && !alone[q]) ? key[v[q]] : 0ull;
     }
-    const u64 k = key[v];
-    const u32 c = order[min((u32)k, n - 1)];
-    const u64 kc = key[c];
-    center[v] = (int)c;
-    dist[v] = (int)((u32)(k >> 32) - (u32)(kc >> 32));
+#pragma unroll
+    for (int q = 0; q < kFinIpt; ++q)
+      c[q] = (live[q] && !alone[q]) ? order[min((u32)k[q], n - 1)] : v[q];
+#pragma unroll
+    for (int q = 0; q < kFinIpt; ++q)
+      kc[q] = (live[q] && !alone[q]) ? key[c[q]] : k[q];
+#pragma unroll
+    for (int q = 0; q < kFinIpt; ++q)
+      if (live[q]) {
+        center[v[q]] = (int)c[q];
+        dist[v[q]] = alone[q] ? 0 : (int)((u32)(k[q] >> 32) - (u32)(kc[q] >> 32));
+      }
   }
 }
 
@@ -375,7 +394,8 @@ u32 grid_for(u32 n, int num_sms) {
 
 int launch_finalize(const u64* key, const u32* order, const u32* solo, u32 n, int* center,
                     int* dist, const u32* err, int num_sms, cudaStream_t s) {
-  k_finalize<<<grid_for(n, num_sms), 256, 0, s>>>(key, order, solo, n, center, dist, err);
+  k_finalize<<<grid_for((n + kFinIpt - 1) / kFinIpt, num_sms), 256, 0, s>>>(key, order, solo, n,
+                                                                         center, dist, err);
   return 1;
 }
 
