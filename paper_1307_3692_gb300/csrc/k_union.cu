@@ -166,24 +166,45 @@ __device__ __forceinline__ int floor_of(double d) {
 // warp's 32 consecutive union vertices belong to one member (members start on
 // 32-vertex boundaries) and share one excl word, so each warp step ends in
 // one atomicMax.
+// Members are padded to multiples of 32 vertices, so every 32-vertex chunk
+// of the union belongs to one member.  A warp takes kSpreadIpt consecutive
+// chunks at a time, finds the member of the first once and walks forward for
+// the others, and issues all their loads before any store.
+constexpr int kSpreadIpt = 4;
+
 __global__ void __launch_bounds__(256) k_union_spread(const double* __restrict__ in,
                                                       UnionOffsets off, u32 k,
                                                       const u32* __restrict__ excl,
                                                       double* __restrict__ out, int* amax) {
   const u32 N = off.v[k];
   const u32 lane = threadIdx.x & 31;
-  const u32 stride = gridDim.x * blockDim.x;
-  for (u32 wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < N; wb += stride) {
-    const u32 u = wb + lane;
-    const u32 s = member_of(off.v, k, wb);
-    const u32 v = u - off.v[s];
-    const u32 n = off.o[s + 1] - off.o[s];
-    const double d = v < n ? __ldcs(in + off.o[s] + v) : 0.0;
-    out[u] = d;
-    int a = ((__ldg(excl + (wb >> 5)) >> lane) & 1u) ? 0 : floor_of(d);
+  const u32 span = 32u * kSpreadIpt;
+  const u32 nwarps = gridDim.x * (blockDim.x / 32);
+  for (u32 wb0 = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * span; wb0 < N;
+       wb0 += nwarps * span) {
+    u32 sm[kSpreadIpt];
+    double d[kSpreadIpt];
+    u32 m = member_of(off.v, k, wb0);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
-    if (lane == 0 && a > 0) atomicMax(amax + s, a);
+    for (int q = 0; q < kSpreadIpt; ++q) {
+      const u32 wb = wb0 + (u32)q * 32;
+      if (wb < N)
+        while (__ldg(off.v + m + 1) <= wb) ++m;
+      sm[q] = m;
+      const u32 v = wb + lane - off.v[m];
+      const u32 n = off.o[m + 1] - off.o[m];
+      d[q] = (wb < N && v < n) ? __ldcs(in + off.o[m] + v) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kSpreadIpt; ++q) {
+      const u32 wb = wb0 + (u32)q * 32;
+      if (wb >= N) break;  // warp-uniform
+      out[wb + lane] = d[q];
+      int a = ((__ldg(excl + (wb >> 5)) >> lane) & 1u) ? 0 : floor_of(d[q]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+      if (lane == 0 && a > 0) atomicMax(amax + sm[q], a);
+    }
   }
 }
 
@@ -213,6 +234,12 @@ __global__ void __launch_bounds__(1024) k_union_lift(const int* __restrict__ ama
 // order[rank] (a union id of the same member); the member-local center id is
 // that minus voff_s, and the hop distance is the key's level minus the
 // center's own level.
+// A warp takes 32 x kUFinIpt consecutive caller-layout entries at a time,
+// finds the member of the first once and walks forward from it per entry;
+// the loads of a lane's entries go out level by level (own keys, centers,
+// centers' keys), so that their dependent gathers overlap.
+constexpr int kUFinIpt = 4;
+
 __global__ void __launch_bounds__(256) k_union_finalize(const u64* __restrict__ key,
                                                         const u32* __restrict__ order,
                                                         const u32* __restrict__ solo,
@@ -221,19 +248,39 @@ __global__ void __launch_bounds__(256) k_union_finalize(const u64* __restrict__ 
                                                         int* __restrict__ dist, const u32* err) {
   if (*(volatile const u32*)err != 0u) return;
   const u32 total = off.o[k], N = off.v[k];
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const u32 s = member_of(off.o, k, i);
-    const u32 v = i - off.o[s], u = off.v[s] + v;
-    if ((__ldg(solo + (u >> 5)) >> (u & 31)) & 1u) {
-      center[i] = (int)v;
-      dist[i] = 0;
-      continue;
+  const u32 lane = threadIdx.x & 31;
+  const u32 span = 32u * kUFinIpt;
+  const u32 nwarps = gridDim.x * (blockDim.x / 32);
+  for (u32 wbase = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * span; wbase < total;
+       wbase += nwarps * span) {
+    const u32 s0 = member_of(off.o, k, wbase);
+    u32 idx[kUFinIpt], sm[kUFinIpt], u[kUFinIpt], c[kUFinIpt];
+    bool live[kUFinIpt], alone[kUFinIpt];
+    u64 kv[kUFinIpt], kc[kUFinIpt];
+#pragma unroll
+    for (int q = 0; q < kUFinIpt; ++q) {
+      idx[q] = wbase + (u32)q * 32 + lane;
+      live[q] = idx[q] < total;
+      u32 m = s0;
+      if (live[q])
+        while (__ldg(off.o + m + 1) <= idx[q]) ++m;
+      sm[q] = m;
+      u[q] = live[q] ? off.v[m] + (idx[q] - off.o[m]) : 0u;
+      alone[q] = live[q] && ((__ldg(solo + (u[q] >> 5)) >> (u[q] & 31)) & 1u);
+      kv[q] = (live[q] && !alone[q]) ? key[u[q]] : 0ull;
     }
-    const u64 kv = key[u];
-    const u32 c = order[min((u32)kv, N - 1)];
-    const u64 kc = key[c];
-    center[i] = (int)(c - off.v[s]);
-    dist[i] = (int)((u32)(kv >> 32) - (u32)(kc >> 32));
+#pragma unroll
+    for (int q = 0; q < kUFinIpt; ++q)
+      c[q] = (live[q] && !alone[q]) ? order[min((u32)kv[q], N - 1)] : u[q];
+#pragma unroll
+    for (int q = 0; q < kUFinIpt; ++q)
+      kc[q] = (live[q] && !alone[q]) ? key[c[q]] : kv[q];
+#pragma unroll
+    for (int q = 0; q < kUFinIpt; ++q)
+      if (live[q]) {
+        center[idx[q]] = (int)(c[q] - off.v[sm[q]]);
+        dist[idx[q]] = alone[q] ? 0 : (int)((u32)(kv[q] >> 32) - (u32)(kc[q] >> 32));
+      }
   }
 }
 
@@ -256,7 +303,8 @@ int launch_union_spread(const double* in, const UnionOffsets& off, u32 k, u32 N,
                         const u32* excl, double* out, int* amax, int* lift, int num_sms,
                         cudaStream_t s) {
   cudaMemsetAsync(amax, 0, (size_t)k * sizeof(int), s);
-  k_union_spread<<<blocks_for(N, num_sms), 256, 0, s>>>(in, off, k, excl, out, amax);
+  k_union_spread<<<blocks_for((N + kSpreadIpt - 1) / kSpreadIpt, num_sms), 256, 0, s>>>(
+      in, off, k, excl, out, amax);
   k_union_lift<<<1, 1024, 0, s>>>(amax, k, lift);
   return 2;
 }
@@ -264,8 +312,8 @@ int launch_union_spread(const double* in, const UnionOffsets& off, u32 k, u32 N,
 int launch_union_finalize(const u64* key, const u32* order, const u32* solo,
                           const UnionOffsets& off, u32 k, u32 total, int* center, int* dist,
                           const u32* err, int num_sms, cudaStream_t s) {
-  k_union_finalize<<<blocks_for(total, num_sms), 256, 0, s>>>(key, order, solo, off, k, center,
-                                                              dist, err);
+  k_union_finalize<<<blocks_for((total + kUFinIpt - 1) / kUFinIpt, num_sms), 256, 0, s>>>(
+      key, order, solo, off, k, center, dist, err);
   return 1;
 }
 
