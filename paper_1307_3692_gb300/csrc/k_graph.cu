@@ -93,14 +93,28 @@ __global__ void k_hot_centers(const u32* __restrict__ hot, u32 n_hot,
 // atomic per warp step when the step's edges share a member.
 constexpr int kCutThreads = 1024;
 
+// Four groups per thread per step, their label gathers in flight together.
+constexpr int kLabIpt = 4;
+
 template <bool U>
 __global__ void __launch_bounds__(256) k_group_labels(CutList cl, const int* __restrict__ center) {
-  for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < cl.ngrp; g += gridDim.x * blockDim.x) {
-    const int lab = center[__ldg(cl.grp_v + g)];
-    if (U)  // member and label in one word: one gather per edge in k_cut
-      reinterpret_cast<u64*>(cl.grp_lab)[g] = ((u64)__ldg(cl.grp_m + g) << 32) | (u32)lab;
-    else
-      cl.grp_lab[g] = lab;
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < cl.ngrp; g0 += stride * kLabIpt) {
+    int lab[kLabIpt];
+#pragma unroll
+    for (int q = 0; q < kLabIpt; ++q) {
+      const u32 g = g0 + (u32)q * stride;
+      lab[q] = g < cl.ngrp ? center[__ldg(cl.grp_v + g)] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kLabIpt; ++q) {
+      const u32 g = g0 + (u32)q * stride;
+      if (g >= cl.ngrp) break;
+      if (U)  // member and label in one word: one gather per edge in k_cut
+        reinterpret_cast<u64*>(cl.grp_lab)[g] = ((u64)__ldg(cl.grp_m + g) << 32) | (u32)lab[q];
+      else
+        cl.grp_lab[g] = lab[q];
+    }
   }
 }
 
@@ -414,7 +428,8 @@ int launch_cut(const CutList& cl, const int* center, const u32* hot, u32 n_hot, 
     k_hot_centers<<<(n_hot + 255) / 256, 256, 0, s>>>(hot, n_hot, center, hot_center);
     ++launches;
   }
-  k_group_labels<false><<<grid_for(cl.ngrp, num_sms), 256, 0, s>>>(cl, center);
+  k_group_labels<false><<<grid_for((cl.ngrp + kLabIpt - 1) / kLabIpt, num_sms), 256, 0, s>>>(
+      cl, center);
   const u32 g = (u32)max(1ll, min((long long)(cl.m + 4095) / 4096, (long long)num_sms));
   k_cut<false><<<g, kCutThreads, (size_t)n_hot * sizeof(int), s>>>(cl, center, hot_center, n_hot,
                                                                    out);
@@ -426,7 +441,8 @@ int launch_union_cut(const CutList& cl, const UnionOffsets& off, const u32* wmem
   (void)off;
   (void)wmem;
   if (cl.m == 0) return 0;
-  k_group_labels<true><<<grid_for(cl.ngrp, num_sms), 256, 0, s>>>(cl, center);
+  k_group_labels<true><<<grid_for((cl.ngrp + kLabIpt - 1) / kLabIpt, num_sms), 256, 0, s>>>(
+      cl, center);
   const u32 g = (u32)max(1ll, min((long long)(cl.m + 4095) / 4096, (long long)num_sms));
   k_cut<true><<<g, kCutThreads, 0, s>>>(cl, center, nullptr, 0, cut);
   return 2;
