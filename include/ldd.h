@@ -296,16 +296,19 @@ int ldd_server_destroy(ldd_server* s);
  *   n, nnz      sizes as in ldd_create_graph; nnz must be <= 2^27 (134,217,728
  *               arcs), the limit of the scratch below, else LDD_ERR_RANGE.
  *   row_ptr, col_idx, center
- *               device memory of the current CUDA device (host pointers give
- *               LDD_ERR_ARG); layouts as in ldd_create_graph / ldd_cut_edges.
- *               The CSR is trusted: it is not validated.
- *   out_cut     host or device int64: receives the count.
+ *               device memory of the current CUDA device (host pointers and
+ *               memory of another GPU give LDD_ERR_ARG); layouts as in
+ *               ldd_create_graph / ldd_cut_edges.  The CSR is trusted: it is
+ *               not validated.
+ *   out_cut     host memory or device memory of the current device: receives
+ *               the count.
  *   cuda_stream the stream to run on (NULL: the legacy default stream); the
  *               call returns after that stream has finished the work.
  * Scratch: a fixed array of about 256 KiB in the library's device image,
  * present on every GPU that loads the library until the process exits.  The
- * first call on each device looks up that array's device address; make that
- * first call before any stream capture begins.  Every call reuses the same
+ * first call on each device (and again after a cudaDeviceReset, which gives
+ * the device a new CUDA context) looks up that array's device address; make
+ * that first call before any stream capture begins.  Every call reuses the same
  * array and clears the part that must start at zero, so two calls whose work
  * overlaps on the GPU (different streams or threads) race and must be
  * serialised by the caller.

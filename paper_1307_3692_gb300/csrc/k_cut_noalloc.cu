@@ -12,11 +12,13 @@
 // g_cut_scratch below, sized for spans up to kMaxSpans (nnz <= 2^27 arcs).
 // Every GPU that loads this library keeps that array (about 256 KiB) until
 // the process exits.  The array's host-side name is only a stand-in, so the
-// host fetches its device address once per device with cudaGetSymbolAddress
-// and passes that pointer to the kernels.
+// host fetches its device address with cudaGetSymbolAddress once per device
+// and CUDA context (a cudaDeviceReset gives the device a new context, in
+// which the array may sit elsewhere) and passes that pointer to the kernels.
 //
 // The paper has no counterpart to this entry point; it computes the same
 // count as ldd_cut_edges (Definition 1.1, second condition).
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +46,7 @@ static __device__ __align__(256) u32 g_cut_scratch[kScratchWords];
 
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};  // the context each address was looked up in
 
 __global__ void k_na_first_rows(const int* __restrict__ row_ptr, u32 n, u32 nspans,
                                 u32* __restrict__ first) {
@@ -100,28 +103,60 @@ bool on_device(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// True for device memory of device `dev` (or managed memory, which every
+// device can read).  Memory of another GPU is refused: reading it would be a
+// fault without peer access and a slow cross-GPU read with it.
+bool on_this_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// The driver's cuCtxGetCurrent, fetched through the runtime (the library does
+// not link the driver API); null if unavailable.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
 int fail(int status, const char* msg) {
   record_error(msg);
   return status;
 }
 
-// Device address of g_cut_scratch on the current device, looked up on the
-// first call for that device.
-int scratch_address(u32** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return fail(LDD_ERR_CUDA, "ldd_cut_edges_noalloc: no usable current CUDA device");
-  }
+// Device address of g_cut_scratch on the current device (dev), looked up on
+// the first call in the device's current CUDA context.  Without the driver's
+// context query the address is looked up on every call.
+int scratch_address(int dev, u32** out) {
+  CUcontext ctx = nullptr;
+  const CtxGetCurrentFn get_ctx = ctx_get_current();
+  const bool keyed = get_ctx && get_ctx(&ctx) == CUDA_SUCCESS && ctx != nullptr;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (!keyed || !g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_cut_scratch);
     if (e != cudaSuccess || p == nullptr) {
       cudaGetLastError();
+      g_scratch_addr[dev] = nullptr;
       return fail(LDD_ERR_CUDA, "ldd_cut_edges_noalloc: cudaGetSymbolAddress of the scratch failed");
     }
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = keyed ? ctx : nullptr;
   }
   *out = static_cast<u32*>(g_scratch_addr[dev]);
   return LDD_OK;
@@ -140,7 +175,14 @@ extern "C" int ldd_cut_edges_noalloc(int32_t n, int64_t nnz, const int32_t* row_
   if (nnz > kMaxArcs)
     return fail(LDD_ERR_RANGE, "ldd_cut_edges_noalloc: nnz exceeds its scratch limit of 2^27 arcs");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return fail(LDD_ERR_CUDA, "ldd_cut_edges_noalloc: no usable current CUDA device");
+  }
   const bool out_dev = on_device(out_cut);
+  if (out_dev && !on_this_device(out_cut, dev))
+    return fail(LDD_ERR_ARG, "ldd_cut_edges_noalloc: out_cut is memory of another device");
   if (n == 0 || nnz == 0) {
     if (!out_dev) {
       *out_cut = 0;
@@ -155,10 +197,13 @@ extern "C" int ldd_cut_edges_noalloc(int32_t n, int64_t nnz, const int32_t* row_
   }
   if (!row_ptr || !col_idx || !center)
     return fail(LDD_ERR_ARG, "ldd_cut_edges_noalloc: NULL input");
-  if (!on_device(row_ptr) || !on_device(col_idx) || !on_device(center))
-    return fail(LDD_ERR_ARG, "ldd_cut_edges_noalloc: row_ptr, col_idx and center must be device memory");
+  if (!on_this_device(row_ptr, dev) || !on_this_device(col_idx, dev) ||
+      !on_this_device(center, dev))
+    return fail(LDD_ERR_ARG,
+                "ldd_cut_edges_noalloc: row_ptr, col_idx and center must be device memory of "
+                "the current device");
   u32* scratch = nullptr;
-  int rc = scratch_address(&scratch);
+  int rc = scratch_address(dev, &scratch);
   if (rc != LDD_OK) return rc;
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(scratch);
   u32* first = scratch + kAccWords;

@@ -70,6 +70,20 @@ def test_rgg_mean_degree():
     assert 7.0 < G.nnz / G.n < 8.2
 
 
+@pytest.mark.parametrize("ctr,key,expected", [
+    ([0, 0, 0, 0], [0, 0], [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]),
+    ([0xffffffff] * 4, [0xffffffff] * 2, [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]),
+    ([0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344], [0xa4093822, 0x299f31d0],
+     [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]),
+], ids=["zeros", "ones", "pi"])
+def test_philox_known_answers(ctr, key, expected):
+    """Philox4x32-10 against the known-answer vectors published with the
+    Random123 library (Salmon et al., SC'11): counter, key -> four words.  The
+    third case takes its counter and key from the hexadecimal digits of pi."""
+    got = [int(x) for x in gen.philox4x32_10(ctr, key)]
+    assert got == expected, [hex(x) for x in got]
+
+
 def test_philox_counter_and_key_sensitivity():
     base = gen.philox4x32_10([0, 0, 0, 0], [1, 0])
     assert not np.array_equal(base, gen.philox4x32_10([1, 0, 0, 0], [1, 0]))

@@ -33,4 +33,9 @@ def test_fullsize_workload(ldd, cuda, name):
         assert nbad == 0, f"{name} beta={beta}: {nbad} mismatches"
         assert cut == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
         assert gd.max() <= np.floor(shifts.max())  # radius <= floor(delta_max), Lemma 3.2
+        if G.nnz <= 1 << 27:  # the allocation-free count, near its span-table limit
+            rp = torch.from_numpy(G.row_ptr).to(cuda)
+            col = torch.from_numpy(G.col).to(cuda)
+            assert ldd.ldd_cut_edges_noalloc(G.n, G.nnz, rp, col, c) == cut
+            del rp, col
     g.close()

@@ -15,6 +15,7 @@ import pytest
 import torch
 
 import ldd_gen as gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +33,8 @@ def _labels(ldd, G, beta, seed, dev):
                          ids=["grid2d", "rmat13", "star_with_isolated"])
 def test_noalloc_matches_cut_edges_twice(ldd, cuda, G, beta):
     g, center = _labels(ldd, G, beta, 7, cuda)
-    expected = g.cut_edges(center)
+    expected = oracle.oracle_cut_edges(G.row_ptr, G.col, center.cpu().numpy())
+    assert g.cut_edges(center) == expected
     rp = torch.from_numpy(G.row_ptr).to(cuda)
     col = torch.from_numpy(G.col).to(cuda)
     first = ldd.ldd_cut_edges_noalloc(G.n, G.nnz, rp, col, center)
@@ -48,7 +50,8 @@ def test_noalloc_matches_cut_edges_twice(ldd, cuda, G, beta):
     assert rc == ldd.LDD_OK and int(out.item()) == expected
     # a different labelling right after: nothing left over from the last call
     other = torch.arange(G.n, dtype=torch.int32, device=cuda)
-    assert ldd.ldd_cut_edges_noalloc(G.n, G.nnz, rp, col, other) == g.cut_edges(other) == G.m
+    assert ldd.ldd_cut_edges_noalloc(G.n, G.nnz, rp, col, other) == G.m
+    assert oracle.oracle_cut_edges(G.row_ptr, G.col, other.cpu().numpy()) == G.m
     g.close()
 
 
@@ -64,3 +67,19 @@ def test_noalloc_rejects_what_it_cannot_do(ldd, cuda):
         ldd.ldd_cut_edges_noalloc(G.n, G.nnz, G.row_ptr, G.col, c)
     assert e.value.status == ldd.LDD_ERR_ARG
     assert ldd.ldd_cut_edges_noalloc(G.n, 0, rp, col[:0], c) == 0
+
+
+def test_noalloc_rejects_memory_of_another_gpu(ldd, cuda):
+    """Inputs on a second GPU are refused before any launch (only where the
+    machine has one: nothing runs on the second device)."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one CUDA device")
+    G = gen.grid2d(10, 10)
+    other = torch.device("cuda", 1)
+    rp = torch.from_numpy(G.row_ptr).to(other)
+    col = torch.from_numpy(G.col).to(other)
+    c = torch.zeros(G.n, dtype=torch.int32, device=other)
+    with torch.cuda.device(0):
+        with pytest.raises(ldd.LddError) as e:
+            ldd.ldd_cut_edges_noalloc(G.n, G.nnz, rp, col, c)
+    assert e.value.status == ldd.LDD_ERR_ARG
