@@ -416,6 +416,40 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out);
 int ldd_set_graph_replay(ldd_graph* g, int enable);
 
 /*
+ * Bounded device-side waits.  The round loop ends every round at a grid-wide
+ * barrier, and the fraction rank's scans wait on their predecessor tiles
+ * (decoupled look-back).  Neither wait can last for ever: after the given
+ * number of polls the kernel records the failure, every later kernel of the
+ * call writes nothing, and the call returns LDD_ERR_TIMEOUT with outputs
+ * invalid; the graph stays usable for the next call.  The defaults (2^22
+ * barrier polls of >= 20 ns, 2^24 look-back polls of >= 64 ns: about 0.1 s
+ * and 1 s) are far beyond any legitimate wait.  The paper has no counterpart:
+ * its PRAM rounds are synchronous by definition.
+ *   barrier_polls   polls of the round loop's grid barrier (0: the default;
+ *                   the environment variable LDD_SPIN_LIMIT, read when the
+ *                   graph is created, sets the initial value).
+ *   lookback_polls  polls of a look-back wait (0: the default).
+ *   stall_barrier   1: every grid barrier also waits for one CTA that does not
+ *                   exist, so the round loop can only end by running out of
+ *                   polls -- for tests of the timeout path; 0 normally.
+ *   stall_lookback  1: the first tile of each scan waits on a predecessor that
+ *                   does not exist, so every look-back runs out of polls (when
+ *                   the call takes the fraction-bucket rank) -- for tests; 0
+ *                   normally.
+ * ldd_set_wait_limits drops a captured replay (ldd_set_graph_replay), since it
+ * holds the old values.  LDD_ERR_ARG if a stall field is not 0 or 1.
+ */
+typedef struct {
+  uint32_t barrier_polls;
+  uint32_t lookback_polls;
+  uint32_t stall_barrier;
+  uint32_t stall_lookback;
+} ldd_wait_limits;
+
+int ldd_set_wait_limits(ldd_graph* g, const ldd_wait_limits* w);
+int ldd_get_wait_limits(const ldd_graph* g, ldd_wait_limits* out);
+
+/*
  * ldd_get_round_profile -- diagnostic: per-round timestamps of the last BFS.
  *   clocks[3i .. 3i+2]  SM clock (cycles) of the first CTA in round i: after
  *              its expansion, after its start-bucket scan, and when its closing

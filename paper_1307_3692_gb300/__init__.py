@@ -130,6 +130,17 @@ _lib.ldd_set_graph_replay.argtypes = [_vp, ctypes.c_int]
 _lib.ldd_set_graph_replay.restype = ctypes.c_int
 
 
+class WaitLimits(ctypes.Structure):
+    _fields_ = [("barrier_polls", ctypes.c_uint32), ("lookback_polls", ctypes.c_uint32),
+                ("stall_barrier", ctypes.c_uint32), ("stall_lookback", ctypes.c_uint32)]
+
+
+_lib.ldd_set_wait_limits.argtypes = [_vp, ctypes.POINTER(WaitLimits)]
+_lib.ldd_set_wait_limits.restype = ctypes.c_int
+_lib.ldd_get_wait_limits.argtypes = [_vp, ctypes.POINTER(WaitLimits)]
+_lib.ldd_get_wait_limits.restype = ctypes.c_int
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -337,6 +348,20 @@ def ldd_set_graph_replay(g: int, enable: bool) -> None:
     _check(_lib.ldd_set_graph_replay(g, int(bool(enable))), "ldd_set_graph_replay")
 
 
+def ldd_get_wait_limits(g: int) -> dict:
+    w = WaitLimits()
+    _check(_lib.ldd_get_wait_limits(g, ctypes.byref(w)), "ldd_get_wait_limits")
+    return {name: getattr(w, name) for name, _ in WaitLimits._fields_}
+
+
+def ldd_set_wait_limits(g: int, barrier_polls: int = 0, lookback_polls: int = 0,
+                        stall_barrier: int = 0, stall_lookback: int = 0) -> None:
+    """Poll limits of the device-side waits (0: default) and the stall
+    switches that tests of the timeout path use (include/ldd.h)."""
+    w = WaitLimits(barrier_polls, lookback_polls, stall_barrier, stall_lookback)
+    _check(_lib.ldd_set_wait_limits(g, ctypes.byref(w)), "ldd_set_wait_limits")
+
+
 def ldd_get_round_profile(g: int, cap: int = 256):
     """(clocks, kinds) of the last BFS's rounds (see include/ldd.h)."""
     import numpy as np
@@ -398,6 +423,12 @@ class LddGraph:
 
     def autotune(self, shifts, reps: int = 2) -> dict:
         return ldd_autotune(self.handle, shifts, reps, self.n)
+
+    def wait_limits(self) -> dict:
+        return ldd_get_wait_limits(self.handle)
+
+    def set_wait_limits(self, **fields) -> None:
+        ldd_set_wait_limits(self.handle, **fields)
 
     def stats(self) -> dict:
         return ldd_get_stats(self.handle)

@@ -66,22 +66,28 @@ struct Smem {
   u64 cand[kBfsMaxSpan + 1];
   int wtot[kBfsThreads / 32];
   u32 minrank;  // this CTA's smallest successful next-level rank in the round
+  u32 stop;     // thread 0 saw an error bit: the whole CTA leaves the loop
 };
 
 // Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a
-// launch completes when the counter reaches k * nblocks, so arrival is one
-// fire-and-forget add and nobody has to reset anything.  Before arriving,
-// thread 0 publishes this CTA's smallest next-level rank to *post (and resets
-// the CTA value).  The wait is bounded: after `limit` polls (or once any CTA
-// has recorded an error) it sets kErrTimeout and returns.
-__device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 limit,
-                                             u32* post, u32* cta_min) {
+// launch completes when the counter reaches k * nblocks (+ phantom), so
+// arrival is one fire-and-forget add and nobody has to reset anything.
+// Before arriving, thread 0 publishes this CTA's smallest next-level rank to
+// *post (and resets the CTA value).  The wait is bounded: after `limit` polls
+// (or once any CTA has recorded an error) it sets kErrTimeout and returns.
+// Thread 0 then reads the error word once for the whole CTA into *stop, so
+// that every thread of the CTA takes the same branch after the barrier (a
+// thread that left the loop alone would leave the others at a CTA barrier).
+// phantom > 0 waits for CTAs that do not exist: the barrier can then only end
+// by running out of polls, which is how the timeout path is tested.
+__device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 phantom,
+                                             u32 limit, u32* post, u32* cta_min, u32* stop) {
   __syncthreads();
   if (threadIdx.x == 0) {
     if (*cta_min != 0xffffffffu) atomicMin(post, *cta_min);
     *cta_min = 0xffffffffu;
     ++gen;
-    const u64 target = (u64)gen * nblocks;
+    const u64 target = (u64)gen * nblocks + phantom;
     __threadfence();
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->bar), "l"(1ull) : "memory");
     u32 spins = 0;
@@ -96,6 +102,7 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
       if (spins > 64) __nanosleep(20);
     }
     __threadfence();
+    *stop = ld_acquire_u32(&ctl->err) != 0u ? 1u : 0u;
   }
   __syncthreads();
 }
@@ -538,7 +545,12 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   if (s_acc)
     for (u32 m = threadIdx.x; m < a.kmem; m += blockDim.x) s_acc[m] = 0xffffffffu;
   Control* ctl = a.ctl;
-  if (ld_acquire_u32(&ctl->err) != 0u) return;  // validation failed upstream
+  if (threadIdx.x == 0) {
+    s.minrank = 0xffffffffu;
+    s.stop = ld_acquire_u32(&ctl->err) != 0u ? 1u : 0u;  // validation failed upstream
+  }
+  __syncthreads();
+  if (s.stop) return;  // CTA-uniform: read once by thread 0
   const int A = ctl->A;
   const u32 par_r = __popc(ctl->mask_r) & 1u;
   const u32* rk = a.rk[par_r];
@@ -546,8 +558,6 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   const u32 G = gridDim.x;
   u32 gen = 0;
   u32 myrank = 0xffffffffu;  // this thread's smallest successful next-level rank
-  if (threadIdx.x == 0) s.minrank = 0xffffffffu;
-  __syncthreads();
 
   // Level 0: the vertices with the largest integer shift part start.
   append_bucket<U>(a, 0, rv, 0, 0, myrank, s_acc);
@@ -556,7 +566,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
     __syncthreads();
     flush_members(a, 0, s_acc);
   }
-  grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[0], &s.minrank);
+  grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, &ctl->minrank[0], &s.minrank, &s.stop);
   const bool profiler = blockIdx.x == 0 && threadIdx.x == 0;
   if (profiler) {
     const long long t = clock64();
@@ -570,7 +580,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   int lvl = 0;
   bool pulling = false;
   for (;;) {
-    if (ld_acquire_u32(&ctl->err) != 0u) break;
+    if (s.stop) break;  // set by the last barrier, the same for every thread of the CTA
     const u64 c = ld_cg_u64(&ctl->qctr[phase % 3]);
     const u32 Q = (u32)(c >> 32), E = (u32)c;
     settled += Q;
@@ -628,7 +638,8 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       __syncthreads();
       flush_members(a, (u32)qi, s_acc);
     }
-    grid_barrier(ctl, gen, G, a.spin_limit, &ctl->minrank[qi], &s.minrank);
+    grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, &ctl->minrank[qi], &s.minrank,
+                 &s.stop);
     ++phase;
     lvl = nlvl;
     if (profiler && phase < (u32)kRoundProfile) {

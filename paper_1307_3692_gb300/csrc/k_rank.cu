@@ -44,7 +44,6 @@ namespace ldd {
 namespace {
 
 constexpr u32 kFull = 0xffffffffu;
-constexpr u32 kLookbackSpinLimit = 1u << 24;  // ~1 s of polling, then kErrTimeout
 constexpr u32 kSlotCap = 64;                  // record slots per fraction bucket (mean <= 16)
 constexpr int kScanThreads = 256;
 constexpr int kScanIpt = 16;
@@ -505,7 +504,7 @@ struct SortSmem {
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     u64* __restrict__ k0, u32* __restrict__ v0, u64* __restrict__ k1, u32* __restrict__ v1, u32 n,
     int pass, int shift, const u32* __restrict__ mask_ptr, const u32* __restrict__ digit_off,
-    u64* __restrict__ status, u32* __restrict__ tile_ctr, u32 epoch, u32* err) {
+    u64* __restrict__ status, u32* __restrict__ tile_ctr, u32 epoch, u32* err, u32 spin_limit) {
   const u32 mask = *mask_ptr;
   if (!((mask >> pass) & 1u) || *(volatile u32*)err != 0u) return;
   const int par = __popc(mask & ((1u << pass) - 1u)) & 1;
@@ -583,7 +582,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     while (p >= 0) {
       const u64 sv = ld_volatile_u64(status + (u64)p * 256 + dg);
       if ((u32)(sv >> 32) != epoch) {
-        if (++spins > kLookbackSpinLimit) {
+        if (++spins > spin_limit) {
           atomicOr(err, kErrTimeout);
           sm.bad = 1;
           break;
@@ -651,12 +650,15 @@ __global__ void __launch_bounds__(256) k_rank_scatter(const u32* __restrict__ v0
 // for the next decomposition); a table of fewer than A + 2 entries (cap) sets
 // kErrBucketCap.  Optionally copies the result to copy[] and records the
 // largest input value in *maxv.  Tiles take tickets in order, so every tile's
-// predecessors are running or done; every wait is bounded.  One warp looks
-// back over 32 predecessor tiles at a time.
+// predecessors are running or done; every wait is bounded (spin_limit polls,
+// then kErrTimeout).  One warp looks back over 32 predecessor tiles at a time.
+// stall = 1 makes tile 0 wait, like the others, on a predecessor that does not
+// exist, so that every look-back runs out of polls (tests of the timeout path).
 __global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy, u32 len_host,
                                                             int len_from_A, u64* __restrict__ status,
                                                             u32 epoch, u32* tile_ctr, u32* maxv,
-                                                            u32* rev_src, u32 cap, Control* ctl) {
+                                                            u32* rev_src, u32 cap, Control* ctl,
+                                                            u32 spin_limit, u32 stall) {
   __shared__ u32 s_tile, s_excl, s_bad;
   __shared__ u32 s_wsum[kScanThreads / 32];
   __shared__ u32 s_wmax[kScanThreads / 32];
@@ -726,7 +728,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy
   if (warp == 0) {
     const u64 tag = (u64)epoch << 32;
     u64* mine = status + tile;
-    if (tile == 0) {
+    if (tile == 0 && !stall) {
       if (lane == 0) st_volatile_u64(mine, tag | (2ull << 30) | tile_tot);
     } else {
       if (lane == 0) st_volatile_u64(mine, tag | (1ull << 30) | tile_tot);
@@ -734,10 +736,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy
       int p = (int)tile - 1;
       u32 spins = 0;
       bool bad = false;
-      while (p >= 0) {
-        // lane l looks at tile p - l; "before tile 0" counts as an inclusive prefix of 0
+      while (p >= 0 || stall) {
+        // lane l looks at tile p - l; "before tile 0" counts as an inclusive
+        // prefix of 0 (with stall: as a tile that never reports)
         const int q = p - (int)lane;
-        const u64 sv = (q >= 0) ? ld_volatile_u64(status + q) : (tag | (2ull << 30));
+        const u64 sv = (q >= 0) ? ld_volatile_u64(status + q) : (stall ? 0ull : (tag | (2ull << 30)));
         const bool ready = (u32)(sv >> 32) == epoch;
         const bool pref = ready && ((((u32)sv) >> 30) == 2u);
         const u32 pmask = __ballot_sync(kFull, pref);
@@ -745,7 +748,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_excl(u32* data, u32* copy
         const u32 rmask = __ballot_sync(kFull, ready);
         const u32 need = (limit == 31u) ? kFull : ((2u << limit) - 1u);
         if ((rmask & need) != need) {
-          if (++spins > kLookbackSpinLimit) {
+          if (++spins > spin_limit) {
             bad = true;
             break;
           }
@@ -1032,10 +1035,10 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
     }
     k_scan_excl<<<(nbkt + 1 + kScanTile - 1) / kScanTile, kScanThreads, 0, s>>>(
         cnt, nullptr, nbkt + 1, 0, r.status, ++(*r.epoch), &ctl->tile_ctr[0], nullptr, nullptr, 0,
-        ctl);
+        ctl, r.lookback_limit, r.stall_lookback);
     k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
                                                  &ctl->tile_ctr[1], nullptr, r.acnt, r.bptr_cap,
-                                                 ctl);
+                                                 ctl, r.lookback_limit, r.stall_lookback);
     allow_bsort_smem();
     const u32 ntiles = (nbkt + kTileBuckets - 1) / kTileBuckets;
     const u32 sort_grid = (u32)min((long long)ntiles, (long long)r.num_sms * kBsortPerSm);
@@ -1058,7 +1061,7 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
   for (int d = 0; d < kFracDigits; ++d) {
     k_onesweep<<<ntiles, kSortThreads, sizeof(SortSmem), s>>>(
         r.k0, r.v0, r.k1, r.v1, n, d, 8 * d, &ctl->mask_f, ctl->off_f[d], r.status,
-        &ctl->tile_ctr[2 + d], ++(*r.epoch), &ctl->err);
+        &ctl->tile_ctr[2 + d], ++(*r.epoch), &ctl->err, r.lookback_limit);
     ++launches;
   }
   k_rank_scatter<<<gs, 256, 0, s>>>(r.v0, r.v1, ctl, n, r.order, rank);
@@ -1066,7 +1069,8 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
                                                                             ctl);
   k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
   k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
-                                               &ctl->tile_ctr[1], nullptr, nullptr, 0, ctl);
+                                               &ctl->tile_ctr[1], nullptr, nullptr, 0, ctl,
+                                               r.lookback_limit, r.stall_lookback);
   k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
                         (long long)r.num_sms * 8),
                256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));
@@ -1087,7 +1091,8 @@ int launch_ranked_and_buckets(const RankBufs& r, const int* levels, const int* p
                                                                             ctl);
   k_keys<<<gs, 256, 0, s>>>(r.a, rank, r.excl, ctl, n, r.key, rcnt);
   k_scan_excl<<<rtiles, kScanThreads, 0, s>>>(rcnt, r.rcur, 0, 1, r.status, ++(*r.epoch),
-                                               &ctl->tile_ctr[1], nullptr, nullptr, 0, ctl);
+                                               &ctl->tile_ctr[1], nullptr, nullptr, 0, ctl,
+                                               r.lookback_limit, r.stall_lookback);
   k_rscatter<<<(u32)min((long long)(n + 256 * kRChunk - 1) / (256 * kRChunk),
                         (long long)r.num_sms * 8),
                256, 0, s>>>(r.a, r.excl, ctl, n, r.rcur, r.v0, reinterpret_cast<u32*>(r.k0));

@@ -397,6 +397,7 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.n_active = g->n_active;
   a.nnz_active = g->nnz_active;
   a.spin_limit = g->spin_limit;
+  a.bar_phantom = g->stall_barrier ? 1u : 0u;
   a.pull_alpha = g->pull_alpha;
   a.pull_beta = g->pull_beta;
   a.pull_gamma = g->pull_gamma;
@@ -438,6 +439,9 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
   return launches;
 }
 
+constexpr u32 kDefaultBarrierPolls = 1u << 22;   // grid barrier: each poll >= 20 ns after 64
+constexpr u32 kDefaultLookbackPolls = 1u << 24;  // look-back: each poll >= 64 ns after 16
+
 // Scratch arena, pinned header, events and launch parameters: the part of
 // graph creation that only depends on the sizes and the tables being built.
 int finish_setup(ldd_graph* g) {
@@ -457,7 +461,8 @@ int finish_setup(ldd_graph* g) {
   const u32 per_sm = env_u32("LDD_BFS_BLOCKS_PER_SM", 0);
   if (per_sm > 0 && (int)per_sm <= max_per_sm) g->bfs_per_sm = (int)per_sm;
   g->bfs_grid = g->bfs_per_sm * g->num_sms;
-  g->spin_limit = env_u32("LDD_SPIN_LIMIT", 1u << 22);
+  g->spin_limit = env_u32("LDD_SPIN_LIMIT", kDefaultBarrierPolls);
+  g->lookback_limit = kDefaultLookbackPolls;
   g->pull_alpha = env_u32("LDD_PULL_ALPHA", 14);
   g->pull_beta = env_u32("LDD_PULL_BETA", 24);
   g->pull_gamma = env_u32("LDD_PULL_GAMMA", 8);
@@ -511,6 +516,8 @@ RankBufs rank_bufs(ldd_graph* g, const double* d_shift) {
   rb.wmem = g->uni ? g->uni->d_wmem : nullptr;
   rb.lift = g->uni ? g->uni->d_amax + g->uni->k : nullptr;
   rb.ctl = g->d_ctl;
+  rb.lookback_limit = g->lookback_limit;
+  rb.stall_lookback = g->stall_lookback;
   rb.bptr = g->d_bptr;
   rb.rcur = g->d_rcur;
   rb.acnt = g->d_acnt;
@@ -1763,6 +1770,29 @@ int ldd_set_graph_replay(ldd_graph* g, int enable) {
     drop_replay(g);
   }
   g->replay_broken = false;  // a new request gets a new capture attempt
+  return LDD_OK;
+}
+
+int ldd_set_wait_limits(ldd_graph* g, const ldd_wait_limits* w) {
+  if (!g || !w) return fail(LDD_ERR_ARG, "NULL graph or limits");
+  if (w->stall_barrier > 1 || w->stall_lookback > 1)
+    return fail(LDD_ERR_ARG, "stall_barrier and stall_lookback must be 0 or 1");
+  DeviceGuard dg(g->device);
+  cudaStreamSynchronize(g->stream);
+  drop_replay(g);  // captured graphs hold the old kernel arguments
+  g->spin_limit = w->barrier_polls ? w->barrier_polls : kDefaultBarrierPolls;
+  g->lookback_limit = w->lookback_polls ? w->lookback_polls : kDefaultLookbackPolls;
+  g->stall_barrier = w->stall_barrier;
+  g->stall_lookback = w->stall_lookback;
+  return LDD_OK;
+}
+
+int ldd_get_wait_limits(const ldd_graph* g, ldd_wait_limits* out) {
+  if (!g || !out) return fail(LDD_ERR_ARG, "NULL graph or output");
+  out->barrier_polls = g->spin_limit;
+  out->lookback_polls = g->lookback_limit;
+  out->stall_barrier = g->stall_barrier;
+  out->stall_lookback = g->stall_lookback;
   return LDD_OK;
 }
 

@@ -109,6 +109,9 @@ struct ldd_graph {
   int bfs_grid = 0;
   int bfs_per_sm = 0;
   u32 spin_limit = 0;
+  u32 lookback_limit = 1u << 24;  // polls of a look-back wait (fraction rank scans)
+  u32 stall_barrier = 0;          // ldd_set_wait_limits: timeout-path tests
+  u32 stall_lookback = 0;
   u32 pull_alpha = 0;
   u32 pull_beta = 0;
   u32 pull_gamma = 0;

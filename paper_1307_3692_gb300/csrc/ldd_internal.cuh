@@ -112,6 +112,8 @@ struct BfsArgs {
   u32 n_active;      // vertices the BFS settles (components of more than 32 vertices)
   u64 nnz_active;    // their arcs
   u32 spin_limit;
+  u32 bar_phantom;   // CTAs the grid barrier waits for beyond the launch's own: 0, or 1 to make
+                     // every barrier end by running out of polls (tests of the timeout path)
   u32 pull_alpha;    // go bottom-up when frontier arcs * alpha > unsettled arcs
   u32 pull_gamma;    //   and frontier arcs * gamma > n_active (a bottom-up round reads every key)
   u32 pull_beta;     // go back top-down when frontier vertices * beta < n_active
@@ -172,6 +174,9 @@ struct RankBufs {
   const u32* wmem;      // unions: member of every 32-vertex word; else null
   const int* lift;      // unions: floor lift of every member (a_u += lift); else null
   Control* ctl;
+  u32 lookback_limit = 1u << 24;  // polls of a look-back wait before kErrTimeout
+  u32 stall_lookback = 0;         // 1: the scans' first tile waits on a status word that nothing
+                                  // writes, so every look-back runs out (timeout-path tests)
 };
 // exact64 = false: fraction buckets + in-bucket exact ranks of the vertices
 // not alone in their component (may set kErrRankRetry); true: exact 64-bit
