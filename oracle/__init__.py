@@ -12,6 +12,9 @@ code.  The only common dependency is ``ldd_gen`` (seeded inputs).
                           levels + a tie-break permutation), through
                           ``oracle_ldd`` on shifts that order the same way.
 * ``oracle_cut_edges`` -- Definition 1.1's count of edges between pieces.
+* ``oracle_block_decompose`` -- blocks by repeated decomposition (Section 1,
+                          related work): decompose, keep the cut edges,
+                          decompose them again, until no edge is left.
 * ``oracle_certify``   -- O(m) optimality certificate (Lemma 3.1 predecessor +
                           non-improvability), usable at any size.
 * ``brute.brute_ldd``  -- Algorithm 2 written out literally: all-pairs BFS and
@@ -132,3 +135,52 @@ def oracle_certify(row_ptr, col, delta, center, dist):
     bad = ctypes.c_int64(-1)
     code = _load().oracle_certify(rp.shape[0] - 1, prp, pcl, pdl, pce, pdi, ctypes.byref(bad))
     return int(code), int(bad.value)
+
+
+def oracle_block_decompose(row_ptr, col, shifts_list):
+    """Block decomposition by repeated low-diameter decomposition.
+
+    Section 1 (related work) observes that Linial and Saks' block
+    decomposition -- O(log n) blocks whose connected pieces have diameter
+    O(log n) -- follows from running a (1/2, O(log n)) decomposition again and
+    again on the edges that are not yet in a block, since each run leaves at
+    most half of them (in expectation; Corollary 3.5 gives 1 - e^-beta).
+
+    The steps, in that order: G_0 = G.  While G_i has an arc and a shift
+    vector is left: decompose G_i = (V, E_i) with shifts_list[i]
+    (``oracle_ldd``); the arcs of E_i whose two ends share a piece form block
+    i; the others, in their original order, are E_{i+1}.
+
+    Returns (centers, dists, arc_block, remaining):
+      centers[i], dists[i]  int32[n]: iteration i's decomposition of G_i;
+      arc_block             int32[nnz]: the block of every arc of the input
+                            CSR, -1 for arcs still cut after the last
+                            iteration;
+      remaining             list of ints: remaining[i] = the undirected edges
+                            of G_i ({v, w} with v < w; the input's self-loops
+                            are not counted and join block 0), for i = 0 ..
+                            blocks, where blocks = len(centers).
+    """
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int64)
+    n = rp.shape[0] - 1
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    alive = np.arange(cl.shape[0], dtype=np.int64)  # input arc ids of E_i
+    arc_block = np.full(cl.shape[0], -1, dtype=np.int32)
+    cur_rp, cur_col = rp, cl
+    remaining = [int((src < cl).sum())]
+    centers, dists = [], []
+    for i, sh in enumerate(shifts_list):
+        if alive.shape[0] == 0:
+            break
+        c, d = oracle_ldd(cur_rp, cur_col, sh)
+        inside = c[src[alive]] == c[cl[alive]]
+        arc_block[alive[inside]] = i
+        alive = alive[~inside]
+        counts = np.bincount(src[alive], minlength=n)
+        cur_rp = np.concatenate(([0], np.cumsum(counts)))
+        cur_col = cl[alive]
+        remaining.append(int((src[alive] < cl[alive]).sum()))
+        centers.append(c)
+        dists.append(d)
+    return centers, dists, arc_block, remaining

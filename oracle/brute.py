@@ -83,3 +83,42 @@ def brute_cut_edges(row_ptr, col, center):
             if v < w and center[v] != center[w]:
                 cut += 1
     return cut
+
+
+def brute_block_decompose(row_ptr, col, shifts_list):
+    """Blocks by repeated decomposition, literally: keep a list of the edges
+    not yet in a block (as input arc ids), rebuild the graph of those edges,
+    decompose it by ``brute_ldd``, move the edges inside a piece to the
+    current block, repeat while edges are left.  Same outputs as
+    ``oracle.oracle_block_decompose`` (lists instead of arrays)."""
+    n = len(row_ptr) - 1
+    arcs = []  # (v, w, input arc id)
+    for v in range(n):
+        for e in range(int(row_ptr[v]), int(row_ptr[v + 1])):
+            arcs.append((v, int(col[e]), e))
+    block = [-1] * len(arcs)
+    left = list(arcs)
+    remaining = [sum(1 for v, w, _ in left if v < w)]
+    centers, dists = [], []
+    for i, sh in enumerate(shifts_list):
+        if not left:
+            break
+        rows = [[] for _ in range(n)]
+        for v, w, _ in left:
+            rows[v].append(w)
+        rp, cl = [0], []
+        for v in range(n):
+            cl.extend(rows[v])
+            rp.append(len(cl))
+        c, d = brute_ldd(rp, cl, sh)
+        nxt = []
+        for v, w, e in left:
+            if c[v] == c[w]:
+                block[e] = i
+            else:
+                nxt.append((v, w, e))
+        left = nxt
+        remaining.append(sum(1 for v, w, _ in left if v < w))
+        centers.append(c)
+        dists.append(d)
+    return centers, dists, block, remaining
