@@ -212,6 +212,44 @@ int ldd_union_decompose(ldd_graph* u, const double* betas, const double* shifts,
                         int32_t* out_center, int32_t* out_dist, int64_t* out_cut);
 
 /*
+ * ldd_block_decompose -- blocks by repeated decomposition.  Section 1
+ * (related work) notes that the block decomposition of Linial and Saks --
+ * O(log n) blocks whose connected pieces have diameter O(log n) -- follows
+ * from running a (1/2, O(log n)) decomposition again and again on the edges
+ * not yet in a block, since each run leaves at most half of them in
+ * expectation (Corollary 3.5: a fraction 1 - e^{-beta} < beta).  Iteration i
+ * decomposes G_i = (V, E_i) (G_0 = g) with shifts[i] exactly as
+ * ldd_decompose would; the edges of E_i whose two ends share a piece form
+ * block i, and the edges it cuts are E_{i+1}.  The loop stops after the first
+ * iteration that leaves no edge, or after k iterations.
+ *   k            number of shift vectors available (iterations at most).
+ *   betas        double[k] on the host: each finite and > 0 (checked, not used;
+ *                the paper's choice is beta = 1/2).
+ *   shifts       k pointers to n doubles (host or device), as in
+ *                ldd_decompose; shift vector i is read only if iteration i runs.
+ *   out_center, out_dist  NULL, or k pointers to n int32 (host or device):
+ *                iteration i's decomposition of G_i (entries of iterations
+ *                that do not run are left untouched).
+ *   out_arc_block NULL, or int32[nnz] (host or device): the block of every arc
+ *                of g's CSR, in g's arc order (both arcs of an edge get the same
+ *                block; self-loops are in block 0), -1 for arcs still cut when
+ *                the shift vectors run out.
+ *   out_remaining NULL, or int64[k + 1] on the host: out_remaining[i] = the
+ *                undirected edges of G_i (arcs (v, w) with v < w), for i = 0 ..
+ *                *out_blocks; later entries are left untouched.
+ *   out_blocks   host: the number of iterations run (0 for a graph without arcs
+ *                or k = 0).
+ * Errors as in ldd_decompose; a failure in iteration i leaves the outputs of
+ * earlier iterations complete and *out_blocks = the iterations that finished.
+ * The first call allocates the residual graphs' buffers (about 24 bytes per
+ * arc and 200 per vertex), which stay with g until ldd_destroy_graph.
+ * LDD_ERR_ARG for a union.
+ */
+int ldd_block_decompose(ldd_graph* g, int k, const double* betas, const double* const* shifts,
+                        int32_t* const* out_center, int32_t* const* out_dist,
+                        int32_t* out_arc_block, int64_t* out_remaining, int32_t* out_blocks);
+
+/*
  * Request server: continuous batching of decomposition requests.
  *
  * A server owns `slots` workspaces (union graphs of fixed capacity, bought

@@ -65,6 +65,9 @@ _lib.ldd_decompose_ranked.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.ldd_decompose_ranked.restype = ctypes.c_int
 _lib.ldd_decompose_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.ldd_decompose_batch.restype = ctypes.c_int
+_lib.ldd_block_decompose.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                     ctypes.POINTER(_i32)]
+_lib.ldd_block_decompose.restype = ctypes.c_int
 _lib.ldd_create_union.argtypes = [ctypes.c_int, _vp, ctypes.POINTER(_vp)]
 _lib.ldd_create_union.restype = ctypes.c_int
 _lib.ldd_union_size.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]
@@ -253,6 +256,33 @@ def ldd_decompose_batch(g: int, betas, shifts, out_center, out_dist, n: int | No
     return [int(cuts[i]) for i in range(k)] if want_cut else None
 
 
+def ldd_block_decompose(g: int, betas, shifts, out_center=None, out_dist=None,
+                        out_arc_block=None, n: int | None = None, nnz: int | None = None):
+    """Blocks by repeated decomposition (include/ldd.h).  shifts: k buffers;
+    out_center / out_dist: None or k buffers; out_arc_block: None or an int32
+    buffer of nnz.  Returns (blocks, remaining) with remaining[i] the edges of
+    G_i for i = 0 .. blocks."""
+    k = len(betas)
+    if len(shifts) != k:
+        raise ValueError("betas and shifts need the same length")
+    for name, arr in (("out_center", out_center), ("out_dist", out_dist)):
+        if arr is not None and len(arr) != k:
+            raise ValueError(f"{name} needs {k} buffers")
+    b = (ctypes.c_double * max(k, 1))(*[float(x) for x in betas])
+    sp = (_vp * max(k, 1))(*[_addr(x, "f64", n, "shifts") for x in shifts])
+    cp = None if out_center is None else (_vp * max(k, 1))(
+        *[_addr(x, "i32", n, "out_center") for x in out_center])
+    dp = None if out_dist is None else (_vp * max(k, 1))(
+        *[_addr(x, "i32", n, "out_dist") for x in out_dist])
+    rem = (_i64 * (k + 1))()
+    blocks = _i32(0)
+    _check(_lib.ldd_block_decompose(g, k, b, sp, cp, dp,
+                                    _addr(out_arc_block, "i32", nnz, "out_arc_block"), rem,
+                                    ctypes.byref(blocks)), "ldd_block_decompose")
+    nb = int(blocks.value)
+    return nb, [int(rem[i]) for i in range(nb + 1)]
+
+
 def ldd_create_union(members) -> int:
     """Handle of the disjoint union of the member graphs (handles or LddGraph)."""
     hs = [getattr(m, "handle", m) for m in members]
@@ -405,6 +435,11 @@ class LddGraph:
 
     def cut_edges(self, center) -> int:
         return ldd_cut_edges(self.handle, center, self.n)
+
+    def block_decompose(self, betas, shifts, out_center=None, out_dist=None,
+                        out_arc_block=None):
+        return ldd_block_decompose(self.handle, betas, shifts, out_center, out_dist,
+                                   out_arc_block, self.n, self.nnz)
 
     def set_stream(self, stream) -> None:
         ldd_set_stream(self.handle, stream)

@@ -13,7 +13,7 @@ OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libldd.so")
 HEADER = os.path.join(ROOT, "include", "ldd.h")
 SOURCES = ["ldd_api.cu", "k_rank.cu", "k_bfs.cu", "k_graph.cu", "k_cut_noalloc.cu", "k_union.cu",
-           "ldd_server.cu"]
+           "ldd_server.cu", "ldd_blocks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

@@ -400,6 +400,183 @@ __global__ void __launch_bounds__(256) k_max_i32(const int* __restrict__ x, u32 
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
+// ---------------------------------------------------------------- residual graphs
+// Blocks by repeated decomposition (Section 1's remark on Linial and Saks'
+// block decompositions): after decomposing G_i, the arcs whose two ends
+// share a piece form block i, and the others make up G_{i+1}.  Two passes
+// over the arcs of G_i.  The count pass counts every vertex's kept arcs (and
+// the kept arcs (v, w) with v < w: the undirected edges left) and stamps the
+// block number on the other arcs; after an exclusive scan of the counts gives
+// G_{i+1}'s row offsets, the write pass writes the kept arcs with their input
+// arc ids and hooks each kept (v, w), v < w, into the union-find forest of
+// G_{i+1}'s components.  Row order inside a row is free, and only the rows
+// walked by one thread or one warp keep it.
+//   * A warp takes 32 consecutive vertices, one per lane; a lane walks a row
+//     of at most kResShort arcs alone.
+//   * Rows of up to kResWarp arcs are walked by the whole warp, kResUnroll
+//     chunks of 32 arcs per step (loads of all chunks first), a ballot giving
+//     every kept arc its place.
+//   * Longer rows (R-MAT hubs) are listed by the count pass and walked by one
+//     CTA each (k_residual_long), which reserves places with a shared counter.
+constexpr int kResShort = 32;
+constexpr int kResWarp = 4096;
+constexpr int kResUnroll = 4;
+constexpr int kResLongThreads = 512;
+
+struct ResArgs {
+  const int* row;
+  const int* col;
+  const int* orig;       // input arc id of every arc (null: the arcs are the input's)
+  const int* center;
+  u32 n;
+  int block;
+  int* arc_block;        // null: not recorded
+  u32* kept;             // count pass: kept arcs per vertex
+  unsigned long long* up_kept;
+  u32* long_rows;        // vertices with more than kResWarp arcs (count pass lists them)
+  u32* n_long;
+  const int* new_row;    // write pass
+  int* new_col;
+  int* new_orig;
+  u32* parent;
+};
+
+template <bool kWrite>
+__device__ __forceinline__ void res_arc(const ResArgs& a, u32 v, u32 w, int e, bool keep, int at,
+                                        u32& up) {
+  if (keep) {
+    if (v < w) ++up;
+    if (kWrite) {
+      a.new_col[at] = (int)w;
+      a.new_orig[at] = a.orig ? a.orig[e] : e;
+      if (v < w) cc_unite(a.parent, w, v);
+    }
+  } else if (!kWrite && a.arc_block) {
+    a.arc_block[a.orig ? a.orig[e] : e] = a.block;
+  }
+}
+
+template <bool kWrite>
+__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
+  const u32 lane = threadIdx.x & 31;
+  const u32 warps = gridDim.x * (blockDim.x / 32);
+  u32 up = 0;
+  for (u32 base = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < a.n;
+       base += warps * 32) {
+    const u32 v = base + lane;
+    int e0 = 0, e1 = 0, cv = 0, out = 0;
+    if (v < a.n) {
+      e0 = a.row[v];
+      e1 = a.row[v + 1];
+      cv = a.center[v];
+      if (kWrite) out = a.new_row[v];
+    }
+    const int deg = e1 - e0;
+    u32 cnt = 0;
+    if (deg <= kResShort) {
+      for (int e = e0; e < e1; ++e) {
+        const u32 w = (u32)a.col[e];
+        const bool keep = w < a.n && a.center[w] != cv;
+        res_arc<kWrite>(a, v, w, e, keep, out, up);
+        if (keep) {
+          ++cnt;
+          ++out;
+        }
+      }
+    } else if (deg > kResWarp && !kWrite) {
+      a.long_rows[atomicAdd(a.n_long, 1u)] = v;  // k_residual_long takes it
+    }
+    u32 lm = __ballot_sync(kFull, deg > kResShort && deg <= kResWarp);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const u32 sv = __shfl_sync(kFull, v, src);
+      const int b0 = __shfl_sync(kFull, e0, src), b1 = __shfl_sync(kFull, e1, src);
+      const int scv = __shfl_sync(kFull, cv, src);
+      int pos = __shfl_sync(kFull, out, src);
+      u32 c = 0;
+      for (int step = b0; step < b1; step += 32 * kResUnroll) {
+        u32 w[kResUnroll];
+        int cw[kResUnroll];
+#pragma unroll
+        for (int q = 0; q < kResUnroll; ++q) {
+          const int e = step + q * 32 + (int)lane;
+          w[q] = e < b1 ? (u32)a.col[e] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int q = 0; q < kResUnroll; ++q) cw[q] = w[q] < a.n ? a.center[w[q]] : scv;
+#pragma unroll
+        for (int q = 0; q < kResUnroll; ++q) {
+          const int e = step + q * 32 + (int)lane;
+          const bool in = e < b1;
+          const bool keep = in && w[q] < a.n && cw[q] != scv;
+          const u32 km = __ballot_sync(kFull, keep);
+          if (in) res_arc<kWrite>(a, sv, w[q], e, keep, pos + __popc(km & lanemask_lt()), up);
+          pos += __popc(km);
+          c += __popc(km);
+        }
+      }
+      if ((int)lane == src) cnt = c;
+    }
+    if (!kWrite && v < a.n && deg <= kResWarp) a.kept[v] = cnt;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(kFull, up, o);
+  if (!kWrite && lane == 0 && up) atomicAdd(a.up_kept, (unsigned long long)up);
+}
+
+// One CTA per listed long row (more than kResWarp arcs), both passes.
+template <bool kWrite>
+__global__ void __launch_bounds__(kResLongThreads) k_residual_long(ResArgs a) {
+  __shared__ u32 s_cnt, s_up;
+  const u32 nl = *a.n_long;
+  for (u32 i = blockIdx.x; i < nl; i += gridDim.x) {
+    const u32 v = a.long_rows[i];
+    const int e0 = a.row[v], e1 = a.row[v + 1];
+    const int cv = a.center[v];
+    if (threadIdx.x == 0) {
+      s_cnt = 0;
+      s_up = 0;
+    }
+    __syncthreads();
+    const int out = kWrite ? a.new_row[v] : 0;
+    u32 up = 0;
+    for (int step = e0; step < e1; step += kResLongThreads * kResUnroll) {
+      u32 w[kResUnroll];
+      int cw[kResUnroll];
+#pragma unroll
+      for (int q = 0; q < kResUnroll; ++q) {
+        const int e = step + q * kResLongThreads + (int)threadIdx.x;
+        w[q] = e < e1 ? (u32)a.col[e] : 0xffffffffu;
+      }
+#pragma unroll
+      for (int q = 0; q < kResUnroll; ++q) cw[q] = w[q] < a.n ? a.center[w[q]] : cv;
+#pragma unroll
+      for (int q = 0; q < kResUnroll; ++q) {
+        const int e = step + q * kResLongThreads + (int)threadIdx.x;
+        const bool keep = e < e1 && w[q] < a.n && cw[q] != cv;
+        const u32 km = __ballot_sync(kFull, keep);
+        int at = 0;
+        if (km) {  // one place reservation per warp step
+          u32 wb = 0;
+          if ((threadIdx.x & 31) == (u32)(__ffs(km) - 1)) wb = atomicAdd(&s_cnt, __popc(km));
+          at = out + (int)__shfl_sync(kFull, wb, __ffs(km) - 1) + __popc(km & lanemask_lt());
+        }
+        if (e < e1) res_arc<kWrite>(a, v, w[q], e, keep, at, up);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(kFull, up, o);
+    if ((threadIdx.x & 31) == 0 && up) atomicAdd(&s_up, up);
+    __syncthreads();
+    if (!kWrite && threadIdx.x == 0) {
+      a.kept[v] = s_cnt;
+      if (s_up) atomicAdd(a.up_kept, (unsigned long long)s_up);
+    }
+    __syncthreads();
+  }
+}
+
 u32 grid_for(u32 n, int num_sms) {
   return (u32)max(1ll, min((long long)(n + 255) / 256, (long long)num_sms * 8));
 }
@@ -468,10 +645,8 @@ int launch_small_comp(const SmallComps& sc, u64* key, const u32* err, int num_sm
   return 1;
 }
 
-cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 n, int num_sms,
-                              const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
-                              cudaStream_t s) {
-  const u32 g = grid_for(n, num_sms);
+cudaError_t components_init(u32 n, int num_sms, const CompScratch& t, u32* excl, u32* solo,
+                            cudaStream_t s) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(t.csize, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(t.fill, 0, (size_t)n * 4, s)) != cudaSuccess) return e;
@@ -479,8 +654,23 @@ cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 
   if ((e = cudaMemsetAsync(t.lane_of, 0xff, (size_t)n * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(excl, 0, ((size_t)n + 31) / 32 * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(solo, 0, ((size_t)n + 31) / 32 * 4, s)) != cudaSuccess) return e;
-  k_iota<<<g, 256, 0, s>>>(t.parent, n);
+  k_iota<<<grid_for(n, num_sms), 256, 0, s>>>(t.parent, n);
+  return cudaGetLastError();
+}
+
+cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 n, int num_sms,
+                              const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
+                              cudaStream_t s) {
+  cudaError_t e = components_init(n, num_sms, t, excl, solo, s);
+  if (e != cudaSuccess) return e;
   if (m_up > 0) k_cc_hook<<<grid_for(m_up, num_sms), 256, 0, s>>>(up, m_up, t.parent);
+  return components_label(row_ptr, n, num_sms, t, excl, solo, counts, s);
+}
+
+cudaError_t components_label(const int* row_ptr, u32 n, int num_sms, const CompScratch& t,
+                             u32* excl, u32* solo, u32 counts[4], cudaStream_t s) {
+  const u32 g = grid_for(n, num_sms);
+  cudaError_t e;
   k_cc_finish<<<g, 256, 0, s>>>(t.parent, t.csize, n);
   k_small_roots<<<g, 256, 0, s>>>(t.parent, t.csize, n, t.root_off, t.comp_off, t.comp_len,
                                   t.counters);
@@ -490,6 +680,23 @@ cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 
     return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
+}
+
+int launch_residual(bool write, const int* row, const int* col, const int* orig,
+                    const int* center, u32 n, int block, int* arc_block, u32* kept,
+                    unsigned long long* up_kept, u32* long_rows, u32* n_long, const int* new_row,
+                    int* new_col, int* new_orig, u32* parent, int num_sms, cudaStream_t s) {
+  ResArgs a{row,      col,      orig,   center,  n,       block,   arc_block, kept,
+            up_kept,  long_rows, n_long, new_row, new_col, new_orig, parent};
+  const u32 blocks = (u32)max(1ll, min(((long long)n + 255) / 256, (long long)num_sms * 8));
+  if (write) {
+    k_residual<true><<<blocks, 256, 0, s>>>(a);
+    k_residual_long<true><<<num_sms, kResLongThreads, 0, s>>>(a);
+  } else {
+    k_residual<false><<<blocks, 256, 0, s>>>(a);
+    k_residual_long<false><<<num_sms, kResLongThreads, 0, s>>>(a);
+  }
+  return 2;
 }
 
 cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,

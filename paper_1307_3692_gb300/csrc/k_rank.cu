@@ -1077,6 +1077,15 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
   return launches + 5;
 }
 
+int launch_exclusive_scan(u32* data, u32 len, u64* status, u32* epoch, u32* tile_ctr,
+                          Control* ctl, u32 spin_limit, cudaStream_t s) {
+  const u32 tiles = (len + kScanTile - 1) / kScanTile;
+  if (tiles == 0) return 0;
+  k_scan_excl<<<tiles, kScanThreads, 0, s>>>(data, nullptr, len, 0, status, ++(*epoch), tile_ctr,
+                                             nullptr, nullptr, 0, ctl, spin_limit, 0);
+  return 1;
+}
+
 int launch_ranked_and_buckets(const RankBufs& r, const int* levels, const int* perm,
                               cudaStream_t s) {
   const u32 n = r.n;

@@ -77,6 +77,7 @@ void record_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error)
 namespace ldd {
 
 int free_graph_memory(ldd_graph* g) {
+  free_blocks(g);
   cudaFree(g->d_row);
   cudaFree(g->d_col);
   cudaFree(g->cut.hot);

@@ -1,0 +1,277 @@
+// ldd_block_decompose: blocks by repeated low-diameter decomposition.
+//
+// Section 1 (related work) of Miller, Peng, Xu 2013 notes that the block
+// decomposition of Linial and Saks -- O(log n) blocks whose connected pieces
+// have diameter O(log n) -- follows from running a (1/2, O(log n))
+// decomposition again and again on the edges not yet in a block: each run
+// cuts at most half of what is left in expectation (Corollary 3.5 bounds the
+// fraction by 1 - e^{-beta}).  Iteration i decomposes G_i = (V, E_i) with the
+// caller's shift vector i; the edges of E_i whose two ends share a piece form
+// block i, and the cut ones are E_{i+1}.
+//
+// Everything stays on the device.  G_0 is the graph itself.  After
+// decomposition i, two passes over G_i's arcs (k_residual in k_graph.cu)
+// stamp block i on the arcs inside pieces and write the kept arcs, with their
+// input arc ids, as G_{i+1}'s CSR; the write pass also hooks G_{i+1}'s
+// union-find forest, so its component tables (the small-component solver and
+// the round loop's exclusion bits) follow without another pass over the
+// arcs.  G_1, G_2, ... share one graph object with ping-pong CSR buffers, all
+// sized by the input, allocated on the first call and kept on the input
+// graph until it is destroyed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "../../include/ldd.h"
+#include "ldd_graph.cuh"
+
+namespace ldd {
+
+struct Blocks {
+  ldd_graph* r = nullptr;      // graph object of G_i, i >= 1
+  int* row[2] = {};            // [n + 1]: kept-arc counts, then G_{i+1}'s row offsets
+  int* col[2] = {};            // [nnz]
+  int* orig[2] = {};           // [nnz] input arc id of every arc of G_i
+  int* arc_block = nullptr;    // [nnz] block of every input arc (when the caller's is not on the device)
+  u32* tmp = nullptr;          // union-find and component scratch
+  CompScratch t{};
+  unsigned long long* up = nullptr;  // undirected edges left (device counter)
+  u32* long_rows = nullptr;    // [n] rows the count pass leaves to one CTA each
+  u32* n_long = nullptr;
+  unsigned long long* h_up = nullptr;  // pinned: [0] edges left, [1] arcs left
+};
+
+void free_blocks(ldd_graph* g) {
+  Blocks* b = g->blk;
+  if (!b) return;
+  if (b->r) {
+    // the CSR and the small-component lists belong to b, not to r
+    b->r->d_row = nullptr;
+    b->r->d_col = nullptr;
+    b->r->sc.comp_off = b->r->sc.comp_len = b->r->sc.comp_v = nullptr;
+    free_graph_memory(b->r);
+    delete b->r;
+  }
+  for (int j = 0; j < 2; ++j) {
+    cudaFree(b->row[j]);
+    cudaFree(b->col[j]);
+    cudaFree(b->orig[j]);
+  }
+  cudaFree(b->arc_block);
+  cudaFree(b->tmp);
+  cudaFree(b->up);
+  cudaFree(b->long_rows);
+  cudaFree(b->n_long);
+  if (b->h_up) cudaFreeHost(b->h_up);
+  delete b;
+  g->blk = nullptr;
+}
+
+namespace {
+
+int setup_blocks(ldd_graph* g) {
+  if (g->blk) return LDD_OK;
+  Blocks* b = new (std::nothrow) Blocks();
+  if (!b) return fail(LDD_ERR_OOM, "host allocation failed");
+  g->blk = b;
+  const size_t n = (size_t)g->n, nnz = std::max<size_t>((size_t)g->nnz, 1);
+  const size_t words = std::max<size_t>((n + 31) / 32, 1);
+  bool ok = true;
+  for (int j = 0; j < 2; ++j)
+    ok = ok && cudaMalloc(&b->row[j], (n + 1) * 4) == cudaSuccess &&
+         cudaMalloc(&b->col[j], nnz * 4) == cudaSuccess &&
+         cudaMalloc(&b->orig[j], nnz * 4) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->arc_block, nnz * 4) == cudaSuccess &&
+       cudaMalloc(&b->tmp, (7 * n + 2 * (n / 2 + 1) + 4) * 4) == cudaSuccess &&
+       cudaMalloc(&b->up, sizeof(unsigned long long)) == cudaSuccess &&
+       cudaMalloc(&b->long_rows, std::max<size_t>(n, 1) * 4) == cudaSuccess &&
+       cudaMalloc(&b->n_long, 4) == cudaSuccess &&
+       cudaMallocHost(&b->h_up, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_blocks(g);
+    return fail(LDD_ERR_OOM, "device allocation for the block decomposition failed");
+  }
+  CompScratch& t = b->t;
+  t.parent = b->tmp;
+  t.csize = b->tmp + n;
+  t.root_off = b->tmp + 2 * n;
+  t.fill = b->tmp + 3 * n;
+  t.lane_of = b->tmp + 4 * n;
+  t.comp_v = b->tmp + 5 * n;
+  t.comp_off = b->tmp + 6 * n;
+  t.comp_len = t.comp_off + (n / 2 + 1);
+  t.counters = t.comp_len + (n / 2 + 1);
+  // the residual graph object: sizes of the input (upper bounds), own scratch
+  ldd_graph* r = new (std::nothrow) ldd_graph();
+  if (!r) {
+    free_blocks(g);
+    return fail(LDD_ERR_OOM, "host allocation failed");
+  }
+  b->r = r;
+  memset(&r->stats, 0, sizeof(r->stats));
+  r->n = g->n;
+  r->nnz = g->nnz;
+  r->device = g->device;
+  r->num_sms = g->num_sms;
+  if (cudaMalloc(&r->d_excl, 2 * words * 4) != cudaSuccess ||
+      cudaMalloc(&r->sc.adj, std::max<size_t>(n, 1) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    free_blocks(g);
+    return fail(LDD_ERR_OOM, "device allocation for the block decomposition failed");
+  }
+  r->d_solo = r->d_excl + words;
+  int rc = finish_setup(r);
+  if (rc != LDD_OK) {
+    free_blocks(g);
+    return rc;
+  }
+  return LDD_OK;
+}
+
+// The residual graph object takes the input graph's stream and launch
+// parameters (tuning and wait limits) for the coming iterations.
+void sync_params(ldd_graph* g, ldd_graph* r) {
+  r->stream = g->stream;
+  r->timing = false;
+  r->spin_limit = g->spin_limit;
+  r->lookback_limit = g->lookback_limit;
+  r->stall_barrier = g->stall_barrier;
+  r->stall_lookback = g->stall_lookback;
+  r->pull_alpha = g->pull_alpha;
+  r->pull_beta = g->pull_beta;
+  r->pull_gamma = g->pull_gamma;
+  r->probe_min_arcs = g->probe_min_arcs;
+}
+
+}  // namespace
+}  // namespace ldd
+
+extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
+                                   const double* const* shifts, int32_t* const* out_center,
+                                   int32_t* const* out_dist, int32_t* out_arc_block,
+                                   int64_t* out_remaining, int32_t* out_blocks) {
+  using namespace ldd;
+  record_error("");  // this call's failures only
+  if (out_blocks) *out_blocks = 0;
+  if (!g || !out_blocks) return fail(LDD_ERR_ARG, "NULL graph or out_blocks");
+  if (g->uni) return fail(LDD_ERR_ARG, "a union graph has no block decomposition");
+  if (k < 0) return fail(LDD_ERR_ARG, "k = %d is negative", k);
+  if (k > 0 && (!betas || !shifts)) return fail(LDD_ERR_ARG, "NULL betas or shifts");
+  for (int i = 0; i < k; ++i) {
+    if (!(betas[i] > 0.0) || isinf(betas[i]))
+      return fail(LDD_ERR_ARG, "betas[%d] must be finite and > 0", i);
+    if (g->n > 0 && !shifts[i]) return fail(LDD_ERR_ARG, "shifts[%d] is NULL", i);
+    if (g->n > 0 && out_center && !out_center[i])
+      return fail(LDD_ERR_ARG, "out_center[%d] is NULL", i);
+    if (g->n > 0 && out_dist && !out_dist[i]) return fail(LDD_ERR_ARG, "out_dist[%d] is NULL", i);
+  }
+  if (out_remaining) out_remaining[0] = (int64_t)g->m_up;
+  if (g->n == 0 || g->nnz == 0 || k == 0) return LDD_OK;
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(LDD_ERR_CUDA, "cannot select device %d", g->device);
+  int rc = setup_blocks(g);
+  if (rc != LDD_OK) return rc;
+  Blocks& B = *g->blk;
+  ldd_graph* r = B.r;
+  sync_params(g, r);
+  cudaStream_t s = g->stream;
+  const size_t n = (size_t)g->n;
+  const bool dev_blk = out_arc_block && is_device_ptr(out_arc_block);
+  int* arc_block = dev_blk ? out_arc_block : B.arc_block;
+  CUDA_TRY(cudaMemsetAsync(arc_block, 0xff, (size_t)g->nnz * 4, s));
+  ldd_graph* cur = g;  // G_i
+  const int* cur_row = g->d_row;
+  const int* cur_col = g->d_col;
+  const int* cur_orig = nullptr;  // G_0's arcs are the input arcs
+  int blocks = 0;
+  for (int i = 0; i < k; ++i) {
+    // decomposition i of G_i
+    const double* d_shift = shifts[i];
+    if (!is_device_ptr(shifts[i])) {
+      CUDA_TRY(cudaMemcpyAsync(cur->d_shift, shifts[i], n * 8, cudaMemcpyHostToDevice, s));
+      d_shift = cur->d_shift;
+    }
+    const bool dev_c = out_center && is_device_ptr(out_center[i]);
+    const bool dev_d = out_dist && is_device_ptr(out_dist[i]);
+    int* center = dev_c ? out_center[i] : cur->d_center;
+    int* dist = dev_d ? out_dist[i] : cur->d_dist;
+    int launches = 0;
+    if ((rc = decompose_on_device(cur, d_shift, center, dist, &launches)) != LDD_OK) {
+      cudaStreamSynchronize(s);
+      *out_blocks = blocks;
+      return rc;
+    }
+    if (out_center && !dev_c)
+      CUDA_TRY(cudaMemcpyAsync(out_center[i], center, n * 4, cudaMemcpyDeviceToHost, s));
+    if (out_dist && !dev_d)
+      CUDA_TRY(cudaMemcpyAsync(out_dist[i], dist, n * 4, cudaMemcpyDeviceToHost, s));
+    blocks = i + 1;
+    // block i and G_{i+1}; r's control block and look-back words serve the scan
+    const int j = i & 1;
+    CUDA_TRY(cudaMemsetAsync(r->d_ctl, 0, sizeof(Control), s));
+    CUDA_TRY(cudaMemsetAsync(B.row[j] + n, 0, 4, s));
+    CUDA_TRY(cudaMemsetAsync(B.up, 0, sizeof(unsigned long long), s));
+    CUDA_TRY(cudaMemsetAsync(B.n_long, 0, 4, s));
+    if (r->epoch > 0xfffff000u) {
+      CUDA_TRY(cudaMemsetAsync(r->d_status, 0, r->status_bytes, s));
+      r->epoch = 0;
+    }
+    launch_residual(false, cur_row, cur_col, cur_orig, center, (u32)n, i, arc_block,
+                    reinterpret_cast<u32*>(B.row[j]), B.up, B.long_rows, B.n_long, nullptr,
+                    nullptr, nullptr, nullptr, g->num_sms, s);
+    launch_exclusive_scan(reinterpret_cast<u32*>(B.row[j]), (u32)n + 1, r->d_status, &r->epoch,
+                          &r->d_ctl->tile_ctr[0], r->d_ctl, r->lookback_limit, s);
+    CUDA_TRY(cudaMemcpyAsync(B.h_up, B.up, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(B.h_up + 1, B.row[j] + n, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(r->h_hdr, r->d_ctl, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));
+    u32 err;
+    memcpy(&err, r->h_hdr, 4);
+    if (err) {
+      *out_blocks = blocks;
+      return (err & kErrTimeout) ? fail(LDD_ERR_TIMEOUT, "a device-side wait ran out")
+                                 : fail(LDD_ERR_CUDA, "device error bits 0x%x", err);
+    }
+    const u64 edges_left = B.h_up[0];
+    const u64 arcs_left = (u32)B.h_up[1];
+    if (out_remaining) out_remaining[i + 1] = (int64_t)edges_left;
+    if (arcs_left == 0 || i + 1 == k) break;
+    // G_{i+1}: arcs, component forest, component tables
+    cudaError_t e = components_init((u32)n, g->num_sms, B.t, r->d_excl, r->d_solo, s);
+    if (e != cudaSuccess) return fail(LDD_ERR_CUDA, "component set-up: %s", cudaGetErrorString(e));
+    launch_residual(true, cur_row, cur_col, cur_orig, center, (u32)n, i, nullptr, nullptr,
+                    nullptr, B.long_rows, B.n_long, B.row[j], B.col[j], B.orig[j], B.t.parent,
+                    g->num_sms, s);
+    u32 counts[4] = {0, 0, 0, 0};
+    e = components_label(B.row[j], (u32)n, g->num_sms, B.t, r->d_excl, r->d_solo, counts, s);
+    if (e != cudaSuccess) return fail(LDD_ERR_CUDA, "component labelling: %s", cudaGetErrorString(e));
+    r->sc.ncomp = counts[0];
+    r->sc.total = counts[1];
+    r->sc.comp_off = B.t.comp_off;
+    r->sc.comp_len = B.t.comp_len;
+    r->sc.comp_v = B.t.comp_v;
+    r->n_active = counts[2];
+    r->nnz_active = counts[3];
+    r->m_up = (u32)edges_left;
+    r->d_row = B.row[j];
+    r->d_col = B.col[j];
+    if ((e = components_phase2(r->d_row, r->d_col, B.t, r->sc, g->num_sms, s)) != cudaSuccess)
+      return fail(LDD_ERR_CUDA, "component adjacency: %s", cudaGetErrorString(e));
+    cur = r;
+    cur_row = B.row[j];
+    cur_col = B.col[j];
+    cur_orig = B.orig[j];
+  }
+  if (out_arc_block && !dev_blk)
+    CUDA_TRY(cudaMemcpyAsync(out_arc_block, arc_block, (size_t)g->nnz * 4, cudaMemcpyDeviceToHost,
+                             s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *out_blocks = blocks;
+  return LDD_OK;
+}

@@ -13,6 +13,8 @@
 
 namespace ldd {
 
+// Sets the text ldd_last_error() returns on this thread.
+void record_error(const char* msg);
 // Sets the thread's ldd_last_error() text and returns status.
 int fail(int status, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 
@@ -53,6 +55,7 @@ struct UnionCaps {
   u64 total = 0;  // caller-layout entries (sum of member sizes)
   u32 k = 0;      // members
 };
+struct Blocks;  // state of ldd_block_decompose (ldd_blocks.cu)
 }  // namespace ldd
 
 using namespace ldd;
@@ -147,6 +150,9 @@ struct ldd_graph {
     u32* d_mrank = nullptr;        // [3][k] the round loop's per-member bottom-up floors
   };
   Union* uni = nullptr;
+  // block decomposition (ldd_block_decompose, ldd_blocks.cu): residual graphs,
+  // created on the first call
+  ldd::Blocks* blk = nullptr;
   // captured CUDA graph of one fast-path decomposition (ldd_set_graph_replay)
   bool replay = false;
   bool replay_broken = false;        // capture failed once: regular path only
@@ -162,6 +168,13 @@ namespace ldd {
 
 // Frees every device and host resource of g (not g itself).
 int free_graph_memory(ldd_graph* g);
+// Scratch arena, pinned header, events and launch parameters of a graph whose
+// sizes (n, nnz, device, num_sms) are set (ldd_api.cu).
+int finish_setup(ldd_graph* g);
+// The block decomposition's state of g (ldd_blocks.cu); null is a no-op.
+void free_blocks(ldd_graph* g);
+void record(ldd_graph* g, int i);
+float elapsed(ldd_graph* g, int a, int b);
 // One decomposition on g's stream from device shifts into device outputs
 // (union: caller layout), with the fast rank path's retries; synchronises.
 // d_levels, d_perm: the ranked variant (integer levels and a tie-break

@@ -249,6 +249,28 @@ int launch_max_dist(const int* dist, u32 n, u32* out, int num_sms, cudaStream_t 
 cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 n, int num_sms,
                               const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
                               cudaStream_t s);
+// components_phase1 in parts, for a caller that hooks the forest itself:
+// components_init clears the tables and makes every vertex its own root
+// (t.parent); components_label then labels the hooked forest as phase 1 does.
+cudaError_t components_init(u32 n, int num_sms, const CompScratch& t, u32* excl, u32* solo,
+                            cudaStream_t s);
+cudaError_t components_label(const int* row_ptr, u32 n, int num_sms, const CompScratch& t,
+                             u32* excl, u32* solo, u32 counts[4], cudaStream_t s);
+// Residual graphs of the block decomposition (k_graph.cu).  Count pass
+// (write = false): kept[v] = arcs of v whose ends have different centers;
+// *up_kept += those with v < w; arc_block[orig ? orig[e] : e] = block for the
+// other arcs (arc_block may be null); rows of more than 4096 arcs are listed
+// in long_rows (*n_long zero on entry; room for every vertex).  Write pass:
+// the kept arcs at new_row[v] .., with their input arc ids, each kept (v, w),
+// v < w, hooked into parent (union-find); the order inside long rows is free.
+int launch_residual(bool write, const int* row, const int* col, const int* orig,
+                    const int* center, u32 n, int block, int* arc_block, u32* kept,
+                    unsigned long long* up_kept, u32* long_rows, u32* n_long, const int* new_row,
+                    int* new_col, int* new_orig, u32* parent, int num_sms, cudaStream_t s);
+// Exclusive scan of data[0 .. len) in place (k_rank.cu; decoupled look-back
+// on status words tagged with ++*epoch; tile_ctr zero on entry).
+int launch_exclusive_scan(u32* data, u32 len, u64* status, u32* epoch, u32* tile_ctr,
+                          Control* ctl, u32 spin_limit, cudaStream_t s);
 // Adjacency masks of the small-component members (sc.comp_v already filled).
 cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,
                               const SmallComps& sc, int num_sms, cudaStream_t s);

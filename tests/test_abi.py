@@ -51,6 +51,13 @@ def test_argument_errors_need_no_device(ldd):
     lib.ldd_decompose_batch.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5
     assert lib.ldd_decompose_batch(None, 1, None, None, None, None, None) == ldd.LDD_ERR_ARG
     assert lib.ldd_set_stream(None, None) == ldd.LDD_ERR_ARG
+    lib.ldd_block_decompose.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 7
+    blocks = ctypes.c_int32(-1)
+    assert lib.ldd_block_decompose(None, 1, None, None, None, None, None, None,
+                                   ctypes.byref(blocks)) == ldd.LDD_ERR_ARG
+    assert blocks.value == 0
+    lib.ldd_set_wait_limits.argtypes = [ctypes.c_void_p] * 2
+    assert lib.ldd_set_wait_limits(None, None) == ldd.LDD_ERR_ARG
     lib.ldd_create_union.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.ldd_union_size.argtypes = [ctypes.c_void_p] * 3
     lib.ldd_union_decompose.argtypes = [ctypes.c_void_p] * 6
