@@ -418,6 +418,10 @@ typedef struct {
   int32_t pull_gamma;        /* ... and bottom-up only when frontier arcs x gamma > BFS vertices */
   int32_t probe_min_arcs;    /* top-down rounds with at least this many arcs read a key
                                 before its atomicMin */
+  int32_t low_degree_rounds; /* 1: when every vertex has at most 32 arcs, run the
+                                low-degree rounds (the frontier a plain vertex list, one
+                                thread per vertex, the next start bucket checked in the
+                                same pass); 0: the edge-balanced rounds always */
   float ms;                  /* ldd_autotune: the best decomposition time seen, ms */
 } ldd_tuning;
 
@@ -429,7 +433,7 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t);
  * ldd_autotune -- pick g's launch parameters for this workload by timing
  * decompositions (CUDA events on g's stream, best of reps after one warm-up)
  * while trying a few values of one parameter at a time (push/pull thresholds,
- * key-probe threshold, CTAs per SM), keeping a value only for a gain of 2 %
+ * key-probe threshold, CTAs per SM, low-degree rounds), keeping a value only for a gain of 2 %
  * or more.  shifts: a representative shift vector (n doubles; a union's
  * caller-layout total), host or device.  The chosen parameters stay on g and
  * are returned in *out.  Results of later decompositions are unaffected.

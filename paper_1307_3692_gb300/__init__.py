@@ -120,7 +120,8 @@ _lib.ldd_set_timing.restype = ctypes.c_int
 class Tuning(ctypes.Structure):
     _fields_ = [("bfs_blocks_per_sm", ctypes.c_int32), ("pull_alpha", ctypes.c_int32),
                 ("pull_beta", ctypes.c_int32), ("pull_gamma", ctypes.c_int32),
-                ("probe_min_arcs", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("probe_min_arcs", ctypes.c_int32), ("low_degree_rounds", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
 
 _lib.ldd_get_tuning.argtypes = [_vp, ctypes.POINTER(Tuning)]

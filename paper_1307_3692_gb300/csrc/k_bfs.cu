@@ -59,6 +59,7 @@ constexpr int kPullCoop = 4;   // neighbours per lane per step of a warp-wide sc
 // Unions of at most this many members keep their per-member floors in shared
 // memory (two tables after Smem); larger unions use the global table directly.
 constexpr u32 kSmemMembers = 4096;
+constexpr int kLdBatch = 8;    // low-degree rounds: arcs per thread in flight
 
 struct Smem {
   int owner[kBfsMaxSpan];
@@ -171,9 +172,49 @@ __device__ __forceinline__ void flush_members(const BfsArgs& a, u32 slot, u32* s
 // (count << 32 | degree sum) over its lanes, reserves that many queue slots
 // and edge offsets, and every lane writes its vertices in slot order.
 // qi: frontier counter index (rotates over 3), qb: queue buffer (ping-pong).
+// Low-degree mode: the frontier is the list q4 of (vertex, row start, row end)
+// entries (items in the counter's high word, its low word unused).  An append
+// is one reservation per warp and one 16-byte store per vertex; its adjacency
+// range is loaded beside the reservation, not before it, so the next round
+// starts without a row_ptr round trip.
 template <int K>
+__device__ __forceinline__ void warp_append_ld(u32 mask, const u32 (&v)[K], const BfsArgs& a,
+                                               int qi, int qb) {
+  const u32 lane = threadIdx.x & 31;
+  int rs[K], re[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    rs[i] = 0;
+    re[i] = 0;
+    if (mask >> i & 1u) {
+      rs[i] = __ldg(a.row_ptr + v[i]);
+      re[i] = __ldg(a.row_ptr + v[i] + 1);
+    }
+  }
+  const u32 mine = __popc(mask);
+  u32 incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= (u32)o) incl += y;
+  }
+  const u32 tot = __shfl_sync(kFull, incl, 31);
+  if (tot == 0) return;
+  u32 base = 0;
+  if (lane == 0) base = (u32)(atomicAdd(&a.ctl->qctr[qi], (u64)tot << 32) >> 32);
+  u32 slot = __shfl_sync(kFull, base, 0) + incl - mine;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (mask >> i & 1u) a.q4[qb][slot++] = make_uint4(v[i], (u32)rs[i], (u32)re[i], 0u);
+}
+
+template <int K, bool LD>
 __device__ __forceinline__ void warp_append(u32 mask, const u32 (&v)[K], const BfsArgs& a, int qi,
                                             int qb) {
+  if (LD) {
+    warp_append_ld<K>(mask, v, a, qi, qb);
+    return;
+  }
   const u32 lane = threadIdx.x & 31;
   int rs[K], dg[K];
 #pragma unroll
@@ -241,7 +282,7 @@ __device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u3
       want = (u32)(k >> 32) == (u32)rr;
     }
     note_rank<U>(a, (u32)qi, want, u[0], (u32)k, myrank, s_acc);
-    warp_append<1>(want ? 1u : 0u, u, a, qi, qb);
+    warp_append<1, false>(want ? 1u : 0u, u, a, qi, qb);
   }
 }
 
@@ -331,9 +372,81 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
 #pragma unroll
       for (int i = 0; i < kEdgeBatch; ++i)
         note_rank<U>(a, (u32)qi, (won >> i) & 1u, w[i], (u32)cand[i], myrank, s_acc);
-      warp_append<kEdgeBatch>(mask, w, a, qi, qb);
+      warp_append<kEdgeBatch, false>(mask, w, a, qi, qb);
     }
     __syncthreads();
+  }
+}
+
+// Low-degree round (every vertex of the graph has at most kLdMaxDegree
+// arcs): one pass over Q frontier vertices (the list q_cur) and the cnt
+// entries of start bucket rb (from lo in rv), a thread per item.
+//   * A frontier vertex v offers key[v] + 2^32 to each of its neighbours
+//     (64-bit atomicMin, after a probe of the key when `probe`), kLdBatch arcs
+//     per step, and appends the neighbours whose level it lowered to lvl + 1.
+//   * A start-bucket entry u joins the next frontier if its key still has its
+//     start level rb (Section 4's delayed start; stable during the round, see
+//     the file comment).
+// A frontier entry carries v's adjacency range, so v's key and its
+// neighbours' ids load in one round trip, like the bucket entries' keys, and
+// the bucket test runs beside the expansion instead of after it: a thin round
+// is a short chain of dependent loads.  `pushed` adds
+// the arcs offered.
+template <bool U>
+__device__ __forceinline__ void expand_ld(const BfsArgs& a, const uint4* q_cur, u32 Q, u32 lvl_next,
+                                          const u32* rv, int lo, u32 cnt, u32 rb, bool probe,
+                                          int qi, int qb, u32& myrank, u32* s_acc, u64& pushed) {
+  constexpr u32 kNone = 0xffffffffu;
+  const u32 lane = threadIdx.x & 31;
+  const u32 total = Q + cnt;
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+    const u32 i = base + lane;
+    const bool front = i < Q;
+    const bool buck = !front && i < total;
+    u32 v = 0;
+    int rs = 0, re = 0;
+    if (front) {
+      const uint4 q = __ldcg(q_cur + i);
+      v = q.x;
+      rs = (int)q.y;
+      re = (int)q.z;
+    } else if (buck) {
+      v = __ldg(rv + lo + (int)(i - Q));
+    }
+    u64 kv = 0;
+    if (front || buck) kv = ld_cg_u64(a.key + v);
+    const bool start = buck && (u32)(kv >> 32) == rb;
+    const u32 sv[1] = {v};
+    note_rank<U>(a, (u32)qi, start, v, (u32)kv, myrank, s_acc);
+    warp_append<1, true>(start ? 1u : 0u, sv, a, qi, qb);
+    pushed += (u64)(re - rs);
+    const u64 cand = kv + kLevelOne;
+    int nch = (re - rs + kLdBatch - 1) / kLdBatch;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nch = max(nch, __shfl_xor_sync(kFull, nch, o));
+    for (int ch = 0; ch < nch; ++ch) {
+      const int e0 = rs + ch * kLdBatch;
+      u32 w[kLdBatch];
+#pragma unroll
+      for (int q = 0; q < kLdBatch; ++q) w[q] = (e0 + q < re) ? (u32)__ldg(a.col + e0 + q) : kNone;
+      u64 cur[kLdBatch];
+#pragma unroll
+      for (int q = 0; q < kLdBatch; ++q)
+        cur[q] = (w[q] < a.n) ? (probe ? ld_cg_u64(a.key + w[q]) : ~0ull) : 0ull;
+      u32 mask = 0, won = 0;
+#pragma unroll
+      for (int q = 0; q < kLdBatch; ++q)
+        if (cand < cur[q]) {
+          const u64 old = atomicMin(a.key + w[q], cand);
+          if (old > cand) won |= 1u << q;
+          if ((u32)(old >> 32) > lvl_next) mask |= 1u << q;
+        }
+#pragma unroll
+      for (int q = 0; q < kLdBatch; ++q)
+        note_rank<U>(a, (u32)qi, (won >> q) & 1u, w[q], (u32)cand, myrank, s_acc);
+      warp_append<kLdBatch, true>(mask, w, a, qi, qb);
+    }
   }
 }
 
@@ -344,11 +457,11 @@ __device__ __forceinline__ void post_cta_min(Smem& s, u32& myrank) {
   myrank = 0xffffffffu;
 }
 
-// Appends every v[i] with bit i of `mask` set to a plain vertex list, one
-// atomic per warp.
+// Appends (v[i], rs[i], re[i]) for every bit i of `mask` to a list of
+// bottom-up candidates with their adjacency ranges, one atomic per warp.
 template <int K>
-__device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], u32* list,
-                                                 u32* count) {
+__device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], const int (&rs)[K],
+                                                 const int (&re)[K], uint4* list, u32* count) {
   const u32 lane = threadIdx.x & 31;
   const u32 mine = __popc(mask);
   u32 incl = mine;
@@ -364,59 +477,87 @@ __device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], u3
   base = __shfl_sync(kFull, base, 0) + incl - mine;
 #pragma unroll
   for (int i = 0; i < K; ++i)
-    if (mask >> i & 1u) list[base++] = v[i];
+    if (mask >> i & 1u) list[base++] = make_uint4(v[i], (u32)rs[i], (u32)re[i], 0u);
 }
 
-// Bottom-up round from level lvl (see the file comment).  Candidates are every
-// vertex not in excl (from_list = false; a.active lists them when it is set)
-// or the list `cand` of ncand vertices.
+// Bottom-up round from level lvl (see the file comment).  Candidates are, in
+// the first bottom-up round of a run (from_list = false), the vertices the
+// BFS handles: the (vertex, row start, row end) list a.active4 of a plain
+// graph, else the id list a.active, else every vertex not in excl; in later
+// rounds the (vertex, row start, row end) list `cand` of ncand vertices that
+// the previous bottom-up round left unsettled.
 // Each lane takes kPullV candidates at a time and advances their neighbour
 // scans in lock-step, one neighbour each per step, so that up to kPullV
-// independent loads are in flight per lane.  Adds the arcs it scans and the
-// vertices it examines to the statistics.
-template <bool U>
+// independent loads are in flight per lane.  A candidate that comes with its
+// adjacency range loads its key and its first neighbour together.  Adds the
+// arcs it scans and the vertices it examines to the statistics.
+template <bool U, bool LD>
 __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minrank, u32 mslot,
-                                           int qi, int qb, bool from_list, const u32* cand,
-                                           u32 ncand, u32* ulist_out, u32* ucnt_out,
+                                           int qi, int qb, bool from_list, const uint4* cand,
+                                           u32 ncand, uint4* ulist_out, u32* ucnt_out,
                                            u32& myrank, u32* s_acc, const u32* s_floor) {
   constexpr u32 kNone = 0xffffffffu;
   u32 scanned = 0, examined = 0;
   const u32 lane = threadIdx.x & 31;
   const u32 L = (u32)lvl;
-  if (!from_list && a.active) {  // the first bottom-up round: the BFS's own vertices
+  const u32* ids = nullptr;  // id list without ranges (a union's active list)
+  if (!from_list && a.active4) {  // the first bottom-up round: the BFS's own vertices
     from_list = true;
-    cand = a.active;
+    cand = a.active4;
+    ncand = a.n_active;
+  } else if (!from_list && a.active) {
+    ids = a.active;
     ncand = a.n_active;
   }
-  const u32 total = from_list ? ncand : a.n;
+  const u32 total = (from_list || ids) ? ncand : a.n;
   const u32 stride = gridDim.x * blockDim.x * kPullV;
   for (u32 base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * kPullV; base < total;
        base += stride) {
     u32 w[kPullV];
+    int e[kPullV], re[kPullV];
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       const u32 i = base + (u32)j * 32 + lane;
       w[j] = kNone;
-      if (from_list) {
-        if (i < total) w[j] = ld_cg_u32(cand + i);
-      } else if (i < total) {
-        const u32 ex = __ldg(a.excl + (i >> 5));  // same word for the whole warp
-        if (!((ex >> lane) & 1u)) w[j] = i;
+      e[j] = 0;
+      re[j] = 0;
+      if (i < total) {
+        if (from_list) {
+          const uint4 q = __ldcg(cand + i);
+          w[j] = q.x;
+          e[j] = (int)q.y;
+          re[j] = (int)q.z;
+        } else if (ids) {
+          w[j] = ld_cg_u32(ids + i);
+        } else {
+          const u32 ex = __ldg(a.excl + (i >> 5));  // same word for the whole warp
+          if (!((ex >> lane) & 1u)) w[j] = i;
+        }
       }
     }
-    // the key and the adjacency range together: one round trip, not two
+    // the key with the adjacency range (ids) or with the first neighbour
+    // (ranges known): one round trip
     u64 kw[kPullV];
-    int e[kPullV], re[kPullV];
+    u32 first[kPullV];
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       kw[j] = 0ull;
-      e[j] = 0;
-      re[j] = 0;
+      first[j] = kNone;
       if (w[j] != kNone) {
         kw[j] = ld_cg_u64(a.key + w[j]);
-        e[j] = __ldg(a.row_ptr + w[j]);
-        re[j] = __ldg(a.row_ptr + w[j] + 1);
+        if (from_list) {
+          if (e[j] < re[j]) first[j] = (u32)__ldg(a.col + e[j]);
+        } else {
+          e[j] = __ldg(a.row_ptr + w[j]);
+          re[j] = __ldg(a.row_ptr + w[j] + 1);
+        }
       }
+    }
+    int rs0[kPullV], re0[kPullV];  // the ranges, for the list of the next bottom-up round
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      rs0[j] = e[j];
+      re0[j] = re[j];
     }
     u64 best[kPullV];
     u32 fr[kPullV];  // floor rank: nothing beats (L + 1, fr); union: w's own member's
@@ -445,7 +586,7 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
       for (int j = 0; j < kPullV; ++j) {
         vv[j] = kNone;
         if (e[j] < re[j]) {
-          vv[j] = (u32)__ldg(a.col + e[j]);
+          vv[j] = (step == 0 && from_list) ? first[j] : (u32)__ldg(a.col + e[j]);
           ++e[j];
           ++scanned;
           any = true;
@@ -512,8 +653,8 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
 #pragma unroll
     for (int j = 0; j < kPullV; ++j)
       note_rank<U>(a, (u32)qi, (won >> j) & 1u, w[j], (u32)best[j], myrank, s_acc);
-    warp_append<kPullV>(mask, w, a, qi, qb);
-    warp_list_append<kPullV>(keep, w, ulist_out, ucnt_out);
+    warp_append<kPullV, LD>(mask, w, a, qi, qb);
+    warp_list_append<kPullV>(keep, w, rs0, re0, ulist_out, ucnt_out);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -533,7 +674,7 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
 // single graphs; two give twice the warps, the best for the wide bottom-up
 // rounds of many-seed unions.  The launch parameter bfs_blocks_per_sm picks
 // the instance.
-template <bool U, int kPerSm>
+template <bool U, int kPerSm, bool LD>
 __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
@@ -559,8 +700,14 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   u32 gen = 0;
   u32 myrank = 0xffffffffu;  // this thread's smallest successful next-level rank
 
+  u64 pushed = 0;  // low-degree mode: arcs offered by this thread
   // Level 0: the vertices with the largest integer shift part start.
-  append_bucket<U>(a, 0, rv, 0, 0, myrank, s_acc);
+  if (LD) {
+    const int lo = __ldg(a.bptr), hi = __ldg(a.bptr + 1);
+    expand_ld<U>(a, nullptr, 0, 0, rv, lo, (u32)(hi - lo), 0, false, 0, 0, myrank, s_acc, pushed);
+  } else {
+    append_bucket<U>(a, 0, rv, 0, 0, myrank, s_acc);
+  }
   post_cta_min(s, myrank);
   if (s_acc) {
     __syncthreads();
@@ -582,7 +729,16 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   for (;;) {
     if (s.stop) break;  // set by the last barrier, the same for every thread of the CTA
     const u64 c = ld_cg_u64(&ctl->qctr[phase % 3]);
-    const u32 Q = (u32)(c >> 32), E = (u32)c;
+    int nb_lo = 0, nb_hi = 0;  // low-degree rounds: start bucket lvl + 1, loaded beside the counter
+    if (LD && lvl + 1 <= A) {
+      nb_lo = __ldg(a.bptr + lvl + 1);
+      nb_hi = __ldg(a.bptr + lvl + 2);
+    }
+    const u32 Q = (u32)(c >> 32);
+    // low-degree mode keeps no arc count: the frontier's arcs are estimated
+    // from the mean degree (direction choice and probe threshold only)
+    const u32 E = LD ? (u32)min((u64)Q * a.nnz_active / max(a.n_active, 1u), 0xffffffffull)
+                     : (u32)c;
     settled += Q;
     if (settled >= a.n_active) break;  // every vertex the BFS owns has its final key
     const u32 minrank = ld_cg_u32(&ctl->minrank[phase % 3]);
@@ -612,15 +768,29 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
             s_floor[m] = ld_cg_u32(a.mrank + (size_t)(phase % 3) * a.kmem + m);
           __syncthreads();
         }
-        pull_round<U>(a, lvl, minrank, phase % 3, qi, qb, was_pulling, a.ulist[phase & 1], ncand,
-                      a.ulist[(phase + 1) & 1], &ctl->ucnt[qi], myrank, s_acc, s_floor);
+        pull_round<U, LD>(a, lvl, minrank, phase % 3, qi, qb, was_pulling, a.ulist[phase & 1],
+                          ncand, a.ulist[(phase + 1) & 1], &ctl->ucnt[qi], myrank, s_acc,
+                          s_floor);
         ++pulls;
+        if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
+        if (lvl + 1 <= A) {
+          if (LD) {
+            expand_ld<U>(a, nullptr, 0, 0, rv, nb_lo, (u32)(nb_hi - nb_lo), (u32)lvl + 1, false,
+                         qi, qb, myrank, s_acc, pushed);
+          } else {
+            append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc);
+          }
+        }
+      } else if (LD) {  // expansion and start bucket lvl + 1 in one pass
+        expand_ld<U>(a, a.q4[phase & 1], Q, (u32)lvl + 1, rv, nb_lo, (u32)(nb_hi - nb_lo),
+                     (u32)lvl + 1, E >= a.probe_min_arcs, qi, qb, myrank, s_acc, pushed);
+        if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
       } else {
         expand<U>(a, s, (int)(phase & 1), Q, E, lvl, qi, qb, myrank, s_acc);
         push_arcs += E;
+        if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
+        if (lvl + 1 <= A) append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc);
       }
-      if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
-      if (lvl + 1 <= A) append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc);
       nlvl = lvl + 1;
     } else {
       if (lvl + 1 > A) break;
@@ -629,7 +799,13 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       const int rr = (int)__ldg(rk + start);  // next non-empty start bucket
       if (rr > A) break;                      // only vertices the BFS does not handle remain
       if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
-      append_bucket<U>(a, rr, rv, qi, qb, myrank, s_acc);
+      if (LD) {
+        const int lo = __ldg(a.bptr + rr), hi = __ldg(a.bptr + rr + 1);
+        expand_ld<U>(a, nullptr, 0, 0, rv, lo, (u32)(hi - lo), (u32)rr, false, qi, qb, myrank,
+                     s_acc, pushed);
+      } else {
+        append_bucket<U>(a, rr, rv, qi, qb, myrank, s_acc);
+      }
       nlvl = rr;
     }
     if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][1] = clock64();
@@ -647,9 +823,14 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       ctl->round_kind[phase] = Q == 0 ? kRoundSkip : (pulling ? kRoundPull : kRoundPush);
     }
   }
+  if (LD) {  // every thread's offered arcs (the estimate above is not a count)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pushed += __shfl_xor_sync(kFull, pushed, o);
+    if ((threadIdx.x & 31) == 0 && pushed) atomicAdd(&ctl->push_arcs, pushed);
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->pull_rounds = pulls;
-    ctl->push_arcs = push_arcs;
+    if (!LD) ctl->push_arcs = push_arcs;
     ctl->rounds = phase;
     ctl->last_level = lvl;
     ctl->items = settled;
@@ -664,9 +845,13 @@ size_t bfs_smem_bytes() { return sizeof(Smem); }
 namespace {
 size_t bfs_smem(bool u) { return sizeof(Smem) + (u ? 2 * kSmemMembers * sizeof(u32) : 0); }
 
-const void* bfs_kernel(bool u, int per_sm) {
-  if (u) return per_sm >= 2 ? (const void*)k_bfs<true, 2> : (const void*)k_bfs<true, 1>;
-  return per_sm >= 2 ? (const void*)k_bfs<false, 2> : (const void*)k_bfs<false, 1>;
+const void* bfs_kernel(bool u, int per_sm, bool ld) {
+  if (ld) {
+    if (u) return per_sm >= 2 ? (const void*)k_bfs<true, 2, true> : (const void*)k_bfs<true, 1, true>;
+    return per_sm >= 2 ? (const void*)k_bfs<false, 2, true> : (const void*)k_bfs<false, 1, true>;
+  }
+  if (u) return per_sm >= 2 ? (const void*)k_bfs<true, 2, false> : (const void*)k_bfs<true, 1, false>;
+  return per_sm >= 2 ? (const void*)k_bfs<false, 2, false> : (const void*)k_bfs<false, 1, false>;
 }
 }  // namespace
 
@@ -676,21 +861,24 @@ int bfs_grid_size(int num_sms, int* blocks_per_sm) {
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
     for (int u = 0; u < 2; ++u)
       for (int p = 1; p <= 2; ++p)
-        cudaFuncSetAttribute(bfs_kernel(u != 0, p), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bfs_smem(u != 0));
+        for (int ld = 0; ld < 2; ++ld)
+          cudaFuncSetAttribute(bfs_kernel(u != 0, p, ld != 0),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bfs_smem(u != 0));
     attr_set[dev] = true;
   }
   // the most CTAs per SM (1 or 2) that every instance built for it reaches
   int per_sm = 2;
   for (int u = 0; u < 2; ++u)
-    for (int p = 1; p <= 2; ++p) {
-      int got = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, bfs_kernel(u != 0, p), kBfsThreads,
-                                                        bfs_smem(u != 0)) != cudaSuccess)
-        return -1;
-      if (got < 1) return -1;
-      if (got < p) per_sm = min(per_sm, got);
-    }
+    for (int p = 1; p <= 2; ++p)
+      for (int ld = 0; ld < 2; ++ld) {
+        int got = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, bfs_kernel(u != 0, p, ld != 0),
+                                                          kBfsThreads, bfs_smem(u != 0)) !=
+            cudaSuccess)
+          return -1;
+        if (got < 1) return -1;
+        if (got < p) per_sm = min(per_sm, got);
+      }
   *blocks_per_sm = per_sm;
   return per_sm * num_sms;
 }
@@ -698,7 +886,8 @@ int bfs_grid_size(int num_sms, int* blocks_per_sm) {
 int launch_bfs(const BfsArgs& a, int grid, int per_sm, cudaStream_t s, cudaError_t* err) {
   BfsArgs copy = a;
   void* args[] = {&copy};
-  *err = cudaLaunchCooperativeKernel(bfs_kernel(a.mrank != nullptr, per_sm), dim3(grid),
+  *err = cudaLaunchCooperativeKernel(bfs_kernel(a.mrank != nullptr, per_sm, a.low_degree != 0),
+                                     dim3(grid),
                                      dim3(kBfsThreads), args, bfs_smem(a.mrank != nullptr), s);
   return *err == cudaSuccess ? 1 : -1;
 }

@@ -89,6 +89,7 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->cut.grp_lab);
   cudaFree(g->d_hot);
   if (!g->uni) cudaFree(g->d_active);  // a union's list lives in d_active_buf
+  cudaFree(g->d_active4);
   cudaFree(g->d_hot_center);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
@@ -175,11 +176,11 @@ int alloc_scratch(ldd_graph* g) {
       {(void**)&g->d_v[0], 4 * n},        {(void**)&g->d_v[1], 4 * n},
       {(void**)&g->d_status, g->status_bytes},
       {(void**)&g->d_order, 4 * n},       {(void**)&g->d_key, 8 * n},
-      {(void**)&g->d_qv[0], 4 * n},       {(void**)&g->d_qv[1], 4 * n},
-      {(void**)&g->d_qrow[0], 4 * n},     {(void**)&g->d_qrow[1], 4 * n},
-      {(void**)&g->d_qoff[0], 4 * n},     {(void**)&g->d_qoff[1], 4 * n},
+      // frontier queues, 16 bytes per vertex and side: (vertex, row, offset)
+      // words of the edge-balanced rounds, or the low-degree rounds' entries
+      {(void**)&g->d_qv[0], 16 * n},      {(void**)&g->d_qv[1], 16 * n},
       {(void**)&g->d_cf[0], 4 * ncf},     {(void**)&g->d_cf[1], 4 * ncf},
-      {(void**)&g->d_ulist[0], 4 * n},    {(void**)&g->d_ulist[1], 4 * n},
+      {(void**)&g->d_ulist[0], 16 * n},   {(void**)&g->d_ulist[1], 16 * n},
       {(void**)&g->d_slots, n ? fraction_slot_bytes((u32)n) : 0},
       {(void**)&g->d_center, 4 * n},      {(void**)&g->d_dist, 4 * n},
       {(void**)&g->d_ctl, sizeof(Control)},
@@ -194,6 +195,10 @@ int alloc_scratch(ldd_graph* g) {
   for (auto& p : parts) {
     *p.p = (char*)g->arena + off;
     off += align_up(p.bytes ? p.bytes : 1, 256);
+  }
+  for (int b = 0; b < 2; ++b) {
+    g->d_qrow[b] = reinterpret_cast<int*>(g->d_qv[b] + n);
+    g->d_qoff[b] = g->d_qv[b] + 2 * n;
   }
   CUDA_TRY(cudaMemset(g->d_status, 0, g->status_bytes));
   g->bptr_cap = (u32)std::min<size_t>(n + 2, 0xffffffffu);
@@ -342,18 +347,33 @@ int build_cut_list(ldd_graph* g, const std::vector<int32_t>& rp, const std::vect
 // round of a decomposition -- built only when they are at most 3/4 of all
 // vertices (else scanning every id and skipping the excluded ones is cheaper
 // than reading the list).
-int build_active_list(ldd_graph* g) {
+int build_active_list(ldd_graph* g, const std::vector<int32_t>& rp) {
   const size_t n = (size_t)g->n;
-  if (n == 0 || (size_t)g->n_active * 4 > n * 3) return LDD_OK;
+  if (n == 0 || g->n_active == 0) return LDD_OK;
   std::vector<u32> excl((n + 31) / 32);
   if (cudaMemcpy(excl.data(), g->d_excl, excl.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(LDD_ERR_CUDA, "copy of the exclusion bitmask failed");
   std::vector<u32> act;
+  std::vector<uint4> act4;
   act.reserve(g->n_active);
+  act4.reserve(g->n_active);
   for (size_t v = 0; v < n; ++v)
-    if (!((excl[v >> 5] >> (v & 31)) & 1u)) act.push_back((u32)v);
+    if (!((excl[v >> 5] >> (v & 31)) & 1u)) {
+      act.push_back((u32)v);
+      act4.push_back(make_uint4((u32)v, (u32)rp[v], (u32)rp[v + 1], 0u));
+    }
   if (act.size() != g->n_active) return fail(LDD_ERR_CUDA, "inconsistent component tables");
-  if (act.empty()) return LDD_OK;
+  // the first bottom-up round's candidates with their adjacency ranges
+  if (cudaMalloc(&g->d_active4, act4.size() * sizeof(uint4)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LDD_ERR_OOM, "device allocation of the active list failed");
+  }
+  if (cudaMemcpy(g->d_active4, act4.data(), act4.size() * sizeof(uint4), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return fail(LDD_ERR_CUDA, "upload of the active list failed");
+  // the plain id list (union members), only when it is short enough to beat
+  // a scan of every id
+  if (g->n_active * 4ull > n * 3) return LDD_OK;
   if (cudaMalloc(&g->d_active, act.size() * 4) != cudaSuccess) {
     cudaGetLastError();
     return fail(LDD_ERR_OOM, "device allocation of the active list failed");
@@ -388,11 +408,13 @@ BfsArgs bfs_args(ldd_graph* g) {
     a.qv[b] = g->d_qv[b];
     a.qrow[b] = g->d_qrow[b];
     a.qoff[b] = g->d_qoff[b];
+    a.q4[b] = reinterpret_cast<uint4*>(g->d_qv[b]);
     a.cf[b] = g->d_cf[b];
     a.ulist[b] = g->d_ulist[b];
   }
   a.excl = g->d_excl;
   a.active = g->d_active;
+  a.active4 = g->uni ? nullptr : g->d_active4;
   a.ctl = g->d_ctl;
   a.n = (u32)g->n;
   a.n_active = g->n_active;
@@ -403,6 +425,7 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.pull_beta = g->pull_beta;
   a.pull_gamma = g->pull_gamma;
   a.probe_min_arcs = g->probe_min_arcs;
+  a.low_degree = (g->low_degree_rounds && g->max_degree <= (u32)kLdMaxDegree) ? 1u : 0u;
   a.wmem = g->uni ? g->uni->d_wmem : nullptr;
   a.mrank = g->uni ? g->uni->d_mrank : nullptr;
   a.kmem = g->uni ? g->uni->k : 0;
@@ -468,6 +491,8 @@ int finish_setup(ldd_graph* g) {
   g->pull_beta = env_u32("LDD_PULL_BETA", 24);
   g->pull_gamma = env_u32("LDD_PULL_GAMMA", 8);
   g->probe_min_arcs = env_u32("LDD_PROBE_MIN_ARCS", 1u << 16);
+  const char* ldr = getenv("LDD_LOW_DEGREE_ROUNDS");  // "0": edge-balanced rounds only
+  g->low_degree_rounds = !(ldr && ldr[0] == '0' && ldr[1] == 0);
   g->stats.n = g->n;
   g->stats.nnz = g->nnz;
   g->stats.n_active = g->n_active;
@@ -893,7 +918,7 @@ u64 union_bytes(const UnionCaps& c) {
   b += 16 * c.total + 8 * c.total + 32ull * (c.k + 1) + 8ull * c.k + sizeof(UnionMember) * c.k;
   const u64 nk = std::max<u64>(N, 64);
   b += 8 * N + 4 * N + 16 * nk + 8 * N + ((N + kSortTile - 1) / kSortTile + 1) * 2048 + 4 * N +
-       8 * N + 24 * N + 8 * (c.E / kBfsBase + 2) + 8 * N + (N ? fraction_slot_bytes((u32)N) : 0) +
+       8 * N + 32 * N + 8 * (c.E / kBfsBase + 2) + 32 * N + (N ? fraction_slot_bytes((u32)N) : 0) +
        8 * N + sizeof(Control);
   b += 12 * (N + 2);
   return b;
@@ -972,6 +997,7 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
   std::vector<u32> offs(8 * K1, 0);
   bool all_active = true;
   u64 nnz_active = 0, n_active = 0;
+  u32 max_deg = 0;
   auto at = [&](int t, int i) -> u32& { return offs[(size_t)t * K1 + (size_t)i]; };
   for (int i = 0; i < k; ++i) {
     const ldd_graph* m = members[i];
@@ -984,6 +1010,7 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
     at(6, i + 1) = at(6, i) + (u32)m->n;
     at(7, i + 1) = at(7, i) + m->cut.ngrp;
     if (m->n_active > 0 && !m->d_active) all_active = false;
+    max_deg = std::max(max_deg, m->max_degree);
     nnz_active += m->nnz_active;
     n_active += m->n_active;
   }
@@ -994,6 +1021,7 @@ int union_fill(ldd_graph* g, int k, ldd_graph* const* members, cudaStream_t s, b
   g->sc.total = (u32)need.T;
   g->n_active = (u32)n_active;
   g->nnz_active = nnz_active;
+  g->max_degree = max_deg;
   g->d_active = (all_active && n_active > 0) ? U.d_active_buf : nullptr;
   U.k = (u32)k;
   U.total = (u32)need.total;
@@ -1129,6 +1157,8 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   if (rp[0] != 0 || (int64_t)rp[n] != nnz)
     return bail(fail(LDD_ERR_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] must be nnz"));
 
+  for (int32_t v = 0; v < n; ++v)
+    g->max_degree = std::max<u32>(g->max_degree, (u32)(rp[v + 1] - rp[v]));
   // The arcs (v, w) with v < w: one entry per undirected edge (cut count,
   // component labelling).
   std::vector<int2> up;
@@ -1157,8 +1187,12 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   cudaFree(d_arcs);
   if (rc != LDD_OK) return bail(rc);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
-  if ((rc = build_active_list(g)) != LDD_OK) return bail(rc);
+  if ((rc = build_active_list(g, rp)) != LDD_OK) return bail(rc);
   if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);
+  // low-degree rounds are latency-bound: a key probe before every atomicMin
+  // is one more dependent round trip, worth it only in wide rounds
+  if (g->max_degree <= (u32)kLdMaxDegree && !getenv("LDD_PROBE_MIN_ARCS"))
+    g->probe_min_arcs = 1u << 20;
   *out = g;
   return LDD_OK;
 }
@@ -1652,6 +1686,7 @@ int ldd_get_tuning(const ldd_graph* g, ldd_tuning* out) {
   out->pull_beta = (int32_t)g->pull_beta;
   out->pull_gamma = (int32_t)g->pull_gamma;
   out->probe_min_arcs = (int32_t)g->probe_min_arcs;
+  out->low_degree_rounds = g->low_degree_rounds ? 1 : 0;
   out->ms = -1.f;
   return LDD_OK;
 }
@@ -1662,7 +1697,8 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
   if (bfs_grid_size(g->num_sms, &max_per_sm) <= 0)
     return fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed");
   if (t->bfs_blocks_per_sm < 1 || t->bfs_blocks_per_sm > max_per_sm || t->pull_alpha < 0 ||
-      t->pull_beta < 1 || t->pull_gamma < 0 || t->probe_min_arcs < 0)
+      t->pull_beta < 1 || t->pull_gamma < 0 || t->probe_min_arcs < 0 ||
+      (t->low_degree_rounds != 0 && t->low_degree_rounds != 1))
     return fail(LDD_ERR_ARG, "tuning out of range (blocks per SM 1 .. %d)", max_per_sm);
   g->bfs_per_sm = t->bfs_blocks_per_sm;
   g->bfs_grid = g->bfs_per_sm * g->num_sms;
@@ -1670,6 +1706,7 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
   g->pull_beta = (u32)t->pull_beta;
   g->pull_gamma = (u32)t->pull_gamma;
   g->probe_min_arcs = (u32)t->probe_min_arcs;
+  g->low_degree_rounds = t->low_degree_rounds != 0;
   g->stats.bfs_grid = g->bfs_grid;
   drop_replay(g);  // captured kernels carry the old parameters
   return LDD_OK;
@@ -1727,7 +1764,9 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) 
   const int32_t betas[] = {8, 16, 24, 48, 96};
   const int32_t gammas[] = {2, 4, 8, 16, 64};
   const int32_t probes[] = {1 << 12, 1 << 16, 1 << 20, 1 << 30};
-  for (int param = 0; param < 5 && rc == LDD_OK; ++param) {
+  const int32_t ld_vals[2] = {0, 1};
+  const bool ld_possible = g->max_degree <= (u32)kLdMaxDegree;
+  for (int param = 0; param < 6 && rc == LDD_OK; ++param) {
     const int32_t* vals = param == 0 ? alphas : param == 1 ? betas : param == 2 ? gammas : probes;
     int nv = param == 3 ? 4 : 5;
     int32_t per_sm_vals[2] = {1, max_per_sm};
@@ -1735,11 +1774,15 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) 
       vals = per_sm_vals;
       nv = max_per_sm > 1 ? 2 : 1;
     }
+    if (param == 5) {  // the low-degree rounds, where the graph allows them
+      vals = ld_vals;
+      nv = ld_possible ? 2 : 0;
+    }
     for (int i = 0; i < nv && rc == LDD_OK; ++i) {
       ldd_tuning t = cur;
       int32_t* field = param == 0 ? &t.pull_alpha : param == 1 ? &t.pull_beta
                      : param == 2 ? &t.pull_gamma : param == 3 ? &t.probe_min_arcs
-                                                  : &t.bfs_blocks_per_sm;
+                     : param == 4 ? &t.bfs_blocks_per_sm : &t.low_degree_rounds;
       if (*field == vals[i]) continue;
       *field = vals[i];
       if ((rc = ldd_set_tuning(g, &t)) != LDD_OK) break;

@@ -146,6 +146,8 @@ void sync_params(ldd_graph* g, ldd_graph* r) {
   r->pull_beta = g->pull_beta;
   r->pull_gamma = g->pull_gamma;
   r->probe_min_arcs = g->probe_min_arcs;
+  r->low_degree_rounds = g->low_degree_rounds;
+  r->max_degree = g->max_degree;  // residual rows are never longer
 }
 
 }  // namespace

@@ -74,6 +74,7 @@ struct ldd_graph {
   int* d_col = nullptr;
   CutList cut;                 // grouped cut list (cut count of Definition 1.1)
   u32* d_active = nullptr;     // vertices the BFS handles, ascending (when few enough)
+  uint4* d_active4 = nullptr;  // all of them with their adjacency ranges (plain graphs)
   u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
   int* d_hot_center = nullptr; // their labels, gathered per cut count
   u32 n_hot = 0;
@@ -93,7 +94,7 @@ struct ldd_graph {
   int* d_qrow[2] = {nullptr, nullptr};
   u32* d_qoff[2] = {nullptr, nullptr};
   u32* d_cf[2] = {nullptr, nullptr};
-  u32* d_ulist[2] = {nullptr, nullptr};
+  uint4* d_ulist[2] = {nullptr, nullptr};
   void* d_slots = nullptr;
   int* d_center = nullptr;
   int* d_dist = nullptr;
@@ -119,6 +120,8 @@ struct ldd_graph {
   u32 pull_beta = 0;
   u32 pull_gamma = 0;
   u32 probe_min_arcs = 1u << 16;
+  u32 max_degree = 0;          // largest row of the CSR (unions: of any member)
+  bool low_degree_rounds = true;  // tuning: low-degree rounds when max_degree allows
   bool timing = false;
   cudaEvent_t ev[8] = {};
   // pipelined batches (ldd_decompose_batch), set up on first use

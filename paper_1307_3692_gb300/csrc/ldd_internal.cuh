@@ -44,6 +44,9 @@ constexpr int kRoundDigits = 4;                      // 32-bit start round
 constexpr int kBfsThreads = 512;
 constexpr int kBfsBase = 256;
 constexpr int kBfsMaxSpan = 4096;
+// Graphs whose vertices all have at most this many arcs may run the round
+// loop's low-degree rounds (k_bfs.cu).
+constexpr int kLdMaxDegree = 32;
 
 // Components with at most this many vertices are solved by one warp each.
 constexpr u32 kSmallComp = 32;
@@ -103,10 +106,14 @@ struct BfsArgs {
   u32* qv[2];        // frontier queues: vertex
   int* qrow[2];      //                  row_ptr[vertex]
   u32* qoff[2];      //                  exclusive edge offset in the frontier
+  uint4* q4[2];      // low-degree rounds' frontier: (vertex, row_ptr[v], row_ptr[v + 1], 0)
+                     // (the same memory as qv/qrow/qoff)
   u32* cf[2];        // first queue slot of every base chunk of edges
-  u32* ulist[2];     // vertices still unsettled after a bottom-up round (ping-pong)
+  uint4* ulist[2];   // vertices still unsettled after a bottom-up round, with their adjacency
+                     // ranges: (v, row_ptr[v], row_ptr[v + 1], 0) (ping-pong)
   const u32* excl;   // bit v: v is not handled by the BFS
   const u32* active; // the vertices the BFS handles, ascending (n_active), or null
+  const uint4* active4;  // the same with their adjacency ranges (plain graphs), or null
   Control* ctl;
   u32 n;
   u32 n_active;      // vertices the BFS settles (components of more than 32 vertices)
@@ -118,6 +125,8 @@ struct BfsArgs {
   u32 pull_gamma;    //   and frontier arcs * gamma > n_active (a bottom-up round reads every key)
   u32 pull_beta;     // go back top-down when frontier vertices * beta < n_active
   u32 probe_min_arcs;  // top-down rounds with at least this many arcs read a key before its atomicMin
+  u32 low_degree;    // 1: every vertex has at most kLdMaxDegree arcs and the low-degree rounds
+                     // run (the frontier a plain vertex list, a thread per vertex)
   const u32* wmem;   // unions: member of every 32-vertex word; else null
   u32* mrank;        // unions: [3][kmem] smallest rank per level slot and member (~0 on entry)
   u32 kmem;          // unions: members

@@ -14,7 +14,9 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 SETTINGS = [dict(pull_alpha=0), dict(pull_alpha=1000, pull_gamma=0), dict(pull_beta=1),
-            dict(probe_min_arcs=0), dict(probe_min_arcs=1 << 30), dict(bfs_blocks_per_sm=1)]
+            dict(probe_min_arcs=0), dict(probe_min_arcs=1 << 30), dict(bfs_blocks_per_sm=1),
+            dict(low_degree_rounds=0), dict(low_degree_rounds=1, probe_min_arcs=0),
+            dict(low_degree_rounds=1, pull_alpha=1000, pull_gamma=0, pull_beta=1000)]
 
 
 @pytest.mark.parametrize("G,beta", [(gen.rmat(14), 0.1), (gen.grid2d(90, 70), 0.05)],
@@ -61,5 +63,49 @@ def test_autotune_plain_and_union(ldd, cuda):
         oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shs[i])
         assert np.array_equal(cu[i * G.n:(i + 1) * G.n], oc)
         assert np.array_equal(du[i * G.n:(i + 1) * G.n], od)
+    u.close()
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["grid3d_40", "grid2d_300x200_small_beta", "rgg_30000",
+                                  "gnp_600", "path_5000"])
+def test_low_degree_rounds_both_ways(ldd, cuda, name):
+    """Graphs whose vertices have at most 32 arcs run the low-degree rounds by
+    default; the edge-balanced rounds give the same labels (both = oracle),
+    with and without bottom-up rounds and key probes, on a plain graph and
+    in a union."""
+    G, beta = {"grid3d_40": (gen.grid3d(40, 40, 40), 0.05),
+               "grid2d_300x200_small_beta": (gen.grid2d(300, 200), 0.01),
+               "rgg_30000": (gen.rgg(30000, 3), 0.2),
+               "gnp_600": (gen.random_graph(600, 0.02, 4), 0.1),
+               "path_5000": (gen.grid2d(5000, 1), 0.02)}[name]
+    assert int(np.diff(G.row_ptr).max()) <= 32
+    sh = gen.shifts(G.n, beta, 8)
+    oc, od = oracle.oracle_ldd(G.row_ptr, G.col, sh)
+    g = ldd.LddGraph(torch.from_numpy(G.row_ptr).to(cuda), torch.from_numpy(G.col).to(cuda))
+    assert g.tuning()["low_degree_rounds"] == 1
+    base = g.tuning()
+    for st in (dict(low_degree_rounds=1), dict(low_degree_rounds=0),
+               dict(low_degree_rounds=1, pull_alpha=1000, pull_gamma=0),
+               dict(low_degree_rounds=1, probe_min_arcs=0, bfs_blocks_per_sm=2)):
+        g.set_tuning(**(base | st))
+        c = torch.empty(G.n, dtype=torch.int32, device=cuda)
+        d = torch.empty(G.n, dtype=torch.int32, device=cuda)
+        g.decompose(beta, torch.from_numpy(sh).to(cuda), c, d)
+        assert np.array_equal(c.cpu().numpy(), oc) and np.array_equal(d.cpu().numpy(), od), st
+        st_ = g.stats()
+        if st.get("low_degree_rounds") == 1 and st_["pull_rounds"] == 0:
+            assert st_["push_arcs"] <= G.nnz  # every arc offered at most once
+    u = ldd.LddUnion([g, g, g])
+    shs = [gen.shifts(G.n, beta, 20 + i) for i in range(3)]
+    for ldr in (1, 0):
+        u.set_tuning(**(u.tuning() | dict(low_degree_rounds=ldr)))
+        cu = torch.empty(u.total, dtype=torch.int32, device=cuda)
+        du = torch.empty(u.total, dtype=torch.int32, device=cuda)
+        u.decompose([beta] * 3, torch.from_numpy(np.concatenate(shs)).to(cuda), cu, du)
+        for i in range(3):
+            oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shs[i])
+            assert np.array_equal(cu[i * G.n:(i + 1) * G.n].cpu().numpy(), oc)
+            assert np.array_equal(du[i * G.n:(i + 1) * G.n].cpu().numpy(), od)
     u.close()
     g.close()
