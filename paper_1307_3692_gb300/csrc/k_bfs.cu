@@ -59,7 +59,8 @@ constexpr int kPullCoop = 4;   // neighbours per lane per step of a warp-wide sc
 // Unions of at most this many members keep their per-member floors in shared
 // memory (two tables after Smem); larger unions use the global table directly.
 constexpr u32 kSmemMembers = 4096;
-constexpr int kLdBatch = 8;    // low-degree rounds: arcs per thread in flight
+constexpr int kLdBatch = 8;    // low-degree rounds: arcs per frontier vertex and step
+constexpr int kLdItems = 1;    // low-degree rounds: items per thread in flight
 
 struct Smem {
   int owner[kBfsMaxSpan];
@@ -112,6 +113,16 @@ __device__ __forceinline__ u32 warp_min(u32 x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(kFull, x, o));
   return x;
+}
+
+// First item of this warp in a grid-stride loop over groups of 32 x k items,
+// numbered so that consecutive groups go to different CTAs (warp w of CTA b
+// takes group w * gridDim.x + b): a round with fewer items than threads still
+// spreads over every SM instead of filling the leading CTAs.  The stride is
+// gridDim.x * blockDim.x * k.  rev: CTAs in reverse order.
+__device__ __forceinline__ u32 warp_first_item(u32 k, bool rev = false) {
+  const u32 b = rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+  return ((threadIdx.x >> 5) * gridDim.x + b) * 32u * k;
 }
 
 __device__ __forceinline__ u64 warp_min64(u64 x) {
@@ -172,25 +183,13 @@ __device__ __forceinline__ void flush_members(const BfsArgs& a, u32 slot, u32* s
 // (count << 32 | degree sum) over its lanes, reserves that many queue slots
 // and edge offsets, and every lane writes its vertices in slot order.
 // qi: frontier counter index (rotates over 3), qb: queue buffer (ping-pong).
-// Low-degree mode: the frontier is the list q4 of (vertex, row start, row end)
-// entries (items in the counter's high word, its low word unused).  An append
-// is one reservation per warp and one 16-byte store per vertex; its adjacency
-// range is loaded beside the reservation, not before it, so the next round
-// starts without a row_ptr round trip.
+// Low-degree mode: the frontier is the plain vertex list qv (items in the
+// counter's high word, its low word unused), so an append is one reservation
+// per warp and one store per vertex, with no adjacency range to load.
 template <int K>
 __device__ __forceinline__ void warp_append_ld(u32 mask, const u32 (&v)[K], const BfsArgs& a,
                                                int qi, int qb) {
   const u32 lane = threadIdx.x & 31;
-  int rs[K], re[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    rs[i] = 0;
-    re[i] = 0;
-    if (mask >> i & 1u) {
-      rs[i] = __ldg(a.row_ptr + v[i]);
-      re[i] = __ldg(a.row_ptr + v[i] + 1);
-    }
-  }
   const u32 mine = __popc(mask);
   u32 incl = mine;
 #pragma unroll
@@ -205,7 +204,7 @@ __device__ __forceinline__ void warp_append_ld(u32 mask, const u32 (&v)[K], cons
   u32 slot = __shfl_sync(kFull, base, 0) + incl - mine;
 #pragma unroll
   for (int i = 0; i < K; ++i)
-    if (mask >> i & 1u) a.q4[qb][slot++] = make_uint4(v[i], (u32)rs[i], (u32)re[i], 0u);
+    if (mask >> i & 1u) a.qv[qb][slot++] = v[i];
 }
 
 template <int K, bool LD>
@@ -270,8 +269,7 @@ __device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u3
   const u32 lane = threadIdx.x & 31;
   const u32 stride = gridDim.x * blockDim.x;
   // trailing CTAs first: in a small round the leading CTAs are expanding
-  const u32 b = gridDim.x - 1 - blockIdx.x;
-  for (u32 base = b * blockDim.x + (threadIdx.x & ~31u); base < cnt; base += stride) {
+  for (u32 base = warp_first_item(1, true); base < cnt; base += stride) {
     const u32 i = base + lane;
     u32 u[1] = {0};
     bool want = false;
@@ -379,7 +377,7 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
 }
 
 // Low-degree round (every vertex of the graph has at most kLdMaxDegree
-// arcs): one pass over Q frontier vertices (the list q_cur) and the cnt
+// arcs): one pass over Q frontier vertices (the list qv_cur) and the cnt
 // entries of start bucket rb (from lo in rv), a thread per item.
 //   * A frontier vertex v offers key[v] + 2^32 to each of its neighbours
 //     (64-bit atomicMin, after a probe of the key when `probe`), kLdBatch arcs
@@ -387,65 +385,91 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
 //   * A start-bucket entry u joins the next frontier if its key still has its
 //     start level rb (Section 4's delayed start; stable during the round, see
 //     the file comment).
-// A frontier entry carries v's adjacency range, so v's key and its
-// neighbours' ids load in one round trip, like the bucket entries' keys, and
-// the bucket test runs beside the expansion instead of after it: a thin round
-// is a short chain of dependent loads.  `pushed` adds
-// the arcs offered.
+// v's key and adjacency range, and the bucket entries' keys, load in one round
+// trip, and the bucket test runs beside the expansion instead of after it: a
+// thin round is a short chain of dependent loads.  A thread takes kLdItems
+// items at a time (a warp 32 kLdItems consecutive ones) and interleaves their
+// loads, so that a round with more items than threads still costs about one
+// such chain.  `pushed` adds the arcs offered.
 template <bool U>
-__device__ __forceinline__ void expand_ld(const BfsArgs& a, const uint4* q_cur, u32 Q, u32 lvl_next,
+__device__ __forceinline__ void expand_ld(const BfsArgs& a, const u32* qv_cur, u32 Q, u32 lvl_next,
                                           const u32* rv, int lo, u32 cnt, u32 rb, bool probe,
                                           int qi, int qb, u32& myrank, u32* s_acc, u64& pushed) {
   constexpr u32 kNone = 0xffffffffu;
+  constexpr int KI = kLdItems;
+  constexpr int KA = kLdItems * kLdBatch;
   const u32 lane = threadIdx.x & 31;
   const u32 total = Q + cnt;
-  const u32 stride = gridDim.x * blockDim.x;
-  for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
-    const u32 i = base + lane;
-    const bool front = i < Q;
-    const bool buck = !front && i < total;
-    u32 v = 0;
-    int rs = 0, re = 0;
-    if (front) {
-      const uint4 q = __ldcg(q_cur + i);
-      v = q.x;
-      rs = (int)q.y;
-      re = (int)q.z;
-    } else if (buck) {
-      v = __ldg(rv + lo + (int)(i - Q));
+  const u32 stride = gridDim.x * blockDim.x * KI;
+  for (u32 base = warp_first_item(KI); base < total; base += stride) {
+    u32 v[KI];
+    bool front[KI], buck[KI];
+#pragma unroll
+    for (int t = 0; t < KI; ++t) {
+      const u32 i = base + (u32)t * 32 + lane;
+      front[t] = i < Q;
+      buck[t] = !front[t] && i < total;
+      v[t] = 0;
+      if (front[t]) v[t] = ld_cg_u32(qv_cur + i);
+      else if (buck[t]) v[t] = __ldg(rv + lo + (int)(i - Q));
     }
-    u64 kv = 0;
-    if (front || buck) kv = ld_cg_u64(a.key + v);
-    const bool start = buck && (u32)(kv >> 32) == rb;
-    const u32 sv[1] = {v};
-    note_rank<U>(a, (u32)qi, start, v, (u32)kv, myrank, s_acc);
-    warp_append<1, true>(start ? 1u : 0u, sv, a, qi, qb);
-    pushed += (u64)(re - rs);
-    const u64 cand = kv + kLevelOne;
-    int nch = (re - rs + kLdBatch - 1) / kLdBatch;
+    u64 kv[KI];
+    int rs[KI], re[KI];
+#pragma unroll
+    for (int t = 0; t < KI; ++t) {
+      kv[t] = 0;
+      rs[t] = 0;
+      re[t] = 0;
+      if (front[t] || buck[t]) kv[t] = ld_cg_u64(a.key + v[t]);
+      if (front[t]) {
+        rs[t] = __ldg(a.row_ptr + v[t]);
+        re[t] = __ldg(a.row_ptr + v[t] + 1);
+      }
+    }
+    u32 smask = 0;
+#pragma unroll
+    for (int t = 0; t < KI; ++t) {
+      const bool start = buck[t] && (u32)(kv[t] >> 32) == rb;
+      if (start) smask |= 1u << t;
+      note_rank<U>(a, (u32)qi, start, v[t], (u32)kv[t], myrank, s_acc);
+    }
+    warp_append<KI, true>(smask, v, a, qi, qb);
+    int nch = 0;
+#pragma unroll
+    for (int t = 0; t < KI; ++t) {
+      pushed += (u64)(re[t] - rs[t]);
+      nch = max(nch, (re[t] - rs[t] + kLdBatch - 1) / kLdBatch);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nch = max(nch, __shfl_xor_sync(kFull, nch, o));
     for (int ch = 0; ch < nch; ++ch) {
-      const int e0 = rs + ch * kLdBatch;
-      u32 w[kLdBatch];
+      u32 w[KA];
 #pragma unroll
-      for (int q = 0; q < kLdBatch; ++q) w[q] = (e0 + q < re) ? (u32)__ldg(a.col + e0 + q) : kNone;
-      u64 cur[kLdBatch];
+      for (int t = 0; t < KI; ++t)
 #pragma unroll
-      for (int q = 0; q < kLdBatch; ++q)
-        cur[q] = (w[q] < a.n) ? (probe ? ld_cg_u64(a.key + w[q]) : ~0ull) : 0ull;
+        for (int q = 0; q < kLdBatch; ++q) {
+          const int e = rs[t] + ch * kLdBatch + q;
+          w[t * kLdBatch + q] = e < re[t] ? (u32)__ldg(a.col + e) : kNone;
+        }
+      u64 cur[KA];
+#pragma unroll
+      for (int x = 0; x < KA; ++x)
+        cur[x] = (w[x] < a.n) ? (probe ? ld_cg_u64(a.key + w[x]) : ~0ull) : 0ull;
       u32 mask = 0, won = 0;
 #pragma unroll
-      for (int q = 0; q < kLdBatch; ++q)
-        if (cand < cur[q]) {
-          const u64 old = atomicMin(a.key + w[q], cand);
-          if (old > cand) won |= 1u << q;
-          if ((u32)(old >> 32) > lvl_next) mask |= 1u << q;
+      for (int x = 0; x < KA; ++x) {
+        const u64 cand = kv[x / kLdBatch] + kLevelOne;
+        if (cand < cur[x]) {
+          const u64 old = atomicMin(a.key + w[x], cand);
+          if (old > cand) won |= 1u << x;
+          if ((u32)(old >> 32) > lvl_next) mask |= 1u << x;
         }
+      }
 #pragma unroll
-      for (int q = 0; q < kLdBatch; ++q)
-        note_rank<U>(a, (u32)qi, (won >> q) & 1u, w[q], (u32)cand, myrank, s_acc);
-      warp_append<kLdBatch, true>(mask, w, a, qi, qb);
+      for (int x = 0; x < KA; ++x)
+        note_rank<U>(a, (u32)qi, (won >> x) & 1u, w[x], (u32)(kv[x / kLdBatch] + kLevelOne),
+                     myrank, s_acc);
+      warp_append<KA, true>(mask, w, a, qi, qb);
     }
   }
 }
@@ -457,11 +481,11 @@ __device__ __forceinline__ void post_cta_min(Smem& s, u32& myrank) {
   myrank = 0xffffffffu;
 }
 
-// Appends (v[i], rs[i], re[i]) for every bit i of `mask` to a list of
-// bottom-up candidates with their adjacency ranges, one atomic per warp.
+// Appends every v[i] with bit i of `mask` set to a plain vertex list, one
+// atomic per warp.
 template <int K>
-__device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], const int (&rs)[K],
-                                                 const int (&re)[K], uint4* list, u32* count) {
+__device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], u32* list,
+                                                 u32* count) {
   const u32 lane = threadIdx.x & 31;
   const u32 mine = __popc(mask);
   u32 incl = mine;
@@ -477,87 +501,58 @@ __device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], co
   base = __shfl_sync(kFull, base, 0) + incl - mine;
 #pragma unroll
   for (int i = 0; i < K; ++i)
-    if (mask >> i & 1u) list[base++] = make_uint4(v[i], (u32)rs[i], (u32)re[i], 0u);
+    if (mask >> i & 1u) list[base++] = v[i];
 }
 
-// Bottom-up round from level lvl (see the file comment).  Candidates are, in
-// the first bottom-up round of a run (from_list = false), the vertices the
-// BFS handles: the (vertex, row start, row end) list a.active4 of a plain
-// graph, else the id list a.active, else every vertex not in excl; in later
-// rounds the (vertex, row start, row end) list `cand` of ncand vertices that
-// the previous bottom-up round left unsettled.
+// Bottom-up round from level lvl (see the file comment).  Candidates are every
+// vertex not in excl (from_list = false; a.active lists them when it is set)
+// or the list `cand` of ncand vertices.
 // Each lane takes kPullV candidates at a time and advances their neighbour
 // scans in lock-step, one neighbour each per step, so that up to kPullV
-// independent loads are in flight per lane.  A candidate that comes with its
-// adjacency range loads its key and its first neighbour together.  Adds the
-// arcs it scans and the vertices it examines to the statistics.
+// independent loads are in flight per lane.  Adds the arcs it scans and the
+// vertices it examines to the statistics.
 template <bool U, bool LD>
 __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minrank, u32 mslot,
-                                           int qi, int qb, bool from_list, const uint4* cand,
-                                           u32 ncand, uint4* ulist_out, u32* ucnt_out,
+                                           int qi, int qb, bool from_list, const u32* cand,
+                                           u32 ncand, u32* ulist_out, u32* ucnt_out,
                                            u32& myrank, u32* s_acc, const u32* s_floor) {
   constexpr u32 kNone = 0xffffffffu;
   u32 scanned = 0, examined = 0;
   const u32 lane = threadIdx.x & 31;
   const u32 L = (u32)lvl;
-  const u32* ids = nullptr;  // id list without ranges (a union's active list)
-  if (!from_list && a.active4) {  // the first bottom-up round: the BFS's own vertices
+  if (!from_list && a.active) {  // the first bottom-up round: the BFS's own vertices
     from_list = true;
-    cand = a.active4;
-    ncand = a.n_active;
-  } else if (!from_list && a.active) {
-    ids = a.active;
+    cand = a.active;
     ncand = a.n_active;
   }
-  const u32 total = (from_list || ids) ? ncand : a.n;
+  const u32 total = from_list ? ncand : a.n;
   const u32 stride = gridDim.x * blockDim.x * kPullV;
-  for (u32 base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * kPullV; base < total;
-       base += stride) {
+  for (u32 base = warp_first_item(kPullV); base < total; base += stride) {
     u32 w[kPullV];
-    int e[kPullV], re[kPullV];
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       const u32 i = base + (u32)j * 32 + lane;
       w[j] = kNone;
-      e[j] = 0;
-      re[j] = 0;
-      if (i < total) {
-        if (from_list) {
-          const uint4 q = __ldcg(cand + i);
-          w[j] = q.x;
-          e[j] = (int)q.y;
-          re[j] = (int)q.z;
-        } else if (ids) {
-          w[j] = ld_cg_u32(ids + i);
-        } else {
-          const u32 ex = __ldg(a.excl + (i >> 5));  // same word for the whole warp
-          if (!((ex >> lane) & 1u)) w[j] = i;
-        }
+      if (from_list) {
+        if (i < total) w[j] = ld_cg_u32(cand + i);
+      } else if (i < total) {
+        const u32 ex = __ldg(a.excl + (i >> 5));  // same word for the whole warp
+        if (!((ex >> lane) & 1u)) w[j] = i;
       }
     }
-    // the key with the adjacency range (ids) or with the first neighbour
-    // (ranges known): one round trip
+    // the key and the adjacency range together: one round trip, not two
     u64 kw[kPullV];
-    u32 first[kPullV];
+    int e[kPullV], re[kPullV];
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       kw[j] = 0ull;
-      first[j] = kNone;
+      e[j] = 0;
+      re[j] = 0;
       if (w[j] != kNone) {
         kw[j] = ld_cg_u64(a.key + w[j]);
-        if (from_list) {
-          if (e[j] < re[j]) first[j] = (u32)__ldg(a.col + e[j]);
-        } else {
-          e[j] = __ldg(a.row_ptr + w[j]);
-          re[j] = __ldg(a.row_ptr + w[j] + 1);
-        }
+        e[j] = __ldg(a.row_ptr + w[j]);
+        re[j] = __ldg(a.row_ptr + w[j] + 1);
       }
-    }
-    int rs0[kPullV], re0[kPullV];  // the ranges, for the list of the next bottom-up round
-#pragma unroll
-    for (int j = 0; j < kPullV; ++j) {
-      rs0[j] = e[j];
-      re0[j] = re[j];
     }
     u64 best[kPullV];
     u32 fr[kPullV];  // floor rank: nothing beats (L + 1, fr); union: w's own member's
@@ -586,7 +581,7 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
       for (int j = 0; j < kPullV; ++j) {
         vv[j] = kNone;
         if (e[j] < re[j]) {
-          vv[j] = (step == 0 && from_list) ? first[j] : (u32)__ldg(a.col + e[j]);
+          vv[j] = (u32)__ldg(a.col + e[j]);
           ++e[j];
           ++scanned;
           any = true;
@@ -654,7 +649,7 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
     for (int j = 0; j < kPullV; ++j)
       note_rank<U>(a, (u32)qi, (won >> j) & 1u, w[j], (u32)best[j], myrank, s_acc);
     warp_append<kPullV, LD>(mask, w, a, qi, qb);
-    warp_list_append<kPullV>(keep, w, rs0, re0, ulist_out, ucnt_out);
+    warp_list_append<kPullV>(keep, w, ulist_out, ucnt_out);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -782,7 +777,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
           }
         }
       } else if (LD) {  // expansion and start bucket lvl + 1 in one pass
-        expand_ld<U>(a, a.q4[phase & 1], Q, (u32)lvl + 1, rv, nb_lo, (u32)(nb_hi - nb_lo),
+        expand_ld<U>(a, a.qv[phase & 1], Q, (u32)lvl + 1, rv, nb_lo, (u32)(nb_hi - nb_lo),
                      (u32)lvl + 1, E >= a.probe_min_arcs, qi, qb, myrank, s_acc, pushed);
         if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
       } else {

@@ -89,7 +89,6 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->cut.grp_lab);
   cudaFree(g->d_hot);
   if (!g->uni) cudaFree(g->d_active);  // a union's list lives in d_active_buf
-  cudaFree(g->d_active4);
   cudaFree(g->d_hot_center);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
@@ -176,11 +175,11 @@ int alloc_scratch(ldd_graph* g) {
       {(void**)&g->d_v[0], 4 * n},        {(void**)&g->d_v[1], 4 * n},
       {(void**)&g->d_status, g->status_bytes},
       {(void**)&g->d_order, 4 * n},       {(void**)&g->d_key, 8 * n},
-      // frontier queues, 16 bytes per vertex and side: (vertex, row, offset)
-      // words of the edge-balanced rounds, or the low-degree rounds' entries
-      {(void**)&g->d_qv[0], 16 * n},      {(void**)&g->d_qv[1], 16 * n},
+      {(void**)&g->d_qv[0], 4 * n},       {(void**)&g->d_qv[1], 4 * n},
+      {(void**)&g->d_qrow[0], 4 * n},     {(void**)&g->d_qrow[1], 4 * n},
+      {(void**)&g->d_qoff[0], 4 * n},     {(void**)&g->d_qoff[1], 4 * n},
       {(void**)&g->d_cf[0], 4 * ncf},     {(void**)&g->d_cf[1], 4 * ncf},
-      {(void**)&g->d_ulist[0], 16 * n},   {(void**)&g->d_ulist[1], 16 * n},
+      {(void**)&g->d_ulist[0], 4 * n},    {(void**)&g->d_ulist[1], 4 * n},
       {(void**)&g->d_slots, n ? fraction_slot_bytes((u32)n) : 0},
       {(void**)&g->d_center, 4 * n},      {(void**)&g->d_dist, 4 * n},
       {(void**)&g->d_ctl, sizeof(Control)},
@@ -195,10 +194,6 @@ int alloc_scratch(ldd_graph* g) {
   for (auto& p : parts) {
     *p.p = (char*)g->arena + off;
     off += align_up(p.bytes ? p.bytes : 1, 256);
-  }
-  for (int b = 0; b < 2; ++b) {
-    g->d_qrow[b] = reinterpret_cast<int*>(g->d_qv[b] + n);
-    g->d_qoff[b] = g->d_qv[b] + 2 * n;
   }
   CUDA_TRY(cudaMemset(g->d_status, 0, g->status_bytes));
   g->bptr_cap = (u32)std::min<size_t>(n + 2, 0xffffffffu);
@@ -347,33 +342,18 @@ int build_cut_list(ldd_graph* g, const std::vector<int32_t>& rp, const std::vect
 // round of a decomposition -- built only when they are at most 3/4 of all
 // vertices (else scanning every id and skipping the excluded ones is cheaper
 // than reading the list).
-int build_active_list(ldd_graph* g, const std::vector<int32_t>& rp) {
+int build_active_list(ldd_graph* g) {
   const size_t n = (size_t)g->n;
-  if (n == 0 || g->n_active == 0) return LDD_OK;
+  if (n == 0 || (size_t)g->n_active * 4 > n * 3) return LDD_OK;
   std::vector<u32> excl((n + 31) / 32);
   if (cudaMemcpy(excl.data(), g->d_excl, excl.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(LDD_ERR_CUDA, "copy of the exclusion bitmask failed");
   std::vector<u32> act;
-  std::vector<uint4> act4;
   act.reserve(g->n_active);
-  act4.reserve(g->n_active);
   for (size_t v = 0; v < n; ++v)
-    if (!((excl[v >> 5] >> (v & 31)) & 1u)) {
-      act.push_back((u32)v);
-      act4.push_back(make_uint4((u32)v, (u32)rp[v], (u32)rp[v + 1], 0u));
-    }
+    if (!((excl[v >> 5] >> (v & 31)) & 1u)) act.push_back((u32)v);
   if (act.size() != g->n_active) return fail(LDD_ERR_CUDA, "inconsistent component tables");
-  // the first bottom-up round's candidates with their adjacency ranges
-  if (cudaMalloc(&g->d_active4, act4.size() * sizeof(uint4)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(LDD_ERR_OOM, "device allocation of the active list failed");
-  }
-  if (cudaMemcpy(g->d_active4, act4.data(), act4.size() * sizeof(uint4), cudaMemcpyHostToDevice) !=
-      cudaSuccess)
-    return fail(LDD_ERR_CUDA, "upload of the active list failed");
-  // the plain id list (union members), only when it is short enough to beat
-  // a scan of every id
-  if (g->n_active * 4ull > n * 3) return LDD_OK;
+  if (act.empty()) return LDD_OK;
   if (cudaMalloc(&g->d_active, act.size() * 4) != cudaSuccess) {
     cudaGetLastError();
     return fail(LDD_ERR_OOM, "device allocation of the active list failed");
@@ -408,13 +388,11 @@ BfsArgs bfs_args(ldd_graph* g) {
     a.qv[b] = g->d_qv[b];
     a.qrow[b] = g->d_qrow[b];
     a.qoff[b] = g->d_qoff[b];
-    a.q4[b] = reinterpret_cast<uint4*>(g->d_qv[b]);
     a.cf[b] = g->d_cf[b];
     a.ulist[b] = g->d_ulist[b];
   }
   a.excl = g->d_excl;
   a.active = g->d_active;
-  a.active4 = g->uni ? nullptr : g->d_active4;
   a.ctl = g->d_ctl;
   a.n = (u32)g->n;
   a.n_active = g->n_active;
@@ -918,7 +896,7 @@ u64 union_bytes(const UnionCaps& c) {
   b += 16 * c.total + 8 * c.total + 32ull * (c.k + 1) + 8ull * c.k + sizeof(UnionMember) * c.k;
   const u64 nk = std::max<u64>(N, 64);
   b += 8 * N + 4 * N + 16 * nk + 8 * N + ((N + kSortTile - 1) / kSortTile + 1) * 2048 + 4 * N +
-       8 * N + 32 * N + 8 * (c.E / kBfsBase + 2) + 32 * N + (N ? fraction_slot_bytes((u32)N) : 0) +
+       8 * N + 24 * N + 8 * (c.E / kBfsBase + 2) + 8 * N + (N ? fraction_slot_bytes((u32)N) : 0) +
        8 * N + sizeof(Control);
   b += 12 * (N + 2);
   return b;
@@ -1187,7 +1165,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   cudaFree(d_arcs);
   if (rc != LDD_OK) return bail(rc);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
-  if ((rc = build_active_list(g, rp)) != LDD_OK) return bail(rc);
+  if ((rc = build_active_list(g)) != LDD_OK) return bail(rc);
   if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);
   // low-degree rounds are latency-bound: a key probe before every atomicMin
   // is one more dependent round trip, worth it only in wide rounds

@@ -74,7 +74,6 @@ struct ldd_graph {
   int* d_col = nullptr;
   CutList cut;                 // grouped cut list (cut count of Definition 1.1)
   u32* d_active = nullptr;     // vertices the BFS handles, ascending (when few enough)
-  uint4* d_active4 = nullptr;  // all of them with their adjacency ranges (plain graphs)
   u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
   int* d_hot_center = nullptr; // their labels, gathered per cut count
   u32 n_hot = 0;
@@ -94,7 +93,7 @@ struct ldd_graph {
   int* d_qrow[2] = {nullptr, nullptr};
   u32* d_qoff[2] = {nullptr, nullptr};
   u32* d_cf[2] = {nullptr, nullptr};
-  uint4* d_ulist[2] = {nullptr, nullptr};
+  u32* d_ulist[2] = {nullptr, nullptr};
   void* d_slots = nullptr;
   int* d_center = nullptr;
   int* d_dist = nullptr;

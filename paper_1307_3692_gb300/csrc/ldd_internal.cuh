@@ -106,14 +106,11 @@ struct BfsArgs {
   u32* qv[2];        // frontier queues: vertex
   int* qrow[2];      //                  row_ptr[vertex]
   u32* qoff[2];      //                  exclusive edge offset in the frontier
-  uint4* q4[2];      // low-degree rounds' frontier: (vertex, row_ptr[v], row_ptr[v + 1], 0)
-                     // (the same memory as qv/qrow/qoff)
+                     // (low-degree rounds use qv alone)
   u32* cf[2];        // first queue slot of every base chunk of edges
-  uint4* ulist[2];   // vertices still unsettled after a bottom-up round, with their adjacency
-                     // ranges: (v, row_ptr[v], row_ptr[v + 1], 0) (ping-pong)
+  u32* ulist[2];     // vertices still unsettled after a bottom-up round (ping-pong)
   const u32* excl;   // bit v: v is not handled by the BFS
   const u32* active; // the vertices the BFS handles, ascending (n_active), or null
-  const uint4* active4;  // the same with their adjacency ranges (plain graphs), or null
   Control* ctl;
   u32 n;
   u32 n_active;      // vertices the BFS settles (components of more than 32 vertices)
