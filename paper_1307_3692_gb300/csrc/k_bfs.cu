@@ -69,25 +69,34 @@ struct Smem {
   int wtot[kBfsThreads / 32];
   u32 minrank;  // this CTA's smallest successful next-level rank in the round
   u32 stop;     // thread 0 saw an error bit: the whole CTA leaves the loop
+  // the next round's frontier counter, bottom-up floor and unsettled-list
+  // length, read by thread 0 as the barrier releases
+  u64 next_c;
+  u32 next_minrank;
+  u32 next_ucnt;
 };
 
 // Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a
 // launch completes when the counter reaches k * nblocks (+ phantom), so
 // arrival is one fire-and-forget add and nobody has to reset anything.
 // Before arriving, thread 0 publishes this CTA's smallest next-level rank to
-// *post (and resets the CTA value).  The wait is bounded: after `limit` polls
-// (or once any CTA has recorded an error) it sets kErrTimeout and returns.
-// Thread 0 then reads the error word once for the whole CTA into *stop, so
-// that every thread of the CTA takes the same branch after the barrier (a
-// thread that left the loop alone would leave the others at a CTA barrier).
-// phantom > 0 waits for CTAs that do not exist: the barrier can then only end
-// by running out of polls, which is how the timeout path is tested.
+// ctl->minrank[post] (and resets the CTA value).  The poll is an acquire
+// load, so once it sees every arrival the round's writes of all CTAs are
+// visible.  The wait is bounded: after `limit` polls (or once any CTA has
+// recorded an error) it sets kErrTimeout and returns.  Thread 0 then reads,
+// in one round trip, the error word and the next round's state (slot `post`
+// of the frontier counter, bottom-up floor and unsettled-list length) into
+// shared memory, so that every thread of the CTA sees the same values and
+// takes the same branch after the barrier (a thread that left the loop alone
+// would leave the others at a CTA barrier).  phantom > 0 waits for CTAs that
+// do not exist: the barrier can then only end by running out of polls, which
+// is how the timeout path is tested.
 __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 phantom,
-                                             u32 limit, u32* post, u32* cta_min, u32* stop) {
+                                             u32 limit, u32 post, Smem& s) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (*cta_min != 0xffffffffu) atomicMin(post, *cta_min);
-    *cta_min = 0xffffffffu;
+    if (s.minrank != 0xffffffffu) atomicMin(&ctl->minrank[post], s.minrank);
+    s.minrank = 0xffffffffu;
     ++gen;
     const u64 target = (u64)gen * nblocks + phantom;
     __threadfence();
@@ -95,16 +104,20 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
     u32 spins = 0;
     for (;;) {
       u64 seen;
-      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(&ctl->bar) : "memory");
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(&ctl->bar) : "memory");
       if (seen >= target) break;
       if (++spins > limit || ld_acquire_u32(&ctl->err) != 0u) {
         atomicOr(&ctl->err, kErrTimeout);
+        __threadfence();
         break;
       }
       if (spins > 64) __nanosleep(20);
     }
-    __threadfence();
-    *stop = ld_acquire_u32(&ctl->err) != 0u ? 1u : 0u;
+    const u32 err = ld_cg_u32(&ctl->err);
+    s.next_c = ld_cg_u64(&ctl->qctr[post]);
+    s.next_minrank = ld_cg_u32(&ctl->minrank[post]);
+    s.next_ucnt = ld_cg_u32(&ctl->ucnt[post]);
+    s.stop = err != 0u ? 1u : 0u;
   }
   __syncthreads();
 }
@@ -481,27 +494,70 @@ __device__ __forceinline__ void post_cta_min(Smem& s, u32& myrank) {
   myrank = 0xffffffffu;
 }
 
-// Appends every v[i] with bit i of `mask` set to a plain vertex list, one
-// atomic per warp.
-template <int K>
-__device__ __forceinline__ void warp_list_append(u32 mask, const u32 (&v)[K], u32* list,
-                                                 u32* count) {
+// The two appends of a bottom-up step in one pass.  The vertices of `mask`
+// join the next frontier; their adjacency ranges [rs, re) are known already,
+// so, unlike warp_append, no row_ptr round trip comes first.  The vertices of
+// `keep` join the list of the next bottom-up round.  Lane 0 sends both
+// reservations before waiting for either.
+template <int K, bool LD>
+__device__ __forceinline__ void pull_append(u32 mask, u32 keep, const u32 (&v)[K],
+                                            const int (&rs)[K], const int (&re)[K],
+                                            const BfsArgs& a, int qi, int qb, u32* list,
+                                            u32* lcount) {
   const u32 lane = threadIdx.x & 31;
-  const u32 mine = __popc(mask);
-  u32 incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= (u32)o) incl += y;
-  }
-  const u32 tot = __shfl_sync(kFull, incl, 31);
-  if (tot == 0) return;
-  u32 base = 0;
-  if (lane == 0) base = atomicAdd(count, tot);
-  base = __shfl_sync(kFull, base, 0) + incl - mine;
+  u32 cnt = 0, dsum = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i)
-    if (mask >> i & 1u) list[base++] = v[i];
+    if (mask >> i & 1u) {
+      if (re[i] <= rs[i]) {
+        mask &= ~(1u << i);  // a vertex without arcs has nothing to expand
+      } else {
+        ++cnt;
+        dsum += (u32)(re[i] - rs[i]);
+      }
+    }
+  const u32 kc = __popc(keep);
+  if (!__any_sync(kFull, mask != 0u || keep != 0u)) return;
+  const u64 mine = ((u64)cnt << 32) | (LD ? 0u : dsum);
+  u64 incl = mine;
+  u32 kincl = kc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 y = __shfl_up_sync(kFull, incl, o);
+    const u32 ky = __shfl_up_sync(kFull, kincl, o);
+    if (lane >= (u32)o) {
+      incl += y;
+      kincl += ky;
+    }
+  }
+  const u64 tot = __shfl_sync(kFull, incl, 31);
+  const u32 ktot = __shfl_sync(kFull, kincl, 31);
+  u64 base = 0;
+  u32 kbase = 0;
+  if (lane == 0) {
+    if (tot) base = atomicAdd(&a.ctl->qctr[qi], tot);
+    if (ktot) kbase = atomicAdd(lcount, ktot);
+  }
+  base = __shfl_sync(kFull, base, 0) + (incl - mine);
+  kbase = __shfl_sync(kFull, kbase, 0) + (kincl - kc);
+  u32 slot = (u32)(base >> 32), off = (u32)base;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (mask >> i & 1u) {
+      a.qv[qb][slot] = v[i];
+      if (!LD) {
+        const u32 dg = (u32)(re[i] - rs[i]);
+        a.qrow[qb][slot] = rs[i];
+        a.qoff[qb][slot] = off;
+        const u32 end = off + dg;
+        for (u32 c = (off + kBfsBase - 1) / kBfsBase; c * kBfsBase < end; ++c) a.cf[qb][c] = slot;
+        off = end;
+      }
+      ++slot;
+    }
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (keep >> i & 1u) list[kbase++] = v[i];
 }
 
 // Bottom-up round from level lvl (see the file comment).  Candidates are every
@@ -553,6 +609,12 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
         e[j] = __ldg(a.row_ptr + w[j]);
         re[j] = __ldg(a.row_ptr + w[j] + 1);
       }
+    }
+    int rs0[kPullV], re0[kPullV];  // the adjacency ranges, for the appends
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      rs0[j] = e[j];
+      re0[j] = re[j];
     }
     u64 best[kPullV];
     u32 fr[kPullV];  // floor rank: nothing beats (L + 1, fr); union: w's own member's
@@ -648,8 +710,7 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
 #pragma unroll
     for (int j = 0; j < kPullV; ++j)
       note_rank<U>(a, (u32)qi, (won >> j) & 1u, w[j], (u32)best[j], myrank, s_acc);
-    warp_append<kPullV, LD>(mask, w, a, qi, qb);
-    warp_list_append<kPullV>(keep, w, ulist_out, ucnt_out);
+    pull_append<kPullV, LD>(mask, keep, w, rs0, re0, a, qi, qb, ulist_out, ucnt_out);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -708,7 +769,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
     __syncthreads();
     flush_members(a, 0, s_acc);
   }
-  grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, &ctl->minrank[0], &s.minrank, &s.stop);
+  grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, 0, s);
   const bool profiler = blockIdx.x == 0 && threadIdx.x == 0;
   if (profiler) {
     const long long t = clock64();
@@ -723,7 +784,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   bool pulling = false;
   for (;;) {
     if (s.stop) break;  // set by the last barrier, the same for every thread of the CTA
-    const u64 c = ld_cg_u64(&ctl->qctr[phase % 3]);
+    const u64 c = s.next_c;  // slot phase % 3, read as the last barrier released
     int nb_lo = 0, nb_hi = 0;  // low-degree rounds: start bucket lvl + 1, loaded beside the counter
     if (LD && lvl + 1 <= A) {
       nb_lo = __ldg(a.bptr + lvl + 1);
@@ -736,8 +797,8 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
                      : (u32)c;
     settled += Q;
     if (settled >= a.n_active) break;  // every vertex the BFS owns has its final key
-    const u32 minrank = ld_cg_u32(&ctl->minrank[phase % 3]);
-    const u32 ncand = ld_cg_u32(&ctl->ucnt[phase % 3]);
+    const u32 minrank = s.next_minrank;
+    const u32 ncand = s.next_ucnt;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctl->qctr[(phase + 2) % 3] = 0;
       ctl->minrank[(phase + 2) % 3] = 0xffffffffu;
@@ -809,8 +870,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       __syncthreads();
       flush_members(a, (u32)qi, s_acc);
     }
-    grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, &ctl->minrank[qi], &s.minrank,
-                 &s.stop);
+    grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, (u32)qi, s);
     ++phase;
     lvl = nlvl;
     if (profiler && phase < (u32)kRoundProfile) {
