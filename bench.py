@@ -15,11 +15,21 @@ library's stream; L2 flushed between steps, outside the events).  `e2e`
 repeats the step through the same C ABI with host buffers (pinned), so the
 shift upload, the result download and all host work are inside the clock.
 
+The default run also nests, under "workloads", one complete line for every
+other configuration (each with its own parity check, roofline, CPU baseline
+and clocks): the 256x256 and 256^3 grids, the batch of 1,024 random geometric
+graphs and the 64 seeds of one R-MAT 20 graph (decompositions/s against one
+at a time), the block decomposition by repeated decomposition, and the
+Poisson request stream against the server (p50/p99 against one at a time, at
+the workload's rate and at rates the one-at-a-time server sustains).
+--single keeps to the named workload's line (profiling commands use it).
+
 Under torchrun (N > 1) every rank decomposes its own replica (the method has
 no exchange step): value = N x per-rank work / the slowest rank's time.
 
 --impl reference runs the CPU oracle (the method's plain definition, single
-threaded) on the same workload, one decomposition per step, beta cycling.
+threaded) on the same workload and the same step: the three decompositions
+and their cut counts.
 """
 from __future__ import annotations
 
@@ -222,6 +232,27 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def gen_sample(name):
+    """The workload's graph family at 1/8 of its vertices: a bounded sample
+    for timing the oracle where the full size would take too long."""
+    import ldd_gen as gen
+
+    g = gen.WORKLOADS[name]["graph"]
+    if g[0] == "grid3d":
+        return gen.grid3d(g[1] // 2, g[2] // 2, g[3] // 2)
+    if g[0] == "grid2d":
+        return gen.grid2d(g[1] // 4, g[2] // 2)
+    if g[0] == "rmat":
+        return gen.rmat(g[1] - 3, *g[2:])
+    raise ValueError(name)
+
+
+def gen_shifts(n, beta, seed):
+    import ldd_gen as gen
+
+    return gen.shifts(n, beta, seed)
+
+
 def step_text(betas):
     """What one step of a single-graph workload does (both arms)."""
     return f"{len(betas)} decompositions (one per beta) + their cut counts"
@@ -270,21 +301,33 @@ def reference_arm(args):
 
 
 # ----------------------------------------------------------------- our arm
-def our_arm(args):
+def create_info(g, wall_s):
+    """Once-per-graph cost that a decomposition step amortises (ldd_create_graph)."""
+    st = g.stats()
+    return {"wall_ms": 1e3 * wall_s, "upload_ms": st["ms_create_upload"],
+            "components_ms": st["ms_create_components"],
+            "note": "once per graph, outside the timed step: CSR upload, component labelling "
+                    "(device), cut-list build (host)"}
+
+
+def our_arm(args, dist):
     import numpy as np
     import torch
 
     import paper_1307_3692_gb300 as ldd
 
     world, rank, local = dist_env()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = init_dist(world, "nccl")
 
     spec, G, shifts, t_graph, t_shift = make_workload(args.workload)
     betas = spec["betas"]
     n, m = G.n, G.m
-    g = ldd.LddGraph(torch.from_numpy(G.row_ptr).to(dev), torch.from_numpy(G.col).to(dev), validate=False)
+    d_rp, d_col = torch.from_numpy(G.row_ptr).to(dev), torch.from_numpy(G.col).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = ldd.LddGraph(d_rp, d_col, validate=False)
+    create = create_info(g, time.perf_counter() - t0)
+    del d_rp, d_col
     stream = torch.cuda.Stream(device=dev)
     g.set_stream(stream)
     g.set_timing(True)
@@ -384,18 +427,46 @@ def our_arm(args):
            "api": "ldd_decompose_batch (pinned host buffers)",
            "cuts_match_device_path": e2e_cuts == [cuts[b] for b in betas]}
 
-    # ---- parity spot check of the timed outputs (last beta) and CPU baseline
+    # ---- parity of the timed outputs (every beta) and CPU baseline
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
 
-        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shifts[-1])
-        assert np.array_equal(center.cpu().numpy(), oc), "timed output differs from the oracle"
-        t_cpu = run_oracle(G, shifts)
-        cpu = {"value": len(betas) * m / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,
-               "host_cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one full step: {len(betas)} decompositions + cut counts of {args.workload}",
-               "seconds": t_cpu}
+        parity = {"decompositions": len(betas), "mismatched_vertices": 0}
+        big = m > 40_000_000  # the oracle's Dijkstra takes ~40 s there: certify instead
+        for b, sh, c_t, d_t in zip(betas, shifts, centers, dists):
+            gc, gd = c_t.cpu().numpy(), d_t.cpu().numpy()
+            if big:
+                code, bad = oracle.oracle_certify(G.row_ptr, G.col, sh, gc, gd)
+                assert code == 0, f"timed output fails the certificate ({code}) at {bad}"
+                parity["method"] = ("O(m) optimality certificate of every vertex (Lemma 3.1 "
+                                    "predecessor + non-improvability) on the timed outputs")
+            else:
+                oc, od = oracle.oracle_ldd(G.row_ptr, G.col, sh)
+                bad = int((gc != oc).sum() + (gd != od).sum())
+                parity["mismatched_vertices"] += bad
+                assert bad == 0, "timed output differs from the oracle"
+                parity["method"] = "oracle labels, element by element, every beta of the timed step"
+            assert cuts[b] == oracle.oracle_cut_edges(G.row_ptr, G.col, gc), "cut count differs"
+        if big:  # the oracle timed on a bounded sample: the same family at 1/8 the size
+            sample_name, S = args.workload, gen_sample(args.workload)
+            t0 = time.perf_counter()
+            for sh in [gen_shifts(S.n, b, spec["shift_seed"]) for b in betas]:
+                oc, _ = oracle.oracle_ldd(S.row_ptr, S.col, sh)
+                oracle.oracle_cut_edges(S.row_ptr, S.col, oc)
+            t_cpu = time.perf_counter() - t0
+            cpu = {"value": len(betas) * S.m / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,
+                   "host_cores": os.cpu_count(), "kind": "oracle", "seconds": t_cpu,
+                   "sample": f"{len(betas)} decompositions + cut counts of {S.name} "
+                             f"({S.n} vertices, {S.m} edges: the same workload at 1/8 size; "
+                             "edges per second of the full size would be no higher)"}
+        else:
+            t_cpu = run_oracle(G, shifts)
+            cpu = {"value": len(betas) * m / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,
+                   "host_cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"one full step: {len(betas)} decompositions + cut counts of "
+                             f"{args.workload}", "seconds": t_cpu}
 
     g.close()
     if rank == 0:
@@ -425,12 +496,12 @@ def our_arm(args):
             "per_beta_source": "single ldd_decompose + ldd_cut_edges calls outside the timed region",
             "wall_s_timed_region": t_wall,
             "host_s": {"graph_generation": t_graph, "shift_draw": t_shift},
+            "create_graph": create,
+            "parity": parity,
             "kernel_source_sha": kernel_source_sha(),
         }
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+        return line
+    return None
 
 
 # ----------------------------------------------------------------- batched workloads
@@ -456,7 +527,7 @@ def make_batch(name):
     return [G] * k, [spec["beta"]] * k, shifts, desc
 
 
-def batch_arm(args):
+def batch_arm(args, dist):
     """One union decomposition of the whole batch per step, against the same
     members decomposed one at a time by ldd_decompose on the same GPU."""
     import numpy as np
@@ -465,9 +536,7 @@ def batch_arm(args):
     import paper_1307_3692_gb300 as ldd
 
     world, rank, local = dist_env()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = init_dist(world, "nccl")
     t0 = time.perf_counter()
     Gs, betas, shifts, desc = make_batch(args.workload)
     t_gen = time.perf_counter() - t0
@@ -610,20 +679,25 @@ def batch_arm(args):
                       "ms_rank": st["ms_rank"], "ms_bfs": st["ms_bfs"], "ms_finalize": st["ms_finalize"],
                       "ms_cut": st["ms_cut"], "ms_total": st["ms_total"], "exact_rank": st["exact_rank"]},
             "host_s": {"generation": t_gen, "graph_and_union_creation": t_create},
+            "create_graph": {"wall_ms": 1e3 * t_create,
+                             "components_ms": sum(mg.stats()["ms_create_components"]
+                                                  for mg in uniq.values()),
+                             "note": "every member graph and the union, once per batch "
+                                     "definition, outside the timed step"},
         }
-        print(json.dumps(line), flush=True)
     u.close()
-    for m in uniq.values():
-        m.close()
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    for mg in uniq.values():
+        mg.close()
+    return line if rank == 0 else None
 
 
 # ----------------------------------------------------------------- serving
-def serve_arm(args):
+def serve_arm(args, dist):
     """A Poisson request stream replayed in real time against the batched
-    server and, on the same stream, against one-at-a-time plain calls."""
+    server and, on the same stream, against one-at-a-time plain calls; at the
+    workload's rate and at lower rates that the one-at-a-time server also
+    sustains, so that its p50/p99 there are service latencies, not queue
+    growth."""
     import numpy as np
     import torch
 
@@ -631,9 +705,7 @@ def serve_arm(args):
     import paper_1307_3692_gb300 as ldd
 
     world, rank, local = dist_env()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = init_dist(world, "nccl")
     spec = gen.SERVE_WORKLOADS[args.workload]
     t0 = time.perf_counter()
     Gs = [gen.rmat(sc) for sc in spec["rmat_scales"]] + [gen.grid2d(w, w) for w in spec["grids"]]
@@ -650,12 +722,10 @@ def serve_arm(args):
     ring = 8  # output buffers per graph (results of a benchmark stream are not kept)
     outs = [[(torch.empty(G.n, dtype=torch.int32).pin_memory(),
               torch.empty(G.n, dtype=torch.int32).pin_memory()) for _ in range(ring)] for G in Gs]
-    reqs = gen.serve_requests(len(Gs), len(betas), S, spec["rate"], spec["seconds"],
-                              spec["master_seed"] + rank)
     t_setup = time.perf_counter() - t0
-    check_every = max(1, len(reqs) // 16)
 
-    def replay(srv):
+    def replay(srv, reqs):
+        check_every = max(1, len(reqs) // 16)
         # warm-up: one request per graph (first-use allocations stay untimed)
         for gi, G in enumerate(Gs):
             c, d = outs[gi][0]
@@ -700,24 +770,42 @@ def serve_arm(args):
                 "max_submit_lag_ms": 1e3 * late}
 
     budget = spec["hbm_budget"]
-    srv = ldd.LddServer(budget, max_batch=args.max_batch, slots=2)
-    with ClockSampler(local) as clocks:
-        infos_b, checks_b, late_b = replay(srv)
-    srv.close()
-    one = ldd.LddServer(budget, max_batch=1, slots=1, one_at_a_time=True)
-    infos_1, checks_1, late_1 = replay(one)
-    one.close()
-    batched, single = summarise(infos_b, late_b), summarise(infos_1, late_1)
-    # mix check: sampled requests equal their results alone (and the other arm)
-    mismatches = 0
-    for i, (c, d) in checks_b.items():
-        _, gi, bi, si = reqs[i]
-        ac = np.empty(Gs[gi].n, np.int32)
-        ad = np.empty(Gs[gi].n, np.int32)
-        gs[gi].decompose(betas[bi], pool[gi, bi, si], ac, ad)
-        c1, d1 = checks_1[i]
-        mismatches += int(not (np.array_equal(c, ac) and np.array_equal(d, ad)
-                               and np.array_equal(c1, ac) and np.array_equal(d1, ad)))
+    rates = sorted(set([r for r in (500.0, 1000.0) if r < spec["rate"]] + [spec["rate"]]))
+    per_rate, mismatches, sampled = [], 0, 0
+    clocks = ClockSampler(local)
+    for rate in rates:
+        reqs = gen.serve_requests(len(Gs), len(betas), S, rate, spec["seconds"],
+                                  spec["master_seed"] + rank)
+        srv = ldd.LddServer(budget, max_batch=args.max_batch, slots=2)
+        if rate == spec["rate"]:
+            with clocks:
+                infos_b, checks_b, late_b = replay(srv, reqs)
+        else:
+            infos_b, checks_b, late_b = replay(srv, reqs)
+        srv.close()
+        one = ldd.LddServer(budget, max_batch=1, slots=1, one_at_a_time=True)
+        infos_1, checks_1, late_1 = replay(one, reqs)
+        one.close()
+        batched, single = summarise(infos_b, late_b), summarise(infos_1, late_1)
+        # mix check: sampled requests equal their results alone (and the other arm)
+        for i, (c, d) in checks_b.items():
+            _, gi, bi, si = reqs[i]
+            ac = np.empty(Gs[gi].n, np.int32)
+            ad = np.empty(Gs[gi].n, np.int32)
+            gs[gi].decompose(betas[bi], pool[gi, bi, si], ac, ad)
+            c1, d1 = checks_1[i]
+            mismatches += int(not (np.array_equal(c, ac) and np.array_equal(d, ad)
+                                   and np.array_equal(c1, ac) and np.array_equal(d1, ad)))
+            sampled += 1
+        sustained = single["throughput_rps"] >= 0.95 * rate
+        per_rate.append({"rate_rps": rate, "requests": len(reqs), "batched": batched,
+                         "one_at_a_time": single,
+                         "one_at_a_time_sustains_rate": bool(sustained),
+                         "p50_speedup": single["p50_ms"] / batched["p50_ms"],
+                         "p99_speedup": single["p99_ms"] / batched["p99_ms"],
+                         "throughput_speedup": batched["throughput_rps"] / single["throughput_rps"]})
+    top = per_rate[-1]
+    batched, single = top["batched"], top["one_at_a_time"]
     m_req = np.mean([Gs[gi].m for _, gi, _, _ in reqs])
     if rank == 0:
         clk = clocks.summary()
@@ -737,9 +825,11 @@ def serve_arm(args):
             "batched": batched, "one_at_a_time": single,
             "p99_speedup": single["p99_ms"] / batched["p99_ms"],
             "throughput_speedup": batched["throughput_rps"] / single["throughput_rps"],
+            "by_rate": per_rate,
             "served_gteps": batched["throughput_rps"] * m_req / 1e9,
-            "mix_check": {"sampled": len(checks_b), "mismatches": mismatches,
-                          "against": "ldd_decompose alone on the same graph and shifts"},
+            "mix_check": {"sampled": sampled, "mismatches": mismatches,
+                          "against": "ldd_decompose alone on the same graph and shifts, and "
+                                     "the one-at-a-time server's result"},
             "roofline": None, "cpu_baseline": None,
             "e2e": {"value": world * batched["throughput_rps"], "unit": "decompositions/s",
                     "h2d_bytes_per_step": int(sum(8 * Gs[gi].n for _, gi, _, _ in reqs)),
@@ -749,13 +839,125 @@ def serve_arm(args):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"]},
             "host_s": {"setup": t_setup},
+            "create_graph": {"components_ms": sum(g.stats()["ms_create_components"] for g in gs),
+                             "note": "the 15 resident graphs, once, before the stream starts"},
         }
-        print(json.dumps(line), flush=True)
     for g in gs:
         g.close()
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
+
+
+# ----------------------------------------------------------------- block decomposition
+def blocks_arm(args, dist):
+    """Blocks by repeated decomposition (ldd_block_decompose) of one graph per
+    step, every block checked against the oracle's loop."""
+    import numpy as np
+    import torch
+
+    import ldd_gen as gen
+    import paper_1307_3692_gb300 as ldd
+
+    world, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    spec = gen.BLOCK_WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    G = gen.make_graph(spec["graph"])
+    k = spec["vectors"]
+    shifts = [gen.shifts(G.n, spec["beta"], spec["first_seed"] + i) for i in range(k)]
+    t_gen = time.perf_counter() - t0
+    d_rp, d_col = torch.from_numpy(G.row_ptr).to(dev), torch.from_numpy(G.col).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = ldd.LddGraph(d_rp, d_col, validate=False)
+    create = create_info(g, time.perf_counter() - t0)
+    del d_rp, d_col
+    stream = torch.cuda.Stream(device=dev)
+    g.set_stream(stream)
+    d_sh = [torch.from_numpy(x).to(dev) for x in shifts]
+    cs = [torch.empty(G.n, dtype=torch.int32, device=dev) for _ in range(k)]
+    ds = [torch.empty(G.n, dtype=torch.int32, device=dev) for _ in range(k)]
+    ab = torch.empty(G.nnz, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    betas = [spec["beta"]] * k
+    for _ in range(args.warmup):
+        g.block_decompose(betas, d_sh, cs, ds, ab)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sts = []
+    barrier(dist)
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+            ev[i][0].record(stream)
+            nb, rem = g.block_decompose(betas, d_sh, cs, ds, ab)
+            ev[i][1].record(stream)
+            sts.append(g.stats())
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = reduce_max(dist, sum(a.elapsed_time(b) for a, b in ev) / args.steps, dev)
+    st = sts[-1]
+    # the residual passes (filter, scan, component tables) move, per arc of G_i
+    # read twice, 4 B col + 4 B input-arc id + 4 B center gather, per arc kept
+    # 8 B written, per vertex and iteration about 28 B (row offsets, labels,
+    # union-find)
+    res_bytes = (24 * st["block_arcs_scanned"] + 8 * st["block_arcs_kept"]
+                 + 28 * G.n * nb)
+    peak, peak_kind = measured_peak_hbm()
+    res_ach = res_bytes / (st["ms_block_residual"] * 1e-3) / 1e9 if st["ms_block_residual"] > 0 else 0.0
+    parity = cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        t0 = time.perf_counter()
+        oc, od, oab, orem = oracle.oracle_block_decompose(G.row_ptr, G.col, shifts)
+        t_cpu = time.perf_counter() - t0
+        bad = int((ab.cpu().numpy() != oab).sum())
+        for i in range(len(oc)):
+            bad += int((cs[i].cpu().numpy() != oc[i]).sum() + (ds[i].cpu().numpy() != od[i]).sum())
+        parity = {"blocks": nb, "oracle_blocks": len(oc), "remaining_equal": rem == list(orem),
+                  "mismatches": bad,
+                  "method": "every arc's block and every iteration's centers and distances "
+                            "against the oracle's loop"}
+        assert bad == 0 and rem == list(orem) and nb == len(oc), parity
+        cpu = {"value": G.m / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,
+               "host_cores": os.cpu_count(), "kind": "oracle", "seconds": t_cpu,
+               "sample": f"one full block decomposition of {args.workload} ({len(oc)} iterations)"}
+    g.close()
+    if rank != 0:
+        return None
+    clk = clocks.summary()
+    return {
+        "metric": "LDD block decompositions/s", "value": world * 1e3 / ms,
+        "unit": "block decompositions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload,
+                   "graph": f"R-MAT scale {spec['graph'][1]}, edge factor 16, seed 7",
+                   "n": G.n, "m": G.m, "beta": spec["beta"], "shift_vectors": k,
+                   "step": "one ldd_block_decompose: decompose, keep the cut edges, repeat until "
+                           "none is left",
+                   "l2": "flushed between steps", "parallelism": f"replicas x{world}"},
+        "gteps": world * G.m / (ms * 1e-3) / 1e9,
+        "blocks": nb, "remaining_edges": rem,
+        "ms_residual_passes": st["ms_block_residual"],
+        "ms_decompositions": st["ms_block_total"] - st["ms_block_residual"],
+        "roofline": {"bound": "hbm", "kernel": "k_residual (count + write passes, scan, "
+                                               "component tables)",
+                     "achieved": res_ach, "peak": peak, "unit": "GB/s", "frac": res_ach / peak,
+                     "traffic": None, "peak_kind": f"of {peak_kind}",
+                     "algorithmic_bytes_per_call": res_bytes,
+                     "share_of_step": st["ms_block_residual"] / max(st["ms_block_total"], 1e-9),
+                     "note": "the decompositions of G_0, G_1, ... are the round-loop kernels of "
+                             "the single-graph lines"},
+        "cpu_baseline": cpu, "parity": parity,
+        "e2e": None, "gpu_launches": None,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"]},
+        "host_s": {"generation": t_gen},
+        "create_graph": create,
+    }
 
 
 # ----------------------------------------------------------------- Figure 1
@@ -823,6 +1025,23 @@ def fig1_arm(args):
     return 0
 
 
+# Lines nested in the default run's output, after the headline: every other
+# configuration of the method (workload, arm, most timed steps).
+EXTRAS = [
+    ("grid2d_256", "single", 20),
+    ("grid3d_256", "single", 10),
+    ("rmat20_seeds_64", "batch", 5),
+    ("rgg_batch_1024", "batch", 3),
+    ("rmat20_blocks", "blocks", 5),
+    ("serve_mix", "serve", 1),
+]
+
+
+def run_arm(kind, args, dist):
+    return {"single": our_arm, "batch": batch_arm, "serve": serve_arm,
+            "blocks": blocks_arm}[kind](args, dist)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -830,6 +1049,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--single", action="store_true",
+                    help="only the named workload's line (the default R-MAT 22 run also nests "
+                         "a line for every other configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-batch", type=int, default=256,
                     help="serving: most requests per batch")
@@ -841,30 +1063,49 @@ def main(argv=None):
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     import ldd_gen
 
-    if args.workload == "fig1":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable":
-                              "the Figure 1 sweep checks every labelling against the oracle "
-                              "itself"}), flush=True)
-            return 0
-        return fig1_arm(args)
-    if args.workload in ldd_gen.SERVE_WORKLOADS:
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable":
-                              "the serving workload has no reference arm; its line compares "
-                              "against one-at-a-time plain calls"}), flush=True)
-            return 0
-        return serve_arm(args)
-    if args.workload in ldd_gen.BATCH_WORKLOADS:
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable":
-                              "the batched workloads have no reference arm; their line carries "
-                              "the oracle's sample as cpu_baseline"}), flush=True)
-            return 0
-        return batch_arm(args)
+    kinds = {name: "single" for name in ldd_gen.WORKLOADS}
+    kinds.update({name: "batch" for name in ldd_gen.BATCH_WORKLOADS})
+    kinds.update({name: "serve" for name in ldd_gen.SERVE_WORKLOADS})
+    kinds.update({name: "blocks" for name in ldd_gen.BLOCK_WORKLOADS})
+    kinds["fig1"] = "fig1"
+    if args.workload not in kinds:
+        ap.error(f"unknown workload {args.workload}")
+    kind = kinds[args.workload]
     if args.impl == "reference":
-        return reference_arm(args)
-    return our_arm(args)
+        if kind == "single":
+            return reference_arm(args)
+        why = {"fig1": "the Figure 1 sweep checks every labelling against the oracle itself",
+               "serve": "the serving workload has no reference arm; its line compares against "
+                        "one-at-a-time plain calls",
+               "batch": "the batched workloads have no reference arm; their line carries the "
+                        "oracle's sample as cpu_baseline",
+               "blocks": "the block decomposition's line carries the oracle's loop as "
+                         "cpu_baseline"}[kind]
+        print(json.dumps({"impl": "reference", "unavailable": why}), flush=True)
+        return 0
+    if kind == "fig1":
+        return fig1_arm(args)
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    line = run_arm(kind, args, dist)
+    if args.workload == "rmat22" and not args.single:
+        nested = {}
+        for name, sub_kind, max_steps in EXTRAS:
+            sub = argparse.Namespace(**vars(args))
+            sub.workload = name
+            sub.steps = max(1, min(args.steps, max_steps))
+            torch.cuda.empty_cache()
+            nested[name] = run_arm(sub_kind, sub, dist)
+        if rank == 0:
+            line["workloads"] = nested
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
 
 
 if __name__ == "__main__":

@@ -264,9 +264,11 @@ int ldd_block_decompose(ldd_graph* g, int k, const double* betas, const double* 
  * workers build their unions and copy shifts in and results out, so requests
  * that arrive while a batch runs join the next one as soon as a workspace
  * frees up.  A request whose input fails (a bad shift) fails alone: its batch
- * is rerun request by request.  Graphs passed to a server must stay alive and
- * must not be destroyed until their requests are collected; with
- * one_at_a_time set, they must not be used on another thread meanwhile.
+ * is rerun request by request.  A batch that holds a single request skips the
+ * union and runs on that request's own graph object (at low arrival rates the
+ * union would only add latency).  Graphs passed to a server must stay alive,
+ * must not be destroyed until their requests are collected, and must not be
+ * used on another thread while they have requests in flight.
  */
 typedef struct ldd_server ldd_server;
 
@@ -402,6 +404,15 @@ typedef struct {
   float ms_cut;           /* whole ldd_cut_edges on the stream */
   float ms_replay;        /* the replayed CUDA graph (rank .. finalize), when replayed */
   int32_t replayed;       /* 1: the last decomposition ran as a graph replay */
+  float ms_create_upload; /* ldd_create_graph: CSR upload to the device (events, once per graph) */
+  float ms_create_components; /* ldd_create_graph: component labelling and the small-component
+                             tables (device span, once per graph) */
+  float ms_create_total;  /* ldd_create_graph: the whole call (host clock), including the host-side
+                             cut-list build */
+  float ms_block_total;   /* last ldd_block_decompose: the whole call on the stream (events) */
+  float ms_block_residual;/* ... of which the residual-graph passes (filter, scan, components) */
+  int64_t block_arcs_scanned; /* arcs of G_0, G_1, ... read by the residual passes */
+  int64_t block_arcs_kept;    /* arcs written as G_1, G_2, ... */
 } ldd_stats;
 
 int ldd_get_stats(const ldd_graph* g, ldd_stats* out);

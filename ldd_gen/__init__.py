@@ -237,6 +237,15 @@ WORKLOADS = {
 # 2D grids 64^2 .. 2048^2; beta from {0.02, 0.05, 0.1, 0.2, 0.5}; each request
 # takes one of two pre-drawn shift vectors per (graph, beta), shift seed
 # 1000 + 100 graph + 10 beta + seed index; a 120 GB HBM budget.
+# Block decomposition by repeated decomposition (Section 1's remark on Linial
+# and Saks' blocks): one R-MAT scale-20 graph (scale-22 parameters, seed 7),
+# beta 1/2, shift vectors of seeds first_seed .. first_seed + vectors - 1
+# (far more than the O(log n) iterations the loop needs).
+BLOCK_WORKLOADS = {
+    "rmat20_blocks": dict(graph=("rmat", 20, 16, 0.57, 0.19, 0.19, 7), beta=0.5, vectors=48,
+                          first_seed=1),
+}
+
 SERVE_WORKLOADS = {
     "serve_mix": dict(rmat_scales=tuple(range(14, 23)), grids=(64, 128, 256, 512, 1024, 2048),
                       betas=(0.02, 0.05, 0.1, 0.2, 0.5), seeds=2, rate=2000.0, seconds=2.0,

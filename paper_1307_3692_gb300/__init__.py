@@ -49,7 +49,11 @@ class _Stats(ctypes.Structure):
         "launches", "cut_launches", "exact_rank")] + [("bfs_grid", ctypes.c_int32), ("bfs_block", ctypes.c_int32)] + [
         (name, ctypes.c_float) for name in (
             "ms_h2d", "ms_rank", "ms_bfs", "ms_finalize", "ms_d2h", "ms_total", "ms_cut",
-            "ms_replay")] + [("replayed", ctypes.c_int32)]
+            "ms_replay")] + [("replayed", ctypes.c_int32)] + [
+        (name, ctypes.c_float) for name in ("ms_create_upload", "ms_create_components",
+                                            "ms_create_total", "ms_block_total",
+                                            "ms_block_residual")] + [
+        (name, ctypes.c_int64) for name in ("block_arcs_scanned", "block_arcs_kept")]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64

@@ -583,11 +583,13 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
   }
   const u32 total = from_list ? ncand : a.n;
   const u32 stride = gridDim.x * blockDim.x * kPullV;
-  for (u32 base = warp_first_item(kPullV); base < total; base += stride) {
-    u32 w[kPullV];
+  // The passes are software-pipelined: pass p + 1's candidates are requested
+  // when pass p starts, and their keys and adjacency ranges while pass p makes
+  // its appends, so a pass waits only on its neighbour scans and its appends.
+  auto load_ids = [&](u32 b, u32 (&w)[kPullV]) {
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
-      const u32 i = base + (u32)j * 32 + lane;
+      const u32 i = b + (u32)j * 32 + lane;
       w[j] = kNone;
       if (from_list) {
         if (i < total) w[j] = ld_cg_u32(cand + i);
@@ -596,9 +598,10 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
         if (!((ex >> lane) & 1u)) w[j] = i;
       }
     }
-    // the key and the adjacency range together: one round trip, not two
-    u64 kw[kPullV];
-    int e[kPullV], re[kPullV];
+  };
+  // the key and the adjacency range together: one round trip, not two
+  auto load_keys = [&](const u32 (&w)[kPullV], u64 (&kw)[kPullV], int (&e)[kPullV],
+                       int (&re)[kPullV]) {
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       kw[j] = 0ull;
@@ -610,6 +613,16 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
         re[j] = __ldg(a.row_ptr + w[j] + 1);
       }
     }
+  };
+  u32 base = warp_first_item(kPullV);
+  u32 w[kPullV];
+  u64 kw[kPullV];
+  int e[kPullV], re[kPullV];
+  load_ids(base, w);
+  load_keys(w, kw, e, re);
+  for (; base < total; base += stride) {
+    u32 wn[kPullV];  // the next pass's candidates, in flight during this pass
+    load_ids(base + stride, wn);
     int rs0[kPullV], re0[kPullV];  // the adjacency ranges, for the appends
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
@@ -695,6 +708,9 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
         }
       }
     }
+    u64 kwn[kPullV];  // the next pass's keys and ranges, beside this pass's appends
+    int en[kPullV], ren[kPullV];
+    load_keys(wn, kwn, en, ren);
     u32 mask = 0, keep = 0, won = 0;
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
@@ -711,6 +727,13 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
     for (int j = 0; j < kPullV; ++j)
       note_rank<U>(a, (u32)qi, (won >> j) & 1u, w[j], (u32)best[j], myrank, s_acc);
     pull_append<kPullV, LD>(mask, keep, w, rs0, re0, a, qi, qb, ulist_out, ucnt_out);
+#pragma unroll
+    for (int j = 0; j < kPullV; ++j) {
+      w[j] = wn[j];
+      kw[j] = kwn[j];
+      e[j] = en[j];
+      re[j] = ren[j];
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -411,14 +411,15 @@ __global__ void __launch_bounds__(256) k_max_i32(const int* __restrict__ x, u32 
 // arc ids and hooks each kept (v, w), v < w, into the union-find forest of
 // G_{i+1}'s components.  Row order inside a row is free, and only the rows
 // walked by one thread or one warp keep it.
-//   * A warp takes 32 consecutive vertices, one per lane; a lane walks a row
-//     of at most kResShort arcs alone.
+//   * A warp takes 32 consecutive vertices, one per lane; a lane takes a row
+//     of at most kResShort arcs alone, loading all its arcs' ids and then all
+//     their centers before any decision.
 //   * Rows of up to kResWarp arcs are walked by the whole warp, kResUnroll
 //     chunks of 32 arcs per step (loads of all chunks first), a ballot giving
 //     every kept arc its place.
 //   * Longer rows (R-MAT hubs) are listed by the count pass and walked by one
 //     CTA each (k_residual_long), which reserves places with a shared counter.
-constexpr int kResShort = 32;
+constexpr int kResShort = 8;
 constexpr int kResWarp = 4096;
 constexpr int kResUnroll = 4;
 constexpr int kResLongThreads = 512;
@@ -474,15 +475,22 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
     const int deg = e1 - e0;
     u32 cnt = 0;
     if (deg <= kResShort) {
-      for (int e = e0; e < e1; ++e) {
-        const u32 w = (u32)a.col[e];
-        const bool keep = w < a.n && a.center[w] != cv;
-        res_arc<kWrite>(a, v, w, e, keep, out, up);
-        if (keep) {
-          ++cnt;
-          ++out;
+      u32 w[kResShort];
+      int cw[kResShort];
+#pragma unroll
+      for (int q = 0; q < kResShort; ++q) w[q] = q < deg ? (u32)a.col[e0 + q] : 0xffffffffu;
+#pragma unroll
+      for (int q = 0; q < kResShort; ++q) cw[q] = w[q] < a.n ? a.center[w[q]] : cv;
+#pragma unroll
+      for (int q = 0; q < kResShort; ++q)
+        if (q < deg) {
+          const bool keep = w[q] < a.n && cw[q] != cv;
+          res_arc<kWrite>(a, v, w[q], e0 + q, keep, out, up);
+          if (keep) {
+            ++cnt;
+            ++out;
+          }
         }
-      }
     } else if (deg > kResWarp && !kWrite) {
       a.long_rows[atomicAdd(a.n_long, 1u)] = v;  // k_residual_long takes it
     }

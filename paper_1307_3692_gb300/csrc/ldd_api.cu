@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <new>
 #include <vector>
 
@@ -1088,6 +1089,7 @@ const char* ldd_last_error(void) { return g_last_error; }
 int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                      int validate, ldd_graph** out) {
   g_last_error[0] = 0;
+  const auto t_start = std::chrono::steady_clock::now();
   if (!out) return fail(LDD_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n < 0 || nnz < 0) return fail(LDD_ERR_ARG, "negative size (n = %d, nnz = %lld)", n,
@@ -1145,6 +1147,31 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
     for (int64_t e = rp[v]; e < rp[v + 1]; ++e)
       if (col[e] > v) up.push_back(make_int2(v, col[e]));
   g->m_up = (u32)up.size();
+  cudaEvent_t ce[3] = {nullptr, nullptr, nullptr};  // upload, component labelling
+  for (auto& e : ce)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      e = nullptr;
+    }
+  auto mark = [&](int i) {
+    if (ce[i]) cudaEventRecord(ce[i], nullptr);
+  };
+  auto span = [&](int a, int b) {
+    float ms = -1.f;
+    if (!ce[a] || !ce[b] || cudaEventSynchronize(ce[b]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, ce[a], ce[b]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.f;
+    }
+    return ms;
+  };
+  struct EventsFree {
+    cudaEvent_t* e;
+    ~EventsFree() {
+      for (int i = 0; i < 3; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    }
+  } events_free{ce};
   int2* d_arcs = nullptr;  // the arcs (v, w), v < w, for the component labelling only
   if (cudaMalloc(&g->d_row, rp.size() * 4) != cudaSuccess ||
       cudaMalloc(&g->d_col, std::max<size_t>(col.size(), 1) * 4) != cudaSuccess ||
@@ -1153,6 +1180,7 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
     cudaFree(d_arcs);
     return bail(fail(LDD_ERR_OOM, "device allocation of the graph failed"));
   }
+  mark(0);
   if (cudaMemcpy(g->d_row, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       (nnz > 0 &&
        cudaMemcpy(g->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
@@ -1161,9 +1189,12 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
     cudaFree(d_arcs);
     return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
   }
+  mark(1);
   rc = build_component_tables(g, d_arcs);
+  mark(2);
   cudaFree(d_arcs);
   if (rc != LDD_OK) return bail(rc);
+  const float ms_upload = span(0, 1), ms_components = span(1, 2);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
   if ((rc = build_active_list(g)) != LDD_OK) return bail(rc);
   if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);
@@ -1171,6 +1202,10 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   // is one more dependent round trip, worth it only in wide rounds
   if (g->max_degree <= (u32)kLdMaxDegree && !getenv("LDD_PROBE_MIN_ARCS"))
     g->probe_min_arcs = 1u << 20;
+  g->stats.ms_create_upload = ms_upload;
+  g->stats.ms_create_components = ms_components;
+  g->stats.ms_create_total =
+      std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   *out = g;
   return LDD_OK;
 }

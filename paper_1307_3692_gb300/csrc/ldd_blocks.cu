@@ -43,6 +43,7 @@ struct Blocks {
   u32* long_rows = nullptr;    // [n] rows the count pass leaves to one CTA each
   u32* n_long = nullptr;
   unsigned long long* h_up = nullptr;  // pinned: [0] edges left, [1] arcs left
+  cudaEvent_t ev[4] = {};      // call start / end, residual passes start / end
 };
 
 void free_blocks(ldd_graph* g) {
@@ -67,6 +68,8 @@ void free_blocks(ldd_graph* g) {
   cudaFree(b->long_rows);
   cudaFree(b->n_long);
   if (b->h_up) cudaFreeHost(b->h_up);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
   delete b;
   g->blk = nullptr;
 }
@@ -91,6 +94,7 @@ int setup_blocks(ldd_graph* g) {
        cudaMalloc(&b->long_rows, std::max<size_t>(n, 1) * 4) == cudaSuccess &&
        cudaMalloc(&b->n_long, 4) == cudaSuccess &&
        cudaMallocHost(&b->h_up, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  for (auto& e : b->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_blocks(g);
@@ -185,7 +189,19 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
   const size_t n = (size_t)g->n;
   const bool dev_blk = out_arc_block && is_device_ptr(out_arc_block);
   int* arc_block = dev_blk ? out_arc_block : B.arc_block;
+  CUDA_TRY(cudaEventRecord(B.ev[0], s));
   CUDA_TRY(cudaMemsetAsync(arc_block, 0xff, (size_t)g->nnz * 4, s));
+  float ms_residual = 0.f;
+  u64 arcs_scanned = 0, arcs_kept = 0;
+  auto residual_ms = [&]() {
+    float ms = 0.f;
+    if (cudaEventSynchronize(B.ev[3]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, B.ev[2], B.ev[3]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    return ms;
+  };
   ldd_graph* cur = g;  // G_i
   const int* cur_row = g->d_row;
   const int* cur_col = g->d_col;
@@ -219,6 +235,7 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     CUDA_TRY(cudaMemsetAsync(B.row[j] + n, 0, 4, s));
     CUDA_TRY(cudaMemsetAsync(B.up, 0, sizeof(unsigned long long), s));
     CUDA_TRY(cudaMemsetAsync(B.n_long, 0, 4, s));
+    CUDA_TRY(cudaEventRecord(B.ev[2], s));
     if (r->epoch > 0xfffff000u) {
       CUDA_TRY(cudaMemsetAsync(r->d_status, 0, r->status_bytes, s));
       r->epoch = 0;
@@ -231,8 +248,11 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     CUDA_TRY(cudaMemcpyAsync(B.h_up, B.up, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(B.h_up + 1, B.row[j] + n, 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(r->h_hdr, r->d_ctl, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaEventRecord(B.ev[3], s));
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
+    ms_residual += residual_ms();
+    arcs_scanned += (u64)(cur == g ? g->nnz : cur->nnz);
     u32 err;
     memcpy(&err, r->h_hdr, 4);
     if (err) {
@@ -245,6 +265,8 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     if (out_remaining) out_remaining[i + 1] = (int64_t)edges_left;
     if (arcs_left == 0 || i + 1 == k) break;
     // G_{i+1}: arcs, component forest, component tables
+    arcs_kept += arcs_left;
+    CUDA_TRY(cudaEventRecord(B.ev[2], s));
     cudaError_t e = components_init((u32)n, g->num_sms, B.t, r->d_excl, r->d_solo, s);
     if (e != cudaSuccess) return fail(LDD_ERR_CUDA, "component set-up: %s", cudaGetErrorString(e));
     launch_residual(true, cur_row, cur_col, cur_orig, center, (u32)n, i, nullptr, nullptr,
@@ -265,6 +287,9 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     r->d_col = B.col[j];
     if ((e = components_phase2(r->d_row, r->d_col, B.t, r->sc, g->num_sms, s)) != cudaSuccess)
       return fail(LDD_ERR_CUDA, "component adjacency: %s", cudaGetErrorString(e));
+    CUDA_TRY(cudaEventRecord(B.ev[3], s));
+    ms_residual += residual_ms();
+    r->nnz = (int64_t)arcs_left;
     cur = r;
     cur_row = B.row[j];
     cur_col = B.col[j];
@@ -273,7 +298,17 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
   if (out_arc_block && !dev_blk)
     CUDA_TRY(cudaMemcpyAsync(out_arc_block, arc_block, (size_t)g->nnz * 4, cudaMemcpyDeviceToHost,
                              s));
+  CUDA_TRY(cudaEventRecord(B.ev[1], s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  float ms_total = -1.f;
+  if (cudaEventElapsedTime(&ms_total, B.ev[0], B.ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    ms_total = -1.f;
+  }
+  g->stats.ms_block_total = ms_total;
+  g->stats.ms_block_residual = ms_residual;
+  g->stats.block_arcs_scanned = (int64_t)arcs_scanned;
+  g->stats.block_arcs_kept = (int64_t)arcs_kept;
   *out_blocks = blocks;
   return LDD_OK;
 }

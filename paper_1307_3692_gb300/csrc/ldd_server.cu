@@ -194,6 +194,23 @@ int run_batch(ldd_server* S, int slot, const std::vector<Request*>& batch) {
   return LDD_OK;
 }
 
+// A batch of one request skips the union: the request runs on its own graph
+// object, as ldd_decompose_batch(g, 1, ...) does, with the device held for the
+// whole call (two workers may hold requests on the same graph).  At low
+// arrival rates most batches are of one, and building a union for them only
+// adds latency.
+int run_alone(ldd_server* S, Request* r) {
+  std::lock_guard<std::mutex> lk(S->dev_mu);
+  const double t0 = S->now_us();
+  const double* sh = r->shifts;
+  int32_t* oc = r->out_center;
+  int32_t* od = r->out_dist;
+  const int rc = ldd_decompose_batch(r->g, 1, &r->beta, &sh, &oc, &od, r->out_cut);
+  r->fill_us = 0.0;
+  r->run_us = S->now_us() - t0;
+  return rc;
+}
+
 void worker_batched(ldd_server* S, int slot) {
   cudaSetDevice(S->device);
   for (;;) {
@@ -218,14 +235,14 @@ void worker_batched(ldd_server* S, int slot) {
       r->batch_id = bid;
       r->batch_size = (int32_t)batch.size();
     }
-    int rc = run_batch(S, slot, batch);
+    int rc = batch.size() == 1 ? run_alone(S, batch[0]) : run_batch(S, slot, batch);
     if (rc != LDD_OK && batch.size() > 1) {
       // rerun one by one so that only the request at fault fails
       cudaStreamSynchronize(S->streams[(size_t)slot]);
       cudaGetLastError();
       for (Request* r : batch) {
         r->batch_size = 1;
-        r->status = run_batch(S, slot, std::vector<Request*>{r});
+        r->status = run_alone(S, r);
         if (r->status != LDD_OK) snprintf(r->msg, sizeof(r->msg), "%s", ldd_last_error());
       }
     } else {
