@@ -74,6 +74,7 @@ struct Smem {
   u64 next_c;
   u32 next_minrank;
   u32 next_ucnt;
+  int next_lo, next_hi;  // the next round's start bucket (lvl + 1) bounds
 };
 
 // Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a
@@ -85,14 +86,15 @@ struct Smem {
 // visible.  The wait is bounded: after `limit` polls (or once any CTA has
 // recorded an error) it sets kErrTimeout and returns.  Thread 0 then reads,
 // in one round trip, the error word and the next round's state (slot `post`
-// of the frontier counter, bottom-up floor and unsettled-list length) into
-// shared memory, so that every thread of the CTA sees the same values and
+// of the frontier counter, bottom-up floor and unsettled-list length, and the
+// bounds of start bucket blevel unless it is negative) into shared memory, so that every thread of the CTA sees the same values and
 // takes the same branch after the barrier (a thread that left the loop alone
 // would leave the others at a CTA barrier).  phantom > 0 waits for CTAs that
 // do not exist: the barrier can then only end by running out of polls, which
 // is how the timeout path is tested.
 __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 phantom,
-                                             u32 limit, u32 post, Smem& s) {
+                                             u32 limit, u32 post, const int* bptr, int blevel,
+                                             Smem& s) {
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s.minrank != 0xffffffffu) atomicMin(&ctl->minrank[post], s.minrank);
@@ -117,6 +119,11 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
     s.next_c = ld_cg_u64(&ctl->qctr[post]);
     s.next_minrank = ld_cg_u32(&ctl->minrank[post]);
     s.next_ucnt = ld_cg_u32(&ctl->ucnt[post]);
+    s.next_lo = s.next_hi = 0;
+    if (blevel >= 0) {  // bounds of start bucket blevel, for the round after the barrier
+      s.next_lo = __ldg(bptr + blevel);
+      s.next_hi = __ldg(bptr + blevel + 1);
+    }
     s.stop = err != 0u ? 1u : 0u;
   }
   __syncthreads();
@@ -276,8 +283,12 @@ __device__ __forceinline__ void warp_append(u32 mask, const u32 (&v)[K], const B
 // Unclaimed vertices of start bucket rr join the frontier of level rr.
 template <bool U>
 __device__ __forceinline__ void append_bucket(const BfsArgs& a, int rr, const u32* rv, int qi,
-                                              int qb, u32& myrank, u32* s_acc) {
-  const int lo = __ldg(a.bptr + rr), hi = __ldg(a.bptr + rr + 1);
+                                              int qb, u32& myrank, u32* s_acc, int lo = -1,
+                                              int hi = -1) {
+  if (lo < 0) {  // bounds not known yet
+    lo = __ldg(a.bptr + rr);
+    hi = __ldg(a.bptr + rr + 1);
+  }
   const u32 cnt = (u32)(hi - lo);
   const u32 lane = threadIdx.x & 31;
   const u32 stride = gridDim.x * blockDim.x;
@@ -792,7 +803,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
     __syncthreads();
     flush_members(a, 0, s_acc);
   }
-  grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, 0, s);
+  grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, 0, a.bptr, A >= 1 ? 1 : -1, s);
   const bool profiler = blockIdx.x == 0 && threadIdx.x == 0;
   if (profiler) {
     const long long t = clock64();
@@ -808,11 +819,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   for (;;) {
     if (s.stop) break;  // set by the last barrier, the same for every thread of the CTA
     const u64 c = s.next_c;  // slot phase % 3, read as the last barrier released
-    int nb_lo = 0, nb_hi = 0;  // low-degree rounds: start bucket lvl + 1, loaded beside the counter
-    if (LD && lvl + 1 <= A) {
-      nb_lo = __ldg(a.bptr + lvl + 1);
-      nb_hi = __ldg(a.bptr + lvl + 2);
-    }
+    const int nb_lo = s.next_lo, nb_hi = s.next_hi;  // start bucket lvl + 1 (if lvl + 1 <= A)
     const u32 Q = (u32)(c >> 32);
     // low-degree mode keeps no arc count: the frontier's arcs are estimated
     // from the mean degree (direction choice and probe threshold only)
@@ -857,7 +864,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
             expand_ld<U>(a, nullptr, 0, 0, rv, nb_lo, (u32)(nb_hi - nb_lo), (u32)lvl + 1, false,
                          qi, qb, myrank, s_acc, pushed);
           } else {
-            append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc);
+            append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc, nb_lo, nb_hi);
           }
         }
       } else if (LD) {  // expansion and start bucket lvl + 1 in one pass
@@ -868,7 +875,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
         expand<U>(a, s, (int)(phase & 1), Q, E, lvl, qi, qb, myrank, s_acc);
         push_arcs += E;
         if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
-        if (lvl + 1 <= A) append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc);
+        if (lvl + 1 <= A) append_bucket<U>(a, lvl + 1, rv, qi, qb, myrank, s_acc, nb_lo, nb_hi);
       }
       nlvl = lvl + 1;
     } else {
@@ -893,7 +900,8 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       __syncthreads();
       flush_members(a, (u32)qi, s_acc);
     }
-    grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, (u32)qi, s);
+    grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, (u32)qi, a.bptr,
+                 nlvl + 1 <= A ? nlvl + 1 : -1, s);
     ++phase;
     lvl = nlvl;
     if (profiler && phase < (u32)kRoundProfile) {

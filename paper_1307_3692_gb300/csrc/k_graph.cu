@@ -23,6 +23,8 @@
 // BFS start buckets, so the round loop ends when the large components are
 // settled instead of visiting every start round up to floor(delta_max).
 //
+#include <algorithm>
+
 #include "ldd_internal.cuh"
 
 namespace ldd {
@@ -289,17 +291,112 @@ __global__ void k_cc_hook(const int2* __restrict__ up, u32 m_up, u32* parent) {
   }
 }
 
-// Final labels.  The walk here only reads: a compressing walk could overwrite
-// a label another thread has just set to the root with a non-root ancestor.
-// Every store is a root, so concurrent walks stay valid.
-__global__ void k_cc_finish(u32* parent, u32* csize, u32 n) {
+// Labelling from the CSR, after Afforest (Sutton, Ben-Nun, Barak 2018): every
+// vertex is first linked to its r-th neighbour only (r = 0, 1), which joins
+// nearly all of a large component; after compression the most common root c
+// is found by sampling, and only the vertices outside c link their remaining
+// arcs.  Every edge {v, w} with an end outside c is then linked from that end
+// (the CSR holds both arcs), and edges inside c need nothing: the components
+// are exact, with a fraction of the union-find work when one component holds
+// most of the graph (R-MAT).
+__global__ void k_cc_link_nth(const int* __restrict__ row_ptr, const int* __restrict__ col, u32 n,
+                              int r, u32* parent) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int e = row_ptr[v] + r;
+    if (e < row_ptr[v + 1]) {
+      const u32 w = (u32)col[e];
+      if (w < n && w != v) cc_unite(parent, v, w);
+    }
+  }
+}
+
+// Every vertex points straight at its root.  Only v's thread writes parent[v],
+// and it writes the root, so concurrent walks through v stay valid.
+__global__ void k_cc_compress(u32* parent, u32 n) {
   volatile u32* p = parent;
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    u32 r = v, nx;
+    u32 r = p[v], nx;
     while ((nx = p[r]) != r) r = nx;
     p[v] = r;
-    atomicAdd(csize + r, 1u);
   }
+}
+
+// The roots of `count` evenly spaced vertices, for the host to find the most
+// common one.
+__global__ void k_cc_sample(const u32* __restrict__ parent, u32 n, u32 count, u32* out) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = parent[(u32)((u64)i * n / count)];
+}
+
+// The arcs from the third on of every vertex outside component c: one lane per
+// row of up to 32 arcs, the whole warp for a longer row.
+__global__ void __launch_bounds__(256) k_cc_link_rest(const int* __restrict__ row_ptr,
+                                                      const int* __restrict__ col, u32 n, u32 c,
+                                                      u32* parent) {
+  const u32 lane = threadIdx.x & 31;
+  const u32 warps = gridDim.x * (blockDim.x / 32);
+  for (u32 base = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < n;
+       base += warps * 32) {
+    const u32 v = base + lane;
+    int e0 = 0, e1 = 0;
+    if (v < n) {
+      e0 = row_ptr[v] + 2;
+      e1 = row_ptr[v + 1];
+      if (e0 < e1 && cc_root(parent, v) == c) e1 = e0;  // inside c: nothing to link
+    }
+    if (e1 - e0 <= 32)
+      for (int e = e0; e < e1; ++e) {
+        const u32 w = (u32)col[e];
+        if (w < n && w != v) cc_unite(parent, v, w);
+      }
+    u32 lm = __ballot_sync(kFull, e1 - e0 > 32);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const u32 sv = __shfl_sync(kFull, v, src);
+      const int b0 = __shfl_sync(kFull, e0, src), b1 = __shfl_sync(kFull, e1, src);
+      for (int e = b0 + (int)lane; e < b1; e += 32) {
+        const u32 w = (u32)col[e];
+        if (w < n && w != sv) cc_unite(parent, sv, w);
+      }
+    }
+  }
+}
+
+// Final labels and component sizes.  The walk only reads, and every store is
+// a root, so concurrent walks stay valid.  Sizes are counted with one atomic
+// per group of lanes that share a root; the vertices of component c (the
+// common root, or ~0 for none) are counted per CTA, so that a giant
+// component does not turn into millions of atomics on one address.
+__global__ void __launch_bounds__(256) k_cc_finish(u32* parent, u32* csize, u32 n, u32 c) {
+  __shared__ u32 s_c;
+  if (threadIdx.x == 0) s_c = 0;
+  __syncthreads();
+  volatile u32* p = parent;
+  const u32 lane = threadIdx.x & 31;
+  const u32 stride = gridDim.x * blockDim.x;
+  u32 in_c = 0;
+  for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const u32 v = base + lane;
+    u32 r = 0xffffffffu;
+    if (v < n) {
+      r = v;
+      u32 nx;
+      while ((nx = p[r]) != r) r = nx;
+      p[v] = r;
+    }
+    if (r == c && c != 0xffffffffu) {
+      ++in_c;
+      r = 0xffffffffu;
+    }
+    const u32 peers = __match_any_sync(kFull, r);
+    if (r != 0xffffffffu && (int)lane == __ffs(peers) - 1) atomicAdd(csize + r, __popc(peers));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) in_c += __shfl_xor_sync(kFull, in_c, o);
+  if (lane == 0 && in_c) atomicAdd(&s_c, in_c);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_c) atomicAdd(csize + c, s_c);
 }
 
 // A root of a component with 2..32 vertices reserves a slot and a range of
@@ -319,27 +416,48 @@ __global__ void k_small_roots(const u32* __restrict__ parent, const u32* __restr
 }
 
 // Members take a lane of their component; every vertex gets its BFS-exclusion
-// bit (no arcs, or a component of at most 32 vertices).
-__global__ void k_small_members(const int* __restrict__ row_ptr, const u32* __restrict__ parent,
-                                const u32* __restrict__ csize, const u32* __restrict__ root_off,
-                                u32 n, u32* fill, u32* comp_v, u32* lane_of, u32* excl,
-                                u32* solo, u32* counters) {
-  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    const u32 r = parent[v];
-    const u32 sz = csize[r];
-    const bool small = sz <= kSmallComp;
-    const bool no_arcs = row_ptr[v + 1] == row_ptr[v];
-    if (small && sz >= 2) {
-      const u32 pos = atomicAdd(fill + r, 1u);
-      comp_v[root_off[r] + pos] = v;
-      lane_of[v] = pos;
+// bit (no arcs, or a component of at most 32 vertices).  A warp owns whole
+// words of the bitmasks (32 consecutive vertices), so it stores them without
+// atomics, and it adds its BFS vertices and their arcs to the counters once.
+__global__ void __launch_bounds__(256) k_small_members(const int* __restrict__ row_ptr,
+                                                       const u32* __restrict__ parent,
+                                                       const u32* __restrict__ csize,
+                                                       const u32* __restrict__ root_off, u32 n,
+                                                       u32* fill, u32* comp_v, u32* lane_of,
+                                                       u32* excl, u32* solo, u32* counters) {
+  const u32 lane = threadIdx.x & 31;
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const u32 v = base + lane;
+    bool is_solo = false, is_excl = false, bfs = false;
+    u32 deg = 0;
+    if (v < n) {
+      const u32 r = parent[v];
+      const u32 sz = csize[r];
+      const bool small = sz <= kSmallComp;
+      deg = (u32)(row_ptr[v + 1] - row_ptr[v]);
+      if (small && sz >= 2) {
+        const u32 pos = atomicAdd(fill + r, 1u);
+        comp_v[root_off[r] + pos] = v;
+        lane_of[v] = pos;
+      }
+      is_solo = sz == 1;
+      is_excl = small || deg == 0;
+      bfs = !is_excl;
     }
-    if (sz == 1) atomicOr(solo + (v >> 5), 1u << (v & 31));
-    if (small || no_arcs) {
-      atomicOr(excl + (v >> 5), 1u << (v & 31));
-    } else {
-      atomicAdd(counters + 2, 1u);  // vertices the BFS settles
-      atomicAdd(counters + 3, (u32)(row_ptr[v + 1] - row_ptr[v]));  // and their arcs
+    const u32 solo_w = __ballot_sync(kFull, is_solo);
+    const u32 excl_w = __ballot_sync(kFull, is_excl);
+    const u32 nbfs = __popc(__ballot_sync(kFull, bfs));
+    u32 arcs = bfs ? deg : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) arcs += __shfl_xor_sync(kFull, arcs, o);
+    if (lane == 0) {
+      solo[base >> 5] = solo_w;  // base is a multiple of 32: the warp owns the word
+      excl[base >> 5] = excl_w;
+      if (nbfs) {
+        atomicAdd(counters + 2, nbfs);  // vertices the BFS settles
+        atomicAdd(counters + 3, arcs);  // and their arcs
+      }
     }
   }
 }
@@ -675,11 +793,43 @@ cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 
   return components_label(row_ptr, n, num_sms, t, excl, solo, counts, s);
 }
 
+cudaError_t components_from_csr(const int* row_ptr, const int* col, u32 n, int num_sms,
+                                const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
+                                cudaStream_t s) {
+  cudaError_t e = components_init(n, num_sms, t, excl, solo, s);
+  if (e != cudaSuccess) return e;
+  const u32 g = grid_for(n, num_sms);
+  for (int r = 0; r < 2; ++r) k_cc_link_nth<<<g, 256, 0, s>>>(row_ptr, col, n, r, t.parent);
+  k_cc_compress<<<g, 256, 0, s>>>(t.parent, n);
+  // the most common root of an even sample (root_off serves as the buffer; it
+  // is written later by k_small_roots)
+  const u32 count = min(n, 1024u);
+  k_cc_sample<<<(count + 255) / 256, 256, 0, s>>>(t.parent, n, count, t.root_off);
+  u32 roots[1024];
+  if ((e = cudaMemcpyAsync(roots, t.root_off, count * 4, cudaMemcpyDeviceToHost, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  std::sort(roots, roots + count);
+  u32 c = roots[0], best = 0;
+  for (u32 i = 0; i < count;) {
+    u32 j = i;
+    while (j < count && roots[j] == roots[i]) ++j;
+    if (j - i > best) {
+      best = j - i;
+      c = roots[i];
+    }
+    i = j;
+  }
+  k_cc_link_rest<<<g, 256, 0, s>>>(row_ptr, col, n, c, t.parent);
+  return components_label(row_ptr, n, num_sms, t, excl, solo, counts, s, c);
+}
+
 cudaError_t components_label(const int* row_ptr, u32 n, int num_sms, const CompScratch& t,
-                             u32* excl, u32* solo, u32 counts[4], cudaStream_t s) {
+                             u32* excl, u32* solo, u32 counts[4], cudaStream_t s, u32 common) {
   const u32 g = grid_for(n, num_sms);
   cudaError_t e;
-  k_cc_finish<<<g, 256, 0, s>>>(t.parent, t.csize, n);
+  k_cc_finish<<<g, 256, 0, s>>>(t.parent, t.csize, n, common);
   k_small_roots<<<g, 256, 0, s>>>(t.parent, t.csize, n, t.root_off, t.comp_off, t.comp_len,
                                   t.counters);
   k_small_members<<<g, 256, 0, s>>>(row_ptr, t.parent, t.csize, t.root_off, n, t.fill, t.comp_v,

@@ -210,7 +210,7 @@ int alloc_scratch(ldd_graph* g) {
 
 // Component labels and the small-component tables (two device phases, the
 // table sizes read back in between).
-int build_component_tables(ldd_graph* g, const int2* d_arcs) {
+int build_component_tables(ldd_graph* g) {
   const size_t n = (size_t)g->n;
   const size_t words = std::max<size_t>((n + 31) / 32, 1);
   if (cudaMalloc(&g->d_excl, 2 * words * 4) != cudaSuccess) {
@@ -235,8 +235,8 @@ int build_component_tables(ldd_graph* g, const int2* d_arcs) {
   t.comp_len = t.comp_off + (n / 2 + 1);
   t.counters = t.comp_len + (n / 2 + 1);
   u32 counts[4] = {0, 0, 0, 0};
-  cudaError_t e = components_phase1(g->d_row, d_arcs, g->m_up, (u32)n, g->num_sms, t, g->d_excl,
-                                    g->d_solo, counts, nullptr);
+  cudaError_t e = components_from_csr(g->d_row, g->d_col, (u32)n, g->num_sms, t, g->d_excl,
+                                      g->d_solo, counts, nullptr);
   int rc = LDD_OK;
   SmallComps& sc = g->sc;
   if (e != cudaSuccess) {
@@ -1172,27 +1172,19 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
         if (e[i]) cudaEventDestroy(e[i]);
     }
   } events_free{ce};
-  int2* d_arcs = nullptr;  // the arcs (v, w), v < w, for the component labelling only
   if (cudaMalloc(&g->d_row, rp.size() * 4) != cudaSuccess ||
-      cudaMalloc(&g->d_col, std::max<size_t>(col.size(), 1) * 4) != cudaSuccess ||
-      cudaMalloc(&d_arcs, std::max<size_t>(up.size(), 1) * sizeof(int2)) != cudaSuccess) {
+      cudaMalloc(&g->d_col, std::max<size_t>(col.size(), 1) * 4) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(d_arcs);
     return bail(fail(LDD_ERR_OOM, "device allocation of the graph failed"));
   }
   mark(0);
   if (cudaMemcpy(g->d_row, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       (nnz > 0 &&
-       cudaMemcpy(g->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
-      (!up.empty() && cudaMemcpy(d_arcs, up.data(), up.size() * sizeof(int2),
-                                 cudaMemcpyHostToDevice) != cudaSuccess)) {
-    cudaFree(d_arcs);
+       cudaMemcpy(g->d_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
     return bail(fail(LDD_ERR_CUDA, "upload of the graph failed"));
-  }
   mark(1);
-  rc = build_component_tables(g, d_arcs);
+  rc = build_component_tables(g);
   mark(2);
-  cudaFree(d_arcs);
   if (rc != LDD_OK) return bail(rc);
   const float ms_upload = span(0, 1), ms_components = span(1, 2);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);

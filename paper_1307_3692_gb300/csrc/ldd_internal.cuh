@@ -261,7 +261,14 @@ cudaError_t components_phase1(const int* row_ptr, const int2* up, u32 m_up, u32 
 cudaError_t components_init(u32 n, int num_sms, const CompScratch& t, u32* excl, u32* solo,
                             cudaStream_t s);
 cudaError_t components_label(const int* row_ptr, u32 n, int num_sms, const CompScratch& t,
-                             u32* excl, u32* solo, u32 counts[4], cudaStream_t s);
+                             u32* excl, u32* solo, u32 counts[4], cudaStream_t s,
+                             u32 common = 0xffffffffu);
+// components_phase1 from the CSR itself (no edge list): Afforest-style
+// linking (first neighbours, the most common root, then the remaining arcs of
+// the vertices outside it).
+cudaError_t components_from_csr(const int* row_ptr, const int* col, u32 n, int num_sms,
+                                const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
+                                cudaStream_t s);
 // Residual graphs of the block decomposition (k_graph.cu).  Count pass
 // (write = false): kept[v] = arcs of v whose ends have different centers;
 // *up_kept += those with v < w; arc_block[orig ? orig[e] : e] = block for the

@@ -280,6 +280,35 @@ def test_component_labels_deep_trees(ldd, cuda):
         assert st["n_active"] == int(sz[lab][sz[lab] > 32].size)
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_component_labels_no_giant(ldd, cuda, seed):
+    """Many mid-size components and no giant one (random trees of 20..80
+    vertices, each in a random vertex order, plus isolated vertices): the
+    sampled common root is an ordinary component, and every other one must
+    still be joined arc by arc.  Counts match scipy's labelling, labels the
+    oracle."""
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+
+    rng = np.random.default_rng(seed)
+    n = 30000
+    perm = rng.permutation(n)
+    edges, at = [], 0
+    while at < n - 100:
+        size = int(rng.integers(20, 81))
+        ids = perm[at:at + size]
+        for i in range(1, size):  # a random tree: vertex i hangs off an earlier one
+            edges.append((int(ids[i]), int(ids[int(rng.integers(0, i))])))
+        at += size
+    G = gen.from_edges(n, edges, f"forest{seed}")
+    A = sp.csr_matrix((np.ones(G.nnz), G.col, G.row_ptr), shape=(G.n, G.n))
+    _, lab = cg.connected_components(A, directed=False)
+    sz = np.bincount(lab)
+    _, _, _, st = assert_parity(ldd, G, gen.shifts(G.n, 0.1, seed), 0.1)
+    assert st["small_components"] == int(((sz >= 2) & (sz <= 32)).sum())
+    assert st["n_active"] == int(sz[lab][sz[lab] > 32].size)
+
+
 @pytest.mark.parametrize("kind,exact", [("equal_codes_unequal_fractions", 1), ("tiny_shifts", 1),
                                         ("half_ties", 1), ("short_equal_runs", 0)])
 def test_fraction_rank_exact_fallback(ldd, cuda, kind, exact):
