@@ -34,9 +34,11 @@
 // (each final level-r key is one of these, and each of these is >= the final
 // key of its vertex).  Only w's own thread writes key[w] in such a round, and a
 // vertex being lowered to level r + 1 is never read as a level-r key, so no
-// atomics are needed.  On a union of graphs (k_union.cu) the floor is kept
-// per member: the smallest level-r rank of w's own member, since no other
-// member's key can reach w.  The first bottom-up round of a run examines every
+// atomics are needed.  On a union of graphs (k_union.cu) the floor is per
+// member: the smallest level-r rank of w's own member, since no other member's
+// key can reach w; it is computed when a round goes bottom-up, by one pass
+// over the frontier list (every level-r vertex is on it) and one more grid
+// barrier.  The first bottom-up round of a run examines every
 // vertex the BFS owns; each round lists the vertices still above level r + 1,
 // and the next bottom-up round examines only those.
 //
@@ -92,13 +94,15 @@ struct Smem {
 // would leave the others at a CTA barrier).  phantom > 0 waits for CTAs that
 // do not exist: the barrier can then only end by running out of polls, which
 // is how the timeout path is tested.
+constexpr u32 kNoPost = 0xffffffffu;  // grid_barrier: a barrier inside a round
+
 __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks, u32 phantom,
                                              u32 limit, u32 post, const int* bptr, int blevel,
                                              Smem& s) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (s.minrank != 0xffffffffu) atomicMin(&ctl->minrank[post], s.minrank);
-    s.minrank = 0xffffffffu;
+    if (post != kNoPost && s.minrank != 0xffffffffu) atomicMin(&ctl->minrank[post], s.minrank);
+    if (post != kNoPost) s.minrank = 0xffffffffu;
     ++gen;
     const u64 target = (u64)gen * nblocks + phantom;
     __threadfence();
@@ -116,13 +120,15 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
       if (spins > 64) __nanosleep(20);
     }
     const u32 err = ld_cg_u32(&ctl->err);
-    s.next_c = ld_cg_u64(&ctl->qctr[post]);
-    s.next_minrank = ld_cg_u32(&ctl->minrank[post]);
-    s.next_ucnt = ld_cg_u32(&ctl->ucnt[post]);
-    s.next_lo = s.next_hi = 0;
-    if (blevel >= 0) {  // bounds of start bucket blevel, for the round after the barrier
-      s.next_lo = __ldg(bptr + blevel);
-      s.next_hi = __ldg(bptr + blevel + 1);
+    if (post != kNoPost) {
+      s.next_c = ld_cg_u64(&ctl->qctr[post]);
+      s.next_minrank = ld_cg_u32(&ctl->minrank[post]);
+      s.next_ucnt = ld_cg_u32(&ctl->ucnt[post]);
+      s.next_lo = s.next_hi = 0;
+      if (blevel >= 0) {  // bounds of start bucket blevel, for the round after the barrier
+        s.next_lo = __ldg(bptr + blevel);
+        s.next_hi = __ldg(bptr + blevel + 1);
+      }
     }
     s.stop = err != 0u ? 1u : 0u;
   }
@@ -152,35 +158,53 @@ __device__ __forceinline__ u64 warp_min64(u64 x) {
 }
 
 // Records a successful next-level key (vertex v, rank) for the bottom-up
-// floor of the next round.  Plain graph: the thread's running minimum
-// (folded into the CTA's and the grid's at the barrier).  Union: the minimum
-// of v's member -- another member's smaller rank can never reach v, so the
-// floor is per member -- in the CTA's shared table s_acc (flushed to slot
-// `slot` of a.mrank before the barrier), or, for unions too large for it,
-// in a.mrank directly, read before the atomic so that the atomic only runs
-// when it lowers the entry.  A warp whose valid lanes share one member makes
-// one update.  Every lane of the warp calls this.
+// floor of the next round: the thread's running minimum, folded into the
+// CTA's and the grid's at the barrier.  Unions track nothing here: their floor
+// is per member (another member's smaller rank can never reach v), and it is
+// computed from the frontier list only when a round goes bottom-up
+// (member_floors), since keeping up to kmem minima per CTA in every round
+// cost more than the rare bottom-up rounds of a batch gain from it.
 template <bool U>
 __device__ __forceinline__ void note_rank(const BfsArgs& a, u32 slot, bool valid, u32 v, u32 rank,
                                           u32& myrank, u32* s_acc) {
-  if (!U) {
-    if (valid) myrank = min(myrank, rank);
-    return;
-  }
-  if (!__any_sync(kFull, valid)) return;
-  const u32 m = valid ? __ldg(a.wmem + (v >> 5)) : 0xffffffffu;
+  (void)a;
+  (void)slot;
+  (void)v;
+  (void)s_acc;
+  if (!U && valid) myrank = min(myrank, rank);
+}
+
+// Unions: the per-member floors of level-L keys (the smallest rank among each
+// member's keys of the frontier's level) from the frontier list qv of Q
+// vertices, into slot `slot` of a.mrank (all ~0 on entry).  A warp whose
+// vertices share one member makes one update; small unions gather the minima
+// per CTA in shared memory (s_acc) and flush them.  The caller then waits at a
+// grid barrier before the floors are read.
+__device__ __forceinline__ void member_floors(const BfsArgs& a, const u32* qv, u32 Q, u32 slot,
+                                              u32* s_acc) {
   const u32 lane = threadIdx.x & 31;
-  const u32 act = __ballot_sync(kFull, valid);
-  const u32 m0 = __shfl_sync(kFull, m, __ffs(act) - 1);
-  const bool one = __all_sync(kFull, !valid || m == m0);
-  const u32 r = one ? warp_min(valid ? rank : 0xffffffffu) : rank;
-  if ((one && lane == 0) || (!one && valid)) {
-    const u32 mm = one ? m0 : m;
-    if (s_acc) {
-      if (r < s_acc[mm]) atomicMin(s_acc + mm, r);
-    } else {
-      u32* p = a.mrank + (size_t)slot * a.kmem + mm;
-      if (r < ld_cg_u32(p)) atomicMin(p, r);
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 base = warp_first_item(1); base < Q; base += stride) {
+    const u32 i = base + lane;
+    const bool valid = i < Q;
+    u32 v = 0, m = 0xffffffffu, r = 0xffffffffu;
+    if (valid) {
+      v = ld_cg_u32(qv + i);
+      m = __ldg(a.wmem + (v >> 5));
+      r = (u32)ld_cg_u64(a.key + v);
+    }
+    const u32 act = __ballot_sync(kFull, valid);
+    const u32 m0 = __shfl_sync(kFull, m, __ffs(act) - 1);
+    const bool one = __all_sync(kFull, !valid || m == m0);
+    const u32 rr = one ? warp_min(r) : r;
+    if ((one && lane == 0) || (!one && valid)) {
+      const u32 mm = one ? m0 : m;
+      if (s_acc) {
+        if (rr < s_acc[mm]) atomicMin(s_acc + mm, rr);
+      } else {
+        u32* p = a.mrank + (size_t)slot * a.kmem + mm;
+        if (rr < ld_cg_u32(p)) atomicMin(p, rr);
+      }
     }
   }
 }
@@ -799,10 +823,6 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
     append_bucket<U>(a, 0, rv, 0, 0, myrank, s_acc);
   }
   post_cta_min(s, myrank);
-  if (s_acc) {
-    __syncthreads();
-    flush_members(a, 0, s_acc);
-  }
   grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, 0, a.bptr, A >= 1 ? 1 : -1, s);
   const bool profiler = blockIdx.x == 0 && threadIdx.x == 0;
   if (profiler) {
@@ -849,10 +869,19 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       else if (pulling && (u64)Q * a.pull_beta < a.n_active)
         pulling = false;
       if (pulling) {
-        if (s_floor) {  // this level's per-member floors, read once per CTA
-          for (u32 m = threadIdx.x; m < a.kmem; m += blockDim.x)
-            s_floor[m] = ld_cg_u32(a.mrank + (size_t)(phase % 3) * a.kmem + m);
-          __syncthreads();
+        if (U) {  // this level's per-member floors, from the frontier list
+          member_floors(a, a.qv[phase & 1], Q, phase % 3, s_acc);
+          if (s_acc) {
+            __syncthreads();
+            flush_members(a, phase % 3, s_acc);
+          }
+          grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, kNoPost, a.bptr, -1, s);
+          if (s.stop) break;
+          if (s_floor) {  // read once per CTA
+            for (u32 m = threadIdx.x; m < a.kmem; m += blockDim.x)
+              s_floor[m] = ld_cg_u32(a.mrank + (size_t)(phase % 3) * a.kmem + m);
+            __syncthreads();
+          }
         }
         pull_round<U, LD>(a, lvl, minrank, phase % 3, qi, qb, was_pulling, a.ulist[phase & 1],
                           ncand, a.ulist[(phase + 1) & 1], &ctl->ucnt[qi], myrank, s_acc,
@@ -896,10 +925,6 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
     }
     if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][1] = clock64();
     post_cta_min(s, myrank);
-    if (s_acc) {
-      __syncthreads();
-      flush_members(a, (u32)qi, s_acc);
-    }
     grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, (u32)qi, a.bptr,
                  nlvl + 1 <= A ? nlvl + 1 : -1, s);
     ++phase;
