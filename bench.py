@@ -187,9 +187,14 @@ def bfs_algorithmic_bytes(st):
     end's key (probe / atomicMin); per vertex examined bottom-up 8 B of its key
     + 8 B row_ptr; per settled vertex 8 B row_ptr + 8 B own key + 24 B queue
     write and read; per start-bucket entry (one per vertex the BFS handles)
-    4 B vertex id + 8 B key test."""
-    return (12 * (st["push_arcs"] + st["pull_arcs"]) + 16 * st["pull_vertices"]
-            + 40 * st["items"] + 12 * st["n_active"])
+    4 B vertex id + 8 B key test.  Windows of levels may expand a vertex (and
+    offer its arcs) more than once; only the first time counts here."""
+    push, items = st["push_arcs"], st["items"]
+    if st.get("bfs_windows", 0) > 0:
+        push = min(push, st["nnz"])  # every arc offered at most once
+        items = min(items, st["n_active"])
+    return (12 * (push + st["pull_arcs"]) + 16 * st["pull_vertices"]
+            + 40 * items + 12 * st["n_active"])
 
 
 def kernel_source_sha():

@@ -413,6 +413,7 @@ typedef struct {
   float ms_block_residual;/* ... of which the residual-graph passes (filter, scan, components) */
   int64_t block_arcs_scanned; /* arcs of G_0, G_1, ... read by the residual passes */
   int64_t block_arcs_kept;    /* arcs written as G_1, G_2, ... */
+  int64_t bfs_windows;    /* windows of levels the last round loop ran (ldd_tuning) */
 } ldd_stats;
 
 int ldd_get_stats(const ldd_graph* g, ldd_stats* out);
@@ -433,6 +434,11 @@ typedef struct {
                                 low-degree rounds (the frontier a plain vertex list, one
                                 thread per vertex, the next start bucket checked in the
                                 same pass); 0: the edge-balanced rounds always */
+  int32_t window_levels;     /* low-degree rounds: levels relaxed between two grid barriers
+                                (each CTA going on with the vertices it reaches; exact, but a
+                                vertex may be expanded twice); 0 or 1: one level per barrier */
+  int32_t window_max_frontier; /* ... a window only while the frontier has at most this many
+                                vertices (>= 0) */
   float ms;                  /* ldd_autotune: the best decomposition time seen, ms */
 } ldd_tuning;
 

@@ -53,7 +53,8 @@ class _Stats(ctypes.Structure):
         (name, ctypes.c_float) for name in ("ms_create_upload", "ms_create_components",
                                             "ms_create_total", "ms_block_total",
                                             "ms_block_residual")] + [
-        (name, ctypes.c_int64) for name in ("block_arcs_scanned", "block_arcs_kept")]
+        (name, ctypes.c_int64) for name in ("block_arcs_scanned", "block_arcs_kept",
+                                            "bfs_windows")]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -125,6 +126,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("bfs_blocks_per_sm", ctypes.c_int32), ("pull_alpha", ctypes.c_int32),
                 ("pull_beta", ctypes.c_int32), ("pull_gamma", ctypes.c_int32),
                 ("probe_min_arcs", ctypes.c_int32), ("low_degree_rounds", ctypes.c_int32),
+                ("window_levels", ctypes.c_int32), ("window_max_frontier", ctypes.c_int32),
                 ("ms", ctypes.c_float)]
 
 

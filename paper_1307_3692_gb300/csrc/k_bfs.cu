@@ -77,7 +77,15 @@ struct Smem {
   u32 next_minrank;
   u32 next_ucnt;
   int next_lo, next_hi;  // the next round's start bucket (lvl + 1) bounds
+  u32 next_ovf;          // the next round's overflow-list length (windows)
+  u32 lcnt[2];           // windows: lengths of the CTA's two local queues
+  u32 nstart;            // a scan's result, shared by the CTA
 };
+// Windows of levels keep two local queues of (vertex, level) pairs in the
+// memory the edge-balanced rounds use for their span windows.
+constexpr int kLq = 3072;
+static_assert(2 * kLq * sizeof(u64) <= sizeof(int) * kBfsMaxSpan * 2 + sizeof(u64) * kBfsMaxSpan,
+              "local queues fit the span-window arrays");
 
 // Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a
 // launch completes when the counter reaches k * nblocks (+ phantom), so
@@ -124,6 +132,7 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
       s.next_c = ld_cg_u64(&ctl->qctr[post]);
       s.next_minrank = ld_cg_u32(&ctl->minrank[post]);
       s.next_ucnt = ld_cg_u32(&ctl->ucnt[post]);
+      s.next_ovf = ld_cg_u32(&ctl->ovf[post]);
       s.next_lo = s.next_hi = 0;
       if (blevel >= 0) {  // bounds of start bucket blevel, for the round after the barrier
         s.next_lo = __ldg(bptr + blevel);
@@ -522,6 +531,248 @@ __device__ __forceinline__ void expand_ld(const BfsArgs& a, const u32* qv_cur, u
   }
 }
 
+// ---------------------------------------------------------------- windows of levels
+// Low-degree rounds may run a window of levels [L, H) between two grid
+// barriers instead of one level.  Each CTA expands its share of the level-L
+// frontier (and of the overflow list of the last window), then keeps going on
+// its own: every vertex whose key it lowers to a level below H goes into the
+// CTA's local queue (shared memory) and is expanded by the same CTA at the
+// next local level, with only a CTA barrier in between; vertices lowered to
+// level H go to the global queue for the next round.  Start bucket lv + 1 is
+// checked at local level lv, as in a one-level round.
+//
+// Exactness: keys only decrease, and the fixed point of the min over all
+// offers does not depend on the order in which they are made (Section 4's
+// shortest path, label-correcting).  Every successful atomicMin makes its
+// vertex be expanded again: it is pushed with the level it got, to a local
+// queue, to the global queue (the first time it reaches level H), or -- when
+// a local queue is full -- to the overflow list that the next round expands.
+// An entry whose vertex has meanwhile been lowered to a smaller level is
+// skipped, since its lowerer pushed it again.  A CTA may run ahead of another
+// inside a window, so a vertex can first get a worse key and be expanded
+// twice (the statistics count every expansion); the result is the same.  A
+// start test inside a window may let a vertex start that a slower CTA lowers
+// later: it is expanded again with the better key.  At the end of a window
+// every key below level H is final unless an overflow entry is pending, and
+// the loop then runs another window before any bottom-up round.
+//
+// Once a window has run, the number of settled vertices is no longer counted
+// exactly; an empty frontier then scans the start buckets from the current
+// level for the next one that still holds an unclaimed vertex (one pass and
+// one grid barrier) instead of stopping when every vertex is settled.
+
+// Pushes (w[i], lev) for every bit i of mask: to the CTA's local queue `nb`
+// while it has room, the rest to the overflow list of the next round.
+template <int K>
+__device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u32 (&lev)[K],
+                                            const BfsArgs& a, Smem& s, int nb, int qi, int qb) {
+  const u32 lane = threadIdx.x & 31;
+  const u32 mine = __popc(mask);
+  u32 incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= (u32)o) incl += y;
+  }
+  const u32 tot = __shfl_sync(kFull, incl, 31);
+  if (tot == 0) return;
+  u32 base = 0;
+  if (lane == 0) base = atomicAdd(&s.lcnt[nb], tot);
+  base = __shfl_sync(kFull, base, 0) + incl - mine;
+  u64* lq = reinterpret_cast<u64*>(&s.owner[0]) + (size_t)nb * kLq;
+  u32 spill = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (mask >> i & 1u) {
+      if (base < (u32)kLq) lq[base] = ((u64)lev[i] << 32) | w[i];
+      else spill |= 1u << i;
+      ++base;
+    }
+  // a full local queue: the rest waits for the next round on the overflow list
+  const u32 smine = __popc(spill);
+  u32 sincl = smine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, sincl, o);
+    if (lane >= (u32)o) sincl += y;
+  }
+  const u32 stot = __shfl_sync(kFull, sincl, 31);
+  if (stot == 0) return;
+  u32 sbase = 0;
+  if (lane == 0) sbase = atomicAdd(&a.ctl->ovf[qi], stot);
+  sbase = __shfl_sync(kFull, sbase, 0) + sincl - smine;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (spill >> i & 1u) {
+      if (sbase < a.n) {
+        reinterpret_cast<u32*>(a.qrow[qb])[sbase] = w[i];
+        a.qoff[qb][sbase] = lev[i];
+      } else {
+        atomicOr(&a.ctl->err, kErrInternal);  // more pushes than vertices: cannot happen
+      }
+      ++sbase;
+    }
+}
+
+// Expands one item per lane (valid: v with push level lev) in a window whose
+// end is H: v's current key is offered to its neighbours; winners below H go
+// to the local queue nb, winners at H that reach it for the first time to the
+// global queue qb.  Every lane of the warp calls this.
+template <bool U>
+__device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool valid, u32 v, u32 lev,
+                                              u32 H, int nb, int qi, int qb, u32& myrank,
+                                              u32* s_acc, u64& pushed, u64& expanded) {
+  constexpr u32 kNone = 0xffffffffu;
+  u64 kv = 0;
+  int rs = 0, re = 0;
+  if (valid) {
+    kv = ld_cg_u64(a.key + v);
+    rs = __ldg(a.row_ptr + v);
+    re = __ldg(a.row_ptr + v + 1);
+    if ((u32)(kv >> 32) < lev) re = rs;  // lowered since it was pushed: its lowerer pushed it again
+    else ++expanded;
+  }
+  pushed += (u64)(re - rs);
+  const u64 cand = kv + kLevelOne;
+  const u32 cl = (u32)(cand >> 32);
+  int nch = (re - rs + kLdBatch - 1) / kLdBatch;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nch = max(nch, __shfl_xor_sync(kFull, nch, o));
+  for (int ch = 0; ch < nch; ++ch) {
+    const int e0 = rs + ch * kLdBatch;
+    u32 w[kLdBatch], wl[kLdBatch];
+#pragma unroll
+    for (int q = 0; q < kLdBatch; ++q) {
+      w[q] = (e0 + q < re) ? (u32)__ldg(a.col + e0 + q) : kNone;
+      wl[q] = cl;
+    }
+    u32 local = 0, glob = 0, won = 0;
+#pragma unroll
+    for (int q = 0; q < kLdBatch; ++q)
+      if (w[q] < a.n) {
+        const u64 old = atomicMin(a.key + w[q], cand);
+        if (old > cand) {
+          won |= 1u << q;
+          if (cl < H) local |= 1u << q;
+          else if ((u32)(old >> 32) > H) glob |= 1u << q;
+        }
+      }
+#pragma unroll
+    for (int q = 0; q < kLdBatch; ++q)  // the next round's bottom-up floor: level-H keys
+      note_rank<U>(a, (u32)qi, ((won >> q) & 1u) && cl == H, w[q], (u32)cand, myrank, s_acc);
+    window_push<kLdBatch>(local, w, wl, a, s, nb, qi, qb);
+    warp_append<kLdBatch, true>(glob, w, a, qi, qb);
+  }
+}
+
+// One window of levels [L, H): the level-L frontier (Q entries of qv_cur) and
+// the nov overflow entries of the last round (qrow/qoff of side qcur), then
+// local levels L .. H - 1.  `expanded` counts expansions.
+template <bool U>
+__device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* rv, int A,
+                                          u32 Q, u32 nov, int qcur, u32 L, u32 H, int qi, int qb,
+                                          u32& myrank, u32* s_acc, u64& pushed, u64& expanded) {
+  const u32 lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s.lcnt[0] = 0;
+    s.lcnt[1] = 0;
+  }
+  __syncthreads();
+  const u64* lq_all = reinterpret_cast<const u64*>(&s.owner[0]);
+  int lb = 0;  // the local queue being read (level lv); the other one is filled
+  for (u32 lv = L; lv < H; ++lv) {
+    const int nb = lb ^ 1;
+    const u32 nloc = min(s.lcnt[lb], (u32)kLq);
+    // (1) the window's first level: the global frontier and the overflow list
+    if (lv == L) {
+      const u32 total = Q + nov;
+      for (u32 base = warp_first_item(1); base < total; base += gridDim.x * blockDim.x) {
+        const u32 i = base + lane;
+        u32 v = 0, lev = L;
+        if (i < Q) {
+          v = ld_cg_u32(a.qv[qcur] + i);
+        } else if (i < total) {
+          v = ld_cg_u32(reinterpret_cast<const u32*>(a.qrow[qcur]) + (i - Q));
+          lev = ld_cg_u32(a.qoff[qcur] + (i - Q));
+        }
+        window_expand<U>(a, s, i < total, v, lev, H, nb, qi, qb, myrank, s_acc, pushed,
+                         expanded);
+      }
+    }
+    // (2) this CTA's local queue of level lv
+    for (u32 base = threadIdx.x & ~31u; base < nloc; base += blockDim.x) {
+      const u32 i = base + lane;
+      u64 e = 0;
+      if (i < nloc) e = lq_all[(size_t)lb * kLq + i];
+      window_expand<U>(a, s, i < nloc, (u32)e, (u32)(e >> 32), H, nb, qi, qb, myrank, s_acc,
+                       pushed, expanded);
+    }
+    // (3) start bucket lv + 1: a vertex whose key still has its start level joins level lv + 1
+    if ((int)lv + 1 <= A) {
+      const int lo = __ldg(a.bptr + lv + 1), hi = __ldg(a.bptr + lv + 2);
+      const u32 cnt = (u32)(hi - lo);
+      for (u32 base = warp_first_item(1, true); base < cnt; base += gridDim.x * blockDim.x) {
+        const u32 i = base + lane;
+        u32 u[1] = {0}, ul[1] = {lv + 1};
+        bool start = false;
+        u64 k = 0;
+        if (i < cnt) {
+          u[0] = __ldg(rv + lo + (int)i);
+          k = ld_cg_u64(a.key + u[0]);
+          start = (u32)(k >> 32) == lv + 1;
+        }
+        if (lv + 1 < H) {
+          window_push<1>(start ? 1u : 0u, u, ul, a, s, nb, qi, qb);
+        } else {
+          note_rank<U>(a, (u32)qi, start, u[0], (u32)k, myrank, s_acc);
+          warp_append<1, true>(start ? 1u : 0u, u, a, qi, qb);
+        }
+      }
+    }
+    __syncthreads();  // every push of level lv + 1 is in; level lv's queue is read
+    if (threadIdx.x == 0) s.lcnt[lb] = 0;
+    __syncthreads();
+    lb = nb;
+  }
+  // Overflow entries carry the levels of an earlier window, so their chains
+  // may still be going at the last level: what is left in the local queue
+  // waits on the overflow list for the next round.
+  const u32 left = min(s.lcnt[lb], (u32)kLq);  // the same for the whole CTA
+  if (left > 0) {
+    if (threadIdx.x == 0) s.lcnt[lb ^ 1] = (u32)kLq;  // no local room: window_push spills all
+    __syncthreads();
+    for (u32 b0 = 0; b0 < left; b0 += blockDim.x) {  // the same trip count for every warp
+      const u32 i = b0 + threadIdx.x;
+      u32 w[1] = {0}, wl[1] = {0};
+      if (i < left) {
+        const u64 e = lq_all[(size_t)lb * kLq + i];
+        w[0] = (u32)e;
+        wl[0] = (u32)(e >> 32);
+      }
+      window_push<1>(i < left ? 1u : 0u, w, wl, a, s, lb ^ 1, qi, qb);
+    }
+  }
+}
+
+// The smallest start level >= from among start-bucket entries whose key still
+// has their start level (a vertex nobody has claimed), into ctl->nstart[slot]
+// as ~level by atomicMax (0 if none); the caller waits at a grid barrier.
+__device__ __forceinline__ void scan_unclaimed(const BfsArgs& a, const u32* rk, const u32* rv,
+                                               int from, int A, u32 slot) {
+  if (from > A) return;
+  const int lo = __ldg(a.bptr + from), hi = __ldg(a.bptr + A + 1);
+  u32 best = 0;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; (int)i < hi - lo;
+       i += gridDim.x * blockDim.x) {
+    const u32 r = __ldg(rk + lo + (int)i);
+    const u64 k = ld_cg_u64(a.key + __ldg(rv + lo + (int)i));
+    if ((u32)(k >> 32) == r) best = max(best, ~r);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(kFull, best, o));
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(&a.ctl->nstart[slot], best);
+}
+
 // Folds a thread's smallest rank into the CTA's (lane 0 of each warp) and resets it.
 __device__ __forceinline__ void post_cta_min(Smem& s, u32& myrank) {
   const u32 wm = warp_min(myrank);
@@ -832,34 +1083,64 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   }
 
   u64 settled = 0, edges = 0;
-  u32 phase = 0, pulls = 0;
+  u64 items = 0;     // vertices expanded (a window may expand a vertex twice)
+  u64 expanded = 0;  // this thread's expansions inside windows
+  u32 phase = 0, pulls = 0, nwin = 0;
   u64 push_arcs = 0;
   int lvl = 0;
   bool pulling = false;
+  bool windowed = false;  // a window has run: settled vertices are no longer counted exactly
+  // No correct run needs more rounds than this (each round settles a level or
+  // jumps to a start bucket); a loop that would is stopped with an error
+  // instead of holding the GPU.
+  const u64 max_rounds = 2ull * ((u64)a.n_active + (u64)A) + 1024;
   for (;;) {
     if (s.stop) break;  // set by the last barrier, the same for every thread of the CTA
+    if (phase > max_rounds) {  // the same for every thread of every CTA
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrInternal);
+      break;
+    }
     const u64 c = s.next_c;  // slot phase % 3, read as the last barrier released
     const int nb_lo = s.next_lo, nb_hi = s.next_hi;  // start bucket lvl + 1 (if lvl + 1 <= A)
     const u32 Q = (u32)(c >> 32);
+    // overflow entries of the last window (more than n cannot have been written:
+    // that sets kErrInternal, and the loop stops at the barrier)
+    const u32 nov = LD ? min(s.next_ovf, a.n) : 0u;
     // low-degree mode keeps no arc count: the frontier's arcs are estimated
     // from the mean degree (direction choice and probe threshold only)
     const u32 E = LD ? (u32)min((u64)Q * a.nnz_active / max(a.n_active, 1u), 0xffffffffull)
                      : (u32)c;
     settled += Q;
-    if (settled >= a.n_active) break;  // every vertex the BFS owns has its final key
+    if (!windowed && settled >= a.n_active) break;  // every vertex the BFS owns has its final key
     const u32 minrank = s.next_minrank;
     const u32 ncand = s.next_ucnt;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctl->qctr[(phase + 2) % 3] = 0;
       ctl->minrank[(phase + 2) % 3] = 0xffffffffu;
       ctl->ucnt[(phase + 2) % 3] = 0;
+      ctl->ovf[(phase + 2) % 3] = 0;
+      ctl->nstart[(phase + 2) % 3] = 0;
     }
     if (U)  // the members' floors of the slot that the next round fills
       for (u32 m = blockIdx.x * blockDim.x + threadIdx.x; m < a.kmem; m += G * blockDim.x)
         a.mrank[(size_t)((phase + 2) % 3) * a.kmem + m] = 0xffffffffu;
     const int qi = (int)((phase + 1) % 3), qb = (int)((phase + 1) & 1);
     int nlvl;
-    if (Q > 0) {
+    // a window of levels: low-degree rounds whose frontier is thin enough, and
+    // always while overflow entries of the last window wait
+    const bool window = LD && a.window_levels > 1 && (nov > 0 || (Q > 0 && Q <= a.window_max_q));
+    if (window) {
+      edges += E;
+      pulling = false;
+      const u32 H = (u32)lvl + a.window_levels;
+      window_ld<U>(a, s, rv, A, Q, nov, (int)(phase & 1), (u32)lvl, H, qi, qb, myrank, s_acc,
+                   pushed, expanded);
+      if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
+      windowed = true;
+      ++nwin;
+      nlvl = (int)H;
+    } else if (Q > 0) {
+      items += Q;
       edges += E;
       const u64 unsettled_arcs = a.nnz_active > edges ? a.nnz_active - edges : 0;
       const bool was_pulling = pulling;
@@ -909,10 +1190,21 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       nlvl = lvl + 1;
     } else {
       if (lvl + 1 > A) break;
-      const int start = __ldg(a.bptr + lvl + 1);
-      if ((u32)start >= a.n) break;
-      const int rr = (int)__ldg(rk + start);  // next non-empty start bucket
-      if (rr > A) break;                      // only vertices the BFS does not handle remain
+      int rr;
+      if (windowed) {  // the next start level that still holds an unclaimed vertex
+        scan_unclaimed(a, rk, rv, lvl + 1, A, phase % 3);
+        grid_barrier(ctl, gen, G, a.bar_phantom, a.spin_limit, kNoPost, a.bptr, -1, s);
+        if (s.stop) break;
+        if (threadIdx.x == 0) s.nstart = ld_cg_u32(&ctl->nstart[phase % 3]);
+        __syncthreads();
+        if (s.nstart == 0u) break;  // none: every vertex the BFS owns is settled
+        rr = (int)~s.nstart;
+      } else {
+        const int start = __ldg(a.bptr + lvl + 1);
+        if ((u32)start >= a.n) break;
+        rr = (int)__ldg(rk + start);  // next non-empty start bucket
+        if (rr > A) break;            // only vertices the BFS does not handle remain
+      }
       if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
       if (LD) {
         const int lo = __ldg(a.bptr + rr), hi = __ldg(a.bptr + rr + 1);
@@ -934,18 +1226,23 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       ctl->round_kind[phase] = Q == 0 ? kRoundSkip : (pulling ? kRoundPull : kRoundPush);
     }
   }
-  if (LD) {  // every thread's offered arcs (the estimate above is not a count)
+  if (LD) {  // every thread's offered arcs (the estimate above is not a count) and expansions
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pushed += __shfl_xor_sync(kFull, pushed, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      pushed += __shfl_xor_sync(kFull, pushed, o);
+      expanded += __shfl_xor_sync(kFull, expanded, o);
+    }
     if ((threadIdx.x & 31) == 0 && pushed) atomicAdd(&ctl->push_arcs, pushed);
+    if ((threadIdx.x & 31) == 0 && expanded) atomicAdd(&ctl->items, expanded);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->pull_rounds = pulls;
     if (!LD) ctl->push_arcs = push_arcs;
     ctl->rounds = phase;
     ctl->last_level = lvl;
-    ctl->items = settled;
+    atomicAdd(&ctl->items, windowed ? items : settled);
     ctl->edges = edges;
+    ctl->windows = nwin;
   }
 }
 

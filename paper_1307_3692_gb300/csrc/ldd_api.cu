@@ -405,6 +405,8 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.pull_gamma = g->pull_gamma;
   a.probe_min_arcs = g->probe_min_arcs;
   a.low_degree = (g->low_degree_rounds && g->max_degree <= (u32)kLdMaxDegree) ? 1u : 0u;
+  a.window_levels = g->window_levels;
+  a.window_max_q = g->window_max_q;
   a.wmem = g->uni ? g->uni->d_wmem : nullptr;
   a.mrank = g->uni ? g->uni->d_mrank : nullptr;
   a.kmem = g->uni ? g->uni->k : 0;
@@ -472,6 +474,8 @@ int finish_setup(ldd_graph* g) {
   g->probe_min_arcs = env_u32("LDD_PROBE_MIN_ARCS", 1u << 16);
   const char* ldr = getenv("LDD_LOW_DEGREE_ROUNDS");  // "0": edge-balanced rounds only
   g->low_degree_rounds = !(ldr && ldr[0] == '0' && ldr[1] == 0);
+  g->window_levels = env_u32("LDD_WINDOW_LEVELS", 0);
+  g->window_max_q = env_u32("LDD_WINDOW_MAX_FRONTIER", 1u << 18);
   g->stats.n = g->n;
   g->stats.nnz = g->nnz;
   g->stats.n_active = g->n_active;
@@ -497,7 +501,7 @@ struct Header {  // the control block up to and including the BFS runtime state
   u64 pull_arcs;
   u64 pull_verts;
   u32 ucnt[3];
-  u32 pad0;
+  u32 windows;
 };
 static_assert(sizeof(Header) == kCtlHeaderBytes + kCtlBfsStateBytes, "header layout");
 
@@ -543,6 +547,7 @@ void header_stats(ldd_graph* g, const Header& h, bool exact64) {
   st.push_arcs = (int64_t)h.push_arcs;
   st.pull_arcs = (int64_t)h.pull_arcs;
   st.pull_vertices = (int64_t)h.pull_verts;
+  st.bfs_windows = h.windows;
 }
 
 int header_error(u32 err) {
@@ -1692,6 +1697,8 @@ int ldd_get_tuning(const ldd_graph* g, ldd_tuning* out) {
   out->pull_gamma = (int32_t)g->pull_gamma;
   out->probe_min_arcs = (int32_t)g->probe_min_arcs;
   out->low_degree_rounds = g->low_degree_rounds ? 1 : 0;
+  out->window_levels = (int32_t)g->window_levels;
+  out->window_max_frontier = (int32_t)std::min<u32>(g->window_max_q, 0x7fffffffu);
   out->ms = -1.f;
   return LDD_OK;
 }
@@ -1703,7 +1710,8 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
     return fail(LDD_ERR_CUDA, "BFS kernel occupancy query failed");
   if (t->bfs_blocks_per_sm < 1 || t->bfs_blocks_per_sm > max_per_sm || t->pull_alpha < 0 ||
       t->pull_beta < 1 || t->pull_gamma < 0 || t->probe_min_arcs < 0 ||
-      (t->low_degree_rounds != 0 && t->low_degree_rounds != 1))
+      (t->low_degree_rounds != 0 && t->low_degree_rounds != 1) || t->window_levels < 0 ||
+      t->window_levels > 4096 || t->window_max_frontier < 0)
     return fail(LDD_ERR_ARG, "tuning out of range (blocks per SM 1 .. %d)", max_per_sm);
   g->bfs_per_sm = t->bfs_blocks_per_sm;
   g->bfs_grid = g->bfs_per_sm * g->num_sms;
@@ -1712,6 +1720,8 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
   g->pull_gamma = (u32)t->pull_gamma;
   g->probe_min_arcs = (u32)t->probe_min_arcs;
   g->low_degree_rounds = t->low_degree_rounds != 0;
+  g->window_levels = (u32)t->window_levels;
+  g->window_max_q = (u32)t->window_max_frontier;
   g->stats.bfs_grid = g->bfs_grid;
   drop_replay(g);  // captured kernels carry the old parameters
   return LDD_OK;

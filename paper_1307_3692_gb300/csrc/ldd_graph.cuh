@@ -121,6 +121,8 @@ struct ldd_graph {
   u32 probe_min_arcs = 1u << 16;
   u32 max_degree = 0;          // largest row of the CSR (unions: of any member)
   bool low_degree_rounds = true;  // tuning: low-degree rounds when max_degree allows
+  u32 window_levels = 0;          // tuning: levels per window in low-degree rounds (0: none)
+  u32 window_max_q = 1u << 18;    // tuning: windows only for frontiers up to this size
   bool timing = false;
   cudaEvent_t ev[8] = {};
   // pipelined batches (ldd_decompose_batch), set up on first use

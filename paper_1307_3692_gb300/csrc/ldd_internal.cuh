@@ -74,7 +74,7 @@ struct Control {
   u64 pull_arcs;   // arcs scanned bottom-up
   u64 pull_verts;  // vertices examined bottom-up
   u32 ucnt[3];     // lengths of the still-unsettled lists of bottom-up rounds
-  u32 pad0;
+  u32 windows;     // windows of levels run by the last round loop
   // sort state
   u32 mask_f;     // bit d: fraction digit pass d is needed (exact path)
   u32 mask_r;     // unused (start buckets are a counting sort)
@@ -90,6 +90,11 @@ struct Control {
   long long round_clk[kRoundProfile][3];
   int round_kind[kRoundProfile];
   u32 radius;  // max dist of the last labelling (ldd_decompose_retry)
+  // windows of levels (low-degree rounds, k_bfs.cu): overflow-list lengths,
+  // rotating like qctr, and the result of a scan for the next start level
+  // (~level, by atomicMax; 0: none)
+  u32 ovf[3];
+  u32 nstart[3];
 };
 constexpr size_t kCtlHeaderBytes = 40;       // err .. cut
 constexpr size_t kCtlBfsStateOffset = 40;    // bar_count .. pull_rounds
@@ -124,6 +129,8 @@ struct BfsArgs {
   u32 probe_min_arcs;  // top-down rounds with at least this many arcs read a key before its atomicMin
   u32 low_degree;    // 1: every vertex has at most kLdMaxDegree arcs and the low-degree rounds
                      // run (the frontier a plain vertex list, a thread per vertex)
+  u32 window_levels; // low-degree rounds: levels per window (0 or 1: one level per grid barrier)
+  u32 window_max_q;  // ... a window only while the frontier has at most this many vertices
   const u32* wmem;   // unions: member of every 32-vertex word; else null
   u32* mrank;        // unions: [3][kmem] smallest rank per level slot and member (~0 on entry)
   u32 kmem;          // unions: members

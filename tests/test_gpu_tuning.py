@@ -109,3 +109,49 @@ def test_low_degree_rounds_both_ways(ldd, cuda, name):
             assert np.array_equal(du[i * G.n:(i + 1) * G.n].cpu().numpy(), od)
     u.close()
     g.close()
+
+
+@pytest.mark.parametrize("name", ["grid3d_48", "grid2d_400x300", "rgg_big_frontiers", "path_3000"])
+def test_windows_of_levels_are_exact(ldd, cuda, name):
+    """Low-degree rounds with windows of 2 .. 64 levels between grid barriers:
+    label-correcting inside a window, so a vertex may be expanded twice, but
+    the labels equal the oracle's.  The random geometric graph at beta 0.5
+    starts many centers at once: with windows allowed for any frontier size,
+    the CTAs' local queues overflow and the overflow list carries vertices
+    into the next round."""
+    G, beta = {"grid3d_48": (gen.grid3d(48, 48, 48), 0.03),
+               "grid2d_400x300": (gen.grid2d(400, 300), 0.02),
+               "rgg_big_frontiers": (gen.rgg(1_500_000, 6), 0.5),
+               "path_3000": (gen.grid2d(3000, 1), 0.01)}[name]
+    sh = gen.shifts(G.n, beta, 13)
+    oc, od = oracle.oracle_ldd(G.row_ptr, G.col, sh)
+    g = ldd.LddGraph(torch.from_numpy(G.row_ptr).to(cuda), torch.from_numpy(G.col).to(cuda))
+    base = g.tuning()
+    c = torch.empty(G.n, dtype=torch.int32, device=cuda)
+    d = torch.empty(G.n, dtype=torch.int32, device=cuda)
+    runs = []
+    for wl, wmax in ((2, 1 << 18), (4, 1 << 18), (8, 1 << 18), (64, 1 << 18), (8, 1 << 30),
+                     (8, 0), (3, 1 << 30)):
+        g.set_tuning(**(base | dict(window_levels=wl, window_max_frontier=wmax)))
+        g.decompose(beta, torch.from_numpy(sh).to(cuda), c, d)
+        st = g.stats()
+        assert np.array_equal(c.cpu().numpy(), oc) and np.array_equal(d.cpu().numpy(), od), (wl, wmax)
+        runs.append((wl, wmax, st["bfs_windows"], st["items"], st["n_active"]))
+        assert st["items"] >= st["n_active"]  # every BFS vertex expanded at least once
+        if wmax == 0:
+            assert st["bfs_windows"] == 0
+    assert any(r[2] > 0 for r in runs), runs
+    # a union of three copies, windows on
+    u = ldd.LddUnion([g, g, g])
+    u.set_tuning(**(u.tuning() | dict(window_levels=8, window_max_frontier=1 << 30)))
+    shs = [gen.shifts(G.n, beta, 40 + i) for i in range(3)]
+    cu = torch.empty(u.total, dtype=torch.int32, device=cuda)
+    du = torch.empty(u.total, dtype=torch.int32, device=cuda)
+    u.decompose([beta] * 3, torch.from_numpy(np.concatenate(shs)).to(cuda), cu, du)
+    assert u.stats()["bfs_windows"] > 0
+    for i in range(3):
+        oc, od = oracle.oracle_ldd(G.row_ptr, G.col, shs[i])
+        assert np.array_equal(cu[i * G.n:(i + 1) * G.n].cpu().numpy(), oc)
+        assert np.array_equal(du[i * G.n:(i + 1) * G.n].cpu().numpy(), od)
+    u.close()
+    g.close()
