@@ -682,7 +682,8 @@ def batch_arm(args, dist):
             "union": {"replayed_in_timed_steps": sts[-1]["replayed"],
                       "ms_replay": sts[-1]["ms_replay"], "rounds": st["rounds"], "pull_rounds": st["pull_rounds"], "A": st["max_floor_shift"],
                       "ms_rank": st["ms_rank"], "ms_bfs": st["ms_bfs"], "ms_finalize": st["ms_finalize"],
-                      "ms_cut": st["ms_cut"], "ms_total": st["ms_total"], "exact_rank": st["exact_rank"]},
+                      "ms_cut": st["ms_cut"], "ms_total": st["ms_total"], "exact_rank": st["exact_rank"],
+                      "bfs_windows": st["bfs_windows"], "bfs_overflow": st["bfs_overflow"]},
             "host_s": {"generation": t_gen, "graph_and_union_creation": t_create},
             "create_graph": {"wall_ms": 1e3 * t_create,
                              "components_ms": sum(mg.stats()["ms_create_components"]

@@ -414,6 +414,8 @@ typedef struct {
   int64_t block_arcs_scanned; /* arcs of G_0, G_1, ... read by the residual passes */
   int64_t block_arcs_kept;    /* arcs written as G_1, G_2, ... */
   int64_t bfs_windows;    /* windows of levels the last round loop ran (ldd_tuning) */
+  int64_t bfs_overflow;   /* vertices that windows carried into the next round because a
+                             CTA's local queue was full */
 } ldd_stats;
 
 int ldd_get_stats(const ldd_graph* g, ldd_stats* out);
@@ -436,9 +438,13 @@ typedef struct {
                                 same pass); 0: the edge-balanced rounds always */
   int32_t window_levels;     /* low-degree rounds: levels relaxed between two grid barriers
                                 (each CTA going on with the vertices it reaches; exact, but a
-                                vertex may be expanded twice); 0 or 1: one level per barrier */
+                                vertex may be expanded twice); 0 or 1: one level per barrier;
+                                8 by default */
   int32_t window_max_frontier; /* ... a window only while the frontier has at most this many
-                                vertices (>= 0) */
+                                vertices (>= 0; 2^18 by default) */
+  int32_t window_queue;      /* ... entries of a CTA's local queue per level: 0 for as many
+                                as fit in shared memory, else at most that many (>= 0); the
+                                rest waits for the next round */
   float ms;                  /* ldd_autotune: the best decomposition time seen, ms */
 } ldd_tuning;
 
@@ -450,9 +456,9 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t);
  * ldd_autotune -- pick g's launch parameters for this workload by timing
  * decompositions (CUDA events on g's stream, best of reps after one warm-up)
  * while trying a few values of one parameter at a time (push/pull thresholds,
- * key-probe threshold, CTAs per SM, low-degree rounds), keeping a value only for a gain of 2 %
- * or more.  shifts: a representative shift vector (n doubles; a union's
- * caller-layout total), host or device.  The chosen parameters stay on g and
+ * key-probe threshold, CTAs per SM, windows of levels, low-degree rounds),
+ * keeping a value only for a gain of 2 % or more.  shifts: a representative
+ * shift vector (n doubles; a union's caller-layout total), host or device.  The chosen parameters stay on g and
  * are returned in *out.  Results of later decompositions are unaffected.
  */
 int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out);

@@ -54,7 +54,7 @@ class _Stats(ctypes.Structure):
                                             "ms_create_total", "ms_block_total",
                                             "ms_block_residual")] + [
         (name, ctypes.c_int64) for name in ("block_arcs_scanned", "block_arcs_kept",
-                                            "bfs_windows")]
+                                            "bfs_windows", "bfs_overflow")]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -127,6 +127,7 @@ class Tuning(ctypes.Structure):
                 ("pull_beta", ctypes.c_int32), ("pull_gamma", ctypes.c_int32),
                 ("probe_min_arcs", ctypes.c_int32), ("low_degree_rounds", ctypes.c_int32),
                 ("window_levels", ctypes.c_int32), ("window_max_frontier", ctypes.c_int32),
+                ("window_queue", ctypes.c_int32),
                 ("ms", ctypes.c_float)]
 
 

@@ -46,6 +46,8 @@
 // bucket; the loop stops as soon as every vertex with an arc is settled.
 // All device-side waits are bounded: a barrier that does not complete within
 // the spin limit sets kErrTimeout and the kernel returns.
+#include <cstddef>
+
 #include "ldd_internal.cuh"
 
 namespace ldd {
@@ -81,11 +83,27 @@ struct Smem {
   u32 lcnt[2];           // windows: lengths of the CTA's two local queues
   u32 nstart;            // a scan's result, shared by the CTA
 };
-// Windows of levels keep two local queues of (vertex, level) pairs in the
-// memory the edge-balanced rounds use for their span windows.
-constexpr int kLq = 3072;
-static_assert(2 * kLq * sizeof(u64) <= sizeof(int) * kBfsMaxSpan * 2 + sizeof(u64) * kBfsMaxSpan,
-              "local queues fit the span-window arrays");
+// Windows of levels keep two local queues of (level, vertex) pairs.  The
+// first sits in the memory the edge-balanced rounds use for their span
+// windows.  With two CTAs per SM the second shares it; with one, which has the
+// room, it gets as much again after Smem and both hold twice the entries.
+constexpr size_t kSpanBytes = sizeof(int) * kBfsMaxSpan * 2 + sizeof(u64) * kBfsMaxSpan;
+static_assert(offsetof(Smem, owner) == 0 && offsetof(Smem, rowd) < offsetof(Smem, cand) &&
+                  offsetof(Smem, cand) + sizeof(u64) * (kBfsMaxSpan + 1) >= kSpanBytes,
+              "the span-window arrays lead Smem and cover its first kSpanBytes bytes");
+constexpr int lq_cap(int per_sm) { return (int)(per_sm >= 2 ? kSpanBytes / 16 : kSpanBytes / 8); }
+constexpr size_t lq_extra(int per_sm) { return per_sm >= 2 ? 0 : kSpanBytes; }
+// the entries a local queue takes: the tuning's limit, if any, else all that fit
+template <int kCap>
+__device__ __forceinline__ u32 lq_limit(const BfsArgs& a) {
+  return a.window_queue ? min(a.window_queue, (u32)kCap) : (u32)kCap;
+}
+template <int kCap>
+__device__ __forceinline__ u64* lq_buf(Smem& s, int b) {
+  u64* span = reinterpret_cast<u64*>(&s.owner[0]);
+  if ((size_t)kCap * 16 <= kSpanBytes) return span + (size_t)b * kCap;
+  return b == 0 ? span : reinterpret_cast<u64*>(reinterpret_cast<unsigned char*>(&s) + sizeof(Smem));
+}
 
 // Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a
 // launch completes when the counter reaches k * nblocks (+ phantom), so
@@ -563,7 +581,7 @@ __device__ __forceinline__ void expand_ld(const BfsArgs& a, const u32* qv_cur, u
 
 // Pushes (w[i], lev) for every bit i of mask: to the CTA's local queue `nb`
 // while it has room, the rest to the overflow list of the next round.
-template <int K>
+template <int K, int kCap>
 __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u32 (&lev)[K],
                                             const BfsArgs& a, Smem& s, int nb, int qi, int qb) {
   const u32 lane = threadIdx.x & 31;
@@ -579,12 +597,13 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
   u32 base = 0;
   if (lane == 0) base = atomicAdd(&s.lcnt[nb], tot);
   base = __shfl_sync(kFull, base, 0) + incl - mine;
-  u64* lq = reinterpret_cast<u64*>(&s.owner[0]) + (size_t)nb * kLq;
+  u64* lq = lq_buf<kCap>(s, nb);
+  const u32 cap = lq_limit<kCap>(a);
   u32 spill = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i)
     if (mask >> i & 1u) {
-      if (base < (u32)kLq) lq[base] = ((u64)lev[i] << 32) | w[i];
+      if (base < cap) lq[base] = ((u64)lev[i] << 32) | w[i];
       else spill |= 1u << i;
       ++base;
     }
@@ -618,7 +637,7 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
 // end is H: v's current key is offered to its neighbours; winners below H go
 // to the local queue nb, winners at H that reach it for the first time to the
 // global queue qb.  Every lane of the warp calls this.
-template <bool U>
+template <bool U, int kCap>
 __device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool valid, u32 v, u32 lev,
                                               u32 H, int nb, int qi, int qb, u32& myrank,
                                               u32* s_acc, u64& pushed, u64& expanded) {
@@ -660,15 +679,17 @@ __device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool va
 #pragma unroll
     for (int q = 0; q < kLdBatch; ++q)  // the next round's bottom-up floor: level-H keys
       note_rank<U>(a, (u32)qi, ((won >> q) & 1u) && cl == H, w[q], (u32)cand, myrank, s_acc);
-    window_push<kLdBatch>(local, w, wl, a, s, nb, qi, qb);
+    window_push<kLdBatch, kCap>(local, w, wl, a, s, nb, qi, qb);
     warp_append<kLdBatch, true>(glob, w, a, qi, qb);
   }
 }
 
 // One window of levels [L, H): the level-L frontier (Q entries of qv_cur) and
 // the nov overflow entries of the last round (qrow/qoff of side qcur), then
-// local levels L .. H - 1.  `expanded` counts expansions.
-template <bool U>
+// local levels L .. H - 1, then whatever the CTA's local queue still holds.
+// Only pushes that find the local queue full wait for the next round (on the
+// overflow list).  `expanded` counts expansions.
+template <bool U, int kCap>
 __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* rv, int A,
                                           u32 Q, u32 nov, int qcur, u32 L, u32 H, int qi, int qb,
                                           u32& myrank, u32* s_acc, u64& pushed, u64& expanded) {
@@ -678,11 +699,14 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
     s.lcnt[1] = 0;
   }
   __syncthreads();
-  const u64* lq_all = reinterpret_cast<const u64*>(&s.owner[0]);
   int lb = 0;  // the local queue being read (level lv); the other one is filled
-  for (u32 lv = L; lv < H; ++lv) {
+  for (u32 lv = L;; ++lv) {
     const int nb = lb ^ 1;
-    const u32 nloc = min(s.lcnt[lb], (u32)kLq);
+    const u32 nloc = min(s.lcnt[lb], lq_limit<kCap>(a));  // the same for the whole CTA
+    // Past the window's last level the CTA goes on with its own queue until
+    // it is empty: entries of overflow from an earlier window run behind the
+    // frontier, and their chains end here instead of one hop per round.
+    if (lv >= H && nloc == 0) break;
     // (1) the window's first level: the global frontier and the overflow list
     if (lv == L) {
       const u32 total = Q + nov;
@@ -695,7 +719,7 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
           v = ld_cg_u32(reinterpret_cast<const u32*>(a.qrow[qcur]) + (i - Q));
           lev = ld_cg_u32(a.qoff[qcur] + (i - Q));
         }
-        window_expand<U>(a, s, i < total, v, lev, H, nb, qi, qb, myrank, s_acc, pushed,
+        window_expand<U, kCap>(a, s, i < total, v, lev, H, nb, qi, qb, myrank, s_acc, pushed,
                          expanded);
       }
     }
@@ -703,12 +727,12 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
     for (u32 base = threadIdx.x & ~31u; base < nloc; base += blockDim.x) {
       const u32 i = base + lane;
       u64 e = 0;
-      if (i < nloc) e = lq_all[(size_t)lb * kLq + i];
-      window_expand<U>(a, s, i < nloc, (u32)e, (u32)(e >> 32), H, nb, qi, qb, myrank, s_acc,
+      if (i < nloc) e = lq_buf<kCap>(s, lb)[i];
+      window_expand<U, kCap>(a, s, i < nloc, (u32)e, (u32)(e >> 32), H, nb, qi, qb, myrank, s_acc,
                        pushed, expanded);
     }
     // (3) start bucket lv + 1: a vertex whose key still has its start level joins level lv + 1
-    if ((int)lv + 1 <= A) {
+    if ((int)lv + 1 <= A && lv + 1 <= H) {
       const int lo = __ldg(a.bptr + lv + 1), hi = __ldg(a.bptr + lv + 2);
       const u32 cnt = (u32)(hi - lo);
       for (u32 base = warp_first_item(1, true); base < cnt; base += gridDim.x * blockDim.x) {
@@ -722,7 +746,7 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
           start = (u32)(k >> 32) == lv + 1;
         }
         if (lv + 1 < H) {
-          window_push<1>(start ? 1u : 0u, u, ul, a, s, nb, qi, qb);
+          window_push<1, kCap>(start ? 1u : 0u, u, ul, a, s, nb, qi, qb);
         } else {
           note_rank<U>(a, (u32)qi, start, u[0], (u32)k, myrank, s_acc);
           warp_append<1, true>(start ? 1u : 0u, u, a, qi, qb);
@@ -733,24 +757,6 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
     if (threadIdx.x == 0) s.lcnt[lb] = 0;
     __syncthreads();
     lb = nb;
-  }
-  // Overflow entries carry the levels of an earlier window, so their chains
-  // may still be going at the last level: what is left in the local queue
-  // waits on the overflow list for the next round.
-  const u32 left = min(s.lcnt[lb], (u32)kLq);  // the same for the whole CTA
-  if (left > 0) {
-    if (threadIdx.x == 0) s.lcnt[lb ^ 1] = (u32)kLq;  // no local room: window_push spills all
-    __syncthreads();
-    for (u32 b0 = 0; b0 < left; b0 += blockDim.x) {  // the same trip count for every warp
-      const u32 i = b0 + threadIdx.x;
-      u32 w[1] = {0}, wl[1] = {0};
-      if (i < left) {
-        const u64 e = lq_all[(size_t)lb * kLq + i];
-        w[0] = (u32)e;
-        wl[0] = (u32)(e >> 32);
-      }
-      window_push<1>(i < left ? 1u : 0u, w, wl, a, s, lb ^ 1, qi, qb);
-    }
   }
 }
 
@@ -1046,7 +1052,8 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   // union with few enough members: per-member next-level minima and
   // current-level floors in shared memory, after Smem
   u32* s_acc = (U && a.kmem <= kSmemMembers)
-                   ? reinterpret_cast<u32*>(smem_raw + sizeof(Smem)) : nullptr;
+                   ? reinterpret_cast<u32*>(smem_raw + sizeof(Smem) + (LD ? lq_extra(kPerSm) : 0))
+                   : nullptr;
   u32* s_floor = s_acc ? s_acc + kSmemMembers : nullptr;
   if (s_acc)
     for (u32 m = threadIdx.x; m < a.kmem; m += blockDim.x) s_acc[m] = 0xffffffffu;
@@ -1085,7 +1092,8 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
   u64 settled = 0, edges = 0;
   u64 items = 0;     // vertices expanded (a window may expand a vertex twice)
   u64 expanded = 0;  // this thread's expansions inside windows
-  u32 phase = 0, pulls = 0, nwin = 0;
+  u32 phase = 0, pulls = 0, nwin = 0, overflowed = 0;
+  u32 wdepth = a.window_levels;  // levels of the next window
   u64 push_arcs = 0;
   int lvl = 0;
   bool pulling = false;
@@ -1128,16 +1136,34 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
     int nlvl;
     // a window of levels: low-degree rounds whose frontier is thin enough, and
     // always while overflow entries of the last window wait
-    const bool window = LD && a.window_levels > 1 && (nov > 0 || (Q > 0 && Q <= a.window_max_q));
+    bool window = false;
+    u32 H = 0;
+    if (LD && a.window_levels > 1 && (nov > 0 || (Q > 0 && Q <= a.window_max_q))) {
+      // The window's depth adapts: halved while the last window's local queues
+      // overflowed by more than a quarter of the frontier, doubled again (up
+      // to the tuning's) once nothing overflowed; and cut before the first
+      // start bucket it would take in locally (buckets lvl + 1 .. H - 1) that
+      // holds more than window_max_q vertices.  One level only drains the
+      // overflow.  The same for every thread: nov, Q and bptr are.
+      if (nov > (Q >> 2)) wdepth = max(wdepth >> 1, 1u);
+      else if (nov == 0) wdepth = min(wdepth << 1, a.window_levels);
+      u32 d = 1;
+      for (; d < wdepth; ++d) {
+        const int r = lvl + (int)d;
+        if (r <= A && (u32)(__ldg(a.bptr + r + 1) - __ldg(a.bptr + r)) > a.window_max_q) break;
+      }
+      window = d > 1 || nov > 0;
+      H = (u32)lvl + d;
+    }
     if (window) {
       edges += E;
       pulling = false;
-      const u32 H = (u32)lvl + a.window_levels;
-      window_ld<U>(a, s, rv, A, Q, nov, (int)(phase & 1), (u32)lvl, H, qi, qb, myrank, s_acc,
+      window_ld<U, lq_cap(kPerSm)>(a, s, rv, A, Q, nov, (int)(phase & 1), (u32)lvl, H, qi, qb, myrank, s_acc,
                    pushed, expanded);
       if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][0] = clock64();
       windowed = true;
       ++nwin;
+      overflowed += nov;
       nlvl = (int)H;
     } else if (Q > 0) {
       items += Q;
@@ -1243,6 +1269,7 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
     atomicAdd(&ctl->items, windowed ? items : settled);
     ctl->edges = edges;
     ctl->windows = nwin;
+    ctl->overflowed = overflowed;
   }
 }
 
@@ -1251,7 +1278,9 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
 size_t bfs_smem_bytes() { return sizeof(Smem); }
 
 namespace {
-size_t bfs_smem(bool u) { return sizeof(Smem) + (u ? 2 * kSmemMembers * sizeof(u32) : 0); }
+size_t bfs_smem(bool u, int per_sm, bool ld) {
+  return sizeof(Smem) + (ld ? lq_extra(per_sm) : 0) + (u ? 2 * kSmemMembers * sizeof(u32) : 0);
+}
 
 const void* bfs_kernel(bool u, int per_sm, bool ld) {
   if (ld) {
@@ -1271,7 +1300,8 @@ int bfs_grid_size(int num_sms, int* blocks_per_sm) {
       for (int p = 1; p <= 2; ++p)
         for (int ld = 0; ld < 2; ++ld)
           cudaFuncSetAttribute(bfs_kernel(u != 0, p, ld != 0),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bfs_smem(u != 0));
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bfs_smem(u != 0, p, ld != 0));
     attr_set[dev] = true;
   }
   // the most CTAs per SM (1 or 2) that every instance built for it reaches
@@ -1281,7 +1311,7 @@ int bfs_grid_size(int num_sms, int* blocks_per_sm) {
       for (int ld = 0; ld < 2; ++ld) {
         int got = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, bfs_kernel(u != 0, p, ld != 0),
-                                                          kBfsThreads, bfs_smem(u != 0)) !=
+                                                          kBfsThreads, bfs_smem(u != 0, p, ld != 0)) !=
             cudaSuccess)
           return -1;
         if (got < 1) return -1;
@@ -1296,7 +1326,8 @@ int launch_bfs(const BfsArgs& a, int grid, int per_sm, cudaStream_t s, cudaError
   void* args[] = {&copy};
   *err = cudaLaunchCooperativeKernel(bfs_kernel(a.mrank != nullptr, per_sm, a.low_degree != 0),
                                      dim3(grid),
-                                     dim3(kBfsThreads), args, bfs_smem(a.mrank != nullptr), s);
+                                     dim3(kBfsThreads), args,
+                                     bfs_smem(a.mrank != nullptr, per_sm, a.low_degree != 0), s);
   return *err == cudaSuccess ? 1 : -1;
 }
 

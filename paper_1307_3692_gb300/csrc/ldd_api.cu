@@ -407,6 +407,7 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.low_degree = (g->low_degree_rounds && g->max_degree <= (u32)kLdMaxDegree) ? 1u : 0u;
   a.window_levels = g->window_levels;
   a.window_max_q = g->window_max_q;
+  a.window_queue = g->window_queue;
   a.wmem = g->uni ? g->uni->d_wmem : nullptr;
   a.mrank = g->uni ? g->uni->d_mrank : nullptr;
   a.kmem = g->uni ? g->uni->k : 0;
@@ -446,6 +447,12 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
 
 constexpr u32 kDefaultBarrierPolls = 1u << 22;   // grid barrier: each poll >= 20 ns after 64
 constexpr u32 kDefaultLookbackPolls = 1u << 24;  // look-back: each poll >= 64 ns after 16
+// Low-degree rounds of a single graph relax eight levels between grid
+// barriers by default, those of a union one (ldd_autotune tries both).
+// Measured: 256^3 grid 4.0 -> 3.4 ms, 256^2 0.49 -> 0.35 ms with windows;
+// unions of random geometric graphs were as fast or faster level by level.
+constexpr u32 kDefaultWindowLevels = 8;
+constexpr u32 kDefaultUnionWindowLevels = 1;
 
 // Scratch arena, pinned header, events and launch parameters: the part of
 // graph creation that only depends on the sizes and the tables being built.
@@ -474,7 +481,8 @@ int finish_setup(ldd_graph* g) {
   g->probe_min_arcs = env_u32("LDD_PROBE_MIN_ARCS", 1u << 16);
   const char* ldr = getenv("LDD_LOW_DEGREE_ROUNDS");  // "0": edge-balanced rounds only
   g->low_degree_rounds = !(ldr && ldr[0] == '0' && ldr[1] == 0);
-  g->window_levels = env_u32("LDD_WINDOW_LEVELS", 0);
+  g->window_levels =
+      env_u32("LDD_WINDOW_LEVELS", g->uni ? kDefaultUnionWindowLevels : kDefaultWindowLevels);
   g->window_max_q = env_u32("LDD_WINDOW_MAX_FRONTIER", 1u << 18);
   g->stats.n = g->n;
   g->stats.nnz = g->nnz;
@@ -502,6 +510,8 @@ struct Header {  // the control block up to and including the BFS runtime state
   u64 pull_verts;
   u32 ucnt[3];
   u32 windows;
+  u32 overflowed;
+  u32 pad_w;
 };
 static_assert(sizeof(Header) == kCtlHeaderBytes + kCtlBfsStateBytes, "header layout");
 
@@ -548,6 +558,7 @@ void header_stats(ldd_graph* g, const Header& h, bool exact64) {
   st.pull_arcs = (int64_t)h.pull_arcs;
   st.pull_vertices = (int64_t)h.pull_verts;
   st.bfs_windows = h.windows;
+  st.bfs_overflow = h.overflowed;
 }
 
 int header_error(u32 err) {
@@ -1699,6 +1710,7 @@ int ldd_get_tuning(const ldd_graph* g, ldd_tuning* out) {
   out->low_degree_rounds = g->low_degree_rounds ? 1 : 0;
   out->window_levels = (int32_t)g->window_levels;
   out->window_max_frontier = (int32_t)std::min<u32>(g->window_max_q, 0x7fffffffu);
+  out->window_queue = (int32_t)std::min<u32>(g->window_queue, 0x7fffffffu);
   out->ms = -1.f;
   return LDD_OK;
 }
@@ -1711,7 +1723,7 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
   if (t->bfs_blocks_per_sm < 1 || t->bfs_blocks_per_sm > max_per_sm || t->pull_alpha < 0 ||
       t->pull_beta < 1 || t->pull_gamma < 0 || t->probe_min_arcs < 0 ||
       (t->low_degree_rounds != 0 && t->low_degree_rounds != 1) || t->window_levels < 0 ||
-      t->window_levels > 4096 || t->window_max_frontier < 0)
+      t->window_levels > 4096 || t->window_max_frontier < 0 || t->window_queue < 0)
     return fail(LDD_ERR_ARG, "tuning out of range (blocks per SM 1 .. %d)", max_per_sm);
   g->bfs_per_sm = t->bfs_blocks_per_sm;
   g->bfs_grid = g->bfs_per_sm * g->num_sms;
@@ -1722,6 +1734,7 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
   g->low_degree_rounds = t->low_degree_rounds != 0;
   g->window_levels = (u32)t->window_levels;
   g->window_max_q = (u32)t->window_max_frontier;
+  g->window_queue = (u32)t->window_queue;
   g->stats.bfs_grid = g->bfs_grid;
   drop_replay(g);  // captured kernels carry the old parameters
   return LDD_OK;
@@ -1780,8 +1793,9 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) 
   const int32_t gammas[] = {2, 4, 8, 16, 64};
   const int32_t probes[] = {1 << 12, 1 << 16, 1 << 20, 1 << 30};
   const int32_t ld_vals[2] = {0, 1};
+  const int32_t window_vals[3] = {1, 8, 16};
   const bool ld_possible = g->max_degree <= (u32)kLdMaxDegree;
-  for (int param = 0; param < 6 && rc == LDD_OK; ++param) {
+  for (int param = 0; param < 7 && rc == LDD_OK; ++param) {
     const int32_t* vals = param == 0 ? alphas : param == 1 ? betas : param == 2 ? gammas : probes;
     int nv = param == 3 ? 4 : 5;
     int32_t per_sm_vals[2] = {1, max_per_sm};
@@ -1789,7 +1803,11 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) 
       vals = per_sm_vals;
       nv = max_per_sm > 1 ? 2 : 1;
     }
-    if (param == 5) {  // the low-degree rounds, where the graph allows them
+    if (param == 5) {  // windows of levels, where low-degree rounds run
+      vals = window_vals;
+      nv = (ld_possible && cur.low_degree_rounds) ? 3 : 0;
+    }
+    if (param == 6) {  // the low-degree rounds, where the graph allows them
       vals = ld_vals;
       nv = ld_possible ? 2 : 0;
     }
@@ -1797,7 +1815,8 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) 
       ldd_tuning t = cur;
       int32_t* field = param == 0 ? &t.pull_alpha : param == 1 ? &t.pull_beta
                      : param == 2 ? &t.pull_gamma : param == 3 ? &t.probe_min_arcs
-                     : param == 4 ? &t.bfs_blocks_per_sm : &t.low_degree_rounds;
+                     : param == 4 ? &t.bfs_blocks_per_sm : param == 5 ? &t.window_levels
+                     : &t.low_degree_rounds;
       if (*field == vals[i]) continue;
       *field = vals[i];
       if ((rc = ldd_set_tuning(g, &t)) != LDD_OK) break;

@@ -75,6 +75,8 @@ struct Control {
   u64 pull_verts;  // vertices examined bottom-up
   u32 ucnt[3];     // lengths of the still-unsettled lists of bottom-up rounds
   u32 windows;     // windows of levels run by the last round loop
+  u32 overflowed;  // ... vertices they carried into the next round (full local queues)
+  u32 pad_w;
   // sort state
   u32 mask_f;     // bit d: fraction digit pass d is needed (exact path)
   u32 mask_r;     // unused (start buckets are a counting sort)
@@ -98,7 +100,7 @@ struct Control {
 };
 constexpr size_t kCtlHeaderBytes = 40;       // err .. cut
 constexpr size_t kCtlBfsStateOffset = 40;    // bar_count .. pull_rounds
-constexpr size_t kCtlBfsStateBytes = 88;
+constexpr size_t kCtlBfsStateBytes = 96;
 constexpr size_t kCtlMinrankOffset = 72;
 
 struct BfsArgs {
@@ -131,6 +133,7 @@ struct BfsArgs {
                      // run (the frontier a plain vertex list, a thread per vertex)
   u32 window_levels; // low-degree rounds: levels per window (0 or 1: one level per grid barrier)
   u32 window_max_q;  // ... a window only while the frontier has at most this many vertices
+  u32 window_queue;  // ... local-queue entries per CTA and level at most (0: as many as fit)
   const u32* wmem;   // unions: member of every 32-vertex word; else null
   u32* mrank;        // unions: [3][kmem] smallest rank per level slot and member (~0 on entry)
   u32 kmem;          // unions: members

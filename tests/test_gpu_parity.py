@@ -382,11 +382,14 @@ def test_self_loops_and_repeated_arcs(ldd, cuda):
 @pytest.mark.parametrize("mode", ["always_pull", "alternate", "default"])
 def test_bottom_up_rounds(ldd, cuda, mode, monkeypatch):
     """Bottom-up (pull) rounds with the exact min-rank early exit give the same
-    keys as top-down rounds: forced every round, alternated, and by heuristic."""
+    keys as top-down rounds: forced every round, alternated, and by heuristic.
+    Low-degree graphs run level by level here (a window of levels is always
+    top-down)."""
     env = {"always_pull": ("1000000000", "1000000000"), "alternate": ("1000000000", "1"),
            "default": ("14", "24")}[mode]
     monkeypatch.setenv("LDD_PULL_ALPHA", env[0])
     monkeypatch.setenv("LDD_PULL_BETA", env[1])
+    monkeypatch.setenv("LDD_WINDOW_LEVELS", "1")
     cases = [(gen.rmat(13), 0.1, 1), (gen.rmat(14), 0.02, 2), (gen.grid2d(60, 70), 0.05, 3),
              (gen.grid3d(14, 15, 16), 0.2, 4), (gen.rgg(4000, 5), 0.3, 5)]
     for G, beta, seed in cases:

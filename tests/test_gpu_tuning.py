@@ -71,9 +71,9 @@ def test_autotune_plain_and_union(ldd, cuda):
                                   "gnp_600", "path_5000"])
 def test_low_degree_rounds_both_ways(ldd, cuda, name):
     """Graphs whose vertices have at most 32 arcs run the low-degree rounds by
-    default; the edge-balanced rounds give the same labels (both = oracle),
-    with and without bottom-up rounds and key probes, on a plain graph and
-    in a union."""
+    default, with windows of eight levels; level by level and the
+    edge-balanced rounds give the same labels (all = oracle), with and without
+    bottom-up rounds and key probes, on a plain graph and in a union."""
     G, beta = {"grid3d_40": (gen.grid3d(40, 40, 40), 0.05),
                "grid2d_300x200_small_beta": (gen.grid2d(300, 200), 0.01),
                "rgg_30000": (gen.rgg(30000, 3), 0.2),
@@ -85,9 +85,10 @@ def test_low_degree_rounds_both_ways(ldd, cuda, name):
     g = ldd.LddGraph(torch.from_numpy(G.row_ptr).to(cuda), torch.from_numpy(G.col).to(cuda))
     assert g.tuning()["low_degree_rounds"] == 1
     base = g.tuning()
-    for st in (dict(low_degree_rounds=1), dict(low_degree_rounds=0),
-               dict(low_degree_rounds=1, pull_alpha=1000, pull_gamma=0),
-               dict(low_degree_rounds=1, probe_min_arcs=0, bfs_blocks_per_sm=2)):
+    assert base["window_levels"] == 8  # windows of levels by default
+    for st in (dict(), dict(low_degree_rounds=1, window_levels=1), dict(low_degree_rounds=0),
+               dict(low_degree_rounds=1, window_levels=1, pull_alpha=1000, pull_gamma=0),
+               dict(low_degree_rounds=1, window_levels=1, probe_min_arcs=0, bfs_blocks_per_sm=2)):
         g.set_tuning(**(base | st))
         c = torch.empty(G.n, dtype=torch.int32, device=cuda)
         d = torch.empty(G.n, dtype=torch.int32, device=cuda)
@@ -95,11 +96,12 @@ def test_low_degree_rounds_both_ways(ldd, cuda, name):
         assert np.array_equal(c.cpu().numpy(), oc) and np.array_equal(d.cpu().numpy(), od), st
         st_ = g.stats()
         if st.get("low_degree_rounds") == 1 and st_["pull_rounds"] == 0:
-            assert st_["push_arcs"] <= G.nnz  # every arc offered at most once
+            assert st_["push_arcs"] <= G.nnz  # level by level: every arc offered at most once
     u = ldd.LddUnion([g, g, g])
+    assert u.tuning()["window_levels"] == 1  # unions: level by level by default
     shs = [gen.shifts(G.n, beta, 20 + i) for i in range(3)]
-    for ldr in (1, 0):
-        u.set_tuning(**(u.tuning() | dict(low_degree_rounds=ldr)))
+    for ldr, wl in ((1, 8), (1, 1), (0, 8)):
+        u.set_tuning(**(u.tuning() | dict(low_degree_rounds=ldr, window_levels=wl)))
         cu = torch.empty(u.total, dtype=torch.int32, device=cuda)
         du = torch.empty(u.total, dtype=torch.int32, device=cuda)
         u.decompose([beta] * 3, torch.from_numpy(np.concatenate(shs)).to(cuda), cu, du)
@@ -115,10 +117,10 @@ def test_low_degree_rounds_both_ways(ldd, cuda, name):
 def test_windows_of_levels_are_exact(ldd, cuda, name):
     """Low-degree rounds with windows of 2 .. 64 levels between grid barriers:
     label-correcting inside a window, so a vertex may be expanded twice, but
-    the labels equal the oracle's.  The random geometric graph at beta 0.5
-    starts many centers at once: with windows allowed for any frontier size,
-    the CTAs' local queues overflow and the overflow list carries vertices
-    into the next round."""
+    the labels equal the oracle's.  Local queues limited to one or a few
+    dozen entries per CTA overflow, and the overflow list carries vertices into
+    the next round; the random geometric graph at beta 0.5 starts many centers
+    at once."""
     G, beta = {"grid3d_48": (gen.grid3d(48, 48, 48), 0.03),
                "grid2d_400x300": (gen.grid2d(400, 300), 0.02),
                "rgg_big_frontiers": (gen.rgg(1_500_000, 6), 0.5),
@@ -130,20 +132,25 @@ def test_windows_of_levels_are_exact(ldd, cuda, name):
     c = torch.empty(G.n, dtype=torch.int32, device=cuda)
     d = torch.empty(G.n, dtype=torch.int32, device=cuda)
     runs = []
-    for wl, wmax in ((2, 1 << 18), (4, 1 << 18), (8, 1 << 18), (64, 1 << 18), (8, 1 << 30),
-                     (8, 0), (3, 1 << 30)):
-        g.set_tuning(**(base | dict(window_levels=wl, window_max_frontier=wmax)))
+    for wl, wmax, wq in ((2, 1 << 18, 0), (4, 1 << 18, 0), (8, 1 << 18, 0), (64, 1 << 18, 0),
+                         (8, 1 << 30, 0), (8, 0, 0), (3, 1 << 30, 0), (8, 1 << 30, 64),
+                         (5, 1 << 30, 1)):
+        g.set_tuning(**(base | dict(window_levels=wl, window_max_frontier=wmax, window_queue=wq)))
         g.decompose(beta, torch.from_numpy(sh).to(cuda), c, d)
         st = g.stats()
-        assert np.array_equal(c.cpu().numpy(), oc) and np.array_equal(d.cpu().numpy(), od), (wl, wmax)
-        runs.append((wl, wmax, st["bfs_windows"], st["items"], st["n_active"]))
+        assert np.array_equal(c.cpu().numpy(), oc) and np.array_equal(d.cpu().numpy(), od), \
+            (wl, wmax, wq)
+        runs.append((wl, wmax, wq, st["bfs_windows"], st["bfs_overflow"], st["items"]))
         assert st["items"] >= st["n_active"]  # every BFS vertex expanded at least once
         if wmax == 0:
-            assert st["bfs_windows"] == 0
-    assert any(r[2] > 0 for r in runs), runs
+            assert st["bfs_windows"] == 0 and st["bfs_overflow"] == 0
+        if wq == 1 and name != "path_3000":  # one local entry per CTA and level: full queues
+            assert st["bfs_overflow"] > 0, runs
+    assert any(r[3] > 0 for r in runs), runs
     # a union of three copies, windows on
     u = ldd.LddUnion([g, g, g])
-    u.set_tuning(**(u.tuning() | dict(window_levels=8, window_max_frontier=1 << 30)))
+    u.set_tuning(**(u.tuning() | dict(window_levels=8, window_max_frontier=1 << 30,
+                                      window_queue=16)))
     shs = [gen.shifts(G.n, beta, 40 + i) for i in range(3)]
     cu = torch.empty(u.total, dtype=torch.int32, device=cuda)
     du = torch.empty(u.total, dtype=torch.int32, device=cuda)
