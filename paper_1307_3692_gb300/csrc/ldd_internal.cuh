@@ -97,6 +97,9 @@ struct Control {
   // (~level, by atomicMax; 0: none)
   u32 ovf[3];
   u32 nstart[3];
+  // bottom-up rounds: the next unit of candidates a warp takes once the
+  // units dealt out in advance are done (rotating like qctr)
+  u32 pull_ctr[3];
 };
 constexpr size_t kCtlHeaderBytes = 40;       // err .. cut
 constexpr size_t kCtlBfsStateOffset = 40;    // bar_count .. pull_rounds
