@@ -445,6 +445,8 @@ typedef struct {
   int32_t window_queue;      /* ... entries of a CTA's local queue per level: 0 for as many
                                 as fit in shared memory, else at most that many (>= 0); the
                                 rest waits for the next round */
+  int32_t bfs_span;          /* edge-balanced rounds: the most arcs a CTA takes per step, a
+                                multiple of 256 from 256 to 4096 (4096 by default) */
   float ms;                  /* ldd_autotune: the best decomposition time seen, ms */
 } ldd_tuning;
 
@@ -456,10 +458,11 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t);
  * ldd_autotune -- pick g's launch parameters for this workload by timing
  * decompositions (CUDA events on g's stream, best of reps after one warm-up)
  * while trying a few values of one parameter at a time (push/pull thresholds,
- * key-probe threshold, CTAs per SM, windows of levels, low-degree rounds),
- * keeping a value only for a gain of 2 % or more.  shifts: a representative
- * shift vector (n doubles; a union's caller-layout total), host or device.  The chosen parameters stay on g and
- * are returned in *out.  Results of later decompositions are unaffected.
+ * key-probe threshold, CTAs per SM, windows of levels, low-degree rounds,
+ * arcs per CTA step), keeping a value only for a gain of 2 % or more.
+ * shifts: a representative shift vector (n doubles; a union's caller-layout
+ * total), host or device.  The chosen parameters stay on g and are returned
+ * in *out.  Results of later decompositions are unaffected.
  */
 int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out);
 

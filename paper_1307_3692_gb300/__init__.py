@@ -127,7 +127,7 @@ class Tuning(ctypes.Structure):
                 ("pull_beta", ctypes.c_int32), ("pull_gamma", ctypes.c_int32),
                 ("probe_min_arcs", ctypes.c_int32), ("low_degree_rounds", ctypes.c_int32),
                 ("window_levels", ctypes.c_int32), ("window_max_frontier", ctypes.c_int32),
-                ("window_queue", ctypes.c_int32),
+                ("window_queue", ctypes.c_int32), ("bfs_span", ctypes.c_int32),
                 ("ms", ctypes.c_float)]
 
 

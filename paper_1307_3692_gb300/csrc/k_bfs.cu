@@ -364,7 +364,7 @@ __device__ __forceinline__ void expand(const BfsArgs& a, Smem& s, int cur, u32 Q
                                        int qi, int qb, u32& myrank, u32* s_acc) {
   const u32 nb = (E + kBfsBase - 1) / kBfsBase;
   u32 k = (nb + gridDim.x - 1) / gridDim.x;
-  k = max(1u, min(k, (u32)(kBfsMaxSpan / kBfsBase)));
+  k = max(1u, min(k, a.span / kBfsBase));
   const u32 nsuper = (nb + k - 1) / k;
   const u32* cf = a.cf[cur];
   const u32* qv = a.qv[cur];

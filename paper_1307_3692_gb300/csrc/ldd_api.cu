@@ -408,6 +408,7 @@ BfsArgs bfs_args(ldd_graph* g) {
   a.window_levels = g->window_levels;
   a.window_max_q = g->window_max_q;
   a.window_queue = g->window_queue;
+  a.span = g->bfs_span;
   a.wmem = g->uni ? g->uni->d_wmem : nullptr;
   a.mrank = g->uni ? g->uni->d_mrank : nullptr;
   a.kmem = g->uni ? g->uni->k : 0;
@@ -1711,6 +1712,7 @@ int ldd_get_tuning(const ldd_graph* g, ldd_tuning* out) {
   out->window_levels = (int32_t)g->window_levels;
   out->window_max_frontier = (int32_t)std::min<u32>(g->window_max_q, 0x7fffffffu);
   out->window_queue = (int32_t)std::min<u32>(g->window_queue, 0x7fffffffu);
+  out->bfs_span = (int32_t)g->bfs_span;
   out->ms = -1.f;
   return LDD_OK;
 }
@@ -1723,7 +1725,8 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
   if (t->bfs_blocks_per_sm < 1 || t->bfs_blocks_per_sm > max_per_sm || t->pull_alpha < 0 ||
       t->pull_beta < 1 || t->pull_gamma < 0 || t->probe_min_arcs < 0 ||
       (t->low_degree_rounds != 0 && t->low_degree_rounds != 1) || t->window_levels < 0 ||
-      t->window_levels > 4096 || t->window_max_frontier < 0 || t->window_queue < 0)
+      t->window_levels > 4096 || t->window_max_frontier < 0 || t->window_queue < 0 ||
+      t->bfs_span < kBfsBase || t->bfs_span > kBfsMaxSpan || t->bfs_span % kBfsBase != 0)
     return fail(LDD_ERR_ARG, "tuning out of range (blocks per SM 1 .. %d)", max_per_sm);
   g->bfs_per_sm = t->bfs_blocks_per_sm;
   g->bfs_grid = g->bfs_per_sm * g->num_sms;
@@ -1735,6 +1738,7 @@ int ldd_set_tuning(ldd_graph* g, const ldd_tuning* t) {
   g->window_levels = (u32)t->window_levels;
   g->window_max_q = (u32)t->window_max_frontier;
   g->window_queue = (u32)t->window_queue;
+  g->bfs_span = (u32)t->bfs_span;
   g->stats.bfs_grid = g->bfs_grid;
   drop_replay(g);  // captured kernels carry the old parameters
   return LDD_OK;
@@ -1794,8 +1798,9 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) 
   const int32_t probes[] = {1 << 12, 1 << 16, 1 << 20, 1 << 30};
   const int32_t ld_vals[2] = {0, 1};
   const int32_t window_vals[3] = {1, 8, 16};
+  const int32_t span_vals[3] = {1024, 2048, 4096};
   const bool ld_possible = g->max_degree <= (u32)kLdMaxDegree;
-  for (int param = 0; param < 7 && rc == LDD_OK; ++param) {
+  for (int param = 0; param < 8 && rc == LDD_OK; ++param) {
     const int32_t* vals = param == 0 ? alphas : param == 1 ? betas : param == 2 ? gammas : probes;
     int nv = param == 3 ? 4 : 5;
     int32_t per_sm_vals[2] = {1, max_per_sm};
@@ -1811,12 +1816,16 @@ int ldd_autotune(ldd_graph* g, const double* shifts, int reps, ldd_tuning* out) 
       vals = ld_vals;
       nv = ld_possible ? 2 : 0;
     }
+    if (param == 7) {  // arcs per CTA step, where edge-balanced rounds run
+      vals = span_vals;
+      nv = (ld_possible && cur.low_degree_rounds) ? 0 : 3;
+    }
     for (int i = 0; i < nv && rc == LDD_OK; ++i) {
       ldd_tuning t = cur;
       int32_t* field = param == 0 ? &t.pull_alpha : param == 1 ? &t.pull_beta
                      : param == 2 ? &t.pull_gamma : param == 3 ? &t.probe_min_arcs
                      : param == 4 ? &t.bfs_blocks_per_sm : param == 5 ? &t.window_levels
-                     : &t.low_degree_rounds;
+                     : param == 6 ? &t.low_degree_rounds : &t.bfs_span;
       if (*field == vals[i]) continue;
       *field = vals[i];
       if ((rc = ldd_set_tuning(g, &t)) != LDD_OK) break;

@@ -124,6 +124,7 @@ struct ldd_graph {
   u32 window_levels = 0;          // tuning: levels per window in low-degree rounds (0: none)
   u32 window_max_q = 1u << 18;    // tuning: windows only for frontiers up to this size
   u32 window_queue = 0;           // tuning: local-queue entries per CTA and level (0: all that fit)
+  u32 bfs_span = kBfsMaxSpan;     // tuning: arcs per CTA step of an edge-balanced round
   bool timing = false;
   cudaEvent_t ev[8] = {};
   // pipelined batches (ldd_decompose_batch), set up on first use

@@ -137,6 +137,7 @@ struct BfsArgs {
   u32 window_levels; // low-degree rounds: levels per window (0 or 1: one level per grid barrier)
   u32 window_max_q;  // ... a window only while the frontier has at most this many vertices
   u32 window_queue;  // ... local-queue entries per CTA and level at most (0: as many as fit)
+  u32 span;          // edge-balanced rounds: arcs per CTA step at most (kBfsBase .. kBfsMaxSpan)
   const u32* wmem;   // unions: member of every 32-vertex word; else null
   u32* mrank;        // unions: [3][kmem] smallest rank per level slot and member (~0 on entry)
   u32 kmem;          // unions: members

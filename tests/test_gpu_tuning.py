@@ -1,5 +1,6 @@
 """Launch parameters (ldd_set_tuning / ldd_autotune): the round loop's
-push/pull thresholds, key-probe threshold and CTAs per SM change speed only --
+push/pull thresholds, key-probe threshold, CTAs per SM, round mode, windows
+and arcs per CTA step change speed only --
 every setting gives the oracle's labels bit for bit -- and the autotuner keeps
 a setting from its candidates."""
 from __future__ import annotations
@@ -16,7 +17,8 @@ pytestmark = pytest.mark.gpu
 SETTINGS = [dict(pull_alpha=0), dict(pull_alpha=1000, pull_gamma=0), dict(pull_beta=1),
             dict(probe_min_arcs=0), dict(probe_min_arcs=1 << 30), dict(bfs_blocks_per_sm=1),
             dict(low_degree_rounds=0), dict(low_degree_rounds=1, probe_min_arcs=0),
-            dict(low_degree_rounds=1, pull_alpha=1000, pull_gamma=0, pull_beta=1000)]
+            dict(low_degree_rounds=1, pull_alpha=1000, pull_gamma=0, pull_beta=1000),
+            dict(bfs_span=256), dict(bfs_span=1024, low_degree_rounds=0, probe_min_arcs=0)]
 
 
 @pytest.mark.parametrize("G,beta", [(gen.rmat(14), 0.1), (gen.grid2d(90, 70), 0.05)],
@@ -37,6 +39,9 @@ def test_every_setting_is_exact(ldd, cuda, G, beta):
         g.set_tuning(bfs_blocks_per_sm=0)
     with pytest.raises(ldd.LddError):
         g.set_tuning(pull_beta=0)
+    for bad in (0, 255, 300, 4352):  # spans: multiples of 256 from 256 to 4096
+        with pytest.raises(ldd.LddError):
+            g.set_tuning(**(base | dict(bfs_span=bad)))
     g.close()
 
 
@@ -47,6 +52,7 @@ def test_autotune_plain_and_union(ldd, cuda):
     t = g.autotune(sh, reps=1)
     assert t["ms"] > 0 and t["pull_alpha"] in (4, 8, 14, 24, 48)
     assert t["bfs_blocks_per_sm"] in (1, 2) and g.tuning()["pull_beta"] == t["pull_beta"]
+    assert t["bfs_span"] in (1024, 2048, 4096)
     c = np.empty(G.n, np.int32)
     d = np.empty(G.n, np.int32)
     g.decompose(0.1, sh, c, d)
