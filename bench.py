@@ -774,7 +774,9 @@ def serve_arm(args, dist):
         run = np.array([x["batch_run_us"] for x in batches.values()]) / 1e3
         return {"requests": len(infos), "throughput_rps": len(infos) / span,
                 "mean_batch_fill_ms": float(fill.mean()), "mean_batch_run_ms": float(run.mean()),
-                "device_busy_fraction": float(run.sum() / 1e3 / span),
+                # batches' device phases summed over the span: above 1 when the
+                # workers' batches overlap on the device
+                "batch_run_sum_over_span": float(run.sum() / 1e3 / span),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
                 "batches": int(len(set(x["batch_id"] for x in infos))),

@@ -260,10 +260,11 @@ int ldd_block_decompose(ldd_graph* g, int k, const double* betas, const double* 
  * arcs, cut-list entries, small components -- against the workspace's
  * capacities) and decomposes them as one disjoint union (see
  * ldd_create_union): exactly the per-request results, computed together.
- * The round loop of one batch holds the device at a time; meanwhile the other
- * workers build their unions and copy shifts in and results out, so requests
- * that arrive while a batch runs join the next one as soon as a workspace
- * frees up.  A request whose input fails (a bad shift) fails alone: its batch
+ * The workers' batches run side by side on the device on the workers' own
+ * streams, except that their round loops (cooperative kernels that occupy
+ * every SM) run one after another, ordered by events: one batch's rank,
+ * finalize, cut counts and copies overlap another's, and requests that arrive
+ * while a batch runs join the next one as soon as a workspace frees up.  A request whose input fails (a bad shift) fails alone: its batch
  * is rerun request by request.  A batch that holds a single request skips the
  * union and runs on that request's own graph object (at low arrival rates the
  * union would only add latency).  Graphs passed to a server must stay alive,
@@ -293,7 +294,8 @@ typedef struct {
   double start_us;    /* taken by a worker */
   double end_us;      /* results in the caller's buffers */
   double batch_fill_us; /* its batch: union built and shifts copied in (host clock) */
-  double batch_run_us;  /* its batch: decomposition and cut counts on the device */
+  double batch_run_us;  /* its batch: decomposition, cut counts and result copies, from
+                           their enqueueing to their end (host clock) */
 } ldd_request_info;
 
 /* ldd_server_create -- a server on the current device.  LDD_ERR_RANGE if the

@@ -107,6 +107,7 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->d_bcut);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
+  if (g->ev_gate) cudaEventDestroy(g->ev_gate);
   for (int i = 0; i < 2; ++i) {
     if (g->ev_in[i]) cudaEventDestroy(g->ev_in[i]);
     if (g->ev_used[i]) cudaEventDestroy(g->ev_used[i]);
@@ -429,10 +430,26 @@ int run_bfs_finalize(ldd_graph* g, int* center, int* dist, int* status) {
       *status = fail(LDD_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
       return -1;
     }
+    std::unique_lock<std::mutex> gate_lk;
+    if (g->gate) {  // after the round loop enqueued last through the same gate
+      gate_lk = std::unique_lock<std::mutex>(g->gate->mu);
+      if (g->gate->last) e = cudaStreamWaitEvent(s, g->gate->last, 0);
+      if (e != cudaSuccess) {
+        *status = fail(LDD_ERR_CUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
+        return -1;
+      }
+    }
     if (launch_bfs(bfs_args(g), g->bfs_grid, g->bfs_per_sm, s, &e) < 0) {
       *status = fail(LDD_ERR_CUDA, "cooperative launch of the BFS kernel (%d x %d) failed: %s",
                      g->bfs_grid, kBfsThreads, cudaGetErrorString(e));
       return -1;
+    }
+    if (g->gate) {
+      if ((e = cudaEventRecord(g->ev_gate, s)) != cudaSuccess) {
+        *status = fail(LDD_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+        return -1;
+      }
+      g->gate->last = g->ev_gate;
     }
     ++launches;
   }

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "../../include/ldd.h"
@@ -59,6 +60,17 @@ struct Blocks;  // state of ldd_block_decompose (ldd_blocks.cu)
 }  // namespace ldd
 
 using namespace ldd;
+
+// Round loops that share a device through a gate run one after another: each
+// one's stream waits on the event recorded after the previous one was
+// enqueued, and only the enqueueing is serialised (under mu).  The round loop
+// is a cooperative kernel that occupies every SM, so two of them never run
+// side by side; what overlaps on the device is everything around them (rank,
+// finalize, cut counts, copies).
+struct BfsGate {
+  std::mutex mu;
+  cudaEvent_t last = nullptr;  // recorded after the last round loop enqueued, or none
+};
 
 struct ldd_graph {
   int32_t n = 0;
@@ -127,6 +139,8 @@ struct ldd_graph {
   u32 bfs_span = kBfsMaxSpan;     // tuning: arcs per CTA step of an edge-balanced round
   bool timing = false;
   cudaEvent_t ev[8] = {};
+  BfsGate* gate = nullptr;       // set by the request server on its workspaces
+  cudaEvent_t ev_gate = nullptr;  // ... recorded after this graph's round loop
   // pipelined batches (ldd_decompose_batch), set up on first use
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaStream_t cut_stream = nullptr;  // cut counts, overlapping the next decomposition's rank

@@ -13,14 +13,16 @@
 // alone):
 //   1. union tables from the members' resident tables (one kernel launch) and
 //      the members' shifts copied in (host -> device);
-//   2. spread, rank, round loop, finalize and the members' cut counts -- the
-//      part that holds the device: one worker at a time (the round loop is a
-//      cooperative kernel that occupies every SM);
+//   2. spread, rank, round loop, finalize and the members' cut counts on the
+//      worker's stream;
 //   3. results copied out (device -> host), requests completed.
-// While one worker is in step 2, the others fill their workspaces and copy
-// shifts in or results out, so requests that arrive while a batch is on the
-// GPU are admitted to the next batch as soon as a slot and memory are free,
-// and their copies overlap the running batch.
+// The workers' streams run side by side on the device except for the round
+// loop, a cooperative kernel that occupies every SM: the workspaces share a
+// gate (BfsGate, ldd_graph.cuh), so each round loop waits on the event of the
+// one enqueued before it.  One batch's rank, finalize, cut count and copies
+// thus overlap another's, requests that arrive while a batch is on the GPU
+// are admitted to the next batch as soon as a slot and memory are free, and
+// no worker holds a lock while the device runs its work.
 //
 // A batch that fails on a request's input (a bad shift) is rerun request by
 // request, so only that request fails.
@@ -116,7 +118,7 @@ struct ldd_server {
   std::vector<std::unique_ptr<Request>> reqs;  // by ticket; released by ldd_server_wait
   bool stop = false;
   int64_t next_batch = 0;
-  std::mutex dev_mu;  // step 2 of one batch at a time
+  BfsGate gate;  // orders the workspaces' round loops (and batches of one)
   std::vector<ldd_graph*> ws;
   std::vector<cudaStream_t> streams;
   std::vector<u64*> h_cut;
@@ -166,19 +168,9 @@ int run_batch(ldd_server* S, int slot, const std::vector<Request*>& batch) {
   CUDA_TRY(cudaStreamSynchronize(s));
   const double t1 = S->now_us();
   int launches = 0, cut_launches = 0;
-  double t2, t3;
-  {
-    std::lock_guard<std::mutex> lk(S->dev_mu);
-    t2 = S->now_us();
-    rc = union_run(u, U.d_shift_in, U.d_out_c, U.d_out_d, want_cut, &launches, &cut_launches);
-    if (rc != LDD_OK) return rc;
-    CUDA_TRY(cudaStreamSynchronize(s));
-    t3 = S->now_us();
-  }
-  for (Request* r : batch) {
-    r->fill_us = t1 - t0;
-    r->run_us = t3 - t2;
-  }
+  const double t2 = S->now_us();
+  rc = union_run(u, U.d_shift_in, U.d_out_c, U.d_out_d, want_cut, &launches, &cut_launches);
+  if (rc != LDD_OK) return rc;
   if (want_cut)
     CUDA_TRY(cudaMemcpyAsync(S->h_cut[(size_t)slot], U.d_cut, (size_t)k * 8,
                              cudaMemcpyDeviceToHost, s));
@@ -189,18 +181,24 @@ int run_batch(ldd_server* S, int slot, const std::vector<Request*>& batch) {
     CUDA_TRY(cudaMemcpyAsync(r->out_dist, U.d_out_d + o, n * 4, cudaMemcpyDeviceToHost, s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
+  const double t3 = S->now_us();
+  for (Request* r : batch) {
+    r->fill_us = t1 - t0;
+    r->run_us = t3 - t2;
+  }
   for (int i = 0; i < k; ++i)
     if (batch[(size_t)i]->out_cut) *batch[(size_t)i]->out_cut = (int64_t)S->h_cut[(size_t)slot][i];
   return LDD_OK;
 }
 
 // A batch of one request skips the union: the request runs on its own graph
-// object, as ldd_decompose_batch(g, 1, ...) does, with the device held for the
-// whole call (two workers may hold requests on the same graph).  At low
-// arrival rates most batches are of one, and building a union for them only
-// adds latency.
+// object, as ldd_decompose_batch(g, 1, ...) does, holding the gate for the
+// whole call (two workers may hold requests on the same graph object) after
+// the round loop enqueued last.  At low arrival rates most batches are of one,
+// and building a union for them only adds latency.
 int run_alone(ldd_server* S, Request* r) {
-  std::lock_guard<std::mutex> lk(S->dev_mu);
+  std::lock_guard<std::mutex> lk(S->gate.mu);
+  if (S->gate.last) CUDA_TRY(cudaStreamWaitEvent(r->g->stream, S->gate.last, 0));
   const double t0 = S->now_us();
   const double* sh = r->shifts;
   int32_t* oc = r->out_center;
@@ -343,6 +341,12 @@ int ldd_server_create(const ldd_server_config* cfg, ldd_server** out) {
         return rc;
       }
       u->stream = st;
+      u->gate = &S->gate;
+      if (cudaEventCreateWithFlags(&u->ev_gate, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_server(S);
+        return fail(LDD_ERR_CUDA, "cudaEventCreate failed");
+      }
     }
     for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker_batched, S, i);
   } else {

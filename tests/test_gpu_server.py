@@ -139,3 +139,38 @@ def test_server_one_at_a_time_and_threads(ldd, cuda):
         srv.close()
     for g in gs:
         g.close()
+
+
+def test_server_slots_overlap_exact(ldd, cuda):
+    """Three workers: their batches run side by side on the device, round
+    loops ordered by the gate; every request still equals its result alone."""
+    Gs = _graphs()
+    gs = [ldd.LddGraph(G.row_ptr, G.col) for G in Gs]
+    rng = np.random.default_rng(9)
+    betas = [0.02, 0.1, 0.5]
+    big = len(Gs) - 1
+    reqs = [(big, 0.005, 500)] + [
+        (int(rng.integers(len(Gs))), betas[int(rng.integers(3))], 600 + i) for i in range(35)]
+    srv = ldd.LddServer(2 << 30, max_batch=4, slots=3)
+    subs = _submit_all(srv, gs, Gs, reqs)
+    infos = []
+    for t, gi, beta, seed, sh, c, d, cut in subs:
+        info = srv.wait(t)
+        infos.append(info)
+        G = Gs[gi]
+        if gi == big:
+            oc, od, ocut = _alone(ldd, G, beta, sh.numpy())
+        else:
+            oc, od = oracle.oracle_ldd(G.row_ptr, G.col, sh.numpy())
+            ocut = oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
+        assert np.array_equal(c, oc) and np.array_equal(d, od), (gi, beta, seed)
+        assert cut[0] == ocut
+    # batches of different workers were in flight at the same time
+    spans = {}
+    for inf in infos:
+        spans[inf["batch_id"]] = (inf["start_us"], inf["end_us"])
+    iv = sorted(spans.values())
+    assert any(iv[i + 1][0] < iv[i][1] for i in range(len(iv) - 1)), iv[:8]
+    srv.close()
+    for g in gs:
+        g.close()
