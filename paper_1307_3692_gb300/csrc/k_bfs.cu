@@ -83,26 +83,43 @@ struct Smem {
   u32 lcnt[2];           // windows: lengths of the CTA's two local queues
   u32 nstart;            // a scan's result, shared by the CTA
 };
-// Windows of levels keep two local queues of (level, vertex) pairs.  The
-// first sits in the memory the edge-balanced rounds use for their span
-// windows.  With two CTAs per SM the second shares it; with one, which has the
-// room, it gets as much again after Smem and both hold twice the entries.
+// Windows of levels keep two local queues whose entries carry a vertex, the
+// key it was pushed with and its adjacency range (20 bytes, as four arrays).
+// The first queue sits in the memory the edge-balanced rounds use for their
+// span windows.  With two CTAs per SM the second shares it; with one, which
+// has the room, it gets as much again after Smem.
 constexpr size_t kSpanBytes = sizeof(int) * kBfsMaxSpan * 2 + sizeof(u64) * kBfsMaxSpan;
 static_assert(offsetof(Smem, owner) == 0 && offsetof(Smem, rowd) < offsetof(Smem, cand) &&
                   offsetof(Smem, cand) + sizeof(u64) * (kBfsMaxSpan + 1) >= kSpanBytes,
               "the span-window arrays lead Smem and cover its first kSpanBytes bytes");
-constexpr int lq_cap(int per_sm) { return (int)(per_sm >= 2 ? kSpanBytes / 16 : kSpanBytes / 8); }
+constexpr size_t kLqEntry = sizeof(u64) + 3 * sizeof(u32);
+constexpr int lq_cap(int per_sm) {
+  return (int)((per_sm >= 2 ? kSpanBytes / 2 : kSpanBytes) / kLqEntry) / 32 * 32;
+}
 constexpr size_t lq_extra(int per_sm) { return per_sm >= 2 ? 0 : kSpanBytes; }
 // the entries a local queue takes: the tuning's limit, if any, else all that fit
 template <int kCap>
 __device__ __forceinline__ u32 lq_limit(const BfsArgs& a) {
   return a.window_queue ? min(a.window_queue, (u32)kCap) : (u32)kCap;
 }
+struct LocalQueue {
+  u64* key;
+  u32* rs;
+  u32* re;
+  u32* v;
+};
 template <int kCap>
-__device__ __forceinline__ u64* lq_buf(Smem& s, int b) {
-  u64* span = reinterpret_cast<u64*>(&s.owner[0]);
-  if ((size_t)kCap * 16 <= kSpanBytes) return span + (size_t)b * kCap;
-  return b == 0 ? span : reinterpret_cast<u64*>(reinterpret_cast<unsigned char*>(&s) + sizeof(Smem));
+__device__ __forceinline__ LocalQueue lq_buf(Smem& s, int b) {
+  unsigned char* span = reinterpret_cast<unsigned char*>(&s.owner[0]);
+  unsigned char* base;
+  if ((size_t)kCap * kLqEntry * 2 <= kSpanBytes) base = span + (size_t)b * kCap * kLqEntry;
+  else base = b == 0 ? span : reinterpret_cast<unsigned char*>(&s) + sizeof(Smem);
+  LocalQueue q;
+  q.key = reinterpret_cast<u64*>(base);
+  q.rs = reinterpret_cast<u32*>(q.key + kCap);
+  q.re = q.rs + kCap;
+  q.v = q.re + kCap;
+  return q;
 }
 
 // Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a
@@ -579,10 +596,12 @@ __device__ __forceinline__ void expand_ld(const BfsArgs& a, const u32* qv_cur, u
 // level for the next one that still holds an unclaimed vertex (one pass and
 // one grid barrier) instead of stopping when every vertex is settled.
 
-// Pushes (w[i], lev) for every bit i of mask: to the CTA's local queue `nb`
-// while it has room, the rest to the overflow list of the next round.
+// Pushes vertex w[i] with key k[i] and adjacency range [rs[i], re[i]) for
+// every bit i of mask: to the CTA's local queue nb while it has room, the rest
+// (as vertex and level) to the overflow list of the next round.
 template <int K, int kCap>
-__device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u32 (&lev)[K],
+__device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u64 (&k)[K],
+                                            const int (&rs)[K], const int (&re)[K],
                                             const BfsArgs& a, Smem& s, int nb, int qi, int qb) {
   const u32 lane = threadIdx.x & 31;
   const u32 mine = __popc(mask);
@@ -597,14 +616,20 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
   u32 base = 0;
   if (lane == 0) base = atomicAdd(&s.lcnt[nb], tot);
   base = __shfl_sync(kFull, base, 0) + incl - mine;
-  u64* lq = lq_buf<kCap>(s, nb);
+  const LocalQueue lq = lq_buf<kCap>(s, nb);
   const u32 cap = lq_limit<kCap>(a);
   u32 spill = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i)
     if (mask >> i & 1u) {
-      if (base < cap) lq[base] = ((u64)lev[i] << 32) | w[i];
-      else spill |= 1u << i;
+      if (base < cap) {
+        lq.key[base] = k[i];
+        lq.rs[base] = (u32)rs[i];
+        lq.re[base] = (u32)re[i];
+        lq.v[base] = w[i];
+      } else {
+        spill |= 1u << i;
+      }
       ++base;
     }
   // a full local queue: the rest waits for the next round on the overflow list
@@ -625,7 +650,7 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
     if (spill >> i & 1u) {
       if (sbase < a.n) {
         reinterpret_cast<u32*>(a.qrow[qb])[sbase] = w[i];
-        a.qoff[qb][sbase] = lev[i];
+        a.qoff[qb][sbase] = (u32)(k[i] >> 32);
       } else {
         atomicOr(&a.ctl->err, kErrInternal);  // more pushes than vertices: cannot happen
       }
@@ -633,24 +658,22 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
     }
 }
 
-// Expands one item per lane (valid: v with push level lev) in a window whose
-// end is H: v's current key is offered to its neighbours; winners below H go
-// to the local queue nb, winners at H that reach it for the first time to the
-// global queue qb.  Every lane of the warp calls this.
+// Expands one item per lane -- valid: key kv, adjacency range [rs, re) -- in a
+// window whose end is H: kv + 2^32 is offered to the neighbours.  Winners
+// below H go to the local queue nb with the key they got and their adjacency
+// range (loaded beside the atomicMin, not after it), winners at H that reach
+// it for the first time to the global queue qb.  A kv that is no longer the
+// vertex's key (it was lowered again, and its lowerer pushed it again) only
+// makes offers that the better key dominates.  Every lane of the warp calls
+// this.
 template <bool U, int kCap>
-__device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool valid, u32 v, u32 lev,
-                                              u32 H, int nb, int qi, int qb, u32& myrank,
-                                              u32* s_acc, u64& pushed, u64& expanded) {
+__device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool valid, u64 kv,
+                                              int rs, int re, u32 H, int nb, int qi, int qb,
+                                              u32& myrank, u32* s_acc, u64& pushed,
+                                              u64& expanded) {
   constexpr u32 kNone = 0xffffffffu;
-  u64 kv = 0;
-  int rs = 0, re = 0;
-  if (valid) {
-    kv = ld_cg_u64(a.key + v);
-    rs = __ldg(a.row_ptr + v);
-    re = __ldg(a.row_ptr + v + 1);
-    if ((u32)(kv >> 32) < lev) re = rs;  // lowered since it was pushed: its lowerer pushed it again
-    else ++expanded;
-  }
+  if (!valid) re = rs;
+  else ++expanded;
   pushed += (u64)(re - rs);
   const u64 cand = kv + kLevelOne;
   const u32 cl = (u32)(cand >> 32);
@@ -659,16 +682,22 @@ __device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool va
   for (int o = 16; o > 0; o >>= 1) nch = max(nch, __shfl_xor_sync(kFull, nch, o));
   for (int ch = 0; ch < nch; ++ch) {
     const int e0 = rs + ch * kLdBatch;
-    u32 w[kLdBatch], wl[kLdBatch];
+    u32 w[kLdBatch];
 #pragma unroll
-    for (int q = 0; q < kLdBatch; ++q) {
-      w[q] = (e0 + q < re) ? (u32)__ldg(a.col + e0 + q) : kNone;
-      wl[q] = cl;
-    }
+    for (int q = 0; q < kLdBatch; ++q) w[q] = (e0 + q < re) ? (u32)__ldg(a.col + e0 + q) : kNone;
+    u64 kk[kLdBatch];
+    int wrs[kLdBatch], wre[kLdBatch];
     u32 local = 0, glob = 0, won = 0;
 #pragma unroll
-    for (int q = 0; q < kLdBatch; ++q)
+    for (int q = 0; q < kLdBatch; ++q) {
+      kk[q] = cand;
+      wrs[q] = 0;
+      wre[q] = 0;
       if (w[q] < a.n) {
+        if (cl < H) {  // the range of a vertex that may be pushed locally, beside the atomic
+          wrs[q] = __ldg(a.row_ptr + w[q]);
+          wre[q] = __ldg(a.row_ptr + w[q] + 1);
+        }
         const u64 old = atomicMin(a.key + w[q], cand);
         if (old > cand) {
           won |= 1u << q;
@@ -676,17 +705,19 @@ __device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool va
           else if ((u32)(old >> 32) > H) glob |= 1u << q;
         }
       }
+    }
 #pragma unroll
     for (int q = 0; q < kLdBatch; ++q)  // the next round's bottom-up floor: level-H keys
       note_rank<U>(a, (u32)qi, ((won >> q) & 1u) && cl == H, w[q], (u32)cand, myrank, s_acc);
-    window_push<kLdBatch, kCap>(local, w, wl, a, s, nb, qi, qb);
+    window_push<kLdBatch, kCap>(local, w, kk, wrs, wre, a, s, nb, qi, qb);
     warp_append<kLdBatch, true>(glob, w, a, qi, qb);
   }
 }
 
 // One window of levels [L, H): the level-L frontier (Q entries of qv_cur) and
-// the nov overflow entries of the last round (qrow/qoff of side qcur), then
-// local levels L .. H - 1, then whatever the CTA's local queue still holds.
+// the nov overflow entries of the last round (qrow/qoff of side qcur, vertex
+// and level), then local levels L .. H - 1, then whatever the CTA's local
+// queue still holds.
 // Only pushes that find the local queue full wait for the next round (on the
 // overflow list).  `expanded` counts expansions.
 template <bool U, int kCap>
@@ -699,6 +730,27 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
     s.lcnt[1] = 0;
   }
   __syncthreads();
+  // Start buckets are read one level ahead: at level lv this thread's first
+  // entry of bucket lv + 1 is known (its key is requested as the level
+  // starts, beside the expansions) and its first entry of bucket lv + 2 and
+  // the bounds of bucket lv + 3 are requested.  A key read before the level's
+  // expansions can only be higher than after them: a start taken on it that a
+  // correction undercuts is an entry that its expansion skips.
+  constexpr u32 kNoItem = 0xffffffffu;
+  const u32 i0 = warp_first_item(1, true) + lane;  // this thread's first entry of a bucket
+  const u32 gstride = gridDim.x * blockDim.x;
+  auto bucket_ok = [&](u32 r) { return (int)r <= A && r <= H; };
+  int b1lo = 0, b1hi = 0, b2lo = 0, b2hi = 0;  // buckets lv + 1 and lv + 2
+  if (bucket_ok(L + 1)) {
+    b1lo = __ldg(a.bptr + L + 1);
+    b1hi = __ldg(a.bptr + L + 2);
+  }
+  if (bucket_ok(L + 2)) {
+    b2lo = __ldg(a.bptr + L + 2);
+    b2hi = __ldg(a.bptr + L + 3);
+  }
+  u32 pu = kNoItem;  // this thread's first entry of bucket lv + 1
+  if (i0 < (u32)(b1hi - b1lo)) pu = __ldg(rv + b1lo + (int)i0);
   int lb = 0;  // the local queue being read (level lv); the other one is filled
   for (u32 lv = L;; ++lv) {
     const int nb = lb ^ 1;
@@ -707,7 +759,22 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
     // it is empty: entries of overflow from an earlier window run behind the
     // frontier, and their chains end here instead of one hop per round.
     if (lv >= H && nloc == 0) break;
-    // (1) the window's first level: the global frontier and the overflow list
+    u64 pk = 0;  // its key and adjacency range
+    int pr0 = 0, pr1 = 0;
+    if (pu != kNoItem) {
+      pk = ld_cg_u64(a.key + pu);
+      pr0 = __ldg(a.row_ptr + pu);
+      pr1 = __ldg(a.row_ptr + pu + 1);
+    }
+    u32 pu2 = kNoItem;
+    if (i0 < (u32)(b2hi - b2lo)) pu2 = __ldg(rv + b2lo + (int)i0);
+    int b3lo = 0, b3hi = 0;
+    if (bucket_ok(lv + 3)) {
+      b3lo = __ldg(a.bptr + lv + 3);
+      b3hi = __ldg(a.bptr + lv + 4);
+    }
+    // (1) the window's first level: the global frontier and the overflow list,
+    // whose keys and ranges are loaded here
     if (lv == L) {
       const u32 total = Q + nov;
       for (u32 base = warp_first_item(1); base < total; base += gridDim.x * blockDim.x) {
@@ -719,36 +786,57 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
           v = ld_cg_u32(reinterpret_cast<const u32*>(a.qrow[qcur]) + (i - Q));
           lev = ld_cg_u32(a.qoff[qcur] + (i - Q));
         }
-        window_expand<U, kCap>(a, s, i < total, v, lev, H, nb, qi, qb, myrank, s_acc, pushed,
-                         expanded);
+        u64 kv = 0;
+        int rs = 0, re = 0;
+        bool ok = i < total;
+        if (ok) {
+          kv = ld_cg_u64(a.key + v);
+          rs = __ldg(a.row_ptr + v);
+          re = __ldg(a.row_ptr + v + 1);
+          ok = (u32)(kv >> 32) >= lev;  // lowered since: its lowerer pushed it again
+        }
+        window_expand<U, kCap>(a, s, ok, kv, rs, re, H, nb, qi, qb, myrank, s_acc, pushed,
+                               expanded);
       }
     }
-    // (2) this CTA's local queue of level lv
-    for (u32 base = threadIdx.x & ~31u; base < nloc; base += blockDim.x) {
-      const u32 i = base + lane;
-      u64 e = 0;
-      if (i < nloc) e = lq_buf<kCap>(s, lb)[i];
-      window_expand<U, kCap>(a, s, i < nloc, (u32)e, (u32)(e >> 32), H, nb, qi, qb, myrank, s_acc,
-                       pushed, expanded);
+    // (2) this CTA's local queue of level lv: keys and ranges come with the entries
+    {
+      const LocalQueue lq = lq_buf<kCap>(s, lb);
+      for (u32 base = threadIdx.x & ~31u; base < nloc; base += blockDim.x) {
+        const u32 i = base + lane;
+        const bool ok = i < nloc;
+        window_expand<U, kCap>(a, s, ok, ok ? lq.key[i] : 0ull, ok ? (int)lq.rs[i] : 0,
+                               ok ? (int)lq.re[i] : 0, H, nb, qi, qb, myrank, s_acc, pushed,
+                               expanded);
+      }
     }
     // (3) start bucket lv + 1: a vertex whose key still has its start level joins level lv + 1
-    if ((int)lv + 1 <= A && lv + 1 <= H) {
-      const int lo = __ldg(a.bptr + lv + 1), hi = __ldg(a.bptr + lv + 2);
-      const u32 cnt = (u32)(hi - lo);
-      for (u32 base = warp_first_item(1, true); base < cnt; base += gridDim.x * blockDim.x) {
+    if (bucket_ok(lv + 1)) {
+      const u32 cnt = (u32)(b1hi - b1lo);
+      for (u32 base = i0 - lane; base < cnt; base += gstride) {  // warp-uniform
         const u32 i = base + lane;
-        u32 u[1] = {0}, ul[1] = {lv + 1};
+        u32 u[1] = {0};
+        u64 k[1] = {0};
+        int urs[1] = {0}, ure[1] = {0};
         bool start = false;
-        u64 k = 0;
         if (i < cnt) {
-          u[0] = __ldg(rv + lo + (int)i);
-          k = ld_cg_u64(a.key + u[0]);
-          start = (u32)(k >> 32) == lv + 1;
+          if (i == i0) {  // the entry read ahead
+            u[0] = pu;
+            k[0] = pk;
+            urs[0] = pr0;
+            ure[0] = pr1;
+          } else {
+            u[0] = __ldg(rv + b1lo + (int)i);
+            k[0] = ld_cg_u64(a.key + u[0]);
+            urs[0] = __ldg(a.row_ptr + u[0]);
+            ure[0] = __ldg(a.row_ptr + u[0] + 1);
+          }
+          start = (u32)(k[0] >> 32) == lv + 1;
         }
         if (lv + 1 < H) {
-          window_push<1, kCap>(start ? 1u : 0u, u, ul, a, s, nb, qi, qb);
+          window_push<1, kCap>(start ? 1u : 0u, u, k, urs, ure, a, s, nb, qi, qb);
         } else {
-          note_rank<U>(a, (u32)qi, start, u[0], (u32)k, myrank, s_acc);
+          note_rank<U>(a, (u32)qi, start, u[0], (u32)k[0], myrank, s_acc);
           warp_append<1, true>(start ? 1u : 0u, u, a, qi, qb);
         }
       }
@@ -757,6 +845,11 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
     if (threadIdx.x == 0) s.lcnt[lb] = 0;
     __syncthreads();
     lb = nb;
+    pu = pu2;
+    b1lo = b2lo;
+    b1hi = b2hi;
+    b2lo = b3lo;
+    b2hi = b3hi;
   }
 }
 
