@@ -521,185 +521,119 @@ __global__ void __launch_bounds__(256) k_max_i32(const int* __restrict__ x, u32 
 // ---------------------------------------------------------------- residual graphs
 // Blocks by repeated decomposition (Section 1's remark on Linial and Saks'
 // block decompositions): after decomposing G_i, the arcs whose two ends
-// share a piece form block i, and the others make up G_{i+1}.  Two passes
-// over the arcs of G_i.  The count pass counts every vertex's kept arcs (and
-// the kept arcs (v, w) with v < w: the undirected edges left) and stamps the
-// block number on the other arcs; after an exclusive scan of the counts gives
-// G_{i+1}'s row offsets, the write pass writes the kept arcs with their input
-// arc ids and hooks each kept (v, w), v < w, into the union-find forest of
-// G_{i+1}'s components.  Row order inside a row is free, and only the rows
-// walked by one thread or one warp keep it.
-//   * A warp takes 32 consecutive vertices, one per lane; a lane takes a row
-//     of at most kResShort arcs alone, loading all its arcs' ids and then all
-//     their centers before any decision.
-//   * Rows of up to kResWarp arcs are walked by the whole warp, kResUnroll
-//     chunks of 32 arcs per step (loads of all chunks first), a ballot giving
-//     every kept arc its place.
-//   * Longer rows (R-MAT hubs) are listed by the count pass and walked by one
-//     CTA each (k_residual_long), which reserves places with a shared counter.
-constexpr int kResShort = 8;
-constexpr int kResWarp = 4096;
-constexpr int kResUnroll = 4;
-constexpr int kResLongThreads = 512;
+// share a piece form block i, and the others make up G_{i+1}.
+//   * The count pass streams G_i's arcs with their source vertices (src, an
+//     arc-aligned copy of the rows), kResIpt arcs per thread with all loads
+//     first: a kept arc (v, w), centers different, adds one to kept[v] and
+//     goes onto the kept list (its arc index, one reservation per warp); the
+//     others get block i in arc_block (at their input arc id).  Rows of any
+//     length cost the same, so hubs hold nobody up.
+//   * After an exclusive scan of kept[] gives G_{i+1}'s row offsets (and a
+//     copy of them as per-row cursors), the write pass takes the kept list
+//     alone: each arc goes to its row's next place with its input arc id and
+//     source, and each kept (v, w), v < w, is hooked into the union-find
+//     forest of G_{i+1}'s components.  The order inside a row is free.
+constexpr int kResIpt = 4;
 
 struct ResArgs {
-  const int* row;
+  const int* src;
   const int* col;
   const int* orig;       // input arc id of every arc (null: the arcs are the input's)
   const int* center;
   u32 n;
+  u32 m;                 // arcs of G_i
   int block;
   int* arc_block;        // null: not recorded
   u32* kept;             // count pass: kept arcs per vertex
   unsigned long long* up_kept;
-  u32* long_rows;        // vertices with more than kResWarp arcs (count pass lists them)
-  u32* n_long;
-  const int* new_row;    // write pass
+  u32* klist;            // count pass: the kept arcs' indices
+  u32* n_kept;
+  u32* cursor;           // write pass: next place of every row
   int* new_col;
   int* new_orig;
+  int* new_src;
   u32* parent;
 };
 
-template <bool kWrite>
-__device__ __forceinline__ void res_arc(const ResArgs& a, u32 v, u32 w, int e, bool keep, int at,
-                                        u32& up) {
-  if (keep) {
-    if (v < w) ++up;
-    if (kWrite) {
-      a.new_col[at] = (int)w;
-      a.new_orig[at] = a.orig ? a.orig[e] : e;
-      if (v < w) cc_unite(a.parent, w, v);
-    }
-  } else if (!kWrite && a.arc_block) {
-    a.arc_block[a.orig ? a.orig[e] : e] = a.block;
-  }
-}
-
-template <bool kWrite>
-__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
+__global__ void __launch_bounds__(256) k_residual_count(ResArgs a) {
   const u32 lane = threadIdx.x & 31;
-  const u32 warps = gridDim.x * (blockDim.x / 32);
+  const u32 stride = gridDim.x * blockDim.x;
   u32 up = 0;
-  for (u32 base = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < a.n;
-       base += warps * 32) {
-    const u32 v = base + lane;
-    int e0 = 0, e1 = 0, cv = 0, out = 0;
-    if (v < a.n) {
-      e0 = a.row[v];
-      e1 = a.row[v + 1];
-      cv = a.center[v];
-      if (kWrite) out = a.new_row[v];
+  // warp-uniform trip count: the kept-list reservation is a warp collective
+  for (u32 b0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b0 < a.m; b0 += stride * kResIpt) {
+    u32 v[kResIpt], w[kResIpt];
+#pragma unroll
+    for (int k = 0; k < kResIpt; ++k) {
+      const u32 e = b0 + lane + (u32)k * stride;
+      v[k] = e < a.m ? (u32)__ldcs(a.src + e) : 0xffffffffu;
+      w[k] = e < a.m ? (u32)__ldcs(a.col + e) : 0xffffffffu;
     }
-    const int deg = e1 - e0;
-    u32 cnt = 0;
-    if (deg <= kResShort) {
-      u32 w[kResShort];
-      int cw[kResShort];
+    int cv[kResIpt], cw[kResIpt];
 #pragma unroll
-      for (int q = 0; q < kResShort; ++q) w[q] = q < deg ? (u32)a.col[e0 + q] : 0xffffffffu;
-#pragma unroll
-      for (int q = 0; q < kResShort; ++q) cw[q] = w[q] < a.n ? a.center[w[q]] : cv;
-#pragma unroll
-      for (int q = 0; q < kResShort; ++q)
-        if (q < deg) {
-          const bool keep = w[q] < a.n && cw[q] != cv;
-          res_arc<kWrite>(a, v, w[q], e0 + q, keep, out, up);
-          if (keep) {
-            ++cnt;
-            ++out;
-          }
-        }
-    } else if (deg > kResWarp && !kWrite) {
-      a.long_rows[atomicAdd(a.n_long, 1u)] = v;  // k_residual_long takes it
+    for (int k = 0; k < kResIpt; ++k) {
+      cv[k] = v[k] < a.n ? __ldg(a.center + v[k]) : 0;
+      cw[k] = w[k] < a.n ? __ldg(a.center + w[k]) : 0;
     }
-    u32 lm = __ballot_sync(kFull, deg > kResShort && deg <= kResWarp);
-    while (lm) {
-      const int src = __ffs(lm) - 1;
-      lm &= lm - 1;
-      const u32 sv = __shfl_sync(kFull, v, src);
-      const int b0 = __shfl_sync(kFull, e0, src), b1 = __shfl_sync(kFull, e1, src);
-      const int scv = __shfl_sync(kFull, cv, src);
-      int pos = __shfl_sync(kFull, out, src);
-      u32 c = 0;
-      for (int step = b0; step < b1; step += 32 * kResUnroll) {
-        u32 w[kResUnroll];
-        int cw[kResUnroll];
 #pragma unroll
-        for (int q = 0; q < kResUnroll; ++q) {
-          const int e = step + q * 32 + (int)lane;
-          w[q] = e < b1 ? (u32)a.col[e] : 0xffffffffu;
-        }
-#pragma unroll
-        for (int q = 0; q < kResUnroll; ++q) cw[q] = w[q] < a.n ? a.center[w[q]] : scv;
-#pragma unroll
-        for (int q = 0; q < kResUnroll; ++q) {
-          const int e = step + q * 32 + (int)lane;
-          const bool in = e < b1;
-          const bool keep = in && w[q] < a.n && cw[q] != scv;
-          const u32 km = __ballot_sync(kFull, keep);
-          if (in) res_arc<kWrite>(a, sv, w[q], e, keep, pos + __popc(km & lanemask_lt()), up);
-          pos += __popc(km);
-          c += __popc(km);
+    for (int k = 0; k < kResIpt; ++k) {
+      const u32 e = b0 + lane + (u32)k * stride;
+      const bool in = e < a.m && v[k] < a.n && w[k] < a.n;
+      const bool keep = in && cv[k] != cw[k];
+      if (in && !keep && a.arc_block) a.arc_block[a.orig ? __ldcs(a.orig + e) : (int)e] = a.block;
+      const u32 km = __ballot_sync(kFull, keep);
+      if (km) {  // kept arcs are few: one reservation per warp and step
+        u32 at = 0;
+        if (lane == (u32)(__ffs(km) - 1)) at = atomicAdd(a.n_kept, (u32)__popc(km));
+        at = __shfl_sync(kFull, at, __ffs(km) - 1) + __popc(km & lanemask_lt());
+        if (keep) {
+          a.klist[at] = e;
+          atomicAdd(a.kept + v[k], 1u);
+          if (v[k] < w[k]) ++up;
         }
       }
-      if ((int)lane == src) cnt = c;
     }
-    if (!kWrite && v < a.n && deg <= kResWarp) a.kept[v] = cnt;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(kFull, up, o);
-  if (!kWrite && lane == 0 && up) atomicAdd(a.up_kept, (unsigned long long)up);
+  if (lane == 0 && up) atomicAdd(a.up_kept, (unsigned long long)up);
 }
 
-// One CTA per listed long row (more than kResWarp arcs), both passes.
-template <bool kWrite>
-__global__ void __launch_bounds__(kResLongThreads) k_residual_long(ResArgs a) {
-  __shared__ u32 s_cnt, s_up;
-  const u32 nl = *a.n_long;
-  for (u32 i = blockIdx.x; i < nl; i += gridDim.x) {
-    const u32 v = a.long_rows[i];
-    const int e0 = a.row[v], e1 = a.row[v + 1];
-    const int cv = a.center[v];
-    if (threadIdx.x == 0) {
-      s_cnt = 0;
-      s_up = 0;
+__global__ void __launch_bounds__(256) k_residual_write(ResArgs a) {
+  const u32 nk = *a.n_kept;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
+    const u32 e = a.klist[i];
+    const u32 v = (u32)a.src[e], w = (u32)a.col[e];
+    const u32 at = atomicAdd(a.cursor + v, 1u);
+    a.new_col[at] = (int)w;
+    a.new_orig[at] = a.orig ? a.orig[e] : (int)e;
+    a.new_src[at] = (int)v;
+    if (v < w) cc_unite(a.parent, w, v);
+  }
+}
+
+// src[e] = v for every arc e of row v: a lane writes a row of up to 16 arcs,
+// the whole warp a longer one (coalesced).
+__global__ void __launch_bounds__(256) k_fill_src(const int* __restrict__ row, u32 n, int* src) {
+  const u32 lane = threadIdx.x & 31;
+  const u32 warps = gridDim.x * (blockDim.x / 32);
+  for (u32 base = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < n;
+       base += warps * 32) {
+    const u32 v = base + lane;
+    int e0 = 0, e1 = 0;
+    if (v < n) {
+      e0 = row[v];
+      e1 = row[v + 1];
     }
-    __syncthreads();
-    const int out = kWrite ? a.new_row[v] : 0;
-    u32 up = 0;
-    for (int step = e0; step < e1; step += kResLongThreads * kResUnroll) {
-      u32 w[kResUnroll];
-      int cw[kResUnroll];
-#pragma unroll
-      for (int q = 0; q < kResUnroll; ++q) {
-        const int e = step + q * kResLongThreads + (int)threadIdx.x;
-        w[q] = e < e1 ? (u32)a.col[e] : 0xffffffffu;
-      }
-#pragma unroll
-      for (int q = 0; q < kResUnroll; ++q) cw[q] = w[q] < a.n ? a.center[w[q]] : cv;
-#pragma unroll
-      for (int q = 0; q < kResUnroll; ++q) {
-        const int e = step + q * kResLongThreads + (int)threadIdx.x;
-        const bool keep = e < e1 && w[q] < a.n && cw[q] != cv;
-        const u32 km = __ballot_sync(kFull, keep);
-        int at = 0;
-        if (km) {  // one place reservation per warp step
-          u32 wb = 0;
-          if ((threadIdx.x & 31) == (u32)(__ffs(km) - 1)) wb = atomicAdd(&s_cnt, __popc(km));
-          at = out + (int)__shfl_sync(kFull, wb, __ffs(km) - 1) + __popc(km & lanemask_lt());
-        }
-        if (e < e1) res_arc<kWrite>(a, v, w[q], e, keep, at, up);
-      }
+    if (e1 - e0 <= 16)
+      for (int e = e0; e < e1; ++e) src[e] = (int)v;
+    u32 lm = __ballot_sync(kFull, e1 - e0 > 16);
+    while (lm) {
+      const int sl = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int b0 = __shfl_sync(kFull, e0, sl), b1 = __shfl_sync(kFull, e1, sl);
+      const int sv = (int)__shfl_sync(kFull, v, sl);
+      for (int e = b0 + (int)lane; e < b1; e += 32) src[e] = sv;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(kFull, up, o);
-    if ((threadIdx.x & 31) == 0 && up) atomicAdd(&s_up, up);
-    __syncthreads();
-    if (!kWrite && threadIdx.x == 0) {
-      a.kept[v] = s_cnt;
-      if (s_up) atomicAdd(a.up_kept, (unsigned long long)s_up);
-    }
-    __syncthreads();
   }
 }
 
@@ -840,21 +774,28 @@ cudaError_t components_label(const int* row_ptr, u32 n, int num_sms, const CompS
   return cudaStreamSynchronize(s);
 }
 
-int launch_residual(bool write, const int* row, const int* col, const int* orig,
-                    const int* center, u32 n, int block, int* arc_block, u32* kept,
-                    unsigned long long* up_kept, u32* long_rows, u32* n_long, const int* new_row,
-                    int* new_col, int* new_orig, u32* parent, int num_sms, cudaStream_t s) {
-  ResArgs a{row,      col,      orig,   center,  n,       block,   arc_block, kept,
-            up_kept,  long_rows, n_long, new_row, new_col, new_orig, parent};
-  const u32 blocks = (u32)max(1ll, min(((long long)n + 255) / 256, (long long)num_sms * 8));
+int launch_residual(bool write, const int* src, const int* col, const int* orig,
+                    const int* center, u32 n, u32 m, int block, int* arc_block, u32* kept,
+                    unsigned long long* up_kept, u32* klist, u32* n_kept, u32* cursor,
+                    int* new_col, int* new_orig, int* new_src, u32* parent, int num_sms,
+                    cudaStream_t s) {
+  ResArgs a{src,    col,     orig,  center, n,       m,       block,    arc_block, kept,
+            up_kept, klist,  n_kept, cursor, new_col, new_orig, new_src, parent};
   if (write) {
-    k_residual<true><<<blocks, 256, 0, s>>>(a);
-    k_residual_long<true><<<num_sms, kResLongThreads, 0, s>>>(a);
+    k_residual_write<<<num_sms * 4, 256, 0, s>>>(a);
   } else {
-    k_residual<false><<<blocks, 256, 0, s>>>(a);
-    k_residual_long<false><<<num_sms, kResLongThreads, 0, s>>>(a);
+    if (m == 0) return 0;
+    const u32 blocks = (u32)max(1ll, min(((long long)m + 256 * kResIpt - 1) / (256 * kResIpt),
+                                         (long long)num_sms * 8));
+    k_residual_count<<<blocks, 256, 0, s>>>(a);
   }
-  return 2;
+  return 1;
+}
+
+int launch_fill_src(const int* row, u32 n, int* src, int num_sms, cudaStream_t s) {
+  if (n == 0) return 0;
+  k_fill_src<<<grid_for(n, num_sms), 256, 0, s>>>(row, n, src);
+  return 1;
 }
 
 cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,

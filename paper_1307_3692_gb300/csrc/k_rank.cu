@@ -1078,10 +1078,10 @@ int launch_rank_and_buckets(const RankBufs& r, bool exact64, cudaStream_t s,
 }
 
 int launch_exclusive_scan(u32* data, u32 len, u64* status, u32* epoch, u32* tile_ctr,
-                          Control* ctl, u32 spin_limit, cudaStream_t s) {
+                          Control* ctl, u32 spin_limit, cudaStream_t s, u32* copy) {
   const u32 tiles = (len + kScanTile - 1) / kScanTile;
   if (tiles == 0) return 0;
-  k_scan_excl<<<tiles, kScanThreads, 0, s>>>(data, nullptr, len, 0, status, ++(*epoch), tile_ctr,
+  k_scan_excl<<<tiles, kScanThreads, 0, s>>>(data, copy, len, 0, status, ++(*epoch), tile_ctr,
                                              nullptr, nullptr, 0, ctl, spin_limit, 0);
   return 1;
 }

@@ -10,14 +10,15 @@
 // block i, and the cut ones are E_{i+1}.
 //
 // Everything stays on the device.  G_0 is the graph itself.  After
-// decomposition i, two passes over G_i's arcs (k_residual in k_graph.cu)
-// stamp block i on the arcs inside pieces and write the kept arcs, with their
-// input arc ids, as G_{i+1}'s CSR; the write pass also hooks G_{i+1}'s
+// decomposition i, one pass over G_i's arcs (k_residual_count in k_graph.cu,
+// arc-parallel with the arcs' source vertices) stamps block i on the arcs
+// inside pieces and lists the others; a pass over that list writes them, with
+// their input arc ids and sources, as G_{i+1}'s CSR and hooks G_{i+1}'s
 // union-find forest, so its component tables (the small-component solver and
 // the round loop's exclusion bits) follow without another pass over the
 // arcs.  G_1, G_2, ... share one graph object with ping-pong CSR buffers, all
-// sized by the input, allocated on the first call and kept on the input
-// graph until it is destroyed.
+// sized by the input, allocated on the first call (with G_0's arc sources)
+// and kept on the input graph until it is destroyed.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -36,12 +37,15 @@ struct Blocks {
   int* row[2] = {};            // [n + 1]: kept-arc counts, then G_{i+1}'s row offsets
   int* col[2] = {};            // [nnz]
   int* orig[2] = {};           // [nnz] input arc id of every arc of G_i
+  int* src[2] = {};            // [nnz] source vertex of every arc of G_i, i >= 1
+  int* src0 = nullptr;         // [nnz] source vertex of every arc of G_0
+  u32* klist = nullptr;        // [nnz] the count pass's kept arcs
+  u32* cursor = nullptr;       // [n + 1] the write pass's next place per row
   int* arc_block = nullptr;    // [nnz] block of every input arc (when the caller's is not on the device)
   u32* tmp = nullptr;          // union-find and component scratch
   CompScratch t{};
   unsigned long long* up = nullptr;  // undirected edges left (device counter)
-  u32* long_rows = nullptr;    // [n] rows the count pass leaves to one CTA each
-  u32* n_long = nullptr;
+  u32* n_kept = nullptr;
   unsigned long long* h_up = nullptr;  // pinned: [0] edges left, [1] arcs left
   cudaEvent_t ev[4] = {};      // call start / end, residual passes start / end
 };
@@ -61,12 +65,15 @@ void free_blocks(ldd_graph* g) {
     cudaFree(b->row[j]);
     cudaFree(b->col[j]);
     cudaFree(b->orig[j]);
+    cudaFree(b->src[j]);
   }
+  cudaFree(b->src0);
+  cudaFree(b->klist);
+  cudaFree(b->cursor);
   cudaFree(b->arc_block);
   cudaFree(b->tmp);
   cudaFree(b->up);
-  cudaFree(b->long_rows);
-  cudaFree(b->n_long);
+  cudaFree(b->n_kept);
   if (b->h_up) cudaFreeHost(b->h_up);
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
@@ -87,12 +94,15 @@ int setup_blocks(ldd_graph* g) {
   for (int j = 0; j < 2; ++j)
     ok = ok && cudaMalloc(&b->row[j], (n + 1) * 4) == cudaSuccess &&
          cudaMalloc(&b->col[j], nnz * 4) == cudaSuccess &&
-         cudaMalloc(&b->orig[j], nnz * 4) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->arc_block, nnz * 4) == cudaSuccess &&
+         cudaMalloc(&b->orig[j], nnz * 4) == cudaSuccess &&
+         cudaMalloc(&b->src[j], nnz * 4) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->src0, nnz * 4) == cudaSuccess &&
+       cudaMalloc(&b->klist, nnz * 4) == cudaSuccess &&
+       cudaMalloc(&b->cursor, (n + 1) * 4) == cudaSuccess &&
+       cudaMalloc(&b->arc_block, nnz * 4) == cudaSuccess &&
        cudaMalloc(&b->tmp, (7 * n + 2 * (n / 2 + 1) + 4) * 4) == cudaSuccess &&
        cudaMalloc(&b->up, sizeof(unsigned long long)) == cudaSuccess &&
-       cudaMalloc(&b->long_rows, std::max<size_t>(n, 1) * 4) == cudaSuccess &&
-       cudaMalloc(&b->n_long, 4) == cudaSuccess &&
+       cudaMalloc(&b->n_kept, 4) == cudaSuccess &&
        cudaMallocHost(&b->h_up, 2 * sizeof(unsigned long long)) == cudaSuccess;
   for (auto& e : b->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
   if (!ok) {
@@ -133,6 +143,11 @@ int setup_blocks(ldd_graph* g) {
   if (rc != LDD_OK) {
     free_blocks(g);
     return rc;
+  }
+  launch_fill_src(g->d_row, (u32)n, b->src0, g->num_sms, g->stream);
+  if (cudaGetLastError() != cudaSuccess) {
+    free_blocks(g);
+    return fail(LDD_ERR_CUDA, "arc sources of the graph");
   }
   return LDD_OK;
 }
@@ -203,9 +218,10 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     return ms;
   };
   ldd_graph* cur = g;  // G_i
-  const int* cur_row = g->d_row;
+  const int* cur_src = B.src0;
   const int* cur_col = g->d_col;
   const int* cur_orig = nullptr;  // G_0's arcs are the input arcs
+  u32 cur_m = (u32)g->nnz;
   int blocks = 0;
   for (int i = 0; i < k; ++i) {
     // decomposition i of G_i
@@ -231,20 +247,20 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     blocks = i + 1;
     // block i and G_{i+1}; r's control block and look-back words serve the scan
     const int j = i & 1;
-    CUDA_TRY(cudaMemsetAsync(r->d_ctl, 0, sizeof(Control), s));
-    CUDA_TRY(cudaMemsetAsync(B.row[j] + n, 0, 4, s));
-    CUDA_TRY(cudaMemsetAsync(B.up, 0, sizeof(unsigned long long), s));
-    CUDA_TRY(cudaMemsetAsync(B.n_long, 0, 4, s));
     CUDA_TRY(cudaEventRecord(B.ev[2], s));
+    CUDA_TRY(cudaMemsetAsync(r->d_ctl, 0, sizeof(Control), s));
+    CUDA_TRY(cudaMemsetAsync(B.row[j], 0, (n + 1) * 4, s));
+    CUDA_TRY(cudaMemsetAsync(B.up, 0, sizeof(unsigned long long), s));
+    CUDA_TRY(cudaMemsetAsync(B.n_kept, 0, 4, s));
     if (r->epoch > 0xfffff000u) {
       CUDA_TRY(cudaMemsetAsync(r->d_status, 0, r->status_bytes, s));
       r->epoch = 0;
     }
-    launch_residual(false, cur_row, cur_col, cur_orig, center, (u32)n, i, arc_block,
-                    reinterpret_cast<u32*>(B.row[j]), B.up, B.long_rows, B.n_long, nullptr,
+    launch_residual(false, cur_src, cur_col, cur_orig, center, (u32)n, cur_m, i, arc_block,
+                    reinterpret_cast<u32*>(B.row[j]), B.up, B.klist, B.n_kept, nullptr, nullptr,
                     nullptr, nullptr, nullptr, g->num_sms, s);
     launch_exclusive_scan(reinterpret_cast<u32*>(B.row[j]), (u32)n + 1, r->d_status, &r->epoch,
-                          &r->d_ctl->tile_ctr[0], r->d_ctl, r->lookback_limit, s);
+                          &r->d_ctl->tile_ctr[0], r->d_ctl, r->lookback_limit, s, B.cursor);
     CUDA_TRY(cudaMemcpyAsync(B.h_up, B.up, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(B.h_up + 1, B.row[j] + n, 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(r->h_hdr, r->d_ctl, 4, cudaMemcpyDeviceToHost, s));
@@ -252,7 +268,7 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     ms_residual += residual_ms();
-    arcs_scanned += (u64)(cur == g ? g->nnz : cur->nnz);
+    arcs_scanned += cur_m;
     u32 err;
     memcpy(&err, r->h_hdr, 4);
     if (err) {
@@ -269,9 +285,9 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     CUDA_TRY(cudaEventRecord(B.ev[2], s));
     cudaError_t e = components_init((u32)n, g->num_sms, B.t, r->d_excl, r->d_solo, s);
     if (e != cudaSuccess) return fail(LDD_ERR_CUDA, "component set-up: %s", cudaGetErrorString(e));
-    launch_residual(true, cur_row, cur_col, cur_orig, center, (u32)n, i, nullptr, nullptr,
-                    nullptr, B.long_rows, B.n_long, B.row[j], B.col[j], B.orig[j], B.t.parent,
-                    g->num_sms, s);
+    launch_residual(true, cur_src, cur_col, cur_orig, center, (u32)n, cur_m, i, nullptr, nullptr,
+                    nullptr, B.klist, B.n_kept, B.cursor, B.col[j], B.orig[j], B.src[j],
+                    B.t.parent, g->num_sms, s);
     u32 counts[4] = {0, 0, 0, 0};
     e = components_label(B.row[j], (u32)n, g->num_sms, B.t, r->d_excl, r->d_solo, counts, s);
     if (e != cudaSuccess) return fail(LDD_ERR_CUDA, "component labelling: %s", cudaGetErrorString(e));
@@ -291,9 +307,10 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     ms_residual += residual_ms();
     r->nnz = (int64_t)arcs_left;
     cur = r;
-    cur_row = B.row[j];
+    cur_src = B.src[j];
     cur_col = B.col[j];
     cur_orig = B.orig[j];
+    cur_m = (u32)arcs_left;
   }
   if (out_arc_block && !dev_blk)
     CUDA_TRY(cudaMemcpyAsync(out_arc_block, arc_block, (size_t)g->nnz * 4, cudaMemcpyDeviceToHost,

@@ -283,21 +283,26 @@ cudaError_t components_label(const int* row_ptr, u32 n, int num_sms, const CompS
 cudaError_t components_from_csr(const int* row_ptr, const int* col, u32 n, int num_sms,
                                 const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
                                 cudaStream_t s);
-// Residual graphs of the block decomposition (k_graph.cu).  Count pass
-// (write = false): kept[v] = arcs of v whose ends have different centers;
-// *up_kept += those with v < w; arc_block[orig ? orig[e] : e] = block for the
-// other arcs (arc_block may be null); rows of more than 4096 arcs are listed
-// in long_rows (*n_long zero on entry; room for every vertex).  Write pass:
-// the kept arcs at new_row[v] .., with their input arc ids, each kept (v, w),
-// v < w, hooked into parent (union-find); the order inside long rows is free.
-int launch_residual(bool write, const int* row, const int* col, const int* orig,
-                    const int* center, u32 n, int block, int* arc_block, u32* kept,
-                    unsigned long long* up_kept, u32* long_rows, u32* n_long, const int* new_row,
-                    int* new_col, int* new_orig, u32* parent, int num_sms, cudaStream_t s);
+// Residual graphs of the block decomposition (k_graph.cu), over the m arcs of
+// G_i given as (src, col).  Count pass (write = false): kept[v] += arcs of v
+// whose ends have different centers (kept zero on entry), those arcs' indices
+// onto klist (*n_kept zero on entry; room for m), *up_kept += those with
+// v < w, and arc_block[orig ? orig[e] : e] = block for the other arcs
+// (arc_block may be null).  Write pass: every listed arc at cursor[v]++ (the
+// row offsets of G_{i+1} on entry) with its input arc id and source; each kept
+// (v, w), v < w, hooked into parent (union-find).  The order inside a row is
+// free.
+int launch_residual(bool write, const int* src, const int* col, const int* orig,
+                    const int* center, u32 n, u32 m, int block, int* arc_block, u32* kept,
+                    unsigned long long* up_kept, u32* klist, u32* n_kept, u32* cursor,
+                    int* new_col, int* new_orig, int* new_src, u32* parent, int num_sms,
+                    cudaStream_t s);
+// src[e] = v for every arc e of row v of the CSR (row_ptr, n).
+int launch_fill_src(const int* row, u32 n, int* src, int num_sms, cudaStream_t s);
 // Exclusive scan of data[0 .. len) in place (k_rank.cu; decoupled look-back
 // on status words tagged with ++*epoch; tile_ctr zero on entry).
 int launch_exclusive_scan(u32* data, u32 len, u64* status, u32* epoch, u32* tile_ctr,
-                          Control* ctl, u32 spin_limit, cudaStream_t s);
+                          Control* ctl, u32 spin_limit, cudaStream_t s, u32* copy = nullptr);
 // Adjacency masks of the small-component members (sc.comp_v already filled).
 cudaError_t components_phase2(const int* row_ptr, const int* col, const CompScratch& t,
                               const SmallComps& sc, int num_sms, cudaStream_t s);
