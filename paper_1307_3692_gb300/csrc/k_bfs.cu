@@ -1356,6 +1356,9 @@ __global__ void __launch_bounds__(kBfsThreads, kPerSm) k_bfs(BfsArgs a) {
       } else {
         append_bucket<U>(a, rr, rv, qi, qb, myrank, s_acc);
       }
+      // this round left no unsettled list: a bottom-up round after it starts
+      // from every vertex the loop owns
+      pulling = false;
       nlvl = rr;
     }
     if (profiler && phase + 1 < (u32)kRoundProfile) ctl->round_clk[phase + 1][1] = clock64();

@@ -379,6 +379,28 @@ def test_self_loops_and_repeated_arcs(ldd, cuda):
         assert_parity(ldd, G, gen.shifts(G.n, beta, 31), beta)
 
 
+@pytest.mark.parametrize("low_degree", ["1", "0"])
+def test_bottom_up_after_an_empty_round(ldd, cuda, low_degree, monkeypatch):
+    """A round with an empty frontier jumps to the next start bucket and
+    leaves no unsettled list, so a bottom-up round after it must start from
+    every vertex the loop owns.  Two 30 x 30 grids: the first starts within
+    levels 0 .. 10 and is settled long before the second starts, from level
+    195 on; every round with enough frontier arcs is forced bottom-up."""
+    monkeypatch.setenv("LDD_PULL_ALPHA", "1000000000")
+    monkeypatch.setenv("LDD_PULL_BETA", "1000000000")
+    monkeypatch.setenv("LDD_WINDOW_LEVELS", "1")
+    monkeypatch.setenv("LDD_LOW_DEGREE_ROUNDS", low_degree)
+    g1 = gen.grid2d(30, 30)
+    src = np.repeat(np.arange(g1.n), np.diff(g1.row_ptr))
+    edges = [(int(u), int(v)) for u, v in zip(src, g1.col) if u < v]
+    edges += [(u + g1.n, v + g1.n) for u, v in edges]
+    G = gen.from_edges(2 * g1.n, edges, "two_grids")
+    rng = np.random.default_rng(3)
+    shifts = np.concatenate([190.0 + 10.0 * rng.random(g1.n), 5.0 * rng.random(g1.n)])
+    _, _, _, st = assert_parity(ldd, G, shifts, 0.1)
+    assert st["pull_rounds"] > 0
+
+
 @pytest.mark.parametrize("mode", ["always_pull", "alternate", "default"])
 def test_bottom_up_rounds(ldd, cuda, mode, monkeypatch):
     """Bottom-up (pull) rounds with the exact min-rank early exit give the same
