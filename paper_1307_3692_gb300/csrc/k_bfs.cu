@@ -997,27 +997,30 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
       }
     }
   };
-  // the key and the adjacency range together: one round trip, not two
+  // the key, the adjacency range and the first neighbour together: one round
+  // trip, and the scan's first probe needs no col load
   auto load_keys = [&](const u32 (&w)[kPullV], u64 (&kw)[kPullV], int (&e)[kPullV],
-                       int (&re)[kPullV]) {
+                       int (&re)[kPullV], u32 (&f)[kPullV]) {
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
       kw[j] = 0ull;
       e[j] = 0;
       re[j] = 0;
+      f[j] = kNone;
       if (w[j] != kNone) {
         kw[j] = ld_cg_u64(a.key + w[j]);
         e[j] = __ldg(a.row_ptr + w[j]);
         re[j] = __ldg(a.row_ptr + w[j] + 1);
+        if (a.first) f[j] = __ldg(a.first + w[j]);
       }
     }
   };
   u32 base = warp_first_item(kPullV);
-  u32 w[kPullV];
+  u32 w[kPullV], f[kPullV];
   u64 kw[kPullV];
   int e[kPullV], re[kPullV];
   load_ids(base, w);
-  load_keys(w, kw, e, re);
+  load_keys(w, kw, e, re, f);
   const u32 gw = base / kUnit;  // this warp's first unit
   auto dealt_base = [&](u32 p) { return (p * W + gw) * kUnit; };  // its pass p < kd
   u32 pass = 0, ticket = 0;
@@ -1061,7 +1064,7 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
       for (int j = 0; j < kPullV; ++j) {
         vv[j] = kNone;
         if (e[j] < re[j]) {
-          vv[j] = (u32)__ldg(a.col + e[j]);
+          vv[j] = (step == 0 && a.first) ? f[j] : (u32)__ldg(a.col + e[j]);
           ++e[j];
           ++scanned;
           any = true;
@@ -1115,7 +1118,8 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
     }
     u64 kwn[kPullV];  // the next pass's keys and ranges, beside this pass's appends
     int en[kPullV], ren[kPullV];
-    load_keys(wn, kwn, en, ren);
+    u32 fnn[kPullV];
+    load_keys(wn, kwn, en, ren, fnn);
     u32 mask = 0, keep = 0, won = 0;
 #pragma unroll
     for (int j = 0; j < kPullV; ++j) {
@@ -1138,6 +1142,7 @@ __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minran
       kw[j] = kwn[j];
       e[j] = en[j];
       re[j] = ren[j];
+      f[j] = fnn[j];
     }
     base = nbase;
     ++pass;

@@ -611,6 +611,15 @@ __global__ void __launch_bounds__(256) k_residual_write(ResArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_first_neighbours(const int* __restrict__ row_ptr,
+                                                          const int* __restrict__ col, u32 n,
+                                                          u32* first) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int e0 = row_ptr[v], e1 = row_ptr[v + 1];
+    first[v] = e0 < e1 ? (u32)col[e0] : 0xffffffffu;
+  }
+}
+
 // src[e] = v for every arc e of row v: a lane writes a row of up to 16 arcs,
 // the whole warp a longer one (coalesced).
 __global__ void __launch_bounds__(256) k_fill_src(const int* __restrict__ row, u32 n, int* src) {
@@ -789,6 +798,13 @@ int launch_residual(bool write, const int* src, const int* col, const int* orig,
                                          (long long)num_sms * 8));
     k_residual_count<<<blocks, 256, 0, s>>>(a);
   }
+  return 1;
+}
+
+int launch_first_neighbours(const int* row_ptr, const int* col, u32 n, u32* first, int num_sms,
+                            cudaStream_t s) {
+  if (n == 0) return 0;
+  k_first_neighbours<<<grid_for(n, num_sms), 256, 0, s>>>(row_ptr, col, n, first);
   return 1;
 }
 

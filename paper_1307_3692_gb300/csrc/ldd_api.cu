@@ -90,6 +90,7 @@ int free_graph_memory(ldd_graph* g) {
   cudaFree(g->cut.grp_lab);
   cudaFree(g->d_hot);
   if (!g->uni) cudaFree(g->d_active);  // a union's list lives in d_active_buf
+  cudaFree(g->d_first);
   cudaFree(g->d_hot_center);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
@@ -395,6 +396,7 @@ BfsArgs bfs_args(ldd_graph* g) {
   }
   a.excl = g->d_excl;
   a.active = g->d_active;
+  a.first = g->d_first;
   a.ctl = g->d_ctl;
   a.n = (u32)g->n;
   a.n_active = g->n_active;
@@ -1223,6 +1225,15 @@ int ldd_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32
   const float ms_upload = span(0, 1), ms_components = span(1, 2);
   if ((rc = build_cut_list(g, rp, up)) != LDD_OK) return bail(rc);
   if ((rc = build_active_list(g)) != LDD_OK) return bail(rc);
+  if (nnz > 0) {  // first neighbours: a bottom-up scan's first probe without a col round trip
+    if (cudaMalloc(&g->d_first, (size_t)n * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(LDD_ERR_OOM, "device allocation of the first-neighbour table failed"));
+    }
+    launch_first_neighbours(g->d_row, g->d_col, (u32)n, g->d_first, g->num_sms, nullptr);
+    if (cudaStreamSynchronize(nullptr) != cudaSuccess)
+      return bail(fail(LDD_ERR_CUDA, "first-neighbour table"));
+  }
   if ((rc = finish_setup(g)) != LDD_OK) return bail(rc);
   // low-degree rounds are latency-bound: a key probe before every atomicMin
   // is one more dependent round trip, worth it only in wide rounds

@@ -86,6 +86,7 @@ struct ldd_graph {
   int* d_col = nullptr;
   CutList cut;                 // grouped cut list (cut count of Definition 1.1)
   u32* d_active = nullptr;     // vertices the BFS handles, ascending (when few enough)
+  u32* d_first = nullptr;      // first neighbour of every vertex (single graphs)
   u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
   int* d_hot_center = nullptr; // their labels, gathered per cut count
   u32 n_hot = 0;

@@ -121,6 +121,7 @@ struct BfsArgs {
   u32* ulist[2];     // vertices still unsettled after a bottom-up round (ping-pong)
   const u32* excl;   // bit v: v is not handled by the BFS
   const u32* active; // the vertices the BFS handles, ascending (n_active), or null
+  const u32* first;  // first neighbour of every vertex (~0 without arcs), or null
   Control* ctl;
   u32 n;
   u32 n_active;      // vertices the BFS settles (components of more than 32 vertices)
@@ -297,6 +298,9 @@ int launch_residual(bool write, const int* src, const int* col, const int* orig,
                     unsigned long long* up_kept, u32* klist, u32* n_kept, u32* cursor,
                     int* new_col, int* new_orig, int* new_src, u32* parent, int num_sms,
                     cudaStream_t s);
+// first[v] = col[row_ptr[v]], or ~0 for a vertex without arcs.
+int launch_first_neighbours(const int* row_ptr, const int* col, u32 n, u32* first, int num_sms,
+                            cudaStream_t s);
 // src[e] = v for every arc e of row v of the CSR (row_ptr, n).
 int launch_fill_src(const int* row, u32 n, int* src, int num_sms, cudaStream_t s);
 // Exclusive scan of data[0 .. len) in place (k_rank.cu; decoupled look-back
