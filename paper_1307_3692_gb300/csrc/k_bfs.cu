@@ -179,11 +179,7 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
   __syncthreads();
 }
 
-__device__ __forceinline__ u32 warp_min(u32 x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(kFull, x, o));
-  return x;
-}
+__device__ __forceinline__ u32 warp_min(u32 x) { return __reduce_min_sync(kFull, x); }
 
 // First item of this warp in a grid-stride loop over groups of 32 x k items,
 // numbered so that consecutive groups go to different CTAs (warp w of CTA b
@@ -532,8 +528,7 @@ __device__ __forceinline__ void expand_ld(const BfsArgs& a, const u32* qv_cur, u
       pushed += (u64)(re[t] - rs[t]);
       nch = max(nch, (re[t] - rs[t] + kLdBatch - 1) / kLdBatch);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nch = max(nch, __shfl_xor_sync(kFull, nch, o));
+    nch = (int)__reduce_max_sync(kFull, (u32)nch);
     for (int ch = 0; ch < nch; ++ch) {
       u32 w[KA];
 #pragma unroll
@@ -633,6 +628,7 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
       ++base;
     }
   // a full local queue: the rest waits for the next round on the overflow list
+  if (!__any_sync(kFull, spill != 0u)) return;
   const u32 smine = __popc(spill);
   u32 sincl = smine;
 #pragma unroll
@@ -677,9 +673,7 @@ __device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool va
   pushed += (u64)(re - rs);
   const u64 cand = kv + kLevelOne;
   const u32 cl = (u32)(cand >> 32);
-  int nch = (re - rs + kLdBatch - 1) / kLdBatch;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nch = max(nch, __shfl_xor_sync(kFull, nch, o));
+  const int nch = (int)__reduce_max_sync(kFull, (u32)((re - rs + kLdBatch - 1) / kLdBatch));
   for (int ch = 0; ch < nch; ++ch) {
     const int e0 = rs + ch * kLdBatch;
     u32 w[kLdBatch];
