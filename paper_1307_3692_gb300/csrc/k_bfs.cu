@@ -80,7 +80,7 @@ struct Smem {
   u32 next_ucnt;
   int next_lo, next_hi;  // the next round's start bucket (lvl + 1) bounds
   u32 next_ovf;          // the next round's overflow-list length (windows)
-  u32 lcnt[2];           // windows: lengths of the CTA's two local queues
+  u32 lcnt[3];           // windows: local-queue lengths, rotating (read, fill, clear)
   u32 nstart;            // a scan's result, shared by the CTA
 };
 // Windows of levels keep two local queues whose entries carry a vertex, the
@@ -181,6 +181,25 @@ __device__ __forceinline__ void grid_barrier(Control* ctl, u32& gen, u32 nblocks
 
 __device__ __forceinline__ u32 warp_min(u32 x) { return __reduce_min_sync(kFull, x); }
 
+// Exclusive prefix over the warp of small counts x < 2^kBits (and, in *tot,
+// their sum), by one ballot per bit instead of a chain of shuffles.
+template <int kBits>
+__device__ __forceinline__ u32 warp_excl_small(u32 x, u32* tot) {
+  const u32 lt = lanemask_lt();
+  u32 pre = 0, sum = 0;
+#pragma unroll
+  for (int b = 0; b < kBits; ++b) {
+    const u32 m = __ballot_sync(kFull, (x >> b) & 1u);
+    pre += (u32)__popc(m & lt) << b;
+    sum += (u32)__popc(m) << b;
+  }
+  *tot = sum;
+  return pre;
+}
+template <int K>
+constexpr int bits_for() { return K < 2 ? 1 : K < 4 ? 2 : K < 8 ? 3 : K < 16 ? 4 : K < 32 ? 5 : 6; }
+
+
 // First item of this warp in a grid-stride loop over groups of 32 x k items,
 // numbered so that consecutive groups go to different CTAs (warp w of CTA b
 // takes group w * gridDim.x + b): a round with fewer items than threads still
@@ -274,18 +293,12 @@ template <int K>
 __device__ __forceinline__ void warp_append_ld(u32 mask, const u32 (&v)[K], const BfsArgs& a,
                                                int qi, int qb) {
   const u32 lane = threadIdx.x & 31;
-  const u32 mine = __popc(mask);
-  u32 incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= (u32)o) incl += y;
-  }
-  const u32 tot = __shfl_sync(kFull, incl, 31);
+  u32 tot;
+  const u32 excl = warp_excl_small<bits_for<K>()>(__popc(mask), &tot);
   if (tot == 0) return;
   u32 base = 0;
   if (lane == 0) base = (u32)(atomicAdd(&a.ctl->qctr[qi], (u64)tot << 32) >> 32);
-  u32 slot = __shfl_sync(kFull, base, 0) + incl - mine;
+  u32 slot = __shfl_sync(kFull, base, 0) + excl;
 #pragma unroll
   for (int i = 0; i < K; ++i)
     if (mask >> i & 1u) a.qv[qb][slot++] = v[i];
@@ -597,20 +610,15 @@ __device__ __forceinline__ void expand_ld(const BfsArgs& a, const u32* qv_cur, u
 template <int K, int kCap>
 __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u64 (&k)[K],
                                             const int (&rs)[K], const int (&re)[K],
-                                            const BfsArgs& a, Smem& s, int nb, int qi, int qb) {
+                                            const BfsArgs& a, Smem& s, int nb, int nc, int qi,
+                                            int qb) {
   const u32 lane = threadIdx.x & 31;
-  const u32 mine = __popc(mask);
-  u32 incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= (u32)o) incl += y;
-  }
-  const u32 tot = __shfl_sync(kFull, incl, 31);
+  u32 tot;
+  const u32 excl = warp_excl_small<bits_for<K>()>(__popc(mask), &tot);
   if (tot == 0) return;
   u32 base = 0;
-  if (lane == 0) base = atomicAdd(&s.lcnt[nb], tot);
-  base = __shfl_sync(kFull, base, 0) + incl - mine;
+  if (lane == 0) base = atomicAdd(&s.lcnt[nc], tot);
+  base = __shfl_sync(kFull, base, 0) + excl;
   const LocalQueue lq = lq_buf<kCap>(s, nb);
   const u32 cap = lq_limit<kCap>(a);
   u32 spill = 0;
@@ -629,18 +637,11 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
     }
   // a full local queue: the rest waits for the next round on the overflow list
   if (!__any_sync(kFull, spill != 0u)) return;
-  const u32 smine = __popc(spill);
-  u32 sincl = smine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, sincl, o);
-    if (lane >= (u32)o) sincl += y;
-  }
-  const u32 stot = __shfl_sync(kFull, sincl, 31);
-  if (stot == 0) return;
+  u32 stot;
+  const u32 sexcl = warp_excl_small<bits_for<K>()>(__popc(spill), &stot);
   u32 sbase = 0;
   if (lane == 0) sbase = atomicAdd(&a.ctl->ovf[qi], stot);
-  sbase = __shfl_sync(kFull, sbase, 0) + sincl - smine;
+  sbase = __shfl_sync(kFull, sbase, 0) + sexcl;
 #pragma unroll
   for (int i = 0; i < K; ++i)
     if (spill >> i & 1u) {
@@ -664,7 +665,8 @@ __device__ __forceinline__ void window_push(u32 mask, const u32 (&w)[K], const u
 // this.
 template <bool U, int kCap>
 __device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool valid, u64 kv,
-                                              int rs, int re, u32 H, int nb, int qi, int qb,
+                                              int rs, int re, u32 H, int nb, int nc, int qi,
+                                              int qb,
                                               u32& myrank, u32* s_acc, u64& pushed,
                                               u64& expanded) {
   constexpr u32 kNone = 0xffffffffu;
@@ -703,7 +705,7 @@ __device__ __forceinline__ void window_expand(const BfsArgs& a, Smem& s, bool va
 #pragma unroll
     for (int q = 0; q < kLdBatch; ++q)  // the next round's bottom-up floor: level-H keys
       note_rank<U>(a, (u32)qi, ((won >> q) & 1u) && cl == H, w[q], (u32)cand, myrank, s_acc);
-    window_push<kLdBatch, kCap>(local, w, kk, wrs, wre, a, s, nb, qi, qb);
+    window_push<kLdBatch, kCap>(local, w, kk, wrs, wre, a, s, nb, nc, qi, qb);
     warp_append<kLdBatch, true>(glob, w, a, qi, qb);
   }
 }
@@ -722,6 +724,7 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
   if (threadIdx.x == 0) {
     s.lcnt[0] = 0;
     s.lcnt[1] = 0;
+    s.lcnt[2] = 0;
   }
   __syncthreads();
   // Start buckets are read one level ahead: at level lv this thread's first
@@ -746,9 +749,14 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
   u32 pu = kNoItem;  // this thread's first entry of bucket lv + 1
   if (i0 < (u32)(b1hi - b1lo)) pu = __ldg(rv + b1lo + (int)i0);
   int lb = 0;  // the local queue being read (level lv); the other one is filled
+  int cr = 0;  // the counter of the queue being read; (cr + 1) % 3 counts the filled one
   for (u32 lv = L;; ++lv) {
     const int nb = lb ^ 1;
-    const u32 nloc = min(s.lcnt[lb], lq_limit<kCap>(a));  // the same for the whole CTA
+    const int nc = cr == 2 ? 0 : cr + 1;
+    // the third counter, read last at level lv - 1 and filled next at level
+    // lv + 1, is cleared now: one CTA barrier per level
+    if (threadIdx.x == 0) s.lcnt[nc == 2 ? 0 : nc + 1] = 0;
+    const u32 nloc = min(s.lcnt[cr], lq_limit<kCap>(a));  // the same for the whole CTA
     // Past the window's last level the CTA goes on with its own queue until
     // it is empty: entries of overflow from an earlier window run behind the
     // frontier, and their chains end here instead of one hop per round.
@@ -789,7 +797,7 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
           re = __ldg(a.row_ptr + v + 1);
           ok = (u32)(kv >> 32) >= lev;  // lowered since: its lowerer pushed it again
         }
-        window_expand<U, kCap>(a, s, ok, kv, rs, re, H, nb, qi, qb, myrank, s_acc, pushed,
+        window_expand<U, kCap>(a, s, ok, kv, rs, re, H, nb, nc, qi, qb, myrank, s_acc, pushed,
                                expanded);
       }
     }
@@ -800,7 +808,7 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
         const u32 i = base + lane;
         const bool ok = i < nloc;
         window_expand<U, kCap>(a, s, ok, ok ? lq.key[i] : 0ull, ok ? (int)lq.rs[i] : 0,
-                               ok ? (int)lq.re[i] : 0, H, nb, qi, qb, myrank, s_acc, pushed,
+                               ok ? (int)lq.re[i] : 0, H, nb, nc, qi, qb, myrank, s_acc, pushed,
                                expanded);
       }
     }
@@ -828,7 +836,7 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
           start = (u32)(k[0] >> 32) == lv + 1;
         }
         if (lv + 1 < H) {
-          window_push<1, kCap>(start ? 1u : 0u, u, k, urs, ure, a, s, nb, qi, qb);
+          window_push<1, kCap>(start ? 1u : 0u, u, k, urs, ure, a, s, nb, nc, qi, qb);
         } else {
           note_rank<U>(a, (u32)qi, start, u[0], (u32)k[0], myrank, s_acc);
           warp_append<1, true>(start ? 1u : 0u, u, a, qi, qb);
@@ -836,9 +844,8 @@ __device__ __forceinline__ void window_ld(const BfsArgs& a, Smem& s, const u32* 
       }
     }
     __syncthreads();  // every push of level lv + 1 is in; level lv's queue is read
-    if (threadIdx.x == 0) s.lcnt[lb] = 0;
-    __syncthreads();
     lb = nb;
+    cr = nc;
     pu = pu2;
     b1lo = b2lo;
     b1hi = b2hi;
