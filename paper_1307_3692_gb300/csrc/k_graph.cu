@@ -549,6 +549,7 @@ struct ResArgs {
   u32* klist;            // count pass: the kept arcs' indices
   u32* n_kept;
   u32* cursor;           // write pass: next place of every row
+  const u32* cid;        // write pass: every vertex's id in G_{i+1} (its rank among kept rows)
   int* new_col;
   int* new_orig;
   int* new_src;
@@ -604,10 +605,11 @@ __global__ void __launch_bounds__(256) k_residual_write(ResArgs a) {
     const u32 e = a.klist[i];
     const u32 v = (u32)a.src[e], w = (u32)a.col[e];
     const u32 at = atomicAdd(a.cursor + v, 1u);
-    a.new_col[at] = (int)w;
+    const u32 cv = a.cid[v], cw = a.cid[w];
+    a.new_col[at] = (int)cw;
     a.new_orig[at] = a.orig ? a.orig[e] : (int)e;
-    a.new_src[at] = (int)v;
-    if (v < w) cc_unite(a.parent, w, v);
+    a.new_src[at] = (int)cv;
+    if (cv < cw) cc_unite(a.parent, cw, cv);
   }
 }
 
@@ -617,6 +619,58 @@ __global__ void __launch_bounds__(256) k_first_neighbours(const int* __restrict_
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int e0 = row_ptr[v], e1 = row_ptr[v + 1];
     first[v] = e0 < e1 ? (u32)col[e0] : 0xffffffffu;
+  }
+}
+
+// Compaction of G_{i+1} to the vertices that kept an arc.  off: the kept arcs'
+// row offsets over G_i's n vertices (off[n] = all of them).
+__global__ void __launch_bounds__(256) k_kept_flags(const int* __restrict__ off, u32 n,
+                                                    u32* flag) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x)
+    flag[v] = (v < n && off[v + 1] > off[v]) ? 1u : 0u;
+}
+
+// cid: exclusive scan of the flags (cid[n] = vertices of G_{i+1}).  Rows of
+// G_{i+1} and its vertices' ids in the input graph.
+__global__ void __launch_bounds__(256) k_compact_rows(const int* __restrict__ off,
+                                                      const u32* __restrict__ cid, u32 n,
+                                                      int* new_row, const u32* __restrict__ map,
+                                                      u32* new_map) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+    if (v == n) {
+      new_row[cid[n]] = off[n];
+    } else if (off[v + 1] > off[v]) {
+      const u32 c = cid[v];
+      new_row[c] = off[v];
+      new_map[c] = map ? map[v] : v;
+    }
+  }
+}
+
+// The shifts of G_{i+1}'s vertices, from the caller's vector over all n.
+__global__ void __launch_bounds__(256) k_gather_shifts(const double* __restrict__ full,
+                                                       const u32* __restrict__ map, u32 nc,
+                                                       double* out) {
+  for (u32 c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    out[c] = full[map[c]];
+}
+
+// Every vertex alone (center itself, distance 0), then G_{i+1}'s results in
+// the input graph's ids.
+__global__ void __launch_bounds__(256) k_blocks_alone(u32 n, int* center, int* dist) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    center[v] = (int)v;
+    dist[v] = 0;
+  }
+}
+__global__ void __launch_bounds__(256) k_blocks_scatter(const int* __restrict__ cc,
+                                                        const int* __restrict__ dc,
+                                                        const u32* __restrict__ map, u32 nc,
+                                                        int* center, int* dist) {
+  for (u32 c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    const u32 v = map[c];
+    center[v] = (int)map[cc[c]];
+    dist[v] = dc[c];
   }
 }
 
@@ -786,10 +840,10 @@ cudaError_t components_label(const int* row_ptr, u32 n, int num_sms, const CompS
 int launch_residual(bool write, const int* src, const int* col, const int* orig,
                     const int* center, u32 n, u32 m, int block, int* arc_block, u32* kept,
                     unsigned long long* up_kept, u32* klist, u32* n_kept, u32* cursor,
-                    int* new_col, int* new_orig, int* new_src, u32* parent, int num_sms,
-                    cudaStream_t s) {
-  ResArgs a{src,    col,     orig,  center, n,       m,       block,    arc_block, kept,
-            up_kept, klist,  n_kept, cursor, new_col, new_orig, new_src, parent};
+                    const u32* cid, int* new_col, int* new_orig, int* new_src, u32* parent,
+                    int num_sms, cudaStream_t s) {
+  ResArgs a{src,     col,    orig,   center, n,   m,       block,    arc_block, kept,  up_kept,
+            klist,   n_kept, cursor, cid,    new_col, new_orig, new_src, parent};
   if (write) {
     k_residual_write<<<num_sms * 4, 256, 0, s>>>(a);
   } else {
@@ -799,6 +853,31 @@ int launch_residual(bool write, const int* src, const int* col, const int* orig,
     k_residual_count<<<blocks, 256, 0, s>>>(a);
   }
   return 1;
+}
+
+int launch_kept_flags(const int* off, u32 n, u32* flag, int num_sms, cudaStream_t s) {
+  k_kept_flags<<<grid_for(n + 1, num_sms), 256, 0, s>>>(off, n, flag);
+  return 1;
+}
+
+int launch_compact_rows(const int* off, const u32* cid, u32 n, int* new_row, const u32* map,
+                        u32* new_map, int num_sms, cudaStream_t s) {
+  k_compact_rows<<<grid_for(n + 1, num_sms), 256, 0, s>>>(off, cid, n, new_row, map, new_map);
+  return 1;
+}
+
+int launch_gather_shifts(const double* full, const u32* map, u32 nc, double* out, int num_sms,
+                         cudaStream_t s) {
+  if (nc == 0) return 0;
+  k_gather_shifts<<<grid_for(nc, num_sms), 256, 0, s>>>(full, map, nc, out);
+  return 1;
+}
+
+int launch_blocks_output(const int* cc, const int* dc, const u32* map, u32 nc, u32 n, int* center,
+                         int* dist, int num_sms, cudaStream_t s) {
+  k_blocks_alone<<<grid_for(n, num_sms), 256, 0, s>>>(n, center, dist);
+  if (nc > 0) k_blocks_scatter<<<grid_for(nc, num_sms), 256, 0, s>>>(cc, dc, map, nc, center, dist);
+  return 2;
 }
 
 int launch_first_neighbours(const int* row_ptr, const int* col, u32 n, u32* first, int num_sms,

@@ -38,6 +38,9 @@ struct Blocks {
   int* col[2] = {};            // [nnz]
   int* orig[2] = {};           // [nnz] input arc id of every arc of G_i
   int* src[2] = {};            // [nnz] source vertex of every arc of G_i, i >= 1
+  u32* map[2] = {};            // [n] input id of every vertex of G_i, i >= 1
+  int* off = nullptr;          // [n + 1] kept arcs per vertex of G_i, then their offsets
+  u32* cid = nullptr;          // [n + 1] vertices with kept arcs, then their ids in G_{i+1}
   int* src0 = nullptr;         // [nnz] source vertex of every arc of G_0
   u32* klist = nullptr;        // [nnz] the count pass's kept arcs
   u32* cursor = nullptr;       // [n + 1] the write pass's next place per row
@@ -66,7 +69,10 @@ void free_blocks(ldd_graph* g) {
     cudaFree(b->col[j]);
     cudaFree(b->orig[j]);
     cudaFree(b->src[j]);
+    cudaFree(b->map[j]);
   }
+  cudaFree(b->off);
+  cudaFree(b->cid);
   cudaFree(b->src0);
   cudaFree(b->klist);
   cudaFree(b->cursor);
@@ -95,7 +101,10 @@ int setup_blocks(ldd_graph* g) {
     ok = ok && cudaMalloc(&b->row[j], (n + 1) * 4) == cudaSuccess &&
          cudaMalloc(&b->col[j], nnz * 4) == cudaSuccess &&
          cudaMalloc(&b->orig[j], nnz * 4) == cudaSuccess &&
-         cudaMalloc(&b->src[j], nnz * 4) == cudaSuccess;
+         cudaMalloc(&b->src[j], nnz * 4) == cudaSuccess &&
+         cudaMalloc(&b->map[j], std::max<size_t>(n, 1) * 4) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->off, (n + 1) * 4) == cudaSuccess &&
+       cudaMalloc(&b->cid, (n + 1) * 4) == cudaSuccess;
   ok = ok && cudaMalloc(&b->src0, nnz * 4) == cudaSuccess &&
        cudaMalloc(&b->klist, nnz * 4) == cudaSuccess &&
        cudaMalloc(&b->cursor, (n + 1) * 4) == cudaSuccess &&
@@ -221,48 +230,64 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
   const int* cur_src = B.src0;
   const int* cur_col = g->d_col;
   const int* cur_orig = nullptr;  // G_0's arcs are the input arcs
-  u32 cur_m = (u32)g->nnz;
+  const u32* cur_map = nullptr;   // G_0's vertices are the input vertices
+  u32 cur_m = (u32)g->nnz, cur_n = (u32)n;
   int blocks = 0;
   for (int i = 0; i < k; ++i) {
-    // decomposition i of G_i
+    // decomposition i of G_i, then its results over all n input vertices
     const double* d_shift = shifts[i];
     if (!is_device_ptr(shifts[i])) {
-      CUDA_TRY(cudaMemcpyAsync(cur->d_shift, shifts[i], n * 8, cudaMemcpyHostToDevice, s));
-      d_shift = cur->d_shift;
+      CUDA_TRY(cudaMemcpyAsync(g->d_shift, shifts[i], n * 8, cudaMemcpyHostToDevice, s));
+      d_shift = g->d_shift;
+    }
+    if (cur != g) {  // G_i's own vertices only
+      launch_gather_shifts(d_shift, cur_map, cur_n, r->d_shift, g->num_sms, s);
+      d_shift = r->d_shift;
     }
     const bool dev_c = out_center && is_device_ptr(out_center[i]);
     const bool dev_d = out_dist && is_device_ptr(out_dist[i]);
-    int* center = dev_c ? out_center[i] : cur->d_center;
-    int* dist = dev_d ? out_dist[i] : cur->d_dist;
+    int* center = dev_c ? out_center[i] : g->d_center;
+    int* dist = dev_d ? out_dist[i] : g->d_dist;
+    int* cur_center = cur == g ? center : r->d_center;  // in G_i's ids
     int launches = 0;
-    if ((rc = decompose_on_device(cur, d_shift, center, dist, &launches)) != LDD_OK) {
+    if ((rc = decompose_on_device(cur, d_shift, cur_center, cur == g ? dist : r->d_dist,
+                                  &launches)) != LDD_OK) {
       cudaStreamSynchronize(s);
       *out_blocks = blocks;
       return rc;
     }
+    if (cur != g)
+      launch_blocks_output(r->d_center, r->d_dist, cur_map, cur_n, (u32)n, center, dist,
+                           g->num_sms, s);
     if (out_center && !dev_c)
       CUDA_TRY(cudaMemcpyAsync(out_center[i], center, n * 4, cudaMemcpyDeviceToHost, s));
     if (out_dist && !dev_d)
       CUDA_TRY(cudaMemcpyAsync(out_dist[i], dist, n * 4, cudaMemcpyDeviceToHost, s));
     blocks = i + 1;
-    // block i and G_{i+1}; r's control block and look-back words serve the scan
+    // block i and G_{i+1}; r's control block and look-back words serve the scans
     const int j = i & 1;
     CUDA_TRY(cudaEventRecord(B.ev[2], s));
     CUDA_TRY(cudaMemsetAsync(r->d_ctl, 0, sizeof(Control), s));
-    CUDA_TRY(cudaMemsetAsync(B.row[j], 0, (n + 1) * 4, s));
+    CUDA_TRY(cudaMemsetAsync(B.off, 0, ((size_t)cur_n + 1) * 4, s));
     CUDA_TRY(cudaMemsetAsync(B.up, 0, sizeof(unsigned long long), s));
     CUDA_TRY(cudaMemsetAsync(B.n_kept, 0, 4, s));
     if (r->epoch > 0xfffff000u) {
       CUDA_TRY(cudaMemsetAsync(r->d_status, 0, r->status_bytes, s));
       r->epoch = 0;
     }
-    launch_residual(false, cur_src, cur_col, cur_orig, center, (u32)n, cur_m, i, arc_block,
-                    reinterpret_cast<u32*>(B.row[j]), B.up, B.klist, B.n_kept, nullptr, nullptr,
-                    nullptr, nullptr, nullptr, g->num_sms, s);
-    launch_exclusive_scan(reinterpret_cast<u32*>(B.row[j]), (u32)n + 1, r->d_status, &r->epoch,
+    launch_residual(false, cur_src, cur_col, cur_orig, cur_center, cur_n, cur_m, i, arc_block,
+                    reinterpret_cast<u32*>(B.off), B.up, B.klist, B.n_kept, nullptr, nullptr,
+                    nullptr, nullptr, nullptr, nullptr, g->num_sms, s);
+    launch_exclusive_scan(reinterpret_cast<u32*>(B.off), cur_n + 1, r->d_status, &r->epoch,
                           &r->d_ctl->tile_ctr[0], r->d_ctl, r->lookback_limit, s, B.cursor);
+    // G_{i+1} keeps the vertices with kept arcs, numbered in their order
+    launch_kept_flags(B.off, cur_n, B.cid, g->num_sms, s);
+    launch_exclusive_scan(B.cid, cur_n + 1, r->d_status, &r->epoch, &r->d_ctl->tile_ctr[1],
+                          r->d_ctl, r->lookback_limit, s);
     CUDA_TRY(cudaMemcpyAsync(B.h_up, B.up, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(B.h_up + 1, B.row[j] + n, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(B.h_up + 1, B.off + cur_n, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<u32*>(B.h_up + 1) + 1, B.cid + cur_n, 4,
+                             cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(r->h_hdr, r->d_ctl, 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaEventRecord(B.ev[3], s));
     CUDA_TRY(cudaGetLastError());
@@ -277,20 +302,23 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
                                  : fail(LDD_ERR_CUDA, "device error bits 0x%x", err);
     }
     const u64 edges_left = B.h_up[0];
-    const u64 arcs_left = (u32)B.h_up[1];
+    const u32 arcs_left = (u32)B.h_up[1];
+    const u32 n_next = (u32)(B.h_up[1] >> 32);
     if (out_remaining) out_remaining[i + 1] = (int64_t)edges_left;
     if (arcs_left == 0 || i + 1 == k) break;
-    // G_{i+1}: arcs, component forest, component tables
+    // G_{i+1}: rows and vertex ids, arcs, component forest, component tables
     arcs_kept += arcs_left;
     CUDA_TRY(cudaEventRecord(B.ev[2], s));
-    cudaError_t e = components_init((u32)n, g->num_sms, B.t, r->d_excl, r->d_solo, s);
+    launch_compact_rows(B.off, B.cid, cur_n, B.row[j], cur_map, B.map[j], g->num_sms, s);
+    cudaError_t e = components_init(n_next, g->num_sms, B.t, r->d_excl, r->d_solo, s);
     if (e != cudaSuccess) return fail(LDD_ERR_CUDA, "component set-up: %s", cudaGetErrorString(e));
-    launch_residual(true, cur_src, cur_col, cur_orig, center, (u32)n, cur_m, i, nullptr, nullptr,
-                    nullptr, B.klist, B.n_kept, B.cursor, B.col[j], B.orig[j], B.src[j],
-                    B.t.parent, g->num_sms, s);
+    launch_residual(true, cur_src, cur_col, cur_orig, cur_center, cur_n, cur_m, i, nullptr,
+                    nullptr, nullptr, B.klist, B.n_kept, B.cursor, B.cid, B.col[j], B.orig[j],
+                    B.src[j], B.t.parent, g->num_sms, s);
     u32 counts[4] = {0, 0, 0, 0};
-    e = components_label(B.row[j], (u32)n, g->num_sms, B.t, r->d_excl, r->d_solo, counts, s);
+    e = components_label(B.row[j], n_next, g->num_sms, B.t, r->d_excl, r->d_solo, counts, s);
     if (e != cudaSuccess) return fail(LDD_ERR_CUDA, "component labelling: %s", cudaGetErrorString(e));
+    r->n = (int32_t)n_next;
     r->sc.ncomp = counts[0];
     r->sc.total = counts[1];
     r->sc.comp_off = B.t.comp_off;
@@ -310,7 +338,9 @@ extern "C" int ldd_block_decompose(ldd_graph* g, int k, const double* betas,
     cur_src = B.src[j];
     cur_col = B.col[j];
     cur_orig = B.orig[j];
-    cur_m = (u32)arcs_left;
+    cur_map = B.map[j];
+    cur_m = arcs_left;
+    cur_n = n_next;
   }
   if (out_arc_block && !dev_blk)
     CUDA_TRY(cudaMemcpyAsync(out_arc_block, arc_block, (size_t)g->nnz * 4, cudaMemcpyDeviceToHost,

@@ -285,19 +285,34 @@ cudaError_t components_from_csr(const int* row_ptr, const int* col, u32 n, int n
                                 const CompScratch& t, u32* excl, u32* solo, u32 counts[4],
                                 cudaStream_t s);
 // Residual graphs of the block decomposition (k_graph.cu), over the m arcs of
-// G_i given as (src, col).  Count pass (write = false): kept[v] += arcs of v
-// whose ends have different centers (kept zero on entry), those arcs' indices
-// onto klist (*n_kept zero on entry; room for m), *up_kept += those with
-// v < w, and arc_block[orig ? orig[e] : e] = block for the other arcs
-// (arc_block may be null).  Write pass: every listed arc at cursor[v]++ (the
-// row offsets of G_{i+1} on entry) with its input arc id and source; each kept
-// (v, w), v < w, hooked into parent (union-find).  The order inside a row is
-// free.
+// G_i given as (src, col) on its n vertices.  Count pass (write = false):
+// kept[v] += arcs of v whose ends have different centers (kept zero on entry),
+// those arcs' indices onto klist (*n_kept zero on entry; room for m),
+// *up_kept += those with v < w, and arc_block[orig ? orig[e] : e] = block for
+// the other arcs (arc_block may be null).  Write pass: every listed arc (v, w)
+// at cursor[v]++ (G_{i+1}'s row offsets over G_i's ids on entry) as
+// (cid[v], cid[w]) -- G_{i+1}'s own ids -- with its input arc id; each kept
+// (v, w), v < w, hooked into parent (union-find on G_{i+1}'s ids).  The order
+// inside a row is free.
 int launch_residual(bool write, const int* src, const int* col, const int* orig,
                     const int* center, u32 n, u32 m, int block, int* arc_block, u32* kept,
                     unsigned long long* up_kept, u32* klist, u32* n_kept, u32* cursor,
-                    int* new_col, int* new_orig, int* new_src, u32* parent, int num_sms,
-                    cudaStream_t s);
+                    const u32* cid, int* new_col, int* new_orig, int* new_src, u32* parent,
+                    int num_sms, cudaStream_t s);
+// G_{i+1} keeps only the vertices with a kept arc.  flag[v] = 1 for them
+// (flag[n] = 0), over G_i's n vertices and the kept-arc offsets off[0 .. n].
+int launch_kept_flags(const int* off, u32 n, u32* flag, int num_sms, cudaStream_t s);
+// With cid the exclusive scan of the flags: G_{i+1}'s row offsets new_row and
+// its vertices' input ids new_map (map: G_i's, null for the input graph).
+int launch_compact_rows(const int* off, const u32* cid, u32 n, int* new_row, const u32* map,
+                        u32* new_map, int num_sms, cudaStream_t s);
+// out[c] = full[map[c]] for G_{i+1}'s nc vertices.
+int launch_gather_shifts(const double* full, const u32* map, u32 nc, double* out, int num_sms,
+                         cudaStream_t s);
+// An iteration's results over all n input vertices: every vertex alone, then
+// G_{i+1}'s nc vertices from (cc, dc) in its own ids.
+int launch_blocks_output(const int* cc, const int* dc, const u32* map, u32 nc, u32 n, int* center,
+                         int* dist, int num_sms, cudaStream_t s);
 // first[v] = col[row_ptr[v]], or ~0 for a vertex without arcs.
 int launch_first_neighbours(const int* row_ptr, const int* col, u32 n, u32* first, int num_sms,
                             cudaStream_t s);
