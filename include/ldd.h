@@ -241,8 +241,8 @@ int ldd_union_decompose(ldd_graph* u, const double* betas, const double* shifts,
  *                or k = 0).
  * Errors as in ldd_decompose; a failure in iteration i leaves the outputs of
  * earlier iterations complete and *out_blocks = the iterations that finished.
- * The first call allocates the residual graphs' buffers (about 24 bytes per
- * arc and 200 per vertex), which stay with g until ldd_destroy_graph.
+ * The first call allocates the residual graphs' buffers (about 36 bytes per
+ * arc and 220 per vertex), which stay with g until ldd_destroy_graph.
  * LDD_ERR_ARG for a union.
  */
 int ldd_block_decompose(ldd_graph* g, int k, const double* betas, const double* const* shifts,
