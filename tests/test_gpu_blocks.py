@@ -62,7 +62,7 @@ def test_golden_block_examples_on_gpu(ldd, cuda, case):
 
 GRAPHS = {
     "rmat14": lambda: gen.rmat(14),
-    "rmat17": lambda: gen.rmat(17),  # hub rows beyond 4096 arcs (one CTA per row)
+    "rmat17": lambda: gen.rmat(17),  # hub rows of thousands of arcs
     "grid2d_96x75": lambda: gen.grid2d(96, 75),
     "grid3d_20": lambda: gen.grid3d(20, 20, 20),
     "rgg_20000": lambda: gen.rgg(20000, 4),
