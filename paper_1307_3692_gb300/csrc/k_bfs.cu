@@ -44,8 +44,11 @@
 //
 // Rounds with an empty frontier jump straight to the next non-empty start
 // bucket; the loop stops as soon as every vertex with an arc is settled.
-// All device-side waits are bounded: a barrier that does not complete within
-// the spin limit sets kErrTimeout and the kernel returns.
+// Graphs whose vertices have at most kLdMaxDegree arcs run low-degree rounds
+// (a plain vertex list, a thread per frontier vertex), and a single such graph
+// relaxes up to eight levels between two grid barriers (windows of levels,
+// below).  All device-side waits are bounded: a barrier that does not complete
+// within the spin limit sets kErrTimeout and the kernel returns.
 #include <cstddef>
 
 #include "ldd_internal.cuh"
@@ -595,8 +598,11 @@ __device__ __forceinline__ void expand_ld(const BfsArgs& a, const u32* qv_cur, u
 // vertex be expanded again: it is pushed with the level it got, to a local
 // queue, to the global queue (the first time it reaches level H), or -- when
 // a local queue is full -- to the overflow list that the next round expands.
-// An entry whose vertex has meanwhile been lowered to a smaller level is
-// skipped, since its lowerer pushed it again.  A CTA may run ahead of another
+// A global-queue or overflow entry whose vertex has meanwhile been lowered to
+// a smaller level is skipped, since its lowerer pushed it again; a local entry
+// carries the key it was pushed with, and if that key is outdated, its offers
+// are dominated by those of the better one.  Past level H - 1 a CTA works its
+// local queue down until it is empty.  A CTA may run ahead of another
 // inside a window, so a vertex can first get a worse key and be expanded
 // twice (the statistics count every expansion); the result is the same.  A
 // start test inside a window may let a vertex start that a slower CTA lowers
@@ -956,8 +962,10 @@ __device__ __forceinline__ void pull_append(u32 mask, u32 keep, const u32 (&v)[K
 // or the list `cand` of ncand vertices.
 // Each lane takes kPullV candidates at a time and advances their neighbour
 // scans in lock-step, one neighbour each per step, so that up to kPullV
-// independent loads are in flight per lane.  Adds the arcs it scans and the
-// vertices it examines to the statistics.
+// independent loads are in flight per lane.  A scan's first probe is the
+// candidate's first neighbour from the per-graph table (when there is one),
+// loaded beside its key, so it needs no col round trip.  Adds the arcs it
+// scans and the vertices it examines to the statistics.
 template <bool U, bool LD, int kPullV>
 __device__ __forceinline__ void pull_round(const BfsArgs& a, int lvl, u32 minrank, u32 mslot,
                                            int qi, int qb, bool from_list, const u32* cand,
