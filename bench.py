@@ -916,8 +916,12 @@ def blocks_arm(args, dist):
     # read twice, 4 B col + 4 B input-arc id + 4 B center gather, per arc kept
     # 8 B written, per vertex and iteration about 28 B (row offsets, labels,
     # union-find)
-    res_bytes = (24 * st["block_arcs_scanned"] + 8 * st["block_arcs_kept"]
-                 + 28 * G.n * nb)
+    # count pass: per arc of G_i its source, target, block stamp and two center
+    # gathers (20 B); write pass: per kept arc the list entry, source, target
+    # and input id read, three words written (28 B); G_0's per-vertex tables
+    # (counts, offsets, flags, new ids: 28 B); later iterations' vertex passes
+    # cover only the few vertices with a kept arc
+    res_bytes = (20 * st["block_arcs_scanned"] + 28 * st["block_arcs_kept"] + 28 * G.n)
     peak, peak_kind = measured_peak_hbm()
     res_ach = res_bytes / (st["ms_block_residual"] * 1e-3) / 1e9 if st["ms_block_residual"] > 0 else 0.0
     parity = cpu = None
