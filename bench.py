@@ -912,11 +912,7 @@ def blocks_arm(args, dist):
     barrier(dist)
     ms = reduce_max(dist, sum(a.elapsed_time(b) for a, b in ev) / args.steps, dev)
     st = sts[-1]
-    # the residual passes (filter, scan, component tables) move, per arc of G_i
-    # read twice, 4 B col + 4 B input-arc id + 4 B center gather, per arc kept
-    # 8 B written, per vertex and iteration about 28 B (row offsets, labels,
-    # union-find)
-    # count pass: per arc of G_i its source, target, block stamp and two center
+    # the residual passes' algorithmic bytes.  Count pass: per arc of G_i its source, target, block stamp and two center
     # gathers (20 B); write pass: per kept arc the list entry, source, target
     # and input id read, three words written (28 B); G_0's per-vertex tables
     # (counts, offsets, flags, new ids: 28 B); later iterations' vertex passes
