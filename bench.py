@@ -912,11 +912,12 @@ def blocks_arm(args, dist):
     barrier(dist)
     ms = reduce_max(dist, sum(a.elapsed_time(b) for a, b in ev) / args.steps, dev)
     st = sts[-1]
-    # the residual passes' algorithmic bytes.  Count pass: per arc of G_i its source, target, block stamp and two center
-    # gathers (20 B); write pass: per kept arc the list entry, source, target
-    # and input id read, three words written (28 B); G_0's per-vertex tables
-    # (counts, offsets, flags, new ids: 28 B); later iterations' vertex passes
-    # cover only the few vertices with a kept arc
+    # the residual passes' algorithmic bytes.  Count pass: per arc of G_i its
+    # source, target, block stamp and two center gathers (20 B); write pass:
+    # per kept arc the list entry, source, target and input id read, three
+    # words written (28 B); G_0's per-vertex tables (counts, offsets, flags,
+    # new ids: 28 B); later iterations' vertex passes cover only the few
+    # vertices with a kept arc
     res_bytes = (20 * st["block_arcs_scanned"] + 28 * st["block_arcs_kept"] + 28 * G.n)
     peak, peak_kind = measured_peak_hbm()
     res_ach = res_bytes / (st["ms_block_residual"] * 1e-3) / 1e9 if st["ms_block_residual"] > 0 else 0.0
