@@ -155,7 +155,11 @@ int ldd_decompose_retry(ldd_graph* g, double beta, int k, const double* const* s
  *   out_dist    k pointers, each to n int32 (host or device).
  *   out_cut     NULL, or int64[k] on the host: out_cut[i] = the cut count of
  *               decomposition i, computed on the device before its labels
- *               are copied back (no upload of the labels).
+ *               are copied back (no upload of the labels).  When every
+ *               out_center is device memory, up to four decompositions'
+ *               counts come from one pass over the edges, with their labels
+ *               packed 16 bytes per vertex (about 16 n bytes more, kept with
+ *               g after the first such call).
  * Host buffers overlap with the device work only if they are page-locked
  * (cudaHostAlloc / cudaHostRegister); otherwise the copies still happen, in
  * order.  The library keeps two shift slots and two output slots (32 n bytes)

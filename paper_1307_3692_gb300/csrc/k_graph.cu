@@ -700,6 +700,132 @@ __global__ void __launch_bounds__(256) k_fill_src(const int* __restrict__ row, u
   }
 }
 
+// ---------------------------------------------------------------- fused cut counts
+// The cut counts of two to four labelings of one graph (the decompositions of
+// a pipelined batch) in one pass over the cut list.  The labelings are packed
+// per vertex into one 16-byte word, lab4[v] = (c_0[v], .., c_3[v]) with unused
+// slots 0, so that one gather per edge serves every labeling: the pass streams
+// the cut list once instead of once per labeling, and makes as many L2 sector
+// reads as a single count does.  The hot table's packed labels sit in shared
+// memory up to kHot4Smem entries; the rest are read from global memory (hot
+// vertices have many edges, so their lines stay cached).
+constexpr u32 kHot4Smem = 12288;  // 192 KiB of packed labels per CTA
+
+struct Labels4 {
+  const int* c[4];
+};
+
+__global__ void __launch_bounds__(256) k_pack_labels(Labels4 L, int K, u32 n,
+                                                     int4* __restrict__ lab4) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int4 x;
+    x.x = __ldg(L.c[0] + v);
+    x.y = K > 1 ? __ldg(L.c[1] + v) : 0;
+    x.z = K > 2 ? __ldg(L.c[2] + v) : 0;
+    x.w = K > 3 ? __ldg(L.c[3] + v) : 0;
+    lab4[v] = x;
+  }
+}
+
+// out[i] = lab4[idx[i]]: the packed labels of the hot table or of every
+// group's cold vertex; four gathers per thread in flight.
+__global__ void __launch_bounds__(256) k_gather_labels4(const u32* __restrict__ idx, u32 cnt,
+                                                        const int4* __restrict__ lab4,
+                                                        int4* __restrict__ out) {
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < cnt; i0 += stride * kLabIpt) {
+    int4 x[kLabIpt];
+#pragma unroll
+    for (int q = 0; q < kLabIpt; ++q) {
+      const u32 i = i0 + (u32)q * stride;
+      x[q] = i < cnt ? __ldg(lab4 + __ldg(idx + i)) : make_int4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < kLabIpt; ++q) {
+      const u32 i = i0 + (u32)q * stride;
+      if (i < cnt) out[i] = x[q];
+    }
+  }
+}
+
+// k_cut's pass with packed labels: every edge compares the packed labels of
+// its two endpoints and adds one to each labeling's count that differs.
+// out[0 .. K) receive the counts (added).
+__global__ void __launch_bounds__(kCutThreads, 1) k_cut4(CutList cl, const int4* __restrict__ lab4,
+                                                         const int4* __restrict__ grp4,
+                                                         const int4* __restrict__ hot4,
+                                                         u32 n_hot, int K, u64* out) {
+  extern __shared__ int4 cut_smem[];
+  __shared__ unsigned long long wsum[kCutThreads / 32][4];
+  const u32 tid = threadIdx.x, lane = tid & 31;
+  const u32 nsm = min(n_hot, kHot4Smem);
+  for (u32 i = tid; i < nsm; i += blockDim.x) cut_smem[i] = __ldg(hot4 + i);
+  __syncthreads();
+  const int4* hotv4 = reinterpret_cast<const int4*>(cl.hot);  // cudaMalloc'd: aligned
+  const u32 nchunk = (cl.m + 127) / 128;                        // 128 edges per warp step
+  const u32 stride = gridDim.x * (kCutThreads / 32);
+  u32 cnt[4] = {0, 0, 0, 0};
+  u32 c = blockIdx.x * (kCutThreads / 32) + (tid >> 5);
+  // lane's four edges: 4 lane .. 4 lane + 3 of the chunk, in block lane / 8
+  auto load = [&](u32 cc, int4& h, u32& bg, u32& bm) {
+    const u32 e0 = cc * 128 + 4 * lane;
+    if (e0 + 3 < cl.m) {
+      h = __ldcs(hotv4 + (e0 >> 2));
+    } else {
+      h.x = e0 < cl.m ? cl.hot[e0] : 0;
+      h.y = e0 + 1 < cl.m ? cl.hot[e0 + 1] : 0;
+      h.z = e0 + 2 < cl.m ? cl.hot[e0 + 2] : 0;
+      h.w = 0;
+    }
+    const u32 b = e0 >> 5;
+    bg = b < cl.nblk ? __ldg(cl.blk_g + b) : 0u;
+    bm = b < cl.nblk ? __ldg(cl.blk_mask + b) : 0u;
+  };
+  int4 h;
+  u32 bg = 0, bm = 0;
+  if (c < nchunk) load(c, h, bg, bm);
+  for (; c < nchunk; c += stride) {
+    int4 nh = make_int4(0, 0, 0, 0);
+    u32 nbg = 0, nbm = 0;
+    if (c + stride < nchunk) load(c + stride, nh, nbg, nbm);
+    const u32 e0 = c * 128 + 4 * lane, j0 = (4 * lane) & 31u;
+    const int hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (e0 + (u32)q >= cl.m) break;
+      const u32 g = bg + __popc(bm & bits_upto(j0 + (u32)q));
+      const int4 a = __ldg(grp4 + g);
+      int4 b;
+      if (hv[q] >= 0) {
+        b = __ldg(lab4 + hv[q]);
+      } else {
+        const u32 i = (u32)hv[q] & 0x7fffffffu;
+        b = i < nsm ? cut_smem[i] : __ldg(hot4 + i);
+      }
+      cnt[0] += a.x != b.x;
+      cnt[1] += a.y != b.y;
+      cnt[2] += a.z != b.z;
+      cnt[3] += a.w != b.w;
+    }
+    h = nh;
+    bg = nbg;
+    bm = nbm;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    unsigned long long t = cnt[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
+    if (lane == 0) wsum[tid >> 5][k] = t;
+  }
+  __syncthreads();
+  if (tid < (u32)K) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += wsum[w][tid];
+    if (tot) atomicAdd(reinterpret_cast<unsigned long long*>(out + tid), tot);
+  }
+}
+
 u32 grid_for(u32 n, int num_sms) {
   return (u32)max(1ll, min((long long)(n + 255) / 256, (long long)num_sms * 8));
 }
@@ -734,6 +860,34 @@ int launch_cut(const CutList& cl, const int* center, const u32* hot, u32 n_hot, 
   k_cut<false><<<g, kCutThreads, (size_t)n_hot * sizeof(int), s>>>(cl, center, hot_center, n_hot,
                                                                    out);
   return launches + 1;
+}
+
+int launch_cut4(const CutList& cl, const int* const* centers, int K, u32 n, const u32* hot,
+                u32 n_hot, int4* lab4, int4* hot4, int4* grp4, u64* out, int num_sms,
+                cudaStream_t s) {
+  if (cl.m == 0 || K < 1 || K > 4) return 0;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(k_cut4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kHot4Smem * sizeof(int4)));
+    attr_set[dev] = true;
+  }
+  Labels4 L = {{centers[0], K > 1 ? centers[1] : nullptr, K > 2 ? centers[2] : nullptr,
+                K > 3 ? centers[3] : nullptr}};
+  k_pack_labels<<<grid_for(n, num_sms), 256, 0, s>>>(L, K, n, lab4);
+  int launches = 1;
+  if (n_hot > 0) {
+    k_gather_labels4<<<grid_for((n_hot + kLabIpt - 1) / kLabIpt, num_sms), 256, 0, s>>>(
+        hot, n_hot, lab4, hot4);
+    ++launches;
+  }
+  k_gather_labels4<<<grid_for((cl.ngrp + kLabIpt - 1) / kLabIpt, num_sms), 256, 0, s>>>(
+      cl.grp_v, cl.ngrp, lab4, grp4);
+  const u32 g = (u32)max(1ll, min((long long)(cl.m + 4095) / 4096, (long long)num_sms));
+  k_cut4<<<g, kCutThreads, (size_t)min(n_hot, kHot4Smem) * sizeof(int4), s>>>(cl, lab4, grp4,
+                                                                            hot4, n_hot, K, out);
+  return launches + 2;
 }
 
 int launch_union_cut(const CutList& cl, const UnionOffsets& off, const u32* wmem,

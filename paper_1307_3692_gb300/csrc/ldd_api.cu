@@ -92,6 +92,9 @@ int free_graph_memory(ldd_graph* g) {
   if (!g->uni) cudaFree(g->d_active);  // a union's list lives in d_active_buf
   cudaFree(g->d_first);
   cudaFree(g->d_hot_center);
+  cudaFree(g->d_lab4);
+  cudaFree(g->d_hot4);
+  cudaFree(g->d_grp4);
   cudaFree(g->d_excl);
   cudaFree(g->sc.comp_off);
   cudaFree(g->sc.comp_len);
@@ -854,6 +857,24 @@ int enqueue_bfs_finalize(ldd_graph* g, int* center, int* dist, int* launches) {
   return LDD_OK;
 }
 
+// Packed-label buffers of the fused cut counts of a batch, allocated on first use.
+int ensure_cut4(ldd_graph* g) {
+  if (g->d_lab4) return LDD_OK;
+  const size_t n = std::max<size_t>((size_t)g->n, 1), nh = std::max<size_t>(g->n_hot, 1),
+               ng = std::max<size_t>(g->cut.ngrp, 1);
+  if (cudaMalloc(&g->d_lab4, n * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&g->d_hot4, nh * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&g->d_grp4, ng * sizeof(int4)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g->d_lab4);
+    cudaFree(g->d_hot4);
+    cudaFree(g->d_grp4);
+    g->d_lab4 = g->d_hot4 = g->d_grp4 = nullptr;
+    return fail(LDD_ERR_OOM, "packed labels for the fused cut counts: allocation failed");
+  }
+  return LDD_OK;
+}
+
 // Pinned headers and the device / pinned cut counts of a batch of k.
 int ensure_batch_headers(ldd_graph* g, int k) {
   if (g->h_bhdr_cap >= k) return LDD_OK;
@@ -1518,10 +1539,21 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
     cudaStreamSynchronize(s);
     return status;
   };
-  // cut counts run on their own stream, each overlapping the next
-  // decomposition's rank; a round loop waits for the previous cut count, so
-  // that it runs alone and the output slot that cut count reads is free
+  // cut counts run on their own stream, W labelings to a pass over the cut
+  // list: a wave of W consecutive decompositions.  With every output on the
+  // device, W = 4 and one pass (launch_cut4) counts a wave after its last
+  // finalize.  With outputs in the two host-side slots, W = 1: each cut count
+  // overlaps the next decomposition's rank instead, which took less time than
+  // waves of two (the second pass of a wave waits for the next round loop).
+  // A round loop waits for the last wave's pass, so that it runs alone and
+  // the output slot that pass reads is free again.
   const bool cuts = out_cut != nullptr;
+  bool all_dev_c = true;
+  for (int i = 0; i < k; ++i) all_dev_c = all_dev_c && is_device_ptr(out_center[i]);
+  const int W = cuts && k > 1 && all_dev_c ? 4 : 1;
+  const int* wave_c[4] = {};
+  int nwave = 0, waves = 0, last_cut = -1;
+  if (W > 1 && (rc = ensure_cut4(g)) != LDD_OK) return rc;
   if (cuts) {
     CUDA_TRY(cudaMemsetAsync(g->d_bcut, 0, (size_t)k * sizeof(u64), s));
     for (int j = 0; j < 2; ++j) CUDA_TRY(cudaEventRecord(g->ev_cut[j], s));
@@ -1542,7 +1574,7 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
     if ((rc = enqueue_rank(g, dev_in ? shifts[i] : d_in[j], &launches,
                            pieces ? &first : nullptr)) != LDD_OK)
       return drain(rc);
-    if (cuts && i > 0) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_cut[(i - 1) & 1], 0));
+    if (cuts && last_cut >= 0) CUDA_TRY(cudaStreamWaitEvent(s, g->ev_cut[last_cut], 0));
     if ((rc = enqueue_bfs_finalize(g, center, dist, &launches)) != LDD_OK) return drain(rc);
     CUDA_TRY(cudaMemcpyAsync(g->h_bhdr + (size_t)i * sizeof(Header), g->d_ctl, sizeof(Header),
                              cudaMemcpyDeviceToHost, s));
@@ -1556,11 +1588,21 @@ int ldd_decompose_batch(ldd_graph* g, int k, const double* betas, const double* 
       CUDA_TRY(cudaEventRecord(g->ev_out[j], g->copy_out));
     }
     if (cuts) {
-      CUDA_TRY(cudaStreamWaitEvent(g->cut_stream, g->ev_used[j], 0));
-      launches += launch_cut(g->cut, center, g->d_hot, g->n_hot, g->d_hot_center, g->d_bcut + i,
-                             g->num_sms, g->cut_stream);
-      CUDA_TRY(cudaGetLastError());
-      CUDA_TRY(cudaEventRecord(g->ev_cut[j], g->cut_stream));
+      wave_c[nwave++] = center;
+      if (nwave == W || i == k - 1) {  // the wave's last finalize is queued: count its cuts
+        CUDA_TRY(cudaStreamWaitEvent(g->cut_stream, g->ev_used[j], 0));
+        u64* out = g->d_bcut + (i + 1 - nwave);
+        if (nwave == 1)
+          launches += launch_cut(g->cut, wave_c[0], g->d_hot, g->n_hot, g->d_hot_center, out,
+                                 g->num_sms, g->cut_stream);
+        else
+          launches += launch_cut4(g->cut, wave_c, nwave, (u32)n, g->d_hot, g->n_hot, g->d_lab4,
+                                  g->d_hot4, g->d_grp4, out, g->num_sms, g->cut_stream);
+        CUDA_TRY(cudaGetLastError());
+        last_cut = waves++ & 1;
+        CUDA_TRY(cudaEventRecord(g->ev_cut[last_cut], g->cut_stream));
+        nwave = 0;
+      }
     }
   }
   if (cuts)

@@ -89,6 +89,9 @@ struct ldd_graph {
   u32* d_first = nullptr;      // first neighbour of every vertex (single graphs)
   u32* d_hot = nullptr;        // hot table: the n_hot highest-degree vertices
   int* d_hot_center = nullptr; // their labels, gathered per cut count
+  int4* d_lab4 = nullptr;      // batches: up to four labelings packed per vertex (fused cut counts)
+  int4* d_hot4 = nullptr;      // ... the hot table's packed labels
+  int4* d_grp4 = nullptr;      // ... every cut-list group's packed cold label
   u32 n_hot = 0;
   u32* d_excl = nullptr;      // bit v: v is not handled by the BFS (no arcs or a small component)
   u32* d_solo = nullptr;      // bit v: v is alone in its component (inside the d_excl allocation)
@@ -217,5 +220,14 @@ int union_fill(ldd_graph* u, int k, ldd_graph* const* members, cudaStream_t s, b
 // members' cut counts into u's d_cut; outputs in the caller layout (device).
 int union_run(ldd_graph* u, const double* d_in, int* center, int* dist, bool want_cut,
               int* launches_out, int* cut_launches_out);
+
+// Cut counts (Definition 1.1) of K = 1 .. 4 labelings centers[0 .. K) of one
+// graph in one pass over its cut list (k_graph.cu): the labelings are packed
+// into lab4 [n], the hot table's and the groups' packed labels gathered into
+// hot4 [n_hot] and grp4 [cl.ngrp], and out[i] += the count of labeling i.
+// Returns the kernels queued on s.
+int launch_cut4(const CutList& cl, const int* const* centers, int K, u32 n, const u32* hot,
+                u32 n_hot, int4* lab4, int4* hot4, int4* grp4, u64* out, int num_sms,
+                cudaStream_t s);
 
 }  // namespace ldd

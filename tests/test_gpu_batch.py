@@ -147,3 +147,32 @@ def test_batch_first_vector_in_pieces_needs_the_exact_rank(ldd, cuda):
         assert np.array_equal(cen[i].numpy(), oc) and np.array_equal(dis[i].numpy(), od), f"item {i}"
         assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc)
     g.close()
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_batch_cut_counts_in_waves(ldd, cuda, where):
+    """With device outputs the cut counts of a batch are counted a wave of up to
+    four labelings at a time (k = 5: a wave of four, then one of one); with host
+    outputs one at a time.  Every count must equal the oracle's, with a hot
+    table larger than the part a CTA keeps in shared memory (R-MAT 15: 32,768
+    hot slots)."""
+    G = gen.rmat(15)
+    betas = [0.02, 0.1, 0.5, 0.2, 0.05]
+    items = [gen.shifts(G.n, b, 70 + i) for i, b in enumerate(betas)]
+    if where == "device":
+        sh = [torch.from_numpy(x).to(cuda) for x in items]
+        cen = [torch.empty(G.n, dtype=torch.int32, device=cuda) for _ in items]
+        dis = [torch.empty(G.n, dtype=torch.int32, device=cuda) for _ in items]
+    else:
+        sh = items
+        cen = [np.empty(G.n, np.int32) for _ in items]
+        dis = [np.empty(G.n, np.int32) for _ in items]
+    g = ldd.LddGraph(G.row_ptr, G.col)
+    for k in (5, 4, 3, 2):
+        cuts = g.decompose_batch(betas[:k], sh[:k], cen[:k], dis[:k])
+        for i in range(k):
+            oc, od = oracle.oracle_ldd(G.row_ptr, G.col, items[i])
+            c = cen[i].cpu().numpy() if where == "device" else cen[i]
+            assert np.array_equal(c, oc), f"k {k} item {i}: center"
+            assert cuts[i] == oracle.oracle_cut_edges(G.row_ptr, G.col, oc), f"k {k} item {i}: cut"
+    g.close()
