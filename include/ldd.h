@@ -158,8 +158,8 @@ int ldd_decompose_retry(ldd_graph* g, double beta, int k, const double* const* s
  *               are copied back (no upload of the labels).  When every
  *               out_center is device memory, up to four decompositions'
  *               counts come from one pass over the edges, with their labels
- *               packed 16 bytes per vertex (about 16 n bytes more, kept with
- *               g after the first such call).
+ *               packed 16 bytes per vertex and per cut-list group (at most
+ *               32 n bytes more, kept with g after the first such call).
  * Host buffers overlap with the device work only if they are page-locked
  * (cudaHostAlloc / cudaHostRegister); otherwise the copies still happen, in
  * order.  The library keeps two shift slots and two output slots (32 n bytes)
