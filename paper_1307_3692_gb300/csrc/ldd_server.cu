@@ -20,9 +20,10 @@
 // loop, a cooperative kernel that occupies every SM: the workspaces share a
 // gate (BfsGate, ldd_graph.cuh), so each round loop waits on the event of the
 // one enqueued before it.  One batch's rank, finalize, cut count and copies
-// thus overlap another's, requests that arrive while a batch is on the GPU
-// are admitted to the next batch as soon as a slot and memory are free, and
-// no worker holds a lock while the device runs its work.
+// thus overlap another's, and requests that arrive while a batch is on the
+// GPU are admitted to the next batch as soon as a slot and memory are free.
+// A worker holds no lock while the device runs a union batch; a batch of one
+// holds the gate for its whole call (run_alone).
 //
 // A batch that fails on a request's input (a bad shift) is rerun request by
 // request, so only that request fails.
